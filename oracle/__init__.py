@@ -1,0 +1,242 @@
+"""FP64 CPU oracle of the PnP-MS2G hot path — TEST INFRASTRUCTURE ONLY.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package.  The product library (``paper_2203_07308_gb300``)
+never imports, links or calls it, and it imports nothing from the product.
+
+The arithmetic lives in ``pnp_oracle.c`` (plain C99, double precision, a naive
+ray march for A and a naive scatter for A^T); this module compiles it with gcc
+into ``oracle/_lib/`` and exposes numpy-level wrappers.  Each wrapper cites the
+part of the paper it follows.
+
+Parity status per function (what pins it, see ``tests/test_oracle_pins.py``):
+  project / backproject   pinned (Gaussian-blob and paraboloid closed forms,
+                           axis-ray row sums, dense matrix built two ways,
+                           adjoint identity)
+  pool / unpool           pinned (closed forms, adjoint identity)
+  grad                    pinned (finite differences, subset-mean identity)
+  power_iter              pinned (dense eigenvalue)
+  fgp                     pinned at convergence (1-D step closed form,
+                           independent primal-dual solve) and at 20 iterations
+                           (generic dense FISTA on the dual problem)
+  pnp_run                 pinned for one and four iterations against a dense
+                           restatement of Algorithm 1; longer trajectories rest
+                           on those step identities
+The mutation tests (tests/test_oracle_mutations.py) plant sixteen plausible
+mistakes in a copy of pnp_oracle.c and check that these pins catch each one.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pnp_oracle.c")
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB = os.path.join(_LIBDIR, "libpnp_oracle.so")
+# The mutation tests point this at a deliberately broken build of pnp_oracle.c
+# to show that the pins catch plausible mistakes.
+_LIB_OVERRIDE = os.environ.get("PNP_ORACLE_LIB")
+_lock = threading.Lock()
+_lib = None
+
+
+class OrcGeom(C.Structure):
+    _fields_ = [("n", C.c_int), ("n_views", C.c_int), ("n_det", C.c_int), ("batch", C.c_int),
+                ("dso", C.c_double), ("ddo", C.c_double), ("pitch", C.c_double),
+                ("angle0", C.c_double), ("span", C.c_double), ("step", C.c_double)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP over rays of the forward projector)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            if _LIB_OVERRIDE:
+                lib = C.CDLL(_LIB_OVERRIDE)
+            else:
+                build()
+                lib = C.CDLL(_LIB)
+            dp = C.POINTER(C.c_double)
+            gp = C.POINTER(OrcGeom)
+            ip = C.POINTER(C.c_int)
+            lib.orc_ray.argtypes = [gp, C.c_int, C.c_int, dp]
+            lib.orc_subset_views.argtypes = [gp, C.c_int, C.c_int]
+            lib.orc_subset_views.restype = C.c_int
+            lib.orc_project.argtypes = [gp, C.c_int, dp, dp, dp, C.c_int, C.c_int]
+            lib.orc_backproject.argtypes = [gp, C.c_int, dp, dp, C.c_int, C.c_int]
+            lib.orc_pool.argtypes = [C.c_int, C.c_int, dp, dp]
+            lib.orc_unpool.argtypes = [C.c_int, C.c_int, dp, dp]
+            lib.orc_grad.argtypes = [gp, C.c_int, dp, dp, dp, C.c_int, C.c_int]
+            lib.orc_fgp.argtypes = [C.c_int, dp, C.c_double, C.c_int, dp]
+            lib.orc_tv.argtypes = [C.c_int, dp]
+            lib.orc_tv.restype = C.c_double
+            lib.orc_power_iter.argtypes = [gp, C.c_int, C.c_int, C.c_double, ip]
+            lib.orc_power_iter.restype = C.c_double
+            lib.orc_psnr.argtypes = [C.c_long, dp, dp]
+            lib.orc_psnr.restype = C.c_double
+            lib.orc_pnp_run.argtypes = [gp, C.c_int, ip, dp, ip, dp, dp, C.c_double, C.c_double,
+                                        C.c_int, C.c_int, dp, dp]
+            lib.orc_objective.argtypes = [gp, dp, dp, dp]
+            lib.orc_sample_count.argtypes = [gp, C.c_int, C.c_int, C.c_int]
+            lib.orc_sample_count.restype = C.c_double
+            _lib = lib
+    return _lib
+
+
+def _dp(a: Optional[np.ndarray]):
+    if a is None:
+        return C.POINTER(C.c_double)()
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def geom(g) -> OrcGeom:
+    """Oracle geometry record from any object with the ``pnp_geom`` field names."""
+    return OrcGeom(int(g.n), int(g.n_views), int(g.n_det), int(getattr(g, "batch", 1)),
+                   float(g.dso), float(g.ddo), float(g.det_pitch), float(g.angle0),
+                   float(g.angle_span), float(g.step))
+
+
+def ray(g, v: int, j: int) -> np.ndarray:
+    """(S_x, S_y, d_x, d_y, F_x, F_y): source, unit direction and foot point of ray (v, j)."""
+    out = np.zeros(6)
+    _load().orc_ray(C.byref(geom(g)), v, j, _dp(out))
+    return out
+
+
+def subset_views(g, p: int, P: int) -> int:
+    return _load().orc_subset_views(C.byref(geom(g)), p, P)
+
+
+def project(g, s: int, img, b=None, p: int = 0, P: int = 1) -> np.ndarray:
+    """A_s^{(p)} img (minus b^{(p)} if given); Eq. 1 / Eq. 4, Alg. 1 Option 2 rows."""
+    lib = _load()
+    gg = geom(g)
+    img = _f64(img)
+    nsub = lib.orc_subset_views(C.byref(gg), p, P)
+    out = np.zeros((nsub, g.n_det))
+    bb = None if b is None else _f64(b)
+    lib.orc_project(C.byref(gg), s, _dp(img), _dp(bb), _dp(out), p, P)
+    return out
+
+
+def backproject(g, s: int, sino, p: int = 0, P: int = 1) -> np.ndarray:
+    """A_s^{(p)T} sino by scatter (transpose of ``project``)."""
+    ns = g.n // s
+    out = np.zeros((ns, ns))
+    sino = _f64(sino)
+    _load().orc_backproject(C.byref(geom(g)), s, _dp(sino), _dp(out), p, P)
+    return out
+
+
+def pool(fine, s: int) -> np.ndarray:
+    """Sketch S: s x s average pooling (Eq. 4's S, read as average pooling)."""
+    fine = _f64(fine)
+    n = fine.shape[-1]
+    out = np.zeros((n // s, n // s))
+    _load().orc_pool(n, s, _dp(fine), _dp(out))
+    return out
+
+
+def unpool(coarse, s: int) -> np.ndarray:
+    """Upsampler U = S^T (replicate / s^2)."""
+    coarse = _f64(coarse)
+    n = coarse.shape[-1] * s
+    out = np.zeros((n, n))
+    _load().orc_unpool(n, s, _dp(coarse), _dp(out))
+    return out
+
+
+def grad(g, s: int, y, b, p: int = 0, P: int = 1) -> np.ndarray:
+    """c S^T A_s^{(p)T}(A_s^{(p)} S y - b^{(p)}), c = max(P, 1) (Alg. 1 G, U = S^T)."""
+    y = _f64(y)
+    b = _f64(b)
+    out = np.zeros((g.n, g.n))
+    _load().orc_grad(C.byref(geom(g)), s, _dp(y), _dp(b), _dp(out), p, P)
+    return out
+
+
+def fgp(z, lam: float, iters: int) -> np.ndarray:
+    """TV-prox denoiser by FGP (Beck & Teboulle 2009), ``iters`` iterations."""
+    z = _f64(z)
+    out = np.zeros_like(z)
+    _load().orc_fgp(z.shape[-1], _dp(z), float(lam), int(iters), _dp(out))
+    return out
+
+
+def tv(x) -> float:
+    x = _f64(x)
+    return float(_load().orc_tv(x.shape[-1], _dp(x)))
+
+
+def power_iter(g, s: int, max_iters: int = 100, tol: float = 1e-7):
+    """(L, iterations): L = ||A_s S||^2 by power iteration (Sec. 3's eta = O(1/L))."""
+    it = C.c_int(0)
+    L = _load().orc_power_iter(C.byref(geom(g)), s, max_iters, tol, C.byref(it))
+    return float(L), int(it.value)
+
+
+def psnr(x, xt) -> float:
+    x = _f64(x)
+    xt = _f64(xt)
+    return float(_load().orc_psnr(x.size, _dp(x), _dp(xt)))
+
+
+def pnp_run(g, stages: Sequence, eta: Sequence[float], seq, b, x0=None, *, alpha: float = 1.0,
+            lam: float = 0.02, tv_iters: int = 20, momentum: bool = True, xt=None):
+    """Algorithm 1 on one image; returns (x, psnr_log or None)."""
+    st = np.ascontiguousarray(np.array([[s.factor, s.iters, s.n_subsets] if hasattr(s, "factor")
+                                         else list(s) for s in stages], dtype=np.int32).ravel())
+    total = int(sum(st[1::3]))
+    seq = np.ascontiguousarray(np.asarray(seq, dtype=np.int32))
+    if seq.size < total:
+        seq = np.concatenate([seq, np.zeros(total - seq.size, np.int32)])
+    eta = _f64(eta)
+    b = _f64(b)
+    x = np.zeros((g.n, g.n)) if x0 is None else _f64(x0).copy()
+    xt_ = None if xt is None else _f64(xt)
+    log = np.zeros(total) if xt is not None else None
+    ip = C.POINTER(C.c_int)
+    _load().orc_pnp_run(C.byref(geom(g)), len(st) // 3, st.ctypes.data_as(ip), _dp(eta),
+                        seq.ctypes.data_as(ip), _dp(b), _dp(x), float(alpha), float(lam),
+                        int(tv_iters), int(bool(momentum)), _dp(xt_), _dp(log))
+    return x, log
+
+
+def objective(g, x, b):
+    """(1/2 ||A x - b||^2, TV(x))."""
+    out = np.zeros(2)
+    x = _f64(x)
+    b = _f64(b)
+    _load().orc_objective(C.byref(geom(g)), _dp(x), _dp(b), _dp(out))
+    return float(out[0]), float(out[1])
+
+
+def sample_count(g, s: int = 1, p: int = 0, P: int = 1) -> float:
+    """Exact number of samples inside the support box over the subset's rays."""
+    return float(_load().orc_sample_count(C.byref(geom(g)), s, p, P))
+
+
+def simulate(g, x_true, w, noise_rel: float):
+    """b = A x_true + sigma w with sigma = noise_rel * max|A x_true| (Eq. 1)."""
+    ax = project(g, 1, x_true)
+    return ax + noise_rel * np.abs(ax).max() * _f64(w).reshape(ax.shape)

@@ -1,0 +1,444 @@
+/*
+ * FP64 CPU oracle of the PnP-MS2G hot path (arXiv 2203.07308).
+ *
+ * TEST INFRASTRUCTURE ONLY.  The product library never includes, links or calls
+ * this file; only the test suite, the smoke check and the benchmark's CPU
+ * baseline leg do.  It is written to be read against the paper, not to be fast:
+ * double precision everywhere, a naive ray march for A, a naive *scatter* for
+ * A^T (the CUDA path uses a pixel-driven gather instead, so the two cannot share
+ * a failure mode), and no blocking, fusion or reordering.
+ *
+ * What it computes
+ *   Eq. 1    measurement model b = A x + w: the forward operator A (fan-beam,
+ *            ray-driven, fixed step, bilinear taps) and its transpose A^T.
+ *   Eq. 4    the sketched objective f(b, A_s S x): S = s x s average pooling,
+ *            A_s = the same fan beam on the grid of pixel size s.
+ *   Alg. 1   the multi-stage loop: v = S_k(y), G (Option 1 or Option 2 with
+ *            angle subsets), z = y - eta U_k G, x = (1-a) z + a D(z),
+ *            y = x + a_i (x - x_prev), with U_k = S_k^T.
+ *   Eq. 5    the PnP proximal-gradient special case (one stage, s = 1, a_i = 0).
+ *   Sec. 3   step size eta = 1/L with L = ||A_s S||^2 (power iteration) and the
+ *            convergent-FISTA momentum a_i = (i-1)/(i+3).
+ *   Beck & Teboulle 2009 (the paper's TV reference): FGP for the TV-prox
+ *            denoiser D(z) = argmin 1/2||x - z||^2 + lambda TV_iso(x).
+ *
+ * Readings (the paper names fan-beam CT but no discretisation):
+ *   grid     level-s image has n_s = n/s pixels per side, pixel size s (fine px),
+ *            pixel (ix,iy) centred at ((ix-(n_s-1)/2) s, (iy-(n_s-1)/2) s),
+ *            stored row-major img[iy*n_s + ix].
+ *   source   view v at beta = angle0 + span*v/n_views, source dso (cos, sin),
+ *            flat detector centred at -ddo (cos, sin), axis (-sin, cos), bin j at
+ *            u_j = (j - (n_det-1)/2) pitch.
+ *   samples  ray (v,j) with unit direction d and foot point F (nearest point to
+ *            the origin); samples q_k = F + (k+1/2) delta d for every integer k,
+ *            delta = step*s; each sample weighs delta.
+ *   interp   bilinear, zero outside the image:
+ *            f(q) = sum_p img[p] hat((q_x-c_px)/s) hat((q_y-c_py)/s),
+ *            hat(t) = max(0, 1-|t|).
+ *   subsets  subset p of P holds views v = p, p+P, p+2P, ...; its sinogram rows
+ *            are those views in increasing order; the minibatch gradient is
+ *            scaled by P so that its mean over p is the full gradient.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int n, n_views, n_det, batch;
+    double dso, ddo, pitch, angle0, span, step;
+} orc_geom;
+
+static double hat(double t)
+{
+    double a = 1.0 - fabs(t);
+    return a > 0.0 ? a : 0.0;
+}
+
+/* Source position and unit ray direction of ray (v, j), centred fine-px coords. */
+void orc_ray(const orc_geom *g, int v, int j, double out[6])
+{
+    double beta = g->angle0 + g->span * (double)v / (double)g->n_views;
+    double cb = cos(beta), sb = sin(beta);
+    double sx = g->dso * cb, sy = g->dso * sb;
+    double u = ((double)j - 0.5 * (double)(g->n_det - 1)) * g->pitch;
+    double px = -g->ddo * cb - u * sb;
+    double py = -g->ddo * sb + u * cb;
+    double ex = px - sx, ey = py - sy;
+    double len = sqrt(ex * ex + ey * ey);
+    double dx = ex / len, dy = ey / len;
+    double sd = sx * dx + sy * dy;            /* foot point F = S - (S.d) d */
+    out[0] = sx;
+    out[1] = sy;
+    out[2] = dx;
+    out[3] = dy;
+    out[4] = sx - sd * dx;
+    out[5] = sy - sd * dy;
+}
+
+/* Number of views in subset p of P. */
+int orc_subset_views(const orc_geom *g, int p, int P)
+{
+    if (P <= 1) return g->n_views;
+    return (g->n_views - p + P - 1) / P;
+}
+
+/* Bilinear interpolant of a level-s image at centred point (qx, qy). */
+static double interp(const double *img, int ns, double s, double qx, double qy)
+{
+    double X = qx / s + 0.5 * (ns - 1), Y = qy / s + 0.5 * (ns - 1);
+    double fx = floor(X), fy = floor(Y);
+    double val = 0.0;
+    for (int b = 0; b < 2; ++b) {
+        for (int a = 0; a < 2; ++a) {
+            double ix = fx + a, iy = fy + b;
+            if (ix < 0 || iy < 0 || ix > ns - 1 || iy > ns - 1) continue;
+            double w = hat(X - ix) * hat(Y - iy);
+            val += w * img[(long)iy * ns + (long)ix];
+        }
+    }
+    return val;
+}
+
+/* Adjoint of interp: add wt * hat * hat into the (up to) four taps. */
+static void scatter(double *img, int ns, double s, double qx, double qy, double wt)
+{
+    double X = qx / s + 0.5 * (ns - 1), Y = qy / s + 0.5 * (ns - 1);
+    double fx = floor(X), fy = floor(Y);
+    for (int b = 0; b < 2; ++b) {
+        for (int a = 0; a < 2; ++a) {
+            double ix = fx + a, iy = fy + b;
+            if (ix < 0 || iy < 0 || ix > ns - 1 || iy > ns - 1) continue;
+            double w = hat(X - ix) * hat(Y - iy);
+            img[(long)iy * ns + (long)ix] += wt * w;
+        }
+    }
+}
+
+/* Sample index bound: every sample with |k| >= K lies outside the support box
+ * (|x|,|y| < (n_s/2 + 1/2) s), where the interpolant is zero. */
+static long sample_bound(const orc_geom *g, int s)
+{
+    int ns = g->n / s;
+    double H = (0.5 * ns + 0.5) * s;
+    double delta = g->step * s;
+    return (long)ceil(sqrt(2.0) * H / delta) + 2;
+}
+
+/* One row of A_s applied to img: delta * sum_k f(q_k). */
+static double ray_sum(const orc_geom *g, int s, const double *img, int v, int j)
+{
+    double r[6];
+    orc_ray(g, v, j, r);
+    int ns = g->n / s;
+    double delta = g->step * s;
+    long K = sample_bound(g, s);
+    double acc = 0.0;
+    for (long k = -K; k < K; ++k) {
+        double t = ((double)k + 0.5) * delta;
+        acc += interp(img, ns, s, r[4] + t * r[2], r[5] + t * r[3]);
+    }
+    return delta * acc;
+}
+
+/* A_s^{(p)} img: sino[vs*n_det + j] for the subset's views in increasing order.
+ * P <= 1 means all views.  b (nullable, full sinogram [n_views][n_det]) is
+ * subtracted row by row, giving the residual A_s^{(p)} v - b^{(p)}. */
+void orc_project(const orc_geom *g, int s, const double *img, const double *b,
+                 double *sino, int p, int P)
+{
+    int nsub = orc_subset_views(g, p, P);
+    int step = P <= 1 ? 1 : P;
+    int first = P <= 1 ? 0 : p;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int vs = 0; vs < nsub; ++vs) {
+        int v = first + vs * step;
+        for (int j = 0; j < g->n_det; ++j) {
+            double val = ray_sum(g, s, img, v, j);
+            if (b) val -= b[(long)v * g->n_det + j];
+            sino[(long)vs * g->n_det + j] = val;
+        }
+    }
+}
+
+/* A_s^{(p)T} sino by scatter: every sample of every ray adds its weighted ray
+ * value into the pixels whose hat functions cover it. */
+void orc_backproject(const orc_geom *g, int s, const double *sino, double *img, int p, int P)
+{
+    int ns = g->n / s;
+    int nsub = orc_subset_views(g, p, P);
+    int step = P <= 1 ? 1 : P;
+    int first = P <= 1 ? 0 : p;
+    double delta = g->step * s;
+    long K = sample_bound(g, s);
+    memset(img, 0, sizeof(double) * (size_t)ns * ns);
+    for (int vs = 0; vs < nsub; ++vs) {
+        int v = first + vs * step;
+        for (int j = 0; j < g->n_det; ++j) {
+            double r[6];
+            orc_ray(g, v, j, r);
+            double val = sino[(long)vs * g->n_det + j];
+            if (val == 0.0) continue;
+            for (long k = -K; k < K; ++k) {
+                double t = ((double)k + 0.5) * delta;
+                scatter(img, ns, s, r[4] + t * r[2], r[5] + t * r[3], delta * val);
+            }
+        }
+    }
+}
+
+/* Sketch S: s x s average pooling, fine [n][n] -> coarse [n/s][n/s]. */
+void orc_pool(int n, int s, const double *fine, double *coarse)
+{
+    int ns = n / s;
+    for (int cy = 0; cy < ns; ++cy) {
+        for (int cx = 0; cx < ns; ++cx) {
+            double acc = 0.0;
+            for (int b = 0; b < s; ++b)
+                for (int a = 0; a < s; ++a)
+                    acc += fine[(long)(cy * s + b) * n + (cx * s + a)];
+            coarse[(long)cy * ns + cx] = acc / (double)(s * s);
+        }
+    }
+}
+
+/* Upsampler U = S^T: replicate each coarse value over its s x s block, / s^2. */
+void orc_unpool(int n, int s, const double *coarse, double *fine)
+{
+    int ns = n / s;
+    for (int y = 0; y < n; ++y)
+        for (int x = 0; x < n; ++x)
+            fine[(long)y * n + x] = coarse[(long)(y / s) * ns + (x / s)] / (double)(s * s);
+}
+
+/* Gradient estimate on the fine grid (Alg. 1, Option 1 for P<=1, Option 2 with
+ * angle subset p of P otherwise):
+ *     g = c * S^T A_s^{(p)T} (A_s^{(p)} S y - b^{(p)}),   c = max(P, 1).
+ * For s = 1 and P <= 1 this is the full gradient A^T (A y - b) of Eq. 5. */
+void orc_grad(const orc_geom *g, int s, const double *y, const double *b, double *grad,
+              int p, int P)
+{
+    int n = g->n, ns = n / s;
+    int nsub = orc_subset_views(g, p, P);
+    double *v = malloc(sizeof(double) * (size_t)ns * ns);
+    double *res = malloc(sizeof(double) * (size_t)nsub * g->n_det);
+    double *gc = malloc(sizeof(double) * (size_t)ns * ns);
+    orc_pool(n, s, y, v);
+    orc_project(g, s, v, b, res, p, P);
+    orc_backproject(g, s, res, gc, p, P);
+    orc_unpool(n, s, gc, grad);
+    double c = P <= 1 ? 1.0 : (double)P;
+    for (long i = 0; i < (long)n * n; ++i) grad[i] *= c;
+    free(v);
+    free(res);
+    free(gc);
+}
+
+/* ---------------- TV prox by FGP (Beck & Teboulle 2009) -------------------
+ * Dual variables (p, q) live on the m x m grid; p[i][j] pairs rows i and i+1
+ * (zero on the last row), q[i][j] pairs columns j and j+1 (zero on the last
+ * column).  L(p,q)[i][j] = p[i][j] + q[i][j] - p[i-1][j] - q[i][j-1];
+ * L^T(x) = (x[i][j] - x[i+1][j], x[i][j] - x[i][j+1]).  Isotropic projection
+ * (p,q)/max(1, sqrt(p^2+q^2)).  No box constraint (P_C = identity).         */
+static void tv_L(int m, const double *p, const double *q, double *out)
+{
+    for (int i = 0; i < m; ++i) {
+        for (int j = 0; j < m; ++j) {
+            double v = p[i * m + j] + q[i * m + j];
+            if (i > 0) v -= p[(i - 1) * m + j];
+            if (j > 0) v -= q[i * m + j - 1];
+            out[i * m + j] = v;
+        }
+    }
+}
+
+static void tv_LT(int m, const double *x, double *p, double *q)
+{
+    for (int i = 0; i < m; ++i) {
+        for (int j = 0; j < m; ++j) {
+            p[i * m + j] = i < m - 1 ? x[i * m + j] - x[(i + 1) * m + j] : 0.0;
+            q[i * m + j] = j < m - 1 ? x[i * m + j] - x[i * m + j + 1] : 0.0;
+        }
+    }
+}
+
+/* x = FGP_lambda^iters(z) on one m x m image. */
+void orc_fgp(int m, const double *z, double lambda, int iters, double *x)
+{
+    size_t N = (size_t)m * m;
+    if (lambda <= 0.0 || iters <= 0) {
+        memcpy(x, z, sizeof(double) * N);
+        return;
+    }
+    double *pk = calloc(N, sizeof(double)), *qk = calloc(N, sizeof(double));
+    double *pp = calloc(N, sizeof(double)), *qp = calloc(N, sizeof(double));
+    double *r = calloc(N, sizeof(double)), *sv = calloc(N, sizeof(double));
+    double *w = malloc(sizeof(double) * N), *gp = malloc(sizeof(double) * N),
+           *gq = malloc(sizeof(double) * N);
+    double t = 1.0;
+    for (int k = 1; k <= iters; ++k) {
+        /* (p_k, q_k) = P_P[(r_k, s_k) + 1/(8 lambda) L^T(z - lambda L(r_k, s_k))] */
+        tv_L(m, r, sv, w);
+        for (size_t i = 0; i < N; ++i) w[i] = z[i] - lambda * w[i];
+        tv_LT(m, w, gp, gq);
+        for (size_t i = 0; i < N; ++i) {
+            double a = r[i] + gp[i] / (8.0 * lambda);
+            double c = sv[i] + gq[i] / (8.0 * lambda);
+            double nrm = sqrt(a * a + c * c);
+            double den = nrm > 1.0 ? nrm : 1.0;
+            pk[i] = a / den;
+            qk[i] = c / den;
+        }
+        /* t_{k+1} and the momentum point (r_{k+1}, s_{k+1}) */
+        double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        double mom = (t - 1.0) / tn;
+        for (size_t i = 0; i < N; ++i) {
+            r[i] = pk[i] + mom * (pk[i] - pp[i]);
+            sv[i] = qk[i] + mom * (qk[i] - qp[i]);
+            pp[i] = pk[i];
+            qp[i] = qk[i];
+        }
+        t = tn;
+    }
+    /* x = z - lambda L(p_N, q_N) */
+    tv_L(m, pp, qp, w);
+    for (size_t i = 0; i < N; ++i) x[i] = z[i] - lambda * w[i];
+    free(pk); free(qk); free(pp); free(qp); free(r); free(sv); free(w); free(gp); free(gq);
+}
+
+/* Isotropic TV with forward differences and zero differences past the edge. */
+double orc_tv(int m, const double *x)
+{
+    double acc = 0.0;
+    for (int i = 0; i < m; ++i) {
+        for (int j = 0; j < m; ++j) {
+            double a = i < m - 1 ? x[(i + 1) * m + j] - x[i * m + j] : 0.0;
+            double c = j < m - 1 ? x[i * m + j + 1] - x[i * m + j] : 0.0;
+            acc += sqrt(a * a + c * c);
+        }
+    }
+    return acc;
+}
+
+/* L = ||A_s S||^2 by power iteration on S^T A_s^T A_s S from the normalised
+ * all-ones vector; stops when the Rayleigh quotient changes by less than tol
+ * (relative) or after max_iters.  Returns L; *iters_out = iterations used. */
+double orc_power_iter(const orc_geom *g, int s, int max_iters, double tol, int *iters_out)
+{
+    int n = g->n, ns = n / s;
+    size_t N = (size_t)n * n;
+    double *u = malloc(sizeof(double) * N), *w = malloc(sizeof(double) * N);
+    double *v = malloc(sizeof(double) * (size_t)ns * ns), *gc = malloc(sizeof(double) * (size_t)ns * ns);
+    double *res = malloc(sizeof(double) * (size_t)g->n_views * g->n_det);
+    for (size_t i = 0; i < N; ++i) u[i] = 1.0 / sqrt((double)N);
+    double lam = 0.0;
+    int it = 0;
+    for (it = 1; it <= max_iters; ++it) {
+        orc_pool(n, s, u, v);
+        orc_project(g, s, v, NULL, res, 0, 1);
+        orc_backproject(g, s, res, gc, 0, 1);
+        orc_unpool(n, s, gc, w);
+        double rq = 0.0, nw = 0.0;
+        for (size_t i = 0; i < N; ++i) {
+            rq += u[i] * w[i];
+            nw += w[i] * w[i];
+        }
+        nw = sqrt(nw);
+        for (size_t i = 0; i < N; ++i) u[i] = w[i] / nw;
+        int done = it > 1 && fabs(rq - lam) <= tol * fabs(rq);
+        lam = rq;
+        if (done) break;
+    }
+    if (iters_out) *iters_out = it > max_iters ? max_iters : it;
+    free(u); free(w); free(v); free(gc); free(res);
+    return lam;
+}
+
+double orc_psnr(long count, const double *x, const double *xt)
+{
+    double mse = 0.0;
+    for (long i = 0; i < count; ++i) mse += (x[i] - xt[i]) * (x[i] - xt[i]);
+    mse /= (double)count;
+    return 10.0 * log10(1.0 / mse);
+}
+
+/* Algorithm 1 (PnP-MS2G) on one image.
+ *   stages      n_stages triples (factor s_k, iterations N_k, subsets P_k)
+ *   eta         per-stage step sizes eta_k
+ *   seq         subset id of every iteration (length sum N_k)
+ *   x           in: x_0 (= y_0); out: x after the last iteration
+ *   momentum    0: a_i = 0 (PnP proximal gradient, Eq. 5); 1: a_i = (i-1)/(i+3)
+ *   xt, psnr    optional ground truth and per-iteration PSNR log
+ * Iteration i = 1, 2, ...:  v = S_k y_{i-1};  G per Option 1/2;
+ *   z_i = y_{i-1} - eta_k S_k^T G;  x_i = (1-alpha) z_i + alpha D(z_i);
+ *   y_i = x_i + a_i (x_i - x_{i-1}).                                          */
+void orc_pnp_run(const orc_geom *g, int n_stages, const int *stages, const double *eta,
+                 const int *seq, const double *b, double *x, double alpha, double lambda,
+                 int tv_iters, int momentum, const double *xt, double *psnr)
+{
+    int n = g->n;
+    size_t N = (size_t)n * n;
+    double *y = malloc(sizeof(double) * N), *xprev = malloc(sizeof(double) * N);
+    double *z = malloc(sizeof(double) * N), *gr = malloc(sizeof(double) * N);
+    double *dz = malloc(sizeof(double) * N);
+    memcpy(y, x, sizeof(double) * N);
+    memcpy(xprev, x, sizeof(double) * N);
+    int i = 0;
+    for (int k = 0; k < n_stages; ++k) {
+        int s = stages[3 * k], Nk = stages[3 * k + 1], P = stages[3 * k + 2];
+        for (int jj = 0; jj < Nk; ++jj) {
+            i += 1;
+            int p = P > 1 ? seq[i - 1] : 0;
+            orc_grad(g, s, y, b, gr, p, P);
+            for (size_t q = 0; q < N; ++q) z[q] = y[q] - eta[k] * gr[q];
+            orc_fgp(n, z, lambda, tv_iters, dz);
+            double a = momentum ? (double)(i - 1) / (double)(i + 3) : 0.0;
+            for (size_t q = 0; q < N; ++q) {
+                double xn = (1.0 - alpha) * z[q] + alpha * dz[q];
+                y[q] = xn + a * (xn - xprev[q]);
+                xprev[q] = xn;
+            }
+            if (xt && psnr) psnr[i - 1] = orc_psnr((long)N, xprev, xt);
+        }
+    }
+    memcpy(x, xprev, sizeof(double) * N);
+    free(y); free(xprev); free(z); free(gr); free(dz);
+}
+
+/* Objective terms: 1/2 ||A x - b||^2 and TV(x) (Eq. 2 with f least squares). */
+void orc_objective(const orc_geom *g, const double *x, const double *b, double out[2])
+{
+    size_t M = (size_t)g->n_views * g->n_det;
+    double *res = malloc(sizeof(double) * M);
+    orc_project(g, 1, x, b, res, 0, 1);
+    double f = 0.0;
+    for (size_t i = 0; i < M; ++i) f += res[i] * res[i];
+    out[0] = 0.5 * f;
+    out[1] = orc_tv(g->n, x);
+    free(res);
+}
+
+/* Number of samples with a nonzero-support position along every ray of the
+ * subset (the exact Joseph sample count used for GRay-samples/s): samples
+ * strictly inside the box |x|,|y| < (n_s/2 + 1/2) s. */
+double orc_sample_count(const orc_geom *g, int s, int p, int P)
+{
+    int ns = g->n / s;
+    int nsub = orc_subset_views(g, p, P);
+    int step = P <= 1 ? 1 : P;
+    int first = P <= 1 ? 0 : p;
+    double H = (0.5 * ns + 0.5) * s, delta = g->step * s;
+    long K = sample_bound(g, s);
+    double count = 0.0;
+    for (int vs = 0; vs < nsub; ++vs) {
+        for (int j = 0; j < g->n_det; ++j) {
+            double r[6];
+            orc_ray(g, first + vs * step, j, r);
+            for (long k = -K; k < K; ++k) {
+                double t = ((double)k + 0.5) * delta;
+                double qx = r[4] + t * r[2], qy = r[5] + t * r[3];
+                if (fabs(qx) < H && fabs(qy) < H) count += 1.0;
+            }
+        }
+    }
+    return count;
+}

@@ -1,0 +1,56 @@
+"""Plants plausible mistakes in a copy of the oracle's C source (on the CPU) and
+checks that the pins in test_oracle_pins.py catch every one of them."""
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "pnp_oracle.c")
+
+# (name, original text, mutated text)
+MUTATIONS = [
+    ("transposed image in interp", "val += w * img[(long)iy * ns + (long)ix];",
+     "val += w * img[(long)ix * ns + (long)iy];"),
+    ("dropped sample weight", "return delta * acc;", "return acc;"),
+    ("foot point sign", "out[4] = sx - sd * dx;", "out[4] = sx + sd * dx;"),
+    ("detector centre offset", "u = ((double)j - 0.5 * (double)(g->n_det - 1)) * g->pitch;",
+     "u = ((double)j - 0.5 * (double)(g->n_det)) * g->pitch;"),
+    ("view angle direction", "double beta = g->angle0 + g->span * (double)v / (double)g->n_views;",
+     "double beta = g->angle0 - g->span * (double)v / (double)g->n_views;"),
+    ("transposed scatter", "img[(long)iy * ns + (long)ix] += wt * w;",
+     "img[(long)ix * ns + (long)iy] += wt * w;"),
+    ("unpool without 1/s^2", "fine[(long)y * n + x] = coarse[(long)(y / s) * ns + (x / s)] / (double)(s * s);",
+     "fine[(long)y * n + x] = coarse[(long)(y / s) * ns + (x / s)];"),
+    ("pool index swap", "acc += fine[(long)(cy * s + b) * n + (cx * s + a)];",
+     "acc += fine[(long)(cx * s + b) * n + (cy * s + a)];"),
+    ("subset scale dropped", "double c = P <= 1 ? 1.0 : (double)P;", "double c = 1.0;"),
+    ("fgp dual step", "double a = r[i] + gp[i] / (8.0 * lambda);", "double a = r[i] + gp[i] / (4.0 * lambda);"),
+    ("fgp momentum dropped", "double mom = (t - 1.0) / tn;", "double mom = 0.0;"),
+    ("fgp divergence sign", "if (i > 0) v -= p[(i - 1) * m + j];", "if (i > 0) v += p[(i - 1) * m + j];"),
+    ("fgp anisotropic projection", "double nrm = sqrt(a * a + c * c);", "double nrm = fabs(a) + fabs(c);"),
+    ("pnp momentum index", "double a = momentum ? (double)(i - 1) / (double)(i + 3) : 0.0;",
+     "double a = momentum ? (double)(i) / (double)(i + 3) : 0.0;"),
+    ("relaxation swapped", "double xn = (1.0 - alpha) * z[q] + alpha * dz[q];",
+     "double xn = alpha * z[q] + (1.0 - alpha) * dz[q];"),
+    ("power iteration unnormalised", "for (size_t i = 0; i < N; ++i) u[i] = w[i] / nw;",
+     "for (size_t i = 0; i < N; ++i) u[i] = w[i];"),
+]
+
+
+@pytest.mark.parametrize("name,orig,mut", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(name, orig, mut, tmp_path):
+    src = open(SRC).read()
+    assert src.count(orig) == 1, f"mutation anchor not found once: {name}"
+    msrc = tmp_path / "mut.c"
+    msrc.write_text(src.replace(orig, mut))
+    lib = tmp_path / "libmut.so"
+    subprocess.run(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", "-o", str(lib),
+                    str(msrc), "-lm"], check=True)
+    env = dict(os.environ, PNP_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
