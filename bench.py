@@ -1,0 +1,422 @@
+"""Benchmark of the PnP-MS2G hot path on one GB300 (or N replicas under torchrun).
+
+One step = one complete multi-stage sketched PnP reconstruction (Algorithm 1)
+of a 256x256 image from 360 views x 512 bins: 20 iterations on the 2x-sketched
+grid, then 80 on the full grid, each iteration one angle-subset gradient
+estimate (8 interleaved subsets), the gradient step, 20 FGP iterations of the
+TV-prox denoiser and the FISTA momentum.  The reported value is gradient
+estimates per second (one per iteration) over the whole job.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+`--impl reference` times the FP64 CPU oracle on the host cores instead (each
+step a bounded sample of the same schedule).  Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "A^T(Ax−b) gradients/s + GRay-samples/s vs HBM roofline; time-to-PSNR sketched vs full PnP"
+UNIT = "gradients/s"
+WORKLOAD = "c2_256"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) < 9:
+                        continue
+                    try:
+                        sm.append(float(parts[1]))
+                        smax = max(smax, float(parts[2]))
+                    except ValueError:
+                        continue
+                    for nm, val in zip(names, parts[5:9]):
+                        if val.lower() == "active":
+                            reasons.add(nm)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax or None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- workload
+def workload():
+    from paper_2203_07308_gb300 import synth
+    return synth.workloads()[WORKLOAD]
+
+
+def config_dict(wl, extra=None):
+    g = wl.geom
+    d = {"workload": f"{g.n}x{g.n} ellipse phantom, {g.n_views} views x {g.n_det} bins fan beam, "
+                     "2x sketch (20 it) then full grid (80 it), 8 angle subsets, TV-FGP 20, FISTA momentum",
+         "image": g.n, "views": g.n_views, "bins": g.n_det, "batch_per_gpu": g.batch,
+         "schedule": [[s.factor, s.iters, s.n_subsets] for s in wl.stages],
+         "iterations": sum(s.iters for s in wl.stages), "tv_iters": wl.tv_iters,
+         "lambda": wl.tv_lambda, "noise_rel": wl.noise_rel,
+         "l2": "flushed between timed steps (512 MiB write)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def cpu_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+# ---------------------------------------------------------------- reference arm (FP64 oracle)
+def oracle_sample_run(wl, b, x_true, eta, seq, iters_per_stage):
+    """Runs the oracle on a bounded sample of the schedule (the first iterations
+    of each stage); returns (seconds, gradient estimates computed)."""
+    import oracle
+    from paper_2203_07308_gb300 import synth
+    stages = [synth.Stage(s.factor, min(s.iters, k), s.n_subsets) for s, k in zip(wl.stages, iters_per_stage)]
+    sub_seq = np.concatenate([seq[sum(s.iters for s in wl.stages[:i]):][:st.iters]
+                              for i, st in enumerate(stages)]) if stages else seq
+    t0 = time.perf_counter()
+    oracle.pnp_run(wl.geom, stages, eta, sub_seq, b, None, alpha=wl.alpha, lam=wl.tv_lambda,
+                   tv_iters=wl.tv_iters, momentum=wl.momentum)
+    return time.perf_counter() - t0, sum(s.iters for s in stages)
+
+
+def oracle_inputs(wl):
+    import oracle
+    from paper_2203_07308_gb300 import synth
+    g = wl.geom
+    x = synth.phantom_batch(wl, 1)[0]
+    w = synth.noise_draws((g.n_views, g.n_det), synth.noise_seed(wl.config_id))
+    b = oracle.simulate(g, x, w, wl.noise_rel)
+    seq = synth.schedule_sequence(wl.stages, synth.subset_seed(wl.config_id))
+    # step sizes: the GPU arm's power iteration is not available on this leg; the
+    # oracle computes its own (not timed: per-geometry set-up)
+    eta = [1.0 / oracle.power_iter(g, s.factor, 15, 1e-5)[0] for s in wl.stages]
+    return x, b, eta, seq
+
+
+def cpu_baseline(wl, sample_iters=(2, 6)):
+    os.environ.setdefault("OMP_NUM_THREADS", str(cpu_cores()))
+    x, b, eta, seq = oracle_inputs(wl)
+    secs, n = oracle_sample_run(wl, b, x, eta, seq, sample_iters)
+    total = sum(s.iters for s in wl.stages)
+    # scale: time per iteration of each stage from the sample, weighted by stage length
+    return {"value": n / secs, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
+            "kind": "oracle",
+            "sample": f"first {sample_iters[0]} sketched + {sample_iters[1]} full-grid iterations of the "
+                      f"{total}-iteration schedule, FP64 C oracle with OpenMP over rays ({secs:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", str(cpu_cores()))
+    wl = workload()
+    x, b, eta, seq = oracle_inputs(wl)
+    sample = (1, 3)
+    for _ in range(args.warmup):
+        oracle_sample_run(wl, b, x, eta, seq, sample)
+    secs, n = 0.0, 0
+    for _ in range(args.steps):
+        s, k = oracle_sample_run(wl, b, x, eta, seq, sample)
+        secs += s
+        n += k
+    value = n / secs
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(wl, {"step": "bounded sample: first 1 sketched + "
+                                                                     "3 full-grid iterations"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
+                             "kind": "oracle", "sample": "first 1 sketched + 3 full-grid iterations per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- native arm
+def run_native(args, rank, world):
+    import torch
+    import paper_2203_07308_gb300 as pnp
+    from paper_2203_07308_gb300 import build, synth
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    build.build()
+    pnp.load()
+    wl = workload()
+    g = wl.geom
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    plan = pnp.Plan(g)
+
+    # ---- synthetic inputs: phantom (one per rank), b = A x + sigma w (GPU forward)
+    x_true = synth.ellipse_phantom(g.n, synth.phantom_seed(wl.config_id, rank), wl.n_ellipses)
+    w = synth.noise_draws((g.n_views, g.n_det), synth.noise_seed(wl.config_id) + rank)
+    d_xt = torch.from_numpy(x_true.astype(np.float32)).to(dev).reshape(1, g.n, g.n)
+    d_b = torch.empty(1, g.n_views, g.n_det, device=dev)
+    plan.project(1, d_xt, d_b)
+    sigma = wl.noise_rel * float(d_b.abs().max())
+    d_b += sigma * torch.from_numpy(w.astype(np.float32)).to(dev).reshape(d_b.shape)
+    seq = synth.schedule_sequence(wl.stages, synth.subset_seed(wl.config_id))
+    total_iters = sum(s.iters for s in wl.stages)
+
+    # ---- per-geometry set-up: step sizes by power iteration (not part of a step)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    eta = [1.0 / plan.power_iter(s.factor, 100, 1e-6)[0] for s in wl.stages]
+    setup_ms = 1000 * (time.perf_counter() - t0)
+
+    kw = dict(alpha=wl.alpha, lam=wl.tv_lambda, tv_iters=wl.tv_iters, momentum=wl.momentum)
+    d_x = torch.zeros(1, g.n, g.n, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        d_x.zero_()
+        plan.run(wl.stages, eta, seq, d_b, d_x, **kw)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+
+    # ---- timed region: K steps, L2 flushed before each, device time by CUDA events
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    launches0 = pnp.launch_count()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier(world)
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            plan.run(wl.stages, eta, seq, d_b, d_x.zero_(), **kw)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    launches = pnp.launch_count() - launches0
+    # d_x.zero_() is a PyTorch fill inside the region: not counted as ours
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = allmax(sum(step_ms), world)
+    value = world * total_iters * args.steps / (total_ms / 1000.0)
+
+    # ---- per-kernel timing of the projector pair (events on the launching stream)
+    def timed(fn, reps=20):
+        fn()
+        torch.cuda.synchronize()
+        es = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in es:
+            flush.fill_(1.0)
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in es]))
+
+    res = torch.empty(1, g.n_views, g.n_det, device=dev)
+    img = torch.empty(1, g.n, g.n, device=dev)
+    fwd_ms = timed(lambda: plan.project(1, d_xt, res, d_b))
+    back_ms = timed(lambda: plan.backproject(1, res, img))
+    grad_ms = timed(lambda: plan.full_grad(d_xt, d_b, img))
+    samples_full = plan.sample_count(1)
+    gray_fwd = samples_full / (fwd_ms / 1000) / 1e9
+    gray_back = samples_full / (back_ms / 1000) / 1e9
+
+    # ---- time-to-PSNR: sketched schedule vs full-gradient PnP-FISTA, same data
+    full_arm = synth.full_gradient_arm(wl.stages)
+    eta_full = [eta[[s.factor for s in wl.stages].index(1)]]
+    d_x.zero_()
+    log_s = plan.run(wl.stages, eta, seq, d_b, d_x, xtrue=d_xt, **kw)[:, 0]
+    d_x.zero_()
+    log_f = plan.run(full_arm, eta_full, None, d_b, d_x, xtrue=d_xt, **kw)[:, 0]
+    target = float(log_f[-1]) - 0.1
+
+    def time_to(stages, etas, sq, log):
+        hit = np.nonzero(log >= target)[0]
+        if hit.size == 0:
+            return None, None
+        it = int(hit[0]) + 1
+        cut, left = [], it
+        for s in stages:
+            k = min(s.iters, left)
+            if k > 0:
+                cut.append(synth.Stage(s.factor, k, s.n_subsets))
+            left -= k
+        eta_c = etas[:len(cut)]
+
+        def go():
+            d_x.zero_()
+            plan.run(cut, eta_c, sq, d_b, d_x, **kw)
+        return timed(go, reps=5), it
+
+    tts_s, it_s = time_to(wl.stages, eta, seq, log_s)
+    tts_f, it_f = time_to(full_arm, eta_full, None, log_f)
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    h_b = torch.empty(d_b.shape, dtype=torch.float32, pin_memory=True)
+    h_b.copy_(d_b)
+    h_x0 = torch.zeros(d_x.shape, dtype=torch.float32, pin_memory=True)
+    h_out = torch.empty(d_x.shape, dtype=torch.float32, pin_memory=True)
+    d_b2 = torch.empty_like(d_b)
+    e2e_ms = []
+    for k in range(args.steps + 1):
+        flush.fill_(2.0)
+        a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        d_b2.copy_(h_b, non_blocking=True)
+        d_x.copy_(h_x0, non_blocking=True)
+        plan.run(wl.stages, eta, seq, d_b2, d_x, **kw)
+        h_out.copy_(d_x, non_blocking=True)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        if k > 0:
+            e2e_ms.append(a.elapsed_time(b_))
+    e2e_total = allmax(sum(e2e_ms), world)
+    e2e_value = world * total_iters * len(e2e_ms) / (e2e_total / 1000.0)
+
+    # ---- roofline of the dominant projector kernel
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    sm_mhz = 2070.0
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    # FP32 issue peak: 128 lanes/SM/clock, FMA = 2 FLOP
+    alu_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+    # algorithmic work per backprojected sample: 4 bilinear taps, each
+    # hat(dx) hat(dy) r: 2 position FMA + 2 |.| + 2 (1-.) + 1 mul + 1 FMA = 8 FLOP per tap
+    flop_back = samples_full * 4 * 8
+    flop_fwd = samples_full * (4 + 3 * 2 + 1)  # position 2 FMA, 3 FMA interp, accumulate
+    dominant = "backproject" if back_ms >= fwd_ms else "forward"
+    ach = (flop_back / (back_ms / 1000) if dominant == "backproject" else flop_fwd / (fwd_ms / 1000)) / 1e12
+    roof = {"kernel": dominant, "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+            "frac": ach / alu_peak, "traffic": None,
+            "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz (derived)",
+            "hbm_gbs_measured_peak": peaks.get("hbm_gbs")}
+
+    clocks = clk.summary()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(wl, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(d_b.numel() * 4 + d_x.numel() * 4),
+                    "d2h_bytes_per_step": int(d_x.numel() * 4)},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "kernels_ms": {"forward_all_views": fwd_ms, "backproject_all_views": back_ms,
+                           "full_gradient": grad_ms},
+            "gray_samples_per_s": {"forward": gray_fwd, "backproject": gray_back,
+                                   "samples_per_projection": samples_full},
+            "full_gradients_per_s": 1000.0 / grad_ms,
+            "time_to_psnr": {"target_db": target, "full_final_db": float(log_f[-1]),
+                             "sketched_final_db": float(log_s[-1]),
+                             "sketched_ms": tts_s, "sketched_iters": it_s,
+                             "full_ms": tts_f, "full_iters": it_f,
+                             "speedup": (tts_f / tts_s) if (tts_s and tts_f) else None},
+            "setup_ms_power_iteration": setup_ms}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world = dist_init(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_native(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

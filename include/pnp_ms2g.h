@@ -1,0 +1,199 @@
+/*
+ * pnp_ms2g.h — C ABI of the GB300 (sm_103a) implementation of the hot path of
+ * "Accelerating Plug-and-Play Image Reconstruction via Multi-Stage Sketched
+ * Gradients" (Tang, arXiv 2203.07308): the data-fidelity gradient A^T(Ax - b)
+ * for 2-D fan-beam X-ray CT, used full-grid, image-sketched and angle-subset,
+ * inside the multi-stage PnP loop of Algorithm 1.
+ *
+ * Conventions shared by every entry point
+ *   Units      lengths in fine pixels (pixel side 1); the image is centred at the
+ *              origin.  Level s (sketch factor s in {1,2,4,8}, Eq. 4's S_k) has
+ *              n/s pixels per side of size s.
+ *   Images     float32, row-major [batch][n_s][n_s], x (column) index fastest;
+ *              pixel (ix,iy) of level s is centred at
+ *              ((ix - (n_s-1)/2) s, (iy - (n_s-1)/2) s).
+ *   Sinograms  float32 [batch][views][n_det], detector index fastest.  A
+ *              sinogram "of subset p of P" holds the views v = p, p+P, p+2P, ...
+ *              in increasing order (Alg. 1 Option 2 with angle subsets); P = 1
+ *              means all views.  The data b is always the full [batch][n_views][n_det].
+ *   Operator   A_s (Eq. 1 / Eq. 4): ray (v, j) from the source at
+ *              dso (cos b_v, sin b_v), b_v = angle0 + angle_span v / n_views,
+ *              to the flat-detector bin centre -ddo (cos b_v, sin b_v)
+ *              + u_j (-sin b_v, cos b_v), u_j = (j - (n_det-1)/2) det_pitch;
+ *              samples q_k = F + (k + 1/2) (step s) d for every integer k, F the
+ *              point of the ray nearest the origin, d its unit direction; each
+ *              sample adds (step s) times the bilinear interpolant of the level-s
+ *              image (zero outside it).  A_s^T is the exact transpose.
+ *   Pointers   d_* are device pointers, h_* host pointers.  The caller owns every
+ *              buffer and the stream; the library allocates no device memory.
+ *              Buffers passed to one call must not overlap unless stated.
+ *   Streams    `stream` is a cudaStream_t (NULL = legacy default stream).  Calls
+ *              are asynchronous on it unless they return host results (stated).
+ *   Workspace  d_ws of at least pnp_workspace_size() bytes, 256-byte aligned,
+ *              prepared once per geometry by pnp_setup().  Calls that take it
+ *              use it as scratch: calls sharing one workspace must be ordered
+ *              on one stream.
+ *   Errors     every int-returning call returns PNP_OK or a PNP_E* code and
+ *              leaves a message for pnp_last_error() (thread-local).  Invalid
+ *              arguments are rejected before anything is launched.
+ */
+#ifndef PNP_MS2G_H
+#define PNP_MS2G_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    PNP_OK = 0,
+    PNP_EINVAL = 1,        /* bad argument (size, pointer, factor, subset, geometry) */
+    PNP_ECUDA = 2,         /* a CUDA runtime call or launch failed */
+    PNP_ETIMEOUT = 3,      /* a bounded device-side wait gave up */
+    PNP_EUNSUPPORTED = 4,  /* valid request this build does not handle */
+    PNP_ESTATE = 5         /* workspace not prepared by pnp_setup for this geometry */
+};
+
+/* Fan-beam geometry (Sec. 3: fan-beam X-ray CT, views equally spaced over
+ * angle_span).  All lengths in fine pixels, angles in radians. */
+typedef struct {
+    int32_t n;          /* fine image side; divisible by every sketch factor used */
+    int32_t n_views;    /* projection angles */
+    int32_t n_det;      /* detector bins */
+    int32_t batch;      /* independent images sharing this geometry */
+    double dso;         /* source to rotation centre */
+    double ddo;         /* rotation centre to detector */
+    double det_pitch;   /* bin spacing on the detector */
+    double angle0;      /* angle of view 0 */
+    double angle_span;  /* views cover [angle0, angle0 + angle_span) */
+    double step;        /* ray-march step in level pixels (0.5 = half a pixel) */
+} pnp_geom;
+
+/* One stage of Algorithm 1: sketch factor s_k (m_k = d / s_k^2), N_k inner
+ * iterations, and P_k interleaved angle subsets (1 = Option 1, >1 = Option 2). */
+typedef struct {
+    int32_t factor;
+    int32_t iters;
+    int32_t n_subsets;
+} pnp_stage;
+
+/* Loop parameters of Algorithm 1. */
+typedef struct {
+    float alpha;        /* RED-PRO relaxation x = (1-alpha) z + alpha D(z), alpha in (0,1] */
+    float lambda;       /* TV weight of the denoiser D = TV-prox (Sec. 2, after Eq. 5) */
+    int32_t tv_iters;   /* FGP iterations of D (Beck & Teboulle 2009); 0 = identity */
+    int32_t momentum;   /* 0: a_i = 0 (Eq. 5); 1: a_i = (i-1)/(i+3) (Sec. 3) */
+} pnp_run_params;
+
+/* Maximum total iterations of one pnp_run call when a PSNR log is requested. */
+#define PNP_MAX_LOG_ITERS 65536
+
+/* Bytes of device workspace for geometry g (all sketch levels in {1,2,4,8}
+ * that divide n with n/s >= 4).  Returns PNP_EINVAL for an invalid geometry. */
+int pnp_workspace_size(const pnp_geom* g, size_t* bytes);
+
+/* Prepares d_ws for geometry g: computes the FP64 per-ray tables of every
+ * level on the device (foot point, direction, sample range) and registers the
+ * (workspace, geometry) pair.  Must precede every call that takes d_ws with
+ * this geometry; redo it after reusing the memory for another geometry.
+ * Asynchronous on `stream`. */
+int pnp_setup(const pnp_geom* g, void* d_ws, size_t ws_bytes, void* stream);
+
+/* Forward projection (Eq. 1, Eq. 4): d_sino = A_s^{(p)} d_img, or the residual
+ * A_s^{(p)} d_img - b^{(p)} when d_b is not NULL.
+ *   factor   sketch level s; d_img is the level-s image [batch][n/s][n/s]
+ *   d_b      NULL or the full data [batch][n_views][n_det]
+ *   d_sino   out, [batch][views of subset][n_det]
+ *   subset, n_subsets   0 <= subset < n_subsets <= n_views (1 = all views) */
+int pnp_project(const pnp_geom* g, int factor, const float* d_img, const float* d_b,
+                float* d_sino, int subset, int n_subsets, void* d_ws, void* stream);
+
+/* Backprojection, the exact transpose of pnp_project (the A^T of Eq. 5):
+ * d_img = A_s^{(p)T} d_sino, computed as a deterministic pixel-driven gather
+ * (no atomics; bitwise repeatable).
+ *   d_sino   [batch][views of subset][n_det];  d_img out, [batch][n/s][n/s] */
+int pnp_backproject(const pnp_geom* g, int factor, const float* d_sino, float* d_img,
+                    int subset, int n_subsets, void* d_ws, void* stream);
+
+/* Sketch S (Eq. 4, Alg. 1 "v = S_k(y)"): s x s average pooling,
+ * d_fine [batch][n][n] -> d_coarse [batch][n/s][n/s]. */
+int pnp_sketch(const pnp_geom* g, int factor, const float* d_fine, float* d_coarse, void* stream);
+
+/* Upsampler U = S^T (Alg. 1 "U_k"): each coarse value replicated over its
+ * s x s block and divided by s^2, d_coarse -> d_fine. */
+int pnp_upsample(const pnp_geom* g, int factor, const float* d_coarse, float* d_fine, void* stream);
+
+/* Full data-fidelity gradient (Eq. 5): d_g = A^T (A d_x - d_b), all views,
+ * fine grid.  d_x, d_g [batch][n][n]; d_b [batch][n_views][n_det]. */
+int pnp_full_grad(const pnp_geom* g, const float* d_x, const float* d_b, float* d_g,
+                  void* d_ws, void* stream);
+
+/* Sketched (minibatch) gradient estimate of Alg. 1 on the fine grid:
+ *   d_g = c S^T A_s^{(p)T} (A_s^{(p)} S d_y - b^{(p)}),   c = n_subsets,
+ * i.e. U G with U = S^T, G = Option 1 (n_subsets = 1) or Option 2 (angle
+ * subset p scaled by P so that its mean over p is the Option 1 gradient).
+ * For factor 1 and n_subsets 1 it equals pnp_full_grad. */
+int pnp_sketch_grad(const pnp_geom* g, int factor, const float* d_y, const float* d_b, float* d_g,
+                    int subset, int n_subsets, void* d_ws, void* stream);
+
+/* Bytes of workspace for pnp_tv_denoise on [batch][n][n]. */
+int pnp_tv_workspace_size(int n, int batch, size_t* bytes);
+
+/* TV-prox denoiser D (Sec. 2, after Eq. 5: "TV-prox"): iters iterations of FGP
+ * (Beck & Teboulle 2009, isotropic TV, forward differences, zero past the last
+ * row/column, dual step 1/(8 lambda), no box constraint) applied to each image:
+ *   d_x ~= argmin_x 1/2 ||x - d_z||^2 + lambda TV(x).
+ * d_z, d_x [batch][n][n] (may not alias); d_ws of pnp_tv_workspace_size bytes. */
+int pnp_tv_denoise(const float* d_z, float* d_x, int n, int batch, float lambda, int iters,
+                   void* d_ws, size_t ws_bytes, void* stream);
+
+/* Step-size constant L = ||A_s S||^2 (Sec. 3: eta = O(1/L)) by power iteration
+ * on S^T A_s^T A_s S from the normalised all-ones image, FP32 operators and FP64
+ * inner products; stops when the Rayleigh quotient changes by less than tol
+ * (relative) or after max_iters.  Uses batch instance 0's buffers only (L does
+ * not depend on the data).  Synchronous: writes *h_L and *h_iters. */
+int pnp_power_iter(const pnp_geom* g, int factor, int max_iters, double tol, double* h_L,
+                   int* h_iters, void* d_ws, void* stream);
+
+/* Algorithm 1 (PnP-MS2G) on every image of the batch.
+ *   stages[n_stages]   the schedule; h_eta[n_stages] step sizes eta_k
+ *   h_subset_seq       subset id of every iteration (length sum iters); may be
+ *                      NULL when every stage has n_subsets == 1
+ *   params             alpha, lambda, tv_iters, momentum
+ *   d_b                data [batch][n_views][n_det]
+ *   d_x                in: x_0 (= y_0), out: x after the last iteration
+ *   d_xtrue, h_psnr_log  optional (both or neither): per-iteration PSNR
+ *                      (peak 1) of every instance, [total_iters][batch];
+ *                      the call then synchronises `stream` before returning
+ * Iteration i: v = S_k y_{i-1}; r = A_s^{(p_i)} v - b^{(p_i)};
+ *   z = y_{i-1} - eta_k c S_k^T A_s^{(p_i)T} r;  x_i = (1-alpha) z + alpha D(z);
+ *   y_i = x_i + a_i (x_i - x_{i-1}). */
+int pnp_run(const pnp_geom* g, const pnp_stage* stages, int n_stages, const double* h_eta,
+            const int32_t* h_subset_seq, const pnp_run_params* params, const float* d_b,
+            float* d_x, const float* d_xtrue, double* h_psnr_log, void* d_ws, void* stream);
+
+/* Final FP64 reductions for every instance: h_out[3*i + 0] = 1/2 ||A x - b||^2,
+ * h_out[3*i + 1] = TV(x) (isotropic, as in the denoiser), h_out[3*i + 2] =
+ * PSNR(x, xtrue) (peak 1; NaN when d_xtrue is NULL).  Synchronous. */
+int pnp_objective(const pnp_geom* g, const float* d_x, const float* d_b, const float* d_xtrue,
+                  double* h_out, void* d_ws, void* stream);
+
+/* Exact number of in-image samples (inside |x|,|y| < (n_s/2 + 1/2) s) over the
+ * rays of the subset, one instance: the work unit of GRay-samples/s.
+ * Synchronous. */
+int pnp_sample_count(const pnp_geom* g, int factor, int subset, int n_subsets, double* h_count,
+                     void* d_ws, void* stream);
+
+/* Number of kernels this library has launched in this process. */
+uint64_t pnp_launch_count(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* pnp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PNP_MS2G_H */

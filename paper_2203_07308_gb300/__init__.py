@@ -1,0 +1,13 @@
+"""GB300-native (sm_103a) hot path of PnP-MS2G (arXiv 2203.07308).
+
+The numerical path lives in ``libpnp_ms2g.so`` (CUDA kernels behind the C ABI
+of ``include/pnp_ms2g.h``); ``_native`` is its ctypes binding, ``synth`` the
+seeded input generators.  Build the library with
+``python -m paper_2203_07308_gb300.build``.
+"""
+from . import synth  # noqa: F401
+from ._native import (  # noqa: F401
+    Geom, Plan, PnpError, backproject, full_grad, header_functions, launch_count, last_error, load,
+    objective, power_iter, project, run, sample_count, setup, sketch, sketch_grad, subset_views,
+    tv_denoise, tv_workspace_size, upsample, workspace_size,
+)

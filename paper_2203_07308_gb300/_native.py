@@ -1,0 +1,313 @@
+"""ctypes binding of libpnp_ms2g.so (C ABI in include/pnp_ms2g.h).
+
+Argument marshalling only: every numerical step runs in the library's CUDA
+kernels.  Tensors are PyTorch CUDA tensors (device memory and streams come from
+PyTorch); they are checked for device, dtype, contiguity and size, and passed
+as raw pointers.  There is no fallback: if the library is missing or a call
+fails, a ``PnpError`` is raised.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpnp_ms2g.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "pnp_ms2g.h")
+
+PNP_OK, PNP_EINVAL, PNP_ECUDA, PNP_ETIMEOUT, PNP_EUNSUPPORTED, PNP_ESTATE = range(6)
+MAX_LOG_ITERS = 65536
+
+
+class PnpError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"pnp error {code}: {msg}")
+        self.code = code
+
+
+class Geom(C.Structure):
+    _fields_ = [("n", C.c_int32), ("n_views", C.c_int32), ("n_det", C.c_int32), ("batch", C.c_int32),
+                ("dso", C.c_double), ("ddo", C.c_double), ("det_pitch", C.c_double),
+                ("angle0", C.c_double), ("angle_span", C.c_double), ("step", C.c_double)]
+
+
+class StageC(C.Structure):
+    _fields_ = [("factor", C.c_int32), ("iters", C.c_int32), ("n_subsets", C.c_int32)]
+
+
+class RunParams(C.Structure):
+    _fields_ = [("alpha", C.c_float), ("lambda_", C.c_float), ("tv_iters", C.c_int32),
+                ("momentum", C.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def header_functions() -> list:
+    """Names of the functions that include/pnp_ms2g.h declares."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pnp_[a-z0-9_]+)\s*\(", text)))
+
+
+def load(path: Optional[str] = None):
+    """Load the library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise PnpError(PNP_EUNSUPPORTED,
+                           f"{p} not built: run `python -m paper_2203_07308_gb300.build`")
+        lib = C.CDLL(p)
+        vp, i32, sz = C.c_void_p, C.c_int, C.c_size_t
+        gp = C.POINTER(Geom)
+        dp = C.POINTER(C.c_double)
+        sig = {
+            "pnp_workspace_size": [gp, C.POINTER(sz)],
+            "pnp_setup": [gp, vp, sz, vp],
+            "pnp_project": [gp, i32, vp, vp, vp, i32, i32, vp, vp],
+            "pnp_backproject": [gp, i32, vp, vp, i32, i32, vp, vp],
+            "pnp_sketch": [gp, i32, vp, vp, vp],
+            "pnp_upsample": [gp, i32, vp, vp, vp],
+            "pnp_full_grad": [gp, vp, vp, vp, vp, vp],
+            "pnp_sketch_grad": [gp, i32, vp, vp, vp, i32, i32, vp, vp],
+            "pnp_tv_workspace_size": [i32, i32, C.POINTER(sz)],
+            "pnp_tv_denoise": [vp, vp, i32, i32, C.c_float, i32, vp, sz, vp],
+            "pnp_power_iter": [gp, i32, i32, C.c_double, dp, C.POINTER(i32), vp, vp],
+            "pnp_run": [gp, C.POINTER(StageC), i32, dp, C.POINTER(C.c_int32), C.POINTER(RunParams),
+                        vp, vp, vp, dp, vp, vp],
+            "pnp_objective": [gp, vp, vp, vp, dp, vp, vp],
+            "pnp_sample_count": [gp, i32, i32, i32, dp, vp, vp],
+        }
+        for name, args in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        lib.pnp_launch_count.argtypes = []
+        lib.pnp_launch_count.restype = C.c_uint64
+        lib.pnp_last_error.argtypes = []
+        lib.pnp_last_error.restype = C.c_char_p
+        _lib = lib
+        return lib
+
+
+def _check(code: int):
+    if code != PNP_OK:
+        msg = load().pnp_last_error().decode(errors="replace")
+        raise PnpError(code, msg)
+
+
+def geom(g) -> Geom:
+    """C geometry record from a ``synth.Geometry`` (or anything with its fields)."""
+    if isinstance(g, Geom):
+        return g
+    return Geom(int(g.n), int(g.n_views), int(g.n_det), int(getattr(g, "batch", 1)), float(g.dso),
+                float(g.ddo), float(g.det_pitch), float(g.angle0), float(g.angle_span), float(g.step))
+
+
+def _stream(stream) -> C.c_void_p:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t, numel: Optional[int] = None, name: str = "tensor", allow_none: bool = False):
+    if t is None:
+        if allow_none:
+            return None
+        raise PnpError(PNP_EINVAL, f"{name} is required")
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise PnpError(PNP_EINVAL, f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32:
+        raise PnpError(PNP_EINVAL, f"{name} must be float32")
+    if not t.is_contiguous():
+        raise PnpError(PNP_EINVAL, f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise PnpError(PNP_EINVAL, f"{name} has {t.numel()} elements, expected {numel}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _ws(ws):
+    import torch
+    if not isinstance(ws, torch.Tensor) or not ws.is_cuda:
+        raise PnpError(PNP_EINVAL, "workspace must be a CUDA tensor")
+    return C.c_void_p(ws.data_ptr()), ws.numel() * ws.element_size()
+
+
+def subset_views(g, p: int, P: int) -> int:
+    return g.n_views if P <= 1 else (g.n_views - p + P - 1) // P
+
+
+# ---------------------------------------------------------------- entry points
+def workspace_size(g) -> int:
+    n = C.c_size_t(0)
+    _check(load().pnp_workspace_size(C.byref(geom(g)), C.byref(n)))
+    return int(n.value)
+
+
+def setup(g, ws, stream=None):
+    p, nbytes = _ws(ws)
+    _check(load().pnp_setup(C.byref(geom(g)), p, nbytes, _stream(stream)))
+
+
+def project(g, factor, img, sino, b=None, subset=0, n_subsets=1, ws=None, stream=None):
+    ns = g.n // factor
+    nsub = subset_views(g, subset, n_subsets)
+    _check(load().pnp_project(C.byref(geom(g)), factor, _ptr(img, g.batch * ns * ns, "img"),
+                              _ptr(b, g.batch * g.n_views * g.n_det, "b", True),
+                              _ptr(sino, g.batch * nsub * g.n_det, "sino"), subset, n_subsets,
+                              _ws(ws)[0], _stream(stream)))
+
+
+def backproject(g, factor, sino, img, subset=0, n_subsets=1, ws=None, stream=None):
+    ns = g.n // factor
+    nsub = subset_views(g, subset, n_subsets)
+    _check(load().pnp_backproject(C.byref(geom(g)), factor, _ptr(sino, g.batch * nsub * g.n_det, "sino"),
+                                  _ptr(img, g.batch * ns * ns, "img"), subset, n_subsets,
+                                  _ws(ws)[0], _stream(stream)))
+
+
+def sketch(g, factor, fine, coarse, stream=None):
+    ns = g.n // factor
+    _check(load().pnp_sketch(C.byref(geom(g)), factor, _ptr(fine, g.batch * g.n * g.n, "fine"),
+                             _ptr(coarse, g.batch * ns * ns, "coarse"), _stream(stream)))
+
+
+def upsample(g, factor, coarse, fine, stream=None):
+    ns = g.n // factor
+    _check(load().pnp_upsample(C.byref(geom(g)), factor, _ptr(coarse, g.batch * ns * ns, "coarse"),
+                               _ptr(fine, g.batch * g.n * g.n, "fine"), _stream(stream)))
+
+
+def full_grad(g, x, b, out, ws, stream=None):
+    img = g.batch * g.n * g.n
+    _check(load().pnp_full_grad(C.byref(geom(g)), _ptr(x, img, "x"), _ptr(b, g.batch * g.n_views * g.n_det, "b"),
+                                _ptr(out, img, "g"), _ws(ws)[0], _stream(stream)))
+
+
+def sketch_grad(g, factor, y, b, out, subset=0, n_subsets=1, ws=None, stream=None):
+    img = g.batch * g.n * g.n
+    _check(load().pnp_sketch_grad(C.byref(geom(g)), factor, _ptr(y, img, "y"),
+                                  _ptr(b, g.batch * g.n_views * g.n_det, "b"), _ptr(out, img, "g"),
+                                  subset, n_subsets, _ws(ws)[0], _stream(stream)))
+
+
+def tv_workspace_size(n: int, batch: int) -> int:
+    v = C.c_size_t(0)
+    _check(load().pnp_tv_workspace_size(n, batch, C.byref(v)))
+    return int(v.value)
+
+
+def tv_denoise(z, x, n, batch, lam, iters, ws, stream=None):
+    p, nbytes = _ws(ws) if ws is not None else (None, 0)
+    _check(load().pnp_tv_denoise(_ptr(z, batch * n * n, "z"), _ptr(x, batch * n * n, "x"), n, batch,
+                                 float(lam), int(iters), p, nbytes, _stream(stream)))
+
+
+def power_iter(g, factor, max_iters=100, tol=1e-7, ws=None, stream=None):
+    L = C.c_double(0.0)
+    it = C.c_int(0)
+    _check(load().pnp_power_iter(C.byref(geom(g)), factor, max_iters, tol, C.byref(L), C.byref(it),
+                                 _ws(ws)[0], _stream(stream)))
+    return float(L.value), int(it.value)
+
+
+def _stages(stages: Sequence):
+    arr = (StageC * len(stages))()
+    for k, s in enumerate(stages):
+        f, it, P = (s.factor, s.iters, s.n_subsets) if hasattr(s, "factor") else s
+        arr[k] = StageC(int(f), int(it), int(P))
+    return arr
+
+
+def run(g, stages, eta, seq, b, x, *, alpha=1.0, lam=0.02, tv_iters=20, momentum=True,
+        xtrue=None, ws=None, stream=None):
+    """Algorithm 1; x holds x_0 on entry and the result on return.  Returns the
+    PSNR log [total_iters, batch] when xtrue is given, else None."""
+    st = _stages(stages)
+    total = sum(a.iters for a in st)
+    eta_a = (C.c_double * len(st))(*[float(e) for e in eta])
+    seq_np = np.ascontiguousarray(np.asarray(seq if seq is not None else np.zeros(total), dtype=np.int32))
+    if seq_np.size < total:
+        raise PnpError(PNP_EINVAL, "subset sequence shorter than the schedule")
+    prm = RunParams(float(alpha), float(lam), int(tv_iters), int(bool(momentum)))
+    img = g.batch * g.n * g.n
+    log = np.zeros((total, g.batch)) if xtrue is not None else None
+    _check(load().pnp_run(C.byref(geom(g)), st, len(st), eta_a,
+                          seq_np.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(prm),
+                          _ptr(b, g.batch * g.n_views * g.n_det, "b"), _ptr(x, img, "x"),
+                          _ptr(xtrue, img, "xtrue", True),
+                          log.ctypes.data_as(C.POINTER(C.c_double)) if log is not None else None,
+                          _ws(ws)[0], _stream(stream)))
+    return log
+
+
+def objective(g, x, b, xtrue=None, ws=None, stream=None):
+    out = np.zeros((g.batch, 3))
+    img = g.batch * g.n * g.n
+    _check(load().pnp_objective(C.byref(geom(g)), _ptr(x, img, "x"),
+                                _ptr(b, g.batch * g.n_views * g.n_det, "b"),
+                                _ptr(xtrue, img, "xtrue", True), out.ctypes.data_as(C.POINTER(C.c_double)),
+                                _ws(ws)[0], _stream(stream)))
+    return out
+
+
+def sample_count(g, factor=1, subset=0, n_subsets=1, ws=None, stream=None) -> float:
+    v = C.c_double(0.0)
+    _check(load().pnp_sample_count(C.byref(geom(g)), factor, subset, n_subsets, C.byref(v),
+                                   _ws(ws)[0], _stream(stream)))
+    return float(v.value)
+
+
+def launch_count() -> int:
+    return int(load().pnp_launch_count())
+
+
+def last_error() -> str:
+    return load().pnp_last_error().decode(errors="replace")
+
+
+class Plan:
+    """A geometry with its device workspace allocated (by PyTorch) and prepared."""
+
+    def __init__(self, g, device="cuda", stream=None):
+        import torch
+        self.g = g
+        self.cg = geom(g)
+        self.ws = torch.empty(workspace_size(g), dtype=torch.uint8, device=device)
+        setup(g, self.ws, stream)
+
+    def project(self, factor, img, sino, b=None, subset=0, n_subsets=1, stream=None):
+        project(self.g, factor, img, sino, b, subset, n_subsets, self.ws, stream)
+
+    def backproject(self, factor, sino, img, subset=0, n_subsets=1, stream=None):
+        backproject(self.g, factor, sino, img, subset, n_subsets, self.ws, stream)
+
+    def full_grad(self, x, b, out, stream=None):
+        full_grad(self.g, x, b, out, self.ws, stream)
+
+    def sketch_grad(self, factor, y, b, out, subset=0, n_subsets=1, stream=None):
+        sketch_grad(self.g, factor, y, b, out, subset, n_subsets, self.ws, stream)
+
+    def power_iter(self, factor, max_iters=100, tol=1e-7, stream=None):
+        return power_iter(self.g, factor, max_iters, tol, self.ws, stream)
+
+    def run(self, stages, eta, seq, b, x, **kw):
+        return run(self.g, stages, eta, seq, b, x, ws=self.ws, **kw)
+
+    def objective(self, x, b, xtrue=None, stream=None):
+        return objective(self.g, x, b, xtrue, self.ws, stream)
+
+    def sample_count(self, factor=1, subset=0, n_subsets=1, stream=None):
+        return sample_count(self.g, factor, subset, n_subsets, self.ws, stream)

@@ -1,0 +1,630 @@
+// C ABI of libpnp_ms2g.so (declared in include/pnp_ms2g.h): argument checks,
+// workspace layout, the (workspace, geometry) registry, and the host side of
+// the gradient estimators, the TV denoiser, the power iteration and the
+// multi-stage loop of Algorithm 1.  Every step of the numerical path runs in
+// the kernels of projector.cu, tv.cu and reduce.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pnp_internal.cuh"
+
+namespace pnp {
+
+int level_index(int factor)
+{
+    switch (factor) {
+        case 1: return 0;
+        case 2: return 1;
+        case 4: return 2;
+        case 8: return 3;
+        default: return -1;
+    }
+}
+
+namespace {
+
+thread_local std::string t_err;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return code;
+}
+
+#define PNP_CUDA(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(PNP_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),      \
+                        __FILE__, __LINE__);                                             \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// A level is available when it divides n, keeps at least 4 pixels per side and
+// leaves the source far enough outside the image for the backprojector's
+// shadow bound (distance >= 4 sqrt(2) level pixels beyond the support).
+bool level_ok(const pnp_geom& g, int s)
+{
+    if (g.n % s != 0 || g.n / s < 4) return false;
+    return g.dso >= std::sqrt(2.0) * (0.5 * g.n + 5.5 * s);
+}
+
+int validate_geom(const pnp_geom* g)
+{
+    if (!g) return fail(PNP_EINVAL, "geometry pointer is NULL");
+    if (g->n < 4 || g->n > 8192) return fail(PNP_EINVAL, "n=%d outside [4, 8192]", g->n);
+    if (g->n_views < 1 || g->n_det < 1 || g->batch < 1)
+        return fail(PNP_EINVAL, "n_views, n_det and batch must be >= 1");
+    if ((double)g->n_views * g->n_det > (double)(1 << 28))
+        return fail(PNP_EINVAL, "n_views * n_det too large");
+    if ((double)g->batch * g->n * g->n > 4.0e9 || (double)g->batch * g->n_views * g->n_det > 4.0e9)
+        return fail(PNP_EINVAL, "batch too large");
+    if (!(std::isfinite(g->dso) && std::isfinite(g->ddo) && std::isfinite(g->det_pitch) &&
+          std::isfinite(g->angle0) && std::isfinite(g->angle_span) && std::isfinite(g->step)))
+        return fail(PNP_EINVAL, "geometry has a non-finite value");
+    if (g->ddo < 0.0 || g->det_pitch <= 0.0 || g->step <= 0.0 || g->step > 4.0)
+        return fail(PNP_EINVAL, "need ddo >= 0, det_pitch > 0, 0 < step <= 4");
+    if (!level_ok(*g, 1))
+        return fail(PNP_EINVAL, "source too close: need dso >= sqrt(2) (n/2 + 5.5) = %g",
+                    std::sqrt(2.0) * (0.5 * g->n + 5.5));
+    // longest ray inside the image in samples must fit an int comfortably
+    if (std::sqrt(2.0) * (g->n + 2) / g->step > 1.0e8) return fail(PNP_EINVAL, "step too small");
+    return PNP_OK;
+}
+
+Layout make_layout(const pnp_geom& g)
+{
+    Layout L;
+    size_t off = 0;
+    const size_t nr = (size_t)g.n_views * g.n_det;
+    const int factors[kMaxLevels] = {1, 2, 4, 8};
+    for (int l = 0; l < kMaxLevels; ++l) {
+        const int s = factors[l];
+        if (!level_ok(g, s)) continue;
+        LevelLayout& v = L.lv[l];
+        v.factor = s;
+        v.ns = g.n / s;
+        v.qw = v.ns + 2 * kPad - 1;
+        v.off_rayf = off; off = align_up(off + nr * sizeof(float4));
+        v.off_rayi = off; off = align_up(off + nr * sizeof(float2));
+        v.off_rayk = off; off = align_up(off + nr * sizeof(int2));
+        v.off_view = off; off = align_up(off + (size_t)g.n_views * sizeof(float4));
+        v.off_quad = off; off = align_up(off + (size_t)g.batch * v.qw * v.qw * sizeof(float4));
+    }
+    const size_t img = (size_t)g.batch * g.n * g.n;
+    L.off_res = off; off = align_up(off + (size_t)g.batch * nr * sizeof(float));
+    L.off_y = off; off = align_up(off + img * sizeof(float));
+    L.off_z = off; off = align_up(off + img * sizeof(float));
+    L.off_tv = off; off = align_up(off + 6 * img * sizeof(float));
+    L.off_pw = off; off = align_up(off + 2 * (size_t)g.n * g.n * sizeof(float));
+    const size_t tv_parts = (size_t)((g.n + 31) / 32) * ((g.n + 7) / 8);
+    const size_t parts = tv_parts > (size_t)kRedBlocks ? tv_parts : (size_t)kRedBlocks;
+    L.off_red = off; off = align_up(off + ((size_t)g.batch * parts + (size_t)g.batch * 8) * sizeof(double));
+    L.off_log = off; off = align_up(off + (size_t)PNP_MAX_LOG_ITERS * sizeof(double));
+    L.total = off;
+    return L;
+}
+
+inline size_t red_parts(const pnp_geom& g)
+{
+    const size_t tv_parts = (size_t)((g.n + 31) / 32) * ((g.n + 7) / 8);
+    return tv_parts > (size_t)kRedBlocks ? tv_parts : (size_t)kRedBlocks;
+}
+
+uint64_t fingerprint(const pnp_geom& g)
+{
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void* p, size_t n) {
+        const unsigned char* c = (const unsigned char*)p;
+        for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    };
+    mix(&g.n, sizeof g.n); mix(&g.n_views, sizeof g.n_views); mix(&g.n_det, sizeof g.n_det);
+    mix(&g.batch, sizeof g.batch); mix(&g.dso, sizeof g.dso); mix(&g.ddo, sizeof g.ddo);
+    mix(&g.det_pitch, sizeof g.det_pitch); mix(&g.angle0, sizeof g.angle0);
+    mix(&g.angle_span, sizeof g.angle_span); mix(&g.step, sizeof g.step);
+    return h;
+}
+
+struct RegEntry { const void* ws; uint64_t fp; size_t bytes; };
+std::mutex g_reg_mu;
+std::vector<RegEntry> g_reg;
+
+void reg_put(const void* ws, uint64_t fp, size_t bytes)
+{
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    for (auto& e : g_reg)
+        if (e.ws == ws) { e.fp = fp; e.bytes = bytes; return; }
+    if (g_reg.size() >= 4096) g_reg.erase(g_reg.begin());
+    g_reg.push_back({ws, fp, bytes});
+}
+
+int check_ws(const pnp_geom& g, const void* ws)
+{
+    if (!ws) return fail(PNP_EINVAL, "workspace pointer is NULL");
+    const uint64_t fp = fingerprint(g);
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    for (const auto& e : g_reg)
+        if (e.ws == ws) {
+            if (e.fp != fp) return fail(PNP_ESTATE, "workspace was set up for another geometry");
+            return PNP_OK;
+        }
+    return fail(PNP_ESTATE, "workspace not prepared: call pnp_setup first");
+}
+
+int check_level(const pnp_geom& g, int factor, const Layout& L, int* li)
+{
+    int l = level_index(factor);
+    if (l < 0) return fail(PNP_EINVAL, "factor %d not in {1,2,4,8}", factor);
+    if (L.lv[l].factor == 0)
+        return fail(PNP_EINVAL, "factor %d unavailable for n=%d, dso=%g (needs n %% s == 0, n/s >= 4, "
+                    "dso >= sqrt(2)(n/2 + 5.5 s))", factor, g.n, g.dso);
+    *li = l;
+    return PNP_OK;
+}
+
+int check_subset(const pnp_geom& g, int p, int P)
+{
+    if (P < 1 || P > g.n_views) return fail(PNP_EINVAL, "n_subsets=%d outside [1, n_views]", P);
+    if (p < 0 || p >= P) return fail(PNP_EINVAL, "subset=%d outside [0, n_subsets)", p);
+    return PNP_OK;
+}
+
+inline int subset_views(const pnp_geom& g, int p, int P)
+{
+    return P <= 1 ? g.n_views : (g.n_views - p + P - 1) / P;
+}
+
+inline cudaStream_t S(void* st) { return (cudaStream_t)st; }
+
+// Forward residual r = A_s^{(p)} (level image in quad) - b^{(p)} into the workspace.
+FwdArgs fwd_args(const pnp_geom& g, const LevelLayout& lv, char* ws, int p, int P, const float* b,
+                 float* out, int batch)
+{
+    FwdArgs a{};
+    a.quad = (const float4*)(ws + lv.off_quad);
+    a.qw = lv.qw;
+    a.quad_stride = (size_t)lv.qw * lv.qw;
+    a.rayf = (const float4*)(ws + lv.off_rayf);
+    a.rayk = (const int2*)(ws + lv.off_rayk);
+    a.n_det = g.n_det;
+    a.first_view = P <= 1 ? 0 : p;
+    a.view_step = P <= 1 ? 1 : P;
+    a.n_sub = subset_views(g, p, P);
+    a.batch = batch;
+    a.step = (float)g.step;
+    a.weight = (float)(g.step * lv.factor);
+    a.b = b;
+    a.n_views = g.n_views;
+    a.out = out;
+    return a;
+}
+
+BackArgs back_args(const pnp_geom& g, const LevelLayout& lv, char* ws, int p, int P, const float* res,
+                   int mode, float scale, const float* y, float eta, float* out, int batch)
+{
+    BackArgs a{};
+    a.res = res;
+    a.rayf = (const float4*)(ws + lv.off_rayf);
+    a.rayi = (const float2*)(ws + lv.off_rayi);
+    a.view = (const float4*)(ws + lv.off_view);
+    a.ns = lv.ns;
+    a.n_det = g.n_det;
+    a.first_view = P <= 1 ? 0 : p;
+    a.view_step = P <= 1 ? 1 : P;
+    a.n_sub = subset_views(g, p, P);
+    a.batch = batch;
+    a.step = (float)g.step;
+    a.mode = mode;
+    a.s = lv.factor;
+    a.n = g.n;
+    a.scale = scale;
+    a.y = y;
+    a.eta = eta;
+    a.out = out;
+    return a;
+}
+
+// Gradient estimate on the fine grid into `out` (mode GradFine) or the fused
+// step z = y - eta * grad (mode Step).  `y` is the fine iterate.
+int grad_into(const pnp_geom& g, const Layout& L, int li, char* ws, const float* y, const float* b,
+              int p, int P, int mode, float eta, float* out, cudaStream_t st)
+{
+    const LevelLayout& lv = L.lv[li];
+    float* res = (float*)(ws + L.off_res);
+    PNP_CUDA(launch_prep_quad(y, g.n, lv.factor, g.batch, (float4*)(ws + lv.off_quad), lv.qw, st));
+    PNP_CUDA(launch_forward(fwd_args(g, lv, ws, p, P, b, res, g.batch), st));
+    const double c = P <= 1 ? 1.0 : (double)P;
+    const float scale = (float)(g.step * lv.factor * c / ((double)lv.factor * lv.factor));
+    PNP_CUDA(launch_backward(back_args(g, lv, ws, p, P, res, mode, scale, y, eta, out, g.batch), st));
+    return PNP_OK;
+}
+
+std::vector<float> fgp_momenta(int iters)
+{
+    std::vector<float> m(iters > 0 ? iters : 0);
+    double t = 1.0;
+    for (int k = 0; k < iters; ++k) {
+        double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+        m[k] = (float)((t - 1.0) / tn);
+        t = tn;
+    }
+    return m;
+}
+
+// TV iterations on z, leaving the dual in tv.p; returns the plane pointer.
+int tv_iterations(const float* z, TvBuffers tv, int n, int batch, float lambda, int iters,
+                  cudaStream_t st)
+{
+    std::vector<float> mom = fgp_momenta(iters);
+    const float* rin = tv.ra;
+    float* rout = tv.rb;
+    for (int k = 0; k < iters; ++k) {
+        PNP_CUDA(launch_tv_iter(z, tv, rin, rout, n, batch, lambda, mom[k], k == 0, st));
+        const float* t = rout;
+        rout = (float*)rin;
+        rin = t;
+    }
+    return PNP_OK;
+}
+
+}  // namespace
+}  // namespace pnp
+
+using namespace pnp;
+
+extern "C" {
+
+const char* pnp_last_error(void) { return t_err.c_str(); }
+
+uint64_t pnp_launch_count(void) { return g_launches.load(); }
+
+int pnp_workspace_size(const pnp_geom* g, size_t* bytes)
+{
+    t_err.clear();
+    if (int e = validate_geom(g)) return e;
+    if (!bytes) return fail(PNP_EINVAL, "bytes pointer is NULL");
+    *bytes = make_layout(*g).total;
+    return PNP_OK;
+}
+
+int pnp_setup(const pnp_geom* g, void* d_ws, size_t ws_bytes, void* stream)
+{
+    t_err.clear();
+    if (int e = validate_geom(g)) return e;
+    if (!d_ws) return fail(PNP_EINVAL, "workspace pointer is NULL");
+    if ((uintptr_t)d_ws % kAlign) return fail(PNP_EINVAL, "workspace must be 256-byte aligned");
+    Layout L = make_layout(*g);
+    if (ws_bytes < L.total)
+        return fail(PNP_EINVAL, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
+    for (int l = 0; l < kMaxLevels; ++l)
+        if (L.lv[l].factor) PNP_CUDA(launch_setup_rays(*g, L.lv[l], (char*)d_ws, S(stream)));
+    reg_put(d_ws, fingerprint(*g), ws_bytes);
+    return PNP_OK;
+}
+
+int pnp_project(const pnp_geom* g, int factor, const float* d_img, const float* d_b, float* d_sino,
+                int subset, int n_subsets, void* d_ws, void* stream)
+{
+    t_err.clear();
+    if (int e = validate_geom(g)) return e;
+    Layout L = make_layout(*g);
+    int li;
+    if (int e = check_level(*g, factor, L, &li)) return e;
+    if (int e = check_subset(*g, subset, n_subsets)) return e;
+    if (!d_img || !d_sino) return fail(PNP_EINVAL, "image or sinogram pointer is NULL");
+    if (int e = check_ws(*g, d_ws)) return e;
+    char* ws = (char*)d_ws;
+    const LevelLayout& lv = L.lv[li];
+    PNP_CUDA(launch_prep_quad(d_img, lv.ns, 1, g->batch, (float4*)(ws + lv.off_quad), lv.qw, S(stream)));
+    PNP_CUDA(launch_forward(fwd_args(*g, lv, ws, subset, n_subsets, d_b, d_sino, g->batch), S(stream)));
+    return PNP_OK;
+}
+
+int pnp_backproject(const pnp_geom* g, int factor, const float* d_sino, float* d_img, int subset,
+                    int n_subsets, void* d_ws, void* stream)
+{
+    t_err.clear();
+    if (int e = validate_geom(g)) return e;
+    Layout L = make_layout(*g);
+    int li;
+    if (int e = check_level(*g, factor, L, &li)) return e;
+    if (int e = check_subset(*g, subset, n_subsets)) return e;
+    if (!d_img || !d_sino) return fail(PNP_EINVAL, "image or sinogram pointer is NULL");
+    if (int e = check_ws(*g, d_ws)) return e;
+    const LevelLayout& lv = L.lv[li];
+    PNP_CUDA(launch_backward(back_args(*g, lv, (char*)d_ws, subset, n_subsets, d_sino, kBackRaw,
+                                       (float)(g->step * factor), nullptr, 0.0f, d_img, g->batch),
+                             S(stream)));
+    return PNP_OK;
+}
+
+int pnp_sketch(const pnp_geom* g, int factor, const float* d_fine, float* d_coarse, void* stream)
+{
+    t_err.clear();
+    if (int e = validate_geom(g)) return e;
+    Layout L = make_layout(*g);
+    int li;
+    if (int e = check_level(*g, factor, L, &li)) return e;
+    if (!d_fine || !d_coarse) return fail(PNP_EINVAL, "image pointer is NULL");
+    PNP_CUDA(launch_pool(d_fine, d_coarse, g->n, factor, g->batch, S(stream)));
+    return PNP_OK;
+}
+
+int pnp_upsample(const pnp_geom* g, int factor, const float* d_coarse, float* d_fine, void* stream)
+{
+    t_err.clear();
+    if (int e = validate_geom(g)) return e;
+    Layout L = make_layout(*g);
+    int li;
+    if (int e = check_level(*g, factor, L, &li)) return e;
+    if (!d_fine || !d_coarse) return fail(PNP_EINVAL, "image pointer is NULL");
+    PNP_CUDA(launch_unpool(d_coarse, d_fine, g->n, factor, g->batch, S(stream)));
+    return PNP_OK;
+}
+
+int pnp_sketch_grad(const pnp_geom* g, int factor, const float* d_y, const float* d_b, float* d_g,
+                    int subset, int n_subsets, void* d_ws, void* stream)
+{
+    t_err.clear();
+    if (int e = validate_geom(g)) return e;
+    Layout L = make_layout(*g);
+    int li;
+    if (int e = check_level(*g, factor, L, &li)) return e;
+    if (int e = check_subset(*g, subset, n_subsets)) return e;
+    if (!d_y || !d_b || !d_g) return fail(PNP_EINVAL, "y, b or g pointer is NULL");
+    if (d_y == d_g) return fail(PNP_EINVAL, "y and g must not alias");
+    if (int e = check_ws(*g, d_ws)) return e;
+    return grad_into(*g, L, li, (char*)d_ws, d_y, d_b, subset, n_subsets, kBackGradFine, 0.0f, d_g,
+                     S(stream));
+}
+
+int pnp_full_grad(const pnp_geom* g, const float* d_x, const float* d_b, float* d_g, void* d_ws,
+                  void* stream)
+{
+    return pnp_sketch_grad(g, 1, d_x, d_b, d_g, 0, 1, d_ws, stream);
+}
+
+int pnp_tv_workspace_size(int n, int batch, size_t* bytes)
+{
+    t_err.clear();
+    if (n < 2 || batch < 1 || (double)n * n * batch > 4.0e9) return fail(PNP_EINVAL, "bad n or batch");
+    if (!bytes) return fail(PNP_EINVAL, "bytes pointer is NULL");
+    *bytes = 6 * (size_t)batch * n * n * sizeof(float);
+    return PNP_OK;
+}
+
+int pnp_tv_denoise(const float* d_z, float* d_x, int n, int batch, float lambda, int iters,
+                   void* d_ws, size_t ws_bytes, void* stream)
+{
+    t_err.clear();
+    size_t need = 0;
+    if (int e = pnp_tv_workspace_size(n, batch, &need)) return e;
+    if (!d_z || !d_x) return fail(PNP_EINVAL, "z or x pointer is NULL");
+    if (d_z == d_x) return fail(PNP_EINVAL, "z and x must not alias");
+    if (iters < 0 || iters > 100000) return fail(PNP_EINVAL, "iters outside [0, 100000]");
+    if (!(lambda >= 0.0f) || !std::isfinite(lambda)) return fail(PNP_EINVAL, "lambda must be >= 0");
+    if (iters > 0 && lambda > 0.0f) {
+        if (!d_ws || ws_bytes < need) return fail(PNP_EINVAL, "TV workspace needs %zu bytes", need);
+        const size_t img = (size_t)batch * n * n;
+        TvBuffers tv{(float*)d_ws, (float*)d_ws + 2 * img, (float*)d_ws + 4 * img};
+        if (int e = tv_iterations(d_z, tv, n, batch, lambda, iters, S(stream))) return e;
+        PNP_CUDA(launch_tv_final(d_z, tv.p, 1, n, batch, lambda, 1.0f, 0.0f, d_x, nullptr, nullptr,
+                                 nullptr, S(stream)));
+    } else {
+        PNP_CUDA(launch_copy(d_z, d_x, (size_t)batch * n * n, S(stream)));
+    }
+    return PNP_OK;
+}
+
+int pnp_power_iter(const pnp_geom* g, int factor, int max_iters, double tol, double* h_L, int* h_iters,
+                   void* d_ws, void* stream)
+{
+    t_err.clear();
+    if (int e = validate_geom(g)) return e;
+    Layout L = make_layout(*g);
+    int li;
+    if (int e = check_level(*g, factor, L, &li)) return e;
+    if (max_iters < 1 || !(tol >= 0.0)) return fail(PNP_EINVAL, "need max_iters >= 1 and tol >= 0");
+    if (!h_L) return fail(PNP_EINVAL, "h_L is NULL");
+    if (int e = check_ws(*g, d_ws)) return e;
+    char* ws = (char*)d_ws;
+    cudaStream_t st = S(stream);
+    pnp_geom g1 = *g;
+    g1.batch = 1;
+    const LevelLayout& lv = L.lv[li];
+    const size_t N = (size_t)g->n * g->n;
+    float* u = (float*)(ws + L.off_pw);
+    float* w = u + N;
+    double* part = (double*)(ws + L.off_red);
+    double* outv = part + (size_t)g->batch * red_parts(*g);
+    float* res = (float*)(ws + L.off_res);
+    PNP_CUDA(launch_fill(u, N, (float)(1.0 / std::sqrt((double)N)), st));
+    const float scale = (float)(g->step * lv.factor / ((double)lv.factor * lv.factor));
+    double lam = 0.0;
+    int it = 0;
+    for (it = 1; it <= max_iters; ++it) {
+        PNP_CUDA(launch_prep_quad(u, g->n, lv.factor, 1, (float4*)(ws + lv.off_quad), lv.qw, st));
+        PNP_CUDA(launch_forward(fwd_args(g1, lv, ws, 0, 1, nullptr, res, 1), st));
+        PNP_CUDA(launch_backward(back_args(g1, lv, ws, 0, 1, res, kBackGradFine, scale, nullptr, 0.0f, w, 1), st));
+        PNP_CUDA(launch_reduce_partial(kRedDot, u, w, N, N, 1, g->n, part, st));
+        PNP_CUDA(launch_reduce_final(part, kRedBlocks, 1, outv, 1, 0, st));
+        PNP_CUDA(launch_reduce_partial(kRedSq, w, nullptr, N, N, 1, g->n, part, st));
+        PNP_CUDA(launch_reduce_final(part, kRedBlocks, 1, outv + 1, 1, 0, st));
+        PNP_CUDA(launch_scale_by_rnorm(w, u, N, outv + 1, st));
+        double hv[2];
+        PNP_CUDA(cudaMemcpyAsync(hv, outv, sizeof hv, cudaMemcpyDeviceToHost, st));
+        PNP_CUDA(cudaStreamSynchronize(st));
+        const double rq = hv[0];
+        const bool done = it > 1 && std::fabs(rq - lam) <= tol * std::fabs(rq);
+        lam = rq;
+        if (done) break;
+    }
+    *h_L = lam;
+    if (h_iters) *h_iters = it > max_iters ? max_iters : it;
+    return PNP_OK;
+}
+
+int pnp_run(const pnp_geom* g, const pnp_stage* stages, int n_stages, const double* h_eta,
+            const int32_t* h_subset_seq, const pnp_run_params* params, const float* d_b, float* d_x,
+            const float* d_xtrue, double* h_psnr_log, void* d_ws, void* stream)
+{
+    t_err.clear();
+    if (int e = validate_geom(g)) return e;
+    Layout L = make_layout(*g);
+    if (!stages || n_stages < 1 || !h_eta || !params || !d_b || !d_x)
+        return fail(PNP_EINVAL, "stages, eta, params, b and x are required");
+    if ((d_xtrue == nullptr) != (h_psnr_log == nullptr))
+        return fail(PNP_EINVAL, "d_xtrue and h_psnr_log must be given together");
+    long total = 0;
+    bool any_subsets = false;
+    for (int k = 0; k < n_stages; ++k) {
+        int li;
+        if (int e = check_level(*g, stages[k].factor, L, &li)) return e;
+        if (stages[k].iters < 0) return fail(PNP_EINVAL, "stage %d has negative iterations", k);
+        if (stages[k].n_subsets < 1 || stages[k].n_subsets > g->n_views)
+            return fail(PNP_EINVAL, "stage %d: n_subsets outside [1, n_views]", k);
+        if (!(std::isfinite(h_eta[k]) && h_eta[k] >= 0.0)) return fail(PNP_EINVAL, "eta[%d] invalid", k);
+        any_subsets |= stages[k].n_subsets > 1;
+        total += stages[k].iters;
+    }
+    if (total > (1L << 30)) return fail(PNP_EINVAL, "too many iterations");
+    if (any_subsets && !h_subset_seq) return fail(PNP_EINVAL, "subset sequence required");
+    const pnp_run_params& pr = *params;
+    if (!(pr.alpha > 0.0f && pr.alpha <= 1.0f)) return fail(PNP_EINVAL, "alpha must be in (0, 1]");
+    if (!(pr.lambda >= 0.0f) || !std::isfinite(pr.lambda)) return fail(PNP_EINVAL, "lambda must be >= 0");
+    if (pr.tv_iters < 0 || pr.tv_iters > 100000) return fail(PNP_EINVAL, "tv_iters outside [0, 100000]");
+    if (h_psnr_log && total * g->batch > PNP_MAX_LOG_ITERS)
+        return fail(PNP_EINVAL, "PSNR log limited to %d iterations x batch", PNP_MAX_LOG_ITERS);
+    if (int e = check_ws(*g, d_ws)) return e;
+    // validate the subset sequence before launching anything
+    {
+        long i = 0;
+        for (int k = 0; k < n_stages; ++k)
+            for (int jj = 0; jj < stages[k].iters; ++jj, ++i)
+                if (stages[k].n_subsets > 1 &&
+                    (h_subset_seq[i] < 0 || h_subset_seq[i] >= stages[k].n_subsets))
+                    return fail(PNP_EINVAL, "subset_seq[%ld]=%d outside stage %d's [0, %d)", i,
+                                h_subset_seq[i], k, stages[k].n_subsets);
+    }
+    char* ws = (char*)d_ws;
+    cudaStream_t st = S(stream);
+    const size_t img = (size_t)g->batch * g->n * g->n;
+    float* y = (float*)(ws + L.off_y);
+    float* z = (float*)(ws + L.off_z);
+    float* tvb = (float*)(ws + L.off_tv);
+    TvBuffers tv{tvb, tvb + 2 * img, tvb + 4 * img};
+    double* part = (double*)(ws + L.off_red);
+    double* dlog = (double*)(ws + L.off_log);
+    const int tv_parts = ((g->n + 31) / 32) * ((g->n + 7) / 8);
+    const bool do_tv = pr.tv_iters > 0 && pr.lambda > 0.0f;
+    std::vector<float> mom = fgp_momenta(do_tv ? pr.tv_iters : 0);
+    PNP_CUDA(launch_copy(d_x, y, img, st));
+    long i = 0;
+    for (int k = 0; k < n_stages; ++k) {
+        const int li = level_index(stages[k].factor);
+        const int P = stages[k].n_subsets;
+        for (int jj = 0; jj < stages[k].iters; ++jj) {
+            ++i;
+            const int p = P > 1 ? h_subset_seq[i - 1] : 0;
+            if (int e = grad_into(*g, L, li, ws, y, d_b, p, P, kBackStep, (float)h_eta[k], z, st)) return e;
+            if (do_tv) {
+                const float* rin = tv.ra;
+                float* rout = tv.rb;
+                for (int t = 0; t < pr.tv_iters; ++t) {
+                    PNP_CUDA(launch_tv_iter(z, tv, rin, rout, g->n, g->batch, pr.lambda, mom[t], t == 0, st));
+                    const float* tmp = rout;
+                    rout = (float*)rin;
+                    rin = tmp;
+                }
+            }
+            const float a = pr.momentum ? (float)((double)(i - 1) / (double)(i + 3)) : 0.0f;
+            double* mp = h_psnr_log ? part : nullptr;
+            PNP_CUDA(launch_tv_final(z, tv.p, do_tv, g->n, g->batch, pr.lambda, pr.alpha, a, d_x, y,
+                                     d_xtrue, mp, st));
+            if (mp) PNP_CUDA(launch_reduce_final(part, tv_parts, g->batch, dlog + (i - 1) * g->batch, 1, 0, st));
+        }
+    }
+    if (h_psnr_log && total > 0) {
+        std::vector<double> mse((size_t)total * g->batch);
+        PNP_CUDA(cudaMemcpyAsync(mse.data(), dlog, mse.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PNP_CUDA(cudaStreamSynchronize(st));
+        const double npix = (double)g->n * g->n;
+        for (size_t q = 0; q < mse.size(); ++q) h_psnr_log[q] = 10.0 * std::log10(npix / mse[q]);
+    }
+    return PNP_OK;
+}
+
+int pnp_objective(const pnp_geom* g, const float* d_x, const float* d_b, const float* d_xtrue,
+                  double* h_out, void* d_ws, void* stream)
+{
+    t_err.clear();
+    if (int e = validate_geom(g)) return e;
+    if (!d_x || !d_b || !h_out) return fail(PNP_EINVAL, "x, b and h_out are required");
+    if (int e = check_ws(*g, d_ws)) return e;
+    Layout L = make_layout(*g);
+    char* ws = (char*)d_ws;
+    cudaStream_t st = S(stream);
+    const LevelLayout& lv = L.lv[0];
+    float* res = (float*)(ws + L.off_res);
+    double* part = (double*)(ws + L.off_red);
+    double* outv = part + (size_t)g->batch * red_parts(*g);
+    const size_t nr = (size_t)g->n_views * g->n_det, N = (size_t)g->n * g->n;
+    PNP_CUDA(launch_prep_quad(d_x, g->n, 1, g->batch, (float4*)(ws + lv.off_quad), lv.qw, st));
+    PNP_CUDA(launch_forward(fwd_args(*g, lv, ws, 0, 1, d_b, res, g->batch), st));
+    PNP_CUDA(launch_reduce_partial(kRedSq, res, nullptr, nr, nr, g->batch, g->n, part, st));
+    PNP_CUDA(launch_reduce_final(part, kRedBlocks, g->batch, outv, 8, 0, st));
+    PNP_CUDA(launch_reduce_partial(kRedTv, d_x, nullptr, N, N, g->batch, g->n, part, st));
+    PNP_CUDA(launch_reduce_final(part, kRedBlocks, g->batch, outv, 8, 1, st));
+    if (d_xtrue) {
+        PNP_CUDA(launch_reduce_partial(kRedDiffSq, d_x, d_xtrue, N, N, g->batch, g->n, part, st));
+        PNP_CUDA(launch_reduce_final(part, kRedBlocks, g->batch, outv, 8, 2, st));
+    }
+    std::vector<double> hv((size_t)g->batch * 8);
+    PNP_CUDA(cudaMemcpyAsync(hv.data(), outv, hv.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PNP_CUDA(cudaStreamSynchronize(st));
+    for (int b = 0; b < g->batch; ++b) {
+        h_out[3 * b + 0] = 0.5 * hv[8 * b + 0];
+        h_out[3 * b + 1] = hv[8 * b + 1];
+        h_out[3 * b + 2] = d_xtrue ? 10.0 * std::log10((double)N / hv[8 * b + 2]) : NAN;
+    }
+    return PNP_OK;
+}
+
+int pnp_sample_count(const pnp_geom* g, int factor, int subset, int n_subsets, double* h_count,
+                     void* d_ws, void* stream)
+{
+    t_err.clear();
+    if (int e = validate_geom(g)) return e;
+    Layout L = make_layout(*g);
+    int li;
+    if (int e = check_level(*g, factor, L, &li)) return e;
+    if (int e = check_subset(*g, subset, n_subsets)) return e;
+    if (!h_count) return fail(PNP_EINVAL, "h_count is NULL");
+    if (int e = check_ws(*g, d_ws)) return e;
+    char* ws = (char*)d_ws;
+    cudaStream_t st = S(stream);
+    double* outv = (double*)(ws + L.off_red) + (size_t)g->batch * red_parts(*g);
+    const LevelLayout& lv = L.lv[li];
+    PNP_CUDA(launch_count_samples((const int2*)(ws + lv.off_rayk), g->n_det, n_subsets <= 1 ? 0 : subset,
+                                  n_subsets <= 1 ? 1 : n_subsets, subset_views(*g, subset, n_subsets),
+                                  outv, st));
+    PNP_CUDA(cudaMemcpyAsync(h_count, outv, sizeof(double), cudaMemcpyDeviceToHost, st));
+    PNP_CUDA(cudaStreamSynchronize(st));
+    return PNP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,122 @@
+// Internal declarations shared by the translation units of libpnp_ms2g.so.
+//
+// Data layout in the caller's workspace (all offsets 256-byte aligned), per
+// sketch level s in {1,2,4,8} with n % s == 0 and n/s >= 4:
+//   rayf  float4 [n_views*n_det]  (F'_x, F'_y, d_x, d_y): foot point in level
+//                                 index units shifted by +1.5 (see below), unit dir
+//   rayi  float2 [n_views*n_det]  (1/d_x, 1/d_y), clamped away from 0
+//   rayk  int2   [n_views*n_det]  first/last sample index k inside the image box
+//   view  float4 [n_views]        (cos b, sin b, dso/s, (dso+ddo)/pitch)
+//   quad  float4 [batch][(n_s+3)^2] bilinear coefficients of the level image
+// then the residual sinogram, the fine-grid loop buffers, the TV buffers, the
+// power-iteration vectors and the FP64 reduction scratch.
+//
+// Index frame: level pixel (ix,iy) has centre index coordinate (ix,iy); the
+// primed frame adds 1.5 so that round(X') = floor(X) + 2 is directly the column
+// of the 2-pixel-padded coefficient image and X' - round(X') = frac(X) - 1/2.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/pnp_ms2g.h"
+
+namespace pnp {
+
+constexpr int kMaxLevels = 4;          // factors 1, 2, 4, 8
+constexpr int kPad = 2;                // padding of the coefficient image
+constexpr int kRedBlocks = 304;        // FP64 partial-sum blocks per instance (2 x 152 SMs)
+constexpr int kRedThreads = 256;
+
+extern std::atomic<uint64_t> g_launches;
+
+struct LevelLayout {
+    int factor = 0;   // 0: level not present
+    int ns = 0;       // n / factor
+    int qw = 0;       // ns + 3 (padded coefficient image side)
+    size_t off_rayf = 0, off_rayi = 0, off_rayk = 0, off_view = 0, off_quad = 0;
+};
+
+struct Layout {
+    LevelLayout lv[kMaxLevels];
+    size_t off_res = 0;      // float [batch][n_views][n_det]
+    size_t off_y = 0;        // float [batch][n][n]
+    size_t off_z = 0;        // float [batch][n][n]
+    size_t off_tv = 0;       // float [6][batch][n][n]
+    size_t off_pw = 0;       // float [2][n][n]   power iteration u, w
+    size_t off_red = 0;      // double [batch][kRedBlocks] partials + [batch][8] results
+    size_t off_log = 0;      // double [PNP_MAX_LOG_ITERS] (not used when batch grows; see api)
+    size_t total = 0;
+};
+
+int level_index(int factor);   // 0..3 or -1
+
+// ---------------------------------------------------------------- kernels (launchers)
+cudaError_t launch_setup_rays(const pnp_geom& g, const LevelLayout& L, char* ws, cudaStream_t st);
+
+cudaError_t launch_prep_quad(const float* fine, int n, int s, int batch, float4* quad, int qw,
+                             cudaStream_t st);
+
+struct FwdArgs {
+    const float4* quad; int qw; size_t quad_stride;
+    const float4* rayf; const int2* rayk;
+    int n_det, first_view, view_step, n_sub, batch;
+    float step, weight;
+    const float* b; int n_views;     // b: [batch][n_views][n_det] or null
+    float* out;                      // [batch][n_sub][n_det]
+};
+cudaError_t launch_forward(const FwdArgs& a, cudaStream_t st);
+
+enum BackMode { kBackRaw = 0, kBackGradFine = 1, kBackStep = 2 };
+struct BackArgs {
+    const float* res;                // [batch][n_sub][n_det]
+    const float4* rayf; const float2* rayi; const float4* view;
+    int ns, n_det, first_view, view_step, n_sub, batch;
+    float step;
+    int mode; int s; int n;          // fine side for modes 1, 2
+    float scale;                     // multiplies the gathered sum
+    const float* y; float eta;       // mode 2: z = y - eta * scale * sum
+    float* out;
+};
+cudaError_t launch_backward(const BackArgs& a, cudaStream_t st);
+
+cudaError_t launch_pool(const float* fine, float* coarse, int n, int s, int batch, cudaStream_t st);
+cudaError_t launch_unpool(const float* coarse, float* fine, int n, int s, int batch, cudaStream_t st);
+
+// TV (FGP) --------------------------------------------------------------------
+struct TvBuffers {
+    float* p;     // [2][batch][n][n]  current dual (p, q)
+    float* ra;    // [2][batch][n][n]  momentum point, ping
+    float* rb;    // [2][batch][n][n]  momentum point, pong
+};
+// One FGP iteration: reads r_in (unless first), p; writes p and r_out.
+cudaError_t launch_tv_iter(const float* z, TvBuffers b, const float* r_in, float* r_out, int n,
+                           int batch, float lambda, float mom, int first, cudaStream_t st);
+// x = z - lambda L(p) (or z when iters == 0), then relaxation and momentum:
+//   xi = (1-alpha) z + alpha x;  y = xi + a (xi - xprev);  xprev <- xi.
+// With y == nullptr it writes x only (plain denoiser output to xprev).
+// If mse_partials != nullptr, accumulates sum (xi - xtrue)^2 per block.
+cudaError_t launch_tv_final(const float* z, const float* p, int have_p, int n, int batch, float lambda,
+                            float alpha, float a, float* xprev, float* y, const float* xtrue,
+                            double* mse_partials, cudaStream_t st);
+
+// Reductions -------------------------------------------------------------------
+enum RedMode { kRedDot = 0, kRedDiffSq = 1, kRedSq = 2, kRedTv = 3 };
+// partials[inst][kRedBlocks] for `count` elements per instance (stride `stride`).
+cudaError_t launch_reduce_partial(int mode, const float* a, const float* b, size_t count,
+                                  size_t stride, int batch, int n, double* partials, cudaStream_t st);
+// out[inst * out_stride + out_off] = sum_k partials[inst][k] (fixed order).
+cudaError_t launch_reduce_final(const double* partials, int nparts, int batch, double* out,
+                                int out_stride, int out_off, cudaStream_t st);
+// u = w * factor, where factor = 1 / sqrt(norm2[0]) (device scalar).
+cudaError_t launch_scale_by_rnorm(const float* w, float* u, size_t count, const double* norm2,
+                                  cudaStream_t st);
+cudaError_t launch_fill(float* x, size_t count, float v, cudaStream_t st);
+cudaError_t launch_copy(const float* src, float* dst, size_t count, cudaStream_t st);
+cudaError_t launch_count_samples(const int2* rayk, int n_det, int first_view, int view_step,
+                                 int n_sub, double* partial, cudaStream_t st);
+
+}  // namespace pnp

@@ -1,0 +1,366 @@
+// Fan-beam projector pair on sm_103a: forward A_s (ray-driven, fixed step,
+// bilinear taps) and its exact transpose A_s^T (pixel-driven gather, no
+// atomics), plus the image-space sketch S (average pooling) and U = S^T.
+//
+// Paper: Eq. 1 (b = A x + w), Eq. 4 (A_s acting on S(x)), Eq. 5 (A^T), Alg. 1.
+// The discretisation (the paper names only "fan-beam X-ray CT", Sec. 3):
+//   ray (v,j) with unit direction d and foot point F (nearest to the origin);
+//   samples q_k = F + (k+1/2) step d (level pixels), each weighted by
+//   step * s fine pixels; value at q = bilinear interpolant of the level image,
+//   zero outside.  The forward sums samples along each ray; the transpose
+//   gathers, for each pixel, every (ray, sample) pair whose bilinear hat covers
+//   the pixel.  Both visit exactly the samples strictly inside the image box.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "pnp_internal.cuh"
+
+namespace pnp {
+
+std::atomic<uint64_t> g_launches{0};
+
+namespace {
+
+constexpr float kMagic = 12582912.0f;      // 1.5 * 2^23: x + kMagic rounds x to an integer
+constexpr int kMagicBits = 0x4B400000;     // bit pattern of kMagic
+
+__host__ __device__ inline int div_up(long a, long b) { return (int)((a + b - 1) / b); }
+
+// ------------------------------------------------------------------ set-up (FP64)
+// One thread per (view, bin): the ray's geometry in double precision, rounded once.
+__global__ void k_setup_rays(int n, int s, int n_views, int n_det, double dso, double ddo,
+                             double pitch, double angle0, double span, double step,
+                             float4* __restrict__ rayf, float2* __restrict__ rayi,
+                             int2* __restrict__ rayk, float4* __restrict__ view)
+{
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)n_views * n_det) return;
+    int v = (int)(idx / n_det), j = (int)(idx % n_det);
+    const int ns = n / s;
+    double beta = angle0 + span * (double)v / (double)n_views;
+    double cb = cos(beta), sb = sin(beta);
+    double sx = dso * cb, sy = dso * sb;
+    double u = ((double)j - 0.5 * (double)(n_det - 1)) * pitch;
+    double px = -ddo * cb - u * sb, py = -ddo * sb + u * cb;
+    double ex = px - sx, ey = py - sy;
+    double len = sqrt(ex * ex + ey * ey);
+    double dx = ex / len, dy = ey / len;
+    double sd = sx * dx + sy * dy;
+    // foot point in level index units (pixel centre ix at ix)
+    double fx = (sx - sd * dx) / s + 0.5 * (ns - 1);
+    double fy = (sy - sd * dy) / s + 0.5 * (ns - 1);
+    // samples strictly inside the box (-1, ns)^2 of index coordinates
+    double tlo = -1e300, thi = 1e300;
+    const double lo = -1.0, hi = (double)ns;
+    if (fabs(dx) > 0.0) {
+        double t1 = (lo - fx) / dx, t2 = (hi - fx) / dx;
+        tlo = fmax(tlo, fmin(t1, t2));
+        thi = fmin(thi, fmax(t1, t2));
+    } else if (!(fx > lo && fx < hi)) {
+        thi = tlo;
+    }
+    if (fabs(dy) > 0.0) {
+        double t1 = (lo - fy) / dy, t2 = (hi - fy) / dy;
+        tlo = fmax(tlo, fmin(t1, t2));
+        thi = fmin(thi, fmax(t1, t2));
+    } else if (!(fy > lo && fy < hi)) {
+        thi = tlo;
+    }
+    int klo = 0, khi = -1;
+    if (thi > tlo) {
+        // (k + 1/2) step > tlo  and  (k + 1/2) step < thi
+        klo = (int)floor(tlo / step - 0.5) + 1;
+        khi = (int)ceil(thi / step - 0.5) - 1;
+        if (khi < klo) { klo = 0; khi = -1; }
+    }
+    rayf[idx] = make_float4((float)(fx + 1.5), (float)(fy + 1.5), (float)dx, (float)dy);
+    const double tiny = 1e-12;
+    double adx = fabs(dx) < tiny ? copysign(tiny, dx) : dx;
+    double ady = fabs(dy) < tiny ? copysign(tiny, dy) : dy;
+    rayi[idx] = make_float2((float)(1.0 / adx), (float)(1.0 / ady));
+    rayk[idx] = make_int2(klo, khi);
+    if (j == 0) view[v] = make_float4((float)cb, (float)sb, (float)(dso / s), (float)((dso + ddo) / pitch));
+}
+
+// ------------------------------------------------------------------ coefficient image
+// quad[iy0+2][ix0+2] holds the bilinear coefficients of the cell whose lower
+// corner is level pixel (ix0, iy0), in the centred variables u, w in [-1/2, 1/2]:
+//   f = c0 + u c1 + w (c2 + u c3)
+// with a = I(ix0,iy0), b = I(ix0+1,iy0), c = I(ix0,iy0+1), d = I(ix0+1,iy0+1)
+// (zero outside), I the s x s average pool of the fine image.
+__device__ __forceinline__ float pooled(const float* __restrict__ fine, int n, int s, int ns, int i,
+                                        int j)
+{
+    if (i < 0 || j < 0 || i >= ns || j >= ns) return 0.0f;
+    if (s == 1) return __ldg(fine + (long)j * n + i);
+    float acc = 0.0f;
+    for (int b = 0; b < s; ++b)
+        for (int a = 0; a < s; ++a) acc += __ldg(fine + (long)(j * s + b) * n + (i * s + a));
+    return acc * (1.0f / (float)(s * s));
+}
+
+__global__ void k_prep_quad(const float* __restrict__ fine, int n, int s, int qw,
+                            float4* __restrict__ quad)
+{
+    int qx = blockIdx.x * blockDim.x + threadIdx.x;
+    int qy = blockIdx.y * blockDim.y + threadIdx.y;
+    int inst = blockIdx.z;
+    if (qx >= qw || qy >= qw) return;
+    const int ns = n / s;
+    const float* f = fine + (long)inst * n * n;
+    int ix0 = qx - kPad, iy0 = qy - kPad;
+    float a = pooled(f, n, s, ns, ix0, iy0), b = pooled(f, n, s, ns, ix0 + 1, iy0);
+    float c = pooled(f, n, s, ns, ix0, iy0 + 1), d = pooled(f, n, s, ns, ix0 + 1, iy0 + 1);
+    float4 q;
+    q.x = 0.25f * ((a + b) + (c + d));
+    q.y = 0.5f * ((b - a) + (d - c));
+    q.z = 0.5f * ((c - a) + (d - b));
+    q.w = (a - b) - (c - d);
+    quad[(long)inst * qw * qw + (long)qy * qw + qx] = q;
+}
+
+// ------------------------------------------------------------------ forward A_s
+// Warp = R rays x Q phases (R*Q = 32): lane (r, q) sums the samples k = k_lo + q,
+// k_lo + q + Q, ... of ray r; the Q partial sums are combined by shuffles in a
+// fixed order, so the result is deterministic.  One 16-byte load per sample.
+template <int Q>
+__global__ void __launch_bounds__(256) k_forward(FwdArgs a)
+{
+    constexpr int R = 32 / Q;
+    const int lane = threadIdx.x & 31;
+    const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int r = lane / Q, q = lane % Q;
+    const long rays_inst = (long)a.n_sub * a.n_det;
+    const long gray = warp * R + r;
+    const bool active = gray < rays_inst * a.batch;
+    float acc = 0.0f;
+    long out_idx = 0;
+    int v = 0, j = 0, inst = 0;
+    if (active) {
+        inst = (int)(gray / rays_inst);
+        long ray = gray - (long)inst * rays_inst;
+        int vs = (int)(ray / a.n_det);
+        j = (int)(ray - (long)vs * a.n_det);
+        v = a.first_view + vs * a.view_step;
+        out_idx = gray;
+        const float4 f = __ldg(a.rayf + (long)v * a.n_det + j);
+        const int2 kr = __ldg(a.rayk + (long)v * a.n_det + j);
+        const float4* __restrict__ img = a.quad + (long)inst * a.quad_stride;
+        const int qw = a.qw;
+        float kf = (float)(kr.x + q) + 0.5f;
+        const float dk = (float)Q;
+#pragma unroll 4
+        for (int k = kr.x + q; k <= kr.y; k += Q) {
+            const float t = kf * a.step;
+            const float X = fmaf(t, f.z, f.x);
+            const float Y = fmaf(t, f.w, f.y);
+            const float mx = __fadd_rn(X, kMagic);
+            const float my = __fadd_rn(Y, kMagic);
+            const float u = __fsub_rn(X, __fsub_rn(mx, kMagic));
+            const float w = __fsub_rn(Y, __fsub_rn(my, kMagic));
+            const int ix = __float_as_int(mx) - kMagicBits;
+            const int iy = __float_as_int(my) - kMagicBits;
+            const float4 c = __ldg(img + iy * qw + ix);
+            acc += fmaf(w, fmaf(u, c.w, c.z), fmaf(u, c.y, c.x));
+            kf += dk;
+        }
+    }
+#pragma unroll
+    for (int o = Q / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (active && q == 0) {
+        float val = a.weight * acc;
+        if (a.b) val -= __ldg(a.b + ((long)inst * a.n_views + v) * a.n_det + j);
+        a.out[out_idx] = val;
+    }
+}
+
+// ------------------------------------------------------------------ transpose A_s^T
+// One thread per level pixel.  For each view: the detector interval that the
+// pixel's hat support (the 2x2 square around its centre) can shadow, then for
+// every bin in it the exact sample range of that ray inside the square (slab
+// test) and the sum of hat(X - ix) hat(Y - iy) over those samples.
+__global__ void __launch_bounds__(256) k_backward(BackArgs a)
+{
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iy = blockIdx.y * blockDim.y + threadIdx.y;
+    const int inst = blockIdx.z;
+    if (ix >= a.ns || iy >= a.ns) return;
+    const float half = 0.5f * (float)(a.ns - 1);
+    const float cx = (float)ix - half, cy = (float)iy - half;   // centred, level units
+    const float px = (float)ix + 1.5f, py = (float)iy + 1.5f;   // primed index frame
+    const float jc = 0.5f * (float)(a.n_det - 1);
+    const float inv_step = 1.0f / a.step;
+    const float kSqrt2 = 1.41421356f;
+    const float* __restrict__ res = a.res + (long)inst * a.n_sub * a.n_det;
+    float total = 0.0f;
+    for (int vs = 0; vs < a.n_sub; ++vs) {
+        const int v = a.first_view + vs * a.view_step;
+        const float4 vp = __ldg(a.view + v);   // cos b, sin b, dso/s, (dso+ddo)/pitch
+        const float along = cx * vp.x + cy * vp.y;
+        const float lat = cy * vp.x - cx * vp.y;
+        const float den = vp.z - along;
+        const float inv = __frcp_rn(den);
+        const float uj = vp.w * lat * inv + jc;
+        // Conservative half-width (in bins) of the shadow of a disc of radius
+        // sqrt(2) around the centre: D_sd sec^2(gamma) asin(rho / dist) / pitch.
+        const float invp = inv * (1.0f + 2.0f * kSqrt2 * inv);
+        const float T = (fabsf(lat) + kSqrt2) * invp;
+        const float hw = kSqrt2 * vp.w * fmaf(T, T, 1.0f) * invp * 1.01f + 0.02f;
+        const int jlo = max(0, (int)ceilf(uj - hw));
+        const int jhi = min(a.n_det - 1, (int)floorf(uj + hw));
+        const long base = (long)v * a.n_det;
+        const float* __restrict__ rrow = res + (long)vs * a.n_det;
+        float accv = 0.0f;
+        for (int j = jlo; j <= jhi; ++j) {
+            const float4 f = __ldg(a.rayf + base + j);
+            const float2 iv = __ldg(a.rayi + base + j);
+            const float ax = px - f.x, ay = py - f.y;
+            const float tx1 = (ax - 1.0f) * iv.x, tx2 = (ax + 1.0f) * iv.x;
+            const float ty1 = (ay - 1.0f) * iv.y, ty2 = (ay + 1.0f) * iv.y;
+            const float tlo = fmaxf(fminf(tx1, tx2), fminf(ty1, ty2));
+            const float thi = fminf(fmaxf(tx1, tx2), fmaxf(ty1, ty2));
+            if (!(thi > tlo)) continue;
+            const int klo = (int)ceilf(fmaf(tlo, inv_step, -0.5f));
+            const int khi = (int)floorf(fmaf(thi, inv_step, -0.5f));
+            float w = 0.0f;
+            float kf = (float)klo + 0.5f;
+            for (int k = klo; k <= khi; ++k) {
+                const float t = kf * a.step;
+                const float X = fmaf(t, f.z, f.x);
+                const float Y = fmaf(t, f.w, f.y);
+                const float hx = 1.0f - fabsf(X - px);
+                const float hy = 1.0f - fabsf(Y - py);
+                w = fmaf(fmaxf(hx, 0.0f), fmaxf(hy, 0.0f), w);
+                kf += 1.0f;
+            }
+            accv = fmaf(w, __ldg(rrow + j), accv);
+        }
+        total += accv;
+    }
+    const float val = a.scale * total;
+    if (a.mode == kBackRaw) {
+        a.out[((long)inst * a.ns + iy) * a.ns + ix] = val;
+        return;
+    }
+    const int s = a.s;
+    for (int bb = 0; bb < s; ++bb) {
+        const long row = ((long)inst * a.n + (long)iy * s + bb) * a.n + (long)ix * s;
+        for (int aa = 0; aa < s; ++aa) {
+            if (a.mode == kBackGradFine)
+                a.out[row + aa] = val;
+            else
+                a.out[row + aa] = __ldg(a.y + row + aa) - a.eta * val;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ S and S^T
+__global__ void k_pool(const float* __restrict__ fine, float* __restrict__ coarse, int n, int s)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    int inst = blockIdx.z;
+    int ns = n / s;
+    if (i >= ns || j >= ns) return;
+    coarse[((long)inst * ns + j) * ns + i] = pooled(fine + (long)inst * n * n, n, s, ns, i, j);
+}
+
+__global__ void k_unpool(const float* __restrict__ coarse, float* __restrict__ fine, int n, int s)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    int inst = blockIdx.z;
+    int ns = n / s;
+    if (x >= n || y >= n) return;
+    fine[((long)inst * n + y) * n + x] =
+        __ldg(coarse + ((long)inst * ns + y / s) * ns + x / s) * (1.0f / (float)(s * s));
+}
+
+__global__ void k_count_samples(const int2* __restrict__ rayk, int n_det, int first_view,
+                                int view_step, int n_sub, double* __restrict__ out)
+{
+    __shared__ double sh[256];
+    double acc = 0.0;
+    long total = (long)n_sub * n_det;
+    for (long i = threadIdx.x; i < total; i += blockDim.x) {
+        int vs = (int)(i / n_det), j = (int)(i % n_det);
+        int2 kr = rayk[(long)(first_view + vs * view_step) * n_det + j];
+        if (kr.y >= kr.x) acc += (double)(kr.y - kr.x + 1);
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+inline cudaError_t counted(cudaError_t e = cudaGetLastError())
+{
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return e;
+}
+
+}  // namespace
+
+cudaError_t launch_setup_rays(const pnp_geom& g, const LevelLayout& L, char* ws, cudaStream_t st)
+{
+    long nr = (long)g.n_views * g.n_det;
+    k_setup_rays<<<div_up(nr, 128), 128, 0, st>>>(
+        g.n, L.factor, g.n_views, g.n_det, g.dso, g.ddo, g.det_pitch, g.angle0, g.angle_span,
+        g.step, (float4*)(ws + L.off_rayf), (float2*)(ws + L.off_rayi), (int2*)(ws + L.off_rayk),
+        (float4*)(ws + L.off_view));
+    return counted();
+}
+
+cudaError_t launch_prep_quad(const float* fine, int n, int s, int batch, float4* quad, int qw,
+                             cudaStream_t st)
+{
+    dim3 blk(32, 8), grd(div_up(qw, 32), div_up(qw, 8), batch);
+    k_prep_quad<<<grd, blk, 0, st>>>(fine, n, s, qw, quad);
+    return counted();
+}
+
+cudaError_t launch_forward(const FwdArgs& a, cudaStream_t st)
+{
+    constexpr int Q = 4;
+    long rays = (long)a.n_sub * a.n_det * a.batch;
+    long warps = (rays + (32 / Q) - 1) / (32 / Q);
+    long threads = warps * 32;
+    k_forward<Q><<<div_up(threads, 256), 256, 0, st>>>(a);
+    return counted();
+}
+
+cudaError_t launch_backward(const BackArgs& a, cudaStream_t st)
+{
+    dim3 blk(16, 16), grd(div_up(a.ns, 16), div_up(a.ns, 16), a.batch);
+    k_backward<<<grd, blk, 0, st>>>(a);
+    return counted();
+}
+
+cudaError_t launch_pool(const float* fine, float* coarse, int n, int s, int batch, cudaStream_t st)
+{
+    int ns = n / s;
+    dim3 blk(32, 8), grd(div_up(ns, 32), div_up(ns, 8), batch);
+    k_pool<<<grd, blk, 0, st>>>(fine, coarse, n, s);
+    return counted();
+}
+
+cudaError_t launch_unpool(const float* coarse, float* fine, int n, int s, int batch, cudaStream_t st)
+{
+    dim3 blk(32, 8), grd(div_up(n, 32), div_up(n, 8), batch);
+    k_unpool<<<grd, blk, 0, st>>>(coarse, fine, n, s);
+    return counted();
+}
+
+cudaError_t launch_count_samples(const int2* rayk, int n_det, int first_view, int view_step,
+                                 int n_sub, double* partial, cudaStream_t st)
+{
+    k_count_samples<<<1, 256, 0, st>>>(rayk, n_det, first_view, view_step, n_sub, partial);
+    return counted();
+}
+
+}  // namespace pnp

@@ -1,0 +1,58 @@
+"""CPU-side checks of the C ABI: the library builds and loads without a GPU,
+exports every function include/pnp_ms2g.h declares, and rejects invalid
+arguments on the host before anything is launched."""
+import ctypes as C
+import math
+
+import pytest
+
+import paper_2203_07308_gb300 as pnp
+from paper_2203_07308_gb300 import _native, build, synth
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _native.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _native.header_functions()
+    assert len(names) >= 15
+    raw = C.CDLL(_native.LIB_PATH)
+    for n in names:
+        assert hasattr(raw, n), n
+
+
+def test_workspace_size_and_invalid_geometry(lib):
+    g = synth.make_geometry(256, 360, 512)
+    nbytes = pnp.workspace_size(g)
+    assert nbytes > 360 * 512 * 24 * 3
+    bad = synth.Geometry(n=256, n_views=360, n_det=512, dso=100.0, ddo=100.0, det_pitch=1.0)
+    with pytest.raises(pnp.PnpError) as e:
+        pnp.workspace_size(bad)
+    assert e.value.code == _native.PNP_EINVAL and "source too close" in str(e.value)
+    for field, val in [("n", 2), ("n_views", 0), ("det_pitch", 0.0), ("step", -1.0), ("dso", math.inf)]:
+        kw = dict(g.__dict__)
+        kw[field] = val
+        with pytest.raises(pnp.PnpError):
+            pnp.workspace_size(synth.Geometry(**kw))
+
+
+def test_calls_reject_bad_arguments_before_launch(lib):
+    g = _native.geom(synth.make_geometry(64, 90, 96))
+    null = C.c_void_p(0)
+    # unprepared (NULL) workspace, bad factor, bad subset: rejected on the host
+    assert lib.pnp_project(C.byref(g), 1, C.c_void_p(16), None, C.c_void_p(16), 0, 1, null, null) == 1
+    assert lib.pnp_project(C.byref(g), 3, C.c_void_p(16), None, C.c_void_p(16), 0, 1, C.c_void_p(256), null) == 1
+    assert lib.pnp_project(C.byref(g), 1, C.c_void_p(16), None, C.c_void_p(16), 5, 4, C.c_void_p(256), null) == 1
+    # a workspace never passed to pnp_setup is reported as such
+    assert lib.pnp_project(C.byref(g), 1, C.c_void_p(16), None, C.c_void_p(16), 0, 1, C.c_void_p(4096), null) == 5
+    assert "pnp_setup" in pnp.last_error()
+    # factor 8 is unavailable at n = 24 (fewer than 4 coarse pixels per side)
+    g24 = _native.geom(synth.make_geometry(24, 10, 32))
+    assert lib.pnp_sketch(C.byref(g24), 8, C.c_void_p(16), C.c_void_p(16), null) == 1
+    assert lib.pnp_tv_denoise(C.c_void_p(16), C.c_void_p(16), 8, 1, C.c_float(0.1), 5, null, 0, null) == 1
+    size = C.c_size_t(0)
+    assert lib.pnp_tv_workspace_size(64, 2, C.byref(size)) == 0 and size.value == 6 * 2 * 64 * 64 * 4
+    assert lib.pnp_launch_count() == 0
