@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="only the warm-up and the timed steps (inside an NVTX range 'timed'), "
+                         "for ncu: no end-to-end, time-to-PSNR or CPU legs")
     return ap.parse_args()
 
 
@@ -257,10 +260,22 @@ def run_native(args, rank, world):
         d_x.zero_()
         plan.run(wl.stages, eta, seq, d_b, d_x, **kw)
 
+    launches_setup = pnp.launch_count()
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
     barrier(world)
+
+    if args.profile:
+        torch.cuda.nvtx.range_push("timed")
+        for _ in range(args.steps):
+            step()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        if rank == 0:
+            print(json.dumps({"profile": True, "steps": args.steps, "launches_per_step":
+                              (pnp.launch_count() - launches_setup) // (args.steps + max(args.warmup, 3))}))
+        return
 
     # ---- timed region: K steps, L2 flushed before each, device time by CUDA events
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))

@@ -417,7 +417,12 @@ int pnp_tv_denoise(const float* d_z, float* d_x, int n, int batch, float lambda,
     if (d_z == d_x) return fail(PNP_EINVAL, "z and x must not alias");
     if (iters < 0 || iters > 100000) return fail(PNP_EINVAL, "iters outside [0, 100000]");
     if (!(lambda >= 0.0f) || !std::isfinite(lambda)) return fail(PNP_EINVAL, "lambda must be >= 0");
-    if (iters > 0 && lambda > 0.0f) {
+    int rows = 0;
+    const int cluster = iters > 0 && lambda > 0.0f && iters <= kFusedTvMaxIters ? fused_tv_cluster(n, &rows) : 0;
+    if (cluster > 0) {
+        PNP_CUDA(launch_tv_fused(d_z, n, batch, lambda, iters, 1.0f, 0.0f, d_x, nullptr, nullptr,
+                                 nullptr, cluster, rows, S(stream)));
+    } else if (iters > 0 && lambda > 0.0f) {
         if (!d_ws || ws_bytes < need) return fail(PNP_EINVAL, "TV workspace needs %zu bytes", need);
         const size_t img = (size_t)batch * n * n;
         TvBuffers tv{(float*)d_ws, (float*)d_ws + 2 * img, (float*)d_ws + 4 * img};
@@ -532,6 +537,8 @@ int pnp_run(const pnp_geom* g, const pnp_stage* stages, int n_stages, const doub
     const int tv_parts = ((g->n + 31) / 32) * ((g->n + 7) / 8);
     const bool do_tv = pr.tv_iters > 0 && pr.lambda > 0.0f;
     std::vector<float> mom = fgp_momenta(do_tv ? pr.tv_iters : 0);
+    int tv_rows = 0;
+    const int tv_cluster = do_tv && pr.tv_iters <= kFusedTvMaxIters ? fused_tv_cluster(g->n, &tv_rows) : 0;
     PNP_CUDA(launch_copy(d_x, y, img, st));
     long i = 0;
     for (int k = 0; k < n_stages; ++k) {
@@ -541,6 +548,14 @@ int pnp_run(const pnp_geom* g, const pnp_stage* stages, int n_stages, const doub
             ++i;
             const int p = P > 1 ? h_subset_seq[i - 1] : 0;
             if (int e = grad_into(*g, L, li, ws, y, d_b, p, P, kBackStep, (float)h_eta[k], z, st)) return e;
+            const float a = pr.momentum ? (float)((double)(i - 1) / (double)(i + 3)) : 0.0f;
+            double* mp = h_psnr_log ? part : nullptr;
+            if (tv_cluster > 0) {
+                PNP_CUDA(launch_tv_fused(z, g->n, g->batch, pr.lambda, pr.tv_iters, pr.alpha, a, d_x, y,
+                                         d_xtrue, mp, tv_cluster, tv_rows, st));
+                if (mp) PNP_CUDA(launch_reduce_final(part, tv_cluster, g->batch, dlog + (i - 1) * g->batch, 1, 0, st));
+                continue;
+            }
             if (do_tv) {
                 const float* rin = tv.ra;
                 float* rout = tv.rb;
@@ -551,8 +566,6 @@ int pnp_run(const pnp_geom* g, const pnp_stage* stages, int n_stages, const doub
                     rin = tmp;
                 }
             }
-            const float a = pr.momentum ? (float)((double)(i - 1) / (double)(i + 3)) : 0.0f;
-            double* mp = h_psnr_log ? part : nullptr;
             PNP_CUDA(launch_tv_final(z, tv.p, do_tv, g->n, g->batch, pr.lambda, pr.alpha, a, d_x, y,
                                      d_xtrue, mp, st));
             if (mp) PNP_CUDA(launch_reduce_final(part, tv_parts, g->batch, dlog + (i - 1) * g->batch, 1, 0, st));

@@ -2,8 +2,8 @@
 //
 // Data layout in the caller's workspace (all offsets 256-byte aligned), per
 // sketch level s in {1,2,4,8} with n % s == 0 and n/s >= 4:
-//   rayf  float4 [n_views*n_det]  (F'_x, F'_y, d_x, d_y): foot point in level
-//                                 index units shifted by +1.5 (see below), unit dir
+//   rayf  float4 [n_views*n_det]  (F'_x, F'_y, d_x, d_y): foot point in the
+//                                 primed frame (see below), unit direction
 //   rayi  float2 [n_views*n_det]  (1/d_x, 1/d_y), clamped away from 0
 //   rayk  int2   [n_views*n_det]  first/last sample index k inside the image box
 //   view  float4 [n_views]        (cos b, sin b, dso/s, (dso+ddo)/pitch)
@@ -11,9 +11,12 @@
 // then the residual sinogram, the fine-grid loop buffers, the TV buffers, the
 // power-iteration vectors and the FP64 reduction scratch.
 //
-// Index frame: level pixel (ix,iy) has centre index coordinate (ix,iy); the
-// primed frame adds 1.5 so that round(X') = floor(X) + 2 is directly the column
-// of the 2-pixel-padded coefficient image and X' - round(X') = frac(X) - 1/2.
+// Index frame: level pixel (ix,iy) has centre index coordinate (ix,iy).  The
+// kernels work in the primed frame X' = X - c0 + 1.5 with c0 = n_s/2: its
+// origin sits at the image centre (coordinates stay below ~0.71 n_s, which
+// halves FP32 position rounding against a corner origin), round(X') + c0 =
+// floor(X) + 2 is the column of the 2-pixel-padded coefficient image, and
+// X' - round(X') = frac(X) - 1/2.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -102,6 +105,17 @@ cudaError_t launch_tv_iter(const float* z, TvBuffers b, const float* r_in, float
 cudaError_t launch_tv_final(const float* z, const float* p, int have_p, int n, int batch, float lambda,
                             float alpha, float a, float* xprev, float* y, const float* xtrue,
                             double* mse_partials, cudaStream_t st);
+
+// Fused FGP in one thread-block cluster per image (state in distributed shared
+// memory).  fused_tv_cluster returns the cluster size (0 = image too large) and
+// the rows per CTA; launch_tv_fused then runs all iterations plus the final
+// step of launch_tv_final in one launch (mse partials: [batch][cluster]).
+constexpr int kFusedTvMaxIters = 256;
+constexpr int kFusedTvSmem = 200 * 1024;
+int fused_tv_cluster(int n, int* rows);
+cudaError_t launch_tv_fused(const float* z, int n, int batch, float lambda, int iters, float alpha,
+                            float amom, float* xprev, float* y, const float* xtrue, double* mse_part,
+                            int cluster, int rows, cudaStream_t st);
 
 // Reductions -------------------------------------------------------------------
 enum RedMode { kRedDot = 0, kRedDiffSq = 1, kRedSq = 2, kRedTv = 3 };

@@ -51,6 +51,7 @@ __global__ void k_setup_rays(int n, int s, int n_views, int n_det, double dso, d
     // foot point in level index units (pixel centre ix at ix)
     double fx = (sx - sd * dx) / s + 0.5 * (ns - 1);
     double fy = (sy - sd * dy) / s + 0.5 * (ns - 1);
+    const int c0 = ns / 2;   // origin of the primed frame: index column/row c0
     // samples strictly inside the box (-1, ns)^2 of index coordinates
     double tlo = -1e300, thi = 1e300;
     const double lo = -1.0, hi = (double)ns;
@@ -75,7 +76,7 @@ __global__ void k_setup_rays(int n, int s, int n_views, int n_det, double dso, d
         khi = (int)ceil(thi / step - 0.5) - 1;
         if (khi < klo) { klo = 0; khi = -1; }
     }
-    rayf[idx] = make_float4((float)(fx + 1.5), (float)(fy + 1.5), (float)dx, (float)dy);
+    rayf[idx] = make_float4((float)(fx - c0 + 1.5), (float)(fy - c0 + 1.5), (float)dx, (float)dy);
     const double tiny = 1e-12;
     double adx = fabs(dx) < tiny ? copysign(tiny, dx) : dx;
     double ady = fabs(dy) < tiny ? copysign(tiny, dy) : dy;
@@ -149,6 +150,7 @@ __global__ void __launch_bounds__(256) k_forward(FwdArgs a)
         const int2 kr = __ldg(a.rayk + (long)v * a.n_det + j);
         const float4* __restrict__ img = a.quad + (long)inst * a.quad_stride;
         const int qw = a.qw;
+        const int bias = kMagicBits - (qw - 3) / 2;   // column = round(X') + c0
         float kf = (float)(kr.x + q) + 0.5f;
         const float dk = (float)Q;
 #pragma unroll 4
@@ -160,8 +162,8 @@ __global__ void __launch_bounds__(256) k_forward(FwdArgs a)
             const float my = __fadd_rn(Y, kMagic);
             const float u = __fsub_rn(X, __fsub_rn(mx, kMagic));
             const float w = __fsub_rn(Y, __fsub_rn(my, kMagic));
-            const int ix = __float_as_int(mx) - kMagicBits;
-            const int iy = __float_as_int(my) - kMagicBits;
+            const int ix = __float_as_int(mx) - bias;
+            const int iy = __float_as_int(my) - bias;
             const float4 c = __ldg(img + iy * qw + ix);
             acc += fmaf(w, fmaf(u, c.w, c.z), fmaf(u, c.y, c.x));
             kf += dk;
@@ -177,69 +179,86 @@ __global__ void __launch_bounds__(256) k_forward(FwdArgs a)
 }
 
 // ------------------------------------------------------------------ transpose A_s^T
-// One thread per level pixel.  For each view: the detector interval that the
-// pixel's hat support (the 2x2 square around its centre) can shadow, then for
-// every bin in it the exact sample range of that ray inside the square (slab
-// test) and the sum of hat(X - ix) hat(Y - iy) over those samples.
-__global__ void __launch_bounds__(256) k_backward(BackArgs a)
+// Block = 8 x 8 level pixels x G view groups.  Thread (pixel, g) gathers the
+// views g, g+G, g+2G, ... of the subset: for each view, the detector interval
+// that the pixel's hat support (the 2x2 square around its centre) can shadow,
+// then for every bin in it the exact sample range of that ray inside the square
+// (slab test) and the sum of hat(X - ix) hat(Y - iy) over those samples.  The G
+// partial sums are added in a fixed order through shared memory, so the result
+// is deterministic for a given G (G depends only on the problem size).
+constexpr int kBackTile = 8;
+constexpr int kBackMaxGroups = 8;
+
+__global__ void __launch_bounds__(512) k_backward(BackArgs a)
 {
-    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
-    const int iy = blockIdx.y * blockDim.y + threadIdx.y;
-    const int inst = blockIdx.z;
-    if (ix >= a.ns || iy >= a.ns) return;
-    const float half = 0.5f * (float)(a.ns - 1);
-    const float cx = (float)ix - half, cy = (float)iy - half;   // centred, level units
-    const float px = (float)ix + 1.5f, py = (float)iy + 1.5f;   // primed index frame
-    const float jc = 0.5f * (float)(a.n_det - 1);
-    const float inv_step = 1.0f / a.step;
-    const float kSqrt2 = 1.41421356f;
-    const float* __restrict__ res = a.res + (long)inst * a.n_sub * a.n_det;
+    const int tx = threadIdx.x, ty = threadIdx.y, g = threadIdx.z, G = blockDim.z;
+    const int tiles_x = (a.ns + kBackTile - 1) / kBackTile;
+    const int ix = (blockIdx.x % tiles_x) * kBackTile + tx;
+    const int iy = (blockIdx.x / tiles_x) * kBackTile + ty;
+    const int inst = blockIdx.y;
+    const bool inside = ix < a.ns && iy < a.ns;
+    __shared__ float part[kBackMaxGroups][kBackTile * kBackTile];
     float total = 0.0f;
-    for (int vs = 0; vs < a.n_sub; ++vs) {
-        const int v = a.first_view + vs * a.view_step;
-        const float4 vp = __ldg(a.view + v);   // cos b, sin b, dso/s, (dso+ddo)/pitch
-        const float along = cx * vp.x + cy * vp.y;
-        const float lat = cy * vp.x - cx * vp.y;
-        const float den = vp.z - along;
-        const float inv = __frcp_rn(den);
-        const float uj = vp.w * lat * inv + jc;
-        // Conservative half-width (in bins) of the shadow of a disc of radius
-        // sqrt(2) around the centre: D_sd sec^2(gamma) asin(rho / dist) / pitch.
-        const float invp = inv * (1.0f + 2.0f * kSqrt2 * inv);
-        const float T = (fabsf(lat) + kSqrt2) * invp;
-        const float hw = kSqrt2 * vp.w * fmaf(T, T, 1.0f) * invp * 1.01f + 0.02f;
-        const int jlo = max(0, (int)ceilf(uj - hw));
-        const int jhi = min(a.n_det - 1, (int)floorf(uj + hw));
-        const long base = (long)v * a.n_det;
-        const float* __restrict__ rrow = res + (long)vs * a.n_det;
-        float accv = 0.0f;
-        for (int j = jlo; j <= jhi; ++j) {
-            const float4 f = __ldg(a.rayf + base + j);
-            const float2 iv = __ldg(a.rayi + base + j);
-            const float ax = px - f.x, ay = py - f.y;
-            const float tx1 = (ax - 1.0f) * iv.x, tx2 = (ax + 1.0f) * iv.x;
-            const float ty1 = (ay - 1.0f) * iv.y, ty2 = (ay + 1.0f) * iv.y;
-            const float tlo = fmaxf(fminf(tx1, tx2), fminf(ty1, ty2));
-            const float thi = fminf(fmaxf(tx1, tx2), fmaxf(ty1, ty2));
-            if (!(thi > tlo)) continue;
-            const int klo = (int)ceilf(fmaf(tlo, inv_step, -0.5f));
-            const int khi = (int)floorf(fmaf(thi, inv_step, -0.5f));
-            float w = 0.0f;
-            float kf = (float)klo + 0.5f;
-            for (int k = klo; k <= khi; ++k) {
-                const float t = kf * a.step;
-                const float X = fmaf(t, f.z, f.x);
-                const float Y = fmaf(t, f.w, f.y);
-                const float hx = 1.0f - fabsf(X - px);
-                const float hy = 1.0f - fabsf(Y - py);
-                w = fmaf(fmaxf(hx, 0.0f), fmaxf(hy, 0.0f), w);
-                kf += 1.0f;
+    if (inside) {
+        const float half = 0.5f * (float)(a.ns - 1);
+        const float cx = (float)ix - half, cy = (float)iy - half;   // centred, level units
+        const int c0 = a.ns / 2;
+        const float px = (float)(ix - c0) + 1.5f, py = (float)(iy - c0) + 1.5f;   // primed frame
+        const float jc = 0.5f * (float)(a.n_det - 1);
+        const float inv_step = 1.0f / a.step;
+        const float kSqrt2 = 1.41421356f;
+        const float* __restrict__ res = a.res + (long)inst * a.n_sub * a.n_det;
+        for (int vs = g; vs < a.n_sub; vs += G) {
+            const int v = a.first_view + vs * a.view_step;
+            const float4 vp = __ldg(a.view + v);   // cos b, sin b, dso/s, (dso+ddo)/pitch
+            const float along = cx * vp.x + cy * vp.y;
+            const float lat = cy * vp.x - cx * vp.y;
+            const float den = vp.z - along;
+            const float inv = __fdividef(1.0f, den);
+            const float uj = vp.w * lat * inv + jc;
+            // Conservative half-width (in bins) of the shadow of a disc of radius
+            // sqrt(2) around the centre: D_sd sec^2(gamma) asin(rho / dist) / pitch.
+            const float invp = inv * (1.0f + 2.0f * kSqrt2 * inv);
+            const float T = (fabsf(lat) + kSqrt2) * invp;
+            const float hw = kSqrt2 * vp.w * fmaf(T, T, 1.0f) * invp * 1.01f + 0.02f;
+            const int jlo = max(0, (int)ceilf(uj - hw));
+            const int jhi = min(a.n_det - 1, (int)floorf(uj + hw));
+            const long base = (long)v * a.n_det;
+            const float* __restrict__ rrow = res + (long)vs * a.n_det;
+            float accv = 0.0f;
+            for (int j = jlo; j <= jhi; ++j) {
+                const float4 f = __ldg(a.rayf + base + j);
+                const float2 iv = __ldg(a.rayi + base + j);
+                const float ax = px - f.x, ay = py - f.y;
+                const float tx1 = (ax - 1.0f) * iv.x, tx2 = (ax + 1.0f) * iv.x;
+                const float ty1 = (ay - 1.0f) * iv.y, ty2 = (ay + 1.0f) * iv.y;
+                const float tlo = fmaxf(fminf(tx1, tx2), fminf(ty1, ty2));
+                const float thi = fminf(fmaxf(tx1, tx2), fmaxf(ty1, ty2));
+                const int klo = (int)ceilf(fmaf(tlo, inv_step, -0.5f));
+                const int khi = (int)floorf(fmaf(thi, inv_step, -0.5f));
+                float w = 0.0f;
+                float kf = (float)klo + 0.5f;
+                for (int k = klo; k <= khi; ++k) {
+                    const float t = kf * a.step;
+                    const float X = fmaf(t, f.z, f.x);
+                    const float Y = fmaf(t, f.w, f.y);
+                    const float hx = 1.0f - fabsf(X - px);
+                    const float hy = 1.0f - fabsf(Y - py);
+                    w = fmaf(fmaxf(hx, 0.0f), fmaxf(hy, 0.0f), w);
+                    kf += 1.0f;
+                }
+                accv = fmaf(w, __ldg(rrow + j), accv);
             }
-            accv = fmaf(w, __ldg(rrow + j), accv);
+            total += accv;
         }
-        total += accv;
     }
-    const float val = a.scale * total;
+    const int pix = ty * kBackTile + tx;
+    part[g][pix] = total;
+    __syncthreads();
+    if (g != 0 || !inside) return;
+    float sum = 0.0f;
+    for (int q = 0; q < G; ++q) sum += part[q][pix];
+    const float val = a.scale * sum;
     if (a.mode == kBackRaw) {
         a.out[((long)inst * a.ns + iy) * a.ns + ix] = val;
         return;
@@ -254,6 +273,16 @@ __global__ void __launch_bounds__(256) k_backward(BackArgs a)
                 a.out[row + aa] = __ldg(a.y + row + aa) - a.eta * val;
         }
     }
+}
+
+// Number of view groups: enough threads for one full wave of the GPU
+// (152 SMs x 2048 threads), at most 8 and at most the number of views.
+inline int back_groups(long pixels, int n_sub)
+{
+    const long target = 152L * 2048L;
+    int G = 1;
+    while (G < kBackMaxGroups && pixels * G < target && G * 2 <= n_sub) G *= 2;
+    return G;
 }
 
 // ------------------------------------------------------------------ S and S^T
@@ -336,7 +365,9 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t st)
 
 cudaError_t launch_backward(const BackArgs& a, cudaStream_t st)
 {
-    dim3 blk(16, 16), grd(div_up(a.ns, 16), div_up(a.ns, 16), a.batch);
+    const int G = back_groups((long)a.ns * a.ns * a.batch, a.n_sub);
+    const int tiles = div_up(a.ns, kBackTile) * div_up(a.ns, kBackTile);
+    dim3 blk(kBackTile, kBackTile, G), grd(tiles, a.batch);
     k_backward<<<grd, blk, 0, st>>>(a);
     return counted();
 }

@@ -11,9 +11,14 @@
 //               (r_{k+1}, s_{k+1}) = (p_k, q_k) + m_k ((p_k, q_k) - (p_{k-1}, q_{k-1}))
 // with Proj the isotropic projection onto unit disks and m_k = (t_k - 1)/t_{k+1}.
 // Output x = z - lambda L(p_N, q_N).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "pnp_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace pnp {
 namespace {
@@ -114,6 +119,122 @@ __global__ void k_tv_final(const float* __restrict__ z, const float* __restrict_
     }
 }
 
+// ------------------------------------------------------------------ fused cluster FGP
+// All FGP iterations of one image in one thread-block cluster: the image rows
+// are split into C bands, one per CTA; z and the state (r, p, x_tmp) of a band
+// live in that CTA's shared memory, and the one neighbour row each phase needs
+// is read from the adjacent CTA through distributed shared memory.  Each
+// iteration is two phases separated by cluster barriers:
+//   A: x_tmp = z - lambda L(r)           (needs r1 of the row above the band)
+//   B: p = Proj[r + L^T(x_tmp)/(8 lambda)], r = p + m_k (p - p_prev)
+//                                          (needs x_tmp of the row below)
+// then x = z - lambda L(p), the relaxation, the momentum and the optional
+// squared-error partial sum are written out.
+struct FusedTvArgs {
+    const float* z; float* xprev; float* y; const float* xtrue; double* mse_part;
+    int n, rows, iters;
+    float lambda, alpha, amom;
+    float mom[kFusedTvMaxIters];
+};
+
+__global__ void __launch_bounds__(1024) k_tv_fused(const FusedTvArgs a)
+{
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks();
+    const int c = (int)cl.block_rank();
+    const int inst = blockIdx.x / C;
+    const int n = a.n, R = a.rows;
+    const int row0 = c * R;
+    const int nrows = max(0, min(R, n - row0));
+    const int band = R * n;
+    extern __shared__ float sm[];
+    float* z = sm;
+    float* r1 = sm + band;
+    float* r2 = sm + 2 * band;
+    float* p1 = sm + 3 * band;
+    float* p2 = sm + 4 * band;
+    float* xt = sm + 5 * band;
+    const long gimg = (long)inst * n * n + (long)row0 * n;
+    const int cnt = nrows * n;
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+        z[q] = __ldg(a.z + gimg + q);
+        r1[q] = 0.0f; r2[q] = 0.0f; p1[q] = 0.0f; p2[q] = 0.0f;
+    }
+    const float* up_r1 = c > 0 ? cl.map_shared_rank(r1, c - 1) : nullptr;   // row R-1 of band c-1
+    const float* dn_xt = c + 1 < C ? cl.map_shared_rank(xt, c + 1) : nullptr;
+    const float* up_p1 = c > 0 ? cl.map_shared_rank(p1, c - 1) : nullptr;
+    const float inv8l = 1.0f / (8.0f * a.lambda);
+    const float lam = a.lambda;
+    cl.sync();
+    for (int k = 0; k < a.iters; ++k) {
+        for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+            const int li = q / n, j = q - li * n;
+            float l = r1[q] + r2[q];
+            if (li > 0) l -= r1[q - n];
+            else if (c > 0) l -= up_r1[(R - 1) * n + j];
+            if (j > 0) l -= r2[q - 1];
+            xt[q] = z[q] - lam * l;
+        }
+        cl.sync();
+        const float m = a.mom[k];
+        for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+            const int li = q / n, j = q - li * n;
+            const int i = row0 + li;
+            const float x0 = xt[q];
+            float g1 = 0.0f, g2 = 0.0f;
+            if (i < n - 1) g1 = x0 - (li + 1 < nrows ? xt[q + n] : dn_xt[j]);
+            if (j < n - 1) g2 = x0 - xt[q + 1];
+            float pa = r1[q] + g1 * inv8l;
+            float pc = r2[q] + g2 * inv8l;
+            const float den = fmaxf(sqrtf(pa * pa + pc * pc), 1.0f);
+            pa = pa / den;
+            pc = pc / den;
+            r1[q] = pa + m * (pa - p1[q]);
+            r2[q] = pc + m * (pc - p2[q]);
+            p1[q] = pa;
+            p2[q] = pc;
+        }
+        cl.sync();
+    }
+    double e2 = 0.0;
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+        const int li = q / n, j = q - li * n;
+        const float zz = z[q];
+        float x = zz;
+        if (a.iters > 0) {
+            float l = p1[q] + p2[q];
+            if (li > 0) l -= p1[q - n];
+            else if (c > 0) l -= up_p1[(R - 1) * n + j];
+            if (j > 0) l -= p2[q - 1];
+            x = zz - lam * l;
+        }
+        const float xi = (1.0f - a.alpha) * zz + a.alpha * x;
+        const long o = gimg + q;
+        if (a.y) {
+            const float xp = a.xprev[o];
+            a.y[o] = xi + a.amom * (xi - xp);
+        }
+        a.xprev[o] = xi;
+        if (a.xtrue) {
+            const double d = (double)xi - (double)__ldg(a.xtrue + o);
+            e2 += d * d;
+        }
+    }
+    if (a.mse_part) {
+        __shared__ double red[32];
+        for (int off = 16; off > 0; off >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, off);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e2;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int nw = blockDim.x >> 5;
+            double v = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (threadIdx.x == 0) a.mse_part[(long)inst * C + c] = v;
+        }
+    }
+    cl.sync();   // keep this CTA's shared memory alive until the neighbours are done
+}
+
 inline cudaError_t counted(cudaError_t e = cudaGetLastError())
 {
     g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -140,6 +261,86 @@ cudaError_t launch_tv_final(const float* z, const float* p, int have_p, int n, i
     k_tv_final<<<grd, blk, 0, st>>>(z, p, have_p, n, plane, lambda, alpha, a, xprev, y, xtrue,
                                     mse_partials);
     return counted();
+}
+
+}  // namespace pnp
+
+namespace pnp {
+
+// Cluster size and band height for the fused kernel, or 0 if the image does
+// not fit in the shared memory of one cluster of at most 16 CTAs.
+int fused_tv_cluster(int n, int* rows)
+{
+    static int max_cluster = -1;
+    if (max_cluster < 0) {
+        // 16-CTA clusters are a non-portable size: use them only if this GPU
+        // can schedule one with the largest band this kernel asks for.
+        max_cluster = 8;
+        cudaFuncSetAttribute(k_tv_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedTvSmem);
+        if (cudaFuncSetAttribute(k_tv_fused, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+            cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = 16;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(16);
+            cfg.blockDim = dim3(1024);
+            cfg.dynamicSmemBytes = kFusedTvSmem;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int nc = 0;
+            if (cudaOccupancyMaxActiveClusters(&nc, k_tv_fused, &cfg) == cudaSuccess && nc > 0)
+                max_cluster = 16;
+        }
+        cudaGetLastError();
+    }
+    for (int C = max_cluster; C >= 1; C /= 2) {
+        const int R = (n + C - 1) / C;
+        if ((C - 1) * R >= n) continue;            // every CTA needs at least one row
+        if ((size_t)6 * R * n * sizeof(float) > (size_t)kFusedTvSmem) return 0;
+        *rows = R;
+        return C;
+    }
+    return 0;
+}
+
+cudaError_t launch_tv_fused(const float* z, int n, int batch, float lambda, int iters, float alpha,
+                            float amom, float* xprev, float* y, const float* xtrue, double* mse_part,
+                            int cluster, int rows, cudaStream_t st)
+{
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(k_tv_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedTvSmem);
+        cudaFuncSetAttribute(k_tv_fused, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        attr_done = true;
+    }
+    FusedTvArgs a{};
+    a.z = z; a.xprev = xprev; a.y = y; a.xtrue = xtrue; a.mse_part = mse_part;
+    a.n = n; a.rows = rows; a.iters = iters;
+    a.lambda = lambda; a.alpha = alpha; a.amom = amom;
+    double t = 1.0;
+    for (int k = 0; k < iters; ++k) {
+        const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+        a.mom[k] = (float)((t - 1.0) / tn);
+        t = tn;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cluster * batch);
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = (size_t)6 * rows * n * sizeof(float);
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_tv_fused, a);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return e;
 }
 
 }  // namespace pnp
