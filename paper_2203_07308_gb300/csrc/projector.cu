@@ -127,7 +127,7 @@ __global__ void k_prep_quad(const float* __restrict__ fine, int n, int s, int qw
 // k_lo + q + Q, ... of ray r; the Q partial sums are combined by shuffles in a
 // fixed order, so the result is deterministic.  One 16-byte load per sample.
 template <int Q>
-__global__ void __launch_bounds__(256) k_forward(FwdArgs a)
+__global__ void __launch_bounds__(256, 4) k_forward(FwdArgs a)
 {
     constexpr int R = 32 / Q;
     const int lane = threadIdx.x & 31;
@@ -189,7 +189,8 @@ __global__ void __launch_bounds__(256) k_forward(FwdArgs a)
 constexpr int kBackTile = 8;
 constexpr int kBackMaxGroups = 8;
 
-__global__ void __launch_bounds__(512) k_backward(BackArgs a)
+template <int NWIN>
+__global__ void __launch_bounds__(512, 2) k_backward(BackArgs a)
 {
     const int tx = threadIdx.x, ty = threadIdx.y, g = threadIdx.z, G = blockDim.z;
     const int tiles_x = (a.ns + kBackTile - 1) / kBackTile;
@@ -207,6 +208,9 @@ __global__ void __launch_bounds__(512) k_backward(BackArgs a)
         const float jc = 0.5f * (float)(a.n_det - 1);
         const float inv_step = 1.0f / a.step;
         const float kSqrt2 = 1.41421356f;
+        // samples of one ray within sqrt(2) of the pixel centre: at most
+        // floor(2 sqrt(2) / step) + 1 of them (6 for step 1/2)
+        const int nwin = NWIN > 0 ? NWIN : (int)floorf(2.0f * kSqrt2 * inv_step) + 1;
         const float* __restrict__ res = a.res + (long)inst * a.n_sub * a.n_det;
         for (int vs = g; vs < a.n_sub; vs += G) {
             const int v = a.first_view + vs * a.view_step;
@@ -228,24 +232,30 @@ __global__ void __launch_bounds__(512) k_backward(BackArgs a)
             float accv = 0.0f;
             for (int j = jlo; j <= jhi; ++j) {
                 const float4 f = __ldg(a.rayf + base + j);
-                const float2 iv = __ldg(a.rayi + base + j);
-                const float ax = px - f.x, ay = py - f.y;
-                const float tx1 = (ax - 1.0f) * iv.x, tx2 = (ax + 1.0f) * iv.x;
-                const float ty1 = (ay - 1.0f) * iv.y, ty2 = (ay + 1.0f) * iv.y;
-                const float tlo = fmaxf(fminf(tx1, tx2), fminf(ty1, ty2));
-                const float thi = fminf(fmaxf(tx1, tx2), fmaxf(ty1, ty2));
-                const int klo = (int)ceilf(fmaf(tlo, inv_step, -0.5f));
-                const int khi = (int)floorf(fmaf(thi, inv_step, -0.5f));
+                const float ax = px - f.x, ay = py - f.y;        // pixel relative to the foot point
+                // the line meets the support square |X-px|,|Y-py| < 1 iff its distance
+                // from the centre is below the square's half-extent |d_x| + |d_y|
+                const float e = ax * f.w - ay * f.z;
+                if (fabsf(e) >= fabsf(f.z) + fabsf(f.w)) continue;
+                const float tau = fmaf(ax, f.z, ay * f.w);       // along-ray position of the centre
+                const float k0 = ceilf(fmaf(tau - kSqrt2, inv_step, -0.5f));
+                const float t0 = (k0 + 0.5f) * a.step;
+                const float X0 = fmaf(t0, f.z, -ax), Y0 = fmaf(t0, f.w, -ay);
+                const float sx = a.step * f.z, sy = a.step * f.w;
                 float w = 0.0f;
-                float kf = (float)klo + 0.5f;
-                for (int k = klo; k <= khi; ++k) {
-                    const float t = kf * a.step;
-                    const float X = fmaf(t, f.z, f.x);
-                    const float Y = fmaf(t, f.w, f.y);
-                    const float hx = 1.0f - fabsf(X - px);
-                    const float hy = 1.0f - fabsf(Y - py);
-                    w = fmaf(fmaxf(hx, 0.0f), fmaxf(hy, 0.0f), w);
-                    kf += 1.0f;
+                if (NWIN > 0) {
+#pragma unroll
+                    for (int m = 0; m < (NWIN > 0 ? NWIN : 1); ++m) {
+                        const float hx = 1.0f - fabsf(fmaf((float)m, sx, X0));
+                        const float hy = 1.0f - fabsf(fmaf((float)m, sy, Y0));
+                        w = fmaf(fmaxf(hx, 0.0f), fmaxf(hy, 0.0f), w);
+                    }
+                } else {
+                    for (int m = 0; m < nwin; ++m) {
+                        const float hx = 1.0f - fabsf(fmaf((float)m, sx, X0));
+                        const float hy = 1.0f - fabsf(fmaf((float)m, sy, Y0));
+                        w = fmaf(fmaxf(hx, 0.0f), fmaxf(hy, 0.0f), w);
+                    }
                 }
                 accv = fmaf(w, __ldg(rrow + j), accv);
             }
@@ -353,13 +363,23 @@ cudaError_t launch_prep_quad(const float* fine, int n, int s, int batch, float4*
     return counted();
 }
 
+template <int Q>
+void forward_q(const FwdArgs& a, long rays, cudaStream_t st)
+{
+    const long warps = (rays + (32 / Q) - 1) / (32 / Q);
+    k_forward<Q><<<div_up(warps * 32, 256), 256, 0, st>>>(a);
+}
+
 cudaError_t launch_forward(const FwdArgs& a, cudaStream_t st)
 {
-    constexpr int Q = 4;
-    long rays = (long)a.n_sub * a.n_det * a.batch;
-    long warps = (rays + (32 / Q) - 1) / (32 / Q);
-    long threads = warps * 32;
-    k_forward<Q><<<div_up(threads, 256), 256, 0, st>>>(a);
+    // lanes per ray: enough threads to fill the GPU (~2 waves of 152 x 2048)
+    const long rays = (long)a.n_sub * a.n_det * a.batch;
+    if (rays * 4 >= 600000L)
+        forward_q<4>(a, rays, st);
+    else if (rays * 8 >= 600000L)
+        forward_q<8>(a, rays, st);
+    else
+        forward_q<16>(a, rays, st);
     return counted();
 }
 
@@ -368,7 +388,10 @@ cudaError_t launch_backward(const BackArgs& a, cudaStream_t st)
     const int G = back_groups((long)a.ns * a.ns * a.batch, a.n_sub);
     const int tiles = div_up(a.ns, kBackTile) * div_up(a.ns, kBackTile);
     dim3 blk(kBackTile, kBackTile, G), grd(tiles, a.batch);
-    k_backward<<<grd, blk, 0, st>>>(a);
+    if (a.step == 0.5f)
+        k_backward<6><<<grd, blk, 0, st>>>(a);
+    else
+        k_backward<0><<<grd, blk, 0, st>>>(a);
     return counted();
 }
 

@@ -121,20 +121,39 @@ __global__ void k_tv_final(const float* __restrict__ z, const float* __restrict_
 
 // ------------------------------------------------------------------ fused cluster FGP
 // All FGP iterations of one image in one thread-block cluster: the image rows
-// are split into C bands, one per CTA; z and the state (r, p, x_tmp) of a band
-// live in that CTA's shared memory, and the one neighbour row each phase needs
-// is read from the adjacent CTA through distributed shared memory.  Each
-// iteration is two phases separated by cluster barriers:
-//   A: x_tmp = z - lambda L(r)           (needs r1 of the row above the band)
-//   B: p = Proj[r + L^T(x_tmp)/(8 lambda)], r = p + m_k (p - p_prev)
-//                                          (needs x_tmp of the row below)
-// then x = z - lambda L(p), the relaxation, the momentum and the optional
+// are split into C bands, one per CTA; z and the state of a band live in that
+// CTA's shared memory and the neighbour rows are read from the adjacent CTAs
+// through distributed shared memory.  The momentum point r is double-buffered,
+// so one cluster barrier per iteration suffices:
+//   A: x_tmp = z - lambda L(r_cur) on the band plus the first row of the next
+//      band (needs r1 of the row above the band and r, z of the row below);
+//   B: p = Proj[r_cur + L^T(x_tmp)/(8 lambda)], r_nxt = p + m_k (p - p_prev);
+//   cluster barrier (r_nxt complete everywhere; nobody still reads r_cur).
+// Then x = z - lambda L(p), the relaxation, the momentum and the optional
 // squared-error partial sum are written out.
 struct FusedTvArgs {
     const float* z; float* xprev; float* y; const float* xtrue; double* mse_part;
     int n, rows, iters;
     float lambda, alpha, amom;
     float mom[kFusedTvMaxIters];
+};
+
+// Walks the band's pixels q = tid, tid + T, ... without a division per step.
+struct BandWalk {
+    int li, j, dli, dj, n;
+    __device__ BandWalk(int tid, int T, int n_) : n(n_)
+    {
+        li = tid / n_;
+        j = tid - li * n_;
+        dli = T / n_;
+        dj = T - dli * n_;
+    }
+    __device__ void next()
+    {
+        li += dli;
+        j += dj;
+        if (j >= n) { j -= n; ++li; }
+    }
 };
 
 __global__ void __launch_bounds__(1024) k_tv_fused(const FusedTvArgs a)
@@ -146,59 +165,88 @@ __global__ void __launch_bounds__(1024) k_tv_fused(const FusedTvArgs a)
     const int n = a.n, R = a.rows;
     const int row0 = c * R;
     const int nrows = max(0, min(R, n - row0));
+    const bool has_next = c + 1 < C && row0 + nrows < n;
     const int band = R * n;
     extern __shared__ float sm[];
     float* z = sm;
-    float* r1 = sm + band;
-    float* r2 = sm + 2 * band;
-    float* p1 = sm + 3 * band;
-    float* p2 = sm + 4 * band;
-    float* xt = sm + 5 * band;
+    float* const r1b0 = sm + band;
+    float* const r1b1 = sm + 2 * band;
+    float* const r2b0 = sm + 3 * band;
+    float* const r2b1 = sm + 4 * band;
+    float* p1 = sm + 5 * band;
+    float* p2 = sm + 6 * band;
+    float* xt = sm + 7 * band;                 // (R + 1) rows
+    const int T = blockDim.x;
     const long gimg = (long)inst * n * n + (long)row0 * n;
     const int cnt = nrows * n;
-    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+    for (int q = threadIdx.x; q < cnt; q += T) {
         z[q] = __ldg(a.z + gimg + q);
-        r1[q] = 0.0f; r2[q] = 0.0f; p1[q] = 0.0f; p2[q] = 0.0f;
+        r1b0[q] = 0.0f; r2b0[q] = 0.0f; p1[q] = 0.0f; p2[q] = 0.0f;
     }
-    const float* up_r1 = c > 0 ? cl.map_shared_rank(r1, c - 1) : nullptr;   // row R-1 of band c-1
-    const float* dn_xt = c + 1 < C ? cl.map_shared_rank(xt, c + 1) : nullptr;
+    // neighbour bands (valid only when they exist); buffer 1 sits `band` floats
+    // after buffer 0 in every CTA
+    const float* up_r1 = c > 0 ? cl.map_shared_rank(r1b0, c - 1) : nullptr;
     const float* up_p1 = c > 0 ? cl.map_shared_rank(p1, c - 1) : nullptr;
+    const float* dn_r1 = has_next ? cl.map_shared_rank(r1b0, c + 1) : nullptr;
+    const float* dn_r2 = has_next ? cl.map_shared_rank(r2b0, c + 1) : nullptr;
+    const float* dn_z = has_next ? cl.map_shared_rank(z, c + 1) : nullptr;
     const float inv8l = 1.0f / (8.0f * a.lambda);
     const float lam = a.lambda;
+    const int xrows = nrows + (has_next ? 1 : 0);
+    const int xcnt = xrows * n;
     cl.sync();
     for (int k = 0; k < a.iters; ++k) {
-        for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
-            const int li = q / n, j = q - li * n;
-            float l = r1[q] + r2[q];
-            if (li > 0) l -= r1[q - n];
-            else if (c > 0) l -= up_r1[(R - 1) * n + j];
-            if (j > 0) l -= r2[q - 1];
-            xt[q] = z[q] - lam * l;
+        const int cur = k & 1;
+        const int boff = cur * band;          // offset of the current buffer
+        const float* r1 = cur ? r1b1 : r1b0;
+        const float* r2 = cur ? r2b1 : r2b0;
+        // phase A: x_tmp on the band and on the next band's first row
+        BandWalk w(threadIdx.x, T, n);
+        for (int q = threadIdx.x; q < xcnt; q += T, w.next()) {
+            const int li = w.li, j = w.j;
+            float rr1, rr2, zz, up, left;
+            if (li < nrows) {
+                rr1 = r1[q]; rr2 = r2[q]; zz = z[q];
+                left = j > 0 ? r2[q - 1] : 0.0f;
+                up = li > 0 ? r1[q - n] : (c > 0 ? up_r1[boff + (R - 1) * n + j] : 0.0f);
+            } else {   // first row of band c + 1
+                rr1 = dn_r1[boff + j]; rr2 = dn_r2[boff + j]; zz = dn_z[j];
+                left = j > 0 ? dn_r2[boff + j - 1] : 0.0f;
+                up = r1[q - n];
+            }
+            xt[q] = zz - lam * (rr1 + rr2 - up - left);
         }
-        cl.sync();
+        __syncthreads();
+        // phase B: dual step, projection, momentum on the band
         const float m = a.mom[k];
-        for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
-            const int li = q / n, j = q - li * n;
+        float* o1 = cur ? r1b0 : r1b1;
+        float* o2 = cur ? r2b0 : r2b1;
+        BandWalk w2(threadIdx.x, T, n);
+        for (int q = threadIdx.x; q < cnt; q += T, w2.next()) {
+            const int li = w2.li, j = w2.j;
             const int i = row0 + li;
             const float x0 = xt[q];
-            float g1 = 0.0f, g2 = 0.0f;
-            if (i < n - 1) g1 = x0 - (li + 1 < nrows ? xt[q + n] : dn_xt[j]);
-            if (j < n - 1) g2 = x0 - xt[q + 1];
-            float pa = r1[q] + g1 * inv8l;
-            float pc = r2[q] + g2 * inv8l;
-            const float den = fmaxf(sqrtf(pa * pa + pc * pc), 1.0f);
-            pa = pa / den;
-            pc = pc / den;
-            r1[q] = pa + m * (pa - p1[q]);
-            r2[q] = pc + m * (pc - p2[q]);
+            const float g1 = i < n - 1 ? x0 - xt[q + n] : 0.0f;
+            const float g2 = j < n - 1 ? x0 - xt[q + 1] : 0.0f;
+            float pa = fmaf(g1, inv8l, r1[q]);
+            float pc = fmaf(g2, inv8l, r2[q]);
+            const float nrm2 = fmaf(pa, pa, pc * pc);
+            if (nrm2 > 1.0f) {
+                const float sc = rsqrtf(nrm2);
+                pa *= sc;
+                pc *= sc;
+            }
+            o1[q] = fmaf(m, pa - p1[q], pa);
+            o2[q] = fmaf(m, pc - p2[q], pc);
             p1[q] = pa;
             p2[q] = pc;
         }
         cl.sync();
     }
     double e2 = 0.0;
-    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
-        const int li = q / n, j = q - li * n;
+    BandWalk w3(threadIdx.x, T, n);
+    for (int q = threadIdx.x; q < cnt; q += T, w3.next()) {
+        const int li = w3.li, j = w3.j;
         const float zz = z[q];
         float x = zz;
         if (a.iters > 0) {
@@ -269,6 +317,9 @@ namespace pnp {
 
 // Cluster size and band height for the fused kernel, or 0 if the image does
 // not fit in the shared memory of one cluster of at most 16 CTAs.
+// z, r (2 buffers x 2 components), p (2 components), x_tmp (one extra row)
+inline size_t fused_tv_smem(int rows, int n) { return ((size_t)8 * rows + 1) * n * sizeof(float); }
+
 int fused_tv_cluster(int n, int* rows)
 {
     static int max_cluster = -1;
@@ -299,7 +350,7 @@ int fused_tv_cluster(int n, int* rows)
     for (int C = max_cluster; C >= 1; C /= 2) {
         const int R = (n + C - 1) / C;
         if ((C - 1) * R >= n) continue;            // every CTA needs at least one row
-        if ((size_t)6 * R * n * sizeof(float) > (size_t)kFusedTvSmem) return 0;
+        if (fused_tv_smem(R, n) > (size_t)kFusedTvSmem) return 0;
         *rows = R;
         return C;
     }
@@ -334,7 +385,7 @@ cudaError_t launch_tv_fused(const float* z, int n, int batch, float lambda, int 
     at[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(cluster * batch);
     cfg.blockDim = dim3(1024);
-    cfg.dynamicSmemBytes = (size_t)6 * rows * n * sizeof(float);
+    cfg.dynamicSmemBytes = fused_tv_smem(rows, n);
     cfg.stream = st;
     cfg.attrs = at;
     cfg.numAttrs = 1;
