@@ -186,6 +186,30 @@ int pnp_objective(const pnp_geom* g, const float* d_x, const float* d_b, const f
 int pnp_sample_count(const pnp_geom* g, int factor, int subset, int n_subsets, double* h_count,
                      void* d_ws, void* stream);
 
+/* Bytes of scratch inside the library for pnp_full_grad_noalloc (per GPU that
+ * loads the library, held until the process exits). */
+#define PNP_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* The full gradient of pnp_full_grad, d_g = A^T (A d_x - d_b), for callers that
+ * cannot allocate device memory: a real-time scanner service that fixes its
+ * memory at start-up so no request can fail or stall on allocation, or a
+ * plug-in inside an application whose allocator owns all of the GPU's memory.
+ * The paper has no counterpart; it is an interface for such callers.
+ *   It allocates nothing and takes no workspace: its scratch lives in a fixed
+ *   PNP_NOALLOC_SCRATCH_BYTES array compiled into the library.  A geometry needs
+ *   24 B per ray and 16 B per view (ray tables), plus per batch image 16 (n+3)^2 B
+ *   (coefficient image) and 4 B per ray (residual), each part rounded up to
+ *   256 B; e.g. 256x256 with 360 views x 512 bins needs about 6.3 MB.
+ *   Geometries that need more are rejected with PNP_EINVAL and a message.
+ *   The first call on a device looks up the array's device address (once per
+ *   device, with that device current); make that first call before any stream
+ *   capture.
+ *   All calls share the array: calls that overlap on the GPU (other streams or
+ *   host threads) race and give wrong results; order them on one stream.
+ *   Every call rewrites all the scratch it reads, so nothing needs clearing.
+ *   d_x, d_g [batch][n][n], d_b [batch][n_views][n_det]; asynchronous on `stream`. */
+int pnp_full_grad_noalloc(const pnp_geom* g, const float* d_x, const float* d_b, float* d_g, void* stream);
+
 /* Number of kernels this library has launched in this process. */
 uint64_t pnp_launch_count(void);
 

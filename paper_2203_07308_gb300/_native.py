@@ -22,6 +22,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "pnp_ms2g.h")
 
 PNP_OK, PNP_EINVAL, PNP_ECUDA, PNP_ETIMEOUT, PNP_EUNSUPPORTED, PNP_ESTATE = range(6)
 MAX_LOG_ITERS = 65536
+NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 class PnpError(RuntimeError):
@@ -87,6 +88,7 @@ def load(path: Optional[str] = None):
                         vp, vp, vp, dp, vp, vp],
             "pnp_objective": [gp, vp, vp, vp, dp, vp, vp],
             "pnp_sample_count": [gp, i32, i32, i32, dp, vp, vp],
+            "pnp_full_grad_noalloc": [gp, vp, vp, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -194,6 +196,15 @@ def full_grad(g, x, b, out, ws, stream=None):
     img = g.batch * g.n * g.n
     _check(load().pnp_full_grad(C.byref(geom(g)), _ptr(x, img, "x"), _ptr(b, g.batch * g.n_views * g.n_det, "b"),
                                 _ptr(out, img, "g"), _ws(ws)[0], _stream(stream)))
+
+
+def full_grad_noalloc(g, x, b, out, stream=None):
+    """pnp_full_grad_noalloc: the full gradient without a workspace (scratch inside
+    the library, PNP_NOALLOC_SCRATCH_BYTES per GPU)."""
+    img = g.batch * g.n * g.n
+    _check(load().pnp_full_grad_noalloc(C.byref(geom(g)), _ptr(x, img, "x"),
+                                        _ptr(b, g.batch * g.n_views * g.n_det, "b"), _ptr(out, img, "g"),
+                                        _stream(stream)))
 
 
 def sketch_grad(g, factor, y, b, out, subset=0, n_subsets=1, ws=None, stream=None):

@@ -28,9 +28,9 @@ int level_index(int factor)
     }
 }
 
-namespace {
-
 thread_local std::string t_err;
+
+void clear_error() { t_err.clear(); }
 
 int fail(int code, const char* fmt, ...)
 {
@@ -51,8 +51,12 @@ int fail(int code, const char* fmt, ...)
                         __FILE__, __LINE__);                                             \
     } while (0)
 
+namespace {
+
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+}  // namespace
 
 // A level is available when it divides n, keeps at least 4 pixels per side and
 // leaves the source far enough outside the image for the backprojector's
@@ -85,6 +89,8 @@ int validate_geom(const pnp_geom* g)
     if (std::sqrt(2.0) * (g->n + 2) / g->step > 1.0e8) return fail(PNP_EINVAL, "step too small");
     return PNP_OK;
 }
+
+namespace {
 
 Layout make_layout(const pnp_geom& g)
 {

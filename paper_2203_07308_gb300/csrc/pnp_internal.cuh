@@ -57,6 +57,13 @@ struct Layout {
 
 int level_index(int factor);   // 0..3 or -1
 
+// Error reporting and geometry checks shared by the C entry points (api.cu):
+// fail() records the message for pnp_last_error() and returns `code`.
+int fail(int code, const char* fmt, ...);
+void clear_error();
+bool level_ok(const pnp_geom& g, int s);
+int validate_geom(const pnp_geom* g);
+
 // ---------------------------------------------------------------- kernels (launchers)
 cudaError_t launch_setup_rays(const pnp_geom& g, const LevelLayout& L, char* ws, cudaStream_t st);
 
