@@ -283,6 +283,238 @@ __global__ void __launch_bounds__(1024) k_tv_fused(const FusedTvArgs a)
     cl.sync();   // keep this CTA's shared memory alive until the neighbours are done
 }
 
+// ------------------------------------------------------------------ register-resident cluster FGP
+// Same iteration as k_tv_fused, for images whose side n is a multiple of 32 and
+// of the cluster size.  Thread (rb, j) of CTA c owns the V rows
+// c*R + rb*V ... + V-1 of column j and keeps z, r and p of those pixels in
+// registers.  Everything a thread needs from outside its strip comes from
+// values its neighbours published at the end of the previous iteration
+// (double-buffered, so one cluster barrier per iteration is enough):
+//   - the momentum point r of the row above / the column to the left (for
+//     x_tmp = z - lambda L(r)),
+//   - r of the row below and of the column to the right, from which the thread
+//     recomputes the neighbouring x_tmp values it needs for L^T(x_tmp).
+// Inside a warp the column neighbours come from shuffles; across warps, row
+// blocks and CTAs from shared memory and distributed shared memory.
+template <int V>
+struct RegTvSmem {
+    // double-buffered publications, index [buf][rb][j] or [buf][rb][w][v]
+    static __device__ __forceinline__ int row_pub(int buf, int rb, int j, int RB, int n)
+    {
+        return (buf * RB + rb) * n + j;
+    }
+    static __device__ __forceinline__ int col_pub(int buf, int rb, int w, int v, int RB, int W)
+    {
+        return ((buf * RB + rb) * W + w) * V + v;
+    }
+};
+
+template <int V>
+__global__ void __launch_bounds__(1024, 1) k_tv_reg(const FusedTvArgs a)
+{
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks();
+    const int c = (int)cl.block_rank();
+    const int inst = blockIdx.x / C;
+    const int n = a.n, R = a.rows;
+    const int RB = R / V;              // row blocks per CTA
+    const int W = n >> 5;              // warps per row block
+    const int tid = threadIdx.x;
+    const int rb = tid / n;
+    const int j = tid - rb * n;
+    const int lane = tid & 31;
+    const int w = j >> 5;
+    const int i0 = c * R + rb * V;     // global row of this strip's first row
+    typedef RegTvSmem<V> L;
+
+    extern __shared__ float sh[];
+    const int rowsz = 2 * RB * n, colsz = 2 * RB * W * V;
+    float* last_r1 = sh;                       // r1 of the strip's last row
+    float* first_r1 = last_r1 + rowsz;         // r1, r2 of the strip's first row
+    float* first_r2 = first_r1 + rowsz;
+    float* col0_r1 = first_r2 + rowsz;         // lane 0's column (all V rows)
+    float* col0_r2 = col0_r1 + colsz;
+    float* col31_r2 = col0_r2 + colsz;         // lane 31's column
+    float* zfirst = col31_r2 + colsz;          // [RB][n] z of each strip's first row
+    float* zcol0 = zfirst + RB * n;            // [RB][W][V] z of lane 0's column
+    float* last_p1 = zcol0 + RB * W * V;       // [RB][n]
+    float* col31_p2 = last_p1 + RB * n;        // [RB][W][V]
+
+    const long gimg = (long)inst * n * n;
+    float z[V], r1[V], r2[V], p1[V], p2[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        z[v] = __ldg(a.z + gimg + (long)(i0 + v) * n + j);
+        r1[v] = r2[v] = p1[v] = p2[v] = 0.0f;
+    }
+    // static publications and the zero momentum point of iteration 0
+    zfirst[rb * n + j] = z[0];
+    last_r1[L::row_pub(0, rb, j, RB, n)] = 0.0f;
+    first_r1[L::row_pub(0, rb, j, RB, n)] = 0.0f;
+    first_r2[L::row_pub(0, rb, j, RB, n)] = 0.0f;
+    if (lane == 0) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            zcol0[(rb * W + w) * V + v] = z[v];
+            col0_r1[L::col_pub(0, rb, w, v, RB, W)] = 0.0f;
+            col0_r2[L::col_pub(0, rb, w, v, RB, W)] = 0.0f;
+        }
+    }
+    if (lane == 31) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) col31_r2[L::col_pub(0, rb, w, v, RB, W)] = 0.0f;
+    }
+    // neighbour CTAs (the one above owns row i0 - 1 when rb == 0; the one below
+    // owns row i0 + V when rb == RB - 1)
+    const bool has_up = c > 0, has_dn = c + 1 < C;
+    const float* up_last_r1 = has_up ? cl.map_shared_rank(last_r1, c - 1) : nullptr;
+    const float* up_last_p1 = has_up ? cl.map_shared_rank(last_p1, c - 1) : nullptr;
+    const float* dn_first_r1 = has_dn ? cl.map_shared_rank(first_r1, c + 1) : nullptr;
+    const float* dn_first_r2 = has_dn ? cl.map_shared_rank(first_r2, c + 1) : nullptr;
+    const float* dn_zfirst = has_dn ? cl.map_shared_rank(zfirst, c + 1) : nullptr;
+    const float lam = a.lambda;
+    const float inv8l = 1.0f / (8.0f * a.lambda);
+    const bool last_img_row = i0 + V == n;      // the strip ends on the image's last row
+    const bool last_col = j == n - 1;
+    cl.sync();
+
+    for (int k = 0; k < a.iters; ++k) {
+        const int cur = k & 1, nxt = cur ^ 1;
+        // r1 of the row above this strip (column j and, for lane 31, column j + 1)
+        float r1_up = 0.0f, r1_up_r = 0.0f;
+        if (rb > 0) {
+            r1_up = last_r1[L::row_pub(cur, rb - 1, j, RB, n)];
+            if (lane == 31 && !last_col) r1_up_r = last_r1[L::row_pub(cur, rb - 1, j + 1, RB, n)];
+        } else if (has_up) {
+            r1_up = up_last_r1[L::row_pub(cur, RB - 1, j, RB, n)];
+            if (lane == 31 && !last_col) r1_up_r = up_last_r1[L::row_pub(cur, RB - 1, j + 1, RB, n)];
+        }
+        // x_tmp on the strip
+        float xt[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            float left = __shfl_up_sync(0xffffffffu, r2[v], 1);
+            if (lane == 0) left = j > 0 ? col31_r2[L::col_pub(cur, rb, w - 1, v, RB, W)] : 0.0f;
+            const float up = v > 0 ? r1[v - 1] : r1_up;
+            xt[v] = z[v] - lam * (r1[v] + r2[v] - up - left);
+        }
+        // x_tmp one row below the strip (same column)
+        float xt_dn = 0.0f;
+        if (!last_img_row) {
+            float rr1, rr2, zz, left;
+            if (rb + 1 < RB) {
+                rr1 = first_r1[L::row_pub(cur, rb + 1, j, RB, n)];
+                rr2 = first_r2[L::row_pub(cur, rb + 1, j, RB, n)];
+                left = j > 0 ? first_r2[L::row_pub(cur, rb + 1, j - 1, RB, n)] : 0.0f;
+                zz = zfirst[(rb + 1) * n + j];
+            } else {
+                rr1 = dn_first_r1[L::row_pub(cur, 0, j, RB, n)];
+                rr2 = dn_first_r2[L::row_pub(cur, 0, j, RB, n)];
+                left = j > 0 ? dn_first_r2[L::row_pub(cur, 0, j - 1, RB, n)] : 0.0f;
+                zz = dn_zfirst[j];
+            }
+            xt_dn = zz - lam * (rr1 + rr2 - r1[V - 1] - left);
+        }
+        // x_tmp one column to the right (same rows)
+        float xt_r[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) xt_r[v] = __shfl_down_sync(0xffffffffu, xt[v], 1);
+        if (lane == 31 && !last_col) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const float rr1 = col0_r1[L::col_pub(cur, rb, w + 1, v, RB, W)];
+                const float rr2 = col0_r2[L::col_pub(cur, rb, w + 1, v, RB, W)];
+                const float up = v > 0 ? col0_r1[L::col_pub(cur, rb, w + 1, v - 1, RB, W)] : r1_up_r;
+                xt_r[v] = zcol0[(rb * W + w + 1) * V + v] - lam * (rr1 + rr2 - up - r2[v]);
+            }
+        }
+        // dual step, projection onto unit disks, momentum
+        const float m = a.mom[k];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const float below = v + 1 < V ? xt[v + 1] : xt_dn;
+            const float g1 = (v + 1 < V || !last_img_row) ? xt[v] - below : 0.0f;
+            const float g2 = last_col ? 0.0f : xt[v] - xt_r[v];
+            float pa = fmaf(g1, inv8l, r1[v]);
+            float pc = fmaf(g2, inv8l, r2[v]);
+            const float nrm2 = fmaf(pa, pa, pc * pc);
+            if (nrm2 > 1.0f) {
+                const float sc = rsqrtf(nrm2);
+                pa *= sc;
+                pc *= sc;
+            }
+            r1[v] = fmaf(m, pa - p1[v], pa);
+            r2[v] = fmaf(m, pc - p2[v], pc);
+            p1[v] = pa;
+            p2[v] = pc;
+        }
+        // publish for the next iteration
+        last_r1[L::row_pub(nxt, rb, j, RB, n)] = r1[V - 1];
+        first_r1[L::row_pub(nxt, rb, j, RB, n)] = r1[0];
+        first_r2[L::row_pub(nxt, rb, j, RB, n)] = r2[0];
+        if (lane == 0) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                col0_r1[L::col_pub(nxt, rb, w, v, RB, W)] = r1[v];
+                col0_r2[L::col_pub(nxt, rb, w, v, RB, W)] = r2[v];
+            }
+        }
+        if (lane == 31) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) col31_r2[L::col_pub(nxt, rb, w, v, RB, W)] = r2[v];
+        }
+        if (k + 1 == a.iters) {
+            last_p1[rb * n + j] = p1[V - 1];
+            if (lane == 31) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) col31_p2[(rb * W + w) * V + v] = p2[v];
+            }
+        }
+        cl.sync();
+    }
+    // x = z - lambda L(p), relaxation, momentum, squared error
+    float p1_up = 0.0f;
+    if (a.iters > 0) {
+        if (rb > 0) p1_up = last_p1[(rb - 1) * n + j];
+        else if (has_up) p1_up = up_last_p1[(RB - 1) * n + j];
+    }
+    double e2 = 0.0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        float x = z[v];
+        if (a.iters > 0) {
+            float left = __shfl_up_sync(0xffffffffu, p2[v], 1);
+            if (lane == 0) left = j > 0 ? col31_p2[(rb * W + w - 1) * V + v] : 0.0f;
+            const float up = v > 0 ? p1[v - 1] : p1_up;
+            x = z[v] - lam * (p1[v] + p2[v] - up - left);
+        }
+        const float xi = (1.0f - a.alpha) * z[v] + a.alpha * x;
+        const long o = gimg + (long)(i0 + v) * n + j;
+        if (a.y) {
+            const float xp = a.xprev[o];
+            a.y[o] = xi + a.amom * (xi - xp);
+        }
+        a.xprev[o] = xi;
+        if (a.xtrue) {
+            const double d = (double)xi - (double)__ldg(a.xtrue + o);
+            e2 += d * d;
+        }
+    }
+    if (a.mse_part) {
+        __shared__ double red[32];
+        for (int off = 16; off > 0; off >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, off);
+        if (lane == 0) red[tid >> 5] = e2;
+        __syncthreads();
+        if (tid < 32) {
+            const int nw = blockDim.x >> 5;
+            double v = tid < nw ? red[tid] : 0.0;
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (tid == 0) a.mse_part[(long)inst * C + c] = v;
+        }
+    }
+    cl.sync();   // keep this CTA's shared memory alive until the neighbours are done
+}
+
 inline cudaError_t counted(cudaError_t e = cudaGetLastError())
 {
     g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -357,6 +589,33 @@ int fused_tv_cluster(int n, int* rows)
     return 0;
 }
 
+// Register-resident variant: V rows per thread, n % 32 == 0, n % C == 0,
+// (R / V) * n <= 1024 threads.  Returns V (0 if not applicable).
+inline size_t reg_tv_smem(int n, int R, int V)
+{
+    const size_t RB = R / V, W = n / 32;
+    return (6 * RB * n + 6 * RB * W * V + RB * n + RB * W * V + RB * n + RB * W * V) * sizeof(float);
+}
+
+int reg_tv_rows_per_thread(int n, int C, int R)
+{
+    if (n % 32 != 0 || C * R != n) return 0;
+    for (int V = 1; V <= 4; V *= 2)
+        if (R % V == 0 && (R / V) * n <= 1024 && reg_tv_smem(n, R, V) <= 48 * 1024) return V;
+    return 0;
+}
+
+template <int V>
+cudaError_t launch_reg(cudaLaunchConfig_t& cfg, const FusedTvArgs& a)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_tv_reg<V>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        attr = true;
+    }
+    return cudaLaunchKernelEx(&cfg, k_tv_reg<V>, a);
+}
+
 cudaError_t launch_tv_fused(const float* z, int n, int batch, float lambda, int iters, float alpha,
                             float amom, float* xprev, float* y, const float* xtrue, double* mse_part,
                             int cluster, int rows, cudaStream_t st)
@@ -384,12 +643,20 @@ cudaError_t launch_tv_fused(const float* z, int n, int batch, float lambda, int 
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(cluster * batch);
-    cfg.blockDim = dim3(1024);
-    cfg.dynamicSmemBytes = fused_tv_smem(rows, n);
     cfg.stream = st;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_tv_fused, a);
+    cudaError_t e;
+    const int V = reg_tv_rows_per_thread(n, cluster, rows);
+    if (V > 0) {
+        cfg.blockDim = dim3((rows / V) * n);
+        cfg.dynamicSmemBytes = reg_tv_smem(n, rows, V);
+        e = V == 1 ? launch_reg<1>(cfg, a) : V == 2 ? launch_reg<2>(cfg, a) : launch_reg<4>(cfg, a);
+    } else {
+        cfg.blockDim = dim3(1024);
+        cfg.dynamicSmemBytes = fused_tv_smem(rows, n);
+        e = cudaLaunchKernelEx(&cfg, k_tv_fused, a);
+    }
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return e;
 }

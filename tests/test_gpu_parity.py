@@ -168,10 +168,12 @@ def test_gradient_parity(name, s, P):
         assert rel(host(out), ref) < TOL
 
 
-# 64, 37, 128, 16: the fused one-cluster-per-image kernel; 512: the multi-launch
-# path (state larger than one cluster's shared memory)
-@pytest.mark.parametrize("n,batch,lam,iters", [(64, 2, 0.02, 20), (37, 1, 0.1, 20), (128, 1, 0.05, 7),
-                                               (16, 3, 0.3, 50), (512, 2, 0.02, 6)])
+# one cluster per image with the state in registers (side a multiple of 32 and
+# of the cluster size): 64, 96, 128, 256; with the state in shared memory: 37,
+# 16, 200; several launches (state larger than one cluster): 512
+@pytest.mark.parametrize("n,batch,lam,iters", [(64, 2, 0.02, 20), (96, 1, 0.04, 20), (128, 1, 0.05, 7),
+                                               (256, 2, 0.02, 20), (37, 1, 0.1, 20), (16, 3, 0.3, 50),
+                                               (200, 1, 0.02, 20), (512, 2, 0.02, 6)])
 def test_tv_denoise_parity(n, batch, lam, iters):
     import torch
     rng = np.random.default_rng(n)
