@@ -115,9 +115,9 @@ Layout make_layout(const pnp_geom& g)
     L.off_res = off; off = align_up(off + (size_t)g.batch * nr * sizeof(float));
     L.off_y = off; off = align_up(off + img * sizeof(float));
     L.off_z = off; off = align_up(off + img * sizeof(float));
-    L.off_tv = off; off = align_up(off + 6 * img * sizeof(float));
+    L.off_tv = off; off = align_up(off + 8 * img * sizeof(float));
     L.off_pw = off; off = align_up(off + 2 * (size_t)g.n * g.n * sizeof(float));
-    const size_t tv_parts = (size_t)((g.n + 31) / 32) * ((g.n + 7) / 8);
+    const size_t tv_parts = (size_t)tile_tv_parts(g.n, g.batch);
     const size_t parts = tv_parts > (size_t)kRedBlocks ? tv_parts : (size_t)kRedBlocks;
     L.off_red = off; off = align_up(off + ((size_t)g.batch * parts + (size_t)g.batch * 8) * sizeof(double));
     L.off_log = off; off = align_up(off + (size_t)PNP_MAX_LOG_ITERS * sizeof(double));
@@ -127,7 +127,7 @@ Layout make_layout(const pnp_geom& g)
 
 inline size_t red_parts(const pnp_geom& g)
 {
-    const size_t tv_parts = (size_t)((g.n + 31) / 32) * ((g.n + 7) / 8);
+    const size_t tv_parts = (size_t)tile_tv_parts(g.n, g.batch);
     return tv_parts > (size_t)kRedBlocks ? tv_parts : (size_t)kRedBlocks;
 }
 
@@ -259,34 +259,6 @@ int grad_into(const pnp_geom& g, const Layout& L, int li, char* ws, const float*
     return PNP_OK;
 }
 
-std::vector<float> fgp_momenta(int iters)
-{
-    std::vector<float> m(iters > 0 ? iters : 0);
-    double t = 1.0;
-    for (int k = 0; k < iters; ++k) {
-        double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
-        m[k] = (float)((t - 1.0) / tn);
-        t = tn;
-    }
-    return m;
-}
-
-// TV iterations on z, leaving the dual in tv.p; returns the plane pointer.
-int tv_iterations(const float* z, TvBuffers tv, int n, int batch, float lambda, int iters,
-                  cudaStream_t st)
-{
-    std::vector<float> mom = fgp_momenta(iters);
-    const float* rin = tv.ra;
-    float* rout = tv.rb;
-    for (int k = 0; k < iters; ++k) {
-        PNP_CUDA(launch_tv_iter(z, tv, rin, rout, n, batch, lambda, mom[k], k == 0, st));
-        const float* t = rout;
-        rout = (float*)rin;
-        rin = t;
-    }
-    return PNP_OK;
-}
-
 }  // namespace
 }  // namespace pnp
 
@@ -409,7 +381,7 @@ int pnp_tv_workspace_size(int n, int batch, size_t* bytes)
     t_err.clear();
     if (n < 2 || batch < 1 || (double)n * n * batch > 4.0e9) return fail(PNP_EINVAL, "bad n or batch");
     if (!bytes) return fail(PNP_EINVAL, "bytes pointer is NULL");
-    *bytes = 6 * (size_t)batch * n * n * sizeof(float);
+    *bytes = 8 * (size_t)batch * n * n * sizeof(float);
     return PNP_OK;
 }
 
@@ -423,18 +395,16 @@ int pnp_tv_denoise(const float* d_z, float* d_x, int n, int batch, float lambda,
     if (d_z == d_x) return fail(PNP_EINVAL, "z and x must not alias");
     if (iters < 0 || iters > 100000) return fail(PNP_EINVAL, "iters outside [0, 100000]");
     if (!(lambda >= 0.0f) || !std::isfinite(lambda)) return fail(PNP_EINVAL, "lambda must be >= 0");
-    int rows = 0;
-    const int cluster = iters > 0 && lambda > 0.0f && iters <= kFusedTvMaxIters ? fused_tv_cluster(n, &rows) : 0;
-    if (cluster > 0) {
-        PNP_CUDA(launch_tv_fused(d_z, n, batch, lambda, iters, 1.0f, 0.0f, d_x, nullptr, nullptr,
-                                 nullptr, cluster, rows, S(stream)));
-    } else if (iters > 0 && lambda > 0.0f) {
-        if (!d_ws || ws_bytes < need) return fail(PNP_EINVAL, "TV workspace needs %zu bytes", need);
+    if (iters > 0 && lambda > 0.0f) {
+        // one launch covers up to 16 iterations; more are chained through the workspace
+        const bool chained = iters > 16;
+        if (chained && (!d_ws || ws_bytes < need))
+            return fail(PNP_EINVAL, "TV workspace of %zu bytes needed for %d iterations", need, iters);
         const size_t img = (size_t)batch * n * n;
-        TvBuffers tv{(float*)d_ws, (float*)d_ws + 2 * img, (float*)d_ws + 4 * img};
-        if (int e = tv_iterations(d_z, tv, n, batch, lambda, iters, S(stream))) return e;
-        PNP_CUDA(launch_tv_final(d_z, tv.p, 1, n, batch, lambda, 1.0f, 0.0f, d_x, nullptr, nullptr,
-                                 nullptr, S(stream)));
+        float* sa = chained ? (float*)d_ws : nullptr;
+        float* sb = chained ? (float*)d_ws + 4 * img : nullptr;
+        PNP_CUDA(launch_tv_tiled(d_z, n, batch, lambda, iters, 1.0f, 0.0f, d_x, nullptr, nullptr,
+                                 nullptr, sa, sb, S(stream)));
     } else {
         PNP_CUDA(launch_copy(d_z, d_x, (size_t)batch * n * n, S(stream)));
     }
@@ -537,14 +507,11 @@ int pnp_run(const pnp_geom* g, const pnp_stage* stages, int n_stages, const doub
     float* y = (float*)(ws + L.off_y);
     float* z = (float*)(ws + L.off_z);
     float* tvb = (float*)(ws + L.off_tv);
-    TvBuffers tv{tvb, tvb + 2 * img, tvb + 4 * img};
     double* part = (double*)(ws + L.off_red);
     double* dlog = (double*)(ws + L.off_log);
-    const int tv_parts = ((g->n + 31) / 32) * ((g->n + 7) / 8);
     const bool do_tv = pr.tv_iters > 0 && pr.lambda > 0.0f;
-    std::vector<float> mom = fgp_momenta(do_tv ? pr.tv_iters : 0);
-    int tv_rows = 0;
-    const int tv_cluster = do_tv && pr.tv_iters <= kFusedTvMaxIters ? fused_tv_cluster(g->n, &tv_rows) : 0;
+    const int tv_parts = do_tv ? tile_tv_parts(g->n, g->batch)
+                               : ((g->n + 31) / 32) * ((g->n + 7) / 8);
     PNP_CUDA(launch_copy(d_x, y, img, st));
     long i = 0;
     for (int k = 0; k < n_stages; ++k) {
@@ -556,24 +523,12 @@ int pnp_run(const pnp_geom* g, const pnp_stage* stages, int n_stages, const doub
             if (int e = grad_into(*g, L, li, ws, y, d_b, p, P, kBackStep, (float)h_eta[k], z, st)) return e;
             const float a = pr.momentum ? (float)((double)(i - 1) / (double)(i + 3)) : 0.0f;
             double* mp = h_psnr_log ? part : nullptr;
-            if (tv_cluster > 0) {
-                PNP_CUDA(launch_tv_fused(z, g->n, g->batch, pr.lambda, pr.tv_iters, pr.alpha, a, d_x, y,
-                                         d_xtrue, mp, tv_cluster, tv_rows, st));
-                if (mp) PNP_CUDA(launch_reduce_final(part, tv_cluster, g->batch, dlog + (i - 1) * g->batch, 1, 0, st));
-                continue;
-            }
-            if (do_tv) {
-                const float* rin = tv.ra;
-                float* rout = tv.rb;
-                for (int t = 0; t < pr.tv_iters; ++t) {
-                    PNP_CUDA(launch_tv_iter(z, tv, rin, rout, g->n, g->batch, pr.lambda, mom[t], t == 0, st));
-                    const float* tmp = rout;
-                    rout = (float*)rin;
-                    rin = tmp;
-                }
-            }
-            PNP_CUDA(launch_tv_final(z, tv.p, do_tv, g->n, g->batch, pr.lambda, pr.alpha, a, d_x, y,
-                                     d_xtrue, mp, st));
+            if (do_tv)
+                PNP_CUDA(launch_tv_tiled(z, g->n, g->batch, pr.lambda, pr.tv_iters, pr.alpha, a, d_x, y,
+                                         d_xtrue, mp, tvb, tvb + 4 * img, st));
+            else
+                PNP_CUDA(launch_tv_final(z, nullptr, 0, g->n, g->batch, pr.lambda, pr.alpha, a, d_x, y,
+                                         d_xtrue, mp, st));
             if (mp) PNP_CUDA(launch_reduce_final(part, tv_parts, g->batch, dlog + (i - 1) * g->batch, 1, 0, st));
         }
     }

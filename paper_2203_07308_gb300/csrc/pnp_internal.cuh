@@ -48,7 +48,7 @@ struct Layout {
     size_t off_res = 0;      // float [batch][n_views][n_det]
     size_t off_y = 0;        // float [batch][n][n]
     size_t off_z = 0;        // float [batch][n][n]
-    size_t off_tv = 0;       // float [6][batch][n][n]
+    size_t off_tv = 0;       // float [8][batch][n][n]  TV state ping/pong (r1 r2 p1 p2)
     size_t off_pw = 0;       // float [2][n][n]   power iteration u, w
     size_t off_red = 0;      // double [batch][kRedBlocks] partials + [batch][8] results
     size_t off_log = 0;      // double [PNP_MAX_LOG_ITERS] (not used when batch grows; see api)
@@ -97,14 +97,6 @@ cudaError_t launch_pool(const float* fine, float* coarse, int n, int s, int batc
 cudaError_t launch_unpool(const float* coarse, float* fine, int n, int s, int batch, cudaStream_t st);
 
 // TV (FGP) --------------------------------------------------------------------
-struct TvBuffers {
-    float* p;     // [2][batch][n][n]  current dual (p, q)
-    float* ra;    // [2][batch][n][n]  momentum point, ping
-    float* rb;    // [2][batch][n][n]  momentum point, pong
-};
-// One FGP iteration: reads r_in (unless first), p; writes p and r_out.
-cudaError_t launch_tv_iter(const float* z, TvBuffers b, const float* r_in, float* r_out, int n,
-                           int batch, float lambda, float mom, int first, cudaStream_t st);
 // x = z - lambda L(p) (or z when iters == 0), then relaxation and momentum:
 //   xi = (1-alpha) z + alpha x;  y = xi + a (xi - xprev);  xprev <- xi.
 // With y == nullptr it writes x only (plain denoiser output to xprev).
@@ -113,16 +105,17 @@ cudaError_t launch_tv_final(const float* z, const float* p, int have_p, int n, i
                             float alpha, float a, float* xprev, float* y, const float* xtrue,
                             double* mse_partials, cudaStream_t st);
 
-// Fused FGP in one thread-block cluster per image (state in distributed shared
-// memory).  fused_tv_cluster returns the cluster size (0 = image too large) and
-// the rows per CTA; launch_tv_fused then runs all iterations plus the final
-// step of launch_tv_final in one launch (mse partials: [batch][cluster]).
-constexpr int kFusedTvMaxIters = 256;
-constexpr int kFusedTvSmem = 200 * 1024;
-int fused_tv_cluster(int n, int* rows);
-cudaError_t launch_tv_fused(const float* z, int n, int batch, float lambda, int iters, float alpha,
+// Temporally blocked FGP: every iteration of the denoiser (iters >= 1) for all
+// images, T x T tiles recomputing their halos (launch_tv_tiled chains launches
+// of at most 20 iterations through state_a / state_b, each [4][batch][n][n]
+// floats).  Then x, the relaxation and momentum as in launch_tv_final; mse
+// partials [batch][tile_tv_parts].
+constexpr int kTileMaxK = 20;
+int tile_tv_tile(int n, int batch);
+int tile_tv_parts(int n, int batch);
+cudaError_t launch_tv_tiled(const float* z, int n, int batch, float lambda, int iters, float alpha,
                             float amom, float* xprev, float* y, const float* xtrue, double* mse_part,
-                            int cluster, int rows, cudaStream_t st);
+                            float* state_a, float* state_b, cudaStream_t st);
 
 // Reductions -------------------------------------------------------------------
 enum RedMode { kRedDot = 0, kRedDiffSq = 1, kRedSq = 2, kRedTv = 3 };
