@@ -54,5 +54,5 @@ def test_calls_reject_bad_arguments_before_launch(lib):
     assert lib.pnp_sketch(C.byref(g24), 8, C.c_void_p(16), C.c_void_p(16), null) == 1
     assert lib.pnp_tv_denoise(C.c_void_p(16), C.c_void_p(16), 8, 1, C.c_float(0.1), 5, null, 0, null) == 1
     size = C.c_size_t(0)
-    assert lib.pnp_tv_workspace_size(64, 2, C.byref(size)) == 0 and size.value == 6 * 2 * 64 * 64 * 4
+    assert lib.pnp_tv_workspace_size(64, 2, C.byref(size)) == 0 and size.value == 8 * 2 * 64 * 64 * 4
     assert lib.pnp_launch_count() == 0
