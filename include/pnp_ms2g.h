@@ -146,7 +146,7 @@ int pnp_tv_workspace_size(int n, int batch, size_t* bytes);
  * row/column, dual step 1/(8 lambda), no box constraint) applied to each image:
  *   d_x ~= argmin_x 1/2 ||x - d_z||^2 + lambda TV(x).
  * d_z, d_x [batch][n][n] (may not alias).  d_ws (pnp_tv_workspace_size bytes)
- * carries the dual state between launches when iters > 16; it may be NULL
+ * carries the dual state between launches when iters > 8; it may be NULL
  * otherwise. */
 int pnp_tv_denoise(const float* d_z, float* d_x, int n, int batch, float lambda, int iters,
                    void* d_ws, size_t ws_bytes, void* stream);

@@ -396,8 +396,8 @@ int pnp_tv_denoise(const float* d_z, float* d_x, int n, int batch, float lambda,
     if (iters < 0 || iters > 100000) return fail(PNP_EINVAL, "iters outside [0, 100000]");
     if (!(lambda >= 0.0f) || !std::isfinite(lambda)) return fail(PNP_EINVAL, "lambda must be >= 0");
     if (iters > 0 && lambda > 0.0f) {
-        // one launch covers up to 16 iterations; more are chained through the workspace
-        const bool chained = iters > 16;
+        // one launch covers up to 8 iterations; more are chained through the workspace
+        const bool chained = iters > 8;
         if (chained && (!d_ws || ws_bytes < need))
             return fail(PNP_EINVAL, "TV workspace of %zu bytes needed for %d iterations", need, iters);
         const size_t img = (size_t)batch * n * n;

@@ -107,7 +107,7 @@ cudaError_t launch_tv_final(const float* z, const float* p, int have_p, int n, i
 
 // Temporally blocked FGP: every iteration of the denoiser (iters >= 1) for all
 // images, T x T tiles recomputing their halos (launch_tv_tiled chains launches
-// of at most 20 iterations through state_a / state_b, each [4][batch][n][n]
+// of at most 10 iterations through state_a / state_b, each [4][batch][n][n]
 // floats).  Then x, the relaxation and momentum as in launch_tv_final; mse
 // partials [batch][tile_tv_parts].
 constexpr int kTileMaxK = 20;

@@ -97,6 +97,25 @@ struct TileTvArgs {
     float mom[kTileMaxK];
 };
 
+// Row stride of the shared arrays: at least S and congruent to 8 mod 32, so
+// that rows sit on distinct bank offsets.
+__host__ __device__ inline int tile_pitch(int S) { return S + ((40 - S % 32) % 32); }
+
+// Visits the pixels of a rows x cols rectangle (origin r0, c0) with all
+// threads of the block, flat index -> (row, col) without an integer division
+// (the float reciprocal is exact for these small counts).
+#define TILE_FOR(r0, c0, rows, cols, ...)                                             \
+    {                                                                                 \
+        const int cnt_ = (rows) * (cols);                                             \
+        const float inv_ = 1.0f / (float)max(cols, 1);                                \
+        for (int f_ = threadIdx.x; f_ < cnt_; f_ += blockDim.x) {                     \
+            const int li_ = __float2int_rz(((float)f_ + 0.5f) * inv_);                \
+            const int i = (r0) + li_;                                                 \
+            const int j = (c0) + f_ - li_ * (cols);                                   \
+            __VA_ARGS__                                                               \
+        }                                                                             \
+    }
+
 template <int T>
 __global__ void __launch_bounds__(256) k_tv_tile(const TileTvArgs a)
 {
@@ -105,34 +124,29 @@ __global__ void __launch_bounds__(256) k_tv_tile(const TileTvArgs a)
     const int i0 = (blockIdx.x / tiles_x) * T, j0 = (blockIdx.x % tiles_x) * T;
     const int inst = blockIdx.y;
     const int S = T + 1 + 2 * K;                 // side of the loaded region
+    const int P = tile_pitch(S);
     const int oi = i0 - 1 - K, oj = j0 - 1 - K;  // its origin (may lie outside the image)
     extern __shared__ float sm[];
     float* z = sm;
-    float* r1 = sm + S * S;
-    float* r2 = sm + 2 * S * S;
-    float* p1 = sm + 3 * S * S;
-    float* p2 = sm + 4 * S * S;
-    float* xt = sm + 5 * S * S;
-    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    float2* rr = reinterpret_cast<float2*>(sm + S * P);          // (r1, r2)
+    float2* pp = reinterpret_cast<float2*>(sm + 3 * S * P);      // (p1, p2)
+    float* xt = sm + 5 * S * P;
     const long img = (long)inst * n * n;
     const float lam = a.lambda, inv8l = 1.0f / (8.0f * a.lambda);
     {   // load R_0
         const int ia = max(oi, 0), ib = min(oi + S, n), ja = max(oj, 0), jb = min(oj + S, n);
-        for (int i = ia + ty; i < ib; i += 8) {
-            for (int j = ja + tx; j < jb; j += 32) {
-                const int q = (i - oi) * S + (j - oj);
-                const long g = img + (long)i * n + j;
-                z[q] = __ldg(a.z + g);
-                if (a.first) {
-                    r1[q] = 0.0f; r2[q] = 0.0f; p1[q] = 0.0f; p2[q] = 0.0f;
-                } else {
-                    r1[q] = __ldg(a.sin + g);
-                    r2[q] = __ldg(a.sin + a.plane + g);
-                    p1[q] = __ldg(a.sin + 2 * a.plane + g);
-                    p2[q] = __ldg(a.sin + 3 * a.plane + g);
-                }
+        TILE_FOR(ia, ja, ib - ia, jb - ja, {
+            const int q = (i - oi) * P + (j - oj);
+            const long g = img + (long)i * n + j;
+            z[q] = __ldg(a.z + g);
+            if (a.first) {
+                rr[q] = make_float2(0.0f, 0.0f);
+                pp[q] = make_float2(0.0f, 0.0f);
+            } else {
+                rr[q] = make_float2(__ldg(a.sin + g), __ldg(a.sin + a.plane + g));
+                pp[q] = make_float2(__ldg(a.sin + 2 * a.plane + g), __ldg(a.sin + 3 * a.plane + g));
             }
-        }
+        })
     }
     __syncthreads();
     for (int k = 1; k <= K; ++k) {
@@ -141,86 +155,85 @@ __global__ void __launch_bounds__(256) k_tv_tile(const TileTvArgs a)
         const int ca = max(j0 - 1 - mg, 0), cb = min(j0 + T + mg, n);   // R_k cols
         // phase A: x_tmp on R_k plus one row below and one column to the right
         const int xrb = min(rb + 1, n), xcb = min(cb + 1, n);
-        for (int i = ra + ty; i < xrb; i += 8) {
-            for (int j = ca + tx; j < xcb; j += 32) {
-                const int q = (i - oi) * S + (j - oj);
-                float l = r1[q] + r2[q];
-                if (i > 0) l -= r1[q - S];
-                if (j > 0) l -= r2[q - 1];
-                xt[q] = z[q] - lam * l;
-            }
-        }
+        TILE_FOR(ra, ca, xrb - ra, xcb - ca, {
+            const int q = (i - oi) * P + (j - oj);
+            const float2 r = rr[q];
+            float l = r.x + r.y;
+            if (i > 0) l -= rr[q - P].x;
+            if (j > 0) l -= rr[q - 1].y;
+            xt[q] = z[q] - lam * l;
+        })
         __syncthreads();
         // phase B: dual step, isotropic projection, momentum on R_k
         const float m = a.mom[k - 1];
-        for (int i = ra + ty; i < rb; i += 8) {
-            for (int j = ca + tx; j < cb; j += 32) {
-                const int q = (i - oi) * S + (j - oj);
-                const float x0 = xt[q];
-                const float g1 = i < n - 1 ? x0 - xt[q + S] : 0.0f;
-                const float g2 = j < n - 1 ? x0 - xt[q + 1] : 0.0f;
-                float pa = fmaf(g1, inv8l, r1[q]);
-                float pc = fmaf(g2, inv8l, r2[q]);
-                const float den = fmaxf(sqrtf(fmaf(pa, pa, pc * pc)), 1.0f);
-                pa = pa / den;
-                pc = pc / den;
-                r1[q] = fmaf(m, pa - p1[q], pa);
-                r2[q] = fmaf(m, pc - p2[q], pc);
-                p1[q] = pa;
-                p2[q] = pc;
+        TILE_FOR(ra, ca, rb - ra, cb - ca, {
+            const int q = (i - oi) * P + (j - oj);
+            const float x0 = xt[q];
+            const float g1 = i < n - 1 ? x0 - xt[q + P] : 0.0f;
+            const float g2 = j < n - 1 ? x0 - xt[q + 1] : 0.0f;
+            const float2 r = rr[q];
+            const float2 po = pp[q];
+            float pa = fmaf(g1, inv8l, r.x);
+            float pc = fmaf(g2, inv8l, r.y);
+            const float nrm2 = fmaf(pa, pa, pc * pc);
+            if (nrm2 > 1.0f) {
+                const float sc = rsqrtf(nrm2);
+                pa *= sc;
+                pc *= sc;
             }
-        }
+            rr[q] = make_float2(fmaf(m, pa - po.x, pa), fmaf(m, pc - po.y, pc));
+            pp[q] = make_float2(pa, pc);
+        })
         __syncthreads();
     }
     const int ie = min(i0 + T, n), je = min(j0 + T, n);
     if (!a.last) {
-        for (int i = i0 + ty; i < ie; i += 8) {
-            for (int j = j0 + tx; j < je; j += 32) {
-                const int q = (i - oi) * S + (j - oj);
-                const long g = img + (long)i * n + j;
-                a.sout[g] = r1[q];
-                a.sout[a.plane + g] = r2[q];
-                a.sout[2 * a.plane + g] = p1[q];
-                a.sout[3 * a.plane + g] = p2[q];
-            }
-        }
+        TILE_FOR(i0, j0, ie - i0, je - j0, {
+            const int q = (i - oi) * P + (j - oj);
+            const long g = img + (long)i * n + j;
+            const float2 r = rr[q], p = pp[q];
+            a.sout[g] = r.x;
+            a.sout[a.plane + g] = r.y;
+            a.sout[2 * a.plane + g] = p.x;
+            a.sout[3 * a.plane + g] = p.y;
+        })
         return;
     }
     // x = z - lambda L(p) on the tile, relaxation, momentum, squared error
     double e2 = 0.0;
-    for (int i = i0 + ty; i < ie; i += 8) {
-        for (int j = j0 + tx; j < je; j += 32) {
-            const int q = (i - oi) * S + (j - oj);
-            const float zz = z[q];
-            float l = p1[q] + p2[q];
-            if (i > 0) l -= p1[q - S];
-            if (j > 0) l -= p2[q - 1];
-            const float x = zz - lam * l;
-            const float xi = (1.0f - a.alpha) * zz + a.alpha * x;
-            const long g = img + (long)i * n + j;
-            if (a.y) {
-                const float xp = a.xprev[g];
-                a.y[g] = xi + a.amom * (xi - xp);
-            }
-            a.xprev[g] = xi;
-            if (a.xtrue) {
-                const double d = (double)xi - (double)__ldg(a.xtrue + g);
-                e2 += d * d;
-            }
+    TILE_FOR(i0, j0, ie - i0, je - j0, {
+        const int q = (i - oi) * P + (j - oj);
+        const float zz = z[q];
+        const float2 p = pp[q];
+        float l = p.x + p.y;
+        if (i > 0) l -= pp[q - P].x;
+        if (j > 0) l -= pp[q - 1].y;
+        const float x = zz - lam * l;
+        const float xi = (1.0f - a.alpha) * zz + a.alpha * x;
+        const long g = img + (long)i * n + j;
+        if (a.y) {
+            const float xp = a.xprev[g];
+            a.y[g] = xi + a.amom * (xi - xp);
         }
-    }
+        a.xprev[g] = xi;
+        if (a.xtrue) {
+            const double d = (double)xi - (double)__ldg(a.xtrue + g);
+            e2 += d * d;
+        }
+    })
     if (a.mse_part) {
         __shared__ double red[8];
         for (int off = 16; off > 0; off >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, off);
-        if (tx == 0) red[ty] = e2;
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e2;
         __syncthreads();
-        if (ty == 0 && tx == 0) {
+        if (threadIdx.x == 0) {
             double v = 0.0;
             for (int w = 0; w < 8; ++w) v += red[w];
             a.mse_part[(long)inst * gridDim.x + blockIdx.x] = v;
         }
     }
 }
+#undef TILE_FOR
 
 inline cudaError_t counted(cudaError_t e = cudaGetLastError())
 {
@@ -246,7 +259,11 @@ cudaError_t launch_tv_final(const float* z, const float* p, int have_p, int n, i
 namespace pnp {
 
 namespace {
-inline size_t tile_smem(int T, int K) { return (size_t)6 * (T + 1 + 2 * K) * (T + 1 + 2 * K) * sizeof(float); }
+inline size_t tile_smem(int T, int K)
+{
+    const int S = T + 1 + 2 * K;
+    return (size_t)6 * S * tile_pitch(S) * sizeof(float);
+}
 
 template <int T>
 void tile_attr()
@@ -276,7 +293,7 @@ cudaError_t launch_tv_tiled(const float* z, int n, int batch, float lambda, int 
                             float* state_a, float* state_b, cudaStream_t st)
 {
     const int T = tile_tv_tile(n, batch);
-    const int kmax = T == 16 ? 20 : 16;
+    const int kmax = T == 16 ? 10 : 8;   // halo recompute vs launches
     const int tiles = ((n + T - 1) / T) * ((n + T - 1) / T);
     if (iters < 1) return cudaErrorInvalidValue;
     if (iters > kmax && (!state_a || !state_b)) return cudaErrorInvalidValue;   // chaining needs state
@@ -303,7 +320,7 @@ cudaError_t launch_tv_tiled(const float* z, int n, int batch, float lambda, int 
         a.sin = sin;
         a.sout = a.last ? nullptr : sout;
         for (int k = 0; k < K; ++k) a.mom[k] = mom[k0 + k];
-        dim3 grd(tiles, batch), blk(32, 8);
+        dim3 grd(tiles, batch), blk(256);
         if (T == 16) {
             tile_attr<16>();
             k_tv_tile<16><<<grd, blk, tile_smem(16, K), st>>>(a);
