@@ -91,7 +91,7 @@ __global__ void k_tv_final(const float* __restrict__ z, const float* __restrict_
 struct TileTvArgs {
     const float* z; const float* sin; float* sout;   // state planes [4][batch][n][n]: r1 r2 p1 p2
     float* xprev; float* y; const float* xtrue; double* mse_part;
-    int n, K, first, last;
+    int n, T, K, first, last;
     long plane;
     float lambda, alpha, amom;
     float mom[kTileMaxK];
@@ -116,10 +116,9 @@ __host__ __device__ inline int tile_pitch(int S) { return S + ((40 - S % 32) % 3
         }                                                                             \
     }
 
-template <int T>
-__global__ void __launch_bounds__(256) k_tv_tile(const TileTvArgs a)
+__global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs a)
 {
-    const int n = a.n, K = a.K;
+    const int n = a.n, K = a.K, T = a.T;
     const int tiles_x = (n + T - 1) / T;
     const int i0 = (blockIdx.x / tiles_x) * T, j0 = (blockIdx.x % tiles_x) * T;
     const int inst = blockIdx.y;
@@ -222,13 +221,13 @@ __global__ void __launch_bounds__(256) k_tv_tile(const TileTvArgs a)
         }
     })
     if (a.mse_part) {
-        __shared__ double red[8];
+        __shared__ double red[32];
         for (int off = 16; off > 0; off >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, off);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e2;
         __syncthreads();
         if (threadIdx.x == 0) {
             double v = 0.0;
-            for (int w = 0; w < 8; ++w) v += red[w];
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
             a.mse_part[(long)inst * gridDim.x + blockIdx.x] = v;
         }
     }
@@ -259,28 +258,38 @@ cudaError_t launch_tv_final(const float* z, const float* p, int have_p, int n, i
 namespace pnp {
 
 namespace {
+constexpr int kTileThreads = 1024;
+constexpr int kTileKMax = 10;            // iterations per launch (halo recompute vs launches)
+constexpr size_t kTileSmemMax = 112 * 1024;
+
 inline size_t tile_smem(int T, int K)
 {
     const int S = T + 1 + 2 * K;
     return (size_t)6 * S * tile_pitch(S) * sizeof(float);
 }
 
-template <int T>
-void tile_attr()
+// Tile side: minimises the busiest SM's work, (tiles per SM, rounded up) x
+// (work per tile ~ (T + 1 + K)^2); CTAs sharing an SM share its issue slots.
+int choose_tile(int n, int batch)
 {
-    static bool done = false;
-    if (!done) {
-        cudaFuncSetAttribute(k_tv_tile<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
-        done = true;
+    int best = 16;
+    double best_cost = 1e300;
+    for (int T = 8; T <= 40; ++T) {
+        if (tile_smem(T, kTileKMax) > kTileSmemMax) break;
+        const long tiles = (long)batch * ((n + T - 1) / T) * ((n + T - 1) / T);
+        const long waves = (tiles + 151) / 152;
+        const double side = (double)std::min(T, n) + 1 + kTileKMax;
+        const double cost = (double)waves * side * side;
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best = T;
+        }
     }
+    return best;
 }
 }  // namespace
 
-int tile_tv_tile(int n, int batch)
-{
-    const long t16 = (long)batch * ((n + 15) / 16) * ((n + 15) / 16);
-    return t16 <= 4L * 152 ? 16 : 32;
-}
+int tile_tv_tile(int n, int batch) { return choose_tile(n, batch); }
 
 int tile_tv_parts(int n, int batch)
 {
@@ -292,11 +301,15 @@ cudaError_t launch_tv_tiled(const float* z, int n, int batch, float lambda, int 
                             float amom, float* xprev, float* y, const float* xtrue, double* mse_part,
                             float* state_a, float* state_b, cudaStream_t st)
 {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_tv_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemMax);
+        attr = true;
+    }
     const int T = tile_tv_tile(n, batch);
-    const int kmax = T == 16 ? 10 : 8;   // halo recompute vs launches
     const int tiles = ((n + T - 1) / T) * ((n + T - 1) / T);
     if (iters < 1) return cudaErrorInvalidValue;
-    if (iters > kmax && (!state_a || !state_b)) return cudaErrorInvalidValue;   // chaining needs state
+    if (iters > kTileKMax && (!state_a || !state_b)) return cudaErrorInvalidValue;   // chaining needs state
     std::vector<float> mom((size_t)iters);
     double t = 1.0;
     for (int k = 0; k < iters; ++k) {
@@ -306,28 +319,21 @@ cudaError_t launch_tv_tiled(const float* z, int n, int batch, float lambda, int 
     }
     TileTvArgs a{};
     a.z = z; a.xprev = xprev; a.y = y; a.xtrue = xtrue; a.mse_part = mse_part;
-    a.n = n; a.plane = (long)batch * n * n;
+    a.n = n; a.T = T; a.plane = (long)batch * n * n;
     a.lambda = lambda; a.alpha = alpha; a.amom = amom;
     const float* sin = nullptr;
     float* sout = state_a;
     int k0 = 0;
     cudaError_t e = cudaSuccess;
     do {
-        const int K = std::min(kmax, iters - k0);
+        const int K = std::min(kTileKMax, iters - k0);
         a.K = K;
         a.first = k0 == 0;
         a.last = k0 + K == iters;
         a.sin = sin;
         a.sout = a.last ? nullptr : sout;
         for (int k = 0; k < K; ++k) a.mom[k] = mom[k0 + k];
-        dim3 grd(tiles, batch), blk(256);
-        if (T == 16) {
-            tile_attr<16>();
-            k_tv_tile<16><<<grd, blk, tile_smem(16, K), st>>>(a);
-        } else {
-            tile_attr<32>();
-            k_tv_tile<32><<<grd, blk, tile_smem(32, K), st>>>(a);
-        }
+        k_tv_tile<<<dim3(tiles, batch), kTileThreads, tile_smem(T, K), st>>>(a);
         e = cudaGetLastError();
         g_launches.fetch_add(1, std::memory_order_relaxed);
         if (e != cudaSuccess) return e;
