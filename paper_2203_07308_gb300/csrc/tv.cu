@@ -101,21 +101,12 @@ struct TileTvArgs {
 // that rows sit on distinct bank offsets.
 __host__ __device__ inline int tile_pitch(int S) { return S + ((40 - S % 32) % 32); }
 
-// Visits the pixels of a rows x cols rectangle (origin r0, c0) with all
-// threads of the block, flat index -> (row, col) without an integer division
-// (the float reciprocal is exact for these small counts).
-#define TILE_FOR(r0, c0, rows, cols, ...)                                             \
-    {                                                                                 \
-        const int cnt_ = (rows) * (cols);                                             \
-        const float inv_ = 1.0f / (float)max(cols, 1);                                \
-        for (int f_ = threadIdx.x; f_ < cnt_; f_ += blockDim.x) {                     \
-            const int li_ = __float2int_rz(((float)f_ + 0.5f) * inv_);                \
-            const int i = (r0) + li_;                                                 \
-            const int j = (c0) + f_ - li_ * (cols);                                   \
-            __VA_ARGS__                                                               \
-        }                                                                             \
-    }
-
+// Thread t owns the region pixels with flat index t, t + 1024, ... (NP of
+// them) for the whole launch: their z, r and p stay in registers together with
+// the pixel's shared-memory offset and two Chebyshev distances that decide in
+// which iterations it is inside the shrinking regions.  Shared memory holds
+// only what neighbours read: r (phase A), x_tmp (phase B) and, at the end, p.
+template <int NP>
 __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs a)
 {
     const int n = a.n, K = a.K, T = a.T;
@@ -126,100 +117,126 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs a)
     const int P = tile_pitch(S);
     const int oi = i0 - 1 - K, oj = j0 - 1 - K;  // its origin (may lie outside the image)
     extern __shared__ float sm[];
-    float* z = sm;
-    float2* rr = reinterpret_cast<float2*>(sm + S * P);          // (r1, r2)
-    float2* pp = reinterpret_cast<float2*>(sm + 3 * S * P);      // (p1, p2)
-    float* xt = sm + 5 * S * P;
+    float2* rr = reinterpret_cast<float2*>(sm);          // (r1, r2)   [S][P]
+    float* xt = sm + 2 * S * P;                           // x_tmp      [S][P]
+    float2* pp = reinterpret_cast<float2*>(sm + 3 * S * P);   // (p1, p2), final step only
     const long img = (long)inst * n * n;
     const float lam = a.lambda, inv8l = 1.0f / (8.0f * a.lambda);
-    {   // load R_0
-        const int ia = max(oi, 0), ib = min(oi + S, n), ja = max(oj, 0), jb = min(oj + S, n);
-        TILE_FOR(ia, ja, ib - ia, jb - ja, {
-            const int q = (i - oi) * P + (j - oj);
+    constexpr int kFar = 1 << 20;
+
+    float z[NP], r1[NP], r2[NP], p1[NP], p2[NP];
+    int q[NP], dA[NP], dB[NP], flags[NP];
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+        const int f = threadIdx.x + m * blockDim.x;
+        const int li = f / S, lj = f - li * S;
+        const int i = oi + li, j = oj + lj;
+        q[m] = li * P + lj;
+        z[m] = r1[m] = r2[m] = p1[m] = p2[m] = 0.0f;
+        flags[m] = 0;
+        dA[m] = dB[m] = kFar;
+        if (f < S * S && i >= 0 && i < n && j >= 0 && j < n) {
+            // distance outside the core of R_k ([i0-1, i0+T) x [j0-1, j0+T)) and of
+            // the phase-A region (core grown by one row below, one column right)
+            dB[m] = max(max(i0 - 1 - i, i - (i0 + T - 1)), max(max(j0 - 1 - j, j - (j0 + T - 1)), 0));
+            dA[m] = max(max(i0 - 1 - i, i - (i0 + T)), max(max(j0 - 1 - j, j - (j0 + T)), 0));
+            flags[m] = (i > 0 ? 1 : 0) | (j > 0 ? 2 : 0) | (i < n - 1 ? 4 : 0) | (j < n - 1 ? 8 : 0) |
+                       (i >= i0 && i < i0 + T && j >= j0 && j < j0 + T ? 16 : 0);
             const long g = img + (long)i * n + j;
-            z[q] = __ldg(a.z + g);
-            if (a.first) {
-                rr[q] = make_float2(0.0f, 0.0f);
-                pp[q] = make_float2(0.0f, 0.0f);
-            } else {
-                rr[q] = make_float2(__ldg(a.sin + g), __ldg(a.sin + a.plane + g));
-                pp[q] = make_float2(__ldg(a.sin + 2 * a.plane + g), __ldg(a.sin + 3 * a.plane + g));
+            z[m] = __ldg(a.z + g);
+            if (!a.first) {
+                r1[m] = __ldg(a.sin + g);
+                r2[m] = __ldg(a.sin + a.plane + g);
+                p1[m] = __ldg(a.sin + 2 * a.plane + g);
+                p2[m] = __ldg(a.sin + 3 * a.plane + g);
             }
-        })
+            rr[q[m]] = make_float2(r1[m], r2[m]);
+        }
     }
     __syncthreads();
     for (int k = 1; k <= K; ++k) {
         const int mg = K - k;
-        const int ra = max(i0 - 1 - mg, 0), rb = min(i0 + T + mg, n);   // R_k rows
-        const int ca = max(j0 - 1 - mg, 0), cb = min(j0 + T + mg, n);   // R_k cols
-        // phase A: x_tmp on R_k plus one row below and one column to the right
-        const int xrb = min(rb + 1, n), xcb = min(cb + 1, n);
-        TILE_FOR(ra, ca, xrb - ra, xcb - ca, {
-            const int q = (i - oi) * P + (j - oj);
-            const float2 r = rr[q];
-            float l = r.x + r.y;
-            if (i > 0) l -= rr[q - P].x;
-            if (j > 0) l -= rr[q - 1].y;
-            xt[q] = z[q] - lam * l;
-        })
-        __syncthreads();
-        // phase B: dual step, isotropic projection, momentum on R_k
-        const float m = a.mom[k - 1];
-        TILE_FOR(ra, ca, rb - ra, cb - ca, {
-            const int q = (i - oi) * P + (j - oj);
-            const float x0 = xt[q];
-            const float g1 = i < n - 1 ? x0 - xt[q + P] : 0.0f;
-            const float g2 = j < n - 1 ? x0 - xt[q + 1] : 0.0f;
-            const float2 r = rr[q];
-            const float2 po = pp[q];
-            float pa = fmaf(g1, inv8l, r.x);
-            float pc = fmaf(g2, inv8l, r.y);
-            const float nrm2 = fmaf(pa, pa, pc * pc);
-            if (nrm2 > 1.0f) {
-                const float sc = rsqrtf(nrm2);
-                pa *= sc;
-                pc *= sc;
+        float x0[NP];
+        // phase A: x_tmp = z - lambda L(r)
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+            x0[m] = 0.0f;
+            if (dA[m] <= mg) {
+                float l = r1[m] + r2[m];
+                if (flags[m] & 1) l -= rr[q[m] - P].x;
+                if (flags[m] & 2) l -= rr[q[m] - 1].y;
+                x0[m] = z[m] - lam * l;
+                xt[q[m]] = x0[m];
             }
-            rr[q] = make_float2(fmaf(m, pa - po.x, pa), fmaf(m, pc - po.y, pc));
-            pp[q] = make_float2(pa, pc);
-        })
+        }
+        __syncthreads();
+        // phase B: dual step, isotropic projection, momentum
+        const float mo = a.mom[k - 1];
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+            if (dB[m] <= mg) {
+                const float g1 = (flags[m] & 4) ? x0[m] - xt[q[m] + P] : 0.0f;
+                const float g2 = (flags[m] & 8) ? x0[m] - xt[q[m] + 1] : 0.0f;
+                float pa = fmaf(g1, inv8l, r1[m]);
+                float pc = fmaf(g2, inv8l, r2[m]);
+                const float nrm2 = fmaf(pa, pa, pc * pc);
+                if (nrm2 > 1.0f) {
+                    const float sc = rsqrtf(nrm2);
+                    pa *= sc;
+                    pc *= sc;
+                }
+                r1[m] = fmaf(mo, pa - p1[m], pa);
+                r2[m] = fmaf(mo, pc - p2[m], pc);
+                p1[m] = pa;
+                p2[m] = pc;
+                rr[q[m]] = make_float2(r1[m], r2[m]);
+            }
+        }
         __syncthreads();
     }
-    const int ie = min(i0 + T, n), je = min(j0 + T, n);
     if (!a.last) {
-        TILE_FOR(i0, j0, ie - i0, je - j0, {
-            const int q = (i - oi) * P + (j - oj);
-            const long g = img + (long)i * n + j;
-            const float2 r = rr[q], p = pp[q];
-            a.sout[g] = r.x;
-            a.sout[a.plane + g] = r.y;
-            a.sout[2 * a.plane + g] = p.x;
-            a.sout[3 * a.plane + g] = p.y;
-        })
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+            if (flags[m] & 16) {
+                const int f = threadIdx.x + m * blockDim.x;
+                const int li = f / S, lj = f - li * S;
+                const long g = img + (long)(oi + li) * n + (oj + lj);
+                a.sout[g] = r1[m];
+                a.sout[a.plane + g] = r2[m];
+                a.sout[2 * a.plane + g] = p1[m];
+                a.sout[3 * a.plane + g] = p2[m];
+            }
+        }
         return;
     }
     // x = z - lambda L(p) on the tile, relaxation, momentum, squared error
+#pragma unroll
+    for (int m = 0; m < NP; ++m)
+        if (dB[m] == 0) pp[q[m]] = make_float2(p1[m], p2[m]);
+    __syncthreads();
     double e2 = 0.0;
-    TILE_FOR(i0, j0, ie - i0, je - j0, {
-        const int q = (i - oi) * P + (j - oj);
-        const float zz = z[q];
-        const float2 p = pp[q];
-        float l = p.x + p.y;
-        if (i > 0) l -= pp[q - P].x;
-        if (j > 0) l -= pp[q - 1].y;
-        const float x = zz - lam * l;
-        const float xi = (1.0f - a.alpha) * zz + a.alpha * x;
-        const long g = img + (long)i * n + j;
-        if (a.y) {
-            const float xp = a.xprev[g];
-            a.y[g] = xi + a.amom * (xi - xp);
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+        if (flags[m] & 16) {
+            float l = p1[m] + p2[m];
+            if (flags[m] & 1) l -= pp[q[m] - P].x;
+            if (flags[m] & 2) l -= pp[q[m] - 1].y;
+            const float x = z[m] - lam * l;
+            const float xi = (1.0f - a.alpha) * z[m] + a.alpha * x;
+            const int f = threadIdx.x + m * blockDim.x;
+            const int li = f / S, lj = f - li * S;
+            const long g = img + (long)(oi + li) * n + (oj + lj);
+            if (a.y) {
+                const float xp = a.xprev[g];
+                a.y[g] = xi + a.amom * (xi - xp);
+            }
+            a.xprev[g] = xi;
+            if (a.xtrue) {
+                const double d = (double)xi - (double)__ldg(a.xtrue + g);
+                e2 += d * d;
+            }
         }
-        a.xprev[g] = xi;
-        if (a.xtrue) {
-            const double d = (double)xi - (double)__ldg(a.xtrue + g);
-            e2 += d * d;
-        }
-    })
+    }
     if (a.mse_part) {
         __shared__ double red[32];
         for (int off = 16; off > 0; off >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, off);
@@ -232,7 +249,6 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs a)
         }
     }
 }
-#undef TILE_FOR
 
 inline cudaError_t counted(cudaError_t e = cudaGetLastError())
 {
@@ -265,7 +281,14 @@ constexpr size_t kTileSmemMax = 112 * 1024;
 inline size_t tile_smem(int T, int K)
 {
     const int S = T + 1 + 2 * K;
-    return (size_t)6 * S * tile_pitch(S) * sizeof(float);
+    return (size_t)5 * S * tile_pitch(S) * sizeof(float);
+}
+
+// pixels per thread needed to cover the (T + 1 + 2K)^2 region with 1024 threads
+inline int tile_np(int T, int K)
+{
+    const int S = T + 1 + 2 * K;
+    return (S * S + kTileThreads - 1) / kTileThreads;
 }
 
 // Tile side: minimises the busiest SM's work, (tiles per SM, rounded up) x
@@ -275,7 +298,7 @@ int choose_tile(int n, int batch)
     int best = 16;
     double best_cost = 1e300;
     for (int T = 8; T <= 40; ++T) {
-        if (tile_smem(T, kTileKMax) > kTileSmemMax) break;
+        if (tile_smem(T, kTileKMax) > kTileSmemMax || tile_np(T, kTileKMax) > 4) break;
         const long tiles = (long)batch * ((n + T - 1) / T) * ((n + T - 1) / T);
         const long waves = (tiles + 151) / 152;
         const double side = (double)std::min(T, n) + 1 + kTileKMax;
@@ -303,7 +326,10 @@ cudaError_t launch_tv_tiled(const float* z, int n, int batch, float lambda, int 
 {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_tv_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemMax);
+        cudaFuncSetAttribute(k_tv_tile<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemMax);
+        cudaFuncSetAttribute(k_tv_tile<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemMax);
+        cudaFuncSetAttribute(k_tv_tile<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemMax);
+        cudaFuncSetAttribute(k_tv_tile<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemMax);
         attr = true;
     }
     const int T = tile_tv_tile(n, batch);
@@ -333,7 +359,13 @@ cudaError_t launch_tv_tiled(const float* z, int n, int batch, float lambda, int 
         a.sin = sin;
         a.sout = a.last ? nullptr : sout;
         for (int k = 0; k < K; ++k) a.mom[k] = mom[k0 + k];
-        k_tv_tile<<<dim3(tiles, batch), kTileThreads, tile_smem(T, K), st>>>(a);
+        const dim3 grd(tiles, batch);
+        switch (tile_np(T, K)) {
+            case 1: k_tv_tile<1><<<grd, kTileThreads, tile_smem(T, K), st>>>(a); break;
+            case 2: k_tv_tile<2><<<grd, kTileThreads, tile_smem(T, K), st>>>(a); break;
+            case 3: k_tv_tile<3><<<grd, kTileThreads, tile_smem(T, K), st>>>(a); break;
+            default: k_tv_tile<4><<<grd, kTileThreads, tile_smem(T, K), st>>>(a); break;
+        }
         e = cudaGetLastError();
         g_launches.fetch_add(1, std::memory_order_relaxed);
         if (e != cudaSuccess) return e;
