@@ -188,6 +188,52 @@ int pnp_objective(const pnp_geom* g, const float* d_x, const float* d_b, const f
 int pnp_sample_count(const pnp_geom* g, int factor, int subset, int n_subsets, double* h_count,
                      void* d_ws, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Differentiable form.  Sec. 2 of the paper remarks that the sketched
+ * iterations (and their denoiser and sampling operators) can be unrolled and
+ * trained end to end.  These calls give one iteration of Algorithm 1 as a
+ * differentiable function of (y_{i-1}, x_{i-1}, lambda) and its exact
+ * vector-Jacobian product; the VJP recomputes the iteration's forward pass, so
+ * a caller that unrolls T iterations keeps only each iteration's inputs
+ * (per-iteration checkpointing).  The FGP reverse sweep follows the FGP
+ * recurrence of pnp_tv_denoise backwards (projection Jacobian
+ * (I - a a^T/|a|^2)/|a| where |a| > 1, identity elsewhere).
+ * --------------------------------------------------------------------------- */
+
+/* Bytes of VJP workspace for pnp_tv_vjp on [batch][n][n] with `iters` FGP
+ * iterations (all pre-projection points of the forward pass are stored). */
+int pnp_tv_vjp_workspace_size(int n, int batch, int iters, size_t* bytes);
+
+/* Reverse mode of pnp_tv_denoise: d_zbar = (dx/dz)^T d_xbar and, if h_lambar is
+ * not NULL, h_lambar[b] = <d_xbar[b], dx[b]/dlambda> for each instance
+ * (synchronous then).  lambda > 0 when iters > 0.  d_ws of
+ * pnp_tv_vjp_workspace_size bytes. */
+int pnp_tv_vjp(const float* d_z, const float* d_xbar, float* d_zbar, double* h_lambar, int n, int batch,
+               float lambda, int iters, void* d_ws, size_t ws_bytes, void* stream);
+
+/* Bytes of the second (VJP) workspace of pnp_unrolled_step_vjp. */
+int pnp_vjp_workspace_size(const pnp_geom* g, int tv_iters, size_t* bytes);
+
+/* One iteration of Algorithm 1 with sketch factor `factor`, angle subset
+ * (subset, n_subsets), step eta, momentum coefficient amom (the a_i of that
+ * iteration) and params alpha, lambda, tv_iters (momentum field unused):
+ *   z = y - eta c S^T A_s^{(p)T}(A_s^{(p)} S y - b^{(p)});
+ *   x_out = (1 - alpha) z + alpha D(z);  y_out = x_out + amom (x_out - x_prev).
+ * Inputs are not modified; outputs must not alias inputs. */
+int pnp_unrolled_step(const pnp_geom* g, int factor, int subset, int n_subsets, double eta,
+                      const pnp_run_params* params, float amom, const float* d_y, const float* d_xprev,
+                      const float* d_b, float* d_xout, float* d_yout, void* d_ws, void* stream);
+
+/* VJP of pnp_unrolled_step: given d_xbar, d_ybar (gradients of a loss with
+ * respect to x_out and y_out) returns d_ybar_in = dJ/dy, d_xpbar = dJ/dx_prev
+ * and, if h_lambar is not NULL, h_lambar[b] = dJ/dlambda for each instance
+ * (synchronous then).  d_vjp_ws of pnp_vjp_workspace_size bytes.  The data b
+ * is treated as a constant. */
+int pnp_unrolled_step_vjp(const pnp_geom* g, int factor, int subset, int n_subsets, double eta,
+                          const pnp_run_params* params, float amom, const float* d_y, const float* d_b,
+                          const float* d_xbar, const float* d_ybar, float* d_ybar_in, float* d_xpbar,
+                          double* h_lambar, void* d_ws, void* d_vjp_ws, size_t vjp_ws_bytes, void* stream);
+
 /* Bytes of scratch inside the library for pnp_full_grad_noalloc (per GPU that
  * loads the library, held until the process exits). */
 #define PNP_NOALLOC_SCRATCH_BYTES (32u << 20)

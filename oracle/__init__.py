@@ -93,6 +93,11 @@ def _load():
             lib.orc_pnp_run.argtypes = [gp, C.c_int, ip, dp, ip, dp, dp, C.c_double, C.c_double,
                                         C.c_int, C.c_int, dp, dp]
             lib.orc_objective.argtypes = [gp, dp, dp, dp]
+            lib.orc_fgp_vjp.argtypes = [C.c_int, dp, C.c_double, C.c_int, dp, dp, dp]
+            lib.orc_step.argtypes = [gp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                     C.c_int, C.c_double, dp, dp, dp, dp, dp]
+            lib.orc_step_vjp.argtypes = [gp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                         C.c_double, C.c_int, C.c_double, dp, dp, dp, dp, dp, dp, dp]
             lib.orc_sample_count.argtypes = [gp, C.c_int, C.c_int, C.c_int]
             lib.orc_sample_count.restype = C.c_double
             _lib = lib
@@ -240,3 +245,43 @@ def simulate(g, x_true, w, noise_rel: float):
     """b = A x_true + sigma w with sigma = noise_rel * max|A x_true| (Eq. 1)."""
     ax = project(g, 1, x_true)
     return ax + noise_rel * np.abs(ax).max() * _f64(w).reshape(ax.shape)
+
+
+# ---------------------------------------------------------------- differentiable form
+def fgp_vjp(z, lam: float, iters: int, xbar):
+    """(zbar, lambar): reverse-mode derivative of ``fgp`` (Beck & Teboulle's FGP
+    unrolled for ``iters`` iterations) applied to the output gradient ``xbar``."""
+    z = _f64(z)
+    xbar = _f64(xbar)
+    zbar = np.zeros_like(z)
+    lb = C.c_double(0.0)
+    _load().orc_fgp_vjp(z.shape[-1], _dp(z), float(lam), int(iters), _dp(xbar), _dp(zbar), C.byref(lb))
+    return zbar, float(lb.value)
+
+
+def step(g, s: int, p: int, P: int, eta: float, alpha: float, lam: float, tv_iters: int, amom: float,
+         y, xprev, b):
+    """One iteration of Algorithm 1: returns (x_i, y_i) from (y_{i-1}, x_{i-1})."""
+    y = _f64(y)
+    xprev = _f64(xprev)
+    b = _f64(b)
+    xo = np.zeros_like(y)
+    yo = np.zeros_like(y)
+    _load().orc_step(C.byref(geom(g)), s, p, P, eta, alpha, lam, tv_iters, amom, _dp(y), _dp(xprev),
+                     _dp(b), _dp(xo), _dp(yo))
+    return xo, yo
+
+
+def step_vjp(g, s: int, p: int, P: int, eta: float, alpha: float, lam: float, tv_iters: int,
+             amom: float, y, b, xbar, ybar):
+    """VJP of ``step``: (dJ/dy_{i-1}, dJ/dx_{i-1}, dJ/dlambda)."""
+    y = _f64(y)
+    b = _f64(b)
+    xbar = _f64(xbar)
+    ybar = _f64(ybar)
+    yb = np.zeros_like(y)
+    xpb = np.zeros_like(y)
+    lb = C.c_double(0.0)
+    _load().orc_step_vjp(C.byref(geom(g)), s, p, P, eta, alpha, lam, tv_iters, amom, _dp(y), _dp(b),
+                         _dp(xbar), _dp(ybar), _dp(yb), _dp(xpb), C.byref(lb))
+    return yb, xpb, float(lb.value)

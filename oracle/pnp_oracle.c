@@ -442,3 +442,162 @@ double orc_sample_count(const orc_geom *g, int s, int p, int P)
     }
     return count;
 }
+
+/* ---------------- differentiable form (reverse mode, FP64) ----------------
+ * Vector-Jacobian products for unrolling Algorithm 1 (Sec. 2 notes that the
+ * sketched iterations can be unrolled and trained end to end).               */
+
+/* FGP with every pre-projection point a_k = r_k + L^T(z - lambda L r_k)/(8 lambda)
+ * kept (a: iters x 2 planes), and p_N (pn: 2 planes).  Same recurrence as
+ * orc_fgp. */
+static void fgp_record(int m, const double *z, double lambda, int iters, double *a, double *pn)
+{
+    size_t N = (size_t)m * m;
+    double *pp = calloc(2 * N, sizeof(double)), *r = calloc(2 * N, sizeof(double));
+    double *w = malloc(sizeof(double) * N), *gp = malloc(sizeof(double) * N), *gq = malloc(sizeof(double) * N);
+    double t = 1.0;
+    for (int k = 1; k <= iters; ++k) {
+        double *ak = a + (size_t)(k - 1) * 2 * N;
+        tv_L(m, r, r + N, w);
+        for (size_t i = 0; i < N; ++i) w[i] = z[i] - lambda * w[i];
+        tv_LT(m, w, gp, gq);
+        double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        double mom = (t - 1.0) / tn;
+        for (size_t i = 0; i < N; ++i) {
+            double a1 = r[i] + gp[i] / (8.0 * lambda);
+            double a2 = r[N + i] + gq[i] / (8.0 * lambda);
+            ak[i] = a1;
+            ak[N + i] = a2;
+            double nrm = sqrt(a1 * a1 + a2 * a2);
+            double den = nrm > 1.0 ? nrm : 1.0;
+            double p1 = a1 / den, p2 = a2 / den;
+            r[i] = p1 + mom * (p1 - pp[i]);
+            r[N + i] = p2 + mom * (p2 - pp[N + i]);
+            pp[i] = p1;
+            pp[N + i] = p2;
+        }
+        t = tn;
+    }
+    memcpy(pn, pp, sizeof(double) * 2 * N);
+    free(pp); free(r); free(w); free(gp); free(gq);
+}
+
+/* Reverse sweep of FGP: given xbar = dJ/dx for x = FGP_lambda^iters(z), returns
+ * zbar = dJ/dz and dJ/dlambda.  With r_{k+1} = (1+m_k) p_k - m_k p_{k-1},
+ * p_k = Proj(a_k), a_k = r_k + L^T z/(8 lambda) - L^T L r_k / 8, x = z - lambda L p_N:
+ *   pbar_N = -lambda L^T xbar,  lambar = -<xbar, L p_N>;  for k = N..1:
+ *   pbar_k += (1+m_k) rbar_{k+1};  carry -m_k rbar_{k+1} to pbar_{k-1};
+ *   abar_k = J_Proj(a_k)^T pbar_k;  rbar_k = abar_k - L^T L abar_k / 8;
+ *   zbar += L abar_k / (8 lambda);  lambar -= <L abar_k, z> / (8 lambda^2).
+ * J_Proj at a with |a| > 1 is (I - a a^T/|a|^2)/|a|, the identity otherwise.   */
+void orc_fgp_vjp(int m, const double *z, double lambda, int iters, const double *xbar,
+                 double *zbar, double *lambar)
+{
+    size_t N = (size_t)m * m;
+    memcpy(zbar, xbar, sizeof(double) * N);
+    *lambar = 0.0;
+    if (lambda <= 0.0 || iters <= 0) return;
+    double *a = malloc(sizeof(double) * 2 * N * (size_t)iters), *pn = malloc(sizeof(double) * 2 * N);
+    double *pbar = calloc(2 * N, sizeof(double)), *carry = calloc(2 * N, sizeof(double));
+    double *rbar = calloc(2 * N, sizeof(double)), *abar = malloc(sizeof(double) * 2 * N);
+    double *w = malloc(sizeof(double) * N), *u1 = malloc(sizeof(double) * N), *u2 = malloc(sizeof(double) * N);
+    double *mom = malloc(sizeof(double) * (size_t)iters);
+    fgp_record(m, z, lambda, iters, a, pn);
+    double t = 1.0;
+    for (int k = 0; k < iters; ++k) {
+        double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        mom[k] = (t - 1.0) / tn;
+        t = tn;
+    }
+    /* x = z - lambda L p_N */
+    tv_L(m, pn, pn + N, w);
+    double acc = 0.0;
+    for (size_t i = 0; i < N; ++i) acc += xbar[i] * w[i];
+    *lambar = -acc;
+    tv_LT(m, xbar, u1, u2);
+    for (size_t i = 0; i < N; ++i) {
+        carry[i] = -lambda * u1[i];
+        carry[N + i] = -lambda * u2[i];
+    }
+    for (int k = iters; k >= 1; --k) {
+        const double *ak = a + (size_t)(k - 1) * 2 * N;
+        double mk = mom[k - 1];
+        for (size_t i = 0; i < 2 * N; ++i) {
+            pbar[i] = carry[i] + (1.0 + mk) * rbar[i];
+            carry[i] = -mk * rbar[i];
+        }
+        for (size_t i = 0; i < N; ++i) {
+            double a1 = ak[i], a2 = ak[N + i];
+            double nrm = sqrt(a1 * a1 + a2 * a2);
+            if (nrm > 1.0) {
+                double h1 = a1 / nrm, h2 = a2 / nrm;
+                double d = h1 * pbar[i] + h2 * pbar[N + i];
+                abar[i] = (pbar[i] - h1 * d) / nrm;
+                abar[N + i] = (pbar[N + i] - h2 * d) / nrm;
+            } else {
+                abar[i] = pbar[i];
+                abar[N + i] = pbar[N + i];
+            }
+        }
+        tv_L(m, abar, abar + N, w);                    /* w = L abar */
+        double dz = 0.0;
+        for (size_t i = 0; i < N; ++i) {
+            zbar[i] += w[i] / (8.0 * lambda);
+            dz += w[i] * z[i];
+        }
+        *lambar -= dz / (8.0 * lambda * lambda);
+        tv_LT(m, w, u1, u2);                           /* L^T L abar */
+        for (size_t i = 0; i < N; ++i) {
+            rbar[i] = abar[i] - u1[i] / 8.0;
+            rbar[N + i] = abar[N + i] - u2[i] / 8.0;
+        }
+    }
+    free(a); free(pn); free(pbar); free(carry); free(rbar); free(abar); free(w); free(u1); free(u2); free(mom);
+}
+
+/* One iteration of Algorithm 1 as a function of (y_{i-1}, x_{i-1}, lambda):
+ *   z = y - eta c S^T A_s^{(p)T}(A_s^{(p)} S y - b^{(p)});  d = FGP(z);
+ *   x = (1-alpha) z + alpha d;  y_new = x + a (x - xprev).                    */
+void orc_step(const orc_geom *g, int s, int p, int P, double eta, double alpha, double lambda,
+              int tv_iters, double amom, const double *y, const double *xprev, const double *b,
+              double *xout, double *yout)
+{
+    size_t N = (size_t)g->n * g->n;
+    double *gr = malloc(sizeof(double) * N), *z = malloc(sizeof(double) * N), *d = malloc(sizeof(double) * N);
+    orc_grad(g, s, y, b, gr, p, P);
+    for (size_t i = 0; i < N; ++i) z[i] = y[i] - eta * gr[i];
+    orc_fgp(g->n, z, lambda, tv_iters, d);
+    for (size_t i = 0; i < N; ++i) {
+        double x = (1.0 - alpha) * z[i] + alpha * d[i];
+        xout[i] = x;
+        yout[i] = x + amom * (x - xprev[i]);
+    }
+    free(gr); free(z); free(d);
+}
+
+/* VJP of orc_step: given xbar, ybar (gradients of the two outputs), returns
+ * ybar_in = dJ/dy_{i-1}, xpbar = dJ/dx_{i-1} and dJ/dlambda.  The data step's
+ * Jacobian I - eta c S^T A_s^T A_s S is symmetric, so ybar_in is that matrix
+ * applied to zbar. */
+void orc_step_vjp(const orc_geom *g, int s, int p, int P, double eta, double alpha, double lambda,
+                  int tv_iters, double amom, const double *y, const double *b, const double *xbar,
+                  const double *ybar, double *ybar_in, double *xpbar, double *lambar)
+{
+    size_t N = (size_t)g->n * g->n;
+    double *gr = malloc(sizeof(double) * N), *z = malloc(sizeof(double) * N);
+    double *xt = malloc(sizeof(double) * N), *dz = malloc(sizeof(double) * N), *zbar = malloc(sizeof(double) * N);
+    double *zero = calloc((size_t)g->n_views * g->n_det, sizeof(double));
+    orc_grad(g, s, y, b, gr, p, P);
+    for (size_t i = 0; i < N; ++i) z[i] = y[i] - eta * gr[i];
+    for (size_t i = 0; i < N; ++i) {
+        xt[i] = xbar[i] + (1.0 + amom) * ybar[i];
+        xpbar[i] = -amom * ybar[i];
+    }
+    double lb = 0.0;
+    orc_fgp_vjp(g->n, z, lambda, tv_iters, xt, dz, &lb);
+    *lambar = alpha * lb;
+    for (size_t i = 0; i < N; ++i) zbar[i] = (1.0 - alpha) * xt[i] + alpha * dz[i];
+    orc_grad(g, s, zbar, zero, gr, p, P);
+    for (size_t i = 0; i < N; ++i) ybar_in[i] = zbar[i] - eta * gr[i];
+    free(gr); free(z); free(xt); free(dz); free(zbar); free(zero);
+}

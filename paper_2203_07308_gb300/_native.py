@@ -89,6 +89,13 @@ def load(path: Optional[str] = None):
             "pnp_objective": [gp, vp, vp, vp, dp, vp, vp],
             "pnp_sample_count": [gp, i32, i32, i32, dp, vp, vp],
             "pnp_full_grad_noalloc": [gp, vp, vp, vp, vp],
+            "pnp_tv_vjp_workspace_size": [i32, i32, i32, C.POINTER(sz)],
+            "pnp_tv_vjp": [vp, vp, vp, dp, i32, i32, C.c_float, i32, vp, sz, vp],
+            "pnp_vjp_workspace_size": [gp, i32, C.POINTER(sz)],
+            "pnp_unrolled_step": [gp, i32, i32, i32, C.c_double, C.POINTER(RunParams), C.c_float,
+                                  vp, vp, vp, vp, vp, vp, vp],
+            "pnp_unrolled_step_vjp": [gp, i32, i32, i32, C.c_double, C.POINTER(RunParams), C.c_float,
+                                      vp, vp, vp, vp, vp, vp, dp, vp, vp, sz, vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -322,3 +329,53 @@ class Plan:
 
     def sample_count(self, factor=1, subset=0, n_subsets=1, stream=None):
         return sample_count(self.g, factor, subset, n_subsets, self.ws, stream)
+
+
+# ---------------------------------------------------------------- differentiable form
+def tv_vjp_workspace_size(n: int, batch: int, iters: int) -> int:
+    v = C.c_size_t(0)
+    _check(load().pnp_tv_vjp_workspace_size(n, batch, iters, C.byref(v)))
+    return int(v.value)
+
+
+def tv_vjp(z, xbar, zbar, n, batch, lam, iters, ws, stream=None):
+    """pnp_tv_vjp: zbar = (dD/dz)^T xbar; returns dJ/dlambda per instance."""
+    lb = np.zeros(batch)
+    p, nbytes = _ws(ws) if ws is not None else (None, 0)
+    img = batch * n * n
+    _check(load().pnp_tv_vjp(_ptr(z, img, "z"), _ptr(xbar, img, "xbar"), _ptr(zbar, img, "zbar"),
+                             lb.ctypes.data_as(C.POINTER(C.c_double)), n, batch, float(lam), int(iters),
+                             p, nbytes, _stream(stream)))
+    return lb
+
+
+def vjp_workspace_size(g, tv_iters: int) -> int:
+    v = C.c_size_t(0)
+    _check(load().pnp_vjp_workspace_size(C.byref(geom(g)), int(tv_iters), C.byref(v)))
+    return int(v.value)
+
+
+def unrolled_step(g, factor, subset, n_subsets, eta, alpha, lam, tv_iters, amom, y, xprev, b, xout, yout,
+                  ws, stream=None):
+    img = g.batch * g.n * g.n
+    prm = RunParams(float(alpha), float(lam), int(tv_iters), 0)
+    _check(load().pnp_unrolled_step(C.byref(geom(g)), factor, subset, n_subsets, float(eta), C.byref(prm),
+                                    float(amom), _ptr(y, img, "y"), _ptr(xprev, img, "xprev"),
+                                    _ptr(b, g.batch * g.n_views * g.n_det, "b"), _ptr(xout, img, "xout"),
+                                    _ptr(yout, img, "yout"), _ws(ws)[0], _stream(stream)))
+
+
+def unrolled_step_vjp(g, factor, subset, n_subsets, eta, alpha, lam, tv_iters, amom, y, b, xbar, ybar,
+                      ybar_in, xpbar, ws, vjp_ws, stream=None):
+    """Returns dJ/dlambda per instance; fills ybar_in and xpbar."""
+    img = g.batch * g.n * g.n
+    prm = RunParams(float(alpha), float(lam), int(tv_iters), 0)
+    lb = np.zeros(g.batch)
+    vp, vbytes = _ws(vjp_ws)
+    _check(load().pnp_unrolled_step_vjp(C.byref(geom(g)), factor, subset, n_subsets, float(eta), C.byref(prm),
+                                        float(amom), _ptr(y, img, "y"),
+                                        _ptr(b, g.batch * g.n_views * g.n_det, "b"), _ptr(xbar, img, "xbar"),
+                                        _ptr(ybar, img, "ybar"), _ptr(ybar_in, img, "ybar_in"),
+                                        _ptr(xpbar, img, "xpbar"), lb.ctypes.data_as(C.POINTER(C.c_double)),
+                                        _ws(ws)[0], vp, vbytes, _stream(stream)))
+    return lb

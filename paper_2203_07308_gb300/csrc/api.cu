@@ -601,4 +601,172 @@ int pnp_sample_count(const pnp_geom* g, int factor, int subset, int n_subsets, d
     return PNP_OK;
 }
 
+
+// ------------------------------------------------------------------ differentiable form
+int pnp_tv_vjp_workspace_size(int n, int batch, int iters, size_t* bytes)
+{
+    t_err.clear();
+    if (n < 2 || batch < 1 || iters < 0 || iters > 10000 || (double)n * n * batch * (2.0 * iters + 12) > 4.0e10)
+        return fail(PNP_EINVAL, "bad n, batch or iters");
+    if (!bytes) return fail(PNP_EINVAL, "bytes pointer is NULL");
+    const size_t fl = tv_vjp_workspace_floats(n, batch, iters) * sizeof(float);
+    *bytes = align_up(fl) + ((size_t)batch * tv_vjp_partials(n) + (size_t)batch) * sizeof(double);
+    return PNP_OK;
+}
+
+namespace {
+// FGP VJP plus the per-instance dJ/dlambda reduction (into dres[batch]).
+int tv_vjp_core(const float* d_z, const float* d_xbar, float* d_zbar, int n, int batch, float lambda,
+                int iters, char* vws, double* dres, cudaStream_t st)
+{
+    const size_t fl = tv_vjp_workspace_floats(n, batch, iters) * sizeof(float);
+    double* part = (double*)(vws + align_up(fl));
+    const int nparts = (int)tv_vjp_partials(n);
+    PNP_CUDA(launch_tv_vjp(d_z, d_xbar, d_zbar, part, n, batch, lambda, iters, (float*)vws, st));
+    PNP_CUDA(launch_reduce_final(part, nparts, batch, dres, 1, 0, st));
+    return PNP_OK;
+}
+}  // namespace
+
+int pnp_tv_vjp(const float* d_z, const float* d_xbar, float* d_zbar, double* h_lambar, int n, int batch,
+               float lambda, int iters, void* d_ws, size_t ws_bytes, void* stream)
+{
+    t_err.clear();
+    size_t need = 0;
+    if (int e = pnp_tv_vjp_workspace_size(n, batch, iters, &need)) return e;
+    if (!d_z || !d_xbar || !d_zbar) return fail(PNP_EINVAL, "z, xbar and zbar are required");
+    if (iters > 0 && !(lambda > 0.0f && std::isfinite(lambda)))
+        return fail(PNP_EINVAL, "lambda must be > 0 to differentiate FGP");
+    cudaStream_t st = S(stream);
+    const size_t img = (size_t)batch * n * n;
+    if (iters == 0) {
+        PNP_CUDA(launch_copy(d_xbar, d_zbar, img, st));
+        if (h_lambar) for (int b = 0; b < batch; ++b) h_lambar[b] = 0.0;
+        return PNP_OK;
+    }
+    if (!d_ws || ws_bytes < need) return fail(PNP_EINVAL, "VJP workspace needs %zu bytes", need);
+    char* vws = (char*)d_ws;
+    double* dres = (double*)(vws + need) - batch;
+    if (int e = tv_vjp_core(d_z, d_xbar, d_zbar, n, batch, lambda, iters, vws, dres, st)) return e;
+    if (h_lambar) {
+        PNP_CUDA(cudaMemcpyAsync(h_lambar, dres, sizeof(double) * batch, cudaMemcpyDeviceToHost, st));
+        PNP_CUDA(cudaStreamSynchronize(st));
+    }
+    return PNP_OK;
+}
+
+int pnp_vjp_workspace_size(const pnp_geom* g, int tv_iters, size_t* bytes)
+{
+    t_err.clear();
+    if (int e = validate_geom(g)) return e;
+    size_t tvb = 0;
+    if (int e = pnp_tv_vjp_workspace_size(g->n, g->batch, tv_iters, &tvb)) return e;
+    if (!bytes) return fail(PNP_EINVAL, "bytes pointer is NULL");
+    *bytes = align_up(tvb) + 3 * align_up((size_t)g->batch * g->n * g->n * sizeof(float));
+    return PNP_OK;
+}
+
+namespace {
+int check_step(const pnp_geom* g, int factor, int subset, int n_subsets, double eta,
+               const pnp_run_params* pr, Layout* L, int* li)
+{
+    if (int e = validate_geom(g)) return e;
+    *L = make_layout(*g);
+    if (int e = check_level(*g, factor, *L, li)) return e;
+    if (int e = check_subset(*g, subset, n_subsets)) return e;
+    if (!pr) return fail(PNP_EINVAL, "params are required");
+    if (!(std::isfinite(eta) && eta >= 0.0)) return fail(PNP_EINVAL, "eta invalid");
+    if (!(pr->alpha > 0.0f && pr->alpha <= 1.0f)) return fail(PNP_EINVAL, "alpha must be in (0, 1]");
+    if (!(pr->lambda >= 0.0f) || !std::isfinite(pr->lambda)) return fail(PNP_EINVAL, "lambda must be >= 0");
+    if (pr->tv_iters < 0 || pr->tv_iters > 10000) return fail(PNP_EINVAL, "tv_iters outside [0, 10000]");
+    return PNP_OK;
+}
+}  // namespace
+
+int pnp_unrolled_step(const pnp_geom* g, int factor, int subset, int n_subsets, double eta,
+                      const pnp_run_params* params, float amom, const float* d_y, const float* d_xprev,
+                      const float* d_b, float* d_xout, float* d_yout, void* d_ws, void* stream)
+{
+    t_err.clear();
+    Layout L;
+    int li;
+    if (int e = check_step(g, factor, subset, n_subsets, eta, params, &L, &li)) return e;
+    if (!d_y || !d_xprev || !d_b || !d_xout || !d_yout) return fail(PNP_EINVAL, "y, xprev, b, xout, yout required");
+    if (d_xout == d_y || d_yout == d_y || d_xout == d_yout || d_xout == d_xprev)
+        return fail(PNP_EINVAL, "outputs must not alias the inputs or each other");
+    if (int e = check_ws(*g, d_ws)) return e;
+    char* ws = (char*)d_ws;
+    cudaStream_t st = S(stream);
+    const size_t img = (size_t)g->batch * g->n * g->n;
+    float* z = (float*)(ws + L.off_z);
+    float* tvb = (float*)(ws + L.off_tv);
+    if (int e = grad_into(*g, L, li, ws, d_y, d_b, subset, n_subsets, kBackStep, (float)eta, z, st)) return e;
+    PNP_CUDA(launch_copy(d_xprev, d_xout, img, st));
+    const pnp_run_params& pr = *params;
+    if (pr.tv_iters > 0 && pr.lambda > 0.0f)
+        PNP_CUDA(launch_tv_tiled(z, g->n, g->batch, pr.lambda, pr.tv_iters, pr.alpha, amom, d_xout, d_yout,
+                                 nullptr, nullptr, tvb, tvb + 4 * img, st));
+    else
+        PNP_CUDA(launch_tv_final(z, nullptr, 0, g->n, g->batch, pr.lambda, pr.alpha, amom, d_xout, d_yout,
+                                 nullptr, nullptr, st));
+    return PNP_OK;
+}
+
+int pnp_unrolled_step_vjp(const pnp_geom* g, int factor, int subset, int n_subsets, double eta,
+                          const pnp_run_params* params, float amom, const float* d_y, const float* d_b,
+                          const float* d_xbar, const float* d_ybar, float* d_ybar_in, float* d_xpbar,
+                          double* h_lambar, void* d_ws, void* d_vjp_ws, size_t vjp_ws_bytes, void* stream)
+{
+    t_err.clear();
+    Layout L;
+    int li;
+    if (int e = check_step(g, factor, subset, n_subsets, eta, params, &L, &li)) return e;
+    if (!d_y || !d_b || !d_xbar || !d_ybar || !d_ybar_in || !d_xpbar)
+        return fail(PNP_EINVAL, "y, b, xbar, ybar, ybar_in, xpbar required");
+    if (d_ybar_in == d_xpbar) return fail(PNP_EINVAL, "outputs must not alias");
+    const pnp_run_params& pr = *params;
+    const bool do_tv = pr.tv_iters > 0 && pr.lambda > 0.0f;
+    size_t need = 0;
+    if (int e = pnp_vjp_workspace_size(g, do_tv ? pr.tv_iters : 0, &need)) return e;
+    if (!d_vjp_ws || vjp_ws_bytes < need) return fail(PNP_EINVAL, "VJP workspace needs %zu bytes", need);
+    if (int e = check_ws(*g, d_ws)) return e;
+    char* ws = (char*)d_ws;
+    char* vws = (char*)d_vjp_ws;
+    cudaStream_t st = S(stream);
+    const size_t img = (size_t)g->batch * g->n * g->n;
+    size_t tvb_bytes = 0;
+    pnp_tv_vjp_workspace_size(g->n, g->batch, do_tv ? pr.tv_iters : 0, &tvb_bytes);
+    float* X = (float*)(vws + align_up(tvb_bytes));
+    float* DZ = (float*)((char*)X + align_up(img * sizeof(float)));
+    float* ZB = (float*)((char*)DZ + align_up(img * sizeof(float)));
+    double* dres = (double*)(vws + tvb_bytes) - g->batch;
+    float* z = (float*)(ws + L.off_z);
+    // forward recomputation of z (per-iteration checkpoint: only y is kept)
+    if (int e = grad_into(*g, L, li, ws, d_y, d_b, subset, n_subsets, kBackStep, (float)eta, z, st)) return e;
+    // through y_i = (1 + a) x_i - a x_{i-1}
+    PNP_CUDA(launch_axpby(d_xbar, 1.0f, d_ybar, 1.0f + amom, X, (long)img, st));
+    PNP_CUDA(launch_axpby(d_ybar, -amom, nullptr, 0.0f, d_xpbar, (long)img, st));
+    // through x_i = (1 - alpha) z + alpha D(z)
+    if (do_tv) {
+        if (int e = tv_vjp_core(z, X, DZ, g->n, g->batch, pr.lambda, pr.tv_iters, vws, dres, st)) return e;
+    } else {
+        PNP_CUDA(launch_copy(X, DZ, img, st));
+    }
+    PNP_CUDA(launch_axpby(X, 1.0f - pr.alpha, DZ, pr.alpha, ZB, (long)img, st));
+    // through z = y - eta c S^T A_s^T (A_s S y - b): symmetric Jacobian
+    if (int e = grad_into(*g, L, li, ws, ZB, nullptr, subset, n_subsets, kBackStep, (float)eta, d_ybar_in, st))
+        return e;
+    if (h_lambar) {
+        if (do_tv) {
+            std::vector<double> lb((size_t)g->batch);
+            PNP_CUDA(cudaMemcpyAsync(lb.data(), dres, sizeof(double) * g->batch, cudaMemcpyDeviceToHost, st));
+            PNP_CUDA(cudaStreamSynchronize(st));
+            for (int b = 0; b < g->batch; ++b) h_lambar[b] = pr.alpha * lb[b];
+        } else {
+            for (int b = 0; b < g->batch; ++b) h_lambar[b] = 0.0;
+        }
+    }
+    return PNP_OK;
+}
+
 }  // extern "C"

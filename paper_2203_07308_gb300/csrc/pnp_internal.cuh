@@ -117,6 +117,15 @@ cudaError_t launch_tv_tiled(const float* z, int n, int batch, float lambda, int 
                             float amom, float* xprev, float* y, const float* xtrue, double* mse_part,
                             float* state_a, float* state_b, cudaStream_t st);
 
+// Reverse mode (vjp.cu) ----------------------------------------------------------
+size_t tv_vjp_workspace_floats(int n, int batch, int iters);
+size_t tv_vjp_partials(int n);
+// zbar = d<xbar, FGP(z)>/dz; partials[batch][tv_vjp_partials] accumulate dJ/dlambda.
+cudaError_t launch_tv_vjp(const float* z, const float* xbar, float* zbar, double* partials, int n,
+                          int batch, float lambda, int iters, float* ws, cudaStream_t st);
+cudaError_t launch_axpby(const float* a, float c1, const float* b, float c2, float* out, long count,
+                         cudaStream_t st);
+
 // Reductions -------------------------------------------------------------------
 enum RedMode { kRedDot = 0, kRedDiffSq = 1, kRedSq = 2, kRedTv = 3 };
 // partials[inst][kRedBlocks] for `count` elements per instance (stride `stride`).

@@ -1,0 +1,181 @@
+"""Differentiable form on the GPU (through the C ABI and torch.autograd):
+FGP reverse sweep, one unrolled iteration and its VJP, and the gradient of an
+unrolled multi-stage run w.r.t. the input image x0 and the TV weight lambda,
+against the FP64 oracle's reverse mode and against central finite differences
+(h = 1e-3) of the GPU forward map.
+
+Tolerances: relative 1e-4 for reverse-mode quantities (FP32 sums through up to
+20 FGP iterations and several PnP iterations), 2e-2 for the FP32 finite
+differences (step 1e-3 on values of order 1)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2203_07308_gb300 as pnp
+from paper_2203_07308_gb300 import _native, build, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_VJP = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    pnp.load()
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("n,batch,lam,iters", [(32, 2, 0.05, 20), (45, 1, 0.1, 9)])
+def test_tv_vjp_parity(n, batch, lam, iters):
+    import torch
+    rng = np.random.default_rng(n)
+    z = f32(rng.random((batch, n, n)))
+    xb = f32(rng.standard_normal((batch, n, n)))
+    ws = torch.empty(_native.tv_vjp_workspace_size(n, batch, iters), dtype=torch.uint8, device="cuda")
+    zb = torch.empty(batch, n, n, device="cuda")
+    lb = _native.tv_vjp(dev(z), dev(xb), zb, n, batch, lam, iters, ws)
+    got = host(zb)
+    for i in range(batch):
+        rz, rl = oracle.fgp_vjp(z[i], lam, iters, xb[i])
+        assert rel(got[i], rz) < TOL_VJP, rel(got[i], rz)
+        assert abs(lb[i] - rl) < TOL_VJP * max(1.0, abs(rl))
+
+
+@pytest.mark.parametrize("s,P,p,alpha,amom", [(1, 1, 0, 1.0, 0.0), (2, 3, 2, 0.8, 0.3)])
+def test_unrolled_step_and_vjp_parity(s, P, p, alpha, amom):
+    import torch
+    g = synth.make_geometry(48, 30, 64, batch=2)
+    plan = pnp.Plan(g)
+    rng = np.random.default_rng(s * 10 + p)
+    b = f32(rng.standard_normal((2, g.n_views, g.n_det)) * 5)
+    y = f32(rng.random((2, 48, 48)))
+    xp = f32(rng.random((2, 48, 48)))
+    xb = f32(rng.standard_normal((2, 48, 48)))
+    yb = f32(rng.standard_normal((2, 48, 48)))
+    eta, lam, it = 2e-4, 0.05, 20
+    xo, yo = torch.empty(2, 48, 48, device="cuda"), torch.empty(2, 48, 48, device="cuda")
+    _native.unrolled_step(g, s, p, P, eta, alpha, lam, it, amom, dev(y), dev(xp), dev(b), xo, yo, plan.ws)
+    vws = torch.empty(_native.vjp_workspace_size(g, it), dtype=torch.uint8, device="cuda")
+    ybi, xpb = torch.empty(2, 48, 48, device="cuda"), torch.empty(2, 48, 48, device="cuda")
+    lb = _native.unrolled_step_vjp(g, s, p, P, eta, alpha, lam, it, amom, dev(y), dev(b), dev(xb), dev(yb),
+                                   ybi, xpb, plan.ws, vws)
+    for i in range(2):
+        rx, ry = oracle.step(g, s, p, P, eta, alpha, lam, it, amom, y[i], xp[i], b[i])
+        assert rel(host(xo)[i], rx) < 1e-5 and rel(host(yo)[i], ry) < 1e-5
+        r_yb, r_xpb, r_lb = oracle.step_vjp(g, s, p, P, eta, alpha, lam, it, amom, y[i], b[i], xb[i], yb[i])
+        assert rel(host(ybi)[i], r_yb) < TOL_VJP, rel(host(ybi)[i], r_yb)
+        assert rel(host(xpb)[i], r_xpb) < 1e-6
+        assert abs(lb[i] - r_lb) < TOL_VJP * max(1.0, abs(r_lb)), (lb[i], r_lb)
+
+
+def _oracle_unrolled(g, stages, eta, seq, b, x0, xt, lam, alpha, tv_iters):
+    ys, plan_ = [x0], []
+    y, x = x0.copy(), x0.copy()
+    i = 0
+    for k, st in enumerate(stages):
+        for _ in range(st.iters):
+            i += 1
+            p = int(seq[i - 1]) if st.n_subsets > 1 else 0
+            a = (i - 1) / (i + 3)
+            x, y = oracle.step(g, st.factor, p, st.n_subsets, eta[k], alpha, lam, tv_iters, a, y, x, b)
+            ys.append(y)
+            plan_.append((st.factor, p, st.n_subsets, eta[k], a))
+    xb, yb, gl = x - xt, np.zeros_like(x), 0.0
+    for t in range(len(plan_), 0, -1):
+        s, p, P, e, a = plan_[t - 1]
+        yb_in, xpb, lb = oracle.step_vjp(g, s, p, P, e, alpha, lam, tv_iters, a, ys[t - 1], b, xb, yb)
+        gl += lb
+        xb, yb = xpb, yb_in
+    return 0.5 * np.sum((x - xt) ** 2), xb + yb, gl
+
+
+def test_unrolled_autograd_matches_oracle_and_fd():
+    import torch
+    from paper_2203_07308_gb300.autograd import unrolled_pnp
+    g = synth.make_geometry(48, 36, 64, batch=2)
+    plan = pnp.Plan(g)
+    rng = np.random.default_rng(5)
+    xt = np.stack([f32(synth.ellipse_phantom(48, 40 + i, (5, 7))) for i in range(2)])
+    b = f32(np.stack([oracle.project(g, 1, x) for x in xt]) + 0.2 * rng.standard_normal((2, 36, 64)))
+    stages = [synth.Stage(2, 2, 3), synth.Stage(1, 2, 2)]
+    eta = [0.9 / oracle.power_iter(g, s.factor, 60, 1e-8)[0] for s in stages]
+    seq = synth.schedule_sequence(stages, 11)
+    x0 = f32(rng.random((2, 48, 48)) * 0.2)
+    lam0, alpha, tvit = 0.03, 0.9, 12
+    X0 = dev(x0).requires_grad_(True)
+    lam = torch.tensor(lam0, dtype=torch.float64, requires_grad=True)
+    xT = unrolled_pnp(plan, stages, eta, seq, dev(b), X0, lam, alpha=alpha, tv_iters=tvit)
+    loss = 0.5 * ((xT - dev(xt)) ** 2).sum()
+    loss.backward()
+    gx = host(X0.grad)
+    gl = float(lam.grad)
+    ref_gl = 0.0
+    for i in range(2):
+        _, rgx, rgl = _oracle_unrolled(g, stages, eta, seq, b[i], x0[i], xt[i], lam0, alpha, tvit)
+        assert rel(gx[i], rgx) < TOL_VJP, rel(gx[i], rgx)
+        ref_gl += rgl
+    assert abs(gl - ref_gl) < TOL_VJP * max(1.0, abs(ref_gl)), (gl, ref_gl)
+    # central finite differences of the GPU forward map (float32), h = 1e-3
+    def F(x0v, lv):
+        with torch.no_grad():
+            xx = unrolled_pnp(plan, stages, eta, seq, dev(b), dev(x0v), torch.tensor(lv, dtype=torch.float64),
+                              alpha=alpha, tv_iters=tvit)
+            return float(0.5 * ((xx.double() - dev(xt).double()) ** 2).sum())
+    d = rng.standard_normal(x0.shape)
+    d /= np.linalg.norm(d)
+    h = 1e-3
+    fdx = (F(x0 + h * d, lam0) - F(x0 - h * d, lam0)) / (2 * h)
+    assert abs(fdx - np.vdot(gx, d)) < 2e-2 * max(1.0, abs(fdx))
+    fdl = (F(x0, lam0 + h) - F(x0, lam0 - h)) / (2 * h)
+    assert abs(fdl - gl) < 2e-2 * max(1.0, abs(fdl)), (fdl, gl)
+
+
+def test_differentiable_workload_full_size():
+    """8 x 256x256, 360 views x 512 bins, 10 unrolled 2x-sketched iterations:
+    the gradient w.r.t. x0 of two instances against the oracle's reverse mode."""
+    import torch
+    from paper_2203_07308_gb300.autograd import unrolled_pnp
+    wl = synth.workloads()["c4_256x8"]
+    g = wl.geom
+    plan = pnp.Plan(g)
+    xt = f32(synth.phantom_batch(wl))
+    rng = np.random.default_rng(4)
+    d_xt = dev(xt)
+    d_b = torch.empty(g.batch, g.n_views, g.n_det, device="cuda")
+    plan.project(1, d_xt, d_b)
+    d_b += 0.01 * float(d_b.abs().max()) * dev(rng.standard_normal((g.batch, g.n_views, g.n_det)))
+    b = host(d_b)
+    eta = [1.0 / plan.power_iter(2, 60, 1e-7)[0]]
+    stages = wl.stages
+    seq = synth.schedule_sequence(stages, 3)
+    X0 = torch.zeros(g.batch, g.n, g.n, device="cuda", requires_grad=True)
+    lam = torch.tensor(wl.tv_lambda, dtype=torch.float64, requires_grad=True)
+    xT = unrolled_pnp(plan, stages, eta, seq, d_b, X0, lam, alpha=wl.alpha, tv_iters=wl.tv_iters)
+    (0.5 * ((xT - d_xt) ** 2).sum()).backward()
+    gx = host(X0.grad)
+    for i in (0, 5):
+        _, rgx, _ = _oracle_unrolled(g, stages, eta, seq, b[i], np.zeros((g.n, g.n)), xt[i], wl.tv_lambda,
+                                     wl.alpha, wl.tv_iters)
+        assert rel(gx[i], rgx) < TOL_VJP, rel(gx[i], rgx)
+    assert np.isfinite(float(lam.grad))

@@ -1,5 +1,5 @@
 """Plants plausible mistakes in a copy of the oracle's C source (on the CPU) and
-checks that the pins in test_oracle_pins.py catch every one of them."""
+checks that the pins in test_oracle_pins.py and test_oracle_vjp.py catch every one."""
 import os
 import subprocess
 import sys
@@ -28,7 +28,7 @@ MUTATIONS = [
      "acc += fine[(long)(cx * s + b) * n + (cy * s + a)];"),
     ("subset scale dropped", "double c = P <= 1 ? 1.0 : (double)P;", "double c = 1.0;"),
     ("fgp dual step", "double a = r[i] + gp[i] / (8.0 * lambda);", "double a = r[i] + gp[i] / (4.0 * lambda);"),
-    ("fgp momentum dropped", "double mom = (t - 1.0) / tn;", "double mom = 0.0;"),
+    ("fgp momentum dropped", "r[i] = pk[i] + mom * (pk[i] - pp[i]);", "r[i] = pk[i];"),
     ("fgp divergence sign", "if (i > 0) v -= p[(i - 1) * m + j];", "if (i > 0) v += p[(i - 1) * m + j];"),
     ("fgp anisotropic projection", "double nrm = sqrt(a * a + c * c);", "double nrm = fabs(a) + fabs(c);"),
     ("pnp momentum index", "double a = momentum ? (double)(i - 1) / (double)(i + 3) : 0.0;",
@@ -37,6 +37,10 @@ MUTATIONS = [
      "double xn = alpha * z[q] + (1.0 - alpha) * dz[q];"),
     ("power iteration unnormalised", "for (size_t i = 0; i < N; ++i) u[i] = w[i] / nw;",
      "for (size_t i = 0; i < N; ++i) u[i] = w[i];"),
+    ("fgp vjp momentum carry", "carry[i] = -mk * rbar[i];", "carry[i] = mk * rbar[i];"),
+    ("fgp vjp projection jacobian", "abar[i] = (pbar[i] - h1 * d) / nrm;", "abar[i] = (pbar[i] + h1 * d) / nrm;"),
+    ("fgp vjp lambda term", "*lambar -= dz / (8.0 * lambda * lambda);", "*lambar += dz / (8.0 * lambda * lambda);"),
+    ("step vjp momentum", "xt[i] = xbar[i] + (1.0 + amom) * ybar[i];", "xt[i] = xbar[i] + amom * ybar[i];"),
 ]
 
 
@@ -51,6 +55,7 @@ def test_pins_catch_planted_mistake(name, orig, mut, tmp_path):
                     str(msrc), "-lm"], check=True)
     env = dict(os.environ, PNP_ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_vjp.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
