@@ -285,6 +285,120 @@ __global__ void __launch_bounds__(512, 2) k_backward(BackArgs a)
     }
 }
 
+// 2 x 2 pixel blocks per thread.  The four pixels share the view set-up and the
+// candidate rays; their union support is the 3 x 3 square around the block
+// centre (radius rho = 1.5 sqrt 2), so a ray's samples that can touch any of
+// them lie within rho of the centre's projection on the ray: at most
+// floor(2 rho / step) + 1 (9 for step 1/2).  Each sample evaluates the two x
+// hats and two y hats once and feeds four products.
+template <int NWIN>
+__global__ void __launch_bounds__(512, 2) k_backward2x2(BackArgs a)
+{
+    const int tx = threadIdx.x, ty = threadIdx.y, g = threadIdx.z, G = blockDim.z;
+    const int nb = (a.ns + 1) / 2;                             // blocks per side
+    const int tiles_x = (nb + kBackTile - 1) / kBackTile;
+    const int bx = (blockIdx.x % tiles_x) * kBackTile + tx;
+    const int by = (blockIdx.x / tiles_x) * kBackTile + ty;
+    const int inst = blockIdx.y;
+    const bool inside = bx < nb && by < nb;
+    __shared__ float4 part[kBackMaxGroups][kBackTile * kBackTile];
+    float t00 = 0.0f, t10 = 0.0f, t01 = 0.0f, t11 = 0.0f;
+    if (inside) {
+        const int ix = 2 * bx, iy = 2 * by;
+        const float half = 0.5f * (float)(a.ns - 1);
+        const float cx = (float)ix + 0.5f - half, cy = (float)iy + 0.5f - half;   // centred, level units
+        const int c0 = a.ns / 2;
+        const float px = (float)(ix - c0) + 2.0f, py = (float)(iy - c0) + 2.0f;   // primed frame
+        const float jc = 0.5f * (float)(a.n_det - 1);
+        const float inv_step = 1.0f / a.step;
+        const float rho = 2.12132034f;                           // 1.5 sqrt(2)
+        const int nwin = NWIN > 0 ? NWIN : (int)floorf(2.0f * rho * inv_step) + 1;
+        const float* __restrict__ res = a.res + (long)inst * a.n_sub * a.n_det;
+        for (int vs = g; vs < a.n_sub; vs += G) {
+            const int v = a.first_view + vs * a.view_step;
+            const float4 vp = __ldg(a.view + v);   // cos b, sin b, dso/s, (dso+ddo)/pitch
+            const float along = cx * vp.x + cy * vp.y;
+            const float lat = cy * vp.x - cx * vp.y;
+            const float inv = __fdividef(1.0f, vp.z - along);
+            const float uj = vp.w * lat * inv + jc;
+            // conservative shadow half-width (bins) of the disc of radius rho
+            const float invp = inv * (1.0f + 2.0f * rho * inv);
+            const float T = (fabsf(lat) + rho) * invp;
+            const float hw = rho * vp.w * fmaf(T, T, 1.0f) * invp * 1.01f + 0.02f;
+            const int jlo = max(0, (int)ceilf(uj - hw));
+            const int jhi = min(a.n_det - 1, (int)floorf(uj + hw));
+            const long base = (long)v * a.n_det;
+            const float* __restrict__ rrow = res + (long)vs * a.n_det;
+            float v00 = 0.0f, v10 = 0.0f, v01 = 0.0f, v11 = 0.0f;
+            for (int j = jlo; j <= jhi; ++j) {
+                const float4 f = __ldg(a.rayf + base + j);
+                const float ax = px - f.x, ay = py - f.y;
+                const float e = ax * f.w - ay * f.z;
+                if (fabsf(e) >= 1.5f * (fabsf(f.z) + fabsf(f.w))) continue;
+                const float tau = fmaf(ax, f.z, ay * f.w);
+                const float k0 = ceilf(fmaf(tau - rho, inv_step, -0.5f));
+                const float t0 = (k0 + 0.5f) * a.step;
+                const float X0 = fmaf(t0, f.z, -ax), Y0 = fmaf(t0, f.w, -ay);
+                const float xa0 = X0 + 0.5f, xb0 = X0 - 0.5f;    // relative to the left / right pixel
+                const float ya0 = Y0 + 0.5f, yb0 = Y0 - 0.5f;    // relative to the lower / upper pixel
+                const float sx = a.step * f.z, sy = a.step * f.w;
+                float w00 = 0.0f, w10 = 0.0f, w01 = 0.0f, w11 = 0.0f;
+                auto sample = [&](float fm) {
+                    const float hxa = fmaxf(1.0f - fabsf(fmaf(fm, sx, xa0)), 0.0f);
+                    const float hxb = fmaxf(1.0f - fabsf(fmaf(fm, sx, xb0)), 0.0f);
+                    const float hya = fmaxf(1.0f - fabsf(fmaf(fm, sy, ya0)), 0.0f);
+                    const float hyb = fmaxf(1.0f - fabsf(fmaf(fm, sy, yb0)), 0.0f);
+                    w00 = fmaf(hxa, hya, w00);
+                    w10 = fmaf(hxb, hya, w10);
+                    w01 = fmaf(hxa, hyb, w01);
+                    w11 = fmaf(hxb, hyb, w11);
+                };
+                if (NWIN > 0) {
+#pragma unroll
+                    for (int m = 0; m < (NWIN > 0 ? NWIN : 1); ++m) sample((float)m);
+                } else {
+                    for (int m = 0; m < nwin; ++m) sample((float)m);
+                }
+                const float r = __ldg(rrow + j);
+                v00 = fmaf(w00, r, v00);
+                v10 = fmaf(w10, r, v10);
+                v01 = fmaf(w01, r, v01);
+                v11 = fmaf(w11, r, v11);
+            }
+            t00 += v00; t10 += v10; t01 += v01; t11 += v11;
+        }
+    }
+    const int slot = ty * kBackTile + tx;
+    part[g][slot] = make_float4(t00, t10, t01, t11);
+    __syncthreads();
+    if (g != 0 || !inside) return;
+    float s00 = 0.0f, s10 = 0.0f, s01 = 0.0f, s11 = 0.0f;
+    for (int q = 0; q < G; ++q) {
+        const float4 pq = part[q][slot];
+        s00 += pq.x; s10 += pq.y; s01 += pq.z; s11 += pq.w;
+    }
+    const float vals[4] = {a.scale * s00, a.scale * s10, a.scale * s01, a.scale * s11};
+    const int s = a.s;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int ix = 2 * bx + (q & 1), iy = 2 * by + (q >> 1);
+        if (ix >= a.ns || iy >= a.ns) continue;
+        if (a.mode == kBackRaw) {
+            a.out[((long)inst * a.ns + iy) * a.ns + ix] = vals[q];
+            continue;
+        }
+        for (int bb = 0; bb < s; ++bb) {
+            const long row = ((long)inst * a.n + (long)iy * s + bb) * a.n + (long)ix * s;
+            for (int aa = 0; aa < s; ++aa) {
+                if (a.mode == kBackGradFine)
+                    a.out[row + aa] = vals[q];
+                else
+                    a.out[row + aa] = __ldg(a.y + row + aa) - a.eta * vals[q];
+            }
+        }
+    }
+}
+
 // Number of view groups: enough threads for one full wave of the GPU
 // (152 SMs x 2048 threads), at most 8 and at most the number of views.
 inline int back_groups(long pixels, int n_sub)
@@ -385,13 +499,14 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t st)
 
 cudaError_t launch_backward(const BackArgs& a, cudaStream_t st)
 {
-    const int G = back_groups((long)a.ns * a.ns * a.batch, a.n_sub);
-    const int tiles = div_up(a.ns, kBackTile) * div_up(a.ns, kBackTile);
+    const int nb = (a.ns + 1) / 2;
+    const int G = back_groups((long)nb * nb * a.batch, a.n_sub);
+    const int tiles = div_up(nb, kBackTile) * div_up(nb, kBackTile);
     dim3 blk(kBackTile, kBackTile, G), grd(tiles, a.batch);
     if (a.step == 0.5f)
-        k_backward<6><<<grd, blk, 0, st>>>(a);
+        k_backward2x2<9><<<grd, blk, 0, st>>>(a);
     else
-        k_backward<0><<<grd, blk, 0, st>>>(a);
+        k_backward2x2<0><<<grd, blk, 0, st>>>(a);
     return counted();
 }
 

@@ -64,6 +64,9 @@ GEOMS = {
     "limited": synth.Geometry(n=48, n_views=30, n_det=140, batch=1, dso=96.0, ddo=80.0,
                               det_pitch=2.3, angle0=0.3, angle_span=math.pi),
     "oneview": synth.make_geometry(32, 1, 48, batch=1),
+    # steps other than half a pixel (generic sample-window paths)
+    "step03": synth.make_geometry(40, 20, 64, batch=2, step=0.3),
+    "step08": synth.make_geometry(36, 24, 60, batch=1, step=0.8),
 }
 
 
