@@ -179,129 +179,35 @@ __global__ void __launch_bounds__(256, 4) k_forward(FwdArgs a)
 }
 
 // ------------------------------------------------------------------ transpose A_s^T
-// Block = 8 x 8 level pixels x G view groups.  Thread (pixel, g) gathers the
-// views g, g+G, g+2G, ... of the subset: for each view, the detector interval
-// that the pixel's hat support (the 2x2 square around its centre) can shadow,
-// then for every bin in it the exact sample range of that ray inside the square
-// (slab test) and the sum of hat(X - ix) hat(Y - iy) over those samples.  The G
-// partial sums are added in a fixed order through shared memory, so the result
-// is deterministic for a given G (G depends only on the problem size).
-constexpr int kBackTile = 8;
-constexpr int kBackMaxGroups = 8;
+// Pixel-driven gather.  Thread (2x2 pixel block, g) gathers the views g, g+G,
+// g+2G, ... of the subset: for each view, the detector interval that the
+// block's hat support can shadow; for every bin in it, a perpendicular-distance
+// test of the ray against the support; for each ray that meets it, the hat
+// products of the block's four pixels summed over the ray's samples near the
+// block.  The G partial sums are added in a fixed order through shared memory,
+// so the result is deterministic for a given G (a function of the problem
+// size).  CTA = 4 x 4 blocks (8 x 8 pixels) x G view groups: small CTAs keep
+// the per-SM load even on 152 SMs.
+constexpr int kBack2Tile = 4;
+constexpr int kBack2MaxGroups = 32;
 
-template <int NWIN>
-__global__ void __launch_bounds__(512, 2) k_backward(BackArgs a)
-{
-    const int tx = threadIdx.x, ty = threadIdx.y, g = threadIdx.z, G = blockDim.z;
-    const int tiles_x = (a.ns + kBackTile - 1) / kBackTile;
-    const int ix = (blockIdx.x % tiles_x) * kBackTile + tx;
-    const int iy = (blockIdx.x / tiles_x) * kBackTile + ty;
-    const int inst = blockIdx.y;
-    const bool inside = ix < a.ns && iy < a.ns;
-    __shared__ float part[kBackMaxGroups][kBackTile * kBackTile];
-    float total = 0.0f;
-    if (inside) {
-        const float half = 0.5f * (float)(a.ns - 1);
-        const float cx = (float)ix - half, cy = (float)iy - half;   // centred, level units
-        const int c0 = a.ns / 2;
-        const float px = (float)(ix - c0) + 1.5f, py = (float)(iy - c0) + 1.5f;   // primed frame
-        const float jc = 0.5f * (float)(a.n_det - 1);
-        const float inv_step = 1.0f / a.step;
-        const float kSqrt2 = 1.41421356f;
-        // samples of one ray within sqrt(2) of the pixel centre: at most
-        // floor(2 sqrt(2) / step) + 1 of them (6 for step 1/2)
-        const int nwin = NWIN > 0 ? NWIN : (int)floorf(2.0f * kSqrt2 * inv_step) + 1;
-        const float* __restrict__ res = a.res + (long)inst * a.n_sub * a.n_det;
-        for (int vs = g; vs < a.n_sub; vs += G) {
-            const int v = a.first_view + vs * a.view_step;
-            const float4 vp = __ldg(a.view + v);   // cos b, sin b, dso/s, (dso+ddo)/pitch
-            const float along = cx * vp.x + cy * vp.y;
-            const float lat = cy * vp.x - cx * vp.y;
-            const float den = vp.z - along;
-            const float inv = __fdividef(1.0f, den);
-            const float uj = vp.w * lat * inv + jc;
-            // Conservative half-width (in bins) of the shadow of a disc of radius
-            // sqrt(2) around the centre: D_sd sec^2(gamma) asin(rho / dist) / pitch.
-            const float invp = inv * (1.0f + 2.0f * kSqrt2 * inv);
-            const float T = (fabsf(lat) + kSqrt2) * invp;
-            const float hw = kSqrt2 * vp.w * fmaf(T, T, 1.0f) * invp * 1.01f + 0.02f;
-            const int jlo = max(0, (int)ceilf(uj - hw));
-            const int jhi = min(a.n_det - 1, (int)floorf(uj + hw));
-            const long base = (long)v * a.n_det;
-            const float* __restrict__ rrow = res + (long)vs * a.n_det;
-            float accv = 0.0f;
-            for (int j = jlo; j <= jhi; ++j) {
-                const float4 f = __ldg(a.rayf + base + j);
-                const float ax = px - f.x, ay = py - f.y;        // pixel relative to the foot point
-                // the line meets the support square |X-px|,|Y-py| < 1 iff its distance
-                // from the centre is below the square's half-extent |d_x| + |d_y|
-                const float e = ax * f.w - ay * f.z;
-                if (fabsf(e) >= fabsf(f.z) + fabsf(f.w)) continue;
-                const float tau = fmaf(ax, f.z, ay * f.w);       // along-ray position of the centre
-                const float k0 = ceilf(fmaf(tau - kSqrt2, inv_step, -0.5f));
-                const float t0 = (k0 + 0.5f) * a.step;
-                const float X0 = fmaf(t0, f.z, -ax), Y0 = fmaf(t0, f.w, -ay);
-                const float sx = a.step * f.z, sy = a.step * f.w;
-                float w = 0.0f;
-                if (NWIN > 0) {
-#pragma unroll
-                    for (int m = 0; m < (NWIN > 0 ? NWIN : 1); ++m) {
-                        const float hx = 1.0f - fabsf(fmaf((float)m, sx, X0));
-                        const float hy = 1.0f - fabsf(fmaf((float)m, sy, Y0));
-                        w = fmaf(fmaxf(hx, 0.0f), fmaxf(hy, 0.0f), w);
-                    }
-                } else {
-                    for (int m = 0; m < nwin; ++m) {
-                        const float hx = 1.0f - fabsf(fmaf((float)m, sx, X0));
-                        const float hy = 1.0f - fabsf(fmaf((float)m, sy, Y0));
-                        w = fmaf(fmaxf(hx, 0.0f), fmaxf(hy, 0.0f), w);
-                    }
-                }
-                accv = fmaf(w, __ldg(rrow + j), accv);
-            }
-            total += accv;
-        }
-    }
-    const int pix = ty * kBackTile + tx;
-    part[g][pix] = total;
-    __syncthreads();
-    if (g != 0 || !inside) return;
-    float sum = 0.0f;
-    for (int q = 0; q < G; ++q) sum += part[q][pix];
-    const float val = a.scale * sum;
-    if (a.mode == kBackRaw) {
-        a.out[((long)inst * a.ns + iy) * a.ns + ix] = val;
-        return;
-    }
-    const int s = a.s;
-    for (int bb = 0; bb < s; ++bb) {
-        const long row = ((long)inst * a.n + (long)iy * s + bb) * a.n + (long)ix * s;
-        for (int aa = 0; aa < s; ++aa) {
-            if (a.mode == kBackGradFine)
-                a.out[row + aa] = val;
-            else
-                a.out[row + aa] = __ldg(a.y + row + aa) - a.eta * val;
-        }
-    }
-}
-
-// 2 x 2 pixel blocks per thread.  The four pixels share the view set-up and the
-// candidate rays; their union support is the 3 x 3 square around the block
-// centre (radius rho = 1.5 sqrt 2), so a ray's samples that can touch any of
-// them lie within rho of the centre's projection on the ray: at most
-// floor(2 rho / step) + 1 (9 for step 1/2).  Each sample evaluates the two x
-// hats and two y hats once and feeds four products.
+// The four pixels share the view set-up and the candidate rays; their union
+// support is the 3 x 3 square around the block centre (radius rho = 1.5 sqrt 2),
+// so a ray's samples that can touch any of them lie within rho of the centre's
+// projection on the ray: at most floor(2 rho / step) + 1 (9 for step 1/2).
+// Each sample evaluates the two x hats and two y hats once and feeds four
+// products.
 template <int NWIN>
 __global__ void __launch_bounds__(512, 2) k_backward2x2(BackArgs a)
 {
     const int tx = threadIdx.x, ty = threadIdx.y, g = threadIdx.z, G = blockDim.z;
     const int nb = (a.ns + 1) / 2;                             // blocks per side
-    const int tiles_x = (nb + kBackTile - 1) / kBackTile;
-    const int bx = (blockIdx.x % tiles_x) * kBackTile + tx;
-    const int by = (blockIdx.x / tiles_x) * kBackTile + ty;
+    const int tiles_x = (nb + kBack2Tile - 1) / kBack2Tile;
+    const int bx = (blockIdx.x % tiles_x) * kBack2Tile + tx;
+    const int by = (blockIdx.x / tiles_x) * kBack2Tile + ty;
     const int inst = blockIdx.y;
     const bool inside = bx < nb && by < nb;
-    __shared__ float4 part[kBackMaxGroups][kBackTile * kBackTile];
+    __shared__ float4 part[kBack2MaxGroups][kBack2Tile * kBack2Tile];
     float t00 = 0.0f, t10 = 0.0f, t01 = 0.0f, t11 = 0.0f;
     if (inside) {
         const int ix = 2 * bx, iy = 2 * by;
@@ -368,7 +274,7 @@ __global__ void __launch_bounds__(512, 2) k_backward2x2(BackArgs a)
             t00 += v00; t10 += v10; t01 += v01; t11 += v11;
         }
     }
-    const int slot = ty * kBackTile + tx;
+    const int slot = ty * kBack2Tile + tx;
     part[g][slot] = make_float4(t00, t10, t01, t11);
     __syncthreads();
     if (g != 0 || !inside) return;
@@ -397,16 +303,6 @@ __global__ void __launch_bounds__(512, 2) k_backward2x2(BackArgs a)
             }
         }
     }
-}
-
-// Number of view groups: enough threads for one full wave of the GPU
-// (152 SMs x 2048 threads), at most 8 and at most the number of views.
-inline int back_groups(long pixels, int n_sub)
-{
-    const long target = 152L * 2048L;
-    int G = 1;
-    while (G < kBackMaxGroups && pixels * G < target && G * 2 <= n_sub) G *= 2;
-    return G;
 }
 
 // ------------------------------------------------------------------ S and S^T
@@ -500,9 +396,11 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t st)
 cudaError_t launch_backward(const BackArgs& a, cudaStream_t st)
 {
     const int nb = (a.ns + 1) / 2;
-    const int G = back_groups((long)nb * nb * a.batch, a.n_sub);
-    const int tiles = div_up(nb, kBackTile) * div_up(nb, kBackTile);
-    dim3 blk(kBackTile, kBackTile, G), grd(tiles, a.batch);
+    // view groups: about two waves of 2048 threads per SM, at most 32 per CTA
+    int G = 1;
+    while (G < kBack2MaxGroups && (long)nb * nb * a.batch * G < 2L * 152 * 2048 && G * 2 <= a.n_sub) G *= 2;
+    const int tiles = div_up(nb, kBack2Tile) * div_up(nb, kBack2Tile);
+    dim3 blk(kBack2Tile, kBack2Tile, G), grd(tiles, a.batch);
     if (a.step == 0.5f)
         k_backward2x2<9><<<grd, blk, 0, st>>>(a);
     else
