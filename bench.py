@@ -258,7 +258,7 @@ def run_native(args, rank, world):
 
     def step():
         d_x.zero_()
-        plan.run(wl.stages, eta, seq, d_b, d_x, **kw)
+        plan.run(wl.stages, eta, seq, d_b, d_x, graph=True, **kw)
 
     launches_setup = pnp.launch_count()
     for _ in range(max(args.warmup, 3)):
@@ -287,7 +287,7 @@ def run_native(args, rank, world):
         for k in range(args.steps):
             flush.fill_(float(k))
             ev[k][0].record(stream)
-            plan.run(wl.stages, eta, seq, d_b, d_x.zero_(), **kw)
+            plan.run(wl.stages, eta, seq, d_b, d_x.zero_(), graph=True, **kw)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         barrier(world)
@@ -296,6 +296,18 @@ def run_native(args, rank, world):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = allmax(sum(step_ms), world)
     value = world * total_iters * args.steps / (total_ms / 1000.0)
+
+    # ---- the same step with direct launches (no CUDA graph), for comparison
+    nog = []
+    for k in range(3):
+        flush.fill_(3.0)
+        a_, b2_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        plan.run(wl.stages, eta, seq, d_b, d_x.zero_(), **kw)
+        b2_.record(stream)
+        torch.cuda.synchronize()
+        nog.append(a_.elapsed_time(b2_))
+    no_graph_ms = float(np.median(nog))
 
     # ---- per-kernel timing of the projector pair (events on the launching stream)
     def timed(fn, reps=20):
@@ -362,7 +374,7 @@ def run_native(args, rank, world):
         a.record(stream)
         d_b2.copy_(h_b, non_blocking=True)
         d_x.copy_(h_x0, non_blocking=True)
-        plan.run(wl.stages, eta, seq, d_b2, d_x, **kw)
+        plan.run(wl.stages, eta, seq, d_b2, d_x, graph=True, **kw)
         h_out.copy_(d_x, non_blocking=True)
         b_.record(stream)
         torch.cuda.synchronize()
@@ -414,7 +426,9 @@ def run_native(args, rank, world):
                              "sketched_ms": tts_s, "sketched_iters": it_s,
                              "full_ms": tts_f, "full_iters": it_f,
                              "speedup": (tts_f / tts_s) if (tts_s and tts_f) else None},
-            "setup_ms_power_iteration": setup_ms}
+            "setup_ms_power_iteration": setup_ms,
+            "launch_mode": "CUDA graph captured once, replayed per step",
+            "ms_per_step_direct_launches": no_graph_ms}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:

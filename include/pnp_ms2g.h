@@ -85,7 +85,30 @@ typedef struct {
     float lambda;       /* TV weight of the denoiser D = TV-prox (Sec. 2, after Eq. 5) */
     int32_t tv_iters;   /* FGP iterations of D (Beck & Teboulle 2009); 0 = identity */
     int32_t momentum;   /* 0: a_i = 0 (Eq. 5); 1: a_i = (i-1)/(i+3) (Sec. 3) */
+    int32_t flags;      /* PNP_RUN_* bits */
 } pnp_run_params;
+
+/* pnp_run / pnp_run_many: capture the whole launch sequence as a CUDA graph the
+ * first time a call with identical arguments (pointers, geometry, schedule,
+ * step sizes, subset sequence, parameters, stream) is made, and replay it on
+ * later identical calls.  Ignored on the legacy default stream (NULL).  The
+ * library keeps up to 16 instantiated graphs. */
+#define PNP_RUN_GRAPH 1
+
+/* One geometry class of a batched run: a uniform batch of images sharing one
+ * geometry, with its own schedule, data, iterate and prepared workspace. */
+typedef struct {
+    pnp_geom geom;
+    const pnp_stage* stages;
+    int32_t n_stages;
+    const double* h_eta;          /* [n_stages] */
+    const int32_t* h_subset_seq;  /* [sum iters], may be NULL when no stage uses subsets */
+    const float* d_b;             /* [batch][n_views][n_det] */
+    float* d_x;                   /* in: x_0, out: x */
+    const float* d_xtrue;         /* optional, with h_psnr_log */
+    double* h_psnr_log;           /* optional, [sum iters][batch] */
+    void* d_ws;                   /* pnp_setup-prepared workspace of this geometry */
+} pnp_problem;
 
 /* Maximum total iterations of one pnp_run call when a PSNR log is requested. */
 #define PNP_MAX_LOG_ITERS 65536
@@ -175,6 +198,25 @@ int pnp_power_iter(const pnp_geom* g, int factor, int max_iters, double tol, dou
 int pnp_run(const pnp_geom* g, const pnp_stage* stages, int n_stages, const double* h_eta,
             const int32_t* h_subset_seq, const pnp_run_params* params, const float* d_b,
             float* d_x, const float* d_xtrue, double* h_psnr_log, void* d_ws, void* stream);
+
+/* Algorithm 1 on up to 4 geometry classes at once (images of uneven size,
+ * views and bins): every iteration runs each projector and denoiser phase as
+ * ONE launch covering all classes that are still iterating (classes may have
+ * schedules of different lengths; iteration i of every class uses the same
+ * momentum a_i and params).  Workspaces and outputs must be distinct per
+ * class.  Synchronous only when some class logs PSNR.  PNP_EUNSUPPORTED for
+ * more than 4 classes. */
+int pnp_run_many(const pnp_problem* problems, int n_problems, const pnp_run_params* params, void* stream);
+
+/* Times the launch shapes of this geometry's kernels on d_ws's own buffers
+ * (forward lanes per ray 4/8/16 and backprojector view groups 1..32 for each
+ * sketch level of the schedule, using its first angle subset; the FGP tile side
+ * around the cost-model choice) and records the fastest for later calls that
+ * use d_ws.  Shapes change only the order of floating-point sums (results stay
+ * within rounding of each other and deterministic for fixed shapes).
+ * Synchronous; overwrites the workspace's scratch buffers. */
+int pnp_autotune(const pnp_geom* g, const pnp_stage* stages, int n_stages, const pnp_run_params* params,
+                 void* d_ws, void* stream);
 
 /* Final FP64 reductions for every instance: h_out[3*i + 0] = 1/2 ||A x - b||^2,
  * h_out[3*i + 1] = TV(x) (isotropic, as in the denoiser), h_out[3*i + 2] =

@@ -9,6 +9,6 @@ from . import synth  # noqa: F401
 from ._native import (  # noqa: F401
     Geom, Plan, PnpError, backproject, full_grad, full_grad_noalloc,
     header_functions, launch_count, last_error, load,
-    objective, power_iter, project, run, sample_count, setup, sketch, sketch_grad, subset_views,
+    objective, power_iter, project, run, run_many, autotune, sample_count, setup, sketch, sketch_grad, subset_views,
     tv_denoise, tv_workspace_size, upsample, workspace_size,
 )

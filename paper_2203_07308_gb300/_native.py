@@ -43,7 +43,17 @@ class StageC(C.Structure):
 
 class RunParams(C.Structure):
     _fields_ = [("alpha", C.c_float), ("lambda_", C.c_float), ("tv_iters", C.c_int32),
-                ("momentum", C.c_int32)]
+                ("momentum", C.c_int32), ("flags", C.c_int32)]
+
+
+RUN_GRAPH = 1
+
+
+class ProblemC(C.Structure):
+    _fields_ = [("geom", Geom), ("stages", C.POINTER(StageC)), ("n_stages", C.c_int32),
+                ("h_eta", C.POINTER(C.c_double)), ("h_subset_seq", C.POINTER(C.c_int32)),
+                ("d_b", C.c_void_p), ("d_x", C.c_void_p), ("d_xtrue", C.c_void_p),
+                ("h_psnr_log", C.POINTER(C.c_double)), ("d_ws", C.c_void_p)]
 
 
 _lock = threading.Lock()
@@ -89,6 +99,8 @@ def load(path: Optional[str] = None):
             "pnp_objective": [gp, vp, vp, vp, dp, vp, vp],
             "pnp_sample_count": [gp, i32, i32, i32, dp, vp, vp],
             "pnp_full_grad_noalloc": [gp, vp, vp, vp, vp],
+            "pnp_run_many": [C.POINTER(ProblemC), i32, C.POINTER(RunParams), vp],
+            "pnp_autotune": [gp, C.POINTER(StageC), i32, C.POINTER(RunParams), vp, vp],
             "pnp_tv_vjp_workspace_size": [i32, i32, i32, C.POINTER(sz)],
             "pnp_tv_vjp": [vp, vp, vp, dp, i32, i32, C.c_float, i32, vp, sz, vp],
             "pnp_vjp_workspace_size": [gp, i32, C.POINTER(sz)],
@@ -250,16 +262,17 @@ def _stages(stages: Sequence):
 
 
 def run(g, stages, eta, seq, b, x, *, alpha=1.0, lam=0.02, tv_iters=20, momentum=True,
-        xtrue=None, ws=None, stream=None):
+        xtrue=None, ws=None, stream=None, graph=False):
     """Algorithm 1; x holds x_0 on entry and the result on return.  Returns the
-    PSNR log [total_iters, batch] when xtrue is given, else None."""
+    PSNR log [total_iters, batch] when xtrue is given, else None.  graph=True
+    captures the launch sequence once per distinct call and replays it."""
     st = _stages(stages)
     total = sum(a.iters for a in st)
     eta_a = (C.c_double * len(st))(*[float(e) for e in eta])
     seq_np = np.ascontiguousarray(np.asarray(seq if seq is not None else np.zeros(total), dtype=np.int32))
     if seq_np.size < total:
         raise PnpError(PNP_EINVAL, "subset sequence shorter than the schedule")
-    prm = RunParams(float(alpha), float(lam), int(tv_iters), int(bool(momentum)))
+    prm = RunParams(float(alpha), float(lam), int(tv_iters), int(bool(momentum)), RUN_GRAPH if graph else 0)
     img = g.batch * g.n * g.n
     log = np.zeros((total, g.batch)) if xtrue is not None else None
     _check(load().pnp_run(C.byref(geom(g)), st, len(st), eta_a,
@@ -324,6 +337,9 @@ class Plan:
     def run(self, stages, eta, seq, b, x, **kw):
         return run(self.g, stages, eta, seq, b, x, ws=self.ws, **kw)
 
+    def autotune(self, stages, **kw):
+        autotune(self.g, stages, self.ws, **kw)
+
     def objective(self, x, b, xtrue=None, stream=None):
         return objective(self.g, x, b, xtrue, self.ws, stream)
 
@@ -358,7 +374,7 @@ def vjp_workspace_size(g, tv_iters: int) -> int:
 def unrolled_step(g, factor, subset, n_subsets, eta, alpha, lam, tv_iters, amom, y, xprev, b, xout, yout,
                   ws, stream=None):
     img = g.batch * g.n * g.n
-    prm = RunParams(float(alpha), float(lam), int(tv_iters), 0)
+    prm = RunParams(float(alpha), float(lam), int(tv_iters), 0, 0)
     _check(load().pnp_unrolled_step(C.byref(geom(g)), factor, subset, n_subsets, float(eta), C.byref(prm),
                                     float(amom), _ptr(y, img, "y"), _ptr(xprev, img, "xprev"),
                                     _ptr(b, g.batch * g.n_views * g.n_det, "b"), _ptr(xout, img, "xout"),
@@ -369,7 +385,7 @@ def unrolled_step_vjp(g, factor, subset, n_subsets, eta, alpha, lam, tv_iters, a
                       ybar_in, xpbar, ws, vjp_ws, stream=None):
     """Returns dJ/dlambda per instance; fills ybar_in and xpbar."""
     img = g.batch * g.n * g.n
-    prm = RunParams(float(alpha), float(lam), int(tv_iters), 0)
+    prm = RunParams(float(alpha), float(lam), int(tv_iters), 0, 0)
     lb = np.zeros(g.batch)
     vp, vbytes = _ws(vjp_ws)
     _check(load().pnp_unrolled_step_vjp(C.byref(geom(g)), factor, subset, n_subsets, float(eta), C.byref(prm),
@@ -379,3 +395,39 @@ def unrolled_step_vjp(g, factor, subset, n_subsets, eta, alpha, lam, tv_iters, a
                                         _ptr(xpbar, img, "xpbar"), lb.ctypes.data_as(C.POINTER(C.c_double)),
                                         _ws(ws)[0], vp, vbytes, _stream(stream)))
     return lb
+
+
+# ---------------------------------------------------------------- uneven batches, autotuning
+def run_many(problems, *, alpha=1.0, lam=0.02, tv_iters=20, momentum=True, stream=None, graph=False):
+    """pnp_run_many.  ``problems``: list of dicts with keys plan, stages, eta, seq,
+    b, x and optional xtrue; returns the list of PSNR logs (None where no xtrue)."""
+    arr = (ProblemC * len(problems))()
+    keep = []
+    logs = []
+    for k, pr in enumerate(problems):
+        plan = pr["plan"]
+        g = plan.g
+        st = _stages(pr["stages"])
+        total = sum(a.iters for a in st)
+        eta_a = (C.c_double * len(st))(*[float(e) for e in pr["eta"]])
+        seq = pr.get("seq")
+        seq_np = np.ascontiguousarray(np.asarray(seq if seq is not None else np.zeros(total), dtype=np.int32))
+        img = g.batch * g.n * g.n
+        xt = pr.get("xtrue")
+        log = np.zeros((total, g.batch)) if xt is not None else None
+        keep += [st, eta_a, seq_np, log]
+        logs.append(log)
+        arr[k] = ProblemC(geom(g), st, len(st), eta_a, seq_np.ctypes.data_as(C.POINTER(C.c_int32)),
+                          _ptr(pr["b"], g.batch * g.n_views * g.n_det, "b"), _ptr(pr["x"], img, "x"),
+                          _ptr(xt, img, "xtrue", True),
+                          log.ctypes.data_as(C.POINTER(C.c_double)) if log is not None else None,
+                          _ws(plan.ws)[0])
+    prm = RunParams(float(alpha), float(lam), int(tv_iters), int(bool(momentum)), RUN_GRAPH if graph else 0)
+    _check(load().pnp_run_many(arr, len(problems), C.byref(prm), _stream(stream)))
+    return logs
+
+
+def autotune(g, stages, ws, *, alpha=1.0, lam=0.02, tv_iters=20, stream=None):
+    st = _stages(stages)
+    prm = RunParams(float(alpha), float(lam), int(tv_iters), 1, 0)
+    _check(load().pnp_autotune(C.byref(geom(g)), st, len(st), C.byref(prm), _ws(ws)[0], _stream(stream)))

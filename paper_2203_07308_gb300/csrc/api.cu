@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -145,7 +146,14 @@ uint64_t fingerprint(const pnp_geom& g)
     return h;
 }
 
-struct RegEntry { const void* ws; uint64_t fp; size_t bytes; };
+// Launch shapes chosen by pnp_autotune for one prepared workspace (0 = heuristic).
+struct Tuned {
+    int lanes[kMaxLevels] = {0, 0, 0, 0};    // forward: lanes per ray
+    int groups[kMaxLevels] = {0, 0, 0, 0};   // backprojector: view groups per CTA
+    int tile = 0;                            // tiled FGP: tile side
+};
+
+struct RegEntry { const void* ws; uint64_t fp; size_t bytes; Tuned tuned; };
 std::mutex g_reg_mu;
 std::vector<RegEntry> g_reg;
 
@@ -153,9 +161,24 @@ void reg_put(const void* ws, uint64_t fp, size_t bytes)
 {
     std::lock_guard<std::mutex> lk(g_reg_mu);
     for (auto& e : g_reg)
-        if (e.ws == ws) { e.fp = fp; e.bytes = bytes; return; }
+        if (e.ws == ws) { e.fp = fp; e.bytes = bytes; e.tuned = Tuned(); return; }
     if (g_reg.size() >= 4096) g_reg.erase(g_reg.begin());
-    g_reg.push_back({ws, fp, bytes});
+    g_reg.push_back({ws, fp, bytes, Tuned()});
+}
+
+Tuned reg_tuned(const void* ws)
+{
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    for (const auto& e : g_reg)
+        if (e.ws == ws) return e.tuned;
+    return Tuned();
+}
+
+void reg_set_tuned(const void* ws, const Tuned& t)
+{
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    for (auto& e : g_reg)
+        if (e.ws == ws) e.tuned = t;
 }
 
 int check_ws(const pnp_geom& g, const void* ws)
@@ -250,12 +273,79 @@ int grad_into(const pnp_geom& g, const Layout& L, int li, char* ws, const float*
               int p, int P, int mode, float eta, float* out, cudaStream_t st)
 {
     const LevelLayout& lv = L.lv[li];
+    const Tuned tu = reg_tuned(ws);
     float* res = (float*)(ws + L.off_res);
     PNP_CUDA(launch_prep_quad(y, g.n, lv.factor, g.batch, (float4*)(ws + lv.off_quad), lv.qw, st));
-    PNP_CUDA(launch_forward(fwd_args(g, lv, ws, p, P, b, res, g.batch), st));
+    PNP_CUDA(launch_forward(fwd_args(g, lv, ws, p, P, b, res, g.batch), st, tu.lanes[li]));
     const double c = P <= 1 ? 1.0 : (double)P;
     const float scale = (float)(g.step * lv.factor * c / ((double)lv.factor * lv.factor));
-    PNP_CUDA(launch_backward(back_args(g, lv, ws, p, P, res, mode, scale, y, eta, out, g.batch), st));
+    PNP_CUDA(launch_backward(back_args(g, lv, ws, p, P, res, mode, scale, y, eta, out, g.batch), st,
+                             tu.groups[li]));
+    return PNP_OK;
+}
+
+// ---------------------------------------------------------------- CUDA graphs
+// pnp_run / pnp_run_many with PNP_RUN_GRAPH capture their launch sequence once
+// per distinct call (same pointers, geometry, schedule, step sizes, subset
+// sequence and parameters) and replay the instantiated graph afterwards.
+struct GraphEntry { uint64_t key; cudaGraphExec_t exec; };
+std::mutex g_graph_mu;
+std::vector<GraphEntry> g_graphs;
+constexpr size_t kMaxGraphs = 16;
+
+struct Hasher {
+    uint64_t h = 1469598103934665603ull;
+    void add(const void* p, size_t n)
+    {
+        const unsigned char* c = (const unsigned char*)p;
+        for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    }
+    template <class T> void val(const T& v) { add(&v, sizeof v); }
+};
+
+cudaGraphExec_t graph_find(uint64_t key)
+{
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (const auto& e : g_graphs)
+        if (e.key == key) return e.exec;
+    return nullptr;
+}
+
+void graph_store(uint64_t key, cudaGraphExec_t exec)
+{
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    if (g_graphs.size() >= kMaxGraphs) {
+        cudaGraphExecDestroy(g_graphs.front().exec);
+        g_graphs.erase(g_graphs.begin());
+    }
+    g_graphs.push_back({key, exec});
+}
+
+// Runs `issue` (which enqueues kernels on st) directly, or through a cached
+// graph keyed by `key` when use_graph is set and st can be captured.
+template <class F>
+int run_maybe_graph(bool use_graph, uint64_t key, cudaStream_t st, F&& issue)
+{
+    if (!use_graph || st == nullptr) return issue();
+    if (cudaGraphExec_t ex = graph_find(key)) {
+        PNP_CUDA(cudaGraphLaunch(ex, st));
+        return PNP_OK;
+    }
+    PNP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const int rc = issue();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+    if (rc != PNP_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (ec != cudaSuccess) return fail(PNP_ECUDA, "graph capture: %s", cudaGetErrorString(ec));
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&ex, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return fail(PNP_ECUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+    graph_store(key, ex);
+    PNP_CUDA(cudaGraphLaunch(ex, st));
     return PNP_OK;
 }
 
@@ -459,86 +549,298 @@ int pnp_power_iter(const pnp_geom* g, int factor, int max_iters, double tol, dou
     return PNP_OK;
 }
 
+namespace {
+
+struct ProblemState {
+    const pnp_problem* pb;
+    Layout L;
+    long total;
+    int tv_parts;
+    Tuned tuned;
+};
+
+int validate_problem(const pnp_problem& q, const pnp_run_params& pr, int idx, ProblemState* out)
+{
+    const pnp_geom* g = &q.geom;
+    if (int e = validate_geom(g)) return e;
+    out->pb = &q;
+    out->L = make_layout(*g);
+    if (!q.stages || q.n_stages < 1 || !q.h_eta || !q.d_b || !q.d_x)
+        return fail(PNP_EINVAL, "problem %d: stages, eta, b and x are required", idx);
+    if ((q.d_xtrue == nullptr) != (q.h_psnr_log == nullptr))
+        return fail(PNP_EINVAL, "problem %d: d_xtrue and h_psnr_log must be given together", idx);
+    long total = 0;
+    bool any_subsets = false;
+    for (int k = 0; k < q.n_stages; ++k) {
+        int li;
+        if (int e = check_level(*g, q.stages[k].factor, out->L, &li)) return e;
+        if (q.stages[k].iters < 0) return fail(PNP_EINVAL, "stage %d has negative iterations", k);
+        if (q.stages[k].n_subsets < 1 || q.stages[k].n_subsets > g->n_views)
+            return fail(PNP_EINVAL, "stage %d: n_subsets outside [1, n_views]", k);
+        if (!(std::isfinite(q.h_eta[k]) && q.h_eta[k] >= 0.0)) return fail(PNP_EINVAL, "eta[%d] invalid", k);
+        any_subsets |= q.stages[k].n_subsets > 1;
+        total += q.stages[k].iters;
+    }
+    if (total > (1L << 30)) return fail(PNP_EINVAL, "too many iterations");
+    if (any_subsets && !q.h_subset_seq) return fail(PNP_EINVAL, "subset sequence required");
+    if (q.h_psnr_log && total * g->batch > PNP_MAX_LOG_ITERS)
+        return fail(PNP_EINVAL, "PSNR log limited to %d iterations x batch", PNP_MAX_LOG_ITERS);
+    if (int e = check_ws(*g, q.d_ws)) return e;
+    long i = 0;
+    for (int k = 0; k < q.n_stages; ++k)
+        for (int jj = 0; jj < q.stages[k].iters; ++jj, ++i)
+            if (q.stages[k].n_subsets > 1 &&
+                (q.h_subset_seq[i] < 0 || q.h_subset_seq[i] >= q.stages[k].n_subsets))
+                return fail(PNP_EINVAL, "subset_seq[%ld]=%d outside stage %d's [0, %d)", i, q.h_subset_seq[i], k,
+                            q.stages[k].n_subsets);
+    out->total = total;
+    out->tuned = reg_tuned(q.d_ws);
+    const bool do_tv = pr.tv_iters > 0 && pr.lambda > 0.0f;
+    out->tv_parts = do_tv ? tile_tv_parts_for(g->n, g->batch, out->tuned.tile)
+                          : ((g->n + 31) / 32) * ((g->n + 7) / 8);
+    return PNP_OK;
+}
+
+int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, void* stream)
+{
+    if (!pb || np < 1) return fail(PNP_EINVAL, "no problems");
+    if (np > kMaxClasses) return fail(PNP_EUNSUPPORTED, "at most %d geometry classes per call", kMaxClasses);
+    if (!params) return fail(PNP_EINVAL, "params are required");
+    const pnp_run_params& pr = *params;
+    if (!(pr.alpha > 0.0f && pr.alpha <= 1.0f)) return fail(PNP_EINVAL, "alpha must be in (0, 1]");
+    if (!(pr.lambda >= 0.0f) || !std::isfinite(pr.lambda)) return fail(PNP_EINVAL, "lambda must be >= 0");
+    if (pr.tv_iters < 0 || pr.tv_iters > 100000) return fail(PNP_EINVAL, "tv_iters outside [0, 100000]");
+    std::vector<ProblemState> ps((size_t)np);
+    for (int c = 0; c < np; ++c)
+        if (int e = validate_problem(pb[c], pr, c, &ps[c])) return e;
+    for (int c = 0; c < np; ++c)
+        for (int d = c + 1; d < np; ++d)
+            if (pb[c].d_ws == pb[d].d_ws || pb[c].d_x == pb[d].d_x)
+                return fail(PNP_EINVAL, "problems %d and %d share a workspace or an output", c, d);
+    cudaStream_t st = S(stream);
+    const bool do_tv = pr.tv_iters > 0 && pr.lambda > 0.0f;
+    long max_total = 0;
+    for (const auto& q : ps) max_total = std::max(max_total, q.total);
+    const bool one = np == 1;
+
+    auto issue = [&]() -> int {
+        for (int c = 0; c < np; ++c) {
+            const pnp_geom& g = pb[c].geom;
+            char* ws = (char*)pb[c].d_ws;
+            PNP_CUDA(launch_copy(pb[c].d_x, (float*)(ws + ps[c].L.off_y), (size_t)g.batch * g.n * g.n, st));
+        }
+        std::vector<int> stage((size_t)np, 0), in_stage((size_t)np, 0);
+        for (long i = 1; i <= max_total; ++i) {
+            PrepArgs prep[kMaxClasses];
+            FwdArgs fwd[kMaxClasses];
+            BackArgs back[kMaxClasses];
+            TvItem tv[kMaxClasses];
+            int act[kMaxClasses];
+            int na = 0;
+            const float amom = pr.momentum ? (float)((double)(i - 1) / (double)(i + 3)) : 0.0f;
+            for (int c = 0; c < np; ++c) {
+                if (i > ps[c].total) continue;
+                const pnp_problem& q = pb[c];
+                while (in_stage[c] >= q.stages[stage[c]].iters) { ++stage[c]; in_stage[c] = 0; }
+                const pnp_stage& sk = q.stages[stage[c]];
+                ++in_stage[c];
+                const pnp_geom& g = q.geom;
+                const Layout& L = ps[c].L;
+                const int li = level_index(sk.factor);
+                const LevelLayout& lv = L.lv[li];
+                char* ws = (char*)q.d_ws;
+                const int P = sk.n_subsets;
+                const int p = P > 1 ? q.h_subset_seq[i - 1] : 0;
+                float* y = (float*)(ws + L.off_y);
+                float* z = (float*)(ws + L.off_z);
+                float* res = (float*)(ws + L.off_res);
+                prep[na] = PrepArgs{y, g.n, lv.factor, g.batch, (float4*)(ws + lv.off_quad), lv.qw};
+                fwd[na] = fwd_args(g, lv, ws, p, P, q.d_b, res, g.batch);
+                const double cs = P <= 1 ? 1.0 : (double)P;
+                const float scale = (float)(g.step * lv.factor * cs / ((double)lv.factor * lv.factor));
+                back[na] = back_args(g, lv, ws, p, P, res, kBackStep, scale, y, (float)q.h_eta[stage[c]], z, g.batch);
+                const size_t img = (size_t)g.batch * g.n * g.n;
+                float* tvb = (float*)(ws + L.off_tv);
+                TvItem t{};
+                t.z = z; t.xprev = q.d_x; t.y = y; t.xtrue = q.d_xtrue;
+                t.mse_part = q.h_psnr_log ? (double*)(ws + L.off_red) : nullptr;
+                t.state_a = tvb; t.state_b = tvb + 4 * img;
+                t.n = g.n; t.batch = g.batch; t.tile = ps[c].tuned.tile; t.amom = amom;
+                tv[na] = t;
+                act[na] = c;
+                ++na;
+                (void)li;
+            }
+            if (na == 0) break;
+            const Tuned& tu = ps[act[0]].tuned;
+            int li0 = 0;
+            if (one) {
+                const pnp_problem& q = pb[0];
+                li0 = level_index(q.stages[stage[0]].factor);
+            }
+            PNP_CUDA(launch_prep_multi(prep, na, st));
+            PNP_CUDA(launch_forward_multi(fwd, na, st, one ? tu.lanes[li0] : 0));
+            PNP_CUDA(launch_backward_multi(back, na, st, one ? tu.groups[li0] : 0));
+            if (do_tv) {
+                PNP_CUDA(launch_tv_tiled_multi(tv, na, pr.lambda, pr.tv_iters, pr.alpha, st));
+            } else {
+                for (int a = 0; a < na; ++a) {
+                    const TvItem& t = tv[a];
+                    PNP_CUDA(launch_tv_final(t.z, nullptr, 0, t.n, t.batch, pr.lambda, pr.alpha, t.amom, t.xprev,
+                                             t.y, t.xtrue, t.mse_part, st));
+                }
+            }
+            for (int a = 0; a < na; ++a) {
+                const int c = act[a];
+                const pnp_problem& q = pb[c];
+                if (!q.h_psnr_log) continue;
+                char* ws = (char*)q.d_ws;
+                double* dlog = (double*)(ws + ps[c].L.off_log);
+                PNP_CUDA(launch_reduce_final((double*)(ws + ps[c].L.off_red), ps[c].tv_parts, q.geom.batch,
+                                             dlog + (i - 1) * q.geom.batch, 1, 0, st));
+            }
+        }
+        return PNP_OK;
+    };
+
+    Hasher h;
+    h.val(np);
+    h.val(pr);
+    h.val(stream);
+    for (int c = 0; c < np; ++c) {
+        const pnp_problem& q = pb[c];
+        h.val(q.geom);
+        h.val(q.d_b); h.val(q.d_x); h.val(q.d_xtrue); h.val(q.d_ws);
+        h.val(q.h_psnr_log != nullptr);
+        h.add(q.stages, sizeof(pnp_stage) * (size_t)q.n_stages);
+        h.add(q.h_eta, sizeof(double) * (size_t)q.n_stages);
+        if (q.h_subset_seq) h.add(q.h_subset_seq, sizeof(int32_t) * (size_t)ps[c].total);
+        h.val(ps[c].tuned);
+    }
+    if (int e = run_maybe_graph((pr.flags & PNP_RUN_GRAPH) != 0, h.h, st, issue)) return e;
+
+    for (int c = 0; c < np; ++c) {
+        const pnp_problem& q = pb[c];
+        if (!q.h_psnr_log || ps[c].total == 0) continue;
+        char* ws = (char*)q.d_ws;
+        std::vector<double> mse((size_t)ps[c].total * q.geom.batch);
+        PNP_CUDA(cudaMemcpyAsync(mse.data(), ws + ps[c].L.off_log, mse.size() * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+        PNP_CUDA(cudaStreamSynchronize(st));
+        const double npix = (double)q.geom.n * q.geom.n;
+        for (size_t k = 0; k < mse.size(); ++k) q.h_psnr_log[k] = 10.0 * std::log10(npix / mse[k]);
+    }
+    return PNP_OK;
+}
+
+}  // namespace
+
 int pnp_run(const pnp_geom* g, const pnp_stage* stages, int n_stages, const double* h_eta,
             const int32_t* h_subset_seq, const pnp_run_params* params, const float* d_b, float* d_x,
             const float* d_xtrue, double* h_psnr_log, void* d_ws, void* stream)
 {
     t_err.clear();
+    if (!g) return fail(PNP_EINVAL, "geometry pointer is NULL");
+    pnp_problem q{};
+    q.geom = *g;
+    q.stages = stages;
+    q.n_stages = n_stages;
+    q.h_eta = h_eta;
+    q.h_subset_seq = h_subset_seq;
+    q.d_b = d_b;
+    q.d_x = d_x;
+    q.d_xtrue = d_xtrue;
+    q.h_psnr_log = h_psnr_log;
+    q.d_ws = d_ws;
+    return run_many_impl(&q, 1, params, stream);
+}
+
+int pnp_run_many(const pnp_problem* problems, int n_problems, const pnp_run_params* params, void* stream)
+{
+    t_err.clear();
+    return run_many_impl(problems, n_problems, params, stream);
+}
+
+int pnp_autotune(const pnp_geom* g, const pnp_stage* stages, int n_stages, const pnp_run_params* params,
+                 void* d_ws, void* stream)
+{
+    t_err.clear();
     if (int e = validate_geom(g)) return e;
+    if (!stages || n_stages < 1 || !params) return fail(PNP_EINVAL, "stages and params are required");
+    if (int e = check_ws(*g, d_ws)) return e;
     Layout L = make_layout(*g);
-    if (!stages || n_stages < 1 || !h_eta || !params || !d_b || !d_x)
-        return fail(PNP_EINVAL, "stages, eta, params, b and x are required");
-    if ((d_xtrue == nullptr) != (h_psnr_log == nullptr))
-        return fail(PNP_EINVAL, "d_xtrue and h_psnr_log must be given together");
-    long total = 0;
-    bool any_subsets = false;
     for (int k = 0; k < n_stages; ++k) {
         int li;
         if (int e = check_level(*g, stages[k].factor, L, &li)) return e;
-        if (stages[k].iters < 0) return fail(PNP_EINVAL, "stage %d has negative iterations", k);
         if (stages[k].n_subsets < 1 || stages[k].n_subsets > g->n_views)
             return fail(PNP_EINVAL, "stage %d: n_subsets outside [1, n_views]", k);
-        if (!(std::isfinite(h_eta[k]) && h_eta[k] >= 0.0)) return fail(PNP_EINVAL, "eta[%d] invalid", k);
-        any_subsets |= stages[k].n_subsets > 1;
-        total += stages[k].iters;
     }
-    if (total > (1L << 30)) return fail(PNP_EINVAL, "too many iterations");
-    if (any_subsets && !h_subset_seq) return fail(PNP_EINVAL, "subset sequence required");
-    const pnp_run_params& pr = *params;
-    if (!(pr.alpha > 0.0f && pr.alpha <= 1.0f)) return fail(PNP_EINVAL, "alpha must be in (0, 1]");
-    if (!(pr.lambda >= 0.0f) || !std::isfinite(pr.lambda)) return fail(PNP_EINVAL, "lambda must be >= 0");
-    if (pr.tv_iters < 0 || pr.tv_iters > 100000) return fail(PNP_EINVAL, "tv_iters outside [0, 100000]");
-    if (h_psnr_log && total * g->batch > PNP_MAX_LOG_ITERS)
-        return fail(PNP_EINVAL, "PSNR log limited to %d iterations x batch", PNP_MAX_LOG_ITERS);
-    if (int e = check_ws(*g, d_ws)) return e;
-    // validate the subset sequence before launching anything
-    {
-        long i = 0;
-        for (int k = 0; k < n_stages; ++k)
-            for (int jj = 0; jj < stages[k].iters; ++jj, ++i)
-                if (stages[k].n_subsets > 1 &&
-                    (h_subset_seq[i] < 0 || h_subset_seq[i] >= stages[k].n_subsets))
-                    return fail(PNP_EINVAL, "subset_seq[%ld]=%d outside stage %d's [0, %d)", i,
-                                h_subset_seq[i], k, stages[k].n_subsets);
-    }
-    char* ws = (char*)d_ws;
     cudaStream_t st = S(stream);
+    char* ws = (char*)d_ws;
     const size_t img = (size_t)g->batch * g->n * g->n;
     float* y = (float*)(ws + L.off_y);
     float* z = (float*)(ws + L.off_z);
+    float* res = (float*)(ws + L.off_res);
     float* tvb = (float*)(ws + L.off_tv);
-    double* part = (double*)(ws + L.off_red);
-    double* dlog = (double*)(ws + L.off_log);
-    const bool do_tv = pr.tv_iters > 0 && pr.lambda > 0.0f;
-    const int tv_parts = do_tv ? tile_tv_parts(g->n, g->batch)
-                               : ((g->n + 31) / 32) * ((g->n + 7) / 8);
-    PNP_CUDA(launch_copy(d_x, y, img, st));
-    long i = 0;
-    for (int k = 0; k < n_stages; ++k) {
+    PNP_CUDA(launch_fill(y, img, 0.5f, st));
+    cudaEvent_t e0, e1;
+    PNP_CUDA(cudaEventCreate(&e0));
+    PNP_CUDA(cudaEventCreate(&e1));
+    auto timeit = [&](auto&& fn, float* ms) -> int {
+        for (int rep = 0; rep < 2; ++rep) if (int e = fn()) return e;   // warm-up
+        PNP_CUDA(cudaEventRecord(e0, st));
+        for (int rep = 0; rep < 5; ++rep) if (int e = fn()) return e;
+        PNP_CUDA(cudaEventRecord(e1, st));
+        PNP_CUDA(cudaEventSynchronize(e1));
+        PNP_CUDA(cudaEventElapsedTime(ms, e0, e1));
+        return PNP_OK;
+    };
+    Tuned tu;
+    int rc = PNP_OK;
+    for (int k = 0; k < n_stages && rc == PNP_OK; ++k) {
         const int li = level_index(stages[k].factor);
+        if (tu.lanes[li]) continue;                     // first stage of a level decides
+        const LevelLayout& lv = L.lv[li];
         const int P = stages[k].n_subsets;
-        for (int jj = 0; jj < stages[k].iters; ++jj) {
-            ++i;
-            const int p = P > 1 ? h_subset_seq[i - 1] : 0;
-            if (int e = grad_into(*g, L, li, ws, y, d_b, p, P, kBackStep, (float)h_eta[k], z, st)) return e;
-            const float a = pr.momentum ? (float)((double)(i - 1) / (double)(i + 3)) : 0.0f;
-            double* mp = h_psnr_log ? part : nullptr;
-            if (do_tv)
-                PNP_CUDA(launch_tv_tiled(z, g->n, g->batch, pr.lambda, pr.tv_iters, pr.alpha, a, d_x, y,
-                                         d_xtrue, mp, tvb, tvb + 4 * img, st));
-            else
-                PNP_CUDA(launch_tv_final(z, nullptr, 0, g->n, g->batch, pr.lambda, pr.alpha, a, d_x, y,
-                                         d_xtrue, mp, st));
-            if (mp) PNP_CUDA(launch_reduce_final(part, tv_parts, g->batch, dlog + (i - 1) * g->batch, 1, 0, st));
+        rc = launch_prep_quad(y, g->n, lv.factor, g->batch, (float4*)(ws + lv.off_quad), lv.qw, st) == cudaSuccess
+                 ? PNP_OK : fail(PNP_ECUDA, "prep failed");
+        const FwdArgs fa = fwd_args(*g, lv, ws, 0, P, nullptr, res, g->batch);
+        float best = 1e30f;
+        for (int Q : {4, 8, 16}) {
+            float ms = 0.0f;
+            if (rc == PNP_OK) rc = timeit([&]() -> int { PNP_CUDA(launch_forward(fa, st, Q)); return PNP_OK; }, &ms);
+            if (rc == PNP_OK && ms < best) { best = ms; tu.lanes[li] = Q; }
+        }
+        const BackArgs ba = back_args(*g, lv, ws, 0, P, res, kBackRaw, 1.0f, nullptr, 0.0f, z, g->batch);
+        best = 1e30f;
+        const int nsub = subset_views(*g, 0, P);
+        for (int G = 1; G <= 32 && G <= nsub; G *= 2) {
+            float ms = 0.0f;
+            if (rc == PNP_OK) rc = timeit([&]() -> int { PNP_CUDA(launch_backward(ba, st, G)); return PNP_OK; }, &ms);
+            if (rc == PNP_OK && ms < best) { best = ms; tu.groups[li] = G; }
         }
     }
-    if (h_psnr_log && total > 0) {
-        std::vector<double> mse((size_t)total * g->batch);
-        PNP_CUDA(cudaMemcpyAsync(mse.data(), dlog, mse.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-        PNP_CUDA(cudaStreamSynchronize(st));
-        const double npix = (double)g->n * g->n;
-        for (size_t q = 0; q < mse.size(); ++q) h_psnr_log[q] = 10.0 * std::log10(npix / mse[q]);
+    const pnp_run_params& pr = *params;
+    if (rc == PNP_OK && pr.tv_iters > 0 && pr.lambda > 0.0f) {
+        const int T0 = tile_tv_tile(g->n, g->batch);
+        float best = 1e30f;
+        const int iters = std::min(pr.tv_iters, 10);
+        for (int T : {T0 - 6, T0 - 4, T0 - 2, T0, T0 + 2, T0 + 4, T0 + 6, 16, 24, 32}) {
+            if (T < 8 || T > 40) continue;
+            float ms = 0.0f;
+            rc = timeit([&]() -> int {
+                PNP_CUDA(launch_tv_tiled(y, g->n, g->batch, pr.lambda, iters, 1.0f, 0.0f, z, nullptr, nullptr,
+                                         nullptr, tvb, tvb + 4 * img, st, T));
+                return PNP_OK;
+            }, &ms);
+            if (rc != PNP_OK) break;
+            if (ms < best) { best = ms; tu.tile = T; }
+        }
     }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != PNP_OK) return rc;
+    reg_set_tuned(d_ws, tu);
     return PNP_OK;
 }
 

@@ -67,8 +67,16 @@ int validate_geom(const pnp_geom* g);
 // ---------------------------------------------------------------- kernels (launchers)
 cudaError_t launch_setup_rays(const pnp_geom& g, const LevelLayout& L, char* ws, cudaStream_t st);
 
+// Every projector and denoiser kernel takes a table of up to kMaxClasses
+// geometry classes (each a uniform batch of images sharing one geometry) and
+// covers all of them in one launch; the single-class launchers below are the
+// one-entry case.  Autotuned launch shapes (0 = heuristic) ride along.
+constexpr int kMaxClasses = 4;
+
+struct PrepArgs { const float* fine; int n, s, batch; float4* quad; int qw; };
 cudaError_t launch_prep_quad(const float* fine, int n, int s, int batch, float4* quad, int qw,
                              cudaStream_t st);
+cudaError_t launch_prep_multi(const PrepArgs* items, int count, cudaStream_t st);
 
 struct FwdArgs {
     const float4* quad; int qw; size_t quad_stride;
@@ -78,7 +86,8 @@ struct FwdArgs {
     const float* b; int n_views;     // b: [batch][n_views][n_det] or null
     float* out;                      // [batch][n_sub][n_det]
 };
-cudaError_t launch_forward(const FwdArgs& a, cudaStream_t st);
+cudaError_t launch_forward(const FwdArgs& a, cudaStream_t st, int lanes = 0);
+cudaError_t launch_forward_multi(const FwdArgs* items, int count, cudaStream_t st, int lanes = 0);
 
 enum BackMode { kBackRaw = 0, kBackGradFine = 1, kBackStep = 2 };
 struct BackArgs {
@@ -91,7 +100,8 @@ struct BackArgs {
     const float* y; float eta;       // mode 2: z = y - eta * scale * sum
     float* out;
 };
-cudaError_t launch_backward(const BackArgs& a, cudaStream_t st);
+cudaError_t launch_backward(const BackArgs& a, cudaStream_t st, int groups = 0);
+cudaError_t launch_backward_multi(const BackArgs* items, int count, cudaStream_t st, int groups = 0);
 
 cudaError_t launch_pool(const float* fine, float* coarse, int n, int s, int batch, cudaStream_t st);
 cudaError_t launch_unpool(const float* coarse, float* fine, int n, int s, int batch, cudaStream_t st);
@@ -115,7 +125,16 @@ int tile_tv_tile(int n, int batch);
 int tile_tv_parts(int n, int batch);
 cudaError_t launch_tv_tiled(const float* z, int n, int batch, float lambda, int iters, float alpha,
                             float amom, float* xprev, float* y, const float* xtrue, double* mse_part,
-                            float* state_a, float* state_b, cudaStream_t st);
+                            float* state_a, float* state_b, cudaStream_t st, int tile = 0);
+struct TvItem {
+    const float* z; float* xprev; float* y; const float* xtrue; double* mse_part;
+    float* state_a; float* state_b;        // [4][batch][n][n] each (chained launches only)
+    int n, batch, tile;                    // tile 0 = cost model
+    float amom;
+};
+cudaError_t launch_tv_tiled_multi(const TvItem* items, int count, float lambda, int iters, float alpha,
+                                  cudaStream_t st);
+int tile_tv_parts_for(int n, int batch, int tile);
 
 // Reverse mode (vjp.cu) ----------------------------------------------------------
 size_t tv_vjp_workspace_floats(int n, int batch, int iters);

@@ -102,50 +102,76 @@ __device__ __forceinline__ float pooled(const float* __restrict__ fine, int n, i
     return acc * (1.0f / (float)(s * s));
 }
 
-__global__ void k_prep_quad(const float* __restrict__ fine, int n, int s, int qw,
-                            float4* __restrict__ quad)
+struct PrepTable {
+    PrepArgs c[kMaxClasses];
+    long begin[kMaxClasses + 1];   // cumulative cell counts (batch * qw * qw)
+    int count;
+};
+
+__global__ void k_prep_quad(const PrepTable t)
 {
-    int qx = blockIdx.x * blockDim.x + threadIdx.x;
-    int qy = blockIdx.y * blockDim.y + threadIdx.y;
-    int inst = blockIdx.z;
-    if (qx >= qw || qy >= qw) return;
-    const int ns = n / s;
-    const float* f = fine + (long)inst * n * n;
-    int ix0 = qx - kPad, iy0 = qy - kPad;
-    float a = pooled(f, n, s, ns, ix0, iy0), b = pooled(f, n, s, ns, ix0 + 1, iy0);
-    float c = pooled(f, n, s, ns, ix0, iy0 + 1), d = pooled(f, n, s, ns, ix0 + 1, iy0 + 1);
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= t.begin[t.count]) return;
+    int c = 0;
+#pragma unroll
+    for (int k = 1; k < kMaxClasses; ++k)
+        if (k < t.count && idx >= t.begin[k]) c = k;
+    const PrepArgs& a = t.c[c];
+    const long local = idx - t.begin[c];
+    const int qw = a.qw;
+    const long cells = (long)qw * qw;
+    const int inst = (int)(local / cells);
+    const int rem = (int)(local - (long)inst * cells);
+    const int qy = rem / qw, qx = rem - qy * qw;
+    const int n = a.n, s = a.s, ns = n / s;
+    const float* f = a.fine + (long)inst * n * n;
+    const int ix0 = qx - kPad, iy0 = qy - kPad;
+    const float pa = pooled(f, n, s, ns, ix0, iy0), pb = pooled(f, n, s, ns, ix0 + 1, iy0);
+    const float pc = pooled(f, n, s, ns, ix0, iy0 + 1), pd = pooled(f, n, s, ns, ix0 + 1, iy0 + 1);
     float4 q;
-    q.x = 0.25f * ((a + b) + (c + d));
-    q.y = 0.5f * ((b - a) + (d - c));
-    q.z = 0.5f * ((c - a) + (d - b));
-    q.w = (a - b) - (c - d);
-    quad[(long)inst * qw * qw + (long)qy * qw + qx] = q;
+    q.x = 0.25f * ((pa + pb) + (pc + pd));
+    q.y = 0.5f * ((pb - pa) + (pd - pc));
+    q.z = 0.5f * ((pc - pa) + (pd - pb));
+    q.w = (pa - pb) - (pc - pd);
+    a.quad[local] = q;
 }
 
 // ------------------------------------------------------------------ forward A_s
 // Warp = R rays x Q phases (R*Q = 32): lane (r, q) sums the samples k = k_lo + q,
 // k_lo + q + Q, ... of ray r; the Q partial sums are combined by shuffles in a
 // fixed order, so the result is deterministic.  One 16-byte load per sample.
+struct FwdTable {
+    FwdArgs c[kMaxClasses];
+    long begin[kMaxClasses + 1];   // cumulative ray counts (batch * n_sub * n_det)
+    int count;
+};
+
 template <int Q>
-__global__ void __launch_bounds__(256, 4) k_forward(FwdArgs a)
+__global__ void __launch_bounds__(256, 4) k_forward(const FwdTable t)
 {
     constexpr int R = 32 / Q;
     const int lane = threadIdx.x & 31;
     const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int r = lane / Q, q = lane % Q;
-    const long rays_inst = (long)a.n_sub * a.n_det;
     const long gray = warp * R + r;
-    const bool active = gray < rays_inst * a.batch;
+    const bool active = gray < t.begin[t.count];
+    int c = 0;
+#pragma unroll
+    for (int k = 1; k < kMaxClasses; ++k)
+        if (k < t.count && gray >= t.begin[k]) c = k;
+    const FwdArgs& a = t.c[c];
     float acc = 0.0f;
     long out_idx = 0;
     int v = 0, j = 0, inst = 0;
     if (active) {
-        inst = (int)(gray / rays_inst);
-        long ray = gray - (long)inst * rays_inst;
-        int vs = (int)(ray / a.n_det);
+        const long rays_inst = (long)a.n_sub * a.n_det;
+        const long local = gray - t.begin[c];
+        inst = (int)(local / rays_inst);
+        const long ray = local - (long)inst * rays_inst;
+        const int vs = (int)(ray / a.n_det);
         j = (int)(ray - (long)vs * a.n_det);
         v = a.first_view + vs * a.view_step;
-        out_idx = gray;
+        out_idx = local;
         const float4 f = __ldg(a.rayf + (long)v * a.n_det + j);
         const int2 kr = __ldg(a.rayk + (long)v * a.n_det + j);
         const float4* __restrict__ img = a.quad + (long)inst * a.quad_stride;
@@ -153,19 +179,20 @@ __global__ void __launch_bounds__(256, 4) k_forward(FwdArgs a)
         const int bias = kMagicBits - (qw - 3) / 2;   // column = round(X') + c0
         float kf = (float)(kr.x + q) + 0.5f;
         const float dk = (float)Q;
+        const float step = a.step;
 #pragma unroll 4
         for (int k = kr.x + q; k <= kr.y; k += Q) {
-            const float t = kf * a.step;
-            const float X = fmaf(t, f.z, f.x);
-            const float Y = fmaf(t, f.w, f.y);
+            const float tt = kf * step;
+            const float X = fmaf(tt, f.z, f.x);
+            const float Y = fmaf(tt, f.w, f.y);
             const float mx = __fadd_rn(X, kMagic);
             const float my = __fadd_rn(Y, kMagic);
             const float u = __fsub_rn(X, __fsub_rn(mx, kMagic));
             const float w = __fsub_rn(Y, __fsub_rn(my, kMagic));
             const int ix = __float_as_int(mx) - bias;
             const int iy = __float_as_int(my) - bias;
-            const float4 c = __ldg(img + iy * qw + ix);
-            acc += fmaf(w, fmaf(u, c.w, c.z), fmaf(u, c.y, c.x));
+            const float4 cq = __ldg(img + iy * qw + ix);
+            acc += fmaf(w, fmaf(u, cq.w, cq.z), fmaf(u, cq.y, cq.x));
             kf += dk;
         }
     }
@@ -197,15 +224,29 @@ constexpr int kBack2MaxGroups = 32;
 // projection on the ray: at most floor(2 rho / step) + 1 (9 for step 1/2).
 // Each sample evaluates the two x hats and two y hats once and feeds four
 // products.
+struct BackTable {
+    BackArgs c[kMaxClasses];
+    long begin[kMaxClasses + 1];   // cumulative CTA counts (batch * tiles)
+    int count;
+};
+
 template <int NWIN>
-__global__ void __launch_bounds__(512, 2) k_backward2x2(BackArgs a)
+__global__ void __launch_bounds__(512, 2) k_backward2x2(const BackTable t)
 {
     const int tx = threadIdx.x, ty = threadIdx.y, g = threadIdx.z, G = blockDim.z;
+    int c = 0;
+#pragma unroll
+    for (int k = 1; k < kMaxClasses; ++k)
+        if (k < t.count && (long)blockIdx.x >= t.begin[k]) c = k;
+    const BackArgs& a = t.c[c];
     const int nb = (a.ns + 1) / 2;                             // blocks per side
     const int tiles_x = (nb + kBack2Tile - 1) / kBack2Tile;
-    const int bx = (blockIdx.x % tiles_x) * kBack2Tile + tx;
-    const int by = (blockIdx.x / tiles_x) * kBack2Tile + ty;
-    const int inst = blockIdx.y;
+    const long local = (long)blockIdx.x - t.begin[c];
+    const int tiles = tiles_x * tiles_x;
+    const int inst = (int)(local / tiles);
+    const int tile = (int)(local - (long)inst * tiles);
+    const int bx = (tile % tiles_x) * kBack2Tile + tx;
+    const int by = (tile / tiles_x) * kBack2Tile + ty;
     const bool inside = bx < nb && by < nb;
     __shared__ float4 part[kBack2MaxGroups][kBack2Tile * kBack2Tile];
     float t00 = 0.0f, t10 = 0.0f, t01 = 0.0f, t11 = 0.0f;
@@ -365,47 +406,100 @@ cudaError_t launch_setup_rays(const pnp_geom& g, const LevelLayout& L, char* ws,
     return counted();
 }
 
+cudaError_t launch_prep_multi(const PrepArgs* items, int count, cudaStream_t st)
+{
+    if (count < 1 || count > kMaxClasses) return cudaErrorInvalidValue;
+    PrepTable t{};
+    t.count = count;
+    t.begin[0] = 0;
+    for (int c = 0; c < count; ++c) {
+        t.c[c] = items[c];
+        t.begin[c + 1] = t.begin[c] + (long)items[c].batch * items[c].qw * items[c].qw;
+    }
+    k_prep_quad<<<div_up(t.begin[count], 256), 256, 0, st>>>(t);
+    return counted();
+}
+
 cudaError_t launch_prep_quad(const float* fine, int n, int s, int batch, float4* quad, int qw,
                              cudaStream_t st)
 {
-    dim3 blk(32, 8), grd(div_up(qw, 32), div_up(qw, 8), batch);
-    k_prep_quad<<<grd, blk, 0, st>>>(fine, n, s, qw, quad);
-    return counted();
+    const PrepArgs a{fine, n, s, batch, quad, qw};
+    return launch_prep_multi(&a, 1, st);
 }
 
 template <int Q>
-void forward_q(const FwdArgs& a, long rays, cudaStream_t st)
+void forward_q(const FwdTable& t, cudaStream_t st)
 {
+    const long rays = t.begin[t.count];
     const long warps = (rays + (32 / Q) - 1) / (32 / Q);
-    k_forward<Q><<<div_up(warps * 32, 256), 256, 0, st>>>(a);
+    k_forward<Q><<<div_up(warps * 32, 256), 256, 0, st>>>(t);
 }
 
-cudaError_t launch_forward(const FwdArgs& a, cudaStream_t st)
+cudaError_t launch_forward_multi(const FwdArgs* items, int count, cudaStream_t st, int lanes)
 {
-    // lanes per ray: enough threads to fill the GPU (~2 waves of 152 x 2048)
-    const long rays = (long)a.n_sub * a.n_det * a.batch;
-    if (rays * 4 >= 600000L)
-        forward_q<4>(a, rays, st);
-    else if (rays * 8 >= 600000L)
-        forward_q<8>(a, rays, st);
+    if (count < 1 || count > kMaxClasses) return cudaErrorInvalidValue;
+    FwdTable t{};
+    t.count = count;
+    t.begin[0] = 0;
+    for (int c = 0; c < count; ++c) {
+        t.c[c] = items[c];
+        t.begin[c + 1] = t.begin[c] + (long)items[c].batch * items[c].n_sub * items[c].n_det;
+    }
+    const long rays = t.begin[count];
+    // lanes per ray: enough threads to fill the GPU (~2 waves of 152 x 2048),
+    // unless the autotuner chose
+    int Q = lanes;
+    if (Q != 4 && Q != 8 && Q != 16) Q = rays * 4 >= 600000L ? 4 : rays * 8 >= 600000L ? 8 : 16;
+    if (Q == 4)
+        forward_q<4>(t, st);
+    else if (Q == 8)
+        forward_q<8>(t, st);
     else
-        forward_q<16>(a, rays, st);
+        forward_q<16>(t, st);
     return counted();
 }
 
-cudaError_t launch_backward(const BackArgs& a, cudaStream_t st)
+cudaError_t launch_forward(const FwdArgs& a, cudaStream_t st, int lanes)
 {
-    const int nb = (a.ns + 1) / 2;
-    // view groups: about two waves of 2048 threads per SM, at most 32 per CTA
-    int G = 1;
-    while (G < kBack2MaxGroups && (long)nb * nb * a.batch * G < 2L * 152 * 2048 && G * 2 <= a.n_sub) G *= 2;
-    const int tiles = div_up(nb, kBack2Tile) * div_up(nb, kBack2Tile);
-    dim3 blk(kBack2Tile, kBack2Tile, G), grd(tiles, a.batch);
-    if (a.step == 0.5f)
-        k_backward2x2<9><<<grd, blk, 0, st>>>(a);
+    return launch_forward_multi(&a, 1, st, lanes);
+}
+
+cudaError_t launch_backward_multi(const BackArgs* items, int count, cudaStream_t st, int groups)
+{
+    if (count < 1 || count > kMaxClasses) return cudaErrorInvalidValue;
+    BackTable t{};
+    t.count = count;
+    t.begin[0] = 0;
+    long blocks = 0;
+    int min_views = 1 << 30;
+    bool half_step = true;
+    for (int c = 0; c < count; ++c) {
+        t.c[c] = items[c];
+        const int nb = (items[c].ns + 1) / 2;
+        const int tiles = div_up(nb, kBack2Tile) * div_up(nb, kBack2Tile);
+        t.begin[c + 1] = t.begin[c] + (long)tiles * items[c].batch;
+        blocks += (long)nb * nb * items[c].batch;
+        min_views = min(min_views, items[c].n_sub);
+        half_step = half_step && items[c].step == 0.5f;
+    }
+    // view groups: about two waves of 2048 threads per SM, at most 32 per CTA,
+    // unless the autotuner chose
+    int G = groups;
+    if (G < 1 || G > kBack2MaxGroups || (G & (G - 1))) {
+        G = 1;
+        while (G < kBack2MaxGroups && blocks * G < 2L * 152 * 2048 && G * 2 <= min_views) G *= 2;
+    }
+    dim3 blk(kBack2Tile, kBack2Tile, G), grd((unsigned)t.begin[count]);
+    if (half_step)
+        k_backward2x2<9><<<grd, blk, 0, st>>>(t);
     else
-        k_backward2x2<0><<<grd, blk, 0, st>>>(a);
+        k_backward2x2<0><<<grd, blk, 0, st>>>(t);
     return counted();
+}
+
+cudaError_t launch_backward(const BackArgs& a, cudaStream_t st, int groups)
+{
+    return launch_backward_multi(&a, 1, st, groups);
 }
 
 cudaError_t launch_pool(const float* fine, float* coarse, int n, int s, int batch, cudaStream_t st)

@@ -88,12 +88,19 @@ __global__ void k_tv_final(const float* __restrict__ z, const float* __restrict_
 //                 R_{k-1};  then p, r on R_k.
 // Launches of K <= kTileMaxK iterations are chained through the state buffers
 // (r and p of every tile) when the denoiser needs more iterations.
-struct TileTvArgs {
+struct TileTvClass {
     const float* z; const float* sin; float* sout;   // state planes [4][batch][n][n]: r1 r2 p1 p2
     float* xprev; float* y; const float* xtrue; double* mse_part;
-    int n, T, K, first, last;
+    int n, T, tiles_x, tiles;
     long plane;
-    float lambda, alpha, amom;
+    float amom;
+};
+
+struct TileTvArgs {
+    TileTvClass c[kMaxClasses];
+    long begin[kMaxClasses + 1];                      // cumulative CTA counts (batch * tiles)
+    int count, K, first, last;
+    float lambda, alpha;
     float mom[kTileMaxK];
 };
 
@@ -107,12 +114,19 @@ __host__ __device__ inline int tile_pitch(int S) { return S + ((40 - S % 32) % 3
 // which iterations it is inside the shrinking regions.  Shared memory holds
 // only what neighbours read: r (phase A), x_tmp (phase B) and, at the end, p.
 template <int NP>
-__global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs a)
+__global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
 {
-    const int n = a.n, K = a.K, T = a.T;
-    const int tiles_x = (n + T - 1) / T;
-    const int i0 = (blockIdx.x / tiles_x) * T, j0 = (blockIdx.x % tiles_x) * T;
-    const int inst = blockIdx.y;
+    int cls = 0;
+#pragma unroll
+    for (int k = 1; k < kMaxClasses; ++k)
+        if (k < t.count && (long)blockIdx.x >= t.begin[k]) cls = k;
+    const TileTvClass& a = t.c[cls];
+    const int n = a.n, K = t.K, T = a.T;
+    const int tiles_x = a.tiles_x;
+    const long local = (long)blockIdx.x - t.begin[cls];
+    const int inst = (int)(local / a.tiles);
+    const int tile = (int)(local - (long)inst * a.tiles);
+    const int i0 = (tile / tiles_x) * T, j0 = (tile % tiles_x) * T;
     const int S = T + 1 + 2 * K;                 // side of the loaded region
     const int P = tile_pitch(S);
     const int oi = i0 - 1 - K, oj = j0 - 1 - K;  // its origin (may lie outside the image)
@@ -121,7 +135,7 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs a)
     float* xt = sm + 2 * S * P;                           // x_tmp      [S][P]
     float2* pp = reinterpret_cast<float2*>(sm + 3 * S * P);   // (p1, p2), final step only
     const long img = (long)inst * n * n;
-    const float lam = a.lambda, inv8l = 1.0f / (8.0f * a.lambda);
+    const float lam = t.lambda, inv8l = 1.0f / (8.0f * t.lambda);
     constexpr int kFar = 1 << 20;
 
     float z[NP], r1[NP], r2[NP], p1[NP], p2[NP];
@@ -144,7 +158,7 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs a)
                        (i >= i0 && i < i0 + T && j >= j0 && j < j0 + T ? 16 : 0);
             const long g = img + (long)i * n + j;
             z[m] = __ldg(a.z + g);
-            if (!a.first) {
+            if (!t.first) {
                 r1[m] = __ldg(a.sin + g);
                 r2[m] = __ldg(a.sin + a.plane + g);
                 p1[m] = __ldg(a.sin + 2 * a.plane + g);
@@ -171,7 +185,7 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs a)
         }
         __syncthreads();
         // phase B: dual step, isotropic projection, momentum
-        const float mo = a.mom[k - 1];
+        const float mo = t.mom[k - 1];
 #pragma unroll
         for (int m = 0; m < NP; ++m) {
             if (dB[m] <= mg) {
@@ -194,7 +208,7 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs a)
         }
         __syncthreads();
     }
-    if (!a.last) {
+    if (!t.last) {
 #pragma unroll
         for (int m = 0; m < NP; ++m) {
             if (flags[m] & 16) {
@@ -222,7 +236,7 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs a)
             if (flags[m] & 1) l -= pp[q[m] - P].x;
             if (flags[m] & 2) l -= pp[q[m] - 1].y;
             const float x = z[m] - lam * l;
-            const float xi = (1.0f - a.alpha) * z[m] + a.alpha * x;
+            const float xi = (1.0f - t.alpha) * z[m] + t.alpha * x;
             const int f = threadIdx.x + m * blockDim.x;
             const int li = f / S, lj = f - li * S;
             const long g = img + (long)(oi + li) * n + (oj + lj);
@@ -245,7 +259,7 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs a)
         if (threadIdx.x == 0) {
             double v = 0.0;
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
-            a.mse_part[(long)inst * gridDim.x + blockIdx.x] = v;
+            a.mse_part[(long)inst * a.tiles + tile] = v;
         }
     }
 }
@@ -314,15 +328,16 @@ int choose_tile(int n, int batch)
 
 int tile_tv_tile(int n, int batch) { return choose_tile(n, batch); }
 
-int tile_tv_parts(int n, int batch)
+int tile_tv_parts_for(int n, int batch, int tile)
 {
-    const int T = tile_tv_tile(n, batch);
+    const int T = tile > 0 ? tile : tile_tv_tile(n, batch);
     return ((n + T - 1) / T) * ((n + T - 1) / T);
 }
 
-cudaError_t launch_tv_tiled(const float* z, int n, int batch, float lambda, int iters, float alpha,
-                            float amom, float* xprev, float* y, const float* xtrue, double* mse_part,
-                            float* state_a, float* state_b, cudaStream_t st)
+int tile_tv_parts(int n, int batch) { return tile_tv_parts_for(n, batch, 0); }
+
+cudaError_t launch_tv_tiled_multi(const TvItem* items, int count, float lambda, int iters, float alpha,
+                                  cudaStream_t st)
 {
     static bool attr = false;
     if (!attr) {
@@ -332,48 +347,75 @@ cudaError_t launch_tv_tiled(const float* z, int n, int batch, float lambda, int 
         cudaFuncSetAttribute(k_tv_tile<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemMax);
         attr = true;
     }
-    const int T = tile_tv_tile(n, batch);
-    const int tiles = ((n + T - 1) / T) * ((n + T - 1) / T);
-    if (iters < 1) return cudaErrorInvalidValue;
-    if (iters > kTileKMax && (!state_a || !state_b)) return cudaErrorInvalidValue;   // chaining needs state
+    if (count < 1 || count > kMaxClasses || iters < 1) return cudaErrorInvalidValue;
     std::vector<float> mom((size_t)iters);
-    double t = 1.0;
+    double tt = 1.0;
     for (int k = 0; k < iters; ++k) {
-        const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
-        mom[k] = (float)((t - 1.0) / tn);
-        t = tn;
+        const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * tt * tt));
+        mom[k] = (float)((tt - 1.0) / tn);
+        tt = tn;
     }
     TileTvArgs a{};
-    a.z = z; a.xprev = xprev; a.y = y; a.xtrue = xtrue; a.mse_part = mse_part;
-    a.n = n; a.T = T; a.plane = (long)batch * n * n;
-    a.lambda = lambda; a.alpha = alpha; a.amom = amom;
-    const float* sin = nullptr;
-    float* sout = state_a;
+    a.count = count;
+    a.lambda = lambda;
+    a.alpha = alpha;
+    a.begin[0] = 0;
+    int Tmax = 0;
+    for (int c = 0; c < count; ++c) {
+        const TvItem& it = items[c];
+        int T = it.tile > 0 ? it.tile : tile_tv_tile(it.n, it.batch);
+        if (T < 4 || T > 64 || tile_np(T, kTileKMax) > 4 || tile_smem(T, kTileKMax) > kTileSmemMax)
+            T = tile_tv_tile(it.n, it.batch);
+        if (iters > kTileKMax && (!it.state_a || !it.state_b)) return cudaErrorInvalidValue;   // chaining needs state
+        TileTvClass& tc = a.c[c];
+        tc.z = it.z; tc.xprev = it.xprev; tc.y = it.y; tc.xtrue = it.xtrue; tc.mse_part = it.mse_part;
+        tc.n = it.n; tc.T = T; tc.tiles_x = (it.n + T - 1) / T; tc.tiles = tc.tiles_x * tc.tiles_x;
+        tc.plane = (long)it.batch * it.n * it.n;
+        tc.amom = it.amom;
+        a.begin[c + 1] = a.begin[c] + (long)tc.tiles * it.batch;
+        Tmax = std::max(Tmax, T);
+    }
     int k0 = 0;
+    int pass = 0;
     cudaError_t e = cudaSuccess;
     do {
         const int K = std::min(kTileKMax, iters - k0);
         a.K = K;
         a.first = k0 == 0;
         a.last = k0 + K == iters;
-        a.sin = sin;
-        a.sout = a.last ? nullptr : sout;
+        for (int c = 0; c < count; ++c) {
+            float* sa = items[c].state_a;
+            float* sb = items[c].state_b;
+            a.c[c].sin = k0 == 0 ? nullptr : (pass % 2 == 1 ? sa : sb);
+            a.c[c].sout = a.last ? nullptr : (pass % 2 == 0 ? sa : sb);
+        }
         for (int k = 0; k < K; ++k) a.mom[k] = mom[k0 + k];
-        const dim3 grd(tiles, batch);
-        switch (tile_np(T, K)) {
-            case 1: k_tv_tile<1><<<grd, kTileThreads, tile_smem(T, K), st>>>(a); break;
-            case 2: k_tv_tile<2><<<grd, kTileThreads, tile_smem(T, K), st>>>(a); break;
-            case 3: k_tv_tile<3><<<grd, kTileThreads, tile_smem(T, K), st>>>(a); break;
-            default: k_tv_tile<4><<<grd, kTileThreads, tile_smem(T, K), st>>>(a); break;
+        const dim3 grd((unsigned)a.begin[count]);
+        const size_t sm = tile_smem(Tmax, K);
+        switch (tile_np(Tmax, K)) {
+            case 1: k_tv_tile<1><<<grd, kTileThreads, sm, st>>>(a); break;
+            case 2: k_tv_tile<2><<<grd, kTileThreads, sm, st>>>(a); break;
+            case 3: k_tv_tile<3><<<grd, kTileThreads, sm, st>>>(a); break;
+            default: k_tv_tile<4><<<grd, kTileThreads, sm, st>>>(a); break;
         }
         e = cudaGetLastError();
         g_launches.fetch_add(1, std::memory_order_relaxed);
         if (e != cudaSuccess) return e;
-        sin = sout;
-        sout = sout == state_a ? state_b : state_a;
         k0 += K;
+        ++pass;
     } while (k0 < iters);
     return e;
+}
+
+cudaError_t launch_tv_tiled(const float* z, int n, int batch, float lambda, int iters, float alpha,
+                            float amom, float* xprev, float* y, const float* xtrue, double* mse_part,
+                            float* state_a, float* state_b, cudaStream_t st, int tile)
+{
+    TvItem it{};
+    it.z = z; it.xprev = xprev; it.y = y; it.xtrue = xtrue; it.mse_part = mse_part;
+    it.state_a = state_a; it.state_b = state_b;
+    it.n = n; it.batch = batch; it.tile = tile; it.amom = amom;
+    return launch_tv_tiled_multi(&it, 1, lambda, iters, alpha, st);
 }
 
 }  // namespace pnp

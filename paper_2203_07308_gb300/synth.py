@@ -120,6 +120,26 @@ def workloads() -> dict:
     return w
 
 
+def mixed_classes(n_instances: int = 64, seed: int = 5308):
+    """Uneven serving-style mix: each of ``n_instances`` images draws one of three
+    size classes (128x128 / 180 views x 256 bins, 256x256 / 360 x 512,
+    512x512 / 720 x 768) uniformly with a seeded generator.  Returns
+    [(Workload of that class with batch = its count, instance ids)]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pick = rng.integers(0, 3, size=n_instances)
+    sizes = [(128, 180, 256), (256, 360, 512), (512, 720, 768)]
+    out = []
+    for c, (n, nv, nd) in enumerate(sizes):
+        ids = np.nonzero(pick == c)[0]
+        if ids.size == 0:
+            continue
+        wl = Workload(name=f"{n}x{n}, {nv} views x {nd} bins, {ids.size} images",
+                      geom=make_geometry(n, nv, nd, batch=int(ids.size)), n_ellipses=(15, 20),
+                      noise_rel=0.01, stages=[Stage(2, 20, 8), Stage(1, 30, 8)], config_id=4 + c)
+        out.append((wl, ids))
+    return out
+
+
 def full_gradient_arm(stages: List[Stage]) -> List[Stage]:
     """The unsketched comparison arm (PnP-FISTA with the true gradient, Option 1)
     with the same total iteration count as ``stages``."""

@@ -1,0 +1,150 @@
+"""Batched forms on the GPU: uneven classes of images (size, views, bins) in one
+launch per phase (pnp_run_many), CUDA-graph replay, and autotuned launch
+shapes, each against the FP64 oracle (relative L2 <= 1e-4 on reconstructions)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2203_07308_gb300 as pnp
+from paper_2203_07308_gb300 import build, synth
+
+pytestmark = pytest.mark.gpu
+TOL_RECON = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    pnp.load()
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+def make_problem(g, stages, seed, lam=0.02):
+    x = np.stack([f32(synth.ellipse_phantom(g.n, seed + i, (5, 8))) for i in range(g.batch)])
+    rng = np.random.default_rng(seed)
+    b = f32(np.stack([oracle.project(g, 1, xi) for xi in x]) +
+            0.3 * rng.standard_normal((g.batch, g.n_views, g.n_det)))
+    eta = [1.0 / oracle.power_iter(g, s.factor, 60, 1e-7)[0] for s in stages]
+    seq = synth.schedule_sequence(stages, seed)
+    return x, b, eta, seq
+
+
+def oracle_runs(g, stages, eta, seq, b, x, lam, alpha=1.0, tv_iters=20):
+    refs, logs = [], []
+    for i in range(g.batch):
+        xr, lr = oracle.pnp_run(g, stages, eta, seq, b[i], None, alpha=alpha, lam=lam, tv_iters=tv_iters,
+                                momentum=True, xt=x[i])
+        refs.append(xr)
+        logs.append(lr)
+    return np.stack(refs), np.stack(logs, axis=1)
+
+
+def test_run_many_uneven_classes():
+    """Three classes with different sizes, views, bins, batch sizes and schedule
+    lengths in one call: every phase of every iteration is one launch."""
+    import torch
+    specs = [
+        (synth.make_geometry(32, 20, 48, batch=3), [synth.Stage(2, 3, 4), synth.Stage(1, 4, 4)]),
+        (synth.make_geometry(48, 36, 64, batch=1), [synth.Stage(4, 2, 3), synth.Stage(2, 2, 3), synth.Stage(1, 5, 2)]),
+        (synth.make_geometry(64, 30, 96, batch=2), [synth.Stage(2, 5, 1)]),
+    ]
+    problems, refs = [], []
+    launches0 = pnp.launch_count()
+    for k, (g, stages) in enumerate(specs):
+        x, b, eta, seq = make_problem(g, stages, 100 + 10 * k)
+        plan = pnp.Plan(g)
+        d_x = torch.zeros(g.batch, g.n, g.n, device="cuda")
+        problems.append(dict(plan=plan, stages=stages, eta=eta, seq=seq, b=dev(b), x=d_x, xtrue=dev(x)))
+        refs.append((g, stages, eta, seq, b, x))
+    launches0 = pnp.launch_count()
+    logs = pnp.run_many(problems, lam=0.02, tv_iters=20)
+    launched = pnp.launch_count() - launches0
+    max_iters = max(sum(s.iters for s in st) for _, st in specs)
+    # per iteration: prep, forward, backprojection, two TV launches (10 FGP
+    # iterations each), plus one PSNR reduction per class; one copy per class
+    assert launched <= len(specs) + max_iters * (5 + len(specs)), launched
+    for prob, (g, stages, eta, seq, b, x), log in zip(problems, refs, logs):
+        rx, rl = oracle_runs(g, stages, eta, seq, b, x, 0.02)
+        got = host(prob["x"])
+        assert rel(got, rx) < TOL_RECON, rel(got, rx)
+        assert np.abs(log - rl).max() < 1e-3
+
+
+def test_graph_replay_matches_direct_launches():
+    import torch
+    g = synth.make_geometry(64, 60, 96, batch=2)
+    stages = [synth.Stage(2, 3, 5), synth.Stage(1, 3, 5)]
+    x, b, eta, seq = make_problem(g, stages, 7)
+    plan = pnp.Plan(g)
+    outs = []
+    for graph in (False, True, True):
+        d_x = torch.zeros(g.batch, g.n, g.n, device="cuda")
+        plan.run(stages, eta, seq, dev(b), d_x, graph=graph)
+        outs.append(host(d_x))
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+
+
+def test_autotuned_shapes_keep_parity():
+    import torch
+    g = synth.make_geometry(64, 90, 96, batch=1)
+    stages = [synth.Stage(2, 4, 3), synth.Stage(1, 4, 3)]
+    x, b, eta, seq = make_problem(g, stages, 9)
+    plan = pnp.Plan(g)
+    plan.autotune(stages)
+    d_x = torch.zeros(1, 64, 64, device="cuda")
+    plan.run(stages, eta, seq, dev(b), d_x)
+    rx, _ = oracle_runs(g, stages, eta, seq, b, x, 0.02)
+    assert rel(host(d_x), rx) < TOL_RECON
+
+
+def test_mixed_64_instances_full_size():
+    """The 64-image uneven mix (128/180/256, 256/360/512, 512/720/768) at full
+    size, 50 sketched iterations, one call; sampled 128x128 and 256x256 images
+    against the oracle, every image finite and improved over x_0 = 0."""
+    import torch
+    classes = synth.mixed_classes()
+    problems, meta = [], []
+    for wl, ids in classes:
+        g = wl.geom
+        plan = pnp.Plan(g)
+        xt = np.stack([f32(synth.ellipse_phantom(g.n, synth.phantom_seed(wl.config_id, int(i)), wl.n_ellipses))
+                       for i in ids])
+        d_xt = dev(xt)
+        d_b = torch.empty(g.batch, g.n_views, g.n_det, device="cuda")
+        plan.project(1, d_xt, d_b)
+        rng = np.random.default_rng(wl.config_id)
+        d_b += wl.noise_rel * float(d_b.abs().max()) * dev(rng.standard_normal((g.batch, g.n_views, g.n_det)))
+        eta = [1.0 / plan.power_iter(s.factor, 60, 1e-6)[0] for s in wl.stages]
+        seq = synth.schedule_sequence(wl.stages, wl.config_id)
+        d_x = torch.zeros(g.batch, g.n, g.n, device="cuda")
+        problems.append(dict(plan=plan, stages=wl.stages, eta=eta, seq=seq, b=d_b, x=d_x, xtrue=d_xt))
+        meta.append((wl, xt, host(d_b), eta, seq))
+    logs = pnp.run_many(problems, lam=0.02, tv_iters=20)
+    for prob, (wl, xt, b, eta, seq), log in zip(problems, meta, logs):
+        got = host(prob["x"])
+        assert np.isfinite(got).all()
+        assert (log[-1] > log[0]).all()
+        if wl.geom.n <= 256:
+            rx, _ = oracle.pnp_run(wl.geom, wl.stages, eta, seq, b[0], None, lam=0.02, tv_iters=20,
+                                   momentum=True)
+            assert rel(got[0], rx) < TOL_RECON, (wl.name, rel(got[0], rx))
