@@ -124,6 +124,15 @@ int pnp_workspace_size(const pnp_geom* g, size_t* bytes);
  * Asynchronous on `stream`. */
 int pnp_setup(const pnp_geom* g, void* d_ws, size_t ws_bytes, void* stream);
 
+/* Weighted least squares.  Sec. 3 simulates transmission data b ~ Poisson(I0
+ * exp(-A x)) and takes the logarithm; the matching data fidelity is
+ * f = 1/2 sum_j w_j ((A x)_j - b_j)^2 with w_j the measured counts.  After this
+ * call every gradient, step size (power iteration; instance 0's weights) and
+ * objective computed with d_ws uses the weights d_w [batch][n_views][n_det]
+ * (the caller keeps them alive); pnp_project stays unweighted.  NULL returns to
+ * plain least squares.  pnp_setup clears it. */
+int pnp_set_weights(const pnp_geom* g, const float* d_w, void* d_ws);
+
 /* Forward projection (Eq. 1, Eq. 4): d_sino = A_s^{(p)} d_img, or the residual
  * A_s^{(p)} d_img - b^{(p)} when d_b is not NULL.
  *   factor   sketch level s; d_img is the level-s image [batch][n/s][n/s]

@@ -93,6 +93,12 @@ def _load():
             lib.orc_pnp_run.argtypes = [gp, C.c_int, ip, dp, ip, dp, dp, C.c_double, C.c_double,
                                         C.c_int, C.c_int, dp, dp]
             lib.orc_objective.argtypes = [gp, dp, dp, dp]
+            lib.orc_grad_w.argtypes = [gp, C.c_int, dp, dp, dp, dp, C.c_int, C.c_int]
+            lib.orc_power_iter_w.argtypes = [gp, C.c_int, dp, C.c_int, C.c_double, ip]
+            lib.orc_power_iter_w.restype = C.c_double
+            lib.orc_pnp_run_w.argtypes = [gp, C.c_int, ip, dp, ip, dp, dp, dp, C.c_double, C.c_double,
+                                          C.c_int, C.c_int, dp, dp]
+            lib.orc_objective_w.argtypes = [gp, dp, dp, dp, dp]
             lib.orc_fgp_vjp.argtypes = [C.c_int, dp, C.c_double, C.c_int, dp, dp, dp]
             lib.orc_step.argtypes = [gp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                      C.c_int, C.c_double, dp, dp, dp, dp, dp]
@@ -171,12 +177,14 @@ def unpool(coarse, s: int) -> np.ndarray:
     return out
 
 
-def grad(g, s: int, y, b, p: int = 0, P: int = 1) -> np.ndarray:
-    """c S^T A_s^{(p)T}(A_s^{(p)} S y - b^{(p)}), c = max(P, 1) (Alg. 1 G, U = S^T)."""
+def grad(g, s: int, y, b, p: int = 0, P: int = 1, w=None) -> np.ndarray:
+    """c S^T A_s^{(p)T} W^{(p)}(A_s^{(p)} S y - b^{(p)}), c = max(P, 1) (Alg. 1 G, U = S^T);
+    W = diag(w) (weighted least squares) when w is given, else the identity."""
     y = _f64(y)
     b = _f64(b)
+    ww = None if w is None else _f64(w)
     out = np.zeros((g.n, g.n))
-    _load().orc_grad(C.byref(geom(g)), s, _dp(y), _dp(b), _dp(out), p, P)
+    _load().orc_grad_w(C.byref(geom(g)), s, _dp(y), _dp(b), _dp(ww), _dp(out), p, P)
     return out
 
 
@@ -193,10 +201,11 @@ def tv(x) -> float:
     return float(_load().orc_tv(x.shape[-1], _dp(x)))
 
 
-def power_iter(g, s: int, max_iters: int = 100, tol: float = 1e-7):
-    """(L, iterations): L = ||A_s S||^2 by power iteration (Sec. 3's eta = O(1/L))."""
+def power_iter(g, s: int, max_iters: int = 100, tol: float = 1e-7, w=None):
+    """(L, iterations): L = ||W^{1/2} A_s S||^2 by power iteration (Sec. 3's eta = O(1/L))."""
     it = C.c_int(0)
-    L = _load().orc_power_iter(C.byref(geom(g)), s, max_iters, tol, C.byref(it))
+    ww = None if w is None else _f64(w)
+    L = _load().orc_power_iter_w(C.byref(geom(g)), s, _dp(ww), max_iters, tol, C.byref(it))
     return float(L), int(it.value)
 
 
@@ -207,7 +216,7 @@ def psnr(x, xt) -> float:
 
 
 def pnp_run(g, stages: Sequence, eta: Sequence[float], seq, b, x0=None, *, alpha: float = 1.0,
-            lam: float = 0.02, tv_iters: int = 20, momentum: bool = True, xt=None):
+            lam: float = 0.02, tv_iters: int = 20, momentum: bool = True, xt=None, w=None):
     """Algorithm 1 on one image; returns (x, psnr_log or None)."""
     st = np.ascontiguousarray(np.array([[s.factor, s.iters, s.n_subsets] if hasattr(s, "factor")
                                          else list(s) for s in stages], dtype=np.int32).ravel())
@@ -221,18 +230,20 @@ def pnp_run(g, stages: Sequence, eta: Sequence[float], seq, b, x0=None, *, alpha
     xt_ = None if xt is None else _f64(xt)
     log = np.zeros(total) if xt is not None else None
     ip = C.POINTER(C.c_int)
-    _load().orc_pnp_run(C.byref(geom(g)), len(st) // 3, st.ctypes.data_as(ip), _dp(eta),
-                        seq.ctypes.data_as(ip), _dp(b), _dp(x), float(alpha), float(lam),
-                        int(tv_iters), int(bool(momentum)), _dp(xt_), _dp(log))
+    ww = None if w is None else _f64(w)
+    _load().orc_pnp_run_w(C.byref(geom(g)), len(st) // 3, st.ctypes.data_as(ip), _dp(eta),
+                          seq.ctypes.data_as(ip), _dp(b), _dp(ww), _dp(x), float(alpha), float(lam),
+                          int(tv_iters), int(bool(momentum)), _dp(xt_), _dp(log))
     return x, log
 
 
-def objective(g, x, b):
-    """(1/2 ||A x - b||^2, TV(x))."""
+def objective(g, x, b, w=None):
+    """(1/2 sum_j w_j (A x - b)_j^2, TV(x)); w = 1 when not given."""
     out = np.zeros(2)
     x = _f64(x)
     b = _f64(b)
-    _load().orc_objective(C.byref(geom(g)), _dp(x), _dp(b), _dp(out))
+    ww = None if w is None else _f64(w)
+    _load().orc_objective_w(C.byref(geom(g)), _dp(x), _dp(b), _dp(ww), _dp(out))
     return float(out[0]), float(out[1])
 
 

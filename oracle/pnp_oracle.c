@@ -214,8 +214,23 @@ void orc_unpool(int n, int s, const double *coarse, double *fine)
  * angle subset p of P otherwise):
  *     g = c * S^T A_s^{(p)T} (A_s^{(p)} S y - b^{(p)}),   c = max(P, 1).
  * For s = 1 and P <= 1 this is the full gradient A^T (A y - b) of Eq. 5. */
-void orc_grad(const orc_geom *g, int s, const double *y, const double *b, double *grad,
-              int p, int P)
+static void apply_weights(const orc_geom *g, const double *w, double *res, int p, int P)
+{
+    if (!w) return;
+    int nsub = orc_subset_views(g, p, P);
+    int step = P <= 1 ? 1 : P;
+    int first = P <= 1 ? 0 : p;
+    for (int vs = 0; vs < nsub; ++vs)
+        for (int j = 0; j < g->n_det; ++j)
+            res[(long)vs * g->n_det + j] *= w[(long)(first + vs * step) * g->n_det + j];
+}
+
+/* Weighted variant (w nullable, full [n_views][n_det]): the data fidelity is
+ * 1/2 sum_j w_j (A x - b)_j^2, the weighted least squares of transmission CT
+ * with Poisson counts (Sec. 3's b ~ Poisson(I0 exp(-A x)) after the log), so
+ * the gradient is c S^T A_s^{(p)T} W^{(p)} (A_s^{(p)} S y - b^{(p)}). */
+void orc_grad_w(const orc_geom *g, int s, const double *y, const double *b, const double *w,
+                double *grad, int p, int P)
 {
     int n = g->n, ns = n / s;
     int nsub = orc_subset_views(g, p, P);
@@ -224,6 +239,7 @@ void orc_grad(const orc_geom *g, int s, const double *y, const double *b, double
     double *gc = malloc(sizeof(double) * (size_t)ns * ns);
     orc_pool(n, s, y, v);
     orc_project(g, s, v, b, res, p, P);
+    apply_weights(g, w, res, p, P);
     orc_backproject(g, s, res, gc, p, P);
     orc_unpool(n, s, gc, grad);
     double c = P <= 1 ? 1.0 : (double)P;
@@ -231,6 +247,11 @@ void orc_grad(const orc_geom *g, int s, const double *y, const double *b, double
     free(v);
     free(res);
     free(gc);
+}
+
+void orc_grad(const orc_geom *g, int s, const double *y, const double *b, double *grad, int p, int P)
+{
+    orc_grad_w(g, s, y, b, NULL, grad, p, P);
 }
 
 /* ---------------- TV prox by FGP (Beck & Teboulle 2009) -------------------
@@ -322,7 +343,17 @@ double orc_tv(int m, const double *x)
 /* L = ||A_s S||^2 by power iteration on S^T A_s^T A_s S from the normalised
  * all-ones vector; stops when the Rayleigh quotient changes by less than tol
  * (relative) or after max_iters.  Returns L; *iters_out = iterations used. */
+double orc_power_iter_w(const orc_geom *g, int s, const double *wts, int max_iters, double tol,
+                        int *iters_out);
+
 double orc_power_iter(const orc_geom *g, int s, int max_iters, double tol, int *iters_out)
+{
+    return orc_power_iter_w(g, s, NULL, max_iters, tol, iters_out);
+}
+
+/* L = ||W^{1/2} A_s S||^2 (wts nullable: W = I). */
+double orc_power_iter_w(const orc_geom *g, int s, const double *wts, int max_iters, double tol,
+                        int *iters_out)
 {
     int n = g->n, ns = n / s;
     size_t N = (size_t)n * n;
@@ -335,6 +366,7 @@ double orc_power_iter(const orc_geom *g, int s, int max_iters, double tol, int *
     for (it = 1; it <= max_iters; ++it) {
         orc_pool(n, s, u, v);
         orc_project(g, s, v, NULL, res, 0, 1);
+        apply_weights(g, wts, res, 0, 1);
         orc_backproject(g, s, res, gc, 0, 1);
         orc_unpool(n, s, gc, w);
         double rq = 0.0, nw = 0.0;
@@ -371,9 +403,21 @@ double orc_psnr(long count, const double *x, const double *xt)
  * Iteration i = 1, 2, ...:  v = S_k y_{i-1};  G per Option 1/2;
  *   z_i = y_{i-1} - eta_k S_k^T G;  x_i = (1-alpha) z_i + alpha D(z_i);
  *   y_i = x_i + a_i (x_i - x_{i-1}).                                          */
+void orc_pnp_run_w(const orc_geom *g, int n_stages, const int *stages, const double *eta,
+                   const int *seq, const double *b, const double *w, double *x, double alpha,
+                   double lambda, int tv_iters, int momentum, const double *xt, double *psnr);
+
 void orc_pnp_run(const orc_geom *g, int n_stages, const int *stages, const double *eta,
                  const int *seq, const double *b, double *x, double alpha, double lambda,
                  int tv_iters, int momentum, const double *xt, double *psnr)
+{
+    orc_pnp_run_w(g, n_stages, stages, eta, seq, b, NULL, x, alpha, lambda, tv_iters, momentum, xt, psnr);
+}
+
+/* Algorithm 1 with the weighted data fidelity (w nullable). */
+void orc_pnp_run_w(const orc_geom *g, int n_stages, const int *stages, const double *eta,
+                   const int *seq, const double *b, const double *w, double *x, double alpha,
+                   double lambda, int tv_iters, int momentum, const double *xt, double *psnr)
 {
     int n = g->n;
     size_t N = (size_t)n * n;
@@ -388,7 +432,7 @@ void orc_pnp_run(const orc_geom *g, int n_stages, const int *stages, const doubl
         for (int jj = 0; jj < Nk; ++jj) {
             i += 1;
             int p = P > 1 ? seq[i - 1] : 0;
-            orc_grad(g, s, y, b, gr, p, P);
+            orc_grad_w(g, s, y, b, w, gr, p, P);
             for (size_t q = 0; q < N; ++q) z[q] = y[q] - eta[k] * gr[q];
             orc_fgp(n, z, lambda, tv_iters, dz);
             double a = momentum ? (double)(i - 1) / (double)(i + 3) : 0.0;
@@ -405,13 +449,23 @@ void orc_pnp_run(const orc_geom *g, int n_stages, const int *stages, const doubl
 }
 
 /* Objective terms: 1/2 ||A x - b||^2 and TV(x) (Eq. 2 with f least squares). */
+void orc_objective_w(const orc_geom *g, const double *x, const double *b, const double *w,
+                     double out[2]);
+
 void orc_objective(const orc_geom *g, const double *x, const double *b, double out[2])
+{
+    orc_objective_w(g, x, b, NULL, out);
+}
+
+/* (1/2 sum_j w_j (A x - b)_j^2, TV(x)); w nullable. */
+void orc_objective_w(const orc_geom *g, const double *x, const double *b, const double *w,
+                     double out[2])
 {
     size_t M = (size_t)g->n_views * g->n_det;
     double *res = malloc(sizeof(double) * M);
     orc_project(g, 1, x, b, res, 0, 1);
     double f = 0.0;
-    for (size_t i = 0; i < M; ++i) f += res[i] * res[i];
+    for (size_t i = 0; i < M; ++i) f += (w ? w[i] : 1.0) * res[i] * res[i];
     out[0] = 0.5 * f;
     out[1] = orc_tv(g->n, x);
     free(res);

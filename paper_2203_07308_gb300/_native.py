@@ -100,6 +100,7 @@ def load(path: Optional[str] = None):
             "pnp_sample_count": [gp, i32, i32, i32, dp, vp, vp],
             "pnp_full_grad_noalloc": [gp, vp, vp, vp, vp],
             "pnp_run_many": [C.POINTER(ProblemC), i32, C.POINTER(RunParams), vp],
+            "pnp_set_weights": [gp, vp, vp],
             "pnp_autotune": [gp, C.POINTER(StageC), i32, C.POINTER(RunParams), vp, vp],
             "pnp_tv_vjp_workspace_size": [i32, i32, i32, C.POINTER(sz)],
             "pnp_tv_vjp": [vp, vp, vp, dp, i32, i32, C.c_float, i32, vp, sz, vp],
@@ -339,6 +340,12 @@ class Plan:
 
     def autotune(self, stages, **kw):
         autotune(self.g, stages, self.ws, **kw)
+
+    def set_weights(self, w):
+        """Weighted least squares for every gradient of this plan (None: unweighted)."""
+        self.weights = w
+        p = None if w is None else _ptr(w, self.g.batch * self.g.n_views * self.g.n_det, "w")
+        _check(load().pnp_set_weights(C.byref(self.cg), p, _ws(self.ws)[0]))
 
     def objective(self, x, b, xtrue=None, stream=None):
         return objective(self.g, x, b, xtrue, self.ws, stream)

@@ -153,7 +153,7 @@ struct Tuned {
     int tile = 0;                            // tiled FGP: tile side
 };
 
-struct RegEntry { const void* ws; uint64_t fp; size_t bytes; Tuned tuned; };
+struct RegEntry { const void* ws; uint64_t fp; size_t bytes; Tuned tuned; const float* weights; };
 std::mutex g_reg_mu;
 std::vector<RegEntry> g_reg;
 
@@ -161,9 +161,9 @@ void reg_put(const void* ws, uint64_t fp, size_t bytes)
 {
     std::lock_guard<std::mutex> lk(g_reg_mu);
     for (auto& e : g_reg)
-        if (e.ws == ws) { e.fp = fp; e.bytes = bytes; e.tuned = Tuned(); return; }
+        if (e.ws == ws) { e.fp = fp; e.bytes = bytes; e.tuned = Tuned(); e.weights = nullptr; return; }
     if (g_reg.size() >= 4096) g_reg.erase(g_reg.begin());
-    g_reg.push_back({ws, fp, bytes, Tuned()});
+    g_reg.push_back({ws, fp, bytes, Tuned(), nullptr});
 }
 
 Tuned reg_tuned(const void* ws)
@@ -172,6 +172,21 @@ Tuned reg_tuned(const void* ws)
     for (const auto& e : g_reg)
         if (e.ws == ws) return e.tuned;
     return Tuned();
+}
+
+const float* reg_weights(const void* ws)
+{
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    for (const auto& e : g_reg)
+        if (e.ws == ws) return e.weights;
+    return nullptr;
+}
+
+void reg_set_weights(const void* ws, const float* w)
+{
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    for (auto& e : g_reg)
+        if (e.ws == ws) e.weights = w;
 }
 
 void reg_set_tuned(const void* ws, const Tuned& t)
@@ -221,9 +236,10 @@ inline cudaStream_t S(void* st) { return (cudaStream_t)st; }
 
 // Forward residual r = A_s^{(p)} (level image in quad) - b^{(p)} into the workspace.
 FwdArgs fwd_args(const pnp_geom& g, const LevelLayout& lv, char* ws, int p, int P, const float* b,
-                 float* out, int batch)
+                 float* out, int batch, const float* w = nullptr)
 {
     FwdArgs a{};
+    a.w = w;
     a.quad = (const float4*)(ws + lv.off_quad);
     a.qw = lv.qw;
     a.quad_stride = (size_t)lv.qw * lv.qw;
@@ -276,7 +292,7 @@ int grad_into(const pnp_geom& g, const Layout& L, int li, char* ws, const float*
     const Tuned tu = reg_tuned(ws);
     float* res = (float*)(ws + L.off_res);
     PNP_CUDA(launch_prep_quad(y, g.n, lv.factor, g.batch, (float4*)(ws + lv.off_quad), lv.qw, st));
-    PNP_CUDA(launch_forward(fwd_args(g, lv, ws, p, P, b, res, g.batch), st, tu.lanes[li]));
+    PNP_CUDA(launch_forward(fwd_args(g, lv, ws, p, P, b, res, g.batch, reg_weights(ws)), st, tu.lanes[li]));
     const double c = P <= 1 ? 1.0 : (double)P;
     const float scale = (float)(g.step * lv.factor * c / ((double)lv.factor * lv.factor));
     PNP_CUDA(launch_backward(back_args(g, lv, ws, p, P, res, mode, scale, y, eta, out, g.batch), st,
@@ -529,7 +545,7 @@ int pnp_power_iter(const pnp_geom* g, int factor, int max_iters, double tol, dou
     int it = 0;
     for (it = 1; it <= max_iters; ++it) {
         PNP_CUDA(launch_prep_quad(u, g->n, lv.factor, 1, (float4*)(ws + lv.off_quad), lv.qw, st));
-        PNP_CUDA(launch_forward(fwd_args(g1, lv, ws, 0, 1, nullptr, res, 1), st));
+        PNP_CUDA(launch_forward(fwd_args(g1, lv, ws, 0, 1, nullptr, res, 1, reg_weights(ws)), st));
         PNP_CUDA(launch_backward(back_args(g1, lv, ws, 0, 1, res, kBackGradFine, scale, nullptr, 0.0f, w, 1), st));
         PNP_CUDA(launch_reduce_partial(kRedDot, u, w, N, N, 1, g->n, part, st));
         PNP_CUDA(launch_reduce_final(part, kRedBlocks, 1, outv, 1, 0, st));
@@ -655,7 +671,7 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
                 float* z = (float*)(ws + L.off_z);
                 float* res = (float*)(ws + L.off_res);
                 prep[na] = PrepArgs{y, g.n, lv.factor, g.batch, (float4*)(ws + lv.off_quad), lv.qw};
-                fwd[na] = fwd_args(g, lv, ws, p, P, q.d_b, res, g.batch);
+                fwd[na] = fwd_args(g, lv, ws, p, P, q.d_b, res, g.batch, reg_weights(ws));
                 const double cs = P <= 1 ? 1.0 : (double)P;
                 const float scale = (float)(g.step * lv.factor * cs / ((double)lv.factor * lv.factor));
                 back[na] = back_args(g, lv, ws, p, P, res, kBackStep, scale, y, (float)q.h_eta[stage[c]], z, g.batch);
@@ -716,6 +732,7 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
         h.add(q.h_eta, sizeof(double) * (size_t)q.n_stages);
         if (q.h_subset_seq) h.add(q.h_subset_seq, sizeof(int32_t) * (size_t)ps[c].total);
         h.val(ps[c].tuned);
+        h.val(reg_weights(q.d_ws));
     }
     if (int e = run_maybe_graph((pr.flags & PNP_RUN_GRAPH) != 0, h.h, st, issue)) return e;
 
@@ -753,6 +770,15 @@ int pnp_run(const pnp_geom* g, const pnp_stage* stages, int n_stages, const doub
     q.h_psnr_log = h_psnr_log;
     q.d_ws = d_ws;
     return run_many_impl(&q, 1, params, stream);
+}
+
+int pnp_set_weights(const pnp_geom* g, const float* d_w, void* d_ws)
+{
+    t_err.clear();
+    if (int e = validate_geom(g)) return e;
+    if (int e = check_ws(*g, d_ws)) return e;
+    reg_set_weights(d_ws, d_w);
+    return PNP_OK;
 }
 
 int pnp_run_many(const pnp_problem* problems, int n_problems, const pnp_run_params* params, void* stream)
@@ -861,7 +887,10 @@ int pnp_objective(const pnp_geom* g, const float* d_x, const float* d_b, const f
     const size_t nr = (size_t)g->n_views * g->n_det, N = (size_t)g->n * g->n;
     PNP_CUDA(launch_prep_quad(d_x, g->n, 1, g->batch, (float4*)(ws + lv.off_quad), lv.qw, st));
     PNP_CUDA(launch_forward(fwd_args(*g, lv, ws, 0, 1, d_b, res, g->batch), st));
-    PNP_CUDA(launch_reduce_partial(kRedSq, res, nullptr, nr, nr, g->batch, g->n, part, st));
+    if (const float* wts = reg_weights(ws))
+        PNP_CUDA(launch_reduce_partial(kRedWSq, res, wts, nr, nr, g->batch, g->n, part, st));
+    else
+        PNP_CUDA(launch_reduce_partial(kRedSq, res, nullptr, nr, nr, g->batch, g->n, part, st));
     PNP_CUDA(launch_reduce_final(part, kRedBlocks, g->batch, outv, 8, 0, st));
     PNP_CUDA(launch_reduce_partial(kRedTv, d_x, nullptr, N, N, g->batch, g->n, part, st));
     PNP_CUDA(launch_reduce_final(part, kRedBlocks, g->batch, outv, 8, 1, st));

@@ -86,6 +86,7 @@ struct FwdArgs {
     float step, weight;
     const float* b; int n_views;     // b: [batch][n_views][n_det] or null
     float* out;                      // [batch][n_sub][n_det]
+    const float* w;                  // null or weights [batch][n_views][n_det]: out = w (A x - b)
 };
 cudaError_t launch_forward(const FwdArgs& a, cudaStream_t st, int lanes = 0);
 cudaError_t launch_forward_multi(const FwdArgs* items, int count, cudaStream_t st, int lanes = 0);
@@ -147,7 +148,7 @@ cudaError_t launch_axpby(const float* a, float c1, const float* b, float c2, flo
                          cudaStream_t st);
 
 // Reductions -------------------------------------------------------------------
-enum RedMode { kRedDot = 0, kRedDiffSq = 1, kRedSq = 2, kRedTv = 3 };
+enum RedMode { kRedDot = 0, kRedDiffSq = 1, kRedSq = 2, kRedTv = 3, kRedWSq = 4 };   // kRedWSq: sum b a^2
 // partials[inst][kRedBlocks] for `count` elements per instance (stride `stride`).
 cudaError_t launch_reduce_partial(int mode, const float* a, const float* b, size_t count,
                                   size_t stride, int batch, int n, double* partials, cudaStream_t st);

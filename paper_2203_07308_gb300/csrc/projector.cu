@@ -205,8 +205,10 @@ __global__ void __launch_bounds__(256, 4) k_forward(const FwdTable t)
 #pragma unroll
     for (int o = Q / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (active && q == 0) {
+        const long bi = ((long)inst * a.n_views + v) * a.n_det + j;
         float val = a.weight * acc;
-        if (a.b) val -= __ldg(a.b + ((long)inst * a.n_views + v) * a.n_det + j);
+        if (a.b) val -= __ldg(a.b + bi);
+        if (a.w) val *= __ldg(a.w + bi);
         a.out[out_idx] = val;
     }
 }

@@ -42,6 +42,7 @@ __global__ void k_reduce_partial(int mode, const float* __restrict__ a, const fl
             case kRedDot: acc += x * (double)__ldg(B + i); break;
             case kRedDiffSq: { double d = x - (double)__ldg(B + i); acc += d * d; } break;
             case kRedSq: acc += x * x; break;
+            case kRedWSq: acc += (double)__ldg(B + i) * x * x; break;
             default: {
                 const size_t r = i / n, c = i % n;
                 double gy = r + 1 < (size_t)n ? (double)__ldg(A + i + n) - x : 0.0;

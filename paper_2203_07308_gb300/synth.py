@@ -120,6 +120,41 @@ def workloads() -> dict:
     return w
 
 
+def paper_workloads() -> dict:
+    """The three fan-beam set-ups of the paper's Sec. 3 (256x256 images, 228 bins
+    so that A has 20520 or 82080 rows), on a synthetic disk-and-ellipse phantom
+    (the head and chest images are not available), with Poisson transmission
+    noise of the stated I0 and the paper's two-stage sketch (m_1 = d/16, then
+    m_2 = d/4, Option 1).  Stage lengths are not given in the paper."""
+    stages = [Stage(4, 30, 1), Stage(2, 70, 1)]
+    return {
+        "sparse_view": (Workload(name="sparse-view: 90 views over [0, 360), I0 = 10^5.5",
+                                 geom=make_geometry(256, 90, 228), n_ellipses=(15, 20), noise_rel=0.0,
+                                 stages=stages, config_id=10), 10 ** 5.5),
+        "low_dose": (Workload(name="low-dose: 360 views over [0, 360), I0 = 10^3.5",
+                              geom=make_geometry(256, 360, 228), n_ellipses=(15, 20), noise_rel=0.0,
+                              stages=stages, config_id=11), 10 ** 3.5),
+        "limited_angle": (Workload(name="limited-angle: 90 views over [0, 180), I0 = 10^5.5",
+                                   geom=make_geometry(256, 90, 228, angle_span=math.pi), n_ellipses=(15, 20),
+                                   noise_rel=0.0, stages=stages, config_id=12), 10 ** 5.5),
+    }
+
+
+def poisson_transmission(line_integrals: np.ndarray, i0: float, seed: int, mu: float = 0.02):
+    """Transmission data of Sec. 3: counts ~ Poisson(I0 exp(-mu * A x)) and their
+    log, b = -log(counts / I0) / mu, with the counts as weighted-least-squares
+    weights (counts below 1 are raised to 1 before the log).  ``mu`` converts
+    the phantom's unit intensities and pixel-length line integrals into an
+    attenuation, so that the counts stay in a realistic range.  Returns
+    (b, w) as float64 arrays shaped like ``line_integrals``."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    expected = i0 * np.exp(-mu * np.asarray(line_integrals, dtype=np.float64))
+    counts = np.maximum(rng.poisson(expected).astype(np.float64), 1.0)
+    b = -np.log(counts / i0) / mu
+    w = counts * mu * mu
+    return b, w
+
+
 def mixed_classes(n_instances: int = 64, seed: int = 5308):
     """Uneven serving-style mix: each of ``n_instances`` images draws one of three
     size classes (128x128 / 180 views x 256 bins, 256x256 / 360 x 512,

@@ -41,6 +41,8 @@ MUTATIONS = [
     ("fgp vjp projection jacobian", "abar[i] = (pbar[i] - h1 * d) / nrm;", "abar[i] = (pbar[i] + h1 * d) / nrm;"),
     ("fgp vjp lambda term", "*lambar -= dz / (8.0 * lambda * lambda);", "*lambar += dz / (8.0 * lambda * lambda);"),
     ("step vjp momentum", "xt[i] = xbar[i] + (1.0 + amom) * ybar[i];", "xt[i] = xbar[i] + amom * ybar[i];"),
+    ("weights on the wrong views", "res[(long)vs * g->n_det + j] *= w[(long)(first + vs * step) * g->n_det + j];",
+     "res[(long)vs * g->n_det + j] *= w[(long)vs * g->n_det + j];"),
 ]
 
 

@@ -532,3 +532,48 @@ def test_sample_count_near_estimate():
     g = synth.make_geometry(64, 90, 96)
     cnt = oracle.sample_count(g)
     assert 7.0e5 < cnt < 8.5e5
+
+
+# ---------------------------------------------------------------- weighted least squares (Poisson data)
+@pytest.mark.parametrize("s,P,p", [(1, 1, 0), (2, 4, 3)])
+def test_weighted_gradient_matches_finite_differences(s, P, p):
+    """With weights w the gradient is that of (c/2) sum_j w_j r_j^2 on the subset rows."""
+    g = synth.make_geometry(16, 16, 24)
+    rng = np.random.default_rng(70 + s)
+    y = rng.random((16, 16))
+    b = rng.standard_normal((g.n_views, g.n_det)) * 3
+    w = rng.uniform(0.2, 3.0, (g.n_views, g.n_det))
+    c = max(P, 1)
+    rows = np.arange(g.n_views)[p::P] if P > 1 else np.arange(g.n_views)
+
+    def f(yy):
+        r = oracle.project(g, s, oracle.pool(yy, s), b, p, P)
+        return 0.5 * c * np.sum(w[rows] * r * r)
+
+    gr = oracle.grad(g, s, y, b, p, P, w=w)
+    h = 1e-3
+    for _ in range(3):
+        d = rng.standard_normal((16, 16))
+        fd = (f(y + h * d) - f(y - h * d)) / (2 * h)
+        assert abs(fd - np.vdot(gr, d)) < 1e-8 * max(abs(fd), 1.0)
+    # unit weights reduce to the unweighted gradient
+    assert np.abs(oracle.grad(g, s, y, b, p, P, w=np.ones_like(w)) - oracle.grad(g, s, y, b, p, P)).max() == 0.0
+
+
+def test_weighted_power_iteration_matches_dense(g16, dense16):
+    rng = np.random.default_rng(80)
+    w = rng.uniform(0.5, 2.0, (g16.n_views, g16.n_det))
+    A = dense16[1]
+    M = np.sqrt(w.ravel())[:, None] * A
+    lmax = np.linalg.eigvalsh(M.T @ M).max()
+    L, _ = oracle.power_iter(g16, 1, 3000, 1e-14, w=w)
+    assert abs(L - lmax) < 1e-8 * lmax
+
+
+def test_weighted_objective():
+    g = synth.make_geometry(24, 16, 32)
+    x = synth.ellipse_phantom(24, 81, (3, 3))
+    b = oracle.project(g, 1, x) + 0.5
+    w = np.full((16, 32), 3.0)
+    f, _ = oracle.objective(g, x, b, w)
+    assert abs(f - 0.5 * 3.0 * 0.25 * b.size) < 1e-9
