@@ -296,9 +296,9 @@ int pnp_unrolled_step_vjp(const pnp_geom* g, int factor, int subset, int n_subse
  * The paper has no counterpart; it is an interface for such callers.
  *   It allocates nothing and takes no workspace: its scratch lives in a fixed
  *   PNP_NOALLOC_SCRATCH_BYTES array compiled into the library.  A geometry needs
- *   24 B per ray and 16 B per view (ray tables), plus per batch image 32 (n+3)^2 B
- *   (coefficient image and its transpose) and 4 B per ray (residual), each part
- *   rounded up to 256 B; e.g. 256x256 with 360 views x 512 bins needs about 7.4 MB.
+ *   24 B per ray and 16 B per view (ray tables), plus per batch image 16 (n+3)^2 B
+ *   (coefficient image) and 4 B per ray (residual), each part rounded up to
+ *   256 B; e.g. 256x256 with 360 views x 512 bins needs about 6.3 MB.
  *   Geometries that need more are rejected with PNP_EINVAL and a message.
  *   The first call on a device looks up the array's device address (once per
  *   device, with that device current); make that first call before any stream

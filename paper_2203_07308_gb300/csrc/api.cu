@@ -110,7 +110,7 @@ Layout make_layout(const pnp_geom& g)
         v.off_rayi = off; off = align_up(off + nr * sizeof(float2));
         v.off_rayk = off; off = align_up(off + nr * sizeof(int2));
         v.off_view = off; off = align_up(off + (size_t)g.n_views * sizeof(float4));
-        v.off_quad = off; off = align_up(off + 2 * (size_t)g.batch * v.qw * v.qw * sizeof(float4));
+        v.off_quad = off; off = align_up(off + (size_t)g.batch * v.qw * v.qw * sizeof(float4));
     }
     const size_t img = (size_t)g.batch * g.n * g.n;
     L.off_res = off; off = align_up(off + (size_t)g.batch * nr * sizeof(float));

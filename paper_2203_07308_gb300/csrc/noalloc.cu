@@ -66,7 +66,7 @@ static size_t noalloc_bytes(const pnp_geom* g)
     off = up256(off + nr * sizeof(float2));                                 // rayi
     off = up256(off + nr * sizeof(int2));                                   // rayk
     off = up256(off + (size_t)g->n_views * sizeof(float4));                 // view
-    off = up256(off + 2 * (size_t)g->batch * qw * qw * sizeof(float4));     // quad and its transpose
+    off = up256(off + (size_t)g->batch * qw * qw * sizeof(float4));         // quad
     off = up256(off + (size_t)g->batch * nr * sizeof(float));               // residual
     return off;
 }
@@ -98,7 +98,7 @@ extern "C" int pnp_full_grad_noalloc(const pnp_geom* g, const float* d_x, const 
     lv.off_rayi = off; off = up256(off + nr * sizeof(float2));
     lv.off_rayk = off; off = up256(off + nr * sizeof(int2));
     lv.off_view = off; off = up256(off + (size_t)g->n_views * sizeof(float4));
-    lv.off_quad = off; off = up256(off + 2 * (size_t)g->batch * lv.qw * lv.qw * sizeof(float4));
+    lv.off_quad = off; off = up256(off + (size_t)g->batch * lv.qw * lv.qw * sizeof(float4));
     float* res = (float*)(ws + off);
     cudaError_t e = launch_setup_rays(*g, lv, ws, st);
     if (e == cudaSuccess)

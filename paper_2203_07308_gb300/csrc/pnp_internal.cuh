@@ -7,8 +7,7 @@
 //   rayi  float2 [n_views*n_det]  (1/d_x, 1/d_y), clamped away from 0
 //   rayk  int2   [n_views*n_det]  first/last sample index k inside the image box
 //   view  float4 [n_views]        (cos b, sin b, dso/s, (dso+ddo)/pitch)
-//   quad  float4 [2][batch][(n_s+3)^2] bilinear coefficients of the level image,
-//                                 row-major then transposed
+//   quad  float4 [batch][(n_s+3)^2] bilinear coefficients of the level image
 // then the residual sinogram, the fine-grid loop buffers, the TV buffers, the
 // power-iteration vectors and the FP64 reduction scratch.
 //

@@ -86,7 +86,7 @@ __global__ void k_setup_rays(int n, int s, int n_views, int n_det, double dso, d
 }
 
 // ------------------------------------------------------------------ coefficient image
-// quad[iy0+2][ix0+2] (and, after the batch, its transpose) holds the bilinear coefficients of the cell whose lower
+// quad[iy0+2][ix0+2] holds the bilinear coefficients of the cell whose lower
 // corner is level pixel (ix0, iy0), in the centred variables u, w in [-1/2, 1/2]:
 //   f = c0 + u c1 + w (c2 + u c3)
 // with a = I(ix0,iy0), b = I(ix0+1,iy0), c = I(ix0,iy0+1), d = I(ix0+1,iy0+1)
@@ -134,8 +134,6 @@ __global__ void k_prep_quad(const PrepTable t)
     q.z = 0.5f * ((pc - pa) + (pd - pb));
     q.w = (pa - pb) - (pc - pd);
     a.quad[local] = q;
-    // transposed copy (row = column index), read by rays steeper than 45 degrees
-    a.quad[(long)a.batch * cells + (long)inst * cells + (long)qx * qw + qy] = q;
 }
 
 // ------------------------------------------------------------------ forward A_s
@@ -176,11 +174,7 @@ __global__ void __launch_bounds__(256, 4) k_forward(const FwdTable t)
         out_idx = local;
         const float4 f = __ldg(a.rayf + (long)v * a.n_det + j);
         const int2 kr = __ldg(a.rayk + (long)v * a.n_det + j);
-        // rays steeper than 45 degrees read the transposed copy, so a warp's
-        // consecutive samples walk along the fast axis of the image
-        const bool steep = fabsf(f.w) > fabsf(f.z);
-        const float4* __restrict__ img = a.quad + (long)inst * a.quad_stride +
-                                         (steep ? (long)a.batch * a.quad_stride : 0L);
+        const float4* __restrict__ img = a.quad + (long)inst * a.quad_stride;
         const int qw = a.qw;
         const int bias = kMagicBits - (qw - 3) / 2;   // column = round(X') + c0
         float kf = (float)(kr.x + q) + 0.5f;
@@ -197,7 +191,7 @@ __global__ void __launch_bounds__(256, 4) k_forward(const FwdTable t)
             const float w = __fsub_rn(Y, __fsub_rn(my, kMagic));
             const int ix = __float_as_int(mx) - bias;
             const int iy = __float_as_int(my) - bias;
-            const float4 cq = __ldg(img + (steep ? ix * qw + iy : iy * qw + ix));
+            const float4 cq = __ldg(img + iy * qw + ix);
             acc += fmaf(w, fmaf(u, cq.w, cq.z), fmaf(u, cq.y, cq.x));
             kf += dk;
         }

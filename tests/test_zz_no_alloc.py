@@ -63,7 +63,7 @@ def test_noalloc_matches_workspace_gradient_twice(g):
 def test_noalloc_rejects_geometry_beyond_its_scratch():
     import torch
     lib = _native.load()
-    g = synth.make_geometry(512, 720, 768, batch=4)   # about 56 MB of scratch > 32 MiB
+    g = synth.make_geometry(512, 720, 768, batch=4)   # about 39 MB of scratch > 32 MiB
     cg = _native.geom(g)
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     code = lib.pnp_full_grad_noalloc(C.byref(cg), C.c_void_p(256), C.c_void_p(512), C.c_void_p(1024), stream)
