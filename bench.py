@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="direct launches instead of graph replay")
+    ap.add_argument("--no-autotune", action="store_true", help="heuristic launch shapes")
     ap.add_argument("--profile", action="store_true",
                     help="only the warm-up and the timed steps (inside an NVTX range 'timed'), "
                          "for ncu: no end-to-end, time-to-PSNR or CPU legs")
@@ -246,11 +248,17 @@ def run_native(args, rank, world):
     seq = synth.schedule_sequence(wl.stages, synth.subset_seed(wl.config_id))
     total_iters = sum(s.iters for s in wl.stages)
 
-    # ---- per-geometry set-up: step sizes by power iteration (not part of a step)
+    # ---- per-geometry set-up (not part of a step): step sizes by power iteration
+    # and the launch shapes chosen by the autotuner for this schedule
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     eta = [1.0 / plan.power_iter(s.factor, 100, 1e-6)[0] for s in wl.stages]
     setup_ms = 1000 * (time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    if not args.no_autotune:
+        plan.autotune(wl.stages, alpha=wl.alpha, lam=wl.tv_lambda, tv_iters=wl.tv_iters)
+    tune_ms = 1000 * (time.perf_counter() - t0)
+    use_graph = not args.no_graph
 
     kw = dict(alpha=wl.alpha, lam=wl.tv_lambda, tv_iters=wl.tv_iters, momentum=wl.momentum)
     d_x = torch.zeros(1, g.n, g.n, device=dev)
@@ -258,7 +266,7 @@ def run_native(args, rank, world):
 
     def step():
         d_x.zero_()
-        plan.run(wl.stages, eta, seq, d_b, d_x, graph=True, **kw)
+        plan.run(wl.stages, eta, seq, d_b, d_x, graph=use_graph, **kw)
 
     launches_setup = pnp.launch_count()
     for _ in range(max(args.warmup, 3)):
@@ -287,7 +295,7 @@ def run_native(args, rank, world):
         for k in range(args.steps):
             flush.fill_(float(k))
             ev[k][0].record(stream)
-            plan.run(wl.stages, eta, seq, d_b, d_x.zero_(), graph=True, **kw)
+            plan.run(wl.stages, eta, seq, d_b, d_x.zero_(), graph=use_graph, **kw)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         barrier(world)
@@ -297,17 +305,18 @@ def run_native(args, rank, world):
     total_ms = allmax(sum(step_ms), world)
     value = world * total_iters * args.steps / (total_ms / 1000.0)
 
-    # ---- the same step with direct launches (no CUDA graph), for comparison
-    nog = []
-    for k in range(3):
+    # ---- the same step in the other launch mode (graph replay vs direct), for comparison
+    other = []
+    for k in range(5):
         flush.fill_(3.0)
         a_, b2_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a_.record(stream)
-        plan.run(wl.stages, eta, seq, d_b, d_x.zero_(), **kw)
+        plan.run(wl.stages, eta, seq, d_b, d_x.zero_(), graph=not use_graph, **kw)
         b2_.record(stream)
         torch.cuda.synchronize()
-        nog.append(a_.elapsed_time(b2_))
-    no_graph_ms = float(np.median(nog))
+        if k >= 2:
+            other.append(a_.elapsed_time(b2_))
+    other_ms = float(np.median(other))
 
     # ---- per-kernel timing of the projector pair (events on the launching stream)
     def timed(fn, reps=20):
@@ -374,7 +383,7 @@ def run_native(args, rank, world):
         a.record(stream)
         d_b2.copy_(h_b, non_blocking=True)
         d_x.copy_(h_x0, non_blocking=True)
-        plan.run(wl.stages, eta, seq, d_b2, d_x, graph=True, **kw)
+        plan.run(wl.stages, eta, seq, d_b2, d_x, graph=use_graph, **kw)
         h_out.copy_(d_x, non_blocking=True)
         b_.record(stream)
         torch.cuda.synchronize()
@@ -427,8 +436,10 @@ def run_native(args, rank, world):
                              "full_ms": tts_f, "full_iters": it_f,
                              "speedup": (tts_f / tts_s) if (tts_s and tts_f) else None},
             "setup_ms_power_iteration": setup_ms,
-            "launch_mode": "CUDA graph captured once, replayed per step",
-            "ms_per_step_direct_launches": no_graph_ms}
+            "setup_ms_autotune": tune_ms,
+            "launch_mode": "CUDA graph captured once, replayed per step" if use_graph else "direct launches",
+            "ms_per_step_other_launch_mode": other_ms,
+            "step_ms_all": step_ms}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
