@@ -106,8 +106,10 @@ typedef struct {
     const float* d_b;             /* [batch][n_views][n_det] */
     float* d_x;                   /* in: x_0, out: x */
     const float* d_xtrue;         /* optional, with h_psnr_log */
-    double* h_psnr_log;           /* optional, [sum iters][batch] */
+    double* h_psnr_log;           /* optional, [sum iters][batch] (entries before start_iter untouched) */
     void* d_ws;                   /* pnp_setup-prepared workspace of this geometry */
+    int32_t start_iter;           /* checkpoint/resume: iterations already done (0 = fresh run) */
+    float* d_y;                   /* optional: in, y_{start_iter} (default: x); out, y after the run */
 } pnp_problem;
 
 /* Maximum total iterations of one pnp_run call when a PSNR log is requested. */
@@ -214,7 +216,11 @@ int pnp_run(const pnp_geom* g, const pnp_stage* stages, int n_stages, const doub
  * schedules of different lengths; iteration i of every class uses the same
  * momentum a_i and params).  Workspaces and outputs must be distinct per
  * class.  Synchronous only when some class logs PSNR.  PNP_EUNSUPPORTED for
- * more than 4 classes. */
+ * more than 4 classes.
+ * Checkpoint/resume: a class with start_iter = k continues Algorithm 1 from
+ * iteration k + 1 with d_x = x_k and d_y = y_k (both returned by an earlier run
+ * that stopped after k iterations, e.g. a schedule cut at k); the result is
+ * bitwise identical to an uninterrupted run. */
 int pnp_run_many(const pnp_problem* problems, int n_problems, const pnp_run_params* params, void* stream);
 
 /* Times the launch shapes of this geometry's kernels on d_ws's own buffers

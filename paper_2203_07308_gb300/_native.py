@@ -53,7 +53,8 @@ class ProblemC(C.Structure):
     _fields_ = [("geom", Geom), ("stages", C.POINTER(StageC)), ("n_stages", C.c_int32),
                 ("h_eta", C.POINTER(C.c_double)), ("h_subset_seq", C.POINTER(C.c_int32)),
                 ("d_b", C.c_void_p), ("d_x", C.c_void_p), ("d_xtrue", C.c_void_p),
-                ("h_psnr_log", C.POINTER(C.c_double)), ("d_ws", C.c_void_p)]
+                ("h_psnr_log", C.POINTER(C.c_double)), ("d_ws", C.c_void_p),
+                ("start_iter", C.c_int32), ("d_y", C.c_void_p)]
 
 
 _lock = threading.Lock()
@@ -407,7 +408,9 @@ def unrolled_step_vjp(g, factor, subset, n_subsets, eta, alpha, lam, tv_iters, a
 # ---------------------------------------------------------------- uneven batches, autotuning
 def run_many(problems, *, alpha=1.0, lam=0.02, tv_iters=20, momentum=True, stream=None, graph=False):
     """pnp_run_many.  ``problems``: list of dicts with keys plan, stages, eta, seq,
-    b, x and optional xtrue; returns the list of PSNR logs (None where no xtrue)."""
+    b, x and optional xtrue, start_iter, y (checkpoint/resume: x and y of
+    iteration start_iter in, x and y of the last iteration out); returns the
+    list of PSNR logs (None where no xtrue)."""
     arr = (ProblemC * len(problems))()
     keep = []
     logs = []
@@ -428,7 +431,8 @@ def run_many(problems, *, alpha=1.0, lam=0.02, tv_iters=20, momentum=True, strea
                           _ptr(pr["b"], g.batch * g.n_views * g.n_det, "b"), _ptr(pr["x"], img, "x"),
                           _ptr(xt, img, "xtrue", True),
                           log.ctypes.data_as(C.POINTER(C.c_double)) if log is not None else None,
-                          _ws(plan.ws)[0])
+                          _ws(plan.ws)[0], int(pr.get("start_iter", 0)),
+                          _ptr(pr.get("y"), img, "y", True))
     prm = RunParams(float(alpha), float(lam), int(tv_iters), int(bool(momentum)), RUN_GRAPH if graph else 0)
     _check(load().pnp_run_many(arr, len(problems), C.byref(prm), _stream(stream)))
     return logs

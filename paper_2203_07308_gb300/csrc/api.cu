@@ -601,6 +601,9 @@ int validate_problem(const pnp_problem& q, const pnp_run_params& pr, int idx, Pr
     if (any_subsets && !q.h_subset_seq) return fail(PNP_EINVAL, "subset sequence required");
     if (q.h_psnr_log && total * g->batch > PNP_MAX_LOG_ITERS)
         return fail(PNP_EINVAL, "PSNR log limited to %d iterations x batch", PNP_MAX_LOG_ITERS);
+    if (q.start_iter < 0 || q.start_iter > total)
+        return fail(PNP_EINVAL, "problem %d: start_iter %d outside [0, %ld]", idx, q.start_iter, total);
+    if (q.d_y && q.d_y == q.d_x) return fail(PNP_EINVAL, "problem %d: d_y must not alias d_x", idx);
     if (int e = check_ws(*g, q.d_ws)) return e;
     long i = 0;
     for (int k = 0; k < q.n_stages; ++k)
@@ -639,14 +642,26 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
     for (const auto& q : ps) max_total = std::max(max_total, q.total);
     const bool one = np == 1;
 
+    long min_start = max_total;
+    for (int c = 0; c < np; ++c) min_start = std::min(min_start, (long)pb[c].start_iter);
     auto issue = [&]() -> int {
         for (int c = 0; c < np; ++c) {
             const pnp_geom& g = pb[c].geom;
             char* ws = (char*)pb[c].d_ws;
-            PNP_CUDA(launch_copy(pb[c].d_x, (float*)(ws + ps[c].L.off_y), (size_t)g.batch * g.n * g.n, st));
+            const float* y0 = pb[c].d_y ? pb[c].d_y : pb[c].d_x;
+            PNP_CUDA(launch_copy(y0, (float*)(ws + ps[c].L.off_y), (size_t)g.batch * g.n * g.n, st));
         }
         std::vector<int> stage((size_t)np, 0), in_stage((size_t)np, 0);
         for (long i = 1; i <= max_total; ++i) {
+            if (i <= min_start) {       // resumed runs: advance the schedule cursors only
+                for (int c = 0; c < np; ++c) {
+                    if (i > ps[c].total) continue;
+                    const pnp_problem& q = pb[c];
+                    while (in_stage[c] >= q.stages[stage[c]].iters) { ++stage[c]; in_stage[c] = 0; }
+                    ++in_stage[c];
+                }
+                continue;
+            }
             PrepArgs prep[kMaxClasses];
             FwdArgs fwd[kMaxClasses];
             BackArgs back[kMaxClasses];
@@ -660,6 +675,7 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
                 while (in_stage[c] >= q.stages[stage[c]].iters) { ++stage[c]; in_stage[c] = 0; }
                 const pnp_stage& sk = q.stages[stage[c]];
                 ++in_stage[c];
+                if (i <= (long)q.start_iter) continue;   // this class resumes later
                 const pnp_geom& g = q.geom;
                 const Layout& L = ps[c].L;
                 const int li = level_index(sk.factor);
@@ -716,6 +732,12 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
                                              dlog + (i - 1) * q.geom.batch, 1, 0, st));
             }
         }
+        for (int c = 0; c < np; ++c) {
+            if (!pb[c].d_y) continue;
+            const pnp_geom& g = pb[c].geom;
+            char* ws = (char*)pb[c].d_ws;
+            PNP_CUDA(launch_copy((float*)(ws + ps[c].L.off_y), pb[c].d_y, (size_t)g.batch * g.n * g.n, st));
+        }
         return PNP_OK;
     };
 
@@ -728,6 +750,7 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
         h.val(q.geom);
         h.val(q.d_b); h.val(q.d_x); h.val(q.d_xtrue); h.val(q.d_ws);
         h.val(q.h_psnr_log != nullptr);
+        h.val(q.start_iter); h.val(q.d_y);
         h.add(q.stages, sizeof(pnp_stage) * (size_t)q.n_stages);
         h.add(q.h_eta, sizeof(double) * (size_t)q.n_stages);
         if (q.h_subset_seq) h.add(q.h_subset_seq, sizeof(int32_t) * (size_t)ps[c].total);
@@ -740,12 +763,15 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
         const pnp_problem& q = pb[c];
         if (!q.h_psnr_log || ps[c].total == 0) continue;
         char* ws = (char*)q.d_ws;
-        std::vector<double> mse((size_t)ps[c].total * q.geom.batch);
-        PNP_CUDA(cudaMemcpyAsync(mse.data(), ws + ps[c].L.off_log, mse.size() * sizeof(double),
+        const size_t first = (size_t)q.start_iter * q.geom.batch;
+        const size_t count = (size_t)ps[c].total * q.geom.batch - first;
+        if (count == 0) continue;
+        std::vector<double> mse(count);
+        PNP_CUDA(cudaMemcpyAsync(mse.data(), (double*)(ws + ps[c].L.off_log) + first, count * sizeof(double),
                                  cudaMemcpyDeviceToHost, st));
         PNP_CUDA(cudaStreamSynchronize(st));
         const double npix = (double)q.geom.n * q.geom.n;
-        for (size_t k = 0; k < mse.size(); ++k) q.h_psnr_log[k] = 10.0 * std::log10(npix / mse[k]);
+        for (size_t k = 0; k < count; ++k) q.h_psnr_log[first + k] = 10.0 * std::log10(npix / mse[k]);
     }
     return PNP_OK;
 }

@@ -148,3 +148,25 @@ def test_mixed_64_instances_full_size():
             rx, _ = oracle.pnp_run(wl.geom, wl.stages, eta, seq, b[0], None, lam=0.02, tv_iters=20,
                                    momentum=True)
             assert rel(got[0], rx) < TOL_RECON, (wl.name, rel(got[0], rx))
+
+
+def test_checkpoint_resume_is_bitwise_identical():
+    """Stop after k iterations, keep (x_k, y_k), resume from k: the result equals
+    the uninterrupted run bit for bit (deterministic kernels, same launch shapes)."""
+    import torch
+    g = synth.make_geometry(64, 60, 96, batch=2)
+    stages = [synth.Stage(2, 4, 3), synth.Stage(1, 6, 4)]
+    x, b, eta, seq = make_problem(g, stages, 13)
+    plan = pnp.Plan(g)
+    d_b = dev(b)
+    full_x = torch.zeros(2, 64, 64, device="cuda")
+    full_y = torch.zeros(2, 64, 64, device="cuda")
+    pnp.run_many([dict(plan=plan, stages=stages, eta=eta, seq=seq, b=d_b, x=full_x, y=full_y)])
+    k = 7
+    cut = [synth.Stage(2, 4, 3), synth.Stage(1, 3, 4)]
+    part_x = torch.zeros(2, 64, 64, device="cuda")
+    part_y = torch.zeros(2, 64, 64, device="cuda")
+    pnp.run_many([dict(plan=plan, stages=cut, eta=eta, seq=seq[:k], b=d_b, x=part_x, y=part_y)])
+    pnp.run_many([dict(plan=plan, stages=stages, eta=eta, seq=seq, b=d_b, x=part_x, y=part_y, start_iter=k)])
+    assert np.array_equal(host(part_x), host(full_x))
+    assert np.array_equal(host(part_y), host(full_y))
