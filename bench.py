@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-graph", action="store_true", help="direct launches instead of graph replay")
+    ap.add_argument("--graph", action="store_true", help="replay a captured CUDA graph instead of direct launches")
     ap.add_argument("--no-autotune", action="store_true", help="heuristic launch shapes")
     ap.add_argument("--profile", action="store_true",
                     help="only the warm-up and the timed steps (inside an NVTX range 'timed'), "
@@ -258,7 +258,7 @@ def run_native(args, rank, world):
     if not args.no_autotune:
         plan.autotune(wl.stages, alpha=wl.alpha, lam=wl.tv_lambda, tv_iters=wl.tv_iters)
     tune_ms = 1000 * (time.perf_counter() - t0)
-    use_graph = not args.no_graph
+    use_graph = args.graph
 
     kw = dict(alpha=wl.alpha, lam=wl.tv_lambda, tv_iters=wl.tv_iters, momentum=wl.momentum)
     d_x = torch.zeros(1, g.n, g.n, device=dev)

@@ -224,7 +224,7 @@ int pnp_run(const pnp_geom* g, const pnp_stage* stages, int n_stages, const doub
 int pnp_run_many(const pnp_problem* problems, int n_problems, const pnp_run_params* params, void* stream);
 
 /* Times the launch shapes of this geometry's kernels on d_ws's own buffers
- * (forward lanes per ray 4/8/16 and backprojector view groups 1..32 for each
+ * (forward lanes per ray 4/8/16 and backprojector view groups 1..16 for each
  * sketch level of the schedule, using its first angle subset; the FGP tile side
  * around the cost-model choice) and records the fastest for later calls that
  * use d_ws.  Shapes change only the order of floating-point sums (results stay

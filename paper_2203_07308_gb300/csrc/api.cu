@@ -866,7 +866,7 @@ int pnp_autotune(const pnp_geom* g, const pnp_stage* stages, int n_stages, const
         const BackArgs ba = back_args(*g, lv, ws, 0, P, res, kBackRaw, 1.0f, nullptr, 0.0f, z, g->batch);
         best = 1e30f;
         const int nsub = subset_views(*g, 0, P);
-        for (int G = 1; G <= 32 && G <= nsub; G *= 2) {
+        for (int G = 1; G <= 16 && G <= nsub; G *= 2) {
             float ms = 0.0f;
             if (rc == PNP_OK) rc = timeit([&]() -> int { PNP_CUDA(launch_backward(ba, st, G)); return PNP_OK; }, &ms);
             if (rc == PNP_OK && ms < best) { best = ms; tu.groups[li] = G; }

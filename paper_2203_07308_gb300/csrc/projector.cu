@@ -215,10 +215,11 @@ __global__ void __launch_bounds__(256, 4) k_forward(const FwdTable t)
 // products of the block's four pixels summed over the ray's samples near the
 // block.  The G partial sums are added in a fixed order through shared memory,
 // so the result is deterministic for a given G (a function of the problem
-// size).  CTA = 4 x 4 blocks (8 x 8 pixels) x G view groups: small CTAs keep
-// the per-SM load even on 152 SMs.
-constexpr int kBack2Tile = 4;
-constexpr int kBack2MaxGroups = 32;
+// size).  CTA = 8 x 4 blocks (16 x 8 pixels) x G view groups, so the 32
+// threads of a warp walk the same views in step.
+constexpr int kBack2TileX = 8;    // a warp = 8 x 4 blocks of one view group
+constexpr int kBack2TileY = 4;
+constexpr int kBack2MaxGroups = 16;
 
 // The four pixels share the view set-up and the candidate rays; their union
 // support is the 3 x 3 square around the block centre (radius rho = 1.5 sqrt 2),
@@ -242,15 +243,16 @@ __global__ void __launch_bounds__(512, 2) k_backward2x2(const BackTable t)
         if (k < t.count && (long)blockIdx.x >= t.begin[k]) c = k;
     const BackArgs& a = t.c[c];
     const int nb = (a.ns + 1) / 2;                             // blocks per side
-    const int tiles_x = (nb + kBack2Tile - 1) / kBack2Tile;
+    const int tiles_x = (nb + kBack2TileX - 1) / kBack2TileX;
+    const int tiles_y = (nb + kBack2TileY - 1) / kBack2TileY;
     const long local = (long)blockIdx.x - t.begin[c];
-    const int tiles = tiles_x * tiles_x;
+    const int tiles = tiles_x * tiles_y;
     const int inst = (int)(local / tiles);
     const int tile = (int)(local - (long)inst * tiles);
-    const int bx = (tile % tiles_x) * kBack2Tile + tx;
-    const int by = (tile / tiles_x) * kBack2Tile + ty;
+    const int bx = (tile % tiles_x) * kBack2TileX + tx;
+    const int by = (tile / tiles_x) * kBack2TileY + ty;
     const bool inside = bx < nb && by < nb;
-    __shared__ float4 part[kBack2MaxGroups][kBack2Tile * kBack2Tile];
+    __shared__ float4 part[kBack2MaxGroups][kBack2TileX * kBack2TileY];
     float t00 = 0.0f, t10 = 0.0f, t01 = 0.0f, t11 = 0.0f;
     if (inside) {
         const int ix = 2 * bx, iy = 2 * by;
@@ -317,7 +319,7 @@ __global__ void __launch_bounds__(512, 2) k_backward2x2(const BackTable t)
             t00 += v00; t10 += v10; t01 += v01; t11 += v11;
         }
     }
-    const int slot = ty * kBack2Tile + tx;
+    const int slot = ty * kBack2TileX + tx;
     part[g][slot] = make_float4(t00, t10, t01, t11);
     __syncthreads();
     if (g != 0 || !inside) return;
@@ -478,7 +480,7 @@ cudaError_t launch_backward_multi(const BackArgs* items, int count, cudaStream_t
     for (int c = 0; c < count; ++c) {
         t.c[c] = items[c];
         const int nb = (items[c].ns + 1) / 2;
-        const int tiles = div_up(nb, kBack2Tile) * div_up(nb, kBack2Tile);
+        const int tiles = div_up(nb, kBack2TileX) * div_up(nb, kBack2TileY);
         t.begin[c + 1] = t.begin[c] + (long)tiles * items[c].batch;
         blocks += (long)nb * nb * items[c].batch;
         min_views = min(min_views, items[c].n_sub);
@@ -491,7 +493,7 @@ cudaError_t launch_backward_multi(const BackArgs* items, int count, cudaStream_t
         G = 1;
         while (G < kBack2MaxGroups && blocks * G < 2L * 152 * 2048 && G * 2 <= min_views) G *= 2;
     }
-    dim3 blk(kBack2Tile, kBack2Tile, G), grd((unsigned)t.begin[count]);
+    dim3 blk(kBack2TileX, kBack2TileY, G), grd((unsigned)t.begin[count]);
     if (half_step)
         k_backward2x2<9><<<grd, blk, 0, st>>>(t);
     else
