@@ -94,6 +94,13 @@ def _load():
                                         C.c_int, C.c_int, dp, dp]
             lib.orc_objective.argtypes = [gp, dp, dp, dp]
             lib.orc_grad_w.argtypes = [gp, C.c_int, dp, dp, dp, dp, C.c_int, C.c_int]
+            lib.orc_grad_wk.argtypes = [gp, C.c_int, C.c_int, dp, dp, dp, dp, C.c_int, C.c_int]
+            lib.orc_power_iter_wk.argtypes = [gp, C.c_int, C.c_int, dp, C.c_int, C.c_double, ip]
+            lib.orc_power_iter_wk.restype = C.c_double
+            lib.orc_keys.argtypes = [C.c_double]
+            lib.orc_keys.restype = C.c_double
+            lib.orc_bicubic_down.argtypes = [C.c_int, C.c_int, dp, dp]
+            lib.orc_bicubic_up.argtypes = [C.c_int, C.c_int, dp, dp]
             lib.orc_power_iter_w.argtypes = [gp, C.c_int, dp, C.c_int, C.c_double, ip]
             lib.orc_power_iter_w.restype = C.c_double
             lib.orc_pnp_run_w.argtypes = [gp, C.c_int, ip, dp, ip, dp, dp, dp, C.c_double, C.c_double,
@@ -177,14 +184,37 @@ def unpool(coarse, s: int) -> np.ndarray:
     return out
 
 
-def grad(g, s: int, y, b, p: int = 0, P: int = 1, w=None) -> np.ndarray:
+def keys(t: float) -> float:
+    """Keys cubic convolution kernel, a = -1/2."""
+    return float(_load().orc_keys(float(t)))
+
+
+def bicubic_down(fine, s: int) -> np.ndarray:
+    """Bicubic sketch S (separable Keys kernel widened by s, normalised)."""
+    fine = _f64(fine)
+    n = fine.shape[-1]
+    out = np.zeros((n // s, n // s))
+    _load().orc_bicubic_down(n, s, _dp(fine), _dp(out))
+    return out
+
+
+def bicubic_up(coarse, s: int) -> np.ndarray:
+    """U = S^T of the bicubic sketch."""
+    coarse = _f64(coarse)
+    n = coarse.shape[-1] * s
+    out = np.zeros((n, n))
+    _load().orc_bicubic_up(n, s, _dp(coarse), _dp(out))
+    return out
+
+
+def grad(g, s: int, y, b, p: int = 0, P: int = 1, w=None, kind: int = 0) -> np.ndarray:
     """c S^T A_s^{(p)T} W^{(p)}(A_s^{(p)} S y - b^{(p)}), c = max(P, 1) (Alg. 1 G, U = S^T);
     W = diag(w) (weighted least squares) when w is given, else the identity."""
     y = _f64(y)
     b = _f64(b)
     ww = None if w is None else _f64(w)
     out = np.zeros((g.n, g.n))
-    _load().orc_grad_w(C.byref(geom(g)), s, _dp(y), _dp(b), _dp(ww), _dp(out), p, P)
+    _load().orc_grad_wk(C.byref(geom(g)), s, int(kind), _dp(y), _dp(b), _dp(ww), _dp(out), p, P)
     return out
 
 
@@ -201,11 +231,11 @@ def tv(x) -> float:
     return float(_load().orc_tv(x.shape[-1], _dp(x)))
 
 
-def power_iter(g, s: int, max_iters: int = 100, tol: float = 1e-7, w=None):
+def power_iter(g, s: int, max_iters: int = 100, tol: float = 1e-7, w=None, kind: int = 0):
     """(L, iterations): L = ||W^{1/2} A_s S||^2 by power iteration (Sec. 3's eta = O(1/L))."""
     it = C.c_int(0)
     ww = None if w is None else _f64(w)
-    L = _load().orc_power_iter_w(C.byref(geom(g)), s, _dp(ww), max_iters, tol, C.byref(it))
+    L = _load().orc_power_iter_wk(C.byref(geom(g)), s, int(kind), _dp(ww), max_iters, tol, C.byref(it))
     return float(L), int(it.value)
 
 
@@ -218,9 +248,10 @@ def psnr(x, xt) -> float:
 def pnp_run(g, stages: Sequence, eta: Sequence[float], seq, b, x0=None, *, alpha: float = 1.0,
             lam: float = 0.02, tv_iters: int = 20, momentum: bool = True, xt=None, w=None):
     """Algorithm 1 on one image; returns (x, psnr_log or None)."""
-    st = np.ascontiguousarray(np.array([[s.factor, s.iters, s.n_subsets] if hasattr(s, "factor")
-                                         else list(s) for s in stages], dtype=np.int32).ravel())
-    total = int(sum(st[1::3]))
+    st = np.ascontiguousarray(np.array([[s.factor, s.iters, s.n_subsets, getattr(s, "kind", 0)]
+                                         if hasattr(s, "factor") else (list(s) + [0])[:4]
+                                         for s in stages], dtype=np.int32).ravel())
+    total = int(sum(st[1::4]))
     seq = np.ascontiguousarray(np.asarray(seq, dtype=np.int32))
     if seq.size < total:
         seq = np.concatenate([seq, np.zeros(total - seq.size, np.int32)])
@@ -231,7 +262,7 @@ def pnp_run(g, stages: Sequence, eta: Sequence[float], seq, b, x0=None, *, alpha
     log = np.zeros(total) if xt is not None else None
     ip = C.POINTER(C.c_int)
     ww = None if w is None else _f64(w)
-    _load().orc_pnp_run_w(C.byref(geom(g)), len(st) // 3, st.ctypes.data_as(ip), _dp(eta),
+    _load().orc_pnp_run_w(C.byref(geom(g)), len(st) // 4, st.ctypes.data_as(ip), _dp(eta),
                           seq.ctypes.data_as(ip), _dp(b), _dp(ww), _dp(x), float(alpha), float(lam),
                           int(tv_iters), int(bool(momentum)), _dp(xt_), _dp(log))
     return x, log

@@ -210,6 +210,90 @@ void orc_unpool(int n, int s, const double *coarse, double *fine)
             fine[(long)y * n + x] = coarse[(long)(y / s) * ns + (x / s)] / (double)(s * s);
 }
 
+/* ---------------- bicubic sketch (Sec. 3 uses bicubic imresize for S and U) --
+ * Reading: S is separable; coarse pixel I (centre s I + (s-1)/2 in fine index
+ * units) averages fine pixels x with weights k((x - X_I)/s), k the Keys cubic
+ * convolution kernel with a = -1/2 (widened by s to avoid aliasing), normalised
+ * to sum to one over the fine pixels inside the image.  U = S^T. */
+double orc_keys(double t)
+{
+    const double a = -0.5;
+    t = fabs(t);
+    if (t <= 1.0) return (a + 2.0) * t * t * t - (a + 3.0) * t * t + 1.0;
+    if (t < 2.0) return a * t * t * t - 5.0 * a * t * t + 8.0 * a * t - 4.0 * a;
+    return 0.0;
+}
+
+/* W[I][x], ns x n, the 1-D bicubic sketch. */
+static void bicubic_matrix(int n, int s, double *W)
+{
+    int ns = n / s;
+    for (int I = 0; I < ns; ++I) {
+        double XI = s * I + 0.5 * (s - 1);
+        double den = 0.0;
+        for (int x = 0; x < n; ++x) den += orc_keys((x - XI) / s);
+        for (int x = 0; x < n; ++x) W[(long)I * n + x] = orc_keys((x - XI) / s) / den;
+    }
+}
+
+void orc_bicubic_down(int n, int s, const double *fine, double *coarse)
+{
+    int ns = n / s;
+    double *W = malloc(sizeof(double) * (size_t)ns * n), *tmp = malloc(sizeof(double) * (size_t)n * ns);
+    bicubic_matrix(n, s, W);
+    /* rows: tmp[y][I] = sum_x W[I][x] fine[y][x] */
+    for (int y = 0; y < n; ++y)
+        for (int I = 0; I < ns; ++I) {
+            double acc = 0.0;
+            for (int x = 0; x < n; ++x) acc += W[(long)I * n + x] * fine[(long)y * n + x];
+            tmp[(long)y * ns + I] = acc;
+        }
+    /* columns: coarse[J][I] = sum_y W[J][y] tmp[y][I] */
+    for (int J = 0; J < ns; ++J)
+        for (int I = 0; I < ns; ++I) {
+            double acc = 0.0;
+            for (int y = 0; y < n; ++y) acc += W[(long)J * n + y] * tmp[(long)y * ns + I];
+            coarse[(long)J * ns + I] = acc;
+        }
+    free(W);
+    free(tmp);
+}
+
+void orc_bicubic_up(int n, int s, const double *coarse, double *fine)
+{
+    int ns = n / s;
+    double *W = malloc(sizeof(double) * (size_t)ns * n), *tmp = malloc(sizeof(double) * (size_t)n * ns);
+    bicubic_matrix(n, s, W);
+    /* tmp[y][I] = sum_J W[J][y] coarse[J][I] */
+    for (int y = 0; y < n; ++y)
+        for (int I = 0; I < ns; ++I) {
+            double acc = 0.0;
+            for (int J = 0; J < ns; ++J) acc += W[(long)J * n + y] * coarse[(long)J * ns + I];
+            tmp[(long)y * ns + I] = acc;
+        }
+    /* fine[y][x] = sum_I W[I][x] tmp[y][I] */
+    for (int y = 0; y < n; ++y)
+        for (int x = 0; x < n; ++x) {
+            double acc = 0.0;
+            for (int I = 0; I < ns; ++I) acc += W[(long)I * n + x] * tmp[(long)y * ns + I];
+            fine[(long)y * n + x] = acc;
+        }
+    free(W);
+    free(tmp);
+}
+
+static void sketch_down(int kind, int n, int s, const double *fine, double *coarse)
+{
+    if (kind == 1) orc_bicubic_down(n, s, fine, coarse);
+    else orc_pool(n, s, fine, coarse);
+}
+
+static void sketch_up(int kind, int n, int s, const double *coarse, double *fine)
+{
+    if (kind == 1) orc_bicubic_up(n, s, coarse, fine);
+    else orc_unpool(n, s, coarse, fine);
+}
+
 /* Gradient estimate on the fine grid (Alg. 1, Option 1 for P<=1, Option 2 with
  * angle subset p of P otherwise):
  *     g = c * S^T A_s^{(p)T} (A_s^{(p)} S y - b^{(p)}),   c = max(P, 1).
@@ -229,19 +313,19 @@ static void apply_weights(const orc_geom *g, const double *w, double *res, int p
  * 1/2 sum_j w_j (A x - b)_j^2, the weighted least squares of transmission CT
  * with Poisson counts (Sec. 3's b ~ Poisson(I0 exp(-A x)) after the log), so
  * the gradient is c S^T A_s^{(p)T} W^{(p)} (A_s^{(p)} S y - b^{(p)}). */
-void orc_grad_w(const orc_geom *g, int s, const double *y, const double *b, const double *w,
-                double *grad, int p, int P)
+void orc_grad_wk(const orc_geom *g, int s, int kind, const double *y, const double *b, const double *w,
+                 double *grad, int p, int P)
 {
     int n = g->n, ns = n / s;
     int nsub = orc_subset_views(g, p, P);
     double *v = malloc(sizeof(double) * (size_t)ns * ns);
     double *res = malloc(sizeof(double) * (size_t)nsub * g->n_det);
     double *gc = malloc(sizeof(double) * (size_t)ns * ns);
-    orc_pool(n, s, y, v);
+    sketch_down(kind, n, s, y, v);
     orc_project(g, s, v, b, res, p, P);
     apply_weights(g, w, res, p, P);
     orc_backproject(g, s, res, gc, p, P);
-    orc_unpool(n, s, gc, grad);
+    sketch_up(kind, n, s, gc, grad);
     double c = P <= 1 ? 1.0 : (double)P;
     for (long i = 0; i < (long)n * n; ++i) grad[i] *= c;
     free(v);
@@ -249,9 +333,15 @@ void orc_grad_w(const orc_geom *g, int s, const double *y, const double *b, cons
     free(gc);
 }
 
+void orc_grad_w(const orc_geom *g, int s, const double *y, const double *b, const double *w,
+                double *grad, int p, int P)
+{
+    orc_grad_wk(g, s, 0, y, b, w, grad, p, P);
+}
+
 void orc_grad(const orc_geom *g, int s, const double *y, const double *b, double *grad, int p, int P)
 {
-    orc_grad_w(g, s, y, b, NULL, grad, p, P);
+    orc_grad_wk(g, s, 0, y, b, NULL, grad, p, P);
 }
 
 /* ---------------- TV prox by FGP (Beck & Teboulle 2009) -------------------
@@ -351,9 +441,19 @@ double orc_power_iter(const orc_geom *g, int s, int max_iters, double tol, int *
     return orc_power_iter_w(g, s, NULL, max_iters, tol, iters_out);
 }
 
+double orc_power_iter_wk(const orc_geom *g, int s, int kind, const double *wts, int max_iters,
+                         double tol, int *iters_out);
+
 /* L = ||W^{1/2} A_s S||^2 (wts nullable: W = I). */
 double orc_power_iter_w(const orc_geom *g, int s, const double *wts, int max_iters, double tol,
                         int *iters_out)
+{
+    return orc_power_iter_wk(g, s, 0, wts, max_iters, tol, iters_out);
+}
+
+/* The same with the sketch of the given kind (0 average pool, 1 bicubic). */
+double orc_power_iter_wk(const orc_geom *g, int s, int kind, const double *wts, int max_iters,
+                         double tol, int *iters_out)
 {
     int n = g->n, ns = n / s;
     size_t N = (size_t)n * n;
@@ -364,11 +464,11 @@ double orc_power_iter_w(const orc_geom *g, int s, const double *wts, int max_ite
     double lam = 0.0;
     int it = 0;
     for (it = 1; it <= max_iters; ++it) {
-        orc_pool(n, s, u, v);
+        sketch_down(kind, n, s, u, v);
         orc_project(g, s, v, NULL, res, 0, 1);
         apply_weights(g, wts, res, 0, 1);
         orc_backproject(g, s, res, gc, 0, 1);
-        orc_unpool(n, s, gc, w);
+        sketch_up(kind, n, s, gc, w);
         double rq = 0.0, nw = 0.0;
         for (size_t i = 0; i < N; ++i) {
             rq += u[i] * w[i];
@@ -394,7 +494,8 @@ double orc_psnr(long count, const double *x, const double *xt)
 }
 
 /* Algorithm 1 (PnP-MS2G) on one image.
- *   stages      n_stages triples (factor s_k, iterations N_k, subsets P_k)
+ *   stages      n_stages records (factor s_k, iterations N_k, subsets P_k, sketch kind:
+ *               0 average pool, 1 bicubic)
  *   eta         per-stage step sizes eta_k
  *   seq         subset id of every iteration (length sum N_k)
  *   x           in: x_0 (= y_0); out: x after the last iteration
@@ -428,11 +529,11 @@ void orc_pnp_run_w(const orc_geom *g, int n_stages, const int *stages, const dou
     memcpy(xprev, x, sizeof(double) * N);
     int i = 0;
     for (int k = 0; k < n_stages; ++k) {
-        int s = stages[3 * k], Nk = stages[3 * k + 1], P = stages[3 * k + 2];
+        int s = stages[4 * k], Nk = stages[4 * k + 1], P = stages[4 * k + 2], kind = stages[4 * k + 3];
         for (int jj = 0; jj < Nk; ++jj) {
             i += 1;
             int p = P > 1 ? seq[i - 1] : 0;
-            orc_grad_w(g, s, y, b, w, gr, p, P);
+            orc_grad_wk(g, s, kind, y, b, w, gr, p, P);
             for (size_t q = 0; q < N; ++q) z[q] = y[q] - eta[k] * gr[q];
             orc_fgp(n, z, lambda, tv_iters, dz);
             double a = momentum ? (double)(i - 1) / (double)(i + 3) : 0.0;

@@ -82,6 +82,7 @@ class Stage:
     factor: int
     iters: int
     n_subsets: int = 1
+    kind: int = 0          # sketch: 0 s x s average pool, 1 bicubic (Keys a = -1/2, widened by s)
 
 
 @dataclass

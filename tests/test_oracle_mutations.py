@@ -41,6 +41,10 @@ MUTATIONS = [
     ("fgp vjp projection jacobian", "abar[i] = (pbar[i] - h1 * d) / nrm;", "abar[i] = (pbar[i] + h1 * d) / nrm;"),
     ("fgp vjp lambda term", "*lambar -= dz / (8.0 * lambda * lambda);", "*lambar += dz / (8.0 * lambda * lambda);"),
     ("step vjp momentum", "xt[i] = xbar[i] + (1.0 + amom) * ybar[i];", "xt[i] = xbar[i] + amom * ybar[i];"),
+    ("keys kernel coefficient", "if (t <= 1.0) return (a + 2.0) * t * t * t - (a + 3.0) * t * t + 1.0;",
+     "if (t <= 1.0) return (a + 2.0) * t * t * t - (a + 2.0) * t * t + 1.0;"),
+    ("bicubic adjoint index", "for (int J = 0; J < ns; ++J) acc += W[(long)J * n + y] * coarse[(long)J * ns + I];",
+     "for (int J = 0; J < ns; ++J) acc += W[(long)J * n + y] * coarse[(long)I * ns + J];"),
     ("weights on the wrong views", "res[(long)vs * g->n_det + j] *= w[(long)(first + vs * step) * g->n_det + j];",
      "res[(long)vs * g->n_det + j] *= w[(long)vs * g->n_det + j];"),
 ]

@@ -577,3 +577,77 @@ def test_weighted_objective():
     w = np.full((16, 32), 3.0)
     f, _ = oracle.objective(g, x, b, w)
     assert abs(f - 0.5 * 3.0 * 0.25 * b.size) < 1e-9
+
+
+# ---------------------------------------------------------------- bicubic sketch (Sec. 3's imresize)
+def keys_np(t, a=-0.5):
+    """Keys (1981) cubic convolution kernel, written out here independently."""
+    t = abs(t)
+    if t <= 1:
+        return (a + 2) * t ** 3 - (a + 3) * t ** 2 + 1
+    if t < 2:
+        return a * t ** 3 - 5 * a * t ** 2 + 8 * a * t - 4 * a
+    return 0.0
+
+
+def bicubic_dense(n, s):
+    """2-D bicubic sketch as a dense matrix: separable normalised widened Keys weights."""
+    ns = n // s
+    W = np.zeros((ns, n))
+    for I in range(ns):
+        XI = s * I + (s - 1) / 2
+        w = np.array([keys_np((x - XI) / s) for x in range(n)])
+        W[I] = w / w.sum()
+    return np.kron(W, W)
+
+
+def test_keys_kernel_textbook_values():
+    """Keys 1981 with a = -1/2: interpolating at a half-way point uses weights
+    -1/16, 9/16, 9/16, -1/16; k vanishes at the other integers."""
+    assert oracle.keys(0.0) == 1.0
+    for t in (1.0, -1.0, 2.0, -2.0, 2.5):
+        assert oracle.keys(t) == 0.0
+    assert abs(oracle.keys(0.5) - 9 / 16) < 1e-15 and abs(oracle.keys(-1.5) + 1 / 16) < 1e-15
+    for t in np.linspace(-2.5, 2.5, 41):
+        assert abs(oracle.keys(t) - keys_np(t)) < 1e-15
+
+
+@pytest.mark.parametrize("s", [2, 4])
+def test_bicubic_sketch_closed_forms_and_adjoint(s):
+    n = 32
+    rng = np.random.default_rng(90 + s)
+    x = rng.standard_normal((n, n))
+    v = rng.standard_normal((n // s, n // s))
+    assert abs(np.vdot(oracle.bicubic_down(x, s), v) - np.vdot(x, oracle.bicubic_up(v, s))) < 1e-12
+    assert np.abs(oracle.bicubic_down(np.full((n, n), 0.7), s) - 0.7).max() < 1e-14
+    # a linear ramp is reproduced at the coarse centres away from the border
+    X, Y = np.meshgrid(np.arange(n, dtype=float), np.arange(n, dtype=float), indexing="xy")
+    c = oracle.bicubic_down(2 * X - Y, s)
+    I = np.arange(n // s)
+    XI = s * I + (s - 1) / 2
+    inner = slice(2, n // s - 2)
+    expect = 2 * XI[None, :] - XI[:, None]
+    assert np.abs(c[inner, inner] - expect[inner, inner]).max() < 1e-12
+    D = bicubic_dense(n, s)
+    assert np.abs(oracle.bicubic_down(x, s).ravel() - D @ x.ravel()).max() < 1e-13
+
+
+def test_bicubic_gradient_and_step_size():
+    g = synth.make_geometry(16, 12, 24)
+    rng = np.random.default_rng(95)
+    y = rng.random((16, 16))
+    b = rng.standard_normal((12, 24))
+
+    def f(yy):
+        r = oracle.project(g, 2, oracle.bicubic_down(yy, 2), b)
+        return 0.5 * np.vdot(r, r)
+
+    gr = oracle.grad(g, 2, y, b, kind=1)
+    d = rng.standard_normal((16, 16))
+    fd = (f(y + 1e-3 * d) - f(y - 1e-3 * d)) / 2e-3
+    assert abs(fd - np.vdot(gr, d)) < 1e-8 * max(1.0, abs(fd))
+    A = dense_rows(g, 2)
+    M = A @ bicubic_dense(16, 2)
+    lmax = np.linalg.eigvalsh(M.T @ M).max()
+    L, _ = oracle.power_iter(g, 2, 3000, 1e-14, kind=1)
+    assert abs(L - lmax) < 1e-8 * lmax
