@@ -222,6 +222,48 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- native arm
+def paper_sparse_view(plan_factory, dev, kw):
+    """Sketched PnP-MS2G vs full-gradient PnP-FISTA on the paper's sparse-view
+    geometry with Poisson transmission data and weighted least squares: final
+    PSNR of both arms and their device times."""
+    import torch
+    from paper_2203_07308_gb300 import synth
+    wl, i0 = synth.paper_workloads()["sparse_view"]
+    g = wl.geom
+    plan = plan_factory(g)
+    x_true = synth.ellipse_phantom(g.n, synth.phantom_seed(wl.config_id, 0), wl.n_ellipses)
+    d_xt = torch.from_numpy(x_true.astype(np.float32)).to(dev).reshape(1, g.n, g.n)
+    d_ax = torch.empty(1, g.n_views, g.n_det, device=dev)
+    plan.project(1, d_xt, d_ax)
+    b, w = synth.poisson_transmission(d_ax.cpu().numpy()[0], i0, 5500)
+    d_b = torch.from_numpy(b.astype(np.float32)).to(dev).reshape(1, g.n_views, g.n_det)
+    d_w = torch.from_numpy(w.astype(np.float32)).to(dev).reshape(1, g.n_views, g.n_det)
+    plan.set_weights(d_w)
+    total = sum(s.iters for s in wl.stages)
+    bicubic = [synth.Stage(s.factor, s.iters, s.n_subsets, kind=1) for s in wl.stages]
+    arms = {"sketched": wl.stages, "sketched_bicubic": bicubic, "full": [synth.Stage(1, total, 1)]}
+    out = {"setup": wl.name + ", WLS, 256x256, 228 bins",
+           "schedule_sketched": [[s.factor, s.iters, s.n_subsets] for s in wl.stages],
+           "iterations": total}
+    pk = dict(kw)
+    for name, stages in arms.items():
+        eta = [1.0 / plan.power_iter(s.factor, 100, 1e-6, kind=s.kind)[0] for s in stages]
+        d_x = torch.zeros(1, g.n, g.n, device=dev)
+        log = plan.run(stages, eta, None, d_b, d_x, xtrue=d_xt, **pk)[:, 0]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        plan.run(stages, eta, None, d_b, d_x.zero_(), **pk)
+        ev[0].record()
+        for _ in range(3):
+            plan.run(stages, eta, None, d_b, d_x.zero_(), **pk)
+        ev[1].record()
+        torch.cuda.synchronize()
+        out[name + "_final_db"] = float(log[-1])
+        out[name + "_ms"] = ev[0].elapsed_time(ev[1]) / 3
+    out["psnr_gap_db"] = out["full_final_db"] - out["sketched_final_db"]
+    out["time_ratio_full_over_sketched"] = out["full_ms"] / out["sketched_ms"]
+    return out
+
+
 def run_native(args, rank, world):
     import torch
     import paper_2203_07308_gb300 as pnp
@@ -370,6 +412,11 @@ def run_native(args, rank, world):
     tts_s, it_s = time_to(wl.stages, eta, seq, log_s)
     tts_f, it_f = time_to(full_arm, eta_full, None, log_f)
 
+    # ---- the paper's sparse-view set-up (Sec. 3: 90 views, 228 bins, Poisson
+    # data with I0 = 10^5.5, two sketch stages m_1 = d/16 then m_2 = d/4,
+    # Option 1) against full-gradient PnP-FISTA with the same iteration count
+    paper = paper_sparse_view(plan_factory=pnp.Plan, dev=dev, kw=kw)
+
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     h_b = torch.empty(d_b.shape, dtype=torch.float32, pin_memory=True)
     h_b.copy_(d_b)
@@ -435,6 +482,7 @@ def run_native(args, rank, world):
                              "sketched_ms": tts_s, "sketched_iters": it_s,
                              "full_ms": tts_f, "full_iters": it_f,
                              "speedup": (tts_f / tts_s) if (tts_s and tts_f) else None},
+            "paper_sparse_view": paper,
             "setup_ms_power_iteration": setup_ms,
             "setup_ms_autotune": tune_ms,
             "launch_mode": "CUDA graph captured once, replayed per step" if use_graph else "direct launches",

@@ -71,12 +71,21 @@ typedef struct {
     double step;        /* ray-march step in level pixels (0.5 = half a pixel) */
 } pnp_geom;
 
+/* Sketch operators S_k (and U_k = S_k^T).  POOL: s x s average pooling.
+ * BICUBIC: the paper's bicubic resize (Sec. 3), read as the separable Keys
+ * cubic convolution kernel (a = -1/2) widened by s, normalised to sum to one
+ * over the fine pixels inside the image. */
+#define PNP_SKETCH_POOL 0
+#define PNP_SKETCH_BICUBIC 1
+
 /* One stage of Algorithm 1: sketch factor s_k (m_k = d / s_k^2), N_k inner
- * iterations, and P_k interleaved angle subsets (1 = Option 1, >1 = Option 2). */
+ * iterations, P_k interleaved angle subsets (1 = Option 1, >1 = Option 2) and
+ * the sketch kind. */
 typedef struct {
     int32_t factor;
     int32_t iters;
     int32_t n_subsets;
+    int32_t kind;       /* PNP_SKETCH_POOL or PNP_SKETCH_BICUBIC (ignored for factor 1) */
 } pnp_stage;
 
 /* Loop parameters of Algorithm 1. */
@@ -159,6 +168,11 @@ int pnp_sketch(const pnp_geom* g, int factor, const float* d_fine, float* d_coar
  * s x s block and divided by s^2, d_coarse -> d_fine. */
 int pnp_upsample(const pnp_geom* g, int factor, const float* d_coarse, float* d_fine, void* stream);
 
+/* pnp_sketch / pnp_upsample with the sketch kind. */
+int pnp_sketch_kind(const pnp_geom* g, int factor, int kind, const float* d_fine, float* d_coarse, void* stream);
+int pnp_upsample_kind(const pnp_geom* g, int factor, int kind, const float* d_coarse, float* d_fine,
+                      void* stream);
+
 /* Full data-fidelity gradient (Eq. 5): d_g = A^T (A d_x - d_b), all views,
  * fine grid.  d_x, d_g [batch][n][n]; d_b [batch][n_views][n_det]. */
 int pnp_full_grad(const pnp_geom* g, const float* d_x, const float* d_b, float* d_g,
@@ -171,6 +185,10 @@ int pnp_full_grad(const pnp_geom* g, const float* d_x, const float* d_b, float* 
  * For factor 1 and n_subsets 1 it equals pnp_full_grad. */
 int pnp_sketch_grad(const pnp_geom* g, int factor, const float* d_y, const float* d_b, float* d_g,
                     int subset, int n_subsets, void* d_ws, void* stream);
+
+/* pnp_sketch_grad with the sketch kind (S and U = S^T of that kind). */
+int pnp_sketch_grad_kind(const pnp_geom* g, int factor, int kind, const float* d_y, const float* d_b,
+                         float* d_g, int subset, int n_subsets, void* d_ws, void* stream);
 
 /* Bytes of workspace for pnp_tv_denoise on [batch][n][n]. */
 int pnp_tv_workspace_size(int n, int batch, size_t* bytes);
@@ -192,6 +210,10 @@ int pnp_tv_denoise(const float* d_z, float* d_x, int n, int batch, float lambda,
  * not depend on the data).  Synchronous: writes *h_L and *h_iters. */
 int pnp_power_iter(const pnp_geom* g, int factor, int max_iters, double tol, double* h_L,
                    int* h_iters, void* d_ws, void* stream);
+
+/* pnp_power_iter for L = ||A_s S||^2 with S of the given kind. */
+int pnp_power_iter_kind(const pnp_geom* g, int factor, int kind, int max_iters, double tol, double* h_L,
+                        int* h_iters, void* d_ws, void* stream);
 
 /* Algorithm 1 (PnP-MS2G) on every image of the batch.
  *   stages[n_stages]   the schedule; h_eta[n_stages] step sizes eta_k

@@ -38,7 +38,10 @@ class Geom(C.Structure):
 
 
 class StageC(C.Structure):
-    _fields_ = [("factor", C.c_int32), ("iters", C.c_int32), ("n_subsets", C.c_int32)]
+    _fields_ = [("factor", C.c_int32), ("iters", C.c_int32), ("n_subsets", C.c_int32), ("kind", C.c_int32)]
+
+
+SKETCH_POOL, SKETCH_BICUBIC = 0, 1
 
 
 class RunParams(C.Structure):
@@ -102,6 +105,10 @@ def load(path: Optional[str] = None):
             "pnp_full_grad_noalloc": [gp, vp, vp, vp, vp],
             "pnp_run_many": [C.POINTER(ProblemC), i32, C.POINTER(RunParams), vp],
             "pnp_set_weights": [gp, vp, vp],
+            "pnp_sketch_kind": [gp, i32, i32, vp, vp, vp],
+            "pnp_upsample_kind": [gp, i32, i32, vp, vp, vp],
+            "pnp_sketch_grad_kind": [gp, i32, i32, vp, vp, vp, i32, i32, vp, vp],
+            "pnp_power_iter_kind": [gp, i32, i32, i32, C.c_double, dp, C.POINTER(i32), vp, vp],
             "pnp_autotune": [gp, C.POINTER(StageC), i32, C.POINTER(RunParams), vp, vp],
             "pnp_tv_vjp_workspace_size": [i32, i32, i32, C.POINTER(sz)],
             "pnp_tv_vjp": [vp, vp, vp, dp, i32, i32, C.c_float, i32, vp, sz, vp],
@@ -201,16 +208,16 @@ def backproject(g, factor, sino, img, subset=0, n_subsets=1, ws=None, stream=Non
                                   _ws(ws)[0], _stream(stream)))
 
 
-def sketch(g, factor, fine, coarse, stream=None):
+def sketch(g, factor, fine, coarse, stream=None, kind=0):
     ns = g.n // factor
-    _check(load().pnp_sketch(C.byref(geom(g)), factor, _ptr(fine, g.batch * g.n * g.n, "fine"),
-                             _ptr(coarse, g.batch * ns * ns, "coarse"), _stream(stream)))
+    _check(load().pnp_sketch_kind(C.byref(geom(g)), factor, int(kind), _ptr(fine, g.batch * g.n * g.n, "fine"),
+                                  _ptr(coarse, g.batch * ns * ns, "coarse"), _stream(stream)))
 
 
-def upsample(g, factor, coarse, fine, stream=None):
+def upsample(g, factor, coarse, fine, stream=None, kind=0):
     ns = g.n // factor
-    _check(load().pnp_upsample(C.byref(geom(g)), factor, _ptr(coarse, g.batch * ns * ns, "coarse"),
-                               _ptr(fine, g.batch * g.n * g.n, "fine"), _stream(stream)))
+    _check(load().pnp_upsample_kind(C.byref(geom(g)), factor, int(kind), _ptr(coarse, g.batch * ns * ns, "coarse"),
+                                    _ptr(fine, g.batch * g.n * g.n, "fine"), _stream(stream)))
 
 
 def full_grad(g, x, b, out, ws, stream=None):
@@ -228,11 +235,11 @@ def full_grad_noalloc(g, x, b, out, stream=None):
                                         _stream(stream)))
 
 
-def sketch_grad(g, factor, y, b, out, subset=0, n_subsets=1, ws=None, stream=None):
+def sketch_grad(g, factor, y, b, out, subset=0, n_subsets=1, ws=None, stream=None, kind=0):
     img = g.batch * g.n * g.n
-    _check(load().pnp_sketch_grad(C.byref(geom(g)), factor, _ptr(y, img, "y"),
-                                  _ptr(b, g.batch * g.n_views * g.n_det, "b"), _ptr(out, img, "g"),
-                                  subset, n_subsets, _ws(ws)[0], _stream(stream)))
+    _check(load().pnp_sketch_grad_kind(C.byref(geom(g)), factor, int(kind), _ptr(y, img, "y"),
+                                       _ptr(b, g.batch * g.n_views * g.n_det, "b"), _ptr(out, img, "g"),
+                                       subset, n_subsets, _ws(ws)[0], _stream(stream)))
 
 
 def tv_workspace_size(n: int, batch: int) -> int:
@@ -247,19 +254,20 @@ def tv_denoise(z, x, n, batch, lam, iters, ws, stream=None):
                                  float(lam), int(iters), p, nbytes, _stream(stream)))
 
 
-def power_iter(g, factor, max_iters=100, tol=1e-7, ws=None, stream=None):
+def power_iter(g, factor, max_iters=100, tol=1e-7, ws=None, stream=None, kind=0):
     L = C.c_double(0.0)
     it = C.c_int(0)
-    _check(load().pnp_power_iter(C.byref(geom(g)), factor, max_iters, tol, C.byref(L), C.byref(it),
-                                 _ws(ws)[0], _stream(stream)))
+    _check(load().pnp_power_iter_kind(C.byref(geom(g)), factor, int(kind), max_iters, tol, C.byref(L),
+                                      C.byref(it), _ws(ws)[0], _stream(stream)))
     return float(L.value), int(it.value)
 
 
 def _stages(stages: Sequence):
     arr = (StageC * len(stages))()
     for k, s in enumerate(stages):
-        f, it, P = (s.factor, s.iters, s.n_subsets) if hasattr(s, "factor") else s
-        arr[k] = StageC(int(f), int(it), int(P))
+        f, it, P, kind = ((s.factor, s.iters, s.n_subsets, getattr(s, "kind", 0)) if hasattr(s, "factor")
+                          else (tuple(s) + (0,))[:4])
+        arr[k] = StageC(int(f), int(it), int(P), int(kind))
     return arr
 
 
@@ -330,11 +338,11 @@ class Plan:
     def full_grad(self, x, b, out, stream=None):
         full_grad(self.g, x, b, out, self.ws, stream)
 
-    def sketch_grad(self, factor, y, b, out, subset=0, n_subsets=1, stream=None):
-        sketch_grad(self.g, factor, y, b, out, subset, n_subsets, self.ws, stream)
+    def sketch_grad(self, factor, y, b, out, subset=0, n_subsets=1, stream=None, kind=0):
+        sketch_grad(self.g, factor, y, b, out, subset, n_subsets, self.ws, stream, kind)
 
-    def power_iter(self, factor, max_iters=100, tol=1e-7, stream=None):
-        return power_iter(self.g, factor, max_iters, tol, self.ws, stream)
+    def power_iter(self, factor, max_iters=100, tol=1e-7, stream=None, kind=0):
+        return power_iter(self.g, factor, max_iters, tol, self.ws, stream, kind)
 
     def run(self, stages, eta, seq, b, x, **kw):
         return run(self.g, stages, eta, seq, b, x, ws=self.ws, **kw)

@@ -118,6 +118,7 @@ Layout make_layout(const pnp_geom& g)
     L.off_z = off; off = align_up(off + img * sizeof(float));
     L.off_tv = off; off = align_up(off + 8 * img * sizeof(float));
     L.off_pw = off; off = align_up(off + 2 * (size_t)g.n * g.n * sizeof(float));
+    L.off_cs = off; off = align_up(off + 2 * (size_t)g.batch * (g.n / 2) * (g.n / 2) * sizeof(float));
     const size_t tv_parts = (size_t)tile_tv_parts(g.n, g.batch);
     const size_t parts = tv_parts > (size_t)kRedBlocks ? tv_parts : (size_t)kRedBlocks;
     L.off_red = off; off = align_up(off + ((size_t)g.batch * parts + (size_t)g.batch * 8) * sizeof(double));
@@ -286,11 +287,25 @@ BackArgs back_args(const pnp_geom& g, const LevelLayout& lv, char* ws, int p, in
 // Gradient estimate on the fine grid into `out` (mode GradFine) or the fused
 // step z = y - eta * grad (mode Step).  `y` is the fine iterate.
 int grad_into(const pnp_geom& g, const Layout& L, int li, char* ws, const float* y, const float* b,
-              int p, int P, int mode, float eta, float* out, cudaStream_t st)
+              int p, int P, int mode, float eta, float* out, cudaStream_t st, int kind = PNP_SKETCH_POOL)
 {
     const LevelLayout& lv = L.lv[li];
     const Tuned tu = reg_tuned(ws);
     float* res = (float*)(ws + L.off_res);
+    if (kind == PNP_SKETCH_BICUBIC && lv.factor > 1) {
+        // S y (bicubic) -> A_s -> A_s^T (coarse) -> U = S^T and the step on the fine grid
+        float* cimg = (float*)(ws + L.off_cs);
+        float* cgrad = cimg + (size_t)g.batch * (g.n / 2) * (g.n / 2);
+        PNP_CUDA(launch_bicubic_down(y, cimg, g.n, lv.factor, g.batch, st));
+        PNP_CUDA(launch_prep_quad(cimg, lv.ns, 1, g.batch, (float4*)(ws + lv.off_quad), lv.qw, st));
+        PNP_CUDA(launch_forward(fwd_args(g, lv, ws, p, P, b, res, g.batch, reg_weights(ws)), st, tu.lanes[li]));
+        const double c = P <= 1 ? 1.0 : (double)P;
+        PNP_CUDA(launch_backward(back_args(g, lv, ws, p, P, res, kBackRaw, (float)(g.step * lv.factor * c), nullptr,
+                                           0.0f, cgrad, g.batch), st, tu.groups[li]));
+        PNP_CUDA(launch_bicubic_up(cgrad, mode == kBackStep ? y : nullptr, out, g.n, lv.factor, g.batch, 1.0f, eta,
+                                   st));
+        return PNP_OK;
+    }
     PNP_CUDA(launch_prep_quad(y, g.n, lv.factor, g.batch, (float4*)(ws + lv.off_quad), lv.qw, st));
     PNP_CUDA(launch_forward(fwd_args(g, lv, ws, p, P, b, res, g.batch, reg_weights(ws)), st, tu.lanes[li]));
     const double c = P <= 1 ? 1.0 : (double)P;
@@ -436,34 +451,60 @@ int pnp_backproject(const pnp_geom* g, int factor, const float* d_sino, float* d
     return PNP_OK;
 }
 
-int pnp_sketch(const pnp_geom* g, int factor, const float* d_fine, float* d_coarse, void* stream)
+int pnp_sketch_kind(const pnp_geom* g, int factor, int kind, const float* d_fine, float* d_coarse, void* stream)
 {
     t_err.clear();
     if (int e = validate_geom(g)) return e;
     Layout L = make_layout(*g);
     int li;
     if (int e = check_level(*g, factor, L, &li)) return e;
+    if (kind != PNP_SKETCH_POOL && kind != PNP_SKETCH_BICUBIC) return fail(PNP_EINVAL, "unknown sketch kind %d", kind);
     if (!d_fine || !d_coarse) return fail(PNP_EINVAL, "image pointer is NULL");
-    PNP_CUDA(launch_pool(d_fine, d_coarse, g->n, factor, g->batch, S(stream)));
+    if (kind == PNP_SKETCH_BICUBIC)
+        PNP_CUDA(launch_bicubic_down(d_fine, d_coarse, g->n, factor, g->batch, S(stream)));
+    else
+        PNP_CUDA(launch_pool(d_fine, d_coarse, g->n, factor, g->batch, S(stream)));
+    return PNP_OK;
+}
+
+int pnp_sketch(const pnp_geom* g, int factor, const float* d_fine, float* d_coarse, void* stream)
+{
+    return pnp_sketch_kind(g, factor, PNP_SKETCH_POOL, d_fine, d_coarse, stream);
+}
+
+int pnp_upsample_kind(const pnp_geom* g, int factor, int kind, const float* d_coarse, float* d_fine,
+                      void* stream)
+{
+    t_err.clear();
+    if (int e = validate_geom(g)) return e;
+    Layout L = make_layout(*g);
+    int li;
+    if (int e = check_level(*g, factor, L, &li)) return e;
+    if (kind != PNP_SKETCH_POOL && kind != PNP_SKETCH_BICUBIC) return fail(PNP_EINVAL, "unknown sketch kind %d", kind);
+    if (!d_fine || !d_coarse) return fail(PNP_EINVAL, "image pointer is NULL");
+    if (kind == PNP_SKETCH_BICUBIC)
+        PNP_CUDA(launch_bicubic_up(d_coarse, nullptr, d_fine, g->n, factor, g->batch, 1.0f, 0.0f, S(stream)));
+    else
+        PNP_CUDA(launch_unpool(d_coarse, d_fine, g->n, factor, g->batch, S(stream)));
     return PNP_OK;
 }
 
 int pnp_upsample(const pnp_geom* g, int factor, const float* d_coarse, float* d_fine, void* stream)
 {
-    t_err.clear();
-    if (int e = validate_geom(g)) return e;
-    Layout L = make_layout(*g);
-    int li;
-    if (int e = check_level(*g, factor, L, &li)) return e;
-    if (!d_fine || !d_coarse) return fail(PNP_EINVAL, "image pointer is NULL");
-    PNP_CUDA(launch_unpool(d_coarse, d_fine, g->n, factor, g->batch, S(stream)));
-    return PNP_OK;
+    return pnp_upsample_kind(g, factor, PNP_SKETCH_POOL, d_coarse, d_fine, stream);
 }
 
 int pnp_sketch_grad(const pnp_geom* g, int factor, const float* d_y, const float* d_b, float* d_g,
                     int subset, int n_subsets, void* d_ws, void* stream)
 {
+    return pnp_sketch_grad_kind(g, factor, PNP_SKETCH_POOL, d_y, d_b, d_g, subset, n_subsets, d_ws, stream);
+}
+
+int pnp_sketch_grad_kind(const pnp_geom* g, int factor, int kind, const float* d_y, const float* d_b, float* d_g,
+                         int subset, int n_subsets, void* d_ws, void* stream)
+{
     t_err.clear();
+    if (kind != PNP_SKETCH_POOL && kind != PNP_SKETCH_BICUBIC) return fail(PNP_EINVAL, "unknown sketch kind %d", kind);
     if (int e = validate_geom(g)) return e;
     Layout L = make_layout(*g);
     int li;
@@ -473,7 +514,7 @@ int pnp_sketch_grad(const pnp_geom* g, int factor, const float* d_y, const float
     if (d_y == d_g) return fail(PNP_EINVAL, "y and g must not alias");
     if (int e = check_ws(*g, d_ws)) return e;
     return grad_into(*g, L, li, (char*)d_ws, d_y, d_b, subset, n_subsets, kBackGradFine, 0.0f, d_g,
-                     S(stream));
+                     S(stream), kind);
 }
 
 int pnp_full_grad(const pnp_geom* g, const float* d_x, const float* d_b, float* d_g, void* d_ws,
@@ -520,7 +561,14 @@ int pnp_tv_denoise(const float* d_z, float* d_x, int n, int batch, float lambda,
 int pnp_power_iter(const pnp_geom* g, int factor, int max_iters, double tol, double* h_L, int* h_iters,
                    void* d_ws, void* stream)
 {
+    return pnp_power_iter_kind(g, factor, PNP_SKETCH_POOL, max_iters, tol, h_L, h_iters, d_ws, stream);
+}
+
+int pnp_power_iter_kind(const pnp_geom* g, int factor, int kind, int max_iters, double tol, double* h_L,
+                        int* h_iters, void* d_ws, void* stream)
+{
     t_err.clear();
+    if (kind != PNP_SKETCH_POOL && kind != PNP_SKETCH_BICUBIC) return fail(PNP_EINVAL, "unknown sketch kind %d", kind);
     if (int e = validate_geom(g)) return e;
     Layout L = make_layout(*g);
     int li;
@@ -544,9 +592,20 @@ int pnp_power_iter(const pnp_geom* g, int factor, int max_iters, double tol, dou
     double lam = 0.0;
     int it = 0;
     for (it = 1; it <= max_iters; ++it) {
-        PNP_CUDA(launch_prep_quad(u, g->n, lv.factor, 1, (float4*)(ws + lv.off_quad), lv.qw, st));
-        PNP_CUDA(launch_forward(fwd_args(g1, lv, ws, 0, 1, nullptr, res, 1, reg_weights(ws)), st));
-        PNP_CUDA(launch_backward(back_args(g1, lv, ws, 0, 1, res, kBackGradFine, scale, nullptr, 0.0f, w, 1), st));
+        if (kind == PNP_SKETCH_BICUBIC && lv.factor > 1) {
+            float* cimg = (float*)(ws + L.off_cs);
+            float* cgrad = cimg + (size_t)g->batch * (g->n / 2) * (g->n / 2);
+            PNP_CUDA(launch_bicubic_down(u, cimg, g->n, lv.factor, 1, st));
+            PNP_CUDA(launch_prep_quad(cimg, lv.ns, 1, 1, (float4*)(ws + lv.off_quad), lv.qw, st));
+            PNP_CUDA(launch_forward(fwd_args(g1, lv, ws, 0, 1, nullptr, res, 1, reg_weights(ws)), st));
+            PNP_CUDA(launch_backward(back_args(g1, lv, ws, 0, 1, res, kBackRaw, (float)(g->step * lv.factor), nullptr,
+                                               0.0f, cgrad, 1), st));
+            PNP_CUDA(launch_bicubic_up(cgrad, nullptr, w, g->n, lv.factor, 1, 1.0f, 0.0f, st));
+        } else {
+            PNP_CUDA(launch_prep_quad(u, g->n, lv.factor, 1, (float4*)(ws + lv.off_quad), lv.qw, st));
+            PNP_CUDA(launch_forward(fwd_args(g1, lv, ws, 0, 1, nullptr, res, 1, reg_weights(ws)), st));
+            PNP_CUDA(launch_backward(back_args(g1, lv, ws, 0, 1, res, kBackGradFine, scale, nullptr, 0.0f, w, 1), st));
+        }
         PNP_CUDA(launch_reduce_partial(kRedDot, u, w, N, N, 1, g->n, part, st));
         PNP_CUDA(launch_reduce_final(part, kRedBlocks, 1, outv, 1, 0, st));
         PNP_CUDA(launch_reduce_partial(kRedSq, w, nullptr, N, N, 1, g->n, part, st));
@@ -594,6 +653,8 @@ int validate_problem(const pnp_problem& q, const pnp_run_params& pr, int idx, Pr
         if (q.stages[k].n_subsets < 1 || q.stages[k].n_subsets > g->n_views)
             return fail(PNP_EINVAL, "stage %d: n_subsets outside [1, n_views]", k);
         if (!(std::isfinite(q.h_eta[k]) && q.h_eta[k] >= 0.0)) return fail(PNP_EINVAL, "eta[%d] invalid", k);
+        if (q.stages[k].kind != PNP_SKETCH_POOL && q.stages[k].kind != PNP_SKETCH_BICUBIC)
+            return fail(PNP_EINVAL, "stage %d: unknown sketch kind %d", k, q.stages[k].kind);
         any_subsets |= q.stages[k].n_subsets > 1;
         total += q.stages[k].iters;
     }
@@ -667,6 +728,7 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
             BackArgs back[kMaxClasses];
             TvItem tv[kMaxClasses];
             int act[kMaxClasses];
+            int bic[kMaxClasses];
             int na = 0;
             const float amom = pr.momentum ? (float)((double)(i - 1) / (double)(i + 3)) : 0.0f;
             for (int c = 0; c < np; ++c) {
@@ -686,6 +748,15 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
                 float* y = (float*)(ws + L.off_y);
                 float* z = (float*)(ws + L.off_z);
                 float* res = (float*)(ws + L.off_res);
+                if (sk.kind == PNP_SKETCH_BICUBIC && lv.factor > 1) {
+                    // bicubic stages run their own gradient launches; the denoiser joins the rest
+                    if (int e = grad_into(g, L, li, ws, y, q.d_b, p, P, kBackStep, (float)q.h_eta[stage[c]], z, st,
+                                          PNP_SKETCH_BICUBIC))
+                        return e;
+                    bic[na] = 1;
+                } else {
+                    bic[na] = 0;
+                }
                 prep[na] = PrepArgs{y, g.n, lv.factor, g.batch, (float4*)(ws + lv.off_quad), lv.qw};
                 fwd[na] = fwd_args(g, lv, ws, p, P, q.d_b, res, g.batch, reg_weights(ws));
                 const double cs = P <= 1 ? 1.0 : (double)P;
@@ -710,9 +781,24 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
                 const pnp_problem& q = pb[0];
                 li0 = level_index(q.stages[stage[0]].factor);
             }
-            PNP_CUDA(launch_prep_multi(prep, na, st));
-            PNP_CUDA(launch_forward_multi(fwd, na, st, one ? tu.lanes[li0] : 0));
-            PNP_CUDA(launch_backward_multi(back, na, st, one ? tu.groups[li0] : 0));
+            {   // pooled-sketch classes share one launch per phase
+                PrepArgs pp[kMaxClasses];
+                FwdArgs ff[kMaxClasses];
+                BackArgs bb[kMaxClasses];
+                int m = 0;
+                for (int a = 0; a < na; ++a) {
+                    if (bic[a]) continue;
+                    pp[m] = prep[a];
+                    ff[m] = fwd[a];
+                    bb[m] = back[a];
+                    ++m;
+                }
+                if (m > 0) {
+                    PNP_CUDA(launch_prep_multi(pp, m, st));
+                    PNP_CUDA(launch_forward_multi(ff, m, st, one ? tu.lanes[li0] : 0));
+                    PNP_CUDA(launch_backward_multi(bb, m, st, one ? tu.groups[li0] : 0));
+                }
+            }
             if (do_tv) {
                 PNP_CUDA(launch_tv_tiled_multi(tv, na, pr.lambda, pr.tv_iters, pr.alpha, st));
             } else {

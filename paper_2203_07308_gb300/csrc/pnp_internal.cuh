@@ -50,6 +50,7 @@ struct Layout {
     size_t off_z = 0;        // float [batch][n][n]
     size_t off_tv = 0;       // float [8][batch][n][n]  TV state ping/pong (r1 r2 p1 p2)
     size_t off_pw = 0;       // float [2][n][n]   power iteration u, w
+    size_t off_cs = 0;       // float [2][batch][(n/2)^2] bicubic coarse image and coarse gradient
     size_t off_red = 0;      // double [batch][kRedBlocks] partials + [batch][8] results
     size_t off_log = 0;      // double [PNP_MAX_LOG_ITERS] (not used when batch grows; see api)
     size_t total = 0;
@@ -105,6 +106,11 @@ cudaError_t launch_backward(const BackArgs& a, cudaStream_t st, int groups = 0);
 cudaError_t launch_backward_multi(const BackArgs* items, int count, cudaStream_t st, int groups = 0);
 
 cudaError_t launch_pool(const float* fine, float* coarse, int n, int s, int batch, cudaStream_t st);
+// Bicubic sketch (kind PNP_SKETCH_BICUBIC) and its adjoint: out = base - eta scale S^T g,
+// or scale S^T g when base is null.
+cudaError_t launch_bicubic_down(const float* fine, float* coarse, int n, int s, int batch, cudaStream_t st);
+cudaError_t launch_bicubic_up(const float* g, const float* base, float* out, int n, int s, int batch,
+                              float scale, float eta, cudaStream_t st);
 cudaError_t launch_unpool(const float* coarse, float* fine, int n, int s, int batch, cudaStream_t st);
 
 // TV (FGP) --------------------------------------------------------------------

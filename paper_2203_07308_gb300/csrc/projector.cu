@@ -350,6 +350,81 @@ __global__ void __launch_bounds__(512, 2) k_backward2x2(const BackTable t)
     }
 }
 
+// ------------------------------------------------------------------ bicubic S and S^T
+// The paper's sketch and upsampler are bicubic resizes (Sec. 3).  Here S is
+// separable: coarse pixel I (centre X_I = s I + (s-1)/2 in fine index units)
+// averages fine pixels x with weights k((x - X_I)/s) / sum_x' k((x' - X_I)/s),
+// k the Keys cubic convolution kernel with a = -1/2, widened by s (so no
+// aliasing), the sum running over the fine pixels inside the image.  U = S^T.
+__device__ __forceinline__ float keys_kernel(float t)
+{
+    const float a = -0.5f;
+    t = fabsf(t);
+    if (t <= 1.0f) return ((a + 2.0f) * t - (a + 3.0f)) * t * t + 1.0f;
+    if (t < 2.0f) return ((a * t - 5.0f * a) * t + 8.0f * a) * t - 4.0f * a;
+    return 0.0f;
+}
+
+// Normalisation of coarse index I's weights (sum over its support inside [0, n)).
+__device__ __forceinline__ float bicubic_den(int I, int s, int n)
+{
+    const float XI = s * I + 0.5f * (s - 1);
+    const int x0 = max(0, (int)ceilf(XI - 2.0f * s)), x1 = min(n - 1, (int)floorf(XI + 2.0f * s));
+    float den = 0.0f;
+    for (int x = x0; x <= x1; ++x) den += keys_kernel(((float)x - XI) / (float)s);
+    return den;
+}
+
+__global__ void k_bicubic_down(const float* __restrict__ fine, float* __restrict__ coarse, int n, int s)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int inst = blockIdx.z;
+    const int ns = n / s;
+    if (I >= ns || J >= ns) return;
+    const float XI = s * I + 0.5f * (s - 1), YJ = s * J + 0.5f * (s - 1);
+    const int x0 = max(0, (int)ceilf(XI - 2.0f * s)), x1 = min(n - 1, (int)floorf(XI + 2.0f * s));
+    const int y0 = max(0, (int)ceilf(YJ - 2.0f * s)), y1 = min(n - 1, (int)floorf(YJ + 2.0f * s));
+    const float inv = 1.0f / ((float)s);
+    const float* f = fine + (long)inst * n * n;
+    float acc = 0.0f;
+    for (int y = y0; y <= y1; ++y) {
+        const float wy = keys_kernel(((float)y - YJ) * inv);
+        float row = 0.0f;
+        for (int x = x0; x <= x1; ++x) row = fmaf(keys_kernel(((float)x - XI) * inv), __ldg(f + (long)y * n + x), row);
+        acc = fmaf(wy, row, acc);
+    }
+    coarse[((long)inst * ns + J) * ns + I] = acc / (bicubic_den(I, s, n) * bicubic_den(J, s, n));
+}
+
+// out = (base ? base - eta * scale * S^T g : scale * S^T g) on the fine grid.
+__global__ void k_bicubic_up(const float* __restrict__ g, const float* __restrict__ base, float* __restrict__ out,
+                             int n, int s, float scale, float eta)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int inst = blockIdx.z;
+    const int ns = n / s;
+    if (x >= n || y >= n) return;
+    const float inv = 1.0f / ((float)s);
+    const float half = 0.5f * (s - 1);
+    const int Ic = (int)floorf(((float)x - half) * inv), Jc = (int)floorf(((float)y - half) * inv);
+    const float* gi = g + (long)inst * ns * ns;
+    float acc = 0.0f;
+    for (int J = max(0, Jc - 2); J <= min(ns - 1, Jc + 2); ++J) {
+        const float wy = keys_kernel(((float)y - (s * J + half)) * inv) / bicubic_den(J, s, n);
+        if (wy == 0.0f) continue;
+        float row = 0.0f;
+        for (int I = max(0, Ic - 2); I <= min(ns - 1, Ic + 2); ++I) {
+            const float wx = keys_kernel(((float)x - (s * I + half)) * inv);
+            if (wx != 0.0f) row = fmaf(wx / bicubic_den(I, s, n), __ldg(gi + (long)J * ns + I), row);
+        }
+        acc = fmaf(wy, row, acc);
+    }
+    const long o = ((long)inst * n + y) * n + x;
+    out[o] = base ? __ldg(base + o) - eta * scale * acc : scale * acc;
+}
+
 // ------------------------------------------------------------------ S and S^T
 __global__ void k_pool(const float* __restrict__ fine, float* __restrict__ coarse, int n, int s)
 {
@@ -518,6 +593,22 @@ cudaError_t launch_unpool(const float* coarse, float* fine, int n, int s, int ba
 {
     dim3 blk(32, 8), grd(div_up(n, 32), div_up(n, 8), batch);
     k_unpool<<<grd, blk, 0, st>>>(coarse, fine, n, s);
+    return counted();
+}
+
+cudaError_t launch_bicubic_down(const float* fine, float* coarse, int n, int s, int batch, cudaStream_t st)
+{
+    const int ns = n / s;
+    dim3 blk(16, 16), grd(div_up(ns, 16), div_up(ns, 16), batch);
+    k_bicubic_down<<<grd, blk, 0, st>>>(fine, coarse, n, s);
+    return counted();
+}
+
+cudaError_t launch_bicubic_up(const float* g, const float* base, float* out, int n, int s, int batch,
+                              float scale, float eta, cudaStream_t st)
+{
+    dim3 blk(32, 8), grd(div_up(n, 32), div_up(n, 8), batch);
+    k_bicubic_up<<<grd, blk, 0, st>>>(g, base, out, n, s, scale, eta);
     return counted();
 }
 
