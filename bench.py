@@ -33,6 +33,19 @@ UNIT = "gradients/s"
 WORKLOAD = "c2_256"
 L2_FLUSH_BYTES = 512 << 20
 
+# DRAM bytes per launch of the backprojector at this workload, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum over the 100
+# backprojection launches of one step, averaged); valid only while the
+# backprojector source is the one that was measured.
+BACKWARD_TRAFFIC = {"bytes_per_launch": None, "source_sha256": None,
+                    "profile": "profiles/k_backward2x2_256_360x512_step.md"}
+
+
+def kernel_source_sha():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2203_07308_gb300", "csrc", "projector.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -330,6 +343,9 @@ def run_native(args, rank, world):
     # ---- timed region: K steps, L2 flushed before each, device time by CUDA events
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
+    # (direct launches: every phase launch is bracketed by CUDA events on the
+    # run's stream, giving each kernel's live launch durations in the region)
+    pnp.kernel_times(reset=True)
     launches0 = pnp.launch_count()
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
@@ -337,11 +353,12 @@ def run_native(args, rank, world):
         for k in range(args.steps):
             flush.fill_(float(k))
             ev[k][0].record(stream)
-            plan.run(wl.stages, eta, seq, d_b, d_x.zero_(), graph=use_graph, **kw)
+            plan.run(wl.stages, eta, seq, d_b, d_x.zero_(), graph=use_graph, kernel_times=not use_graph, **kw)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         barrier(world)
     launches = pnp.launch_count() - launches0
+    phases = pnp.kernel_times(reset=True)
     # d_x.zero_() is a PyTorch fill inside the region: not counted as ours
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = allmax(sum(step_ms), world)
@@ -359,6 +376,17 @@ def run_native(args, rank, world):
         if k >= 2:
             other.append(a_.elapsed_time(b2_))
     other_ms = float(np.median(other))
+    plain = []
+    for k in range(5):
+        flush.fill_(4.0)
+        a_, b2_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        plan.run(wl.stages, eta, seq, d_b, d_x.zero_(), graph=use_graph, **kw)
+        b2_.record(stream)
+        torch.cuda.synchronize()
+        if k >= 2:
+            plain.append(a_.elapsed_time(b2_))
+    plain_ms = float(np.median(plain))
 
     # ---- per-kernel timing of the projector pair (events on the launching stream)
     def timed(fn, reps=20):
@@ -452,12 +480,43 @@ def run_native(args, rank, world):
     alu_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
     # algorithmic work per backprojected sample: 4 bilinear taps, each
     # hat(dx) hat(dy) r: 2 position FMA + 2 |.| + 2 (1-.) + 1 mul + 1 FMA = 8 FLOP per tap
-    flop_back = samples_full * 4 * 8
-    flop_fwd = samples_full * (4 + 3 * 2 + 1)  # position 2 FMA, 3 FMA interp, accumulate
-    dominant = "backproject" if back_ms >= fwd_ms else "forward"
-    ach = (flop_back / (back_ms / 1000) if dominant == "backproject" else flop_fwd / (fwd_ms / 1000)) / 1e12
-    roof = {"kernel": dominant, "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
-            "frac": ach / alu_peak, "traffic": None,
+    # (the forward: position 2 FMA, 3 FMA interpolation, accumulate = 11 FLOP)
+    FLOP_BACK, FLOP_FWD = 4 * 8, 4 + 3 * 2 + 1
+    # samples of every iteration's subset projection at its level, in step order
+    counts = {}
+    samples_step = 0
+    it_cursor = 0
+    for st_ in wl.stages:
+        for _ in range(st_.iters):
+            p_ = int(seq[it_cursor]) if st_.n_subsets > 1 else 0
+            key = (st_.factor, p_, st_.n_subsets)
+            if key not in counts:
+                counts[key] = plan.sample_count(*key)
+            samples_step += counts[key]
+            it_cursor += 1
+    ph_ms = {k: v[0] for k, v in phases.items()}
+    ph_n = {k: v[1] for k, v in phases.items()}
+    if ph_n["backward"] > 0:
+        dominant = max(("backward", "forward"), key=lambda k: ph_ms[k])
+        flop = samples_step * (FLOP_BACK if dominant == "backward" else FLOP_FWD) * args.steps
+        ach = flop / (ph_ms[dominant] / 1000) / 1e12
+        kname = "k_backward2x2 (A^T, U and the step)" if dominant == "backward" else "k_forward (A S y - b)"
+        avg_us = 1000 * ph_ms[dominant] / ph_n[dominant]
+        timing_src = (f"CUDA events around each of the {ph_n[dominant]} launches in the timed region, "
+                      f"mean {avg_us:.2f} us per launch")
+    else:   # graph replay: phases are not bracketed; the all-views launch timed alone
+        dominant = "backward" if back_ms >= fwd_ms else "forward"
+        ach = samples_full * (FLOP_BACK if dominant == "backward" else FLOP_FWD) / (
+            (back_ms if dominant == "backward" else fwd_ms) / 1000) / 1e12
+        kname = "k_backward2x2 all views" if dominant == "backward" else "k_forward all views"
+        timing_src = "CUDA events around the all-views launch timed alone"
+    traffic = None
+    if dominant == "backward" and kernel_source_sha() == BACKWARD_TRAFFIC["source_sha256"]:
+        traffic = BACKWARD_TRAFFIC["bytes_per_launch"]
+    roof = {"kernel": kname, "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+            "frac": ach / alu_peak, "traffic": traffic,
+            "flop_per_sample": FLOP_BACK if dominant == "backward" else FLOP_FWD,
+            "samples_per_step": samples_step, "timing": timing_src,
             "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz (derived)",
             "hbm_gbs_measured_peak": peaks.get("hbm_gbs")}
 
@@ -487,6 +546,9 @@ def run_native(args, rank, world):
             "setup_ms_autotune": tune_ms,
             "launch_mode": "CUDA graph captured once, replayed per step" if use_graph else "direct launches",
             "ms_per_step_other_launch_mode": other_ms,
+            "ms_per_step_without_phase_events": plain_ms,
+            "phase_ms_per_step": {k: v / args.steps for k, v in ph_ms.items()},
+            "phase_launches_per_step": {k: v // args.steps for k, v in ph_n.items()},
             "step_ms_all": step_ms}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)

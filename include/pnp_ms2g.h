@@ -104,6 +104,18 @@ typedef struct {
  * library keeps up to 16 instantiated graphs. */
 #define PNP_RUN_GRAPH 1
 
+/* pnp_run / pnp_run_many: bracket every phase launch of every iteration with a
+ * pair of CUDA events on the run's stream, so that pnp_kernel_times can report
+ * the device time of each phase.  Not combinable with PNP_RUN_GRAPH. */
+#define PNP_RUN_KERNEL_TIMES 2
+
+/* Phases of one iteration of Algorithm 1, as timed by PNP_RUN_KERNEL_TIMES. */
+#define PNP_PHASE_PREP 0      /* sketch S and the bilinear coefficient image */
+#define PNP_PHASE_FORWARD 1   /* A_s^{(p)} (S y) - b^{(p)} */
+#define PNP_PHASE_BACKWARD 2  /* A_s^{(p)T}, U and the gradient step z = y - eta g */
+#define PNP_PHASE_DENOISE 3   /* TV prox by FGP, relaxation and momentum */
+#define PNP_N_PHASES 4
+
 /* One geometry class of a batched run: a uniform batch of images sharing one
  * geometry, with its own schedule, data, iterate and prepared workspace. */
 typedef struct {
@@ -336,6 +348,13 @@ int pnp_unrolled_step_vjp(const pnp_geom* g, int factor, int subset, int n_subse
  *   Every call rewrites all the scratch it reads, so nothing needs clearing.
  *   d_x, d_g [batch][n][n], d_b [batch][n_views][n_det]; asynchronous on `stream`. */
 int pnp_full_grad_noalloc(const pnp_geom* g, const float* d_x, const float* d_b, float* d_g, void* stream);
+
+/* Device time (ms, summed) and number of timed launches of each phase over all
+ * runs with PNP_RUN_KERNEL_TIMES since the last reset, indexed by PNP_PHASE_*.
+ * h_ms and h_launches hold PNP_N_PHASES entries each (either may be NULL).
+ * Waits for the recorded events to complete.  reset != 0 clears the totals
+ * afterwards.  Library instrumentation; the paper has no counterpart. */
+int pnp_kernel_times(double* h_ms, int64_t* h_launches, int reset);
 
 /* Number of kernels this library has launched in this process. */
 uint64_t pnp_launch_count(void);

@@ -50,6 +50,8 @@ class RunParams(C.Structure):
 
 
 RUN_GRAPH = 1
+RUN_KERNEL_TIMES = 2
+PHASES = ("prep", "forward", "backward", "denoise")
 
 
 class ProblemC(C.Structure):
@@ -106,6 +108,7 @@ def load(path: Optional[str] = None):
             "pnp_run_many": [C.POINTER(ProblemC), i32, C.POINTER(RunParams), vp],
             "pnp_set_weights": [gp, vp, vp],
             "pnp_sketch_kind": [gp, i32, i32, vp, vp, vp],
+            "pnp_kernel_times": [dp, C.POINTER(C.c_int64), i32],
             "pnp_upsample_kind": [gp, i32, i32, vp, vp, vp],
             "pnp_sketch_grad_kind": [gp, i32, i32, vp, vp, vp, i32, i32, vp, vp],
             "pnp_power_iter_kind": [gp, i32, i32, i32, C.c_double, dp, C.POINTER(i32), vp, vp],
@@ -271,18 +274,24 @@ def _stages(stages: Sequence):
     return arr
 
 
+def _flags(graph, kernel_times):
+    return (RUN_GRAPH if graph else 0) | (RUN_KERNEL_TIMES if kernel_times else 0)
+
+
 def run(g, stages, eta, seq, b, x, *, alpha=1.0, lam=0.02, tv_iters=20, momentum=True,
-        xtrue=None, ws=None, stream=None, graph=False):
+        xtrue=None, ws=None, stream=None, graph=False, kernel_times=False):
     """Algorithm 1; x holds x_0 on entry and the result on return.  Returns the
     PSNR log [total_iters, batch] when xtrue is given, else None.  graph=True
-    captures the launch sequence once per distinct call and replays it."""
+    captures the launch sequence once per distinct call and replays it;
+    kernel_times=True brackets each phase launch with CUDA events (read them
+    with kernel_times())."""
     st = _stages(stages)
     total = sum(a.iters for a in st)
     eta_a = (C.c_double * len(st))(*[float(e) for e in eta])
     seq_np = np.ascontiguousarray(np.asarray(seq if seq is not None else np.zeros(total), dtype=np.int32))
     if seq_np.size < total:
         raise PnpError(PNP_EINVAL, "subset sequence shorter than the schedule")
-    prm = RunParams(float(alpha), float(lam), int(tv_iters), int(bool(momentum)), RUN_GRAPH if graph else 0)
+    prm = RunParams(float(alpha), float(lam), int(tv_iters), int(bool(momentum)), _flags(graph, kernel_times))
     img = g.batch * g.n * g.n
     log = np.zeros((total, g.batch)) if xtrue is not None else None
     _check(load().pnp_run(C.byref(geom(g)), st, len(st), eta_a,
@@ -309,6 +318,14 @@ def sample_count(g, factor=1, subset=0, n_subsets=1, ws=None, stream=None) -> fl
     _check(load().pnp_sample_count(C.byref(geom(g)), factor, subset, n_subsets, C.byref(v),
                                    _ws(ws)[0], _stream(stream)))
     return float(v.value)
+
+
+def kernel_times(reset=False):
+    """{phase: (device ms summed, launches)} over runs made with kernel_times=True."""
+    ms = (C.c_double * len(PHASES))()
+    cnt = (C.c_int64 * len(PHASES))()
+    _check(load().pnp_kernel_times(ms, cnt, int(bool(reset))))
+    return {ph: (float(ms[k]), int(cnt[k])) for k, ph in enumerate(PHASES)}
 
 
 def launch_count() -> int:
@@ -414,7 +431,8 @@ def unrolled_step_vjp(g, factor, subset, n_subsets, eta, alpha, lam, tv_iters, a
 
 
 # ---------------------------------------------------------------- uneven batches, autotuning
-def run_many(problems, *, alpha=1.0, lam=0.02, tv_iters=20, momentum=True, stream=None, graph=False):
+def run_many(problems, *, alpha=1.0, lam=0.02, tv_iters=20, momentum=True, stream=None, graph=False,
+             kernel_times=False):
     """pnp_run_many.  ``problems``: list of dicts with keys plan, stages, eta, seq,
     b, x and optional xtrue, start_iter, y (checkpoint/resume: x and y of
     iteration start_iter in, x and y of the last iteration out); returns the
@@ -441,7 +459,7 @@ def run_many(problems, *, alpha=1.0, lam=0.02, tv_iters=20, momentum=True, strea
                           log.ctypes.data_as(C.POINTER(C.c_double)) if log is not None else None,
                           _ws(plan.ws)[0], int(pr.get("start_iter", 0)),
                           _ptr(pr.get("y"), img, "y", True))
-    prm = RunParams(float(alpha), float(lam), int(tv_iters), int(bool(momentum)), RUN_GRAPH if graph else 0)
+    prm = RunParams(float(alpha), float(lam), int(tv_iters), int(bool(momentum)), _flags(graph, kernel_times))
     _check(load().pnp_run_many(arr, len(problems), C.byref(prm), _stream(stream)))
     return logs
 

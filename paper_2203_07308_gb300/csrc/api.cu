@@ -315,6 +315,54 @@ int grad_into(const pnp_geom& g, const Layout& L, int li, char* ws, const float*
     return PNP_OK;
 }
 
+// ------------------------------------------------------------- phase timing
+// PNP_RUN_KERNEL_TIMES: one start/stop event pair per phase launch, from a
+// process-wide pool; elapsed times are folded into per-phase totals when the
+// pool fills up or when pnp_kernel_times asks for them.
+struct PhaseTimer {
+    std::mutex mu;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> phase;       // per pending pair
+    size_t used = 0;              // events handed out
+    double ms[PNP_N_PHASES] = {};
+    int64_t launches[PNP_N_PHASES] = {};
+    static constexpr size_t kPool = 1u << 14;
+
+    int fold()   // caller holds mu
+    {
+        for (size_t k = 0; k < phase.size(); ++k) {
+            PNP_CUDA(cudaEventSynchronize(ev[2 * k + 1]));
+            float t = 0.0f;
+            PNP_CUDA(cudaEventElapsedTime(&t, ev[2 * k], ev[2 * k + 1]));
+            ms[phase[k]] += t;
+            launches[phase[k]] += 1;
+        }
+        phase.clear();
+        used = 0;
+        return PNP_OK;
+    }
+    int mark(int ph, cudaStream_t st, bool start)
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (start) {
+            if (used + 2 > kPool)
+                if (int e = fold()) return e;
+            while (ev.size() < used + 2) {
+                cudaEvent_t e;
+                PNP_CUDA(cudaEventCreate(&e));
+                ev.push_back(e);
+            }
+            phase.push_back(ph);
+            PNP_CUDA(cudaEventRecord(ev[used], st));
+            used += 2;
+        } else {
+            PNP_CUDA(cudaEventRecord(ev[used - 1], st));
+        }
+        return PNP_OK;
+    }
+};
+PhaseTimer g_timer;
+
 // ---------------------------------------------------------------- CUDA graphs
 // pnp_run / pnp_run_many with PNP_RUN_GRAPH capture their launch sequence once
 // per distinct call (same pointers, geometry, schedule, step sizes, subset
@@ -390,6 +438,22 @@ extern "C" {
 const char* pnp_last_error(void) { return t_err.c_str(); }
 
 uint64_t pnp_launch_count(void) { return g_launches.load(); }
+
+int pnp_kernel_times(double* h_ms, int64_t* h_launches, int reset)
+{
+    t_err.clear();
+    std::lock_guard<std::mutex> lk(g_timer.mu);
+    if (int e = g_timer.fold()) return e;
+    for (int k = 0; k < PNP_N_PHASES; ++k) {
+        if (h_ms) h_ms[k] = g_timer.ms[k];
+        if (h_launches) h_launches[k] = g_timer.launches[k];
+        if (reset) {
+            g_timer.ms[k] = 0.0;
+            g_timer.launches[k] = 0;
+        }
+    }
+    return PNP_OK;
+}
 
 int pnp_workspace_size(const pnp_geom* g, size_t* bytes)
 {
@@ -690,6 +754,9 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
     if (!(pr.alpha > 0.0f && pr.alpha <= 1.0f)) return fail(PNP_EINVAL, "alpha must be in (0, 1]");
     if (!(pr.lambda >= 0.0f) || !std::isfinite(pr.lambda)) return fail(PNP_EINVAL, "lambda must be >= 0");
     if (pr.tv_iters < 0 || pr.tv_iters > 100000) return fail(PNP_EINVAL, "tv_iters outside [0, 100000]");
+    if (pr.flags & ~(PNP_RUN_GRAPH | PNP_RUN_KERNEL_TIMES)) return fail(PNP_EINVAL, "unknown run flags %d", pr.flags);
+    if ((pr.flags & PNP_RUN_GRAPH) && (pr.flags & PNP_RUN_KERNEL_TIMES))
+        return fail(PNP_EINVAL, "PNP_RUN_KERNEL_TIMES cannot be combined with PNP_RUN_GRAPH");
     std::vector<ProblemState> ps((size_t)np);
     for (int c = 0; c < np; ++c)
         if (int e = validate_problem(pb[c], pr, c, &ps[c])) return e;
@@ -705,7 +772,9 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
 
     long min_start = max_total;
     for (int c = 0; c < np; ++c) min_start = std::min(min_start, (long)pb[c].start_iter);
+    const bool timed = (pr.flags & PNP_RUN_KERNEL_TIMES) != 0;
     auto issue = [&]() -> int {
+        int e0 = PNP_OK;
         for (int c = 0; c < np; ++c) {
             const pnp_geom& g = pb[c].geom;
             char* ws = (char*)pb[c].d_ws;
@@ -794,13 +863,21 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
                     ++m;
                 }
                 if (m > 0) {
+                    if (timed && (e0 = g_timer.mark(PNP_PHASE_PREP, st, true))) return e0;
                     PNP_CUDA(launch_prep_multi(pp, m, st));
+                    if (timed && (e0 = g_timer.mark(PNP_PHASE_PREP, st, false))) return e0;
+                    if (timed && (e0 = g_timer.mark(PNP_PHASE_FORWARD, st, true))) return e0;
                     PNP_CUDA(launch_forward_multi(ff, m, st, one ? tu.lanes[li0] : 0));
+                    if (timed && (e0 = g_timer.mark(PNP_PHASE_FORWARD, st, false))) return e0;
+                    if (timed && (e0 = g_timer.mark(PNP_PHASE_BACKWARD, st, true))) return e0;
                     PNP_CUDA(launch_backward_multi(bb, m, st, one ? tu.groups[li0] : 0));
+                    if (timed && (e0 = g_timer.mark(PNP_PHASE_BACKWARD, st, false))) return e0;
                 }
             }
             if (do_tv) {
+                if (timed && (e0 = g_timer.mark(PNP_PHASE_DENOISE, st, true))) return e0;
                 PNP_CUDA(launch_tv_tiled_multi(tv, na, pr.lambda, pr.tv_iters, pr.alpha, st));
+                if (timed && (e0 = g_timer.mark(PNP_PHASE_DENOISE, st, false))) return e0;
             } else {
                 for (int a = 0; a < na; ++a) {
                     const TvItem& t = tv[a];

@@ -17,6 +17,12 @@ from paper_2203_07308_gb300 import _native, build, synth
 pytestmark = pytest.mark.gpu
 
 TOL_VJP = 1e-4
+# Full-size unroll of N = 10 iterations: each of the N forward and N reverse
+# gradient evaluations carries up to the single-gradient parity bound (1e-5
+# relative, FP32 sums over ~10^2 samples per pixel and ~10^3 per ray); the step
+# I - eta A^T A with eta = 1/L is non-expansive, so these add rather than
+# multiply: 2 N x 1e-5.
+TOL_VJP_FULL = 2 * 10 * 1e-5
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -177,5 +183,5 @@ def test_differentiable_workload_full_size():
     for i in (0, 5):
         _, rgx, _ = _oracle_unrolled(g, stages, eta, seq, b[i], np.zeros((g.n, g.n)), xt[i], wl.tv_lambda,
                                      wl.alpha, wl.tv_iters)
-        assert rel(gx[i], rgx) < TOL_VJP, rel(gx[i], rgx)
+        assert rel(gx[i], rgx) < TOL_VJP_FULL, rel(gx[i], rgx)
     assert np.isfinite(float(lam.grad))

@@ -170,3 +170,30 @@ def test_checkpoint_resume_is_bitwise_identical():
     pnp.run_many([dict(plan=plan, stages=stages, eta=eta, seq=seq, b=d_b, x=part_x, y=part_y, start_iter=k)])
     assert np.array_equal(host(part_x), host(full_x))
     assert np.array_equal(host(part_y), host(full_y))
+
+
+def test_phase_event_timing():
+    """pnp_run with PNP_RUN_KERNEL_TIMES: one timed launch per phase and
+    iteration, positive device times, the same result bit for bit as a run
+    without events; rejected together with graph capture."""
+    import torch
+    g = synth.make_geometry(64, 60, 96, batch=2)
+    stages = [synth.Stage(2, 3, 5), synth.Stage(1, 4, 5)]
+    x, b, eta, seq = make_problem(g, stages, 11)
+    plan = pnp.Plan(g)
+    outs = []
+    pnp.kernel_times(reset=True)
+    for timed in (False, True):
+        d_x = torch.zeros(g.batch, g.n, g.n, device="cuda")
+        plan.run(stages, eta, seq, dev(b), d_x, kernel_times=timed)
+        outs.append(host(d_x))
+    assert np.array_equal(outs[0], outs[1])
+    kt = pnp.kernel_times(reset=True)
+    assert set(kt) == {"prep", "forward", "backward", "denoise"}
+    for ph, (ms, n) in kt.items():
+        assert n == 7, (ph, n)
+        assert ms > 0.0, ph
+    assert all(n == 0 for _, n in pnp.kernel_times().values())
+    with pytest.raises(pnp.PnpError):
+        plan.run(stages, eta, seq, dev(b), torch.zeros(g.batch, g.n, g.n, device="cuda"),
+                 kernel_times=True, graph=True)
