@@ -95,6 +95,8 @@ def _load():
             lib.orc_objective.argtypes = [gp, dp, dp, dp]
             lib.orc_grad_w.argtypes = [gp, C.c_int, dp, dp, dp, dp, C.c_int, C.c_int]
             lib.orc_grad_wk.argtypes = [gp, C.c_int, C.c_int, dp, dp, dp, dp, C.c_int, C.c_int]
+            lib.orc_svrg_estimate.argtypes = [gp, C.c_int, C.c_int, dp, dp, dp, dp, dp, C.c_int, C.c_int, dp]
+            lib.orc_saga_estimate.argtypes = [gp, C.c_int, C.c_int, dp, dp, dp, dp, C.c_int, C.c_int, dp]
             lib.orc_power_iter_wk.argtypes = [gp, C.c_int, C.c_int, dp, C.c_int, C.c_double, ip]
             lib.orc_power_iter_wk.restype = C.c_double
             lib.orc_keys.argtypes = [C.c_double]
@@ -248,10 +250,11 @@ def psnr(x, xt) -> float:
 def pnp_run(g, stages: Sequence, eta: Sequence[float], seq, b, x0=None, *, alpha: float = 1.0,
             lam: float = 0.02, tv_iters: int = 20, momentum: bool = True, xt=None, w=None):
     """Algorithm 1 on one image; returns (x, psnr_log or None)."""
-    st = np.ascontiguousarray(np.array([[s.factor, s.iters, s.n_subsets, getattr(s, "kind", 0)]
-                                         if hasattr(s, "factor") else (list(s) + [0])[:4]
+    st = np.ascontiguousarray(np.array([[s.factor, s.iters, s.n_subsets, getattr(s, "kind", 0),
+                                          getattr(s, "estimator", 0)]
+                                         if hasattr(s, "factor") else (list(s) + [0, 0])[:5]
                                          for s in stages], dtype=np.int32).ravel())
-    total = int(sum(st[1::4]))
+    total = int(sum(st[1::5]))
     seq = np.ascontiguousarray(np.asarray(seq, dtype=np.int32))
     if seq.size < total:
         seq = np.concatenate([seq, np.zeros(total - seq.size, np.int32)])
@@ -262,10 +265,31 @@ def pnp_run(g, stages: Sequence, eta: Sequence[float], seq, b, x0=None, *, alpha
     log = np.zeros(total) if xt is not None else None
     ip = C.POINTER(C.c_int)
     ww = None if w is None else _f64(w)
-    _load().orc_pnp_run_w(C.byref(geom(g)), len(st) // 4, st.ctypes.data_as(ip), _dp(eta),
+    _load().orc_pnp_run_w(C.byref(geom(g)), len(st) // 5, st.ctypes.data_as(ip), _dp(eta),
                           seq.ctypes.data_as(ip), _dp(b), _dp(ww), _dp(x), float(alpha), float(lam),
                           int(tv_iters), int(bool(momentum)), _dp(xt_), _dp(log))
     return x, log
+
+
+def svrg_estimate(g, s: int, y, yt, mu, b, p: int, P: int, w=None, kind: int = 0) -> np.ndarray:
+    """SVRG estimate G_p(y) - G_p(yt) + mu (Johnson & Zhang 2013), G_p the vanilla
+    subset estimate of grad() (scaled by P); mu the full sketched gradient at yt."""
+    out = np.zeros((g.n, g.n))
+    ww = None if w is None else _f64(w)
+    _load().orc_svrg_estimate(C.byref(geom(g)), s, int(kind), _dp(_f64(y)), _dp(_f64(yt)), _dp(_f64(mu)),
+                              _dp(_f64(b)), _dp(ww), p, P, _dp(out))
+    return out
+
+
+def saga_estimate(g, s: int, y, psi, b, p: int, P: int, w=None, kind: int = 0) -> np.ndarray:
+    """SAGA estimate G_p(y) - psi_p + mean_j psi_j (Defazio et al. 2014); updates
+    psi[p] = G_p(y) in place (psi: float64 array [P, n, n])."""
+    assert psi.dtype == np.float64 and psi.flags.c_contiguous and psi.shape == (P, g.n, g.n)
+    out = np.zeros((g.n, g.n))
+    ww = None if w is None else _f64(w)
+    _load().orc_saga_estimate(C.byref(geom(g)), s, int(kind), _dp(_f64(y)), _dp(psi), _dp(_f64(b)), _dp(ww),
+                              p, P, _dp(out))
+    return out
 
 
 def objective(g, x, b, w=None):

@@ -495,7 +495,7 @@ double orc_psnr(long count, const double *x, const double *xt)
 
 /* Algorithm 1 (PnP-MS2G) on one image.
  *   stages      n_stages records (factor s_k, iterations N_k, subsets P_k, sketch kind:
- *               0 average pool, 1 bicubic)
+ *               0 average pool, 1 bicubic; subset estimator: 0 vanilla, 1 SVRG, 2 SAGA)
  *   eta         per-stage step sizes eta_k
  *   seq         subset id of every iteration (length sum N_k)
  *   x           in: x_0 (= y_0); out: x after the last iteration
@@ -515,7 +515,46 @@ void orc_pnp_run(const orc_geom *g, int n_stages, const int *stages, const doubl
     orc_pnp_run_w(g, n_stages, stages, eta, seq, b, NULL, x, alpha, lambda, tv_iters, momentum, xt, psnr);
 }
 
-/* Algorithm 1 with the weighted data fidelity (w nullable). */
+/* ---------------- variance-reduced subset estimators ----------------------
+ * Sec. 2 (after the minibatch form of the sketched step) names SVRG and SAGA
+ * as drop-in replacements for the vanilla minibatch estimate.  With
+ * G_p(y) = orc_grad_wk(..., p, P) (the vanilla estimate on subset p, already
+ * scaled by P so that its mean over p is the full sketched gradient):
+ *   SVRG (Johnson & Zhang 2013): snapshot yt and mu = full sketched gradient
+ *     at yt taken at the start of every epoch (P iterations);
+ *     v = G_p(y) - G_p(yt) + mu.
+ *   SAGA (Defazio, Bach & Lacoste-Julien 2014): a table psi_j of the last
+ *     G_j evaluated for every subset j, filled at the start of the stage;
+ *     v = G_p(y) - psi_p + (1/P) sum_j psi_j, then psi_p = G_p(y).        */
+void orc_svrg_estimate(const orc_geom *g, int s, int kind, const double *y, const double *yt,
+                       const double *mu, const double *b, const double *w, int p, int P, double *out)
+{
+    size_t N = (size_t)g->n * g->n;
+    double *gt = malloc(sizeof(double) * N);
+    orc_grad_wk(g, s, kind, y, b, w, out, p, P);
+    orc_grad_wk(g, s, kind, yt, b, w, gt, p, P);
+    for (size_t q = 0; q < N; ++q) out[q] = out[q] - gt[q] + mu[q];
+    free(gt);
+}
+
+void orc_saga_estimate(const orc_geom *g, int s, int kind, const double *y, double *psi,
+                       const double *b, const double *w, int p, int P, double *out)
+{
+    size_t N = (size_t)g->n * g->n;
+    double *gp = malloc(sizeof(double) * N);
+    orc_grad_wk(g, s, kind, y, b, w, gp, p, P);
+    for (size_t q = 0; q < N; ++q) {
+        double mean = 0.0;
+        for (int j = 0; j < P; ++j) mean += psi[(size_t)j * N + q];
+        out[q] = gp[q] - psi[(size_t)p * N + q] + mean / (double)P;
+    }
+    memcpy(psi + (size_t)p * N, gp, sizeof(double) * N);
+    free(gp);
+}
+
+/* Algorithm 1 with the weighted data fidelity (w nullable).  Stage records
+ * hold 5 ints: factor, iterations, subsets P, sketch kind, estimator
+ * (0 vanilla minibatch, 1 SVRG, 2 SAGA; the last two only when P > 1). */
 void orc_pnp_run_w(const orc_geom *g, int n_stages, const int *stages, const double *eta,
                    const int *seq, const double *b, const double *w, double *x, double alpha,
                    double lambda, int tv_iters, int momentum, const double *xt, double *psnr)
@@ -525,15 +564,30 @@ void orc_pnp_run_w(const orc_geom *g, int n_stages, const int *stages, const dou
     double *y = malloc(sizeof(double) * N), *xprev = malloc(sizeof(double) * N);
     double *z = malloc(sizeof(double) * N), *gr = malloc(sizeof(double) * N);
     double *dz = malloc(sizeof(double) * N);
+    double *yt = malloc(sizeof(double) * N), *mu = malloc(sizeof(double) * N);
     memcpy(y, x, sizeof(double) * N);
     memcpy(xprev, x, sizeof(double) * N);
     int i = 0;
     for (int k = 0; k < n_stages; ++k) {
-        int s = stages[4 * k], Nk = stages[4 * k + 1], P = stages[4 * k + 2], kind = stages[4 * k + 3];
+        int s = stages[5 * k], Nk = stages[5 * k + 1], P = stages[5 * k + 2], kind = stages[5 * k + 3];
+        int est = P > 1 ? stages[5 * k + 4] : 0;
+        double *psi = est == 2 ? malloc(sizeof(double) * N * (size_t)P) : NULL;
         for (int jj = 0; jj < Nk; ++jj) {
             i += 1;
             int p = P > 1 ? seq[i - 1] : 0;
-            orc_grad_wk(g, s, kind, y, b, w, gr, p, P);
+            if (est == 1) {
+                if (jj % P == 0) {   /* new epoch: snapshot and its full gradient */
+                    memcpy(yt, y, sizeof(double) * N);
+                    orc_grad_wk(g, s, kind, yt, b, w, mu, 0, 1);
+                }
+                orc_svrg_estimate(g, s, kind, y, yt, mu, b, w, p, P, gr);
+            } else if (est == 2) {
+                if (jj == 0)         /* table filled at the stage's first iterate */
+                    for (int j = 0; j < P; ++j) orc_grad_wk(g, s, kind, y, b, w, psi + (size_t)j * N, j, P);
+                orc_saga_estimate(g, s, kind, y, psi, b, w, p, P, gr);
+            } else {
+                orc_grad_wk(g, s, kind, y, b, w, gr, p, P);
+            }
             for (size_t q = 0; q < N; ++q) z[q] = y[q] - eta[k] * gr[q];
             orc_fgp(n, z, lambda, tv_iters, dz);
             double a = momentum ? (double)(i - 1) / (double)(i + 3) : 0.0;
@@ -544,9 +598,10 @@ void orc_pnp_run_w(const orc_geom *g, int n_stages, const int *stages, const dou
             }
             if (xt && psnr) psnr[i - 1] = orc_psnr((long)N, xprev, xt);
         }
+        free(psi);
     }
     memcpy(x, xprev, sizeof(double) * N);
-    free(y); free(xprev); free(z); free(gr); free(dz);
+    free(y); free(xprev); free(z); free(gr); free(dz); free(yt); free(mu);
 }
 
 /* Objective terms: 1/2 ||A x - b||^2 and TV(x) (Eq. 2 with f least squares). */

@@ -83,6 +83,7 @@ class Stage:
     iters: int
     n_subsets: int = 1
     kind: int = 0          # sketch: 0 s x s average pool, 1 bicubic (Keys a = -1/2, widened by s)
+    estimator: int = 0     # subset gradient estimate (P > 1): 0 vanilla minibatch, 1 SVRG, 2 SAGA
 
 
 @dataclass

@@ -45,6 +45,15 @@ MUTATIONS = [
      "if (t <= 1.0) return (a + 2.0) * t * t * t - (a + 2.0) * t * t + 1.0;"),
     ("bicubic adjoint index", "for (int J = 0; J < ns; ++J) acc += W[(long)J * n + y] * coarse[(long)J * ns + I];",
      "for (int J = 0; J < ns; ++J) acc += W[(long)J * n + y] * coarse[(long)I * ns + J];"),
+    ("svrg correction sign", "for (size_t q = 0; q < N; ++q) out[q] = out[q] - gt[q] + mu[q];",
+     "for (size_t q = 0; q < N; ++q) out[q] = out[q] + gt[q] + mu[q];"),
+    ("svrg snapshot gradient on a subset", "orc_grad_wk(g, s, kind, yt, b, w, mu, 0, 1);",
+     "orc_grad_wk(g, s, kind, yt, b, w, mu, 0, P);"),
+    ("svrg snapshot never refreshed", "if (jj % P == 0) {   /* new epoch",
+     "if (jj == 0) {   /* new epoch"),
+    ("saga table mean unscaled", "out[q] = gp[q] - psi[(size_t)p * N + q] + mean / (double)P;",
+     "out[q] = gp[q] - psi[(size_t)p * N + q] + mean;"),
+    ("saga table not updated", "memcpy(psi + (size_t)p * N, gp, sizeof(double) * N);", "(void)0;"),
     ("weights on the wrong views", "res[(long)vs * g->n_det + j] *= w[(long)(first + vs * step) * g->n_det + j];",
      "res[(long)vs * g->n_det + j] *= w[(long)vs * g->n_det + j];"),
 ]
