@@ -37,7 +37,8 @@ L2_FLUSH_BYTES = 512 << 20
 # capture (dram__bytes_read.sum + dram__bytes_write.sum over the 100
 # backprojection launches of one step, averaged); valid only while the
 # backprojector source is the one that was measured.
-BACKWARD_TRAFFIC = {"bytes_per_launch": None, "source_sha256": None,
+BACKWARD_TRAFFIC = {"bytes_per_launch": 718592,
+                    "source_sha256": "b883818d309124dbe395efd064b3d06f16ad5df6cfd18062bad7601df69a95d0",
                     "profile": "profiles/k_backward2x2_256_360x512_step.md"}
 
 
@@ -343,9 +344,6 @@ def run_native(args, rank, world):
     # ---- timed region: K steps, L2 flushed before each, device time by CUDA events
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    # (direct launches: every phase launch is bracketed by CUDA events on the
-    # run's stream, giving each kernel's live launch durations in the region)
-    pnp.kernel_times(reset=True)
     launches0 = pnp.launch_count()
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
@@ -353,12 +351,28 @@ def run_native(args, rank, world):
         for k in range(args.steps):
             flush.fill_(float(k))
             ev[k][0].record(stream)
-            plan.run(wl.stages, eta, seq, d_b, d_x.zero_(), graph=use_graph, kernel_times=not use_graph, **kw)
+            plan.run(wl.stages, eta, seq, d_b, d_x.zero_(), graph=use_graph, **kw)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         barrier(world)
     launches = pnp.launch_count() - launches0
+
+    # ---- the same K steps again with a CUDA event pair on the run's stream
+    # around every phase launch: each kernel's live launch durations.  (The
+    # events cost ~2 us of front-end time each, so the step above carries none.)
+    pnp.kernel_times(reset=True)
+    ev_ph = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for _ in range(args.steps)]
+    if not use_graph:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev_ph[k][0].record(stream)
+            plan.run(wl.stages, eta, seq, d_b, d_x.zero_(), kernel_times=True, **kw)
+            ev_ph[k][1].record(stream)
+        torch.cuda.synchronize()
     phases = pnp.kernel_times(reset=True)
+    ms_with_events = (float(np.mean([a.elapsed_time(b) for a, b in ev_ph])) if not use_graph else None)
     # d_x.zero_() is a PyTorch fill inside the region: not counted as ours
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = allmax(sum(step_ms), world)
@@ -376,17 +390,6 @@ def run_native(args, rank, world):
         if k >= 2:
             other.append(a_.elapsed_time(b2_))
     other_ms = float(np.median(other))
-    plain = []
-    for k in range(5):
-        flush.fill_(4.0)
-        a_, b2_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a_.record(stream)
-        plan.run(wl.stages, eta, seq, d_b, d_x.zero_(), graph=use_graph, **kw)
-        b2_.record(stream)
-        torch.cuda.synchronize()
-        if k >= 2:
-            plain.append(a_.elapsed_time(b2_))
-    plain_ms = float(np.median(plain))
 
     # ---- per-kernel timing of the projector pair (events on the launching stream)
     def timed(fn, reps=20):
@@ -502,8 +505,8 @@ def run_native(args, rank, world):
         ach = flop / (ph_ms[dominant] / 1000) / 1e12
         kname = "k_backward2x2 (A^T, U and the step)" if dominant == "backward" else "k_forward (A S y - b)"
         avg_us = 1000 * ph_ms[dominant] / ph_n[dominant]
-        timing_src = (f"CUDA events around each of the {ph_n[dominant]} launches in the timed region, "
-                      f"mean {avg_us:.2f} us per launch")
+        timing_src = (f"CUDA event pair around each of the {ph_n[dominant]} launches of the K timed steps "
+                      f"re-run with phase events, mean {avg_us:.2f} us per launch")
     else:   # graph replay: phases are not bracketed; the all-views launch timed alone
         dominant = "backward" if back_ms >= fwd_ms else "forward"
         ach = samples_full * (FLOP_BACK if dominant == "backward" else FLOP_FWD) / (
@@ -546,7 +549,7 @@ def run_native(args, rank, world):
             "setup_ms_autotune": tune_ms,
             "launch_mode": "CUDA graph captured once, replayed per step" if use_graph else "direct launches",
             "ms_per_step_other_launch_mode": other_ms,
-            "ms_per_step_without_phase_events": plain_ms,
+            "ms_per_step_with_phase_events": ms_with_events,
             "phase_ms_per_step": {k: v / args.steps for k, v in ph_ms.items()},
             "phase_launches_per_step": {k: v // args.steps for k, v in ph_n.items()},
             "step_ms_all": step_ms}
