@@ -78,14 +78,27 @@ typedef struct {
 #define PNP_SKETCH_POOL 0
 #define PNP_SKETCH_BICUBIC 1
 
+/* Subset gradient estimates for Option 2 (P_k > 1).  Sec. 2 uses the vanilla
+ * minibatch estimate and names variance-reduced ones as alternatives:
+ *   SVRG (Johnson & Zhang 2013): snapshot yt and its full sketched gradient mu at
+ *     the start of every epoch of P_k iterations; v = G_p(y) - G_p(yt) + mu.
+ *   SAGA (Defazio, Bach & Lacoste-Julien 2014): the last gradient of every subset
+ *     is kept (filled at the stage's first iterate); v = G_p(y) - T_p + mean_j T_j,
+ *     then T_p = G_p(y).
+ * Both need a buffer registered with pnp_set_vr_buffer. */
+#define PNP_EST_MINIBATCH 0
+#define PNP_EST_SVRG 1
+#define PNP_EST_SAGA 2
+
 /* One stage of Algorithm 1: sketch factor s_k (m_k = d / s_k^2), N_k inner
- * iterations, P_k interleaved angle subsets (1 = Option 1, >1 = Option 2) and
- * the sketch kind. */
+ * iterations, P_k interleaved angle subsets (1 = Option 1, >1 = Option 2), the
+ * sketch kind and the subset estimate. */
 typedef struct {
     int32_t factor;
     int32_t iters;
     int32_t n_subsets;
     int32_t kind;       /* PNP_SKETCH_POOL or PNP_SKETCH_BICUBIC (ignored for factor 1) */
+    int32_t estimator;  /* PNP_EST_* (ignored when n_subsets == 1) */
 } pnp_stage;
 
 /* Loop parameters of Algorithm 1. */
@@ -226,6 +239,18 @@ int pnp_power_iter(const pnp_geom* g, int factor, int max_iters, double tol, dou
 /* pnp_power_iter for L = ||A_s S||^2 with S of the given kind. */
 int pnp_power_iter_kind(const pnp_geom* g, int factor, int kind, int max_iters, double tol, double* h_L,
                         int* h_iters, void* d_ws, void* stream);
+
+/* Bytes of the estimator-state buffer that pnp_run needs for this schedule
+ * (0 when no stage uses SVRG or SAGA): snapshot, difference image, the running
+ * sums and, for SAGA, P_k level-grid images per image of the batch. */
+int pnp_vr_buffer_size(const pnp_geom* g, const pnp_stage* stages, int n_stages, size_t* bytes);
+
+/* Registers (d_buf != NULL) or clears the estimator-state buffer of a prepared
+ * workspace; caller-owned device memory of `bytes` bytes (256-byte aligned).
+ * The buffer carries the SVRG snapshot and the SAGA table between calls, so a run
+ * resumed with start_iter continues bit for bit when the buffer is the one the
+ * interrupted run left.  PNP_ESTATE from pnp_run when a stage needs a larger one. */
+int pnp_set_vr_buffer(const pnp_geom* g, void* d_buf, size_t bytes, void* d_ws);
 
 /* Algorithm 1 (PnP-MS2G) on every image of the batch.
  *   stages[n_stages]   the schedule; h_eta[n_stages] step sizes eta_k

@@ -38,10 +38,12 @@ class Geom(C.Structure):
 
 
 class StageC(C.Structure):
-    _fields_ = [("factor", C.c_int32), ("iters", C.c_int32), ("n_subsets", C.c_int32), ("kind", C.c_int32)]
+    _fields_ = [("factor", C.c_int32), ("iters", C.c_int32), ("n_subsets", C.c_int32), ("kind", C.c_int32),
+                ("estimator", C.c_int32)]
 
 
 SKETCH_POOL, SKETCH_BICUBIC = 0, 1
+EST_MINIBATCH, EST_SVRG, EST_SAGA = 0, 1, 2
 
 
 class RunParams(C.Structure):
@@ -109,6 +111,8 @@ def load(path: Optional[str] = None):
             "pnp_set_weights": [gp, vp, vp],
             "pnp_sketch_kind": [gp, i32, i32, vp, vp, vp],
             "pnp_kernel_times": [dp, C.POINTER(C.c_int64), i32],
+            "pnp_vr_buffer_size": [gp, C.POINTER(StageC), i32, C.POINTER(sz)],
+            "pnp_set_vr_buffer": [gp, vp, sz, vp],
             "pnp_upsample_kind": [gp, i32, i32, vp, vp, vp],
             "pnp_sketch_grad_kind": [gp, i32, i32, vp, vp, vp, i32, i32, vp, vp],
             "pnp_power_iter_kind": [gp, i32, i32, i32, C.c_double, dp, C.POINTER(i32), vp, vp],
@@ -268,10 +272,18 @@ def power_iter(g, factor, max_iters=100, tol=1e-7, ws=None, stream=None, kind=0)
 def _stages(stages: Sequence):
     arr = (StageC * len(stages))()
     for k, s in enumerate(stages):
-        f, it, P, kind = ((s.factor, s.iters, s.n_subsets, getattr(s, "kind", 0)) if hasattr(s, "factor")
-                          else (tuple(s) + (0,))[:4])
-        arr[k] = StageC(int(f), int(it), int(P), int(kind))
+        f, it, P, kind, est = ((s.factor, s.iters, s.n_subsets, getattr(s, "kind", 0), getattr(s, "estimator", 0))
+                               if hasattr(s, "factor") else (tuple(s) + (0, 0))[:5])
+        arr[k] = StageC(int(f), int(it), int(P), int(kind), int(est))
     return arr
+
+
+def vr_buffer_size(g, stages) -> int:
+    """Bytes of the SVRG/SAGA estimator buffer the schedule needs (0 if none)."""
+    st = _stages(stages)
+    v = C.c_size_t(0)
+    _check(load().pnp_vr_buffer_size(C.byref(geom(g)), st, len(st), C.byref(v)))
+    return int(v.value)
 
 
 def _flags(graph, kernel_times):
@@ -361,7 +373,23 @@ class Plan:
     def power_iter(self, factor, max_iters=100, tol=1e-7, stream=None, kind=0):
         return power_iter(self.g, factor, max_iters, tol, self.ws, stream, kind)
 
+    def ensure_vr_buffer(self, stages):
+        """Allocates (PyTorch) and registers the SVRG/SAGA state buffer the
+        schedule needs, keeping a large enough one that is already registered."""
+        import torch
+        need = vr_buffer_size(self.g, stages)
+        have = getattr(self, "vr", None)
+        if need == 0 or (have is not None and have.numel() >= need):
+            return
+        self.set_vr_buffer(torch.empty(need, dtype=torch.uint8, device=self.ws.device))
+
+    def set_vr_buffer(self, buf):
+        self.vr = buf
+        p, n = (None, 0) if buf is None else (C.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size())
+        _check(load().pnp_set_vr_buffer(C.byref(self.cg), p, n, _ws(self.ws)[0]))
+
     def run(self, stages, eta, seq, b, x, **kw):
+        self.ensure_vr_buffer(stages)
         return run(self.g, stages, eta, seq, b, x, ws=self.ws, **kw)
 
     def autotune(self, stages, **kw):
@@ -443,6 +471,7 @@ def run_many(problems, *, alpha=1.0, lam=0.02, tv_iters=20, momentum=True, strea
     for k, pr in enumerate(problems):
         plan = pr["plan"]
         g = plan.g
+        plan.ensure_vr_buffer(pr["stages"])
         st = _stages(pr["stages"])
         total = sum(a.iters for a in st)
         eta_a = (C.c_double * len(st))(*[float(e) for e in pr["eta"]])

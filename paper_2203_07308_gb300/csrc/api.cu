@@ -154,7 +154,10 @@ struct Tuned {
     int tile = 0;                            // tiled FGP: tile side
 };
 
-struct RegEntry { const void* ws; uint64_t fp; size_t bytes; Tuned tuned; const float* weights; };
+struct RegEntry {
+    const void* ws; uint64_t fp; size_t bytes; Tuned tuned; const float* weights;
+    void* vr = nullptr; size_t vr_bytes = 0;     // estimator-state buffer (SVRG / SAGA)
+};
 std::mutex g_reg_mu;
 std::vector<RegEntry> g_reg;
 
@@ -162,9 +165,60 @@ void reg_put(const void* ws, uint64_t fp, size_t bytes)
 {
     std::lock_guard<std::mutex> lk(g_reg_mu);
     for (auto& e : g_reg)
-        if (e.ws == ws) { e.fp = fp; e.bytes = bytes; e.tuned = Tuned(); e.weights = nullptr; return; }
+        if (e.ws == ws) {
+            e.fp = fp; e.bytes = bytes; e.tuned = Tuned(); e.weights = nullptr; e.vr = nullptr; e.vr_bytes = 0;
+            return;
+        }
     if (g_reg.size() >= 4096) g_reg.erase(g_reg.begin());
-    g_reg.push_back({ws, fp, bytes, Tuned(), nullptr});
+    RegEntry e{ws, fp, bytes, Tuned(), nullptr};
+    g_reg.push_back(e);
+}
+
+void reg_vr(const void* ws, void** buf, size_t* bytes)
+{
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    *buf = nullptr;
+    *bytes = 0;
+    for (const auto& e : g_reg)
+        if (e.ws == ws) { *buf = e.vr; *bytes = e.vr_bytes; }
+}
+
+void reg_set_vr(const void* ws, void* buf, size_t bytes)
+{
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    for (auto& e : g_reg)
+        if (e.ws == ws) { e.vr = buf; e.vr_bytes = buf ? bytes : 0; }
+}
+
+// Estimator-state buffer: fine snapshot and difference image, then level-grid
+// running sum (SVRG mu / SAGA Phi), combined estimate, raw subset gradient, and
+// the SAGA table of P_k level-grid images, each [batch][.][.].
+struct VrLayout { size_t off_yt = 0, off_diff = 0, off_acc = 0, off_v = 0, off_G = 0, off_tab = 0, bytes = 0; };
+
+VrLayout vr_layout(const pnp_geom& g, const pnp_stage* st, int n_stages)
+{
+    VrLayout V;
+    bool any = false;
+    size_t tab = 0;
+    for (int k = 0; k < n_stages; ++k) {
+        if (st[k].n_subsets <= 1 || st[k].estimator == PNP_EST_MINIBATCH) continue;
+        any = true;
+        if (st[k].estimator == PNP_EST_SAGA && st[k].factor > 0) {
+            const size_t ns = (size_t)(g.n / st[k].factor);
+            tab = std::max(tab, (size_t)st[k].n_subsets * g.batch * ns * ns);
+        }
+    }
+    if (!any) return V;
+    const size_t img = (size_t)g.batch * g.n * g.n * sizeof(float);
+    size_t off = 0;
+    V.off_yt = off; off = align_up(off + img);
+    V.off_diff = off; off = align_up(off + img);
+    V.off_acc = off; off = align_up(off + img);
+    V.off_v = off; off = align_up(off + img);
+    V.off_G = off; off = align_up(off + img);
+    V.off_tab = off; off = align_up(off + tab * sizeof(float));
+    V.bytes = off;
+    return V;
 }
 
 Tuned reg_tuned(const void* ws)
@@ -362,6 +416,66 @@ struct PhaseTimer {
     }
 };
 PhaseTimer g_timer;
+
+// Raw level-s gradient step*s * A_s^{(p)T} W (A_s^{(p)} S img - b^{(p)}) into
+// `out` [batch][ns][ns] (no U, no subset factor); b may be null (no data term).
+int coarse_grad(const pnp_geom& g, const Layout& L, int li, char* ws, int kind, const float* img,
+                const float* b, int p, int P, float* out, cudaStream_t st)
+{
+    const LevelLayout& lv = L.lv[li];
+    const Tuned tu = reg_tuned(ws);
+    float* res = (float*)(ws + L.off_res);
+    if (kind == PNP_SKETCH_BICUBIC && lv.factor > 1) {
+        float* cimg = (float*)(ws + L.off_cs);
+        PNP_CUDA(launch_bicubic_down(img, cimg, g.n, lv.factor, g.batch, st));
+        PNP_CUDA(launch_prep_quad(cimg, lv.ns, 1, g.batch, (float4*)(ws + lv.off_quad), lv.qw, st));
+    } else {
+        PNP_CUDA(launch_prep_quad(img, g.n, lv.factor, g.batch, (float4*)(ws + lv.off_quad), lv.qw, st));
+    }
+    PNP_CUDA(launch_forward(fwd_args(g, lv, ws, p, P, b, res, g.batch, reg_weights(ws)), st, tu.lanes[li]));
+    PNP_CUDA(launch_backward(back_args(g, lv, ws, p, P, res, kBackRaw, (float)(g.step * lv.factor), nullptr,
+                                       0.0f, out, g.batch), st, tu.groups[li]));
+    return PNP_OK;
+}
+
+// One SVRG or SAGA iteration's gradient step z = y - eta U v on subset p of P;
+// jj is the iteration's index inside its stage (epoch starts at jj % P == 0).
+int vr_step(const pnp_geom& g, const Layout& L, int li, char* ws, char* vb, const VrLayout& V, int est,
+            int kind, const float* y, const float* b, int p, int P, int jj, float eta, float* z, cudaStream_t st)
+{
+    const LevelLayout& lv = L.lv[li];
+    const int s = lv.factor, ns = lv.ns;
+    const size_t cnt = (size_t)g.batch * ns * ns;
+    const size_t img = (size_t)g.batch * g.n * g.n;
+    float* yt = (float*)(vb + V.off_yt);
+    float* dif = (float*)(vb + V.off_diff);
+    float* acc = (float*)(vb + V.off_acc);
+    float* v = (float*)(vb + V.off_v);
+    float* G = (float*)(vb + V.off_G);
+    float* tab = (float*)(vb + V.off_tab);
+    const bool bic = kind == PNP_SKETCH_BICUBIC && s > 1;
+    if (est == PNP_EST_SVRG) {
+        if (jj % P == 0) {      // new epoch: snapshot and its full sketched gradient
+            PNP_CUDA(launch_copy(y, yt, img, st));
+            if (int e = coarse_grad(g, L, li, ws, kind, yt, b, 0, 1, acc, st)) return e;
+        }
+        PNP_CUDA(launch_axpby(y, 1.0f, yt, -1.0f, dif, (long)img, st));
+        if (int e = coarse_grad(g, L, li, ws, kind, dif, nullptr, p, P, G, st)) return e;
+        PNP_CUDA(launch_vr_combine(PNP_EST_SVRG, G, acc, nullptr, (float)P, ns, g.batch, bic ? v : nullptr, y,
+                                   bic ? nullptr : z, s, eta, st));
+    } else {
+        if (jj == 0) {          // table of every subset's gradient at the stage's first iterate
+            for (int j = 0; j < P; ++j)
+                if (int e = coarse_grad(g, L, li, ws, kind, y, b, j, P, tab + (size_t)j * cnt, st)) return e;
+            PNP_CUDA(launch_vr_table_sum(tab, P, (long)cnt, acc, st));
+        }
+        if (int e = coarse_grad(g, L, li, ws, kind, y, b, p, P, G, st)) return e;
+        PNP_CUDA(launch_vr_combine(PNP_EST_SAGA, G, acc, tab + (size_t)p * cnt, (float)P, ns, g.batch,
+                                   bic ? v : nullptr, y, bic ? nullptr : z, s, eta, st));
+    }
+    if (bic) PNP_CUDA(launch_bicubic_up(v, y, z, g.n, s, g.batch, 1.0f, eta, st));
+    return PNP_OK;
+}
 
 // ---------------------------------------------------------------- CUDA graphs
 // pnp_run / pnp_run_many with PNP_RUN_GRAPH capture their launch sequence once
@@ -696,6 +810,8 @@ struct ProblemState {
     long total;
     int tv_parts;
     Tuned tuned;
+    VrLayout vr;
+    char* vr_buf = nullptr;
 };
 
 int validate_problem(const pnp_problem& q, const pnp_run_params& pr, int idx, ProblemState* out)
@@ -719,6 +835,8 @@ int validate_problem(const pnp_problem& q, const pnp_run_params& pr, int idx, Pr
         if (!(std::isfinite(q.h_eta[k]) && q.h_eta[k] >= 0.0)) return fail(PNP_EINVAL, "eta[%d] invalid", k);
         if (q.stages[k].kind != PNP_SKETCH_POOL && q.stages[k].kind != PNP_SKETCH_BICUBIC)
             return fail(PNP_EINVAL, "stage %d: unknown sketch kind %d", k, q.stages[k].kind);
+        if (q.stages[k].estimator < PNP_EST_MINIBATCH || q.stages[k].estimator > PNP_EST_SAGA)
+            return fail(PNP_EINVAL, "stage %d: unknown estimator %d", k, q.stages[k].estimator);
         any_subsets |= q.stages[k].n_subsets > 1;
         total += q.stages[k].iters;
     }
@@ -739,6 +857,16 @@ int validate_problem(const pnp_problem& q, const pnp_run_params& pr, int idx, Pr
                             q.stages[k].n_subsets);
     out->total = total;
     out->tuned = reg_tuned(q.d_ws);
+    out->vr = vr_layout(*g, q.stages, q.n_stages);
+    if (out->vr.bytes > 0) {
+        void* vb;
+        size_t vbytes;
+        reg_vr(q.d_ws, &vb, &vbytes);
+        if (!vb || vbytes < out->vr.bytes)
+            return fail(PNP_ESTATE, "problem %d: SVRG/SAGA stages need an estimator buffer of %zu bytes "
+                        "(pnp_set_vr_buffer); registered: %zu", idx, out->vr.bytes, vbytes);
+        out->vr_buf = (char*)vb;
+    }
     const bool do_tv = pr.tv_iters > 0 && pr.lambda > 0.0f;
     out->tv_parts = do_tv ? tile_tv_parts_for(g->n, g->batch, out->tuned.tile)
                           : ((g->n + 31) / 32) * ((g->n + 7) / 8);
@@ -817,8 +945,15 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
                 float* y = (float*)(ws + L.off_y);
                 float* z = (float*)(ws + L.off_z);
                 float* res = (float*)(ws + L.off_res);
-                if (sk.kind == PNP_SKETCH_BICUBIC && lv.factor > 1) {
-                    // bicubic stages run their own gradient launches; the denoiser joins the rest
+                const int est = P > 1 ? sk.estimator : PNP_EST_MINIBATCH;
+                if (est != PNP_EST_MINIBATCH) {
+                    // SVRG / SAGA stages run their own gradient launches; the denoiser joins the rest
+                    if (int e = vr_step(g, L, li, ws, ps[c].vr_buf, ps[c].vr, est, sk.kind, y, q.d_b, p, P,
+                                        in_stage[c] - 1, (float)q.h_eta[stage[c]], z, st))
+                        return e;
+                    bic[na] = 1;
+                } else if (sk.kind == PNP_SKETCH_BICUBIC && lv.factor > 1) {
+                    // so do bicubic stages
                     if (int e = grad_into(g, L, li, ws, y, q.d_b, p, P, kBackStep, (float)q.h_eta[stage[c]], z, st,
                                           PNP_SKETCH_BICUBIC))
                         return e;
@@ -919,6 +1054,7 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
         if (q.h_subset_seq) h.add(q.h_subset_seq, sizeof(int32_t) * (size_t)ps[c].total);
         h.val(ps[c].tuned);
         h.val(reg_weights(q.d_ws));
+        h.val(ps[c].vr_buf);
     }
     if (int e = run_maybe_graph((pr.flags & PNP_RUN_GRAPH) != 0, h.h, st, issue)) return e;
 
@@ -967,6 +1103,28 @@ int pnp_set_weights(const pnp_geom* g, const float* d_w, void* d_ws)
     if (int e = validate_geom(g)) return e;
     if (int e = check_ws(*g, d_ws)) return e;
     reg_set_weights(d_ws, d_w);
+    return PNP_OK;
+}
+
+int pnp_vr_buffer_size(const pnp_geom* g, const pnp_stage* stages, int n_stages, size_t* bytes)
+{
+    t_err.clear();
+    if (int e = validate_geom(g)) return e;
+    if (!stages || n_stages < 1 || !bytes) return fail(PNP_EINVAL, "stages and bytes are required");
+    for (int k = 0; k < n_stages; ++k)
+        if (stages[k].factor < 1 || g->n % stages[k].factor)
+            return fail(PNP_EINVAL, "stage %d: factor %d does not divide n", k, stages[k].factor);
+    *bytes = vr_layout(*g, stages, n_stages).bytes;
+    return PNP_OK;
+}
+
+int pnp_set_vr_buffer(const pnp_geom* g, void* d_buf, size_t bytes, void* d_ws)
+{
+    t_err.clear();
+    if (int e = validate_geom(g)) return e;
+    if (int e = check_ws(*g, d_ws)) return e;
+    if (d_buf && ((uintptr_t)d_buf & 255u)) return fail(PNP_EINVAL, "estimator buffer must be 256-byte aligned");
+    reg_set_vr(d_ws, d_buf, bytes);
     return PNP_OK;
 }
 

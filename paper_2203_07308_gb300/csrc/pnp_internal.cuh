@@ -152,6 +152,15 @@ cudaError_t launch_tv_vjp(const float* z, const float* xbar, float* zbar, double
 cudaError_t launch_axpby(const float* a, float c1, const float* b, float c2, float* out, long count,
                          cudaStream_t st);
 
+// Variance-reduced subset estimates (vr.cu) ----------------------------------------
+// phi = sum over P planes of `count` values (fixed order).
+cudaError_t launch_vr_table_sum(const float* table, int P, long count, float* phi, cudaStream_t st);
+// est 1: v = c G + acc; est 2: v = c (G - Tp) + acc, acc += G - Tp, Tp = G.  Level grid
+// [batch][ns][ns].  v_out (nullable) receives v; z (nullable) receives y - eta v / s^2
+// replicated over each s x s block (the pooled sketch's U = S^T).
+cudaError_t launch_vr_combine(int est, const float* G, float* acc, float* Tp, float c, int ns, int batch,
+                              float* v_out, const float* y, float* z, int s, float eta, cudaStream_t st);
+
 // Reductions -------------------------------------------------------------------
 enum RedMode { kRedDot = 0, kRedDiffSq = 1, kRedSq = 2, kRedTv = 3, kRedWSq = 4 };   // kRedWSq: sum b a^2
 // partials[inst][kRedBlocks] for `count` elements per instance (stride `stride`).

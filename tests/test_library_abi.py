@@ -56,3 +56,18 @@ def test_calls_reject_bad_arguments_before_launch(lib):
     size = C.c_size_t(0)
     assert lib.pnp_tv_workspace_size(64, 2, C.byref(size)) == 0 and size.value == 8 * 2 * 64 * 64 * 4
     assert lib.pnp_launch_count() == 0
+
+
+def test_estimator_buffer_sizes(lib):
+    """pnp_vr_buffer_size: 0 for vanilla schedules (and for SVRG/SAGA stages with
+    one subset), five image planes for SVRG, plus P_k level images per instance
+    for SAGA's table; factors that do not divide n are rejected."""
+    g = synth.make_geometry(64, 60, 96, batch=2)
+    img = 2 * 64 * 64 * 4
+    assert pnp.vr_buffer_size(g, [synth.Stage(2, 5, 3), synth.Stage(1, 5, 1)]) == 0
+    assert pnp.vr_buffer_size(g, [synth.Stage(2, 5, 1, estimator=2)]) == 0
+    assert pnp.vr_buffer_size(g, [synth.Stage(2, 5, 3, estimator=1)]) == 5 * img
+    saga = pnp.vr_buffer_size(g, [synth.Stage(2, 5, 3, estimator=2), synth.Stage(1, 5, 2, estimator=2)])
+    assert saga == 5 * img + max(3 * 2 * 32 * 32 * 4, 2 * img)
+    with pytest.raises(pnp.PnpError):
+        pnp.vr_buffer_size(g, [synth.Stage(3, 5, 3, estimator=1)])
