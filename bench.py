@@ -548,6 +548,7 @@ def run_native(args, rank, world):
             "setup_ms_power_iteration": setup_ms,
             "setup_ms_autotune": tune_ms,
             "launch_mode": "CUDA graph captured once, replayed per step" if use_graph else "direct launches",
+            "launch_shapes": plan.launch_shapes(),
             "ms_per_step_other_launch_mode": other_ms,
             "ms_per_step_with_phase_events": ms_with_events,
             "phase_ms_per_step": {k: v / args.steps for k, v in ph_ms.items()},

@@ -282,6 +282,27 @@ int pnp_run(const pnp_geom* g, const pnp_stage* stages, int n_stages, const doub
  * bitwise identical to an uninterrupted run. */
 int pnp_run_many(const pnp_problem* problems, int n_problems, const pnp_run_params* params, void* stream);
 
+/* Launch shapes of a prepared workspace, per sketch level (index 0..3 for the
+ * factors 1, 2, 4, 8), 0 meaning the built-in heuristic:
+ *   lanes   forward projector lanes per ray: 4, 8 or 16
+ *   back    backprojector: PNP_BACK_BLOCKS(G), 2x2 pixel blocks with G = 1, 2, 4,
+ *           8 or 16 view groups per CTA; or PNP_BACK_COLUMNS(L, W), runs of L = 4,
+ *           8 or 16 rows per lane with W = 1..32 view groups (warps) per CTA
+ *   tile    side of the FGP tile (8..40)
+ * The backprojector's shape fixes its summation order: results are bitwise
+ * reproducible for fixed shapes.  pnp_autotune sets them; pnp_set_launch_shapes
+ * pins them (PNP_EINVAL for a shape outside these sets). */
+#define PNP_BACK_COLUMNS_FLAG (1 << 16)
+#define PNP_BACK_BLOCKS(G) (G)
+#define PNP_BACK_COLUMNS(L, W) (PNP_BACK_COLUMNS_FLAG | ((L) << 8) | (W))
+typedef struct {
+    int32_t lanes[4];
+    int32_t back[4];
+    int32_t tile;
+} pnp_launch_shapes;
+int pnp_get_launch_shapes(const pnp_geom* g, pnp_launch_shapes* out, void* d_ws);
+int pnp_set_launch_shapes(const pnp_geom* g, const pnp_launch_shapes* in, void* d_ws);
+
 /* Times the launch shapes of this geometry's kernels on d_ws's own buffers
  * (forward lanes per ray 4/8/16 and backprojector view groups 1..16 for each
  * sketch level of the schedule, using its first angle subset; the FGP tile side

@@ -42,6 +42,23 @@ class StageC(C.Structure):
                 ("estimator", C.c_int32)]
 
 
+class LaunchShapes(C.Structure):
+    _fields_ = [("lanes", C.c_int32 * 4), ("back", C.c_int32 * 4), ("tile", C.c_int32)]
+
+
+BACK_COLUMNS_FLAG = 1 << 16
+
+
+def back_blocks(G: int) -> int:
+    """Backprojector shape: 2x2 pixel blocks, G view groups per CTA."""
+    return int(G)
+
+
+def back_columns(L: int, W: int) -> int:
+    """Backprojector shape: column runs of L rows per lane, W view groups per CTA."""
+    return BACK_COLUMNS_FLAG | (int(L) << 8) | int(W)
+
+
 SKETCH_POOL, SKETCH_BICUBIC = 0, 1
 EST_MINIBATCH, EST_SVRG, EST_SAGA = 0, 1, 2
 
@@ -112,6 +129,8 @@ def load(path: Optional[str] = None):
             "pnp_sketch_kind": [gp, i32, i32, vp, vp, vp],
             "pnp_kernel_times": [dp, C.POINTER(C.c_int64), i32],
             "pnp_vr_buffer_size": [gp, C.POINTER(StageC), i32, C.POINTER(sz)],
+            "pnp_get_launch_shapes": [gp, C.POINTER(LaunchShapes), vp],
+            "pnp_set_launch_shapes": [gp, C.POINTER(LaunchShapes), vp],
             "pnp_set_vr_buffer": [gp, vp, sz, vp],
             "pnp_upsample_kind": [gp, i32, i32, vp, vp, vp],
             "pnp_sketch_grad_kind": [gp, i32, i32, vp, vp, vp, i32, i32, vp, vp],
@@ -394,6 +413,17 @@ class Plan:
 
     def autotune(self, stages, **kw):
         autotune(self.g, stages, self.ws, **kw)
+
+    def launch_shapes(self) -> dict:
+        """{"lanes": [4], "back": [4], "tile": int} of this workspace (0 = heuristic)."""
+        ls = LaunchShapes()
+        _check(load().pnp_get_launch_shapes(C.byref(self.cg), C.byref(ls), _ws(self.ws)[0]))
+        return {"lanes": list(ls.lanes), "back": list(ls.back), "tile": int(ls.tile)}
+
+    def set_launch_shapes(self, lanes=(0, 0, 0, 0), back=(0, 0, 0, 0), tile=0):
+        """Pins launch shapes per level (factors 1, 2, 4, 8); see back_blocks / back_columns."""
+        ls = LaunchShapes((C.c_int32 * 4)(*lanes), (C.c_int32 * 4)(*back), int(tile))
+        _check(load().pnp_set_launch_shapes(C.byref(self.cg), C.byref(ls), _ws(self.ws)[0]))
 
     def set_weights(self, w):
         """Weighted least squares for every gradient of this plan (None: unweighted)."""

@@ -321,6 +321,7 @@ BackArgs back_args(const pnp_geom& g, const LevelLayout& lv, char* ws, int p, in
     a.rayf = (const float4*)(ws + lv.off_rayf);
     a.rayi = (const float2*)(ws + lv.off_rayi);
     a.view = (const float4*)(ws + lv.off_view);
+    a.rayk = (const int2*)(ws + lv.off_rayk);
     a.ns = lv.ns;
     a.n_det = g.n_det;
     a.first_view = P <= 1 ? 0 : p;
@@ -1187,10 +1188,16 @@ int pnp_autotune(const pnp_geom* g, const pnp_stage* stages, int n_stages, const
         const BackArgs ba = back_args(*g, lv, ws, 0, P, res, kBackRaw, 1.0f, nullptr, 0.0f, z, g->batch);
         best = 1e30f;
         const int nsub = subset_views(*g, 0, P);
-        for (int G = 1; G <= 16 && G <= nsub; G *= 2) {
+        std::vector<int> shapes;
+        for (int G = 1; G <= 16 && G <= nsub; G *= 2) shapes.push_back(G);
+        for (int Lr : {4, 8, 16})
+            for (int W : {4, 8, 16, 32})
+                if (W <= nsub) shapes.push_back(back_col_shape(Lr, W));
+        for (int shp : shapes) {
             float ms = 0.0f;
-            if (rc == PNP_OK) rc = timeit([&]() -> int { PNP_CUDA(launch_backward(ba, st, G)); return PNP_OK; }, &ms);
-            if (rc == PNP_OK && ms < best) { best = ms; tu.groups[li] = G; }
+            if (rc == PNP_OK)
+                rc = timeit([&]() -> int { PNP_CUDA(launch_backward(ba, st, shp)); return PNP_OK; }, &ms);
+            if (rc == PNP_OK && ms < best) { best = ms; tu.groups[li] = shp; }
         }
     }
     const pnp_run_params& pr = *params;
@@ -1213,6 +1220,47 @@ int pnp_autotune(const pnp_geom* g, const pnp_stage* stages, int n_stages, const
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != PNP_OK) return rc;
+    reg_set_tuned(d_ws, tu);
+    return PNP_OK;
+}
+
+int pnp_get_launch_shapes(const pnp_geom* g, pnp_launch_shapes* out, void* d_ws)
+{
+    t_err.clear();
+    if (int e = validate_geom(g)) return e;
+    if (!out) return fail(PNP_EINVAL, "output pointer is NULL");
+    if (int e = check_ws(*g, d_ws)) return e;
+    const Tuned tu = reg_tuned(d_ws);
+    for (int k = 0; k < 4; ++k) {
+        out->lanes[k] = tu.lanes[k];
+        out->back[k] = tu.groups[k];
+    }
+    out->tile = tu.tile;
+    return PNP_OK;
+}
+
+int pnp_set_launch_shapes(const pnp_geom* g, const pnp_launch_shapes* in, void* d_ws)
+{
+    t_err.clear();
+    if (int e = validate_geom(g)) return e;
+    if (!in) return fail(PNP_EINVAL, "input pointer is NULL");
+    if (int e = check_ws(*g, d_ws)) return e;
+    Tuned tu;
+    for (int k = 0; k < 4; ++k) {
+        const int q = in->lanes[k], b = in->back[k];
+        if (q != 0 && q != 4 && q != 8 && q != 16) return fail(PNP_EINVAL, "lanes[%d] = %d not in {0, 4, 8, 16}", k, q);
+        bool ok = b == 0 || (b >= 1 && b <= 16 && (b & (b - 1)) == 0);
+        if (b & PNP_BACK_COLUMNS_FLAG) {
+            const int Lr = (b >> 8) & 0xff, W = b & 0xff;
+            ok = (b & ~(PNP_BACK_COLUMNS_FLAG | 0xffff)) == 0 && (Lr == 4 || Lr == 8 || Lr == 16) && W >= 1 && W <= 32;
+        }
+        if (!ok) return fail(PNP_EINVAL, "back[%d] = %#x is not a backprojector shape", k, b);
+        tu.lanes[k] = q;
+        tu.groups[k] = b;
+    }
+    if (in->tile != 0 && (in->tile < 8 || in->tile > 40))
+        return fail(PNP_EINVAL, "tile %d outside [8, 40]", in->tile);
+    tu.tile = in->tile;
     reg_set_tuned(d_ws, tu);
     return PNP_OK;
 }

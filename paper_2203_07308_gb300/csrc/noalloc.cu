@@ -128,6 +128,7 @@ extern "C" int pnp_full_grad_noalloc(const pnp_geom* g, const float* d_x, const 
         a.rayf = (const float4*)(ws + lv.off_rayf);
         a.rayi = (const float2*)(ws + lv.off_rayi);
         a.view = (const float4*)(ws + lv.off_view);
+        a.rayk = (const int2*)(ws + lv.off_rayk);
         a.ns = g->n;
         a.n_det = g->n_det;
         a.first_view = 0;

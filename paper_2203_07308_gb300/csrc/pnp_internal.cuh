@@ -94,7 +94,7 @@ cudaError_t launch_forward_multi(const FwdArgs* items, int count, cudaStream_t s
 enum BackMode { kBackRaw = 0, kBackGradFine = 1, kBackStep = 2 };
 struct BackArgs {
     const float* res;                // [batch][n_sub][n_det]
-    const float4* rayf; const float2* rayi; const float4* view;
+    const float4* rayf; const float2* rayi; const float4* view; const int2* rayk;
     int ns, n_det, first_view, view_step, n_sub, batch;
     float step;
     int mode; int s; int n;          // fine side for modes 1, 2
@@ -102,6 +102,11 @@ struct BackArgs {
     const float* y; float eta;       // mode 2: z = y - eta * scale * sum
     float* out;
 };
+// `groups` selects the kernel and its launch shape (0 = heuristic):
+//   1..16                      2x2-block gather with that many view groups per CTA;
+//   back_col_shape(L, W)       column-run gather, runs of L rows, W view groups (warps).
+constexpr int kBackColFlag = PNP_BACK_COLUMNS_FLAG;
+constexpr int back_col_shape(int L, int W) { return kBackColFlag | (L << 8) | W; }
 cudaError_t launch_backward(const BackArgs& a, cudaStream_t st, int groups = 0);
 cudaError_t launch_backward_multi(const BackArgs* items, int count, cudaStream_t st, int groups = 0);
 

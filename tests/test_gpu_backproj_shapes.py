@@ -1,0 +1,157 @@
+"""Every backprojector launch shape against the FP64 oracle: the 2x2-block
+gather and the column-run gather (runs of L rows, W view groups), pinned with
+pnp_set_launch_shapes, on ragged sizes, limited-angle rays that miss the image,
+one view, sample steps other than half a pixel and every sketch level; the
+three epilogues (raw, gradient, fused step); bitwise repeatability per shape."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2203_07308_gb300 as pnp
+from paper_2203_07308_gb300 import _native, build, synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+GEOMS = {
+    "c1": synth.make_geometry(64, 90, 96, batch=2),
+    "ragged": synth.make_geometry(60, 37, 101, batch=3),
+    "limited": synth.Geometry(n=48, n_views=30, n_det=140, batch=1, dso=96.0, ddo=80.0,
+                              det_pitch=2.3, angle0=0.3, angle_span=math.pi),
+    "oneview": synth.make_geometry(32, 1, 48, batch=1),
+    "step03": synth.make_geometry(40, 20, 64, batch=2, step=0.3),
+    "step08": synth.make_geometry(36, 24, 60, batch=1, step=0.8),
+    "wide": synth.make_geometry(100, 16, 160, batch=1),
+}
+SHAPES = {
+    "blocks4": _native.back_blocks(4),
+    "cols4x8": _native.back_columns(4, 8),
+    "cols8x1": _native.back_columns(8, 1),
+    "cols8x16": _native.back_columns(8, 16),
+    "cols16x32": _native.back_columns(16, 32),
+    "cols16x3": _native.back_columns(16, 3),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    pnp.load()
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+def empty(*shape):
+    import torch
+    return torch.full(shape, float("nan"), dtype=torch.float32, device="cuda")
+
+
+def pinned(g, shape):
+    plan = pnp.Plan(g)
+    plan.set_launch_shapes(back=(shape,) * 4)
+    assert plan.launch_shapes()["back"] == [shape] * 4
+    return plan
+
+
+@pytest.mark.parametrize("shape", list(SHAPES))
+@pytest.mark.parametrize("name", list(GEOMS))
+def test_backprojection_every_shape(name, shape):
+    g = GEOMS[name]
+    plan = pinned(g, SHAPES[shape])
+    rng = np.random.default_rng(5)
+    for s in (1, 2, 4):
+        if g.n % s or g.n // s < 4:
+            continue
+        ns = g.n // s
+        for P in sorted({1, min(4, g.n_views)}):
+            p = P - 1
+            nsub = pnp.subset_views(g, p, P)
+            y = f32(rng.standard_normal((g.batch, nsub, g.n_det)))
+            out = empty(g.batch, ns, ns)
+            plan.backproject(s, dev(y), out, p, P)
+            got = host(out)
+            ref = np.stack([oracle.backproject(g, s, y[i], p, P) for i in range(g.batch)])
+            assert rel(got, ref) < TOL, (name, shape, s, P, rel(got, ref))
+            again = empty(g.batch, ns, ns)
+            plan.backproject(s, dev(y), again, p, P)
+            assert np.array_equal(host(again), got)
+
+
+@pytest.mark.parametrize("shape", ["cols8x16", "cols4x8", "cols16x3"])
+@pytest.mark.parametrize("name,s,P", [("c1", 2, 5), ("ragged", 1, 3), ("ragged", 2, 1), ("step03", 4, 2)])
+def test_gradient_and_step_epilogues(name, s, P, shape):
+    """Gradient on the fine grid (U = S^T) and, through a one-iteration PGD run,
+    the fused step z = y - eta grad, against the oracle."""
+    import torch
+    g = GEOMS[name]
+    if g.n % s or g.n // s < 4:
+        pytest.skip("level not available")
+    plan = pinned(g, SHAPES[shape])
+    x = np.stack([f32(synth.ellipse_phantom(g.n, 30 + i, (5, 8))) for i in range(g.batch)])
+    rng = np.random.default_rng(31)
+    b = f32(np.stack([oracle.project(g, 1, xi) for xi in x]) + rng.standard_normal((g.batch, g.n_views, g.n_det)))
+    y = f32(x + 0.1 * rng.standard_normal(x.shape))
+    out = empty(g.batch, g.n, g.n)
+    plan.sketch_grad(s, dev(y), dev(b), out, P - 1, P)
+    ref = np.stack([oracle.grad(g, s, y[i], b[i], P - 1, P) for i in range(g.batch)])
+    assert rel(host(out), ref) < TOL, rel(host(out), ref)
+    stages = [synth.Stage(s, 1, P)]
+    seq = [P - 1]
+    eta = [1e-3]
+    d_x = dev(y)
+    plan.run(stages, eta, seq, dev(b), d_x, tv_iters=0, lam=0.0, momentum=False)
+    for i in range(g.batch):
+        xr, _ = oracle.pnp_run(g, stages, eta, seq, b[i], y[i], tv_iters=0, lam=0.0, momentum=False)
+        assert rel(host(d_x)[i], xr) < TOL, rel(host(d_x)[i], xr)
+
+
+def test_full_size_256_column_gather():
+    """The 256x256 / 360 x 512 workload at full size with column-run shapes:
+    a 45-view subset backprojection at both levels of the benchmark schedule."""
+    wl = synth.workloads()["c2_256"]
+    g = wl.geom
+    rng = np.random.default_rng(6)
+    for shape in (_native.back_columns(8, 16), _native.back_columns(16, 8)):
+        plan = pinned(g, shape)
+        for s in (1, 2):
+            ns = g.n // s
+            nsub = pnp.subset_views(g, 3, 8)
+            y = f32(rng.standard_normal((1, nsub, g.n_det)))
+            out = empty(1, ns, ns)
+            plan.backproject(s, dev(y), out, 3, 8)
+            ref = oracle.backproject(g, s, y[0], 3, 8)
+            assert rel(host(out)[0], ref) < TOL, (shape, s, rel(host(out)[0], ref))
+
+
+def test_launch_shapes_validation():
+    g = GEOMS["c1"]
+    plan = pnp.Plan(g)
+    assert plan.launch_shapes() == {"lanes": [0] * 4, "back": [0] * 4, "tile": 0}
+    for bad in (dict(back=(3, 0, 0, 0)), dict(back=(_native.back_columns(5, 8), 0, 0, 0)),
+                dict(back=(_native.back_columns(8, 33), 0, 0, 0)), dict(lanes=(2, 0, 0, 0)), dict(tile=50)):
+        with pytest.raises(pnp.PnpError):
+            plan.set_launch_shapes(**bad)
+    plan.set_launch_shapes(lanes=(8, 4, 0, 0), back=(_native.back_columns(16, 2), 2, 0, 0), tile=24)
+    assert plan.launch_shapes() == {"lanes": [8, 4, 0, 0], "back": [_native.back_columns(16, 2), 2, 0, 0],
+                                    "tile": 24}
