@@ -285,16 +285,11 @@ int pnp_run_many(const pnp_problem* problems, int n_problems, const pnp_run_para
 /* Launch shapes of a prepared workspace, per sketch level (index 0..3 for the
  * factors 1, 2, 4, 8), 0 meaning the built-in heuristic:
  *   lanes   forward projector lanes per ray: 4, 8 or 16
- *   back    backprojector: PNP_BACK_BLOCKS(G), 2x2 pixel blocks with G = 1, 2, 4,
- *           8 or 16 view groups per CTA; or PNP_BACK_COLUMNS(L, W), runs of L = 4,
- *           8 or 16 rows per lane with W = 1..32 view groups (warps) per CTA
+ *   back    backprojector view groups per CTA: 1, 2, 4, 8 or 16
  *   tile    side of the FGP tile (8..40)
- * The backprojector's shape fixes its summation order: results are bitwise
+ * The backprojector's view groups fix its summation order: results are bitwise
  * reproducible for fixed shapes.  pnp_autotune sets them; pnp_set_launch_shapes
  * pins them (PNP_EINVAL for a shape outside these sets). */
-#define PNP_BACK_COLUMNS_FLAG (1 << 16)
-#define PNP_BACK_BLOCKS(G) (G)
-#define PNP_BACK_COLUMNS(L, W) (PNP_BACK_COLUMNS_FLAG | ((L) << 8) | (W))
 typedef struct {
     int32_t lanes[4];
     int32_t back[4];

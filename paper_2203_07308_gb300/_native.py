@@ -46,19 +46,6 @@ class LaunchShapes(C.Structure):
     _fields_ = [("lanes", C.c_int32 * 4), ("back", C.c_int32 * 4), ("tile", C.c_int32)]
 
 
-BACK_COLUMNS_FLAG = 1 << 16
-
-
-def back_blocks(G: int) -> int:
-    """Backprojector shape: 2x2 pixel blocks, G view groups per CTA."""
-    return int(G)
-
-
-def back_columns(L: int, W: int) -> int:
-    """Backprojector shape: column runs of L rows per lane, W view groups per CTA."""
-    return BACK_COLUMNS_FLAG | (int(L) << 8) | int(W)
-
-
 SKETCH_POOL, SKETCH_BICUBIC = 0, 1
 EST_MINIBATCH, EST_SVRG, EST_SAGA = 0, 1, 2
 
@@ -421,7 +408,8 @@ class Plan:
         return {"lanes": list(ls.lanes), "back": list(ls.back), "tile": int(ls.tile)}
 
     def set_launch_shapes(self, lanes=(0, 0, 0, 0), back=(0, 0, 0, 0), tile=0):
-        """Pins launch shapes per level (factors 1, 2, 4, 8); see back_blocks / back_columns."""
+        """Pins launch shapes per level (factors 1, 2, 4, 8): forward lanes per ray,
+        backprojector view groups, FGP tile side (0 = heuristic)."""
         ls = LaunchShapes((C.c_int32 * 4)(*lanes), (C.c_int32 * 4)(*back), int(tile))
         _check(load().pnp_set_launch_shapes(C.byref(self.cg), C.byref(ls), _ws(self.ws)[0]))
 

@@ -608,7 +608,8 @@ int pnp_project(const pnp_geom* g, int factor, const float* d_img, const float* 
     char* ws = (char*)d_ws;
     const LevelLayout& lv = L.lv[li];
     PNP_CUDA(launch_prep_quad(d_img, lv.ns, 1, g->batch, (float4*)(ws + lv.off_quad), lv.qw, S(stream)));
-    PNP_CUDA(launch_forward(fwd_args(*g, lv, ws, subset, n_subsets, d_b, d_sino, g->batch), S(stream)));
+    PNP_CUDA(launch_forward(fwd_args(*g, lv, ws, subset, n_subsets, d_b, d_sino, g->batch), S(stream),
+                            reg_tuned(d_ws).lanes[li]));
     return PNP_OK;
 }
 
@@ -626,7 +627,7 @@ int pnp_backproject(const pnp_geom* g, int factor, const float* d_sino, float* d
     const LevelLayout& lv = L.lv[li];
     PNP_CUDA(launch_backward(back_args(*g, lv, (char*)d_ws, subset, n_subsets, d_sino, kBackRaw,
                                        (float)(g->step * factor), nullptr, 0.0f, d_img, g->batch),
-                             S(stream)));
+                             S(stream), reg_tuned(d_ws).groups[li]));
     return PNP_OK;
 }
 
@@ -1188,16 +1189,10 @@ int pnp_autotune(const pnp_geom* g, const pnp_stage* stages, int n_stages, const
         const BackArgs ba = back_args(*g, lv, ws, 0, P, res, kBackRaw, 1.0f, nullptr, 0.0f, z, g->batch);
         best = 1e30f;
         const int nsub = subset_views(*g, 0, P);
-        std::vector<int> shapes;
-        for (int G = 1; G <= 16 && G <= nsub; G *= 2) shapes.push_back(G);
-        for (int Lr : {4, 8, 16})
-            for (int W : {4, 8, 16, 32})
-                if (W <= nsub) shapes.push_back(back_col_shape(Lr, W));
-        for (int shp : shapes) {
+        for (int G = 1; G <= 16 && G <= nsub; G *= 2) {
             float ms = 0.0f;
-            if (rc == PNP_OK)
-                rc = timeit([&]() -> int { PNP_CUDA(launch_backward(ba, st, shp)); return PNP_OK; }, &ms);
-            if (rc == PNP_OK && ms < best) { best = ms; tu.groups[li] = shp; }
+            if (rc == PNP_OK) rc = timeit([&]() -> int { PNP_CUDA(launch_backward(ba, st, G)); return PNP_OK; }, &ms);
+            if (rc == PNP_OK && ms < best) { best = ms; tu.groups[li] = G; }
         }
     }
     const pnp_run_params& pr = *params;
@@ -1249,12 +1244,8 @@ int pnp_set_launch_shapes(const pnp_geom* g, const pnp_launch_shapes* in, void* 
     for (int k = 0; k < 4; ++k) {
         const int q = in->lanes[k], b = in->back[k];
         if (q != 0 && q != 4 && q != 8 && q != 16) return fail(PNP_EINVAL, "lanes[%d] = %d not in {0, 4, 8, 16}", k, q);
-        bool ok = b == 0 || (b >= 1 && b <= 16 && (b & (b - 1)) == 0);
-        if (b & PNP_BACK_COLUMNS_FLAG) {
-            const int Lr = (b >> 8) & 0xff, W = b & 0xff;
-            ok = (b & ~(PNP_BACK_COLUMNS_FLAG | 0xffff)) == 0 && (Lr == 4 || Lr == 8 || Lr == 16) && W >= 1 && W <= 32;
-        }
-        if (!ok) return fail(PNP_EINVAL, "back[%d] = %#x is not a backprojector shape", k, b);
+        const bool ok = b == 0 || (b >= 1 && b <= 16 && (b & (b - 1)) == 0);
+        if (!ok) return fail(PNP_EINVAL, "back[%d] = %d not in {0, 1, 2, 4, 8, 16}", k, b);
         tu.lanes[k] = q;
         tu.groups[k] = b;
     }

@@ -102,11 +102,7 @@ struct BackArgs {
     const float* y; float eta;       // mode 2: z = y - eta * scale * sum
     float* out;
 };
-// `groups` selects the kernel and its launch shape (0 = heuristic):
-//   1..16                      2x2-block gather with that many view groups per CTA;
-//   back_col_shape(L, W)       column-run gather, runs of L rows, W view groups (warps).
-constexpr int kBackColFlag = PNP_BACK_COLUMNS_FLAG;
-constexpr int back_col_shape(int L, int W) { return kBackColFlag | (L << 8) | W; }
+// `groups`: view groups per CTA of the 2x2-block gather (1..16, 0 = heuristic).
 cudaError_t launch_backward(const BackArgs& a, cudaStream_t st, int groups = 0);
 cudaError_t launch_backward_multi(const BackArgs* items, int count, cudaStream_t st, int groups = 0);
 

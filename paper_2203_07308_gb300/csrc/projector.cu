@@ -350,169 +350,6 @@ __global__ void __launch_bounds__(512, 2) k_backward2x2(const BackTable t)
     }
 }
 
-// Column-run gather.  Lane x of a warp owns level pixels (x, y0 .. y0+L-1); the
-// pixels that a sample at (X, Y) feeds are the bilinear corners of its cell, so
-// the lane takes every sample inside its band (x-1, x+1) x (y0-1, y0+L): weight
-// h = 1 - |X - x| for column x, split (1 - fy, fy) over rows floor(Y) and
-// floor(Y) + 1.  Per view, the band's detector shadow (its corners projected)
-// gives the candidate rays and each ray's samples in the band follow from the
-// slab test with 1/d, so no sample outside the band is visited and every lane
-// sees about the same number of samples (band area x sample density) for any
-// ray direction.  The (ray, sample) pairs are walked as one flat loop, so lanes
-// change rays independently.  Rows accumulate in a lane-private shared-memory
-// column (row-major with the lane fastest: conflict-free); warp w takes the
-// views w, w + W, ... and the W columns are summed in a fixed order, so the
-// result is deterministic for a given (L, W).
-struct BackColTable {
-    BackArgs c[kMaxClasses];
-    long begin[kMaxClasses + 1];   // cumulative CTA counts (batch * tiles)
-    int count;
-};
-
-__device__ __forceinline__ float shadow_bin(float4 vp, float jc, float px, float py)
-{
-    const float along = px * vp.x + py * vp.y;
-    const float lat = py * vp.x - px * vp.y;
-    return fmaf(vp.w * lat, __fdividef(1.0f, vp.z - along), jc);
-}
-
-template <int L>
-__global__ void __launch_bounds__(1024, 1) k_backward_col(const BackColTable t)
-{
-    extern __shared__ float colacc[];            // [W][L + 2][32]
-    const int lane = threadIdx.x, w = threadIdx.y, W = blockDim.y;
-    int c = 0;
-#pragma unroll
-    for (int k = 1; k < kMaxClasses; ++k)
-        if (k < t.count && (long)blockIdx.x >= t.begin[k]) c = k;
-    const BackArgs& a = t.c[c];
-    const int tiles_x = (a.ns + 31) / 32;
-    const int tiles_y = (a.ns + L - 1) / L;
-    const long local = (long)blockIdx.x - t.begin[c];
-    const int tiles = tiles_x * tiles_y;
-    const int inst = (int)(local / tiles);
-    const int tile = (int)(local - (long)inst * tiles);
-    const int x = (tile % tiles_x) * 32 + lane;
-    const int y0 = (tile / tiles_x) * L;
-    float* col = colacc + (size_t)w * (L + 2) * 32 + lane;
-#pragma unroll
-    for (int m = 0; m < L + 2; ++m) col[m * 32] = 0.0f;
-    if (x < a.ns) {
-        const int c0 = a.ns / 2;
-        const float px = (float)(x - c0) + 1.5f;             // primed frame (ray tables)
-        const float py0 = (float)(y0 - c0) + 1.5f;
-        const float half = 0.5f * (float)(a.ns - 1);
-        const float bx0 = (float)x - 1.0f - half, bx1 = (float)x + 1.0f - half;       // band, centred
-        const float by0 = (float)y0 - 1.0f - half, by1 = (float)(y0 + L) - half;
-        const float jc = 0.5f * (float)(a.n_det - 1);
-        const float step = a.step, inv_step = 1.0f / a.step;
-        const float Lf = (float)L;
-        const float* __restrict__ res = a.res + (long)inst * a.n_sub * a.n_det;
-        for (int vs = w; vs < a.n_sub; vs += W) {
-            const int v = a.first_view + vs * a.view_step;
-            const float4 vp = __ldg(a.view + v);    // cos b, sin b, dso/s, (dso+ddo)/pitch
-            const float u0 = shadow_bin(vp, jc, bx0, by0), u1 = shadow_bin(vp, jc, bx1, by0);
-            const float u2 = shadow_bin(vp, jc, bx0, by1), u3 = shadow_bin(vp, jc, bx1, by1);
-            const float umin = fminf(fminf(u0, u1), fminf(u2, u3));
-            const float umax = fmaxf(fmaxf(u0, u1), fmaxf(u2, u3));
-            const int jlo = max(0, (int)ceilf(umin - 0.01f));
-            const int jhi = min(a.n_det - 1, (int)floorf(umax + 0.01f));
-            const long base = (long)v * a.n_det;
-            const float* __restrict__ rrow = res + (long)vs * a.n_det;
-            int j = jlo;
-            int k = 1, khi = 0;
-            float ax = 0.0f, ay = 0.0f, dx = 0.0f, dy = 0.0f, r = 0.0f;
-            for (;;) {
-                if (k > khi) {                       // next ray with samples in the band
-                    bool found = false;
-                    while (j <= jhi) {
-                        const float4 f = __ldg(a.rayf + base + j);
-                        const float2 ri = __ldg(a.rayi + base + j);
-                        const int2 kr = __ldg(a.rayk + base + j);
-                        const float bxr = f.x - px, byr = f.y - py0;
-                        const float tx1 = (-1.0f - bxr) * ri.x, tx2 = (1.0f - bxr) * ri.x;
-                        const float ty1 = (-1.0f - byr) * ri.y, ty2 = (Lf - byr) * ri.y;
-                        const float tlo = fmaxf(fminf(tx1, tx2), fminf(ty1, ty2));
-                        const float thi = fminf(fmaxf(tx1, tx2), fmaxf(ty1, ty2));
-                        // (k + 1/2) step in (tlo, thi), within the ray's samples in the image box
-                        const float klf = fmaxf(floorf(fmaf(tlo, inv_step, -0.5f)) + 1.0f, (float)kr.x);
-                        const float khf = fminf(ceilf(fmaf(thi, inv_step, -0.5f)) - 1.0f, (float)kr.y);
-                        const int rj = j++;
-                        if (klf <= khf) {
-                            k = (int)klf;
-                            khi = (int)khf;
-                            ax = bxr; ay = byr; dx = f.z; dy = f.w;
-                            r = __ldg(rrow + rj);
-                            found = true;
-                            break;
-                        }
-                    }
-                    if (!found) break;
-                }
-                const float tk = ((float)k + 0.5f) * step;
-                const float X = fmaf(tk, dx, ax);
-                const float Y = fmaf(tk, dy, ay);
-                const float h = fmaxf(1.0f - fabsf(X), 0.0f) * r;
-                const float my = __fadd_rn(Y - 0.5f, kMagic);           // round(Y - 1/2) = floor(Y)
-                const int iy = min(max(__float_as_int(my) - kMagicBits, -1), L - 1);
-                const float fy = Y - (float)iy;
-                const float hi_part = h * fy;
-                float* cell = col + (iy + 1) * 32;
-                cell[0] += h - hi_part;
-                cell[32] += hi_part;
-                ++k;
-            }
-        }
-    }
-    __syncthreads();
-    const int s = a.s;
-    for (int m = w; m < L; m += W) {
-        const int y = y0 + m;
-        if (x >= a.ns || y >= a.ns) continue;
-        float sum = 0.0f;
-        for (int q = 0; q < W; ++q) sum += colacc[((size_t)q * (L + 2) + m + 1) * 32 + lane];
-        const float val = a.scale * sum;
-        if (a.mode == kBackRaw) {
-            a.out[((long)inst * a.ns + y) * a.ns + x] = val;
-            continue;
-        }
-        for (int bb = 0; bb < s; ++bb) {
-            const long row = ((long)inst * a.n + (long)y * s + bb) * a.n + (long)x * s;
-            for (int aa = 0; aa < s; ++aa) {
-                if (a.mode == kBackGradFine)
-                    a.out[row + aa] = val;
-                else
-                    a.out[row + aa] = __ldg(a.y + row + aa) - a.eta * val;
-            }
-        }
-    }
-}
-
-template <int L>
-cudaError_t launch_backward_col(const BackArgs* items, int count, int W, cudaStream_t st)
-{
-    BackColTable t{};
-    t.count = count;
-    t.begin[0] = 0;
-    for (int c = 0; c < count; ++c) {
-        t.c[c] = items[c];
-        const int tiles = div_up(items[c].ns, 32) * div_up(items[c].ns, L);
-        t.begin[c + 1] = t.begin[c] + (long)tiles * items[c].batch;
-    }
-    const size_t smem = (size_t)W * (L + 2) * 32 * sizeof(float);
-    static bool opted_in = false;    // W <= 32 keeps smem <= 73,728 B: one opt-in covers every W
-    if (smem > 48 * 1024 && !opted_in) {
-        cudaError_t e = cudaFuncSetAttribute(k_backward_col<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             32 * (L + 2) * 32 * (int)sizeof(float));
-        if (e != cudaSuccess) return e;
-        opted_in = true;
-    }
-    dim3 blk(32, W), grd((unsigned)t.begin[count]);
-    k_backward_col<L><<<grd, blk, smem, st>>>(t);
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-    return cudaGetLastError();
-}
-
 // ------------------------------------------------------------------ bicubic S and S^T
 // The paper's sketch and upsampler are bicubic resizes (Sec. 3).  Here S is
 // separable: coarse pixel I (centre X_I = s I + (s-1)/2 in fine index units)
@@ -723,16 +560,6 @@ cudaError_t launch_backward_multi(const BackArgs* items, int count, cudaStream_t
         blocks += (long)nb * nb * items[c].batch;
         min_views = min(min_views, items[c].n_sub);
         half_step = half_step && items[c].step == 0.5f;
-    }
-    if (groups & kBackColFlag) {
-        const int L = (groups >> 8) & 0xff, W = groups & 0xff;
-        if (W < 1 || W > 32) return cudaErrorInvalidValue;
-        switch (L) {
-        case 4: return launch_backward_col<4>(items, count, W, st);
-        case 8: return launch_backward_col<8>(items, count, W, st);
-        case 16: return launch_backward_col<16>(items, count, W, st);
-        default: return cudaErrorInvalidValue;
-        }
     }
     // view groups: about two waves of 2048 threads per SM, at most 32 per CTA,
     // unless the autotuner chose
