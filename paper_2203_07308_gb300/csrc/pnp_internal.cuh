@@ -27,7 +27,46 @@
 
 #include "../../include/pnp_ms2g.h"
 
+#include <utility>
+
 namespace pnp {
+
+// Programmatic dependent launch.  The loop kernels (coefficient image, forward,
+// backprojection, denoiser) are launched with programmatic stream serialisation:
+// each one waits for its predecessor's completion (griddepcontrol.wait) before
+// touching memory and then lets its own successor be scheduled
+// (griddepcontrol.launch_dependents), so the successor's launch and CTA set-up
+// overlap this kernel instead of following it.  PNP_PDL=0 in the environment
+// launches them the ordinary way (the waits are then no-ops).
+__device__ __forceinline__ void pdl_begin()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+
+bool pdl_enabled();
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args&&... args)
+{
+    if (!pdl_enabled()) {
+        kernel<<<grid, block, smem, st>>>(std::forward<Args>(args)...);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 
 constexpr int kMaxLevels = 4;          // factors 1, 2, 4, 8
 constexpr int kPad = 2;                // padding of the coefficient image

@@ -110,6 +110,7 @@ struct PrepTable {
 
 __global__ void k_prep_quad(const PrepTable t)
 {
+    pdl_begin();
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= t.begin[t.count]) return;
     int c = 0;
@@ -149,6 +150,7 @@ struct FwdTable {
 template <int Q>
 __global__ void __launch_bounds__(256, 4) k_forward(const FwdTable t)
 {
+    pdl_begin();
     constexpr int R = 32 / Q;
     const int lane = threadIdx.x & 31;
     const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -236,6 +238,7 @@ struct BackTable {
 template <int NWIN>
 __global__ void __launch_bounds__(512, 2) k_backward2x2(const BackTable t)
 {
+    pdl_begin();
     const int tx = threadIdx.x, ty = threadIdx.y, g = threadIdx.z, G = blockDim.z;
     int c = 0;
 #pragma unroll
@@ -495,7 +498,8 @@ cudaError_t launch_prep_multi(const PrepArgs* items, int count, cudaStream_t st)
         t.c[c] = items[c];
         t.begin[c + 1] = t.begin[c] + (long)items[c].batch * items[c].qw * items[c].qw;
     }
-    k_prep_quad<<<div_up(t.begin[count], 256), 256, 0, st>>>(t);
+    const cudaError_t e = launch_pdl(k_prep_quad, dim3(div_up(t.begin[count], 256)), dim3(256), 0, st, t);
+    if (e != cudaSuccess) return e;
     return counted();
 }
 
@@ -507,11 +511,11 @@ cudaError_t launch_prep_quad(const float* fine, int n, int s, int batch, float4*
 }
 
 template <int Q>
-void forward_q(const FwdTable& t, cudaStream_t st)
+cudaError_t forward_q(const FwdTable& t, cudaStream_t st)
 {
     const long rays = t.begin[t.count];
     const long warps = (rays + (32 / Q) - 1) / (32 / Q);
-    k_forward<Q><<<div_up(warps * 32, 256), 256, 0, st>>>(t);
+    return launch_pdl(k_forward<Q>, dim3(div_up(warps * 32, 256)), dim3(256), 0, st, t);
 }
 
 cudaError_t launch_forward_multi(const FwdArgs* items, int count, cudaStream_t st, int lanes)
@@ -529,12 +533,8 @@ cudaError_t launch_forward_multi(const FwdArgs* items, int count, cudaStream_t s
     // unless the autotuner chose
     int Q = lanes;
     if (Q != 4 && Q != 8 && Q != 16) Q = rays * 4 >= 600000L ? 4 : rays * 8 >= 600000L ? 8 : 16;
-    if (Q == 4)
-        forward_q<4>(t, st);
-    else if (Q == 8)
-        forward_q<8>(t, st);
-    else
-        forward_q<16>(t, st);
+    const cudaError_t e = Q == 4 ? forward_q<4>(t, st) : Q == 8 ? forward_q<8>(t, st) : forward_q<16>(t, st);
+    if (e != cudaSuccess) return e;
     return counted();
 }
 
@@ -569,10 +569,9 @@ cudaError_t launch_backward_multi(const BackArgs* items, int count, cudaStream_t
         while (G < kBack2MaxGroups && blocks * G < 2L * 152 * 2048 && G * 2 <= min_views) G *= 2;
     }
     dim3 blk(kBack2TileX, kBack2TileY, G), grd((unsigned)t.begin[count]);
-    if (half_step)
-        k_backward2x2<9><<<grd, blk, 0, st>>>(t);
-    else
-        k_backward2x2<0><<<grd, blk, 0, st>>>(t);
+    const cudaError_t e = half_step ? launch_pdl(k_backward2x2<9>, grd, blk, 0, st, t)
+                                    : launch_pdl(k_backward2x2<0>, grd, blk, 0, st, t);
+    if (e != cudaSuccess) return e;
     return counted();
 }
 

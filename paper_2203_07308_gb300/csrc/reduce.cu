@@ -5,10 +5,21 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 
 #include "pnp_internal.cuh"
 
 namespace pnp {
+
+bool pdl_enabled()
+{
+    static const bool on = [] {
+        const char* e = std::getenv("PNP_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
 namespace {
 
 __device__ __forceinline__ double block_sum(double v)

@@ -30,6 +30,7 @@ __global__ void k_tv_final(const float* __restrict__ z, const float* __restrict_
                            float* __restrict__ xprev, float* __restrict__ y,
                            const float* __restrict__ xtrue, double* __restrict__ mse_part)
 {
+    pdl_begin();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y * blockDim.y + threadIdx.y;
     const int inst = blockIdx.z;
@@ -116,6 +117,7 @@ __host__ __device__ inline int tile_pitch(int S) { return S + ((40 - S % 32) % 3
 template <int NP>
 __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
 {
+    pdl_begin();
     int cls = 0;
 #pragma unroll
     for (int k = 1; k < kMaxClasses; ++k)
@@ -278,8 +280,9 @@ cudaError_t launch_tv_final(const float* z, const float* p, int have_p, int n, i
 {
     dim3 blk(32, 8), grd(div_up(n, 32), div_up(n, 8), batch);
     long plane = (long)batch * n * n;
-    k_tv_final<<<grd, blk, 0, st>>>(z, p, have_p, n, plane, lambda, alpha, a, xprev, y, xtrue,
-                                    mse_partials);
+    const cudaError_t e = launch_pdl(k_tv_final, grd, blk, 0, st, z, p, have_p, n, plane, lambda, alpha, a, xprev,
+                                     y, xtrue, mse_partials);
+    if (e != cudaSuccess) return e;
     return counted();
 }
 
@@ -392,13 +395,13 @@ cudaError_t launch_tv_tiled_multi(const TvItem* items, int count, float lambda, 
         for (int k = 0; k < K; ++k) a.mom[k] = mom[k0 + k];
         const dim3 grd((unsigned)a.begin[count]);
         const size_t sm = tile_smem(Tmax, K);
+        const dim3 blk(kTileThreads);
         switch (tile_np(Tmax, K)) {
-            case 1: k_tv_tile<1><<<grd, kTileThreads, sm, st>>>(a); break;
-            case 2: k_tv_tile<2><<<grd, kTileThreads, sm, st>>>(a); break;
-            case 3: k_tv_tile<3><<<grd, kTileThreads, sm, st>>>(a); break;
-            default: k_tv_tile<4><<<grd, kTileThreads, sm, st>>>(a); break;
+            case 1: e = launch_pdl(k_tv_tile<1>, grd, blk, sm, st, a); break;
+            case 2: e = launch_pdl(k_tv_tile<2>, grd, blk, sm, st, a); break;
+            case 3: e = launch_pdl(k_tv_tile<3>, grd, blk, sm, st, a); break;
+            default: e = launch_pdl(k_tv_tile<4>, grd, blk, sm, st, a); break;
         }
-        e = cudaGetLastError();
         g_launches.fetch_add(1, std::memory_order_relaxed);
         if (e != cudaSuccess) return e;
         k0 += K;
