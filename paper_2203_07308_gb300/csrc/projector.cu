@@ -139,8 +139,10 @@ __global__ void k_prep_quad(const PrepTable t)
 
 // ------------------------------------------------------------------ forward A_s
 // Warp = R rays x Q phases (R*Q = 32): lane (r, q) sums the samples k = k_lo + q,
-// k_lo + q + Q, ... of ray r; the Q partial sums are combined by shuffles in a
-// fixed order, so the result is deterministic.  One 16-byte load per sample.
+// k_lo + q + Q, ... of ray r into four interleaved partial sums (independent
+// chains keep four loads in flight); the four, then the Q lanes' sums, are
+// combined in a fixed order, so the result is deterministic.  One 16-byte load
+// per sample.
 struct FwdTable {
     FwdArgs c[kMaxClasses];
     long begin[kMaxClasses + 1];   // cumulative ray counts (batch * n_sub * n_det)
@@ -182,9 +184,9 @@ __global__ void __launch_bounds__(256, 4) k_forward(const FwdTable t)
         float kf = (float)(kr.x + q) + 0.5f;
         const float dk = (float)Q;
         const float step = a.step;
-#pragma unroll 4
-        for (int k = kr.x + q; k <= kr.y; k += Q) {
-            const float tt = kf * step;
+        float acc2 = 0.0f, acc3 = 0.0f, acc4 = 0.0f;
+        auto smp = [&](float kk) {
+            const float tt = kk * step;
             const float X = fmaf(tt, f.z, f.x);
             const float Y = fmaf(tt, f.w, f.y);
             const float mx = __fadd_rn(X, kMagic);
@@ -194,9 +196,22 @@ __global__ void __launch_bounds__(256, 4) k_forward(const FwdTable t)
             const int ix = __float_as_int(mx) - bias;
             const int iy = __float_as_int(my) - bias;
             const float4 cq = __ldg(img + iy * qw + ix);
-            acc += fmaf(w, fmaf(u, cq.w, cq.z), fmaf(u, cq.y, cq.x));
+            return fmaf(w, fmaf(u, cq.w, cq.z), fmaf(u, cq.y, cq.x));
+        };
+        int k = kr.x + q;
+#pragma unroll 2
+        for (; k + 3 * Q <= kr.y; k += 4 * Q) {
+            acc += smp(kf);
+            acc2 += smp(kf + dk);
+            acc3 += smp(kf + 2.0f * dk);
+            acc4 += smp(kf + 3.0f * dk);
+            kf += 4.0f * dk;
+        }
+        for (; k <= kr.y; k += Q) {
+            acc += smp(kf);
             kf += dk;
         }
+        acc = (acc + acc2) + (acc3 + acc4);
     }
 #pragma unroll
     for (int o = Q / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -283,9 +298,19 @@ __global__ void __launch_bounds__(512, 2) k_backward2x2(const BackTable t)
             const int jhi = min(a.n_det - 1, (int)floorf(uj + hw));
             const long base = (long)v * a.n_det;
             const float* __restrict__ rrow = res + (long)vs * a.n_det;
-            float v00 = 0.0f, v10 = 0.0f, v01 = 0.0f, v11 = 0.0f;
+            float4 fn = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+            float rn = 0.0f;
+            if (jlo <= jhi) {
+                fn = __ldg(a.rayf + base + jlo);
+                rn = __ldg(rrow + jlo);
+            }
             for (int j = jlo; j <= jhi; ++j) {
-                const float4 f = __ldg(a.rayf + base + j);
+                const float4 f = fn;
+                const float r = rn;
+                if (j < jhi) {
+                    fn = __ldg(a.rayf + base + j + 1);
+                    rn = __ldg(rrow + j + 1);
+                }
                 const float ax = px - f.x, ay = py - f.y;
                 const float e = ax * f.w - ay * f.z;
                 if (fabsf(e) >= 1.5f * (fabsf(f.z) + fabsf(f.w))) continue;
@@ -313,13 +338,11 @@ __global__ void __launch_bounds__(512, 2) k_backward2x2(const BackTable t)
                 } else {
                     for (int m = 0; m < nwin; ++m) sample((float)m);
                 }
-                const float r = __ldg(rrow + j);
-                v00 = fmaf(w00, r, v00);
-                v10 = fmaf(w10, r, v10);
-                v01 = fmaf(w01, r, v01);
-                v11 = fmaf(w11, r, v11);
+                t00 = fmaf(w00, r, t00);
+                t10 = fmaf(w10, r, t10);
+                t01 = fmaf(w01, r, t01);
+                t11 = fmaf(w11, r, t11);
             }
-            t00 += v00; t10 += v10; t01 += v01; t11 += v11;
         }
     }
     const int slot = ty * kBack2TileX + tx;
