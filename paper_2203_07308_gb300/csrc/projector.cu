@@ -323,10 +323,10 @@ __global__ void __launch_bounds__(512, 2) k_backward2x2(const BackTable t)
                 const float sx = a.step * f.z, sy = a.step * f.w;
                 float w00 = 0.0f, w10 = 0.0f, w01 = 0.0f, w11 = 0.0f;
                 auto sample = [&](float fm) {
-                    const float hxa = fmaxf(1.0f - fabsf(fmaf(fm, sx, xa0)), 0.0f);
-                    const float hxb = fmaxf(1.0f - fabsf(fmaf(fm, sx, xb0)), 0.0f);
-                    const float hya = fmaxf(1.0f - fabsf(fmaf(fm, sy, ya0)), 0.0f);
-                    const float hyb = fmaxf(1.0f - fabsf(fmaf(fm, sy, yb0)), 0.0f);
+                    const float hxa = __saturatef(1.0f - fabsf(fmaf(fm, sx, xa0)));
+                    const float hxb = __saturatef(1.0f - fabsf(fmaf(fm, sx, xb0)));
+                    const float hya = __saturatef(1.0f - fabsf(fmaf(fm, sy, ya0)));
+                    const float hyb = __saturatef(1.0f - fabsf(fmaf(fm, sy, yb0)));
                     w00 = fmaf(hxa, hya, w00);
                     w10 = fmaf(hxb, hya, w10);
                     w01 = fmaf(hxa, hyb, w01);
