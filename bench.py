@@ -37,8 +37,8 @@ L2_FLUSH_BYTES = 512 << 20
 # capture (dram__bytes_read.sum + dram__bytes_write.sum over the 100
 # backprojection launches of one step, averaged); valid only while the
 # backprojector source is the one that was measured.
-BACKWARD_TRAFFIC = {"bytes_per_launch": 718592,
-                    "source_sha256": "b883818d309124dbe395efd064b3d06f16ad5df6cfd18062bad7601df69a95d0",
+BACKWARD_TRAFFIC = {"bytes_per_launch": 718428,
+                    "source_sha256": "e2cf86e2006b20b3eaa581b2883ab07c55cef7f5d73b451203940b802a89e66d",
                     "profile": "profiles/k_backward2x2_256_360x512_step.md"}
 
 

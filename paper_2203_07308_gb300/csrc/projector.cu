@@ -239,11 +239,13 @@ constexpr int kBack2TileY = 4;
 constexpr int kBack2MaxGroups = 16;
 
 // The four pixels share the view set-up and the candidate rays; their union
-// support is the 3 x 3 square around the block centre (radius rho = 1.5 sqrt 2),
-// so a ray's samples that can touch any of them lie within rho of the centre's
-// projection on the ray: at most floor(2 rho / step) + 1 (9 for step 1/2).
-// Each sample evaluates the two x hats and two y hats once and feeds four
-// products.
+// support is the 3 x 3 square around the block centre, whose extent across and
+// along a ray of direction d is 3 (|d_x| + |d_y|) <= 3 sqrt 2 = 2 rho.  A ray
+// meets it only if its distance from the centre is below half that, and then
+// only samples whose projection lies within half that of the centre's can touch
+// a pixel: floor(3 (|d_x| + |d_y|) / step) + 1 samples (7 to 9 for step 1/2).
+// Each sample evaluates the two x hats and two y hats once (saturated 1 - |x|)
+// and feeds four products.
 struct BackTable {
     BackArgs c[kMaxClasses];
     long begin[kMaxClasses + 1];   // cumulative CTA counts (batch * tiles)
@@ -313,9 +315,11 @@ __global__ void __launch_bounds__(512, 2) k_backward2x2(const BackTable t)
                 }
                 const float ax = px - f.x, ay = py - f.y;
                 const float e = ax * f.w - ay * f.z;
-                if (fabsf(e) >= 1.5f * (fabsf(f.z) + fabsf(f.w))) continue;
+                const float hwid = 1.5f * (fabsf(f.z) + fabsf(f.w));   // half the support's width across / along d
+                if (fabsf(e) >= hwid) continue;
                 const float tau = fmaf(ax, f.z, ay * f.w);
-                const float k0 = ceilf(fmaf(tau - rho, inv_step, -0.5f));
+                const float k0 = ceilf(fmaf(tau - hwid, inv_step, -0.5f));
+                const int cnt = (int)(2.0f * hwid * inv_step) + 1;
                 const float t0 = (k0 + 0.5f) * a.step;
                 const float X0 = fmaf(t0, f.z, -ax), Y0 = fmaf(t0, f.w, -ay);
                 const float xa0 = X0 + 0.5f, xb0 = X0 - 0.5f;    // relative to the left / right pixel
@@ -334,9 +338,11 @@ __global__ void __launch_bounds__(512, 2) k_backward2x2(const BackTable t)
                 };
                 if (NWIN > 0) {
 #pragma unroll
-                    for (int m = 0; m < (NWIN > 0 ? NWIN : 1); ++m) sample((float)m);
+                    for (int m = 0; m < (NWIN > 2 ? NWIN - 2 : 1); ++m) sample((float)m);
+                    if (cnt > NWIN - 2) sample((float)(NWIN - 2));
+                    if (cnt > NWIN - 1) sample((float)(NWIN - 1));
                 } else {
-                    for (int m = 0; m < nwin; ++m) sample((float)m);
+                    for (int m = 0; m < min(cnt, nwin); ++m) sample((float)m);
                 }
                 t00 = fmaf(w00, r, t00);
                 t10 = fmaf(w10, r, t10);
