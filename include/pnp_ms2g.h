@@ -285,11 +285,13 @@ int pnp_run_many(const pnp_problem* problems, int n_problems, const pnp_run_para
 /* Launch shapes of a prepared workspace, per sketch level (index 0..3 for the
  * factors 1, 2, 4, 8), 0 meaning the built-in heuristic:
  *   lanes   forward projector lanes per ray: 4, 8 or 16
- *   back    backprojector view groups per CTA: 1, 2, 4, 8 or 16
+ *   back    backprojector CTA: G view groups (1..32) of 8 x 4 pixel blocks, or
+ *           PNP_BACK_TILE4 | G: G view groups (1..64) of 4 x 4 pixel blocks
  *   tile    side of the FGP tile (8..40)
  * The backprojector's view groups fix its summation order: results are bitwise
  * reproducible for fixed shapes.  pnp_autotune sets them; pnp_set_launch_shapes
  * pins them (PNP_EINVAL for a shape outside these sets). */
+#define PNP_BACK_TILE4 (1 << 8)
 typedef struct {
     int32_t lanes[4];
     int32_t back[4];

@@ -46,6 +46,8 @@ class LaunchShapes(C.Structure):
     _fields_ = [("lanes", C.c_int32 * 4), ("back", C.c_int32 * 4), ("tile", C.c_int32)]
 
 
+BACK_TILE4 = 1 << 8     # backprojector CTAs of 4 x 4 pixel blocks (| view groups)
+
 SKETCH_POOL, SKETCH_BICUBIC = 0, 1
 EST_MINIBATCH, EST_SVRG, EST_SAGA = 0, 1, 2
 

@@ -1189,10 +1189,17 @@ int pnp_autotune(const pnp_geom* g, const pnp_stage* stages, int n_stages, const
         const BackArgs ba = back_args(*g, lv, ws, 0, P, res, kBackRaw, 1.0f, nullptr, 0.0f, z, g->batch);
         best = 1e30f;
         const int nsub = subset_views(*g, 0, P);
-        for (int G = 1; G <= 16 && G <= nsub; G *= 2) {
+        // 8 x 4 blocks with 1..16 view groups; 4 x 4 blocks with 16, 32, 64 groups,
+        // one or two views per thread
+        std::vector<int> shapes;
+        for (int G = 1; G <= 16 && G <= nsub; G *= 2) shapes.push_back(G);
+        for (int G : {16, 32, 64, nsub, (nsub + 1) / 2})
+            if (G >= 8 && G <= 64 && G <= nsub) shapes.push_back(PNP_BACK_TILE4 | G);
+        for (int shp : shapes) {
             float ms = 0.0f;
-            if (rc == PNP_OK) rc = timeit([&]() -> int { PNP_CUDA(launch_backward(ba, st, G)); return PNP_OK; }, &ms);
-            if (rc == PNP_OK && ms < best) { best = ms; tu.groups[li] = G; }
+            if (rc == PNP_OK)
+                rc = timeit([&]() -> int { PNP_CUDA(launch_backward(ba, st, shp)); return PNP_OK; }, &ms);
+            if (rc == PNP_OK && ms < best) { best = ms; tu.groups[li] = shp; }
         }
     }
     const pnp_run_params& pr = *params;
@@ -1244,8 +1251,10 @@ int pnp_set_launch_shapes(const pnp_geom* g, const pnp_launch_shapes* in, void* 
     for (int k = 0; k < 4; ++k) {
         const int q = in->lanes[k], b = in->back[k];
         if (q != 0 && q != 4 && q != 8 && q != 16) return fail(PNP_EINVAL, "lanes[%d] = %d not in {0, 4, 8, 16}", k, q);
-        const bool ok = b == 0 || (b >= 1 && b <= 16 && (b & (b - 1)) == 0);
-        if (!ok) return fail(PNP_EINVAL, "back[%d] = %d not in {0, 1, 2, 4, 8, 16}", k, b);
+        const int bg = b & 0xff;
+        const bool ok = b == 0 || ((b & ~(PNP_BACK_TILE4 | 0xff)) == 0 && bg >= 1 &&
+                                   bg <= ((b & PNP_BACK_TILE4) ? 64 : 32));
+        if (!ok) return fail(PNP_EINVAL, "back[%d] = %#x is not a backprojector shape", k, b);
         tu.lanes[k] = q;
         tu.groups[k] = b;
     }

@@ -233,7 +233,10 @@ __global__ void __launch_bounds__(256, 4) k_forward(const FwdTable t)
 // block.  The G partial sums are added in a fixed order through shared memory,
 // so the result is deterministic for a given G (a function of the problem
 // size).  CTA = 8 x 4 blocks (16 x 8 pixels) x G view groups, so the 32
-// threads of a warp walk the same views in step.
+// threads of a warp walk the same views in step; or 4 x 4 blocks x G, two view
+// groups per warp, which allows up to 64 groups (one view per thread for
+// subsets of up to 64 views) and four times as many CTAs, so that the CTAs
+// pack the SMs with a smaller partial last wave.
 constexpr int kBack2TileX = 8;    // a warp = 8 x 4 blocks of one view group
 constexpr int kBack2TileY = 4;
 constexpr int kBack2MaxGroups = 16;
@@ -252,8 +255,8 @@ struct BackTable {
     int count;
 };
 
-template <int NWIN>
-__global__ void __launch_bounds__(512, 2) k_backward2x2(const BackTable t)
+template <int NWIN, int TX>
+__global__ void __launch_bounds__(1024, 1) k_backward2x2(const BackTable t)
 {
     pdl_begin();
     const int tx = threadIdx.x, ty = threadIdx.y, g = threadIdx.z, G = blockDim.z;
@@ -263,16 +266,16 @@ __global__ void __launch_bounds__(512, 2) k_backward2x2(const BackTable t)
         if (k < t.count && (long)blockIdx.x >= t.begin[k]) c = k;
     const BackArgs& a = t.c[c];
     const int nb = (a.ns + 1) / 2;                             // blocks per side
-    const int tiles_x = (nb + kBack2TileX - 1) / kBack2TileX;
+    const int tiles_x = (nb + TX - 1) / TX;
     const int tiles_y = (nb + kBack2TileY - 1) / kBack2TileY;
     const long local = (long)blockIdx.x - t.begin[c];
     const int tiles = tiles_x * tiles_y;
     const int inst = (int)(local / tiles);
     const int tile = (int)(local - (long)inst * tiles);
-    const int bx = (tile % tiles_x) * kBack2TileX + tx;
+    const int bx = (tile % tiles_x) * TX + tx;
     const int by = (tile / tiles_x) * kBack2TileY + ty;
     const bool inside = bx < nb && by < nb;
-    __shared__ float4 part[kBack2MaxGroups][kBack2TileX * kBack2TileY];
+    extern __shared__ float4 part[];                           // [G][TX * kBack2TileY]
     float t00 = 0.0f, t10 = 0.0f, t01 = 0.0f, t11 = 0.0f;
     if (inside) {
         const int ix = 2 * bx, iy = 2 * by;
@@ -351,13 +354,14 @@ __global__ void __launch_bounds__(512, 2) k_backward2x2(const BackTable t)
             }
         }
     }
-    const int slot = ty * kBack2TileX + tx;
-    part[g][slot] = make_float4(t00, t10, t01, t11);
+    constexpr int kSlots = TX * kBack2TileY;
+    const int slot = ty * TX + tx;
+    part[g * kSlots + slot] = make_float4(t00, t10, t01, t11);
     __syncthreads();
     if (g != 0 || !inside) return;
     float s00 = 0.0f, s10 = 0.0f, s01 = 0.0f, s11 = 0.0f;
     for (int q = 0; q < G; ++q) {
-        const float4 pq = part[q][slot];
+        const float4 pq = part[q * kSlots + slot];
         s00 += pq.x; s10 += pq.y; s01 += pq.z; s11 += pq.w;
     }
     const float vals[4] = {a.scale * s00, a.scale * s10, a.scale * s01, a.scale * s11};
@@ -575,6 +579,9 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t st, int lanes)
 cudaError_t launch_backward_multi(const BackArgs* items, int count, cudaStream_t st, int groups)
 {
     if (count < 1 || count > kMaxClasses) return cudaErrorInvalidValue;
+    // CTA shape: TX x 4 blocks x G view groups; PNP_BACK_TILE4 selects TX = 4
+    const int TX = (groups & PNP_BACK_TILE4) ? 4 : kBack2TileX;
+    int G = groups & 0xff;
     BackTable t{};
     t.count = count;
     t.begin[0] = 0;
@@ -584,22 +591,27 @@ cudaError_t launch_backward_multi(const BackArgs* items, int count, cudaStream_t
     for (int c = 0; c < count; ++c) {
         t.c[c] = items[c];
         const int nb = (items[c].ns + 1) / 2;
-        const int tiles = div_up(nb, kBack2TileX) * div_up(nb, kBack2TileY);
+        const int tiles = div_up(nb, TX) * div_up(nb, kBack2TileY);
         t.begin[c + 1] = t.begin[c] + (long)tiles * items[c].batch;
         blocks += (long)nb * nb * items[c].batch;
         min_views = min(min_views, items[c].n_sub);
         half_step = half_step && items[c].step == 0.5f;
     }
-    // view groups: about two waves of 2048 threads per SM, at most 32 per CTA,
+    // view groups: about two waves of 2048 threads per SM, at most 16 per CTA,
     // unless the autotuner chose
-    int G = groups;
-    if (G < 1 || G > kBack2MaxGroups || (G & (G - 1))) {
+    if (G < 1 || G * TX * kBack2TileY > 1024) {
         G = 1;
         while (G < kBack2MaxGroups && blocks * G < 2L * 152 * 2048 && G * 2 <= min_views) G *= 2;
     }
-    dim3 blk(kBack2TileX, kBack2TileY, G), grd((unsigned)t.begin[count]);
-    const cudaError_t e = half_step ? launch_pdl(k_backward2x2<9>, grd, blk, 0, st, t)
-                                    : launch_pdl(k_backward2x2<0>, grd, blk, 0, st, t);
+    dim3 blk(TX, kBack2TileY, G), grd((unsigned)t.begin[count]);
+    const size_t smem = (size_t)G * TX * kBack2TileY * sizeof(float4);
+    cudaError_t e;
+    if (TX == 4)
+        e = half_step ? launch_pdl(k_backward2x2<9, 4>, grd, blk, smem, st, t)
+                      : launch_pdl(k_backward2x2<0, 4>, grd, blk, smem, st, t);
+    else
+        e = half_step ? launch_pdl(k_backward2x2<9, kBack2TileX>, grd, blk, smem, st, t)
+                      : launch_pdl(k_backward2x2<0, kBack2TileX>, grd, blk, smem, st, t);
     if (e != cudaSuccess) return e;
     return counted();
 }
