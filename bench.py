@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--graph", action="store_true", help="replay a captured CUDA graph instead of direct launches")
     ap.add_argument("--no-autotune", action="store_true", help="heuristic launch shapes")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched, mixed and differentiable comparisons")
     ap.add_argument("--profile", action="store_true",
                     help="only the warm-up and the timed steps (inside an NVTX range 'timed'), "
                          "for ncu: no end-to-end, time-to-PSNR or CPU legs")
@@ -278,6 +280,140 @@ def paper_sparse_view(plan_factory, dev, kw):
     return out
 
 
+def _simulate(plan, wl, dev, seed_offset=0):
+    """x_true [B, n, n], b = A x_true + sigma w per image (GPU forward), on the device."""
+    import torch
+    from paper_2203_07308_gb300 import synth
+    g = wl.geom
+    xt = synth.phantom_batch(wl).astype(np.float32)
+    d_xt = torch.from_numpy(xt).to(dev)
+    d_b = torch.empty(g.batch, g.n_views, g.n_det, device=dev)
+    plan.project(1, d_xt, d_b)
+    w = synth.noise_draws((g.batch, g.n_views, g.n_det), synth.noise_seed(wl.config_id) + seed_offset)
+    sig = wl.noise_rel * d_b.abs().amax(dim=(1, 2), keepdim=True)
+    d_b += sig * torch.from_numpy(w.astype(np.float32)).to(dev)
+    return d_xt, d_b
+
+
+def _device_ms(fn, stream):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def _time_to_target(plan, stages, eta, seq, d_b, d_x, log, target, kw, stream):
+    """Device time of the run cut at the first iteration whose mean PSNR reaches target."""
+    from paper_2203_07308_gb300 import synth
+    hit = np.nonzero(log.mean(axis=1) >= target)[0]
+    if hit.size == 0:
+        return None, None
+    it = int(hit[0]) + 1
+    cut, left = [], it
+    for st_ in stages:
+        k = min(st_.iters, left)
+        if k > 0:
+            cut.append(synth.Stage(st_.factor, k, st_.n_subsets))
+        left -= k
+    plan.run(cut, eta[:len(cut)], seq, d_b, d_x.zero_(), **kw)     # warm
+    return _device_ms(lambda: plan.run(cut, eta[:len(cut)], seq, d_b, d_x.zero_(), **kw), stream), it
+
+
+def batched_512x16(dev, stream):
+    """16 x 512^2, 720 views x 768 bins in one launch per phase: the three-stage
+    sketched schedule (4x, 2x, full; 12 angle subsets) against full-gradient
+    PnP-FISTA with the same iteration count, time to the full arm's final mean
+    PSNR - 0.1 dB, and the sketched run's gradient estimates per second."""
+    import torch
+    import paper_2203_07308_gb300 as pnp
+    from paper_2203_07308_gb300 import synth
+    wl = synth.workloads()["c3_512x16"]
+    g = wl.geom
+    plan = pnp.Plan(g)
+    d_xt, d_b = _simulate(plan, wl, dev)
+    kw = dict(alpha=wl.alpha, lam=wl.tv_lambda, tv_iters=wl.tv_iters, momentum=wl.momentum)
+    plan.autotune(wl.stages, **kw)
+    eta = [1.0 / plan.power_iter(st_.factor, 100, 1e-6)[0] for st_ in wl.stages]
+    seq = synth.schedule_sequence(wl.stages, synth.subset_seed(wl.config_id))
+    full = synth.full_gradient_arm(wl.stages)
+    d_x = torch.zeros(g.batch, g.n, g.n, device=dev)
+    log_s = plan.run(wl.stages, eta, seq, d_b, d_x.zero_(), xtrue=d_xt, **kw)
+    ms_s = _device_ms(lambda: plan.run(wl.stages, eta, seq, d_b, d_x.zero_(), **kw), stream)
+    log_f = plan.run(full, [eta[-1]], None, d_b, d_x.zero_(), xtrue=d_xt, **kw)
+    target = float(log_f[-1].mean()) - 0.1
+    tts_s, it_s = _time_to_target(plan, wl.stages, eta, seq, d_b, d_x, log_s, target, kw, stream)
+    tts_f, it_f = _time_to_target(plan, full, [eta[-1]], None, d_b, d_x, log_f, target, kw, stream)
+    total = sum(st_.iters for st_ in wl.stages)
+    return {"workload": "16 x 512x512, 720 views x 768 bins, stages (4x,24),(2x,24),(1x,72), 12 subsets",
+            "sketched_run_ms": ms_s, "gradients_per_s": g.batch * total / (ms_s / 1000.0),
+            "target_db": target, "sketched_final_db": float(log_s[-1].mean()),
+            "full_final_db": float(log_f[-1].mean()),
+            "sketched_ms": tts_s, "sketched_iters": it_s, "full_ms": tts_f, "full_iters": it_f,
+            "speedup": (tts_f / tts_s) if (tts_s and tts_f) else None}
+
+
+def mixed_64(dev, stream):
+    """64 instances of 128^2/180/256, 256^2/360/512 and 512^2/720/768 (seeded mix)
+    in one call: every phase of every iteration one launch over the three
+    classes; 50 sketched iterations each."""
+    import torch
+    import paper_2203_07308_gb300 as pnp
+    from paper_2203_07308_gb300 import synth
+    probs, n_img, iters = [], 0, 0
+    for wl, _ids in synth.mixed_classes(64):
+        g = wl.geom
+        plan = pnp.Plan(g)
+        d_xt, d_b = _simulate(plan, wl, dev)
+        kw = dict(alpha=wl.alpha, lam=wl.tv_lambda, tv_iters=wl.tv_iters, momentum=wl.momentum)
+        plan.autotune(wl.stages, **kw)
+        eta = [1.0 / plan.power_iter(st_.factor, 60, 1e-6)[0] for st_ in wl.stages]
+        seq = synth.schedule_sequence(wl.stages, synth.subset_seed(wl.config_id))
+        probs.append(dict(plan=plan, stages=wl.stages, eta=eta, seq=seq, b=d_b,
+                          x=torch.zeros(g.batch, g.n, g.n, device=dev)))
+        n_img += g.batch
+        iters = sum(st_.iters for st_ in wl.stages)
+    pnp.run_many(probs, alpha=1.0, lam=0.02, tv_iters=20, momentum=True)      # warm
+    ms = _device_ms(lambda: pnp.run_many(probs, alpha=1.0, lam=0.02, tv_iters=20, momentum=True), stream)
+    return {"workload": "64 mixed instances (seed 5308), 3 geometry classes, 50 iterations",
+            "classes": [[p_["plan"].g.n, p_["plan"].g.n_views, p_["plan"].g.n_det, p_["plan"].g.batch] for p_ in probs],
+            "run_ms": ms, "gradients_per_s": n_img * iters / (ms / 1000.0)}
+
+
+def differentiable_256x8(dev, stream):
+    """8 x 256^2, 360 x 512: 10 unrolled iterations through torch.autograd with
+    the 2x sketch against the full-gradient unroll: forward + backward device
+    time and the mean PSNR of x_T."""
+    import torch
+    import paper_2203_07308_gb300 as pnp
+    from paper_2203_07308_gb300 import synth
+    from paper_2203_07308_gb300.autograd import unrolled_pnp
+    wl = synth.workloads()["c4_256x8"]
+    g = wl.geom
+    plan = pnp.Plan(g)
+    d_xt, d_b = _simulate(plan, wl, dev)
+    out = {"workload": "8 x 256x256, 360 views x 512 bins, 10 unrolled iterations, loss 1/2 ||x_T - x_true||^2"}
+    for name, stages in (("sketched", wl.stages), ("full", [synth.Stage(1, sum(s_.iters for s_ in wl.stages), 1)])):
+        eta = [1.0 / plan.power_iter(st_.factor, 60, 1e-6)[0] for st_ in stages]
+        seq = synth.schedule_sequence(stages, 3)
+
+        def fwd_bwd():
+            x0 = torch.zeros(g.batch, g.n, g.n, device=dev, requires_grad=True)
+            lam = torch.tensor(wl.tv_lambda, dtype=torch.float64, requires_grad=True)
+            xT = unrolled_pnp(plan, stages, eta, seq, d_b, x0, lam, alpha=wl.alpha, tv_iters=wl.tv_iters)
+            (0.5 * ((xT - d_xt) ** 2).sum()).backward()
+            return xT.detach()
+        xT = fwd_bwd()
+        mse = ((xT - d_xt) ** 2).mean(dim=(1, 2)).double().cpu().numpy()
+        out[name + "_fwd_bwd_ms"] = _device_ms(fwd_bwd, stream)
+        out[name + "_psnr_db"] = float(np.mean(10 * np.log10(1.0 / mse)))
+    out["time_ratio_full_over_sketched"] = out["full_fwd_bwd_ms"] / out["sketched_fwd_bwd_ms"]
+    return out
+
+
 def run_native(args, rank, world):
     import torch
     import paper_2203_07308_gb300 as pnp
@@ -447,6 +583,10 @@ def run_native(args, rank, world):
     # data with I0 = 10^5.5, two sketch stages m_1 = d/16 then m_2 = d/4,
     # Option 1) against full-gradient PnP-FISTA with the same iteration count
     paper = paper_sparse_view(plan_factory=pnp.Plan, dev=dev, kw=kw)
+    extras = {}
+    if not args.no_extras:
+        extras = {"batched_512x16": batched_512x16(dev, stream), "mixed_64": mixed_64(dev, stream),
+                  "differentiable_256x8": differentiable_256x8(dev, stream)}
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     h_b = torch.empty(d_b.shape, dtype=torch.float32, pin_memory=True)
@@ -545,6 +685,7 @@ def run_native(args, rank, world):
                              "full_ms": tts_f, "full_iters": it_f,
                              "speedup": (tts_f / tts_s) if (tts_s and tts_f) else None},
             "paper_sparse_view": paper,
+            **extras,
             "setup_ms_power_iteration": setup_ms,
             "setup_ms_autotune": tune_ms,
             "launch_mode": "CUDA graph captured once, replayed per step" if use_graph else "direct launches",

@@ -513,7 +513,7 @@ def run_many(problems, *, alpha=1.0, lam=0.02, tv_iters=20, momentum=True, strea
     return logs
 
 
-def autotune(g, stages, ws, *, alpha=1.0, lam=0.02, tv_iters=20, stream=None):
+def autotune(g, stages, ws, *, alpha=1.0, lam=0.02, tv_iters=20, momentum=True, stream=None):
     st = _stages(stages)
-    prm = RunParams(float(alpha), float(lam), int(tv_iters), 1, 0)
+    prm = RunParams(float(alpha), float(lam), int(tv_iters), int(bool(momentum)), 0)
     _check(load().pnp_autotune(C.byref(geom(g)), st, len(st), C.byref(prm), _ws(ws)[0], _stream(stream)))
