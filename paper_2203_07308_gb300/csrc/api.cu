@@ -1189,11 +1189,11 @@ int pnp_autotune(const pnp_geom* g, const pnp_stage* stages, int n_stages, const
         const BackArgs ba = back_args(*g, lv, ws, 0, P, res, kBackRaw, 1.0f, nullptr, 0.0f, z, g->batch);
         best = 1e30f;
         const int nsub = subset_views(*g, 0, P);
-        // 8 x 4 blocks with 1..16 view groups; 4 x 4 blocks with 16, 32, 64 groups,
-        // one or two views per thread
+        // 8 x 4 blocks with 1..16 view groups; 4 x 4 blocks with 8..64 groups (one,
+        // two or a few views per thread; smaller CTAs pack the SMs more evenly)
         std::vector<int> shapes;
         for (int G = 1; G <= 16 && G <= nsub; G *= 2) shapes.push_back(G);
-        for (int G : {16, 32, 64, nsub, (nsub + 1) / 2})
+        for (int G : {8, 12, 16, 32, 64, nsub, (nsub + 1) / 2})
             if (G >= 8 && G <= 64 && G <= nsub) shapes.push_back(PNP_BACK_TILE4 | G);
         for (int shp : shapes) {
             float ms = 0.0f;

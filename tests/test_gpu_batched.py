@@ -197,3 +197,37 @@ def test_phase_event_timing():
     with pytest.raises(pnp.PnpError):
         plan.run(stages, eta, seq, dev(b), torch.zeros(g.batch, g.n, g.n, device="cuda"),
                  kernel_times=True, graph=True)
+
+
+def test_dependent_launch_changes_no_bit(tmp_path):
+    """The loop kernels' programmatic dependent launch only moves launch overhead:
+    a run in a process with PNP_PDL=0 (ordinary launches) gives the same bits."""
+    import os
+    import subprocess
+    import sys
+    import torch
+    g = synth.make_geometry(64, 60, 96, batch=2)
+    stages = [synth.Stage(2, 3, 5), synth.Stage(1, 4, 5)]
+    x, b, eta, seq = make_problem(g, stages, 17)
+    np.save(tmp_path / "b.npy", b)
+    script = tmp_path / "run.py"
+    script.write_text(f"""
+import sys, numpy as np, torch
+sys.path.insert(0, {os.path.dirname(os.path.dirname(os.path.abspath(__file__)))!r})
+import paper_2203_07308_gb300 as pnp
+from paper_2203_07308_gb300 import synth
+g = synth.make_geometry(64, 60, 96, batch=2)
+plan = pnp.Plan(g)
+plan.set_launch_shapes(lanes=(8, 8, 0, 0), back=(4, 4, 0, 0), tile=16)
+b = torch.from_numpy(np.load({str(tmp_path / "b.npy")!r}).astype(np.float32)).cuda()
+x = torch.zeros(2, 64, 64, device="cuda")
+plan.run([synth.Stage(2, 3, 5), synth.Stage(1, 4, 5)], {eta!r}, {list(map(int, seq))!r}, b, x)
+np.save(sys.argv[1], x.cpu().numpy())
+""")
+    outs = []
+    for pdl in ("1", "0"):
+        out = tmp_path / f"x{pdl}.npy"
+        env = dict(os.environ, PNP_PDL=pdl)
+        subprocess.run([sys.executable, str(script), str(out)], env=env, check=True, timeout=600)
+        outs.append(np.load(out))
+    assert np.array_equal(outs[0], outs[1])
