@@ -1193,7 +1193,7 @@ int pnp_autotune(const pnp_geom* g, const pnp_stage* stages, int n_stages, const
         // two or a few views per thread; smaller CTAs pack the SMs more evenly)
         std::vector<int> shapes;
         for (int G = 1; G <= 16 && G <= nsub; G *= 2) shapes.push_back(G);
-        for (int G : {8, 12, 16, 32, 64, nsub, (nsub + 1) / 2})
+        for (int G : {8, 12, 16, 18, 20, 24, 32, 64, nsub, (nsub + 1) / 2})
             if (G >= 8 && G <= 64 && G <= nsub) shapes.push_back(PNP_BACK_TILE4 | G);
         for (int shp : shapes) {
             float ms = 0.0f;
