@@ -37,8 +37,8 @@ L2_FLUSH_BYTES = 512 << 20
 # capture (dram__bytes_read.sum + dram__bytes_write.sum over the 100
 # backprojection launches of one step, averaged); valid only while the
 # backprojector source is the one that was measured.
-BACKWARD_TRAFFIC = {"bytes_per_launch": 718428,
-                    "source_sha256": "e2cf86e2006b20b3eaa581b2883ab07c55cef7f5d73b451203940b802a89e66d",
+BACKWARD_TRAFFIC = {"bytes_per_launch": 716293,
+                    "source_sha256": "e2aa4e69a260e096d57831ba1af2919f83d2838e8ed6257c9c370423a6dd603e",
                     "profile": "profiles/k_backward2x2_256_360x512_step.md"}
 
 
