@@ -1161,13 +1161,20 @@ int pnp_autotune(const pnp_geom* g, const pnp_stage* stages, int n_stages, const
     cudaEvent_t e0, e1;
     PNP_CUDA(cudaEventCreate(&e0));
     PNP_CUDA(cudaEventCreate(&e1));
+    // best of three batches of eight launches after two warm-up launches
     auto timeit = [&](auto&& fn, float* ms) -> int {
-        for (int rep = 0; rep < 2; ++rep) if (int e = fn()) return e;   // warm-up
-        PNP_CUDA(cudaEventRecord(e0, st));
-        for (int rep = 0; rep < 5; ++rep) if (int e = fn()) return e;
-        PNP_CUDA(cudaEventRecord(e1, st));
-        PNP_CUDA(cudaEventSynchronize(e1));
-        PNP_CUDA(cudaEventElapsedTime(ms, e0, e1));
+        for (int rep = 0; rep < 2; ++rep) if (int e = fn()) return e;
+        float best = 1e30f;
+        for (int trial = 0; trial < 3; ++trial) {
+            PNP_CUDA(cudaEventRecord(e0, st));
+            for (int rep = 0; rep < 8; ++rep) if (int e = fn()) return e;
+            PNP_CUDA(cudaEventRecord(e1, st));
+            PNP_CUDA(cudaEventSynchronize(e1));
+            float t = 0.0f;
+            PNP_CUDA(cudaEventElapsedTime(&t, e0, e1));
+            best = std::min(best, t);
+        }
+        *ms = best;
         return PNP_OK;
     };
     Tuned tu;
