@@ -204,11 +204,40 @@ def cpu_baseline(wl, sample_iters=(2, 6)):
     x, b, eta, seq = oracle_inputs(wl)
     secs, n = oracle_sample_run(wl, b, x, eta, seq, sample_iters)
     total = sum(s.iters for s in wl.stages)
-    # scale: time per iteration of each stage from the sample, weighted by stage length
-    return {"value": n / secs, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
-            "kind": "oracle",
+    # per-operation times of the full-view operators at this size, all cores and one thread
+    import oracle
+    g = wl.geom
+    cores = int(os.environ["OMP_NUM_THREADS"])
+    per_op = {}
+    for label, threads in (("all_cores", cores), ("one_thread", 1)):
+        prev = oracle.set_threads(threads)
+        t0 = time.perf_counter()
+        sino = oracle.project(g, 1, x)
+        t1 = time.perf_counter()
+        oracle.backproject(g, 1, sino)
+        t2 = time.perf_counter()
+        oracle.grad(g, 1, x, b)
+        t3 = time.perf_counter()
+        oracle.set_threads(prev)
+        per_op[label] = {"threads": threads, "forward_s": t1 - t0, "backproject_s": t2 - t1, "gradient_s": t3 - t2}
+    return {"value": n / secs, "unit": UNIT, "cores": cores,
+            "kind": "oracle", "cpu_model": cpu_model(),
             "sample": f"first {sample_iters[0]} sketched + {sample_iters[1]} full-grid iterations of the "
-                      f"{total}-iteration schedule, FP64 C oracle with OpenMP over rays ({secs:.1f} s)"}
+                      f"{total}-iteration schedule, FP64 C oracle with OpenMP over rays ({secs:.1f} s)",
+            "per_op_all_views": per_op}
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                if k.strip() in ("model name", "Model", "CPU part"):
+                    return v.strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def run_reference(args, rank, world):

@@ -95,6 +95,8 @@ def _load():
             lib.orc_objective.argtypes = [gp, dp, dp, dp]
             lib.orc_grad_w.argtypes = [gp, C.c_int, dp, dp, dp, dp, C.c_int, C.c_int]
             lib.orc_grad_wk.argtypes = [gp, C.c_int, C.c_int, dp, dp, dp, dp, C.c_int, C.c_int]
+            lib.orc_set_threads.argtypes = [C.c_int]
+            lib.orc_get_threads.restype = C.c_int
             lib.orc_svrg_estimate.argtypes = [gp, C.c_int, C.c_int, dp, dp, dp, dp, dp, C.c_int, C.c_int, dp]
             lib.orc_saga_estimate.argtypes = [gp, C.c_int, C.c_int, dp, dp, dp, dp, C.c_int, C.c_int, dp]
             lib.orc_power_iter_wk.argtypes = [gp, C.c_int, C.c_int, dp, C.c_int, C.c_double, ip]
@@ -290,6 +292,15 @@ def saga_estimate(g, s: int, y, psi, b, p: int, P: int, w=None, kind: int = 0) -
     _load().orc_saga_estimate(C.byref(geom(g)), s, int(kind), _dp(_f64(y)), _dp(psi), _dp(_f64(b)), _dp(ww),
                               p, P, _dp(out))
     return out
+
+
+def set_threads(n: int) -> int:
+    """Sets the OpenMP thread count of the oracle's parallel loops (timing only);
+    returns the previous count."""
+    lib = _load()
+    old = int(lib.orc_get_threads())
+    lib.orc_set_threads(int(n))
+    return old
 
 
 def objective(g, x, b, w=None):

@@ -42,6 +42,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef struct {
     int n, n_views, n_det, batch;
@@ -810,4 +813,23 @@ void orc_step_vjp(const orc_geom *g, int s, int p, int P, double eta, double alp
     orc_grad(g, s, zbar, zero, gr, p, P);
     for (size_t i = 0; i < N; ++i) ybar_in[i] = zbar[i] - eta * gr[i];
     free(gr); free(z); free(xt); free(dz); free(zbar); free(zero);
+}
+
+/* Threads of the OpenMP loops (timing only; results do not depend on it). */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int orc_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
