@@ -232,8 +232,11 @@ def cpu_model():
         with open("/proc/cpuinfo") as f:
             for line in f:
                 k, _, v = line.partition(":")
-                if k.strip() in ("model name", "Model", "CPU part"):
+                if k.strip() in ("model name", "Model"):
                     return v.strip()
+                if k.strip() == "CPU part":
+                    part = v.strip()
+                    return {"0xd4f": "Arm Neoverse V2"}.get(part, "Arm CPU part " + part)
     except OSError:
         pass
     import platform
