@@ -287,7 +287,8 @@ int pnp_run_many(const pnp_problem* problems, int n_problems, const pnp_run_para
  *   lanes   forward projector lanes per ray: 4, 8 or 16
  *   back    backprojector CTA: G view groups (1..32) of 8 x 4 pixel blocks, or
  *           PNP_BACK_TILE4 | G: G view groups (1..64) of 4 x 4 pixel blocks
- *   tile    side of the FGP tile (8..40)
+ *   tile    FGP denoiser: side of the shared-memory tile (8..40), or 1 for the
+ *           register-resident variant (warp tiles, five iterations per launch)
  * The backprojector's view groups fix its summation order: results are bitwise
  * reproducible for fixed shapes.  pnp_autotune sets them; pnp_set_launch_shapes
  * pins them (PNP_EINVAL for a shape outside these sets). */

@@ -119,7 +119,9 @@ Layout make_layout(const pnp_geom& g)
     L.off_tv = off; off = align_up(off + 8 * img * sizeof(float));
     L.off_pw = off; off = align_up(off + 2 * (size_t)g.n * g.n * sizeof(float));
     L.off_cs = off; off = align_up(off + 2 * (size_t)g.batch * (g.n / 2) * (g.n / 2) * sizeof(float));
-    const size_t tv_parts = (size_t)tile_tv_parts(g.n, g.batch);
+    // partials of the largest part count any denoiser shape may use (smallest tile 8, warp tiles)
+    const size_t tv_parts = std::max((size_t)tile_tv_parts_for(g.n, g.batch, 8),
+                                     (size_t)tile_tv_parts_for(g.n, g.batch, kTvTileWarp));
     const size_t parts = tv_parts > (size_t)kRedBlocks ? tv_parts : (size_t)kRedBlocks;
     L.off_red = off; off = align_up(off + ((size_t)g.batch * parts + (size_t)g.batch * 8) * sizeof(double));
     L.off_log = off; off = align_up(off + (size_t)PNP_MAX_LOG_ITERS * sizeof(double));
@@ -129,7 +131,8 @@ Layout make_layout(const pnp_geom& g)
 
 inline size_t red_parts(const pnp_geom& g)
 {
-    const size_t tv_parts = (size_t)tile_tv_parts(g.n, g.batch);
+    const size_t tv_parts = std::max((size_t)tile_tv_parts_for(g.n, g.batch, 8),
+                                     (size_t)tile_tv_parts_for(g.n, g.batch, kTvTileWarp));
     return tv_parts > (size_t)kRedBlocks ? tv_parts : (size_t)kRedBlocks;
 }
 
@@ -896,6 +899,14 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
                 return fail(PNP_EINVAL, "problems %d and %d share a workspace or an output", c, d);
     cudaStream_t st = S(stream);
     const bool do_tv = pr.tv_iters > 0 && pr.lambda > 0.0f;
+    // one denoiser launch covers every class, so the classes share its variant:
+    // the register-resident one only when every class was tuned to it
+    bool all_warp = true;
+    for (int c = 0; c < np; ++c) all_warp = all_warp && ps[c].tuned.tile == kTvTileWarp;
+    for (int c = 0; c < np; ++c) {
+        if (!all_warp && ps[c].tuned.tile == kTvTileWarp) ps[c].tuned.tile = 0;
+        if (do_tv) ps[c].tv_parts = tile_tv_parts_for(pb[c].geom.n, pb[c].geom.batch, ps[c].tuned.tile);
+    }
     long max_total = 0;
     for (const auto& q : ps) max_total = std::max(max_total, q.total);
     const bool one = np == 1;
@@ -1214,8 +1225,8 @@ int pnp_autotune(const pnp_geom* g, const pnp_stage* stages, int n_stages, const
         const int T0 = tile_tv_tile(g->n, g->batch);
         float best = 1e30f;
         const int iters = std::min(pr.tv_iters, 10);
-        for (int T : {T0 - 6, T0 - 4, T0 - 2, T0, T0 + 2, T0 + 4, T0 + 6, 16, 24, 32}) {
-            if (T < 8 || T > 40) continue;
+        for (int T : {T0 - 6, T0 - 4, T0 - 2, T0, T0 + 2, T0 + 4, T0 + 6, 16, 24, 32, kTvTileWarp}) {
+            if (T != kTvTileWarp && (T < 8 || T > 40)) continue;
             float ms = 0.0f;
             rc = timeit([&]() -> int {
                 PNP_CUDA(launch_tv_tiled(y, g->n, g->batch, pr.lambda, iters, 1.0f, 0.0f, z, nullptr, nullptr,
@@ -1265,8 +1276,8 @@ int pnp_set_launch_shapes(const pnp_geom* g, const pnp_launch_shapes* in, void* 
         tu.lanes[k] = q;
         tu.groups[k] = b;
     }
-    if (in->tile != 0 && (in->tile < 8 || in->tile > 40))
-        return fail(PNP_EINVAL, "tile %d outside [8, 40]", in->tile);
+    if (in->tile != 0 && in->tile != kTvTileWarp && (in->tile < 8 || in->tile > 40))
+        return fail(PNP_EINVAL, "tile %d is neither 0, 1 nor in [8, 40]", in->tile);
     tu.tile = in->tile;
     reg_set_tuned(d_ws, tu);
     return PNP_OK;

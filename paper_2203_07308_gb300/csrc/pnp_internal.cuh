@@ -173,10 +173,13 @@ int tile_tv_parts(int n, int batch);
 cudaError_t launch_tv_tiled(const float* z, int n, int batch, float lambda, int iters, float alpha,
                             float amom, float* xprev, float* y, const float* xtrue, double* mse_part,
                             float* state_a, float* state_b, cudaStream_t st, int tile = 0);
+// TvItem::tile: 0 = cost model, 8..40 = shared-memory tiles of that side,
+// kTvTileWarp = register-resident warp tiles (the first item decides the variant).
+constexpr int kTvTileWarp = 1;
 struct TvItem {
     const float* z; float* xprev; float* y; const float* xtrue; double* mse_part;
     float* state_a; float* state_b;        // [4][batch][n][n] each (chained launches only)
-    int n, batch, tile;                    // tile 0 = cost model
+    int n, batch, tile;
     float amom;
 };
 cudaError_t launch_tv_tiled_multi(const TvItem* items, int count, float lambda, int iters, float alpha,

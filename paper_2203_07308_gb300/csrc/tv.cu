@@ -266,6 +266,152 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
     }
 }
 
+// ------------------------------------------------------------------ register-resident FGP
+// The same K-iteration temporal blocking with no shared memory and no barrier:
+// a warp owns a tile of kWarpTvWV x kWarpTvHV output pixels; lane l holds one
+// column of the loaded region (the tile grown by K + 1 above/left and K
+// below/right) in registers, kWarpTvH rows deep.  Vertical neighbours are the
+// lane's own registers, horizontal ones come from the adjacent lanes by warp
+// shuffles; values outside the shrinking valid region are computed but never
+// reach the output, exactly as in the shared-memory tiles.
+constexpr int kWarpTvK = 5;                                  // FGP iterations per launch
+constexpr int kWarpTvHV = 10;                                // output rows per warp tile
+constexpr int kWarpTvH = kWarpTvHV + 2 * kWarpTvK + 1;       // rows held per lane
+constexpr int kWarpTvWV = 31 - 2 * kWarpTvK;                 // output columns per warp tile
+constexpr int kWarpTvWarps = 1;                              // warp tiles per CTA
+
+struct WarpTvClass {
+    const float* z; const float* sin; float* sout;          // state planes [4][batch][n][n]: r1 r2 p1 p2
+    float* xprev; float* y; const float* xtrue; double* mse_part;
+    int n, tiles_x, tiles;
+    long plane;
+    float amom;
+};
+
+struct WarpTvArgs {
+    WarpTvClass c[kMaxClasses];
+    long begin[kMaxClasses + 1];                             // cumulative warp tiles (batch * tiles)
+    int count, K, first, last;
+    float lambda, alpha;
+    float mom[kWarpTvK];
+};
+
+__global__ void __launch_bounds__(32 * kWarpTvWarps) k_tv_warp(const WarpTvArgs t)
+{
+    pdl_begin();
+    constexpr int H = kWarpTvH;
+    constexpr unsigned kAll = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long wt = (long)blockIdx.x * kWarpTvWarps + (threadIdx.x >> 5);
+    if (wt >= t.begin[t.count]) return;                      // whole warps only
+    int cls = 0;
+#pragma unroll
+    for (int k = 1; k < kMaxClasses; ++k)
+        if (k < t.count && wt >= t.begin[k]) cls = k;
+    const WarpTvClass& a = t.c[cls];
+    const long local = wt - t.begin[cls];
+    const int inst = (int)(local / a.tiles);
+    const int tile = (int)(local - (long)inst * a.tiles);
+    const int n = a.n;
+    const int r0 = (tile / a.tiles_x) * kWarpTvHV, c0 = (tile % a.tiles_x) * kWarpTvWV;
+    const int j = c0 - kWarpTvK - 1 + lane;                  // this lane's column
+    const int ib = r0 - kWarpTvK - 1;                        // row of register m = 0
+    const bool jin = j >= 0 && j < n, jpos = j > 0, jlast = j < n - 1;
+    const long img = (long)inst * n * n;
+    float z[H], r1[H], r2[H], p1[H], p2[H];
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+        const int i = ib + m;
+        const bool in = jin && i >= 0 && i < n;
+        const long g = img + (long)i * n + j;
+        z[m] = in ? __ldg(a.z + g) : 0.0f;
+        r1[m] = r2[m] = p1[m] = p2[m] = 0.0f;
+        if (in && !t.first) {
+            r1[m] = __ldg(a.sin + g);
+            r2[m] = __ldg(a.sin + a.plane + g);
+            p1[m] = __ldg(a.sin + 2 * a.plane + g);
+            p2[m] = __ldg(a.sin + 3 * a.plane + g);
+        }
+    }
+    const float lam = t.lambda, inv8l = 1.0f / (8.0f * t.lambda);
+    for (int k = 0; k < t.K; ++k) {
+        const float mo = t.mom[k];
+        float xt[H];
+        // x_tmp = z - lambda L(r)
+#pragma unroll
+        for (int m = 0; m < H; ++m) {
+            const float left = __shfl_up_sync(kAll, r2[m], 1);
+            float l = r1[m] + r2[m];
+            if (m > 0 && ib + m > 0) l -= r1[m - 1];
+            if (jpos) l -= left;
+            xt[m] = z[m] - lam * l;
+        }
+        // dual step, isotropic projection, momentum
+#pragma unroll
+        for (int m = 0; m < H; ++m) {
+            const float right = __shfl_down_sync(kAll, xt[m], 1);
+            const float g1 = (m + 1 < H && ib + m < n - 1) ? xt[m] - xt[m + 1 < H ? m + 1 : m] : 0.0f;
+            const float g2 = jlast ? xt[m] - right : 0.0f;
+            float pa = fmaf(g1, inv8l, r1[m]);
+            float pc = fmaf(g2, inv8l, r2[m]);
+            const float nrm2 = fmaf(pa, pa, pc * pc);
+            if (nrm2 > 1.0f) {
+                const float sc = rsqrtf(nrm2);
+                pa *= sc;
+                pc *= sc;
+            }
+            r1[m] = fmaf(mo, pa - p1[m], pa);
+            r2[m] = fmaf(mo, pc - p2[m], pc);
+            p1[m] = pa;
+            p2[m] = pc;
+        }
+    }
+    // the tile's output pixels: registers [K + 1, K + 1 + HV), lanes [K + 1, K + 1 + WV)
+    const bool lane_out = lane >= kWarpTvK + 1 && lane < kWarpTvK + 1 + kWarpTvWV && jin;
+    if (!t.last) {
+#pragma unroll
+        for (int m = kWarpTvK + 1; m < kWarpTvK + 1 + kWarpTvHV; ++m) {
+            const int i = ib + m;
+            if (lane_out && i < n) {
+                const long g = img + (long)i * n + j;
+                a.sout[g] = r1[m];
+                a.sout[a.plane + g] = r2[m];
+                a.sout[2 * a.plane + g] = p1[m];
+                a.sout[3 * a.plane + g] = p2[m];
+            }
+        }
+        return;
+    }
+    // x = z - lambda L(p) on the tile, relaxation, momentum, squared error
+    double e2 = 0.0;
+#pragma unroll
+    for (int m = kWarpTvK + 1; m < kWarpTvK + 1 + kWarpTvHV; ++m) {
+        const float left = __shfl_up_sync(kAll, p2[m], 1);
+        const int i = ib + m;
+        if (lane_out && i < n) {
+            float l = p1[m] + p2[m];
+            if (i > 0) l -= p1[m - 1];
+            if (jpos) l -= left;
+            const float x = z[m] - lam * l;
+            const float xi = (1.0f - t.alpha) * z[m] + t.alpha * x;
+            const long g = img + (long)i * n + j;
+            if (a.y) {
+                const float xp = a.xprev[g];
+                a.y[g] = xi + a.amom * (xi - xp);
+            }
+            a.xprev[g] = xi;
+            if (a.xtrue) {
+                const double d = (double)xi - (double)__ldg(a.xtrue + g);
+                e2 += d * d;
+            }
+        }
+    }
+    if (a.mse_part) {
+        for (int off = 16; off > 0; off >>= 1) e2 += __shfl_xor_sync(kAll, e2, off);
+        if (lane == 0) a.mse_part[(long)inst * a.tiles + tile] = e2;
+    }
+}
+
 inline cudaError_t counted(cudaError_t e = cudaGetLastError())
 {
     g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -333,9 +479,56 @@ int tile_tv_tile(int n, int batch) { return choose_tile(n, batch); }
 
 int tile_tv_parts_for(int n, int batch, int tile)
 {
+    if (tile == kTvTileWarp)
+        return ((n + kWarpTvWV - 1) / kWarpTvWV) * ((n + kWarpTvHV - 1) / kWarpTvHV);
     const int T = tile > 0 ? tile : tile_tv_tile(n, batch);
     return ((n + T - 1) / T) * ((n + T - 1) / T);
 }
+
+namespace {
+// Register-resident variant: warp tiles of kWarpTvWV x kWarpTvHV, kWarpTvK iterations per launch.
+cudaError_t launch_tv_warp_multi(const TvItem* items, int count, float lambda, int iters, float alpha,
+                                 const std::vector<float>& mom, cudaStream_t st)
+{
+    WarpTvArgs a{};
+    a.count = count;
+    a.lambda = lambda;
+    a.alpha = alpha;
+    a.begin[0] = 0;
+    for (int c = 0; c < count; ++c) {
+        const TvItem& it = items[c];
+        if (iters > kWarpTvK && (!it.state_a || !it.state_b)) return cudaErrorInvalidValue;
+        WarpTvClass& wc = a.c[c];
+        wc.z = it.z; wc.xprev = it.xprev; wc.y = it.y; wc.xtrue = it.xtrue; wc.mse_part = it.mse_part;
+        wc.n = it.n;
+        wc.tiles_x = (it.n + kWarpTvWV - 1) / kWarpTvWV;
+        wc.tiles = wc.tiles_x * ((it.n + kWarpTvHV - 1) / kWarpTvHV);
+        wc.plane = (long)it.batch * it.n * it.n;
+        wc.amom = it.amom;
+        a.begin[c + 1] = a.begin[c] + (long)wc.tiles * it.batch;
+    }
+    const dim3 grd((unsigned)((a.begin[count] + kWarpTvWarps - 1) / kWarpTvWarps)), blk(32 * kWarpTvWarps);
+    int k0 = 0, pass = 0;
+    cudaError_t e = cudaSuccess;
+    do {
+        const int K = std::min(kWarpTvK, iters - k0);
+        a.K = K;
+        a.first = k0 == 0;
+        a.last = k0 + K == iters;
+        for (int c = 0; c < count; ++c) {
+            a.c[c].sin = k0 == 0 ? nullptr : (pass % 2 == 1 ? items[c].state_a : items[c].state_b);
+            a.c[c].sout = a.last ? nullptr : (pass % 2 == 0 ? items[c].state_a : items[c].state_b);
+        }
+        for (int k = 0; k < K; ++k) a.mom[k] = mom[k0 + k];
+        e = launch_pdl(k_tv_warp, grd, blk, 0, st, a);
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        if (e != cudaSuccess) return e;
+        k0 += K;
+        ++pass;
+    } while (k0 < iters);
+    return e;
+}
+}  // namespace
 
 int tile_tv_parts(int n, int batch) { return tile_tv_parts_for(n, batch, 0); }
 
@@ -358,6 +551,7 @@ cudaError_t launch_tv_tiled_multi(const TvItem* items, int count, float lambda, 
         mom[k] = (float)((tt - 1.0) / tn);
         tt = tn;
     }
+    if (items[0].tile == kTvTileWarp) return launch_tv_warp_multi(items, count, lambda, iters, alpha, mom, st);
     TileTvArgs a{};
     a.count = count;
     a.lambda = lambda;
@@ -366,7 +560,7 @@ cudaError_t launch_tv_tiled_multi(const TvItem* items, int count, float lambda, 
     int Tmax = 0;
     for (int c = 0; c < count; ++c) {
         const TvItem& it = items[c];
-        int T = it.tile > 0 ? it.tile : tile_tv_tile(it.n, it.batch);
+        int T = it.tile >= 4 ? it.tile : tile_tv_tile(it.n, it.batch);
         if (T < 4 || T > 64 || tile_np(T, kTileKMax) > 4 || tile_smem(T, kTileKMax) > kTileSmemMax)
             T = tile_tv_tile(it.n, it.batch);
         if (iters > kTileKMax && (!it.state_a || !it.state_b)) return cudaErrorInvalidValue;   // chaining needs state

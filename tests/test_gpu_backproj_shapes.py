@@ -146,7 +146,7 @@ def test_launch_shapes_validation():
     assert plan.launch_shapes() == {"lanes": [0] * 4, "back": [0] * 4, "tile": 0}
     for bad in (dict(back=(33, 0, 0, 0)), dict(back=(T4 | 65, 0, 0, 0)), dict(back=(T4, 0, 0, 0)),
                 dict(back=(-1, 0, 0, 0)), dict(back=(1 << 9 | 4, 0, 0, 0)), dict(lanes=(2, 0, 0, 0)),
-                dict(tile=50)):
+                dict(tile=50), dict(tile=2), dict(tile=7)):
         with pytest.raises(pnp.PnpError):
             plan.set_launch_shapes(**bad)
     plan.set_launch_shapes(lanes=(8, 4, 0, 0), back=(16, T4 | 45, 3, 0), tile=24)
