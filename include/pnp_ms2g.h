@@ -162,7 +162,8 @@ int pnp_setup(const pnp_geom* g, void* d_ws, size_t ws_bytes, void* stream);
 
 /* Weighted least squares.  Sec. 3 simulates transmission data b ~ Poisson(I0
  * exp(-A x)) and takes the logarithm; the matching data fidelity is
- * f = 1/2 sum_j w_j ((A x)_j - b_j)^2 with w_j the measured counts.  After this
+ * f = 1/2 sum_j w_j ((A x)_j - b_j)^2 with w_j the inverse variance of b_j
+ * (proportional to the measured counts for log transmission data).  After this
  * call every gradient, step size (power iteration; instance 0's weights) and
  * objective computed with d_ws uses the weights d_w [batch][n_views][n_det]
  * (the caller keeps them alive); pnp_project stays unweighted.  NULL returns to
@@ -264,7 +265,10 @@ int pnp_set_vr_buffer(const pnp_geom* g, void* d_buf, size_t bytes, void* d_ws);
  *                      the call then synchronises `stream` before returning
  * Iteration i: v = S_k y_{i-1}; r = A_s^{(p_i)} v - b^{(p_i)};
  *   z = y_{i-1} - eta_k c S_k^T A_s^{(p_i)T} r;  x_i = (1-alpha) z + alpha D(z);
- *   y_i = x_i + a_i (x_i - x_{i-1}). */
+ *   y_i = x_i + a_i (x_i - x_{i-1}).
+ * S_k and U_k = S_k^T follow the stage's sketch kind; with an SVRG or SAGA
+ * stage the gradient term is that estimator's (see PNP_EST_*), which needs an
+ * estimator buffer (pnp_set_vr_buffer; PNP_ESTATE without one). */
 int pnp_run(const pnp_geom* g, const pnp_stage* stages, int n_stages, const double* h_eta,
             const int32_t* h_subset_seq, const pnp_run_params* params, const float* d_b,
             float* d_x, const float* d_xtrue, double* h_psnr_log, void* d_ws, void* stream);
