@@ -409,6 +409,35 @@ def batched_512x16(dev, stream):
             "speedup": (tts_f / tts_s) if (tts_s and tts_f) else None}
 
 
+def gray_by_config(dev, stream):
+    """All-view forward and backprojection throughput (GRay-samples/s: exact
+    sample count / device time) for every workload size, one launch each with
+    launch shapes from the autotuner."""
+    import torch
+    import paper_2203_07308_gb300 as pnp
+    from paper_2203_07308_gb300 import synth
+    wls = synth.workloads()
+    cases = [("64x64, 90 x 96", wls["c1_64"].geom), ("256x256, 360 x 512", wls["c2_256"].geom),
+             ("16 x 512x512, 720 x 768", wls["c3_512x16"].geom),
+             ("128x128, 180 x 256", synth.make_geometry(128, 180, 256))]
+    out = {}
+    for name, g in cases:
+        plan = pnp.Plan(g)
+        plan.autotune([synth.Stage(1, 1, 1)])
+        img = torch.rand(g.batch, g.n, g.n, device=dev)
+        sino = torch.empty(g.batch, g.n_views, g.n_det, device=dev)
+        back = torch.empty_like(img)
+        samples = plan.sample_count(1) * g.batch
+        plan.project(1, img, sino)
+        plan.backproject(1, sino, back)
+        f_ms = _device_ms(lambda: plan.project(1, img, sino), stream)
+        b_ms = _device_ms(lambda: plan.backproject(1, sino, back), stream)
+        out[name] = {"samples": samples, "forward_ms": f_ms, "backproject_ms": b_ms,
+                     "forward_gsamples_per_s": samples / (f_ms / 1000) / 1e9,
+                     "backproject_gsamples_per_s": samples / (b_ms / 1000) / 1e9}
+    return out
+
+
 def mixed_64(dev, stream):
     """64 instances of 128^2/180/256, 256^2/360/512 and 512^2/720/768 (seeded mix)
     in one call: every phase of every iteration one launch over the three
@@ -639,7 +668,8 @@ def run_native(args, rank, world):
     extras = {}
     if not args.no_extras:
         extras = {"batched_512x16": batched_512x16(dev, stream), "mixed_64": mixed_64(dev, stream),
-                  "differentiable_256x8": differentiable_256x8(dev, stream)}
+                  "differentiable_256x8": differentiable_256x8(dev, stream),
+                  "gray_by_config": gray_by_config(dev, stream)}
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     h_b = torch.empty(d_b.shape, dtype=torch.float32, pin_memory=True)
