@@ -373,6 +373,22 @@ int pnp_unrolled_step_vjp(const pnp_geom* g, int factor, int subset, int n_subse
                           const float* d_xbar, const float* d_ybar, float* d_ybar_in, float* d_xpbar,
                           double* h_lambar, void* d_ws, void* d_vjp_ws, size_t vjp_ws_bytes, void* stream);
 
+/* pnp_unrolled_step that also stores z = y - eta c S^T A_s^{(p)T}(...) into
+ * d_zout [batch][n][n] (may not alias the other arguments), so that the VJP can
+ * start from it instead of recomputing the gradient step. */
+int pnp_unrolled_step_save(const pnp_geom* g, int factor, int subset, int n_subsets, double eta,
+                           const pnp_run_params* params, float amom, const float* d_y, const float* d_xprev,
+                           const float* d_b, float* d_xout, float* d_yout, float* d_zout, void* d_ws,
+                           void* stream);
+
+/* pnp_unrolled_step_vjp from the z that pnp_unrolled_step_save stored (d_z)
+ * instead of recomputing it from y: one projector pair fewer per iteration. */
+int pnp_unrolled_step_vjp_saved(const pnp_geom* g, int factor, int subset, int n_subsets, double eta,
+                                const pnp_run_params* params, float amom, const float* d_z,
+                                const float* d_xbar, const float* d_ybar, float* d_ybar_in, float* d_xpbar,
+                                double* h_lambar, void* d_ws, void* d_vjp_ws, size_t vjp_ws_bytes,
+                                void* stream);
+
 /* Bytes of scratch inside the library for pnp_full_grad_noalloc (per GPU that
  * loads the library, held until the process exits). */
 #define PNP_NOALLOC_SCRATCH_BYTES (32u << 20)

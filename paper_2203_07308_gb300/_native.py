@@ -132,6 +132,10 @@ def load(path: Optional[str] = None):
                                   vp, vp, vp, vp, vp, vp, vp],
             "pnp_unrolled_step_vjp": [gp, i32, i32, i32, C.c_double, C.POINTER(RunParams), C.c_float,
                                       vp, vp, vp, vp, vp, vp, dp, vp, vp, sz, vp],
+            "pnp_unrolled_step_save": [gp, i32, i32, i32, C.c_double, C.POINTER(RunParams), C.c_float,
+                                       vp, vp, vp, vp, vp, vp, vp, vp],
+            "pnp_unrolled_step_vjp_saved": [gp, i32, i32, i32, C.c_double, C.POINTER(RunParams), C.c_float,
+                                            vp, vp, vp, vp, vp, dp, vp, vp, sz, vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -460,6 +464,34 @@ def unrolled_step(g, factor, subset, n_subsets, eta, alpha, lam, tv_iters, amom,
                                     float(amom), _ptr(y, img, "y"), _ptr(xprev, img, "xprev"),
                                     _ptr(b, g.batch * g.n_views * g.n_det, "b"), _ptr(xout, img, "xout"),
                                     _ptr(yout, img, "yout"), _ws(ws)[0], _stream(stream)))
+
+
+def unrolled_step_save(g, factor, subset, n_subsets, eta, alpha, lam, tv_iters, amom, y, xprev, b, xout, yout,
+                       zout, ws, stream=None):
+    """unrolled_step that also stores the gradient step z into zout."""
+    img = g.batch * g.n * g.n
+    prm = RunParams(float(alpha), float(lam), int(tv_iters), 0, 0)
+    _check(load().pnp_unrolled_step_save(C.byref(geom(g)), factor, subset, n_subsets, float(eta), C.byref(prm),
+                                         float(amom), _ptr(y, img, "y"), _ptr(xprev, img, "xprev"),
+                                         _ptr(b, g.batch * g.n_views * g.n_det, "b"), _ptr(xout, img, "xout"),
+                                         _ptr(yout, img, "yout"), _ptr(zout, img, "zout"), _ws(ws)[0],
+                                         _stream(stream)))
+
+
+def unrolled_step_vjp_saved(g, factor, subset, n_subsets, eta, alpha, lam, tv_iters, amom, z, xbar, ybar,
+                            ybar_in, xpbar, ws, vjp_ws, stream=None):
+    """unrolled_step_vjp from the stored z; returns dJ/dlambda per instance."""
+    img = g.batch * g.n * g.n
+    prm = RunParams(float(alpha), float(lam), int(tv_iters), 0, 0)
+    lb = np.zeros(g.batch)
+    vp, vbytes = _ws(vjp_ws)
+    _check(load().pnp_unrolled_step_vjp_saved(C.byref(geom(g)), factor, subset, n_subsets, float(eta),
+                                              C.byref(prm), float(amom), _ptr(z, img, "z"),
+                                              _ptr(xbar, img, "xbar"), _ptr(ybar, img, "ybar"),
+                                              _ptr(ybar_in, img, "ybar_in"), _ptr(xpbar, img, "xpbar"),
+                                              lb.ctypes.data_as(C.POINTER(C.c_double)), _ws(ws)[0], vp, vbytes,
+                                              _stream(stream)))
+    return lb
 
 
 def unrolled_step_vjp(g, factor, subset, n_subsets, eta, alpha, lam, tv_iters, amom, y, b, xbar, ybar,

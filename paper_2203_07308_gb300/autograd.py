@@ -3,10 +3,12 @@
 Sec. 2 of the paper notes that the sketched iterations can be unrolled and
 trained end to end.  ``UnrolledStep`` is one iteration of Algorithm 1 as an
 autograd Function of (y_{i-1}, x_{i-1}, lambda): its forward is
-``pnp_unrolled_step`` and its backward ``pnp_unrolled_step_vjp``, which
-recomputes the iteration's forward pass from the saved input y_{i-1}.  So an
-unrolled run keeps one image per iteration (per-iteration checkpointing) and
-every numerical step, forward and backward, runs in the CUDA kernels.
+``pnp_unrolled_step_save`` (or ``pnp_unrolled_step``) and its backward
+``pnp_unrolled_step_vjp_saved``, which starts from the iteration's stored
+gradient step z (or ``pnp_unrolled_step_vjp``, which recomputes it from the
+saved input y_{i-1}).  So an unrolled run keeps one image per iteration
+(per-iteration checkpointing) and every numerical step, forward and backward,
+runs in the CUDA kernels.
 The data b is a constant of the unrolled map.
 """
 from __future__ import annotations
@@ -20,37 +22,51 @@ from . import _native
 
 class UnrolledStep(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, y, xprev, lam, plan, b, factor, subset, n_subsets, eta, alpha, tv_iters, amom, vjp_ws):
+    def forward(ctx, y, xprev, lam, plan, b, factor, subset, n_subsets, eta, alpha, tv_iters, amom, vjp_ws,
+                keep_z=True):
         g = plan.g
         xout = torch.empty_like(y)
         yout = torch.empty_like(y)
-        _native.unrolled_step(g, factor, subset, n_subsets, eta, alpha, float(lam), tv_iters, amom,
-                              y.contiguous(), xprev.contiguous(), b, xout, yout, plan.ws)
-        ctx.save_for_backward(y)
+        if keep_z:      # keep the gradient step z too: the backward then skips one projector pair
+            z = torch.empty_like(y)
+            _native.unrolled_step_save(g, factor, subset, n_subsets, eta, alpha, float(lam), tv_iters, amom,
+                                       y.contiguous(), xprev.contiguous(), b, xout, yout, z, plan.ws)
+            ctx.save_for_backward(z)
+        else:           # keep y only and recompute z in the backward
+            _native.unrolled_step(g, factor, subset, n_subsets, eta, alpha, float(lam), tv_iters, amom,
+                                  y.contiguous(), xprev.contiguous(), b, xout, yout, plan.ws)
+            ctx.save_for_backward(y)
+        ctx.keep_z = keep_z
         ctx.args = (plan, b, factor, subset, n_subsets, eta, alpha, float(lam), tv_iters, amom, vjp_ws)
         ctx.lam_meta = (lam.dtype, lam.device) if torch.is_tensor(lam) else None
         return xout, yout
 
     @staticmethod
     def backward(ctx, xbar, ybar):
-        (y,) = ctx.saved_tensors
+        (saved,) = ctx.saved_tensors
         plan, b, factor, subset, n_subsets, eta, alpha, lam, tv_iters, amom, vjp_ws = ctx.args
-        xbar = torch.zeros_like(y) if xbar is None else xbar.contiguous()
-        ybar = torch.zeros_like(y) if ybar is None else ybar.contiguous()
-        ybar_in = torch.empty_like(y)
-        xpbar = torch.empty_like(y)
-        lb = _native.unrolled_step_vjp(plan.g, factor, subset, n_subsets, eta, alpha, lam, tv_iters, amom,
-                                       y.contiguous(), b, xbar, ybar, ybar_in, xpbar, plan.ws, vjp_ws)
+        xbar = torch.zeros_like(saved) if xbar is None else xbar.contiguous()
+        ybar = torch.zeros_like(saved) if ybar is None else ybar.contiguous()
+        ybar_in = torch.empty_like(saved)
+        xpbar = torch.empty_like(saved)
+        if ctx.keep_z:
+            lb = _native.unrolled_step_vjp_saved(plan.g, factor, subset, n_subsets, eta, alpha, lam, tv_iters,
+                                                 amom, saved, xbar, ybar, ybar_in, xpbar, plan.ws, vjp_ws)
+        else:
+            lb = _native.unrolled_step_vjp(plan.g, factor, subset, n_subsets, eta, alpha, lam, tv_iters, amom,
+                                           saved.contiguous(), b, xbar, ybar, ybar_in, xpbar, plan.ws, vjp_ws)
         lam_grad = None
         if ctx.lam_meta is not None:
             lam_grad = torch.tensor(float(lb.sum()), dtype=ctx.lam_meta[0], device=ctx.lam_meta[1])
-        return (ybar_in, xpbar, lam_grad) + (None,) * 10
+        return (ybar_in, xpbar, lam_grad) + (None,) * 11
 
 
 def unrolled_pnp(plan, stages: Sequence, eta: Sequence[float], seq, b, x0, lam, *, alpha: float = 1.0,
-                 tv_iters: int = 20, momentum: bool = True):
+                 tv_iters: int = 20, momentum: bool = True, keep_z: bool = True):
     """x_T of Algorithm 1 as a differentiable function of x0 (float32 CUDA
-    tensor [batch, n, n]) and lam (a float64 scalar tensor, may require grad)."""
+    tensor [batch, n, n]) and lam (a float64 scalar tensor, may require grad).
+    keep_z: keep each iteration's gradient step z for the backward pass (one
+    projector pair fewer per iteration); False keeps only y and recomputes z."""
     g = plan.g
     vjp_ws = torch.empty(_native.vjp_workspace_size(g, tv_iters), dtype=torch.uint8, device=x0.device)
     y = x0
@@ -62,5 +78,6 @@ def unrolled_pnp(plan, stages: Sequence, eta: Sequence[float], seq, b, x0, lam, 
             i += 1
             p = int(seq[i - 1]) if P > 1 else 0
             a = (i - 1) / (i + 3) if momentum else 0.0
-            x, y = UnrolledStep.apply(y, x, lam, plan, b, f, p, P, float(eta[k]), alpha, tv_iters, a, vjp_ws)
+            x, y = UnrolledStep.apply(y, x, lam, plan, b, f, p, P, float(eta[k]), alpha, tv_iters, a, vjp_ws,
+                                      keep_z)
     return x

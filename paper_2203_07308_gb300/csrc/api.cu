@@ -1427,9 +1427,11 @@ int check_step(const pnp_geom* g, int factor, int subset, int n_subsets, double 
 }
 }  // namespace
 
-int pnp_unrolled_step(const pnp_geom* g, int factor, int subset, int n_subsets, double eta,
-                      const pnp_run_params* params, float amom, const float* d_y, const float* d_xprev,
-                      const float* d_b, float* d_xout, float* d_yout, void* d_ws, void* stream)
+namespace {
+// One unrolled iteration; z (the gradient step) is also copied to d_zout when given.
+int unrolled_step_impl(const pnp_geom* g, int factor, int subset, int n_subsets, double eta,
+                       const pnp_run_params* params, float amom, const float* d_y, const float* d_xprev,
+                       const float* d_b, float* d_xout, float* d_yout, float* d_zout, void* d_ws, void* stream)
 {
     t_err.clear();
     Layout L;
@@ -1438,6 +1440,8 @@ int pnp_unrolled_step(const pnp_geom* g, int factor, int subset, int n_subsets, 
     if (!d_y || !d_xprev || !d_b || !d_xout || !d_yout) return fail(PNP_EINVAL, "y, xprev, b, xout, yout required");
     if (d_xout == d_y || d_yout == d_y || d_xout == d_yout || d_xout == d_xprev)
         return fail(PNP_EINVAL, "outputs must not alias the inputs or each other");
+    if (d_zout && (d_zout == d_y || d_zout == d_xprev || d_zout == d_xout || d_zout == d_yout))
+        return fail(PNP_EINVAL, "z output must not alias the other arguments");
     if (int e = check_ws(*g, d_ws)) return e;
     char* ws = (char*)d_ws;
     cudaStream_t st = S(stream);
@@ -1445,6 +1449,7 @@ int pnp_unrolled_step(const pnp_geom* g, int factor, int subset, int n_subsets, 
     float* z = (float*)(ws + L.off_z);
     float* tvb = (float*)(ws + L.off_tv);
     if (int e = grad_into(*g, L, li, ws, d_y, d_b, subset, n_subsets, kBackStep, (float)eta, z, st)) return e;
+    if (d_zout) PNP_CUDA(launch_copy(z, d_zout, img, st));
     PNP_CUDA(launch_copy(d_xprev, d_xout, img, st));
     const pnp_run_params& pr = *params;
     if (pr.tv_iters > 0 && pr.lambda > 0.0f)
@@ -1456,17 +1461,19 @@ int pnp_unrolled_step(const pnp_geom* g, int factor, int subset, int n_subsets, 
     return PNP_OK;
 }
 
-int pnp_unrolled_step_vjp(const pnp_geom* g, int factor, int subset, int n_subsets, double eta,
-                          const pnp_run_params* params, float amom, const float* d_y, const float* d_b,
-                          const float* d_xbar, const float* d_ybar, float* d_ybar_in, float* d_xpbar,
-                          double* h_lambar, void* d_ws, void* d_vjp_ws, size_t vjp_ws_bytes, void* stream)
+// VJP of one unrolled iteration; z is recomputed from d_y, or taken from d_zsaved.
+int unrolled_step_vjp_impl(const pnp_geom* g, int factor, int subset, int n_subsets, double eta,
+                           const pnp_run_params* params, float amom, const float* d_y, const float* d_b,
+                           const float* d_zsaved, const float* d_xbar, const float* d_ybar, float* d_ybar_in,
+                           float* d_xpbar, double* h_lambar, void* d_ws, void* d_vjp_ws, size_t vjp_ws_bytes,
+                           void* stream)
 {
     t_err.clear();
     Layout L;
     int li;
     if (int e = check_step(g, factor, subset, n_subsets, eta, params, &L, &li)) return e;
-    if (!d_y || !d_b || !d_xbar || !d_ybar || !d_ybar_in || !d_xpbar)
-        return fail(PNP_EINVAL, "y, b, xbar, ybar, ybar_in, xpbar required");
+    if (!(d_zsaved || (d_y && d_b)) || !d_xbar || !d_ybar || !d_ybar_in || !d_xpbar)
+        return fail(PNP_EINVAL, "z (or y and b), xbar, ybar, ybar_in, xpbar required");
     if (d_ybar_in == d_xpbar) return fail(PNP_EINVAL, "outputs must not alias");
     const pnp_run_params& pr = *params;
     const bool do_tv = pr.tv_iters > 0 && pr.lambda > 0.0f;
@@ -1484,9 +1491,12 @@ int pnp_unrolled_step_vjp(const pnp_geom* g, int factor, int subset, int n_subse
     float* DZ = (float*)((char*)X + align_up(img * sizeof(float)));
     float* ZB = (float*)((char*)DZ + align_up(img * sizeof(float)));
     double* dres = (double*)(vws + tvb_bytes) - g->batch;
-    float* z = (float*)(ws + L.off_z);
-    // forward recomputation of z (per-iteration checkpoint: only y is kept)
-    if (int e = grad_into(*g, L, li, ws, d_y, d_b, subset, n_subsets, kBackStep, (float)eta, z, st)) return e;
+    const float* z = d_zsaved;
+    if (!z) {   // forward recomputation of z (per-iteration checkpoint: only y is kept)
+        float* zw = (float*)(ws + L.off_z);
+        if (int e = grad_into(*g, L, li, ws, d_y, d_b, subset, n_subsets, kBackStep, (float)eta, zw, st)) return e;
+        z = zw;
+    }
     // through y_i = (1 + a) x_i - a x_{i-1}
     PNP_CUDA(launch_axpby(d_xbar, 1.0f, d_ybar, 1.0f + amom, X, (long)img, st));
     PNP_CUDA(launch_axpby(d_ybar, -amom, nullptr, 0.0f, d_xpbar, (long)img, st));
@@ -1511,6 +1521,46 @@ int pnp_unrolled_step_vjp(const pnp_geom* g, int factor, int subset, int n_subse
         }
     }
     return PNP_OK;
+}
+}  // namespace
+
+int pnp_unrolled_step(const pnp_geom* g, int factor, int subset, int n_subsets, double eta,
+                      const pnp_run_params* params, float amom, const float* d_y, const float* d_xprev,
+                      const float* d_b, float* d_xout, float* d_yout, void* d_ws, void* stream)
+{
+    return unrolled_step_impl(g, factor, subset, n_subsets, eta, params, amom, d_y, d_xprev, d_b, d_xout, d_yout,
+                              nullptr, d_ws, stream);
+}
+
+int pnp_unrolled_step_save(const pnp_geom* g, int factor, int subset, int n_subsets, double eta,
+                           const pnp_run_params* params, float amom, const float* d_y, const float* d_xprev,
+                           const float* d_b, float* d_xout, float* d_yout, float* d_zout, void* d_ws,
+                           void* stream)
+{
+    if (!d_zout) return fail(PNP_EINVAL, "z output required");
+    return unrolled_step_impl(g, factor, subset, n_subsets, eta, params, amom, d_y, d_xprev, d_b, d_xout, d_yout,
+                              d_zout, d_ws, stream);
+}
+
+int pnp_unrolled_step_vjp(const pnp_geom* g, int factor, int subset, int n_subsets, double eta,
+                          const pnp_run_params* params, float amom, const float* d_y, const float* d_b,
+                          const float* d_xbar, const float* d_ybar, float* d_ybar_in, float* d_xpbar,
+                          double* h_lambar, void* d_ws, void* d_vjp_ws, size_t vjp_ws_bytes, void* stream)
+{
+    if (!d_y || !d_b) return fail(PNP_EINVAL, "y and b required");
+    return unrolled_step_vjp_impl(g, factor, subset, n_subsets, eta, params, amom, d_y, d_b, nullptr, d_xbar,
+                                  d_ybar, d_ybar_in, d_xpbar, h_lambar, d_ws, d_vjp_ws, vjp_ws_bytes, stream);
+}
+
+int pnp_unrolled_step_vjp_saved(const pnp_geom* g, int factor, int subset, int n_subsets, double eta,
+                                const pnp_run_params* params, float amom, const float* d_z,
+                                const float* d_xbar, const float* d_ybar, float* d_ybar_in, float* d_xpbar,
+                                double* h_lambar, void* d_ws, void* d_vjp_ws, size_t vjp_ws_bytes,
+                                void* stream)
+{
+    if (!d_z) return fail(PNP_EINVAL, "z required");
+    return unrolled_step_vjp_impl(g, factor, subset, n_subsets, eta, params, amom, nullptr, nullptr, d_z, d_xbar,
+                                  d_ybar, d_ybar_in, d_xpbar, h_lambar, d_ws, d_vjp_ws, vjp_ws_bytes, stream);
 }
 
 }  // extern "C"

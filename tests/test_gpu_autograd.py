@@ -93,6 +93,16 @@ def test_unrolled_step_and_vjp_parity(s, P, p, alpha, amom):
         assert rel(host(ybi)[i], r_yb) < TOL_VJP, rel(host(ybi)[i], r_yb)
         assert rel(host(xpb)[i], r_xpb) < 1e-6
         assert abs(lb[i] - r_lb) < TOL_VJP * max(1.0, abs(r_lb)), (lb[i], r_lb)
+    # keeping z instead of recomputing it gives the same bits
+    xo2, yo2, z = (torch.empty(2, 48, 48, device="cuda") for _ in range(3))
+    _native.unrolled_step_save(g, s, p, P, eta, alpha, lam, it, amom, dev(y), dev(xp), dev(b), xo2, yo2, z,
+                               plan.ws)
+    assert np.array_equal(host(xo2), host(xo)) and np.array_equal(host(yo2), host(yo))
+    ybi2, xpb2 = torch.empty(2, 48, 48, device="cuda"), torch.empty(2, 48, 48, device="cuda")
+    lb2 = _native.unrolled_step_vjp_saved(g, s, p, P, eta, alpha, lam, it, amom, z, dev(xb), dev(yb), ybi2, xpb2,
+                                          plan.ws, vws)
+    assert np.array_equal(host(ybi2), host(ybi)) and np.array_equal(host(xpb2), host(xpb))
+    assert np.array_equal(lb2, lb)
 
 
 def _oracle_unrolled(g, stages, eta, seq, b, x0, xt, lam, alpha, tv_iters):
@@ -116,7 +126,8 @@ def _oracle_unrolled(g, stages, eta, seq, b, x0, xt, lam, alpha, tv_iters):
     return 0.5 * np.sum((x - xt) ** 2), xb + yb, gl
 
 
-def test_unrolled_autograd_matches_oracle_and_fd():
+@pytest.mark.parametrize("keep_z", [True, False])
+def test_unrolled_autograd_matches_oracle_and_fd(keep_z):
     import torch
     from paper_2203_07308_gb300.autograd import unrolled_pnp
     g = synth.make_geometry(48, 36, 64, batch=2)
@@ -131,7 +142,7 @@ def test_unrolled_autograd_matches_oracle_and_fd():
     lam0, alpha, tvit = 0.03, 0.9, 12
     X0 = dev(x0).requires_grad_(True)
     lam = torch.tensor(lam0, dtype=torch.float64, requires_grad=True)
-    xT = unrolled_pnp(plan, stages, eta, seq, dev(b), X0, lam, alpha=alpha, tv_iters=tvit)
+    xT = unrolled_pnp(plan, stages, eta, seq, dev(b), X0, lam, alpha=alpha, tv_iters=tvit, keep_z=keep_z)
     loss = 0.5 * ((xT - dev(xt)) ** 2).sum()
     loss.backward()
     gx = host(X0.grad)
