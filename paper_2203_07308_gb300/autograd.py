@@ -20,6 +20,59 @@ import torch
 from . import _native
 
 
+class Project(torch.autograd.Function):
+    """A_s^{(p)} v (Eq. 1, Eq. 4) as a differentiable operation on the level-s
+    image v [batch, n/s, n/s]: the backward pass is the matched backprojector
+    A_s^{(p)T} (pnp_backproject), so autograd gradients of any loss of A v are
+    exact for the discrete operator."""
+
+    @staticmethod
+    def forward(ctx, img, plan, factor, subset, n_subsets):
+        g = plan.g
+        sino = torch.empty(g.batch, _native.subset_views(g, subset, n_subsets), g.n_det, device=img.device)
+        plan.project(factor, img.contiguous(), sino, None, subset, n_subsets)
+        ctx.args = (plan, factor, subset, n_subsets)
+        return sino
+
+    @staticmethod
+    def backward(ctx, gsino):
+        plan, factor, subset, n_subsets = ctx.args
+        ns = plan.g.n // factor
+        gimg = torch.empty(plan.g.batch, ns, ns, device=gsino.device)
+        plan.backproject(factor, gsino.contiguous(), gimg, subset, n_subsets)
+        return gimg, None, None, None, None
+
+
+class Backproject(torch.autograd.Function):
+    """A_s^{(p)T} r as a differentiable operation; its backward is A_s^{(p)}."""
+
+    @staticmethod
+    def forward(ctx, sino, plan, factor, subset, n_subsets):
+        ns = plan.g.n // factor
+        img = torch.empty(plan.g.batch, ns, ns, device=sino.device)
+        plan.backproject(factor, sino.contiguous(), img, subset, n_subsets)
+        ctx.args = (plan, factor, subset, n_subsets)
+        return img
+
+    @staticmethod
+    def backward(ctx, gimg):
+        plan, factor, subset, n_subsets = ctx.args
+        g = plan.g
+        gsino = torch.empty(g.batch, _native.subset_views(g, subset, n_subsets), g.n_det, device=gimg.device)
+        plan.project(factor, gimg.contiguous(), gsino, None, subset, n_subsets)
+        return gsino, None, None, None, None
+
+
+def project(plan, img, factor: int = 1, subset: int = 0, n_subsets: int = 1):
+    """Differentiable forward projection of the level-`factor` image."""
+    return Project.apply(img, plan, factor, subset, n_subsets)
+
+
+def backproject(plan, sino, factor: int = 1, subset: int = 0, n_subsets: int = 1):
+    """Differentiable backprojection of a subset sinogram."""
+    return Backproject.apply(sino, plan, factor, subset, n_subsets)
+
+
 class UnrolledStep(torch.autograd.Function):
     @staticmethod
     def forward(ctx, y, xprev, lam, plan, b, factor, subset, n_subsets, eta, alpha, tv_iters, amom, vjp_ws,

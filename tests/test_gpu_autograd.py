@@ -196,3 +196,33 @@ def test_differentiable_workload_full_size():
                                      wl.alpha, wl.tv_iters)
         assert rel(gx[i], rgx) < TOL_VJP_FULL, rel(gx[i], rgx)
     assert np.isfinite(float(lam.grad))
+
+
+@pytest.mark.parametrize("s,P,p", [(1, 1, 0), (2, 3, 1)])
+def test_projector_autograd_functions(s, P, p):
+    """Project / Backproject as autograd Functions: the autograd gradient of
+    1/2 ||A_s v - b||^2 is the library's gradient and the oracle's A^T(A v - b);
+    the two Functions are each other's adjoint through autograd."""
+    import torch
+    from paper_2203_07308_gb300.autograd import backproject, project
+    g = synth.make_geometry(48, 30, 64, batch=2)
+    plan = pnp.Plan(g)
+    ns = 48 // s
+    rng = np.random.default_rng(7 + s)
+    v = f32(rng.random((2, ns, ns)))
+    nsub = pnp.subset_views(g, p, P)
+    b = f32(rng.standard_normal((2, nsub, g.n_det)) * 3)
+    V = dev(v).requires_grad_(True)
+    r = project(plan, V, s, p, P) - dev(b)
+    (0.5 * (r ** 2).sum()).backward()
+    got = host(V.grad)
+    for i in range(2):
+        ref = oracle.backproject(g, s, oracle.project(g, s, v[i], None, p, P) - b[i], p, P)
+        assert rel(got[i], ref) < 1e-5, rel(got[i], ref)
+    # Backproject's backward is the projector: d/dw <x, A^T w> = A x
+    W = dev(b).requires_grad_(True)
+    x = dev(rng.random((2, ns, ns)))
+    (backproject(plan, W, s, p, P) * x).sum().backward()
+    ax = torch.empty(2, nsub, g.n_det, device="cuda")
+    plan.project(s, x, ax, None, p, P)
+    assert np.array_equal(host(W.grad), host(ax))

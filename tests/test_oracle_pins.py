@@ -127,6 +127,33 @@ def test_gaussian_blob_line_integrals():
     assert np.abs(sino - swapped).max() / exact.max() > 0.1
 
 
+def test_centred_disk_chord_lengths():
+    """Binary disk of radius r (pixels whose centre lies inside): a ray at
+    distance p < r from the centre has line integral ~ 2 sqrt(r^2 - p^2), the
+    chord.  The pixelised edge moves each end of the chord by at most about one
+    pixel, so the error is O(1) pixel-lengths (below 1.5 away from grazing
+    rays, under half a pixel on average) and its ratio to the diameter halves
+    when the grid is refined with the disk fixed relative to the image."""
+    rel_errs = []
+    for n in (64, 128):
+        g = synth.make_geometry(n, 12, 96)
+        r = 0.3 * n
+        X, Y = pixel_centres(n)
+        img = (X ** 2 + Y ** 2 <= r * r).astype(float)
+        sino = oracle.project(g, 1, img)
+        errs = []
+        for v in range(g.n_views):
+            for j in range(g.n_det):
+                S, P = ray_endpoints(g, v, j)
+                p = line_distance((0.0, 0.0), S, P)
+                if p < r - 2.0:
+                    errs.append(abs(sino[v, j] - 2.0 * math.sqrt(r * r - p * p)))
+        errs = np.array(errs)
+        assert errs.size > 100 and errs.max() < 1.5 and errs.mean() < 0.5, (n, errs.max(), errs.mean())
+        rel_errs.append(errs.mean() / (2 * r))
+    assert rel_errs[1] < 0.7 * rel_errs[0], rel_errs
+
+
 def test_paraboloid_closed_form_and_order():
     """max(0, r^2 - rho^2) has line integral (4/3)(r^2 - p^2)^{3/2}; the error
     falls at second order when the grid is refined (same physical object)."""
