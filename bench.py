@@ -441,11 +441,13 @@ def gray_by_config(dev, stream):
 def mixed_64(dev, stream):
     """64 instances of 128^2/180/256, 256^2/360/512 and 512^2/720/768 (seeded mix)
     in one call: every phase of every iteration one launch over the three
-    classes; 50 sketched iterations each."""
+    classes; 50 sketched iterations each.  Also the time for every class to
+    reach its full-gradient arm's final mean PSNR - 0.1 dB, sketched vs full,
+    each class's schedule cut at its own first iteration on target."""
     import torch
     import paper_2203_07308_gb300 as pnp
     from paper_2203_07308_gb300 import synth
-    probs, n_img, iters = [], 0, 0
+    sk, fu, n_img, iters = [], [], 0, 0
     for wl, _ids in synth.mixed_classes(64):
         g = wl.geom
         plan = pnp.Plan(g)
@@ -454,15 +456,47 @@ def mixed_64(dev, stream):
         plan.autotune(wl.stages, **kw)
         eta = [1.0 / plan.power_iter(st_.factor, 60, 1e-6)[0] for st_ in wl.stages]
         seq = synth.schedule_sequence(wl.stages, synth.subset_seed(wl.config_id))
-        probs.append(dict(plan=plan, stages=wl.stages, eta=eta, seq=seq, b=d_b,
-                          x=torch.zeros(g.batch, g.n, g.n, device=dev)))
+        full = synth.full_gradient_arm(wl.stages)
+        base = dict(plan=plan, b=d_b, xtrue=d_xt)
+        sk.append(dict(base, stages=wl.stages, eta=eta, seq=seq, x=torch.zeros(g.batch, g.n, g.n, device=dev)))
+        fu.append(dict(base, stages=full, eta=[eta[-1]], seq=None, x=torch.zeros(g.batch, g.n, g.n, device=dev)))
         n_img += g.batch
         iters = sum(st_.iters for st_ in wl.stages)
-    pnp.run_many(probs, alpha=1.0, lam=0.02, tv_iters=20, momentum=True)      # warm
-    ms = _device_ms(lambda: pnp.run_many(probs, alpha=1.0, lam=0.02, tv_iters=20, momentum=True), stream)
+    kw = dict(alpha=1.0, lam=0.02, tv_iters=20, momentum=True)
+
+    def fresh(probs):                 # every run starts from x_0 = 0
+        for p_ in probs:
+            p_["x"].zero_()
+        return probs
+    untimed = [{k: v for k, v in p_.items() if k != "xtrue"} for p_ in sk]
+    pnp.run_many(fresh(untimed), **kw)      # warm
+    ms = _device_ms(lambda: pnp.run_many(fresh(untimed), **kw), stream)
+    logs_s = pnp.run_many(fresh(sk), **kw)
+    logs_f = pnp.run_many(fresh(fu), **kw)
+    arms = {}
+    for name, probs, logs in (("sketched", sk, logs_s), ("full", fu, logs_f)):
+        cut_probs, hits = [], []
+        for p_, log, lf in zip(probs, logs, logs_f):
+            target = float(lf[-1].mean()) - 0.1
+            hit = np.nonzero(log.mean(axis=1) >= target)[0]
+            it = int(hit[0]) + 1 if hit.size else int(log.shape[0])
+            hits.append(it)
+            cut, left = [], it
+            for st_ in p_["stages"]:
+                k = min(st_.iters, left)
+                if k > 0:
+                    cut.append(synth.Stage(st_.factor, k, st_.n_subsets))
+                left -= k
+            cut_probs.append(dict(plan=p_["plan"], b=p_["b"], x=p_["x"], stages=cut,
+                                  eta=p_["eta"][:len(cut)], seq=p_["seq"]))
+        run = lambda: pnp.run_many(fresh(cut_probs), **kw)      # noqa: E731
+        run()
+        arms[name] = {"ms": _device_ms(run, stream), "iters_per_class": hits}
     return {"workload": "64 mixed instances (seed 5308), 3 geometry classes, 50 iterations",
-            "classes": [[p_["plan"].g.n, p_["plan"].g.n_views, p_["plan"].g.n_det, p_["plan"].g.batch] for p_ in probs],
-            "run_ms": ms, "gradients_per_s": n_img * iters / (ms / 1000.0)}
+            "classes": [[p_["plan"].g.n, p_["plan"].g.n_views, p_["plan"].g.n_det, p_["plan"].g.batch] for p_ in sk],
+            "run_ms": ms, "gradients_per_s": n_img * iters / (ms / 1000.0),
+            "time_to_psnr": {"sketched": arms["sketched"], "full": arms["full"],
+                             "speedup": arms["full"]["ms"] / arms["sketched"]["ms"]}}
 
 
 def differentiable_256x8(dev, stream):
