@@ -116,6 +116,7 @@ Layout make_layout(const pnp_geom& g)
     L.off_res = off; off = align_up(off + (size_t)g.batch * nr * sizeof(float));
     L.off_y = off; off = align_up(off + img * sizeof(float));
     L.off_z = off; off = align_up(off + img * sizeof(float));
+    L.off_x2 = off; off = align_up(off + img * sizeof(float));
     L.off_tv = off; off = align_up(off + 8 * img * sizeof(float));
     L.off_pw = off; off = align_up(off + 2 * (size_t)g.n * g.n * sizeof(float));
     L.off_cs = off; off = align_up(off + 2 * (size_t)g.batch * (g.n / 2) * (g.n / 2) * sizeof(float));
@@ -914,6 +915,9 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
     long min_start = max_total;
     for (int c = 0; c < np; ++c) min_start = std::min(min_start, (long)pb[c].start_iter);
     const bool timed = (pr.flags & PNP_RUN_KERNEL_TIMES) != 0;
+    // the denoiser's last launch also writes the level-1 coefficient image of y
+    // when the next iteration is a full-grid mini-batch one (it then needs no prep)
+    const bool fuse_quad = do_tv && !all_warp && fuse_quad_enabled();
     auto issue = [&]() -> int {
         int e0 = PNP_OK;
         for (int c = 0; c < np; ++c) {
@@ -923,6 +927,10 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
             PNP_CUDA(launch_copy(y0, (float*)(ws + ps[c].L.off_y), (size_t)g.batch * g.n * g.n, st));
         }
         std::vector<int> stage((size_t)np, 0), in_stage((size_t)np, 0);
+        // x alternates between d_x (even iteration count) and the workspace copy, so
+        // that the denoiser can read x_{i-1} around its tile while writing x_i
+        std::vector<long> done((size_t)np, 0);
+        std::vector<char> quad_ready((size_t)np, 0);
         for (long i = 1; i <= max_total; ++i) {
             if (i <= min_start) {       // resumed runs: advance the schedule cursors only
                 for (int c = 0; c < np; ++c) {
@@ -939,6 +947,7 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
             TvItem tv[kMaxClasses];
             int act[kMaxClasses];
             int bic[kMaxClasses];
+            int need_prep[kMaxClasses];
             int na = 0;
             const float amom = pr.momentum ? (float)((double)(i - 1) / (double)(i + 3)) : 0.0f;
             for (int c = 0; c < np; ++c) {
@@ -974,6 +983,7 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
                 } else {
                     bic[na] = 0;
                 }
+                need_prep[na] = !(quad_ready[c] && lv.factor == 1);
                 prep[na] = PrepArgs{y, g.n, lv.factor, g.batch, (float4*)(ws + lv.off_quad), lv.qw};
                 fwd[na] = fwd_args(g, lv, ws, p, P, q.d_b, res, g.batch, reg_weights(ws));
                 const double cs = P <= 1 ? 1.0 : (double)P;
@@ -981,8 +991,26 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
                 back[na] = back_args(g, lv, ws, p, P, res, kBackStep, scale, y, (float)q.h_eta[stage[c]], z, g.batch);
                 const size_t img = (size_t)g.batch * g.n * g.n;
                 float* tvb = (float*)(ws + L.off_tv);
+                float* x2 = (float*)(ws + L.off_x2);
                 TvItem t{};
-                t.z = z; t.xprev = q.d_x; t.y = y; t.xtrue = q.d_xtrue;
+                t.xin = done[c] % 2 == 0 ? q.d_x : x2;
+                t.xprev = done[c] % 2 == 0 ? x2 : q.d_x;
+                ++done[c];
+                quad_ready[c] = 0;
+                if (fuse_quad && i < ps[c].total) {
+                    // the stage of iteration i + 1 (the cursor skips stages without iterations)
+                    int sn = stage[c];
+                    if (in_stage[c] >= q.stages[sn].iters)
+                        do ++sn; while (q.stages[sn].iters == 0);
+                    const pnp_stage& nx = q.stages[sn];
+                    if (nx.factor == 1 && (nx.n_subsets <= 1 || nx.estimator == PNP_EST_MINIBATCH)) {
+                        const LevelLayout& l1 = L.lv[level_index(1)];
+                        t.quad = (float4*)(ws + l1.off_quad);
+                        t.qw = l1.qw;
+                        quad_ready[c] = 1;
+                    }
+                }
+                t.z = z; t.y = y; t.xtrue = q.d_xtrue;
                 t.mse_part = q.h_psnr_log ? (double*)(ws + L.off_red) : nullptr;
                 t.state_a = tvb; t.state_b = tvb + 4 * img;
                 t.n = g.n; t.batch = g.batch; t.tile = ps[c].tuned.tile; t.amom = amom;
@@ -1002,18 +1030,20 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
                 PrepArgs pp[kMaxClasses];
                 FwdArgs ff[kMaxClasses];
                 BackArgs bb[kMaxClasses];
-                int m = 0;
+                int m = 0, mp = 0;
                 for (int a = 0; a < na; ++a) {
                     if (bic[a]) continue;
-                    pp[m] = prep[a];
+                    if (need_prep[a]) pp[mp++] = prep[a];
                     ff[m] = fwd[a];
                     bb[m] = back[a];
                     ++m;
                 }
-                if (m > 0) {
+                if (mp > 0) {
                     if (timed && (e0 = g_timer.mark(PNP_PHASE_PREP, st, true))) return e0;
-                    PNP_CUDA(launch_prep_multi(pp, m, st));
+                    PNP_CUDA(launch_prep_multi(pp, mp, st));
                     if (timed && (e0 = g_timer.mark(PNP_PHASE_PREP, st, false))) return e0;
+                }
+                if (m > 0) {
                     if (timed && (e0 = g_timer.mark(PNP_PHASE_FORWARD, st, true))) return e0;
                     PNP_CUDA(launch_forward_multi(ff, m, st, one ? tu.lanes[li0] : 0));
                     if (timed && (e0 = g_timer.mark(PNP_PHASE_FORWARD, st, false))) return e0;
@@ -1030,7 +1060,7 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
                 for (int a = 0; a < na; ++a) {
                     const TvItem& t = tv[a];
                     PNP_CUDA(launch_tv_final(t.z, nullptr, 0, t.n, t.batch, pr.lambda, pr.alpha, t.amom, t.xprev,
-                                             t.y, t.xtrue, t.mse_part, st));
+                                             t.y, t.xtrue, t.mse_part, st, t.xin));
                 }
             }
             for (int a = 0; a < na; ++a) {
@@ -1042,6 +1072,12 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
                 PNP_CUDA(launch_reduce_final((double*)(ws + ps[c].L.off_red), ps[c].tv_parts, q.geom.batch,
                                              dlog + (i - 1) * q.geom.batch, 1, 0, st));
             }
+        }
+        for (int c = 0; c < np; ++c) {
+            const pnp_geom& g = pb[c].geom;
+            char* ws = (char*)pb[c].d_ws;
+            if (done[c] % 2 == 1)
+                PNP_CUDA(launch_copy((float*)(ws + ps[c].L.off_x2), pb[c].d_x, (size_t)g.batch * g.n * g.n, st));
         }
         for (int c = 0; c < np; ++c) {
             if (!pb[c].d_y) continue;

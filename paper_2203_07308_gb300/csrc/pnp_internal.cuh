@@ -45,6 +45,8 @@ __device__ __forceinline__ void pdl_begin()
 }
 
 bool pdl_enabled();
+// PNP_FUSE_QUAD=0 keeps the coefficient-image kernel in every iteration
+bool fuse_quad_enabled();
 
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
@@ -70,6 +72,20 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 
 constexpr int kMaxLevels = 4;          // factors 1, 2, 4, 8
 constexpr int kPad = 2;                // padding of the coefficient image
+
+// Bilinear coefficients (c0, c1, c2, c3) of a cell with corner values a = I(x0,y0),
+// b = I(x0+1,y0), c = I(x0,y0+1), d = I(x0+1,y0+1): f = c0 + u c1 + w (c2 + u c3)
+// in the centred variables u, w in [-1/2, 1/2].  One definition for every kernel
+// that writes the coefficient image, so they agree bit for bit.
+__device__ __forceinline__ float4 make_quad(float a, float b, float c, float d)
+{
+    float4 q;
+    q.x = 0.25f * ((a + b) + (c + d));
+    q.y = 0.5f * ((b - a) + (d - c));
+    q.z = 0.5f * ((c - a) + (d - b));
+    q.w = (a - b) - (c - d);
+    return q;
+}
 constexpr int kRedBlocks = 304;        // FP64 partial-sum blocks per instance (2 x 152 SMs)
 constexpr int kRedThreads = 256;
 
@@ -87,6 +103,7 @@ struct Layout {
     size_t off_res = 0;      // float [batch][n_views][n_det]
     size_t off_y = 0;        // float [batch][n][n]
     size_t off_z = 0;        // float [batch][n][n]
+    size_t off_x2 = 0;       // float [batch][n][n]  second buffer of the iterate x (odd iterations)
     size_t off_tv = 0;       // float [8][batch][n][n]  TV state ping/pong (r1 r2 p1 p2)
     size_t off_pw = 0;       // float [2][n][n]   power iteration u, w
     size_t off_cs = 0;       // float [2][batch][(n/2)^2] bicubic coarse image and coarse gradient
@@ -155,12 +172,13 @@ cudaError_t launch_unpool(const float* coarse, float* fine, int n, int s, int ba
 
 // TV (FGP) --------------------------------------------------------------------
 // x = z - lambda L(p) (or z when iters == 0), then relaxation and momentum:
-//   xi = (1-alpha) z + alpha x;  y = xi + a (xi - xprev);  xprev <- xi.
+//   xi = (1-alpha) z + alpha x;  y = xi + a (xi - x_{i-1});  xprev <- xi,
+// x_{i-1} read from xin (nullptr: from xprev itself).
 // With y == nullptr it writes x only (plain denoiser output to xprev).
 // If mse_partials != nullptr, accumulates sum (xi - xtrue)^2 per block.
 cudaError_t launch_tv_final(const float* z, const float* p, int have_p, int n, int batch, float lambda,
                             float alpha, float a, float* xprev, float* y, const float* xtrue,
-                            double* mse_partials, cudaStream_t st);
+                            double* mse_partials, cudaStream_t st, const float* xin = nullptr);
 
 // Temporally blocked FGP: every iteration of the denoiser (iters >= 1) for all
 // images, T x T tiles recomputing their halos (launch_tv_tiled chains launches
@@ -181,6 +199,9 @@ struct TvItem {
     float* state_a; float* state_b;        // [4][batch][n][n] each (chained launches only)
     int n, batch, tile;
     float amom;
+    const float* xin = nullptr;            // x_{i-1} when it is not xprev (double-buffered x)
+    float4* quad = nullptr;                // shared-memory tiles only: also write the level-1
+    int qw = 0;                            // coefficient image of y (qw = n + 2 kPad - 1)
 };
 cudaError_t launch_tv_tiled_multi(const TvItem* items, int count, float lambda, int iters, float alpha,
                                   cudaStream_t st);

@@ -129,12 +129,7 @@ __global__ void k_prep_quad(const PrepTable t)
     const int ix0 = qx - kPad, iy0 = qy - kPad;
     const float pa = pooled(f, n, s, ns, ix0, iy0), pb = pooled(f, n, s, ns, ix0 + 1, iy0);
     const float pc = pooled(f, n, s, ns, ix0, iy0 + 1), pd = pooled(f, n, s, ns, ix0 + 1, iy0 + 1);
-    float4 q;
-    q.x = 0.25f * ((pa + pb) + (pc + pd));
-    q.y = 0.5f * ((pb - pa) + (pd - pc));
-    q.z = 0.5f * ((pc - pa) + (pd - pb));
-    q.w = (pa - pb) - (pc - pd);
-    a.quad[local] = q;
+    a.quad[local] = make_quad(pa, pb, pc, pd);
 }
 
 // ------------------------------------------------------------------ forward A_s

@@ -20,6 +20,15 @@ bool pdl_enabled()
     return on;
 }
 
+bool fuse_quad_enabled()
+{
+    static const bool on = [] {
+        const char* e = std::getenv("PNP_FUSE_QUAD");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
 namespace {
 
 __device__ __forceinline__ double block_sum(double v)

@@ -28,7 +28,8 @@ __host__ __device__ inline int div_up(long a, long b) { return (int)((a + b - 1)
 __global__ void k_tv_final(const float* __restrict__ z, const float* __restrict__ p, int have_p,
                            int n, long plane, float lambda, float alpha, float amom,
                            float* __restrict__ xprev, float* __restrict__ y,
-                           const float* __restrict__ xtrue, double* __restrict__ mse_part)
+                           const float* __restrict__ xtrue, double* __restrict__ mse_part,
+                           const float* __restrict__ xin)
 {
     pdl_begin();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -48,7 +49,7 @@ __global__ void k_tv_final(const float* __restrict__ z, const float* __restrict_
         }
         const float xi = (1.0f - alpha) * zz + alpha * x;
         if (y) {
-            const float xp = xprev[o];
+            const float xp = xin ? xin[o] : xprev[o];
             y[o] = xi + amom * (xi - xp);
         }
         xprev[o] = xi;
@@ -92,6 +93,9 @@ __global__ void k_tv_final(const float* __restrict__ z, const float* __restrict_
 struct TileTvClass {
     const float* z; const float* sin; float* sout;   // state planes [4][batch][n][n]: r1 r2 p1 p2
     float* xprev; float* y; const float* xtrue; double* mse_part;
+    const float* xin;                                 // x_{i-1} (nullptr: xprev)
+    float4* quad;                                     // last launch: level-1 coefficient image of y
+    int qw, ring;                                     // ring = 1 when quad is written
     int n, T, tiles_x, tiles;
     long plane;
     float amom;
@@ -129,7 +133,10 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
     const int inst = (int)(local / a.tiles);
     const int tile = (int)(local - (long)inst * a.tiles);
     const int i0 = (tile / tiles_x) * T, j0 = (tile % tiles_x) * T;
-    const int S = T + 1 + 2 * K;                 // side of the loaded region
+    // with ring = 1 the region (and every R_k) reaches one row and column further
+    // below/right, so that y is also known on the ring around the tile
+    const int ring = a.ring;
+    const int S = T + 1 + 2 * K + ring;          // side of the loaded region
     const int P = tile_pitch(S);
     const int oi = i0 - 1 - K, oj = j0 - 1 - K;  // its origin (may lie outside the image)
     extern __shared__ float sm[];
@@ -154,8 +161,8 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
         if (f < S * S && i >= 0 && i < n && j >= 0 && j < n) {
             // distance outside the core of R_k ([i0-1, i0+T) x [j0-1, j0+T)) and of
             // the phase-A region (core grown by one row below, one column right)
-            dB[m] = max(max(i0 - 1 - i, i - (i0 + T - 1)), max(max(j0 - 1 - j, j - (j0 + T - 1)), 0));
-            dA[m] = max(max(i0 - 1 - i, i - (i0 + T)), max(max(j0 - 1 - j, j - (j0 + T)), 0));
+            dB[m] = max(max(i0 - 1 - i, i - (i0 + T - 1 + ring)), max(max(j0 - 1 - j, j - (j0 + T - 1 + ring)), 0));
+            dA[m] = max(max(i0 - 1 - i, i - (i0 + T + ring)), max(max(j0 - 1 - j, j - (j0 + T + ring)), 0));
             flags[m] = (i > 0 ? 1 : 0) | (j > 0 ? 2 : 0) | (i < n - 1 ? 4 : 0) | (j < n - 1 ? 8 : 0) |
                        (i >= i0 && i < i0 + T && j >= j0 && j < j0 + T ? 16 : 0);
             const long g = img + (long)i * n + j;
@@ -225,32 +232,59 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
         }
         return;
     }
-    // x = z - lambda L(p) on the tile, relaxation, momentum, squared error
+    // x = z - lambda L(p) on the tile (and its ring), relaxation, momentum, squared error
 #pragma unroll
     for (int m = 0; m < NP; ++m)
         if (dB[m] == 0) pp[q[m]] = make_float2(p1[m], p2[m]);
     __syncthreads();
     double e2 = 0.0;
+    float* ys = xt;                     // y on the tile and its ring, for the coefficient image
 #pragma unroll
     for (int m = 0; m < NP; ++m) {
-        if (flags[m] & 16) {
+        const int f = threadIdx.x + m * blockDim.x;
+        const int li = f / S, lj = f - li * S;
+        const int i = oi + li, j = oj + lj;
+        const bool own = flags[m] & 16;
+        const bool rim = ring && f < S * S && !own && i >= i0 && j >= j0 && i <= i0 + T && j <= j0 + T &&
+                         i < n && j < n;
+        if (own || rim) {
             float l = p1[m] + p2[m];
             if (flags[m] & 1) l -= pp[q[m] - P].x;
             if (flags[m] & 2) l -= pp[q[m] - 1].y;
             const float x = z[m] - lam * l;
             const float xi = (1.0f - t.alpha) * z[m] + t.alpha * x;
-            const int f = threadIdx.x + m * blockDim.x;
-            const int li = f / S, lj = f - li * S;
-            const long g = img + (long)(oi + li) * n + (oj + lj);
+            const long g = img + (long)i * n + j;
+            float yv = 0.0f;
             if (a.y) {
-                const float xp = a.xprev[g];
-                a.y[g] = xi + a.amom * (xi - xp);
+                const float xp = a.xin ? a.xin[g] : a.xprev[g];
+                yv = xi + a.amom * (xi - xp);
             }
-            a.xprev[g] = xi;
-            if (a.xtrue) {
-                const double d = (double)xi - (double)__ldg(a.xtrue + g);
-                e2 += d * d;
+            if (own) {
+                if (a.y) a.y[g] = yv;
+                a.xprev[g] = xi;
+                if (a.xtrue) {
+                    const double d = (double)xi - (double)__ldg(a.xtrue + g);
+                    e2 += d * d;
+                }
             }
+            if (ring) ys[q[m]] = yv;
+        }
+    }
+    if (ring) {
+        // coefficient cells whose lower corner lies in the tile; the first tiles
+        // of a row/column also take the padding cells before the image, the last
+        // ones the cell after it (corners outside the image are zero)
+        __syncthreads();
+        const int r_lo = i0 == 0 ? -kPad : i0, r_hi = i0 + T >= n ? n + 1 : i0 + T;
+        const int c_lo = j0 == 0 ? -kPad : j0, c_hi = j0 + T >= n ? n + 1 : j0 + T;
+        const int cw = c_hi - c_lo, cells = (r_hi - r_lo) * cw;
+        float4* qimg = a.quad + (long)inst * a.qw * a.qw;
+        auto Y = [&](int r, int c) -> float {
+            return (r < 0 || c < 0 || r >= n || c >= n) ? 0.0f : ys[(r - oi) * P + (c - oj)];
+        };
+        for (int k = threadIdx.x; k < cells; k += blockDim.x) {
+            const int r = r_lo + k / cw, c = c_lo + k % cw;
+            qimg[(long)(r + kPad) * a.qw + (c + kPad)] = make_quad(Y(r, c), Y(r, c + 1), Y(r + 1, c), Y(r + 1, c + 1));
         }
     }
     if (a.mse_part) {
@@ -283,6 +317,7 @@ constexpr int kWarpTvWarps = 1;                              // warp tiles per C
 struct WarpTvClass {
     const float* z; const float* sin; float* sout;          // state planes [4][batch][n][n]: r1 r2 p1 p2
     float* xprev; float* y; const float* xtrue; double* mse_part;
+    const float* xin;                                        // x_{i-1} (nullptr: xprev)
     int n, tiles_x, tiles;
     long plane;
     float amom;
@@ -396,7 +431,7 @@ __global__ void __launch_bounds__(32 * kWarpTvWarps) k_tv_warp(const WarpTvArgs 
             const float xi = (1.0f - t.alpha) * z[m] + t.alpha * x;
             const long g = img + (long)i * n + j;
             if (a.y) {
-                const float xp = a.xprev[g];
+                const float xp = a.xin ? a.xin[g] : a.xprev[g];
                 a.y[g] = xi + a.amom * (xi - xp);
             }
             a.xprev[g] = xi;
@@ -422,12 +457,12 @@ inline cudaError_t counted(cudaError_t e = cudaGetLastError())
 
 cudaError_t launch_tv_final(const float* z, const float* p, int have_p, int n, int batch, float lambda,
                             float alpha, float a, float* xprev, float* y, const float* xtrue,
-                            double* mse_partials, cudaStream_t st)
+                            double* mse_partials, cudaStream_t st, const float* xin)
 {
     dim3 blk(32, 8), grd(div_up(n, 32), div_up(n, 8), batch);
     long plane = (long)batch * n * n;
     const cudaError_t e = launch_pdl(k_tv_final, grd, blk, 0, st, z, p, have_p, n, plane, lambda, alpha, a, xprev,
-                                     y, xtrue, mse_partials);
+                                     y, xtrue, mse_partials, xin);
     if (e != cudaSuccess) return e;
     return counted();
 }
@@ -441,16 +476,16 @@ constexpr int kTileThreads = 1024;
 constexpr int kTileKMax = 10;            // iterations per launch (halo recompute vs launches)
 constexpr size_t kTileSmemMax = 112 * 1024;
 
-inline size_t tile_smem(int T, int K)
+inline size_t tile_smem(int T, int K, int ring = 0)
 {
-    const int S = T + 1 + 2 * K;
+    const int S = T + 1 + 2 * K + ring;
     return (size_t)5 * S * tile_pitch(S) * sizeof(float);
 }
 
-// pixels per thread needed to cover the (T + 1 + 2K)^2 region with 1024 threads
-inline int tile_np(int T, int K)
+// pixels per thread needed to cover the (T + 1 + 2K + ring)^2 region with 1024 threads
+inline int tile_np(int T, int K, int ring = 0)
 {
-    const int S = T + 1 + 2 * K;
+    const int S = T + 1 + 2 * K + ring;
     return (S * S + kTileThreads - 1) / kTileThreads;
 }
 
@@ -461,7 +496,7 @@ int choose_tile(int n, int batch)
     int best = 16;
     double best_cost = 1e300;
     for (int T = 8; T <= 40; ++T) {
-        if (tile_smem(T, kTileKMax) > kTileSmemMax || tile_np(T, kTileKMax) > 4) break;
+        if (tile_smem(T, kTileKMax, 1) > kTileSmemMax || tile_np(T, kTileKMax, 1) > 4) break;
         const long tiles = (long)batch * ((n + T - 1) / T) * ((n + T - 1) / T);
         const long waves = (tiles + 151) / 152;
         const double side = (double)std::min(T, n) + 1 + kTileKMax;
@@ -477,11 +512,20 @@ int choose_tile(int n, int batch)
 
 int tile_tv_tile(int n, int batch) { return choose_tile(n, batch); }
 
+// The tile side a launch uses: the requested one when it fits (ring included),
+// else the default.
+int resolve_tile(int tile, int n, int batch)
+{
+    if (tile < 4 || tile > 64 || tile_np(tile, kTileKMax, 1) > 4 || tile_smem(tile, kTileKMax, 1) > kTileSmemMax)
+        return tile_tv_tile(n, batch);
+    return tile;
+}
+
 int tile_tv_parts_for(int n, int batch, int tile)
 {
     if (tile == kTvTileWarp)
         return ((n + kWarpTvWV - 1) / kWarpTvWV) * ((n + kWarpTvHV - 1) / kWarpTvHV);
-    const int T = tile > 0 ? tile : tile_tv_tile(n, batch);
+    const int T = resolve_tile(tile, n, batch);
     return ((n + T - 1) / T) * ((n + T - 1) / T);
 }
 
@@ -500,6 +544,7 @@ cudaError_t launch_tv_warp_multi(const TvItem* items, int count, float lambda, i
         if (iters > kWarpTvK && (!it.state_a || !it.state_b)) return cudaErrorInvalidValue;
         WarpTvClass& wc = a.c[c];
         wc.z = it.z; wc.xprev = it.xprev; wc.y = it.y; wc.xtrue = it.xtrue; wc.mse_part = it.mse_part;
+        wc.xin = it.xin;
         wc.n = it.n;
         wc.tiles_x = (it.n + kWarpTvWV - 1) / kWarpTvWV;
         wc.tiles = wc.tiles_x * ((it.n + kWarpTvHV - 1) / kWarpTvHV);
@@ -560,12 +605,11 @@ cudaError_t launch_tv_tiled_multi(const TvItem* items, int count, float lambda, 
     int Tmax = 0;
     for (int c = 0; c < count; ++c) {
         const TvItem& it = items[c];
-        int T = it.tile >= 4 ? it.tile : tile_tv_tile(it.n, it.batch);
-        if (T < 4 || T > 64 || tile_np(T, kTileKMax) > 4 || tile_smem(T, kTileKMax) > kTileSmemMax)
-            T = tile_tv_tile(it.n, it.batch);
+        const int T = resolve_tile(it.tile, it.n, it.batch);
         if (iters > kTileKMax && (!it.state_a || !it.state_b)) return cudaErrorInvalidValue;   // chaining needs state
         TileTvClass& tc = a.c[c];
         tc.z = it.z; tc.xprev = it.xprev; tc.y = it.y; tc.xtrue = it.xtrue; tc.mse_part = it.mse_part;
+        tc.xin = it.xin; tc.quad = it.quad; tc.qw = it.qw;
         tc.n = it.n; tc.T = T; tc.tiles_x = (it.n + T - 1) / T; tc.tiles = tc.tiles_x * tc.tiles_x;
         tc.plane = (long)it.batch * it.n * it.n;
         tc.amom = it.amom;
@@ -580,17 +624,21 @@ cudaError_t launch_tv_tiled_multi(const TvItem* items, int count, float lambda, 
         a.K = K;
         a.first = k0 == 0;
         a.last = k0 + K == iters;
+        int ring = 0;
         for (int c = 0; c < count; ++c) {
             float* sa = items[c].state_a;
             float* sb = items[c].state_b;
             a.c[c].sin = k0 == 0 ? nullptr : (pass % 2 == 1 ? sa : sb);
             a.c[c].sout = a.last ? nullptr : (pass % 2 == 0 ? sa : sb);
+            // the coefficient image needs y on a one-pixel ring: last launch only
+            a.c[c].ring = a.last && items[c].quad && items[c].y && items[c].xin ? 1 : 0;
+            ring = std::max(ring, a.c[c].ring);
         }
         for (int k = 0; k < K; ++k) a.mom[k] = mom[k0 + k];
         const dim3 grd((unsigned)a.begin[count]);
-        const size_t sm = tile_smem(Tmax, K);
+        const size_t sm = tile_smem(Tmax, K, ring);
         const dim3 blk(kTileThreads);
-        switch (tile_np(Tmax, K)) {
+        switch (tile_np(Tmax, K, ring)) {
             case 1: e = launch_pdl(k_tv_tile<1>, grd, blk, sm, st, a); break;
             case 2: e = launch_pdl(k_tv_tile<2>, grd, blk, sm, st, a); break;
             case 3: e = launch_pdl(k_tv_tile<3>, grd, blk, sm, st, a); break;
