@@ -37,8 +37,8 @@ L2_FLUSH_BYTES = 512 << 20
 # capture (dram__bytes_read.sum + dram__bytes_write.sum over the 100
 # backprojection launches of one step, averaged); valid only while the
 # backprojector source is the one that was measured.
-BACKWARD_TRAFFIC = {"bytes_per_launch": 716293,
-                    "source_sha256": "e2aa4e69a260e096d57831ba1af2919f83d2838e8ed6257c9c370423a6dd603e",
+BACKWARD_TRAFFIC = {"bytes_per_launch": 716815,
+                    "source_sha256": "b2a5107c8625219eca365ffa9aaf304dd423e4d15a982cd54df56391abc8c2ad",
                     "profile": "profiles/k_backward2x2_256_360x512_step.md"}
 
 

@@ -1204,15 +1204,15 @@ int pnp_autotune(const pnp_geom* g, const pnp_stage* stages, int n_stages, const
     float* z = (float*)(ws + L.off_z);
     float* res = (float*)(ws + L.off_res);
     float* tvb = (float*)(ws + L.off_tv);
-    PNP_CUDA(launch_fill(y, img, 0.5f, st));
+    PNP_CUDA(launch_fill_hash(y, img, 0.0f, 1.0f, st));   // a noisy image: the denoiser's projections engage
     cudaEvent_t e0, e1;
     PNP_CUDA(cudaEventCreate(&e0));
     PNP_CUDA(cudaEventCreate(&e1));
-    // best of three batches of eight launches after two warm-up launches
+    // best of five batches of eight launches after two warm-up launches
     auto timeit = [&](auto&& fn, float* ms) -> int {
         for (int rep = 0; rep < 2; ++rep) if (int e = fn()) return e;
         float best = 1e30f;
-        for (int trial = 0; trial < 3; ++trial) {
+        for (int trial = 0; trial < 5; ++trial) {
             PNP_CUDA(cudaEventRecord(e0, st));
             for (int rep = 0; rep < 8; ++rep) if (int e = fn()) return e;
             PNP_CUDA(cudaEventRecord(e1, st));
@@ -1258,20 +1258,47 @@ int pnp_autotune(const pnp_geom* g, const pnp_stage* stages, int n_stages, const
     }
     const pnp_run_params& pr = *params;
     if (rc == PNP_OK && pr.tv_iters > 0 && pr.lambda > 0.0f) {
+        // a denoise as the run issues it (up to 20 FGP iterations), momentum, and, when
+        // a full-grid mini-batch stage follows, the level-1 coefficient image of y
+        // (from the shared-memory tiles' last launch, or a separate kernel after the
+        // register-resident variant, which does not write it)
+        bool fused = fuse_quad_enabled();
+        bool full_minibatch = false;
+        for (int k = 0; k < n_stages; ++k)
+            full_minibatch |= stages[k].factor == 1 &&
+                              (stages[k].n_subsets <= 1 || stages[k].estimator == PNP_EST_MINIBATCH);
+        fused = fused && full_minibatch;
+        const LevelLayout& l1 = L.lv[level_index(1)];
+        float* scratch = nullptr;                       // x_{i-1} and y of the timed denoise
+        PNP_CUDA(cudaMallocAsync((void**)&scratch, 2 * img * sizeof(float), st));
+        if (launch_fill_hash(scratch, 2 * img, 0.0f, 1.0f, st) != cudaSuccess) rc = fail(PNP_ECUDA, "fill failed");
         const int T0 = tile_tv_tile(g->n, g->batch);
+        const int iters = std::min(pr.tv_iters, 20);   // up to two launches, the last one with the ring
         float best = 1e30f;
-        const int iters = std::min(pr.tv_iters, 10);
         for (int T : {T0 - 6, T0 - 4, T0 - 2, T0, T0 + 2, T0 + 4, T0 + 6, 16, 24, 32, kTvTileWarp}) {
+            if (rc != PNP_OK) break;
             if (T != kTvTileWarp && (T < 8 || T > 40)) continue;
+            TvItem it{};
+            it.z = y; it.xprev = z; it.y = scratch + img; it.xin = scratch;
+            it.state_a = tvb; it.state_b = tvb + 4 * img;
+            it.n = g->n; it.batch = g->batch; it.tile = T; it.amom = 0.5f;
+            const bool own_prep = full_minibatch && T == kTvTileWarp;
+            if (fused && !own_prep) {
+                it.quad = (float4*)(ws + l1.off_quad);
+                it.qw = l1.qw;
+            }
             float ms = 0.0f;
             rc = timeit([&]() -> int {
-                PNP_CUDA(launch_tv_tiled(y, g->n, g->batch, pr.lambda, iters, 1.0f, 0.0f, z, nullptr, nullptr,
-                                         nullptr, tvb, tvb + 4 * img, st, T));
+                PNP_CUDA(launch_tv_tiled_multi(&it, 1, pr.lambda, iters, pr.alpha, st));
+                if (own_prep || (full_minibatch && !fused))
+                    PNP_CUDA(launch_prep_quad(scratch + img, g->n, 1, g->batch, (float4*)(ws + l1.off_quad), l1.qw,
+                                              st));
                 return PNP_OK;
             }, &ms);
             if (rc != PNP_OK) break;
             if (ms < best) { best = ms; tu.tile = T; }
         }
+        cudaFreeAsync(scratch, st);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -237,6 +237,7 @@ cudaError_t launch_reduce_final(const double* partials, int nparts, int batch, d
 cudaError_t launch_scale_by_rnorm(const float* w, float* u, size_t count, const double* norm2,
                                   cudaStream_t st);
 cudaError_t launch_fill(float* x, size_t count, float v, cudaStream_t st);
+cudaError_t launch_fill_hash(float* x, size_t count, float lo, float hi, cudaStream_t st);
 cudaError_t launch_copy(const float* src, float* dst, size_t count, cudaStream_t st);
 cudaError_t launch_count_samples(const int2* rayk, int n_det, int first_view, int view_step,
                                  int n_sub, double* partial, cudaStream_t st);

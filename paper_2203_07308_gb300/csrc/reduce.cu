@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdlib>
 
 #include "pnp_internal.cuh"
@@ -101,6 +102,22 @@ __global__ void k_fill(float* __restrict__ x, size_t count, float v)
         x[i] = v;
 }
 
+// x[i] = lo + (hi - lo) u_i, u_i in [0, 1) from an integer hash of i (the
+// "lowbias32" mixer: xor-shift / multiply rounds): a fixed noisy test image
+__global__ void k_fill_hash(float* __restrict__ x, size_t count, float lo, float hi)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (size_t)gridDim.x * blockDim.x) {
+        uint32_t h = (uint32_t)i * 0x9E3779B9u;
+        h ^= h >> 16;
+        h *= 0x7FEB352Du;
+        h ^= h >> 15;
+        h *= 0x846CA68Bu;
+        h ^= h >> 16;
+        x[i] = fmaf((float)(h >> 8) * (1.0f / 16777216.0f), hi - lo, lo);
+    }
+}
+
 __global__ void k_copy(const float* __restrict__ s, float* __restrict__ d, size_t count)
 {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
@@ -147,6 +164,12 @@ cudaError_t launch_scale_by_rnorm(const float* w, float* u, size_t count, const 
 cudaError_t launch_fill(float* x, size_t count, float v, cudaStream_t st)
 {
     k_fill<<<grid_for(count), 256, 0, st>>>(x, count, v);
+    return counted();
+}
+
+cudaError_t launch_fill_hash(float* x, size_t count, float lo, float hi, cudaStream_t st)
+{
+    k_fill_hash<<<grid_for(count), 256, 0, st>>>(x, count, lo, hi);
     return counted();
 }
 

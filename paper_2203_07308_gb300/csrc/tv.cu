@@ -117,7 +117,8 @@ __host__ __device__ inline int tile_pitch(int S) { return S + ((40 - S % 32) % 3
 // them) for the whole launch: their z, r and p stay in registers together with
 // the pixel's shared-memory offset and two Chebyshev distances that decide in
 // which iterations it is inside the shrinking regions.  Shared memory holds
-// only what neighbours read: r (phase A), x_tmp (phase B) and, at the end, p.
+// only what neighbours read: r (phase A; zero outside the image, so that the
+// edge rule of L needs no test there), x_tmp (phase B) and, at the end, p.
 template <int NP>
 __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
 {
@@ -173,8 +174,8 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
                 p1[m] = __ldg(a.sin + 2 * a.plane + g);
                 p2[m] = __ldg(a.sin + 3 * a.plane + g);
             }
-            rr[q[m]] = make_float2(r1[m], r2[m]);
         }
+        if (f < S * S) rr[q[m]] = make_float2(r1[m], r2[m]);
     }
     __syncthreads();
     for (int k = 1; k <= K; ++k) {
@@ -186,8 +187,8 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
             x0[m] = 0.0f;
             if (dA[m] <= mg) {
                 float l = r1[m] + r2[m];
-                if (flags[m] & 1) l -= rr[q[m] - P].x;
-                if (flags[m] & 2) l -= rr[q[m] - 1].y;
+                l -= rr[q[m] - P].x;
+                l -= rr[q[m] - 1].y;
                 x0[m] = z[m] - lam * l;
                 xt[q[m]] = x0[m];
             }
