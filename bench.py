@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--graph", action="store_true", help="replay a captured CUDA graph instead of direct launches")
     ap.add_argument("--no-autotune", action="store_true", help="heuristic launch shapes")
+    ap.add_argument("--shapes", default=None,
+                    help='pinned launch shapes instead of the autotuner, as printed in "launch_shapes", '
+                         'e.g. \'{"lanes": [16, 8, 0, 0], "back": [272, 280, 0, 0], "tile": 22}\' '
+                         '(for profiler runs, whose timing would mislead the autotuner)')
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched, mixed and differentiable comparisons")
     ap.add_argument("--profile", action="store_true",
@@ -563,7 +567,10 @@ def run_native(args, rank, world):
     eta = [1.0 / plan.power_iter(s.factor, 100, 1e-6)[0] for s in wl.stages]
     setup_ms = 1000 * (time.perf_counter() - t0)
     t0 = time.perf_counter()
-    if not args.no_autotune:
+    if args.shapes:
+        shp = json.loads(args.shapes)
+        plan.set_launch_shapes(lanes=tuple(shp["lanes"]), back=tuple(shp["back"]), tile=int(shp["tile"]))
+    elif not args.no_autotune:
         plan.autotune(wl.stages, alpha=wl.alpha, lam=wl.tv_lambda, tv_iters=wl.tv_iters)
     tune_ms = 1000 * (time.perf_counter() - t0)
     use_graph = args.graph
