@@ -291,12 +291,21 @@ int pnp_run_many(const pnp_problem* problems, int n_problems, const pnp_run_para
  *   lanes   forward projector lanes per ray: 4, 8 or 16
  *   back    backprojector CTA: G view groups (1..32) of 8 x 4 pixel blocks, or
  *           PNP_BACK_TILE4 | G: G view groups (1..64) of 4 x 4 pixel blocks
+ *           (the pixel-driven gather), or PNP_BACK_SCATTER | TS: the
+ *           sample-driven scatter on TS x TS tiles, TS in {12, 16, 22, 32}
  *   tile    FGP denoiser: side of the shared-memory tile (8..40), or 1 for the
  *           register-resident variant (warp tiles, five iterations per launch)
- * The backprojector's view groups fix its summation order: results are bitwise
- * reproducible for fixed shapes.  pnp_autotune sets them; pnp_set_launch_shapes
- * pins them (PNP_EINVAL for a shape outside these sets). */
+ * The gather's view groups fix its summation order: results are bitwise
+ * reproducible for fixed shapes.  The scatter adds each sample's four bilinear
+ * terms as 32-bit fixed-point integers (scale: the tile's largest |residual|
+ * maps to at most 2^21, lower where the geometry lets more terms reach one
+ * pixel within a chunk of views), so its sums do not depend on the order of
+ * the adds and are bitwise reproducible too; they differ from the gather's by
+ * that quantisation (relative ~1e-7 of the gradient).  pnp_autotune sets the
+ * shapes; pnp_set_launch_shapes pins them (PNP_EINVAL for a shape outside
+ * these sets). */
 #define PNP_BACK_TILE4 (1 << 8)
+#define PNP_BACK_SCATTER (1 << 9)
 typedef struct {
     int32_t lanes[4];
     int32_t back[4];

@@ -47,6 +47,7 @@ class LaunchShapes(C.Structure):
 
 
 BACK_TILE4 = 1 << 8     # backprojector CTAs of 4 x 4 pixel blocks (| view groups)
+BACK_SCATTER = 1 << 9   # backprojector as the fixed-point scatter (| tile side 12, 16, 22 or 32)
 
 SKETCH_POOL, SKETCH_BICUBIC = 0, 1
 EST_MINIBATCH, EST_SVRG, EST_SAGA = 0, 1, 2

@@ -317,10 +317,36 @@ FwdArgs fwd_args(const pnp_geom& g, const LevelLayout& lv, char* ws, int p, int 
     return a;
 }
 
+// Bound on the (ray, sample) terms that one level pixel receives from one view,
+// for the fixed-point scatter: the rays whose line passes within sqrt 2 of the
+// pixel centre (the hat support is the 2 x 2 square around it; adjacent rays
+// are at least delta apart there: their angular spacing, smallest at the
+// detector's edge bins, times the distance from the source, at least dso minus
+// the image's circumradius and the apron) times the samples of one ray inside
+// that square.
+float scatter_terms_bound(const pnp_geom& g, int factor)
+{
+    const double r2 = std::sqrt(2.0);
+    double dgam = 0.5 * M_PI;
+    if (g.n_det > 1) {
+        const double dsd = g.dso + g.ddo;
+        const double u1 = 0.5 * (g.n_det - 1) * g.det_pitch, u0 = u1 - g.det_pitch;
+        dgam = std::atan(u1 / dsd) - std::atan(u0 / dsd);
+    }
+    const double dmin = g.dso - (0.5 * g.n + 3.0 * factor) * r2;
+    if (!(dmin > 0.0) || !(dgam > 0.0)) return 0.0f;
+    const double delta = dmin * std::sin(std::min(dgam, 0.5 * M_PI)) / factor;
+    const double rays = std::floor(2.0 * r2 / delta) + 2.0;
+    const double samples = std::floor(2.0 * r2 / g.step) + 2.0;
+    const double b = rays * samples;
+    return b < 1e9 ? (float)b : 0.0f;
+}
+
 BackArgs back_args(const pnp_geom& g, const LevelLayout& lv, char* ws, int p, int P, const float* res,
                    int mode, float scale, const float* y, float eta, float* out, int batch)
 {
     BackArgs a{};
+    a.cmax = scatter_terms_bound(g, lv.factor);
     a.res = res;
     a.rayf = (const float4*)(ws + lv.off_rayf);
     a.rayi = (const float2*)(ws + lv.off_rayi);
@@ -1249,6 +1275,8 @@ int pnp_autotune(const pnp_geom* g, const pnp_stage* stages, int n_stages, const
         for (int G = 1; G <= 16 && G <= nsub; G *= 2) shapes.push_back(G);
         for (int G : {8, 12, 16, 18, 20, 24, 32, 64, nsub, (nsub + 1) / 2})
             if (G >= 8 && G <= 64 && G <= nsub) shapes.push_back(PNP_BACK_TILE4 | G);
+        // the fixed-point scatter on square tiles (where the geometry allows it)
+        for (int TS : {12, 16, 22, 32}) shapes.push_back(PNP_BACK_SCATTER | TS);
         for (int shp : shapes) {
             float ms = 0.0f;
             if (rc == PNP_OK)
@@ -1333,8 +1361,9 @@ int pnp_set_launch_shapes(const pnp_geom* g, const pnp_launch_shapes* in, void* 
         const int q = in->lanes[k], b = in->back[k];
         if (q != 0 && q != 4 && q != 8 && q != 16) return fail(PNP_EINVAL, "lanes[%d] = %d not in {0, 4, 8, 16}", k, q);
         const int bg = b & 0xff;
-        const bool ok = b == 0 || ((b & ~(PNP_BACK_TILE4 | 0xff)) == 0 && bg >= 1 &&
-                                   bg <= ((b & PNP_BACK_TILE4) ? 64 : 32));
+        const bool scatter = (b & ~0xff) == PNP_BACK_SCATTER && (bg == 12 || bg == 16 || bg == 22 || bg == 32);
+        const bool ok = b == 0 || scatter ||
+                        ((b & ~(PNP_BACK_TILE4 | 0xff)) == 0 && bg >= 1 && bg <= ((b & PNP_BACK_TILE4) ? 64 : 32));
         if (!ok) return fail(PNP_EINVAL, "back[%d] = %#x is not a backprojector shape", k, b);
         tu.lanes[k] = q;
         tu.groups[k] = b;

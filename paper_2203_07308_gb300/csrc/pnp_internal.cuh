@@ -157,8 +157,12 @@ struct BackArgs {
     float scale;                     // multiplies the gathered sum
     const float* y; float eta;       // mode 2: z = y - eta * scale * sum
     float* out;
+    float cmax = 0.0f;               // bound on the (ray, sample) terms one pixel receives from one
+                                     // view (scatter form; 0: scatter unavailable, gather used)
 };
-// `groups`: view groups per CTA of the 2x2-block gather (1..16, 0 = heuristic).
+// `groups`: view groups per CTA of the 2x2-block gather (1..16, 0 = heuristic),
+// PNP_BACK_TILE4 | G for 4 x 4-block CTAs, or PNP_BACK_SCATTER | TS for the
+// fixed-point scatter form on TS x TS tiles (TS in {12, 16, 22, 32}).
 cudaError_t launch_backward(const BackArgs& a, cudaStream_t st, int groups = 0);
 cudaError_t launch_backward_multi(const BackArgs* items, int count, cudaStream_t st, int groups = 0);
 

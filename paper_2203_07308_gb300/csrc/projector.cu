@@ -381,6 +381,189 @@ __global__ void __launch_bounds__(1024, 1) k_backward2x2(const BackTable t)
     }
 }
 
+// ------------------------------------------------------------------ transpose A_s^T, scatter form
+// CTA = one TS x TS tile of the level image of one instance, all views of the
+// subset.  Every sample of every ray that can touch the tile is splatted with
+// the weights of the forward interpolant, (1/2 -+ u)(1/2 -+ w) on the four
+// pixels of its cell, as a 32-bit fixed-point shared-memory atomic add: integer
+// sums do not depend on the order of the adds, so the result is deterministic.
+// Scale: the largest |r| among the rays that reach the tile maps to qmax, small
+// enough that no accumulator overflows within a chunk of views (one view per
+// warp), given the geometric bound cmax on the terms a pixel receives from one
+// view; after each chunk the integers are folded into FP32 totals in a fixed
+// order.  A two-pixel apron around the tile takes the terms of neighbouring
+// tiles' pixels (those tiles splat the same samples for their own pixels).
+// A lane walks the samples of a ray inside the tile grown by the hat support
+// (plus one sample each way), so every sample with a weight on the tile is
+// visited.  (Measured and dropped: two rays per lane, in two loops or one
+// fused loop, to even out the lanes' sample counts — 30 % slower; trimmed
+// sample ranges instead of clamped taps — 15 % slower.)  Tap positions are clamped to the apron, so a sample that
+// float rounding lets in from outside lands there.
+struct BackScTable {
+    BackArgs c[kMaxClasses];
+    long begin[kMaxClasses + 1];   // cumulative CTA counts (batch * tiles)
+    int count;
+    float qsum;                    // 2^30 / (views per chunk): qmax = min(2^21, qsum / cmax)
+};
+
+template <int TS, int NT>
+__global__ void __launch_bounds__(NT) k_backward_scatter(const BackScTable t)
+{
+    pdl_begin();
+    constexpr int AP = TS + 4;                  // accumulator side: the tile and a 2-pixel apron
+    constexpr int NW = NT / 32;                 // warps = views per chunk
+    constexpr int PPT = (TS * TS + NT - 1) / NT;
+    __shared__ int acc[AP * AP];
+    __shared__ float wmax[NW];
+    int c = 0;
+#pragma unroll
+    for (int k = 1; k < kMaxClasses; ++k)
+        if (k < t.count && (long)blockIdx.x >= t.begin[k]) c = k;
+    const BackArgs& a = t.c[c];
+    const int ns = a.ns;
+    const int tiles_x = (ns + TS - 1) / TS;
+    const int tiles = tiles_x * tiles_x;
+    const long local = (long)blockIdx.x - t.begin[c];
+    const int inst = (int)(local / tiles);
+    const int tile = (int)(local - (long)inst * tiles);
+    const int tx0 = (tile % tiles_x) * TS, ty0 = (tile / tiles_x) * TS;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < AP * AP; i += NT) acc[i] = 0;
+    const float* __restrict__ res = a.res + (long)inst * a.n_sub * a.n_det;
+    const float half = 0.5f * (float)(ns - 1);
+    const float jc = 0.5f * (float)(a.n_det - 1);
+    // bins of a view that can reach the tile: the central projection of the
+    // corners of the tile grown by the apron (a convex polygon projects onto the
+    // flat detector as the interval between its extreme corners), one bin wider
+    auto shadow = [&](const float4 vp, int& jlo, int& jhi) {
+        float lo = 1e30f, hi = -1e30f;
+        bool ok = true;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float x = (float)((q & 1) ? tx0 + TS + 1 : tx0 - 2) - half;
+            const float y = (float)((q & 2) ? ty0 + TS + 1 : ty0 - 2) - half;
+            const float along = x * vp.x + y * vp.y;
+            const float lat = y * vp.x - x * vp.y;
+            const float den = vp.z - along;
+            ok = ok && den > 1e-3f * vp.z;
+            const float uj = vp.w * lat / den + jc;
+            lo = fminf(lo, uj);
+            hi = fmaxf(hi, uj);
+        }
+        if (!ok) {
+            jlo = 0;
+            jhi = a.n_det - 1;
+            return;
+        }
+        jlo = max(0, (int)floorf(fmaxf(lo, -2.0f)) - 1);
+        jhi = min(a.n_det - 1, (int)ceilf(fminf(hi, (float)a.n_det + 1.0f)) + 1);
+    };
+    // the largest |r| that can reach the tile
+    float m = 0.0f;
+    for (int vs = wid; vs < a.n_sub; vs += NW) {
+        int jlo, jhi;
+        shadow(__ldg(a.view + a.first_view + vs * a.view_step), jlo, jhi);
+        const float* __restrict__ rrow = res + (long)vs * a.n_det;
+        for (int j = jlo + lane; j <= jhi; j += 32) m = fmaxf(m, fabsf(__ldg(rrow + j)));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) wmax[wid] = m;
+    __syncthreads();
+    float M = 0.0f;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) M = fmaxf(M, wmax[w]);
+    const float qmax = fminf(2097152.0f, t.qsum / a.cmax);
+    const float S = M > 0.0f ? qmax / M : 0.0f;
+    const int c0 = ns / 2;
+    const int biasx = kMagicBits - c0 + tx0;   // float_as_int(X' + kMagic) - biasx: tap a's column in acc
+    const int biasy = kMagicBits - c0 + ty0;
+    // sample region in the primed frame: index coordinates (tx0 - 1, tx0 + TS)
+    const float xlo = (float)(tx0 - c0) + 0.5f, xhi = (float)(tx0 + TS - c0) + 1.5f;
+    const float ylo = (float)(ty0 - c0) + 0.5f, yhi = (float)(ty0 + TS - c0) + 1.5f;
+    const float inv_step = 1.0f / a.step;
+    float tot[PPT];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) tot[q] = 0.0f;
+    for (int v0 = 0; v0 < a.n_sub; v0 += NW) {
+        const int vs = v0 + wid;
+        if (vs < a.n_sub) {
+            const int v = a.first_view + vs * a.view_step;
+            int jlo, jhi;
+            shadow(__ldg(a.view + v), jlo, jhi);
+            const long base = (long)v * a.n_det;
+            const float* __restrict__ rrow = res + (long)vs * a.n_det;
+            // lane = ray; lanes start five rays apart, so that the samples of one
+            // atomic instruction rarely share a pixel
+            for (int j = jlo + ((lane * 5) & 31); j <= jhi; j += 32) {
+                const float4 f = __ldg(a.rayf + base + j);
+                const float2 ri = __ldg(a.rayi + base + j);
+                const int2 kr = __ldg(a.rayk + base + j);
+                const float tx1 = (xlo - f.x) * ri.x, tx2 = (xhi - f.x) * ri.x;
+                const float ty1 = (ylo - f.y) * ri.y, ty2 = (yhi - f.y) * ri.y;
+                const float tlo = fmaxf(fminf(tx1, tx2), fminf(ty1, ty2));
+                const float thi = fminf(fmaxf(tx1, tx2), fmaxf(ty1, ty2));
+                const float fa = fmaxf(fmaf(tlo, inv_step, -0.5f), (float)kr.x - 2.0f);
+                const float fb = fminf(fmaf(thi, inv_step, -0.5f), (float)kr.y + 2.0f);
+                const int ka = max(kr.x, (int)ceilf(fa) - 1);
+                const int kb = min(kr.y, (int)floorf(fb) + 1);
+                const float rS = __ldg(rrow + j) * S;
+                for (int k = ka; k <= kb; ++k) {
+                    const float tt = ((float)k + 0.5f) * a.step;
+                    const float X = fmaf(tt, f.z, f.x);
+                    const float Y = fmaf(tt, f.w, f.y);
+                    const float mx = __fadd_rn(X, kMagic);
+                    const float my = __fadd_rn(Y, kMagic);
+                    const float u = __fsub_rn(X, __fsub_rn(mx, kMagic));
+                    const float w = __fsub_rn(Y, __fsub_rn(my, kMagic));
+                    const int lc = min(max(__float_as_int(mx) - biasx, 0), TS + 2);
+                    const int lr = min(max(__float_as_int(my) - biasy, 0), TS + 2);
+                    int* const p = acc + lr * AP + lc;
+                    const float r0 = rS * (0.5f - w), r1 = rS * (0.5f + w);
+                    const float ua = 0.5f - u, ub = 0.5f + u;
+                    atomicAdd(p, __float_as_int(fmaf(ua, r0, kMagic)) - kMagicBits);
+                    atomicAdd(p + 1, __float_as_int(fmaf(ub, r0, kMagic)) - kMagicBits);
+                    atomicAdd(p + AP, __float_as_int(fmaf(ua, r1, kMagic)) - kMagicBits);
+                    atomicAdd(p + AP + 1, __float_as_int(fmaf(ub, r1, kMagic)) - kMagicBits);
+                }
+            }
+        }
+        __syncthreads();
+        // fold the chunk into the totals and clear the tile's cells (the apron is never read)
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            const int pix = threadIdx.x + q * NT;
+            if (pix < TS * TS) {
+                int* const cell = acc + (pix / TS + 2) * AP + (pix % TS) + 2;
+                tot[q] += (float)*cell;
+                *cell = 0;
+            }
+        }
+        __syncthreads();
+    }
+    const float inv_s = S > 0.0f ? M / qmax : 0.0f;
+    const int s = a.s;
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        const int pix = threadIdx.x + q * NT;
+        const int ix = tx0 + pix % TS, iy = ty0 + pix / TS;
+        if (pix >= TS * TS || ix >= ns || iy >= ns) continue;
+        const float val = a.scale * (tot[q] * inv_s);
+        if (a.mode == kBackRaw) {
+            a.out[((long)inst * ns + iy) * ns + ix] = val;
+            continue;
+        }
+        for (int bb = 0; bb < s; ++bb) {
+            const long row = ((long)inst * a.n + (long)iy * s + bb) * a.n + (long)ix * s;
+            for (int aa = 0; aa < s; ++aa) {
+                if (a.mode == kBackGradFine)
+                    a.out[row + aa] = val;
+                else
+                    a.out[row + aa] = __ldg(a.y + row + aa) - a.eta * val;
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ bicubic S and S^T
 // The paper's sketch and upsampler are bicubic resizes (Sec. 3).  Here S is
 // separable: coarse pixel I (centre X_I = s I + (s-1)/2 in fine index units)
@@ -571,9 +754,53 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t st, int lanes)
     return launch_forward_multi(&a, 1, st, lanes);
 }
 
+namespace {
+template <int TS, int NT>
+cudaError_t scatter_launch(const BackArgs* items, int count, cudaStream_t st)
+{
+    BackScTable t{};
+    t.count = count;
+    t.begin[0] = 0;
+    for (int c = 0; c < count; ++c) {
+        t.c[c] = items[c];
+        const long tl = div_up(items[c].ns, TS);
+        t.begin[c + 1] = t.begin[c] + tl * tl * items[c].batch;
+    }
+    t.qsum = 1073741824.0f / (float)(NT / 32);
+    const cudaError_t e = launch_pdl(k_backward_scatter<TS, NT>, dim3((unsigned)t.begin[count]), dim3(NT), 0, st, t);
+    if (e != cudaSuccess) return e;
+    return counted();
+}
+
+// The scatter needs the geometric term bound of every class and a scale that
+// keeps at least 12 bits per term; otherwise the gather runs.
+bool scatter_usable(const BackArgs* items, int count, int nt)
+{
+    for (int c = 0; c < count; ++c) {
+        const float cm = items[c].cmax;
+        if (!(cm > 0.0f) || 1073741824.0f / (float)(nt / 32) / cm < 4096.0f) return false;
+    }
+    return true;
+}
+}  // namespace
+
 cudaError_t launch_backward_multi(const BackArgs* items, int count, cudaStream_t st, int groups)
 {
     if (count < 1 || count > kMaxClasses) return cudaErrorInvalidValue;
+    if (groups & PNP_BACK_SCATTER) {
+        const int ts = groups & 0xff;
+        const int nt = ts >= 22 ? 512 : 256;
+        if (scatter_usable(items, count, nt)) {
+            switch (ts) {
+                case 12: return scatter_launch<12, 256>(items, count, st);
+                case 16: return scatter_launch<16, 256>(items, count, st);
+                case 22: return scatter_launch<22, 512>(items, count, st);
+                case 32: return scatter_launch<32, 512>(items, count, st);
+                default: break;
+            }
+        }
+        groups = 0;
+    }
     // CTA shape: TX x 4 blocks x G view groups; PNP_BACK_TILE4 selects TX = 4
     const int TX = (groups & PNP_BACK_TILE4) ? 4 : kBack2TileX;
     int G = groups & 0xff;

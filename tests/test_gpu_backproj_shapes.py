@@ -1,5 +1,6 @@
-"""Every backprojector launch shape (8 x 4 or 4 x 4 pixel blocks per CTA and the
-number of view groups), pinned with pnp_set_launch_shapes, against the FP64
+"""Every backprojector launch shape (the gather's 8 x 4 or 4 x 4 pixel blocks per
+CTA and number of view groups; the fixed-point scatter's tile side), pinned
+with pnp_set_launch_shapes, against the FP64
 oracle on ragged sizes, limited-angle rays that miss the image, one view,
 sample steps other than half a pixel and every sketch level; the three
 epilogues (raw, gradient, fused step); bitwise repeatability per shape."""
@@ -26,8 +27,10 @@ GEOMS = {
     "wide": synth.make_geometry(100, 16, 160, batch=1),
 }
 T4 = 1 << 8     # CTAs of 4 x 4 pixel blocks
+SC = 1 << 9     # the fixed-point scatter on square tiles
 SHAPES = {**{f"groups{G}": G for G in (1, 2, 4, 8, 16, 32)},
-          **{f"tile4_groups{G}": T4 | G for G in (7, 16, 45, 64)}}
+          **{f"tile4_groups{G}": T4 | G for G in (7, 16, 45, 64)},
+          **{f"scatter{TS}": SC | TS for TS in (12, 16, 22, 32)}}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -93,7 +96,8 @@ def test_backprojection_every_shape(name, shape):
             assert np.array_equal(host(again), got)
 
 
-@pytest.mark.parametrize("shape", ["groups1", "groups16", "tile4_groups7", "tile4_groups64"])
+@pytest.mark.parametrize("shape", ["groups1", "groups16", "tile4_groups7", "tile4_groups64", "scatter12",
+                                   "scatter32"])
 @pytest.mark.parametrize("name,s,P", [("c1", 2, 5), ("ragged", 1, 3), ("ragged", 2, 1), ("step03", 4, 2)])
 def test_gradient_and_step_epilogues(name, s, P, shape):
     """Gradient on the fine grid (U = S^T) and, through a one-iteration PGD run,
@@ -145,9 +149,10 @@ def test_launch_shapes_validation():
     plan = pnp.Plan(g)
     assert plan.launch_shapes() == {"lanes": [0] * 4, "back": [0] * 4, "tile": 0}
     for bad in (dict(back=(33, 0, 0, 0)), dict(back=(T4 | 65, 0, 0, 0)), dict(back=(T4, 0, 0, 0)),
-                dict(back=(-1, 0, 0, 0)), dict(back=(1 << 9 | 4, 0, 0, 0)), dict(lanes=(2, 0, 0, 0)),
+                dict(back=(-1, 0, 0, 0)), dict(back=(SC | 4, 0, 0, 0)), dict(back=(SC | T4 | 16, 0, 0, 0)),
+                dict(back=(SC | 24, 0, 0, 0)), dict(lanes=(2, 0, 0, 0)),
                 dict(tile=50), dict(tile=2), dict(tile=7)):
         with pytest.raises(pnp.PnpError):
             plan.set_launch_shapes(**bad)
-    plan.set_launch_shapes(lanes=(8, 4, 0, 0), back=(16, T4 | 45, 3, 0), tile=24)
-    assert plan.launch_shapes() == {"lanes": [8, 4, 0, 0], "back": [16, T4 | 45, 3, 0], "tile": 24}
+    plan.set_launch_shapes(lanes=(8, 4, 0, 0), back=(16, T4 | 45, 3, SC | 22), tile=24)
+    assert plan.launch_shapes() == {"lanes": [8, 4, 0, 0], "back": [16, T4 | 45, 3, SC | 22], "tile": 24}
