@@ -137,40 +137,48 @@ __global__ void k_prep_quad(const PrepTable t)
 // k_lo + q + Q, ... of ray r into four interleaved partial sums (independent
 // chains keep four loads in flight); the four, then the Q lanes' sums, are
 // combined in a fixed order, so the result is deterministic.  One 16-byte load
-// per sample.
+// per sample.  A CTA (8 warps) takes 8R adjacent bins of one view; CTAs are
+// numbered from the detector's centre outwards, all views of a rank together,
+// so the long central rays go first and the last wave holds the short rays at
+// the fan's edges (a shorter tail than in bin order).
 struct FwdTable {
     FwdArgs c[kMaxClasses];
-    long begin[kMaxClasses + 1];   // cumulative ray counts (batch * n_sub * n_det)
+    long begin[kMaxClasses + 1];   // cumulative CTA counts (batch * n_sub * bin blocks)
     int count;
 };
 
+constexpr int kFwdWarps = 8;       // warps per forward CTA
+
 template <int Q>
-__global__ void __launch_bounds__(256, 4) k_forward(const FwdTable t)
+__global__ void __launch_bounds__(32 * kFwdWarps, 4) k_forward(const FwdTable t)
 {
     pdl_begin();
     constexpr int R = 32 / Q;
+    constexpr int RB = kFwdWarps * R;   // bins per CTA
     const int lane = threadIdx.x & 31;
-    const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int r = lane / Q, q = lane % Q;
-    const long gray = warp * R + r;
-    const bool active = gray < t.begin[t.count];
+    const long cta = blockIdx.x;
     int c = 0;
 #pragma unroll
     for (int k = 1; k < kMaxClasses; ++k)
-        if (k < t.count && gray >= t.begin[k]) c = k;
+        if (k < t.count && cta >= t.begin[k]) c = k;
     const FwdArgs& a = t.c[c];
+    const int nb = (a.n_det + RB - 1) / RB;
+    const long per_inst = (long)a.n_sub * nb;
+    const long local = cta - t.begin[c];
+    const int inst = (int)(local / per_inst);
+    const int rem = (int)(local - (long)inst * per_inst);
+    const int rank = rem / a.n_sub, vs = rem - rank * a.n_sub;
+    const int mid = nb >> 1;
+    const int blk = (rank & 1) ? mid - ((rank + 1) >> 1) : mid + (rank >> 1);
+    const int j = blk * RB + (threadIdx.x >> 5) * R + r;
+    const bool active = j < a.n_det;
     float acc = 0.0f;
     long out_idx = 0;
-    int v = 0, j = 0, inst = 0;
+    int v = 0;
     if (active) {
-        const long rays_inst = (long)a.n_sub * a.n_det;
-        const long local = gray - t.begin[c];
-        inst = (int)(local / rays_inst);
-        const long ray = local - (long)inst * rays_inst;
-        const int vs = (int)(ray / a.n_det);
-        j = (int)(ray - (long)vs * a.n_det);
         v = a.first_view + vs * a.view_step;
-        out_idx = local;
+        out_idx = ((long)inst * a.n_sub + vs) * a.n_det + j;
         const float4 f = __ldg(a.rayf + (long)v * a.n_det + j);
         const int2 kr = __ldg(a.rayk + (long)v * a.n_det + j);
         const float4* __restrict__ img = a.quad + (long)inst * a.quad_stride;
@@ -722,11 +730,12 @@ cudaError_t launch_prep_quad(const float* fine, int n, int s, int batch, float4*
 }
 
 template <int Q>
-cudaError_t forward_q(const FwdTable& t, cudaStream_t st)
+cudaError_t forward_q(FwdTable t, cudaStream_t st)
 {
-    const long rays = t.begin[t.count];
-    const long warps = (rays + (32 / Q) - 1) / (32 / Q);
-    return launch_pdl(k_forward<Q>, dim3(div_up(warps * 32, 256)), dim3(256), 0, st, t);
+    constexpr int RB = kFwdWarps * (32 / Q);
+    for (int c = 0; c < t.count; ++c)
+        t.begin[c + 1] = t.begin[c] + (long)t.c[c].batch * t.c[c].n_sub * div_up(t.c[c].n_det, RB);
+    return launch_pdl(k_forward<Q>, dim3((unsigned)t.begin[t.count]), dim3(32 * kFwdWarps), 0, st, t);
 }
 
 cudaError_t launch_forward_multi(const FwdArgs* items, int count, cudaStream_t st, int lanes)
@@ -735,11 +744,11 @@ cudaError_t launch_forward_multi(const FwdArgs* items, int count, cudaStream_t s
     FwdTable t{};
     t.count = count;
     t.begin[0] = 0;
+    long rays = 0;
     for (int c = 0; c < count; ++c) {
         t.c[c] = items[c];
-        t.begin[c + 1] = t.begin[c] + (long)items[c].batch * items[c].n_sub * items[c].n_det;
+        rays += (long)items[c].batch * items[c].n_sub * items[c].n_det;
     }
-    const long rays = t.begin[count];
     // lanes per ray: enough threads to fill the GPU (~2 waves of 152 x 2048),
     // unless the autotuner chose
     int Q = lanes;
