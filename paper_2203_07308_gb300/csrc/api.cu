@@ -941,8 +941,9 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
     long min_start = max_total;
     for (int c = 0; c < np; ++c) min_start = std::min(min_start, (long)pb[c].start_iter);
     const bool timed = (pr.flags & PNP_RUN_KERNEL_TIMES) != 0;
-    // the denoiser's last launch also writes the level-1 coefficient image of y
-    // when the next iteration is a full-grid mini-batch one (it then needs no prep)
+    // the denoiser's last launch also writes the coefficient image of the next
+    // iteration's level (full grid, or the 2x pooled sketch) when that iteration
+    // is a mini-batch one (it then needs no coefficient-image kernel)
     const bool fuse_quad = do_tv && !all_warp && fuse_quad_enabled();
     auto issue = [&]() -> int {
         int e0 = PNP_OK;
@@ -1009,7 +1010,7 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
                 } else {
                     bic[na] = 0;
                 }
-                need_prep[na] = !(quad_ready[c] && lv.factor == 1);
+                need_prep[na] = quad_ready[c] != lv.factor;
                 prep[na] = PrepArgs{y, g.n, lv.factor, g.batch, (float4*)(ws + lv.off_quad), lv.qw};
                 fwd[na] = fwd_args(g, lv, ws, p, P, q.d_b, res, g.batch, reg_weights(ws));
                 const double cs = P <= 1 ? 1.0 : (double)P;
@@ -1029,11 +1030,14 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
                     if (in_stage[c] >= q.stages[sn].iters)
                         do ++sn; while (q.stages[sn].iters == 0);
                     const pnp_stage& nx = q.stages[sn];
-                    if (nx.factor == 1 && (nx.n_subsets <= 1 || nx.estimator == PNP_EST_MINIBATCH)) {
-                        const LevelLayout& l1 = L.lv[level_index(1)];
-                        t.quad = (float4*)(ws + l1.off_quad);
-                        t.qw = l1.qw;
-                        quad_ready[c] = 1;
+                    const bool minibatch = nx.n_subsets <= 1 || nx.estimator == PNP_EST_MINIBATCH;
+                    const bool pooled = nx.factor == 1 || nx.kind == PNP_SKETCH_POOL;
+                    if (minibatch && pooled && tv_fuses_quad(ps[c].tuned.tile, g.n, g.batch, nx.factor)) {
+                        const LevelLayout& lq = L.lv[level_index(nx.factor)];
+                        t.quad = (float4*)(ws + lq.off_quad);
+                        t.qw = lq.qw;
+                        t.qs = nx.factor;
+                        quad_ready[c] = (char)nx.factor;
                     }
                 }
                 t.z = z; t.y = y; t.xtrue = q.d_xtrue;

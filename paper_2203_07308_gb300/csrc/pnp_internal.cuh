@@ -204,12 +204,16 @@ struct TvItem {
     int n, batch, tile;
     float amom;
     const float* xin = nullptr;            // x_{i-1} when it is not xprev (double-buffered x)
-    float4* quad = nullptr;                // shared-memory tiles only: also write the level-1
-    int qw = 0;                            // coefficient image of y (qw = n + 2 kPad - 1)
+    float4* quad = nullptr;                // shared-memory tiles only: also write the coefficient
+    int qw = 0;                            // image of S_qs y (qw = n/qs + 2 kPad - 1), qs = 1 or 2
+    int qs = 1;                            // (2: pooled; needs an even tile side and n)
 };
 cudaError_t launch_tv_tiled_multi(const TvItem* items, int count, float lambda, int iters, float alpha,
                                   cudaStream_t st);
 int tile_tv_parts_for(int n, int batch, int tile);
+// whether the shared-memory tiles' last launch can write the coefficient image of
+// S_qs y (qs = 1 always; qs = 2 for an even tile side and n); never for tile = 1
+bool tv_fuses_quad(int tile, int n, int batch, int qs);
 
 // Reverse mode (vjp.cu) ----------------------------------------------------------
 size_t tv_vjp_workspace_floats(int n, int batch, int iters);

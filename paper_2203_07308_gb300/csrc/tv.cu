@@ -94,8 +94,8 @@ struct TileTvClass {
     const float* z; const float* sin; float* sout;   // state planes [4][batch][n][n]: r1 r2 p1 p2
     float* xprev; float* y; const float* xtrue; double* mse_part;
     const float* xin;                                 // x_{i-1} (nullptr: xprev)
-    float4* quad;                                     // last launch: level-1 coefficient image of y
-    int qw, ring;                                     // ring = 1 when quad is written
+    float4* quad;                                     // last launch: coefficient image of S_qs y
+    int qw, qs, ring;                                 // qs = 1 or 2; ring = qs when quad is written
     int n, T, tiles_x, tiles;
     long plane;
     float amom;
@@ -134,8 +134,8 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
     const int inst = (int)(local / a.tiles);
     const int tile = (int)(local - (long)inst * a.tiles);
     const int i0 = (tile / tiles_x) * T, j0 = (tile % tiles_x) * T;
-    // with ring = 1 the region (and every R_k) reaches one row and column further
-    // below/right, so that y is also known on the ring around the tile
+    // with ring = 1 or 2 the region (and every R_k) reaches that many rows and
+    // columns further below/right, so that y is also known on the ring around the tile
     const int ring = a.ring;
     const int S = T + 1 + 2 * K + ring;          // side of the loaded region
     const int P = tile_pitch(S);
@@ -246,8 +246,8 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
         const int li = f / S, lj = f - li * S;
         const int i = oi + li, j = oj + lj;
         const bool own = flags[m] & 16;
-        const bool rim = ring && f < S * S && !own && i >= i0 && j >= j0 && i <= i0 + T && j <= j0 + T &&
-                         i < n && j < n;
+        const bool rim = ring && f < S * S && !own && i >= i0 && j >= j0 && i < i0 + T + ring &&
+                         j < j0 + T + ring && i < n && j < n;
         if (own || rim) {
             float l = p1[m] + p2[m];
             if (flags[m] & 1) l -= pp[q[m] - P].x;
@@ -272,16 +272,24 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
         }
     }
     if (ring) {
-        // coefficient cells whose lower corner lies in the tile; the first tiles
-        // of a row/column also take the padding cells before the image, the last
-        // ones the cell after it (corners outside the image are zero)
+        // coefficient cells of the level-qs image whose lower corner lies in the
+        // tile; the first tiles of a row/column also take the padding cells before
+        // the image, the last ones the cell after it (corners outside are zero).
+        // Level pixel (r, c) is the qs x qs average of y, summed in the order of
+        // the separate coefficient-image kernel, so the two agree bit for bit.
         __syncthreads();
-        const int r_lo = i0 == 0 ? -kPad : i0, r_hi = i0 + T >= n ? n + 1 : i0 + T;
-        const int c_lo = j0 == 0 ? -kPad : j0, c_hi = j0 + T >= n ? n + 1 : j0 + T;
+        const int qs = a.qs, ns = n / qs;
+        const int r_lo = i0 == 0 ? -kPad : i0 / qs, r_hi = i0 + T >= n ? ns + 1 : (i0 + T) / qs;
+        const int c_lo = j0 == 0 ? -kPad : j0 / qs, c_hi = j0 + T >= n ? ns + 1 : (j0 + T) / qs;
         const int cw = c_hi - c_lo, cells = (r_hi - r_lo) * cw;
         float4* qimg = a.quad + (long)inst * a.qw * a.qw;
         auto Y = [&](int r, int c) -> float {
-            return (r < 0 || c < 0 || r >= n || c >= n) ? 0.0f : ys[(r - oi) * P + (c - oj)];
+            if (r < 0 || c < 0 || r >= ns || c >= ns) return 0.0f;
+            if (qs == 1) return ys[(r - oi) * P + (c - oj)];
+            float acc = 0.0f;
+            for (int bb = 0; bb < qs; ++bb)
+                for (int aa = 0; aa < qs; ++aa) acc += ys[(r * qs + bb - oi) * P + (c * qs + aa - oj)];
+            return acc * (1.0f / (float)(qs * qs));
         };
         for (int k = threadIdx.x; k < cells; k += blockDim.x) {
             const int r = r_lo + k / cw, c = c_lo + k % cw;
@@ -497,7 +505,7 @@ int choose_tile(int n, int batch)
     int best = 16;
     double best_cost = 1e300;
     for (int T = 8; T <= 40; ++T) {
-        if (tile_smem(T, kTileKMax, 1) > kTileSmemMax || tile_np(T, kTileKMax, 1) > 4) break;
+        if (tile_smem(T, kTileKMax, 2) > kTileSmemMax || tile_np(T, kTileKMax, 2) > 4) break;
         const long tiles = (long)batch * ((n + T - 1) / T) * ((n + T - 1) / T);
         const long waves = (tiles + 151) / 152;
         const double side = (double)std::min(T, n) + 1 + kTileKMax;
@@ -517,9 +525,16 @@ int tile_tv_tile(int n, int batch) { return choose_tile(n, batch); }
 // else the default.
 int resolve_tile(int tile, int n, int batch)
 {
-    if (tile < 4 || tile > 64 || tile_np(tile, kTileKMax, 1) > 4 || tile_smem(tile, kTileKMax, 1) > kTileSmemMax)
+    if (tile < 4 || tile > 64 || tile_np(tile, kTileKMax, 2) > 4 || tile_smem(tile, kTileKMax, 2) > kTileSmemMax)
         return tile_tv_tile(n, batch);
     return tile;
+}
+
+bool tv_fuses_quad(int tile, int n, int batch, int qs)
+{
+    if (tile == kTvTileWarp) return false;
+    if (qs == 1) return true;
+    return qs == 2 && n % 2 == 0 && resolve_tile(tile, n, batch) % 2 == 0;
 }
 
 int tile_tv_parts_for(int n, int batch, int tile)
@@ -610,7 +625,7 @@ cudaError_t launch_tv_tiled_multi(const TvItem* items, int count, float lambda, 
         if (iters > kTileKMax && (!it.state_a || !it.state_b)) return cudaErrorInvalidValue;   // chaining needs state
         TileTvClass& tc = a.c[c];
         tc.z = it.z; tc.xprev = it.xprev; tc.y = it.y; tc.xtrue = it.xtrue; tc.mse_part = it.mse_part;
-        tc.xin = it.xin; tc.quad = it.quad; tc.qw = it.qw;
+        tc.xin = it.xin; tc.quad = it.quad; tc.qw = it.qw; tc.qs = it.qs;
         tc.n = it.n; tc.T = T; tc.tiles_x = (it.n + T - 1) / T; tc.tiles = tc.tiles_x * tc.tiles_x;
         tc.plane = (long)it.batch * it.n * it.n;
         tc.amom = it.amom;
@@ -631,8 +646,11 @@ cudaError_t launch_tv_tiled_multi(const TvItem* items, int count, float lambda, 
             float* sb = items[c].state_b;
             a.c[c].sin = k0 == 0 ? nullptr : (pass % 2 == 1 ? sa : sb);
             a.c[c].sout = a.last ? nullptr : (pass % 2 == 0 ? sa : sb);
-            // the coefficient image needs y on a one-pixel ring: last launch only
-            a.c[c].ring = a.last && items[c].quad && items[c].y && items[c].xin ? 1 : 0;
+            // the coefficient image needs y on a ring of qs pixels: last launch only
+            const bool fuse = a.last && items[c].quad && items[c].y && items[c].xin &&
+                              tv_fuses_quad(items[c].tile, items[c].n, items[c].batch, items[c].qs);
+            a.c[c].ring = fuse ? items[c].qs : 0;
+            a.c[c].qs = items[c].qs;
             ring = std::max(ring, a.c[c].ring);
         }
         for (int k = 0; k < K; ++k) a.mom[k] = mom[k0 + k];

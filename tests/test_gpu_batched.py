@@ -181,6 +181,7 @@ def test_phase_event_timing():
     stages = [synth.Stage(2, 3, 5), synth.Stage(1, 4, 5)]
     x, b, eta, seq = make_problem(g, stages, 11)
     plan = pnp.Plan(g)
+    plan.set_launch_shapes(tile=16)
     outs = []
     pnp.kernel_times(reset=True)
     for timed in (False, True):
@@ -190,12 +191,13 @@ def test_phase_event_timing():
     assert np.array_equal(outs[0], outs[1])
     kt = pnp.kernel_times(reset=True)
     assert set(kt) == {"prep", "forward", "backward", "denoise"}
-    # the full-grid iterations take y's coefficient image from the denoiser's last
-    # launch of the iteration before (unless PNP_FUSE_QUAD=0): prep only at factor 2
+    # every iteration after the first takes y's coefficient image (2x pooled or full
+    # grid; tiles of even side) from the denoiser's last launch of the iteration
+    # before, unless PNP_FUSE_QUAD=0: the coefficient-image kernel runs once
     import os
     fused = os.environ.get("PNP_FUSE_QUAD", "1")[:1] != "0"
     for ph, (ms, n) in kt.items():
-        assert n == (3 if fused and ph == "prep" else 7), (ph, n)
+        assert n == (1 if fused and ph == "prep" else 7), (ph, n)
         assert ms > 0.0, ph
     assert all(n == 0 for _, n in pnp.kernel_times().values())
     with pytest.raises(pnp.PnpError):
