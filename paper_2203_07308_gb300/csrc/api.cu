@@ -936,7 +936,6 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
     }
     long max_total = 0;
     for (const auto& q : ps) max_total = std::max(max_total, q.total);
-    const bool one = np == 1;
 
     long min_start = max_total;
     for (int c = 0; c < np; ++c) min_start = std::min(min_start, (long)pb[c].start_iter);
@@ -975,6 +974,7 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
             int act[kMaxClasses];
             int bic[kMaxClasses];
             int need_prep[kMaxClasses];
+            int lvl[kMaxClasses];
             int na = 0;
             const float amom = pr.momentum ? (float)((double)(i - 1) / (double)(i + 3)) : 0.0f;
             for (int c = 0; c < np; ++c) {
@@ -1011,6 +1011,7 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
                     bic[na] = 0;
                 }
                 need_prep[na] = quad_ready[c] != lv.factor;
+                lvl[na] = li;
                 prep[na] = PrepArgs{y, g.n, lv.factor, g.batch, (float4*)(ws + lv.off_quad), lv.qw};
                 fwd[na] = fwd_args(g, lv, ws, p, P, q.d_b, res, g.batch, reg_weights(ws));
                 const double cs = P <= 1 ? 1.0 : (double)P;
@@ -1050,11 +1051,22 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
                 (void)li;
             }
             if (na == 0) break;
-            const Tuned& tu = ps[act[0]].tuned;
-            int li0 = 0;
-            if (one) {
-                const pnp_problem& q = pb[0];
-                li0 = level_index(q.stages[stage[0]].factor);
+            // one launch shape per phase: the tuned one of the class with the most
+            // level pixels in it (the only class when there is one)
+            int lanes_sel = 0, groups_sel = 0;
+            {
+                double wmax = -1.0;
+                for (int a = 0; a < na; ++a) {
+                    if (bic[a]) continue;
+                    const pnp_geom& g = pb[act[a]].geom;
+                    const double ns = (double)g.n / (double)(1 << lvl[a]);
+                    const double work = (double)g.batch * ns * ns;
+                    if (work > wmax) {
+                        wmax = work;
+                        lanes_sel = ps[act[a]].tuned.lanes[lvl[a]];
+                        groups_sel = ps[act[a]].tuned.groups[lvl[a]];
+                    }
+                }
             }
             {   // pooled-sketch classes share one launch per phase
                 PrepArgs pp[kMaxClasses];
@@ -1075,10 +1087,10 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
                 }
                 if (m > 0) {
                     if (timed && (e0 = g_timer.mark(PNP_PHASE_FORWARD, st, true))) return e0;
-                    PNP_CUDA(launch_forward_multi(ff, m, st, one ? tu.lanes[li0] : 0));
+                    PNP_CUDA(launch_forward_multi(ff, m, st, lanes_sel));
                     if (timed && (e0 = g_timer.mark(PNP_PHASE_FORWARD, st, false))) return e0;
                     if (timed && (e0 = g_timer.mark(PNP_PHASE_BACKWARD, st, true))) return e0;
-                    PNP_CUDA(launch_backward_multi(bb, m, st, one ? tu.groups[li0] : 0));
+                    PNP_CUDA(launch_backward_multi(bb, m, st, groups_sel));
                     if (timed && (e0 = g_timer.mark(PNP_PHASE_BACKWARD, st, false))) return e0;
                 }
             }
