@@ -116,7 +116,7 @@ Layout make_layout(const pnp_geom& g)
     L.off_res = off; off = align_up(off + (size_t)g.batch * nr * sizeof(float));
     L.off_y = off; off = align_up(off + img * sizeof(float));
     L.off_z = off; off = align_up(off + img * sizeof(float));
-    L.off_x2 = off; off = align_up(off + img * sizeof(float));
+    L.off_x2 = off; off = align_up(off + 2 * img * sizeof(float));
     L.off_tv = off; off = align_up(off + 8 * img * sizeof(float));
     L.off_pw = off; off = align_up(off + 2 * (size_t)g.n * g.n * sizeof(float));
     L.off_cs = off; off = align_up(off + 2 * (size_t)g.batch * (g.n / 2) * (g.n / 2) * sizeof(float));
@@ -1313,8 +1313,7 @@ int pnp_autotune(const pnp_geom* g, const pnp_stage* stages, int n_stages, const
                               (stages[k].n_subsets <= 1 || stages[k].estimator == PNP_EST_MINIBATCH);
         fused = fused && full_minibatch;
         const LevelLayout& l1 = L.lv[level_index(1)];
-        float* scratch = nullptr;                       // x_{i-1} and y of the timed denoise
-        PNP_CUDA(cudaMallocAsync((void**)&scratch, 2 * img * sizeof(float), st));
+        float* scratch = (float*)(ws + L.off_x2);       // x_{i-1} and y of the timed denoise
         if (launch_fill_hash(scratch, 2 * img, 0.0f, 1.0f, st) != cudaSuccess) rc = fail(PNP_ECUDA, "fill failed");
         const int T0 = tile_tv_tile(g->n, g->batch);
         const int iters = std::min(pr.tv_iters, 20);   // up to two launches, the last one with the ring
@@ -1342,7 +1341,6 @@ int pnp_autotune(const pnp_geom* g, const pnp_stage* stages, int n_stages, const
             if (rc != PNP_OK) break;
             if (ms < best) { best = ms; tu.tile = T; }
         }
-        cudaFreeAsync(scratch, st);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -103,7 +103,8 @@ struct Layout {
     size_t off_res = 0;      // float [batch][n_views][n_det]
     size_t off_y = 0;        // float [batch][n][n]
     size_t off_z = 0;        // float [batch][n][n]
-    size_t off_x2 = 0;       // float [batch][n][n]  second buffer of the iterate x (odd iterations)
+    size_t off_x2 = 0;       // float [2][batch][n][n]  second buffer of the iterate x (odd iterations);
+                             // the autotuner's timed denoise uses both images
     size_t off_tv = 0;       // float [8][batch][n][n]  TV state ping/pong (r1 r2 p1 p2)
     size_t off_pw = 0;       // float [2][n][n]   power iteration u, w
     size_t off_cs = 0;       // float [2][batch][(n/2)^2] bicubic coarse image and coarse gradient
