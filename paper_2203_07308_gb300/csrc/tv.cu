@@ -283,17 +283,30 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
         const int c_lo = j0 == 0 ? -kPad : j0 / qs, c_hi = j0 + T >= n ? ns + 1 : (j0 + T) / qs;
         const int cw = c_hi - c_lo, cells = (r_hi - r_lo) * cw;
         float4* qimg = a.quad + (long)inst * a.qw * a.qw;
-        auto Y = [&](int r, int c) -> float {
-            if (r < 0 || c < 0 || r >= ns || c >= ns) return 0.0f;
-            if (qs == 1) return ys[(r - oi) * P + (c - oj)];
-            float acc = 0.0f;
-            for (int bb = 0; bb < qs; ++bb)
-                for (int aa = 0; aa < qs; ++aa) acc += ys[(r * qs + bb - oi) * P + (c * qs + aa - oj)];
-            return acc * (1.0f / (float)(qs * qs));
-        };
-        for (int k = threadIdx.x; k < cells; k += blockDim.x) {
-            const int r = r_lo + k / cw, c = c_lo + k % cw;
-            qimg[(long)(r + kPad) * a.qw + (c + kPad)] = make_quad(Y(r, c), Y(r, c + 1), Y(r + 1, c), Y(r + 1, c + 1));
+        auto inside = [&](int r, int c) { return r >= 0 && c >= 0 && r < ns && c < ns; };
+        if (qs == 1) {
+            auto Y = [&](int r, int c) -> float { return inside(r, c) ? ys[(r - oi) * P + (c - oj)] : 0.0f; };
+            for (int k = threadIdx.x; k < cells; k += blockDim.x) {
+                const int r = r_lo + k / cw, c = c_lo + k % cw;
+                qimg[(long)(r + kPad) * a.qw + (c + kPad)] =
+                    make_quad(Y(r, c), Y(r, c + 1), Y(r + 1, c), Y(r + 1, c + 1));
+            }
+        } else {
+            auto Y = [&](int r, int c) -> float {
+                if (!inside(r, c)) return 0.0f;
+                const float* p0 = ys + (2 * r - oi) * P + (2 * c - oj);
+                float acc = 0.0f;
+                acc += p0[0];
+                acc += p0[1];
+                acc += p0[P];
+                acc += p0[P + 1];
+                return acc * 0.25f;
+            };
+            for (int k = threadIdx.x; k < cells; k += blockDim.x) {
+                const int r = r_lo + k / cw, c = c_lo + k % cw;
+                qimg[(long)(r + kPad) * a.qw + (c + kPad)] =
+                    make_quad(Y(r, c), Y(r, c + 1), Y(r + 1, c), Y(r + 1, c + 1));
+            }
         }
     }
     if (a.mse_part) {
