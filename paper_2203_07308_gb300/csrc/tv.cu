@@ -119,7 +119,7 @@ __host__ __device__ inline int tile_pitch(int S) { return S + ((40 - S % 32) % 3
 // which iterations it is inside the shrinking regions.  Shared memory holds
 // only what neighbours read: r (phase A; zero outside the image, so that the
 // edge rule of L needs no test there), x_tmp (phase B) and, at the end, p.
-template <int NP>
+template <int NP, bool LAST>
 __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
 {
     pdl_begin();
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
         }
         __syncthreads();
     }
-    if (!t.last) {
+    if (!LAST) {
 #pragma unroll
         for (int m = 0; m < NP; ++m) {
             if (flags[m] & 16) {
@@ -611,10 +611,15 @@ cudaError_t launch_tv_tiled_multi(const TvItem* items, int count, float lambda, 
 {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_tv_tile<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemMax);
-        cudaFuncSetAttribute(k_tv_tile<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemMax);
-        cudaFuncSetAttribute(k_tv_tile<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemMax);
-        cudaFuncSetAttribute(k_tv_tile<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemMax);
+        const int mx = (int)kTileSmemMax;
+        cudaFuncSetAttribute(k_tv_tile<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_tv_tile<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_tv_tile<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_tv_tile<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_tv_tile<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_tv_tile<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_tv_tile<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_tv_tile<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         attr = true;
     }
     if (count < 1 || count > kMaxClasses || iters < 1) return cudaErrorInvalidValue;
@@ -671,10 +676,14 @@ cudaError_t launch_tv_tiled_multi(const TvItem* items, int count, float lambda, 
         const size_t sm = tile_smem(Tmax, K, ring);
         const dim3 blk(kTileThreads);
         switch (tile_np(Tmax, K, ring)) {
-            case 1: e = launch_pdl(k_tv_tile<1>, grd, blk, sm, st, a); break;
-            case 2: e = launch_pdl(k_tv_tile<2>, grd, blk, sm, st, a); break;
-            case 3: e = launch_pdl(k_tv_tile<3>, grd, blk, sm, st, a); break;
-            default: e = launch_pdl(k_tv_tile<4>, grd, blk, sm, st, a); break;
+            case 1: e = a.last ? launch_pdl(k_tv_tile<1, true>, grd, blk, sm, st, a)
+                               : launch_pdl(k_tv_tile<1, false>, grd, blk, sm, st, a); break;
+            case 2: e = a.last ? launch_pdl(k_tv_tile<2, true>, grd, blk, sm, st, a)
+                               : launch_pdl(k_tv_tile<2, false>, grd, blk, sm, st, a); break;
+            case 3: e = a.last ? launch_pdl(k_tv_tile<3, true>, grd, blk, sm, st, a)
+                               : launch_pdl(k_tv_tile<3, false>, grd, blk, sm, st, a); break;
+            default: e = a.last ? launch_pdl(k_tv_tile<4, true>, grd, blk, sm, st, a)
+                                : launch_pdl(k_tv_tile<4, false>, grd, blk, sm, st, a); break;
         }
         g_launches.fetch_add(1, std::memory_order_relaxed);
         if (e != cudaSuccess) return e;
