@@ -301,7 +301,11 @@ int pnp_run_many(const pnp_problem* problems, int n_problems, const pnp_run_para
  * maps to at most 2^21, lower where the geometry lets more terms reach one
  * pixel within a chunk of views), so its sums do not depend on the order of
  * the adds and are bitwise reproducible too; they differ from the gather's by
- * that quantisation (relative ~1e-7 of the gradient).  pnp_autotune sets the
+ * that quantisation: about 2^-21 of the tile's largest |residual| per term, so
+ * the error grows with the residual's dynamic range within a tile (measured
+ * 2-3e-6 relative for residuals spread over three decades, 8e-7 for the FP32
+ * gather, which has no such dependence and is the shape to pin where that
+ * matters).  pnp_autotune sets the
  * shapes; pnp_set_launch_shapes pins them (PNP_EINVAL for a shape outside
  * these sets). */
 #define PNP_BACK_TILE4 (1 << 8)
