@@ -305,7 +305,8 @@ int pnp_run_many(const pnp_problem* problems, int n_problems, const pnp_run_para
  * the error grows with the residual's dynamic range within a tile (measured
  * 2-3e-6 relative for residuals spread over three decades, 8e-7 for the FP32
  * gather, which has no such dependence and is the shape to pin where that
- * matters).  pnp_autotune sets the
+ * matters); a non-finite residual turns the outputs of every scatter tile its
+ * ray can reach into NaN.  pnp_autotune sets the
  * shapes; pnp_set_launch_shapes pins them (PNP_EINVAL for a shape outside
  * these sets). */
 #define PNP_BACK_TILE4 (1 << 8)

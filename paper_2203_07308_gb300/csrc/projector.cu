@@ -466,22 +466,28 @@ __global__ void __launch_bounds__(NT) k_backward_scatter(const BackScTable t)
         jlo = max(0, (int)floorf(fmaxf(lo, -2.0f)) - 1);
         jhi = min(a.n_det - 1, (int)ceilf(fminf(hi, (float)a.n_det + 1.0f)) + 1);
     };
-    // the largest |r| that can reach the tile
+    // the largest |r| that can reach the tile; a non-finite one makes the tile's
+    // outputs NaN (fixed point cannot carry it)
     float m = 0.0f;
+    int bad = 0;
     for (int vs = wid; vs < a.n_sub; vs += NW) {
         int jlo, jhi;
         shadow(__ldg(a.view + a.first_view + vs * a.view_step), jlo, jhi);
         const float* __restrict__ rrow = res + (long)vs * a.n_det;
-        for (int j = jlo + lane; j <= jhi; j += 32) m = fmaxf(m, fabsf(__ldg(rrow + j)));
+        for (int j = jlo + lane; j <= jhi; j += 32) {
+            const float rv = fabsf(__ldg(rrow + j));
+            bad |= !(rv <= 3.402823466e38f);
+            m = fmaxf(m, rv);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) wmax[wid] = m;
-    __syncthreads();
+    const bool nonfinite = __syncthreads_or(bad) != 0;
     float M = 0.0f;
 #pragma unroll
     for (int w = 0; w < NW; ++w) M = fmaxf(M, wmax[w]);
     const float qmax = fminf(2097152.0f, t.qsum / a.cmax);
-    const float S = M > 0.0f ? qmax / M : 0.0f;
+    const float S = M > 0.0f && !nonfinite ? qmax / M : 0.0f;
     const int c0 = ns / 2;
     const int biasx = kMagicBits - c0 + tx0;   // float_as_int(X' + kMagic) - biasx: tap a's column in acc
     const int biasy = kMagicBits - c0 + ty0;
@@ -555,7 +561,7 @@ __global__ void __launch_bounds__(NT) k_backward_scatter(const BackScTable t)
         const int pix = threadIdx.x + q * NT;
         const int ix = tx0 + pix % TS, iy = ty0 + pix / TS;
         if (pix >= TS * TS || ix >= ns || iy >= ns) continue;
-        const float val = a.scale * (tot[q] * inv_s);
+        const float val = nonfinite ? __int_as_float(0x7FC00000) : a.scale * (tot[q] * inv_s);
         if (a.mode == kBackRaw) {
             a.out[((long)inst * ns + iy) * ns + ix] = val;
             continue;

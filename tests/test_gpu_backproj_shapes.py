@@ -178,3 +178,26 @@ def test_scatter_precision_follows_the_residual_range():
     print("relative L2 error by shape:", errs)
     assert errs["groups16"] < TOL, errs
     assert errs["scatter16"] < TOL and errs["scatter32"] < TOL, errs
+
+
+def test_nonfinite_residual_propagates():
+    """A NaN or infinite residual cannot be carried in fixed point: the scatter
+    turns the outputs of every tile its ray reaches into NaN (the gather, those
+    of the pixels the ray touches); tiles it does not reach stay exact."""
+    g = GEOMS["c1"]
+    rng = np.random.default_rng(23)
+    y = f32(rng.standard_normal((g.batch, g.n_views, g.n_det)))
+    ref = np.stack([oracle.backproject(g, 1, y[i]) for i in range(g.batch)])
+    for bad in (float("nan"), float("inf")):
+        yb = y.copy()
+        yb[0, 5, 3] = bad                  # one ray near the fan's edge, instance 0
+        for name in ("groups16", "scatter16"):
+            plan = pinned(g, SHAPES[name])
+            out = empty(g.batch, g.n, g.n)
+            plan.backproject(1, dev(yb), out)
+            got = host(out)
+            assert not np.isfinite(got[0]).all(), (name, bad)
+            ok = np.isfinite(got[0])
+            assert ok.any(), name
+            assert rel(got[0][ok], ref[0][ok]) < TOL, name
+            assert rel(got[1], ref[1]) < TOL, name     # the other instance is untouched
