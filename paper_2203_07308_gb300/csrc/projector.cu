@@ -403,10 +403,11 @@ __global__ void __launch_bounds__(1024, 1) k_backward2x2(const BackTable t)
 // tiles' pixels (those tiles splat the same samples for their own pixels).
 // A lane walks the samples of a ray inside the tile grown by the hat support
 // (plus one sample each way), so every sample with a weight on the tile is
-// visited.  (Measured and dropped: two rays per lane, in two loops or one
-// fused loop, to even out the lanes' sample counts — 30 % slower; trimmed
-// sample ranges instead of clamped taps — 15 % slower.)  Tap positions are clamped to the apron, so a sample that
-// float rounding lets in from outside lands there.
+// visited; tap positions are clamped to the apron, so a sample that float
+// rounding lets in from outside lands there.  (Measured and dropped: two rays
+// per lane, in two loops or one fused loop, to even out the lanes' sample
+// counts, 30 % slower; sample ranges trimmed instead of clamped taps, 15 %
+// slower.)
 struct BackScTable {
     BackArgs c[kMaxClasses];
     long begin[kMaxClasses + 1];   // cumulative CTA counts (batch * tiles)
