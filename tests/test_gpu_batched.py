@@ -90,6 +90,34 @@ def test_run_many_uneven_classes():
         assert np.abs(log - rl).max() < 1e-3
 
 
+@pytest.mark.parametrize("back", [1 << 9 | 16, 1 << 8 | 8])
+def test_run_many_takes_the_largest_class_shapes(back):
+    """One launch per phase uses the tuned (here pinned) projector shapes of the
+    class with the most level pixels: the fixed-point scatter or 4 x 4-block
+    gather pinned on the 64^2 class runs every class's backprojection, and every
+    class still matches the oracle."""
+    import torch
+    specs = [
+        (synth.make_geometry(32, 20, 48, batch=3), [synth.Stage(2, 3, 4), synth.Stage(1, 4, 4)]),
+        (synth.make_geometry(64, 30, 96, batch=2), [synth.Stage(2, 3, 1), synth.Stage(1, 3, 2)]),
+    ]
+    problems, refs = [], []
+    for k, (g, stages) in enumerate(specs):
+        x, b, eta, seq = make_problem(g, stages, 300 + 10 * k)
+        plan = pnp.Plan(g)
+        if g.n == 64:
+            plan.set_launch_shapes(lanes=(4, 4, 0, 0), back=(back, back, 0, 0))
+        d_x = torch.zeros(g.batch, g.n, g.n, device="cuda")
+        problems.append(dict(plan=plan, stages=stages, eta=eta, seq=seq, b=dev(b), x=d_x, xtrue=dev(x)))
+        refs.append((g, stages, eta, seq, b, x))
+    logs = pnp.run_many(problems, lam=0.02, tv_iters=20)
+    for prob, (g, stages, eta, seq, b, x), log in zip(problems, refs, logs):
+        rx, rl = oracle_runs(g, stages, eta, seq, b, x, 0.02)
+        got = host(prob["x"])
+        assert rel(got, rx) < TOL_RECON, rel(got, rx)
+        assert np.abs(log - rl).max() < 1e-3
+
+
 def test_graph_replay_matches_direct_launches():
     import torch
     g = synth.make_geometry(64, 60, 96, batch=2)
