@@ -144,6 +144,25 @@ def test_full_size_256_every_shape():
             assert rel(host(out)[0], refs[s]) < TOL, (shape, s, rel(host(out)[0], refs[s]))
 
 
+def test_full_size_512_batch_scatter_and_gather():
+    """16 x 512^2 / 720 x 768 with 12 subsets (the batched workload, where the
+    autotuner picks the scatter at the full grid): a 60-view subset
+    backprojection of the whole batch with the scatter on 32 x 32 tiles and the
+    default gather, two sampled instances against the oracle."""
+    wl = synth.workloads()["c3_512x16"]
+    g = wl.geom
+    nsub = pnp.subset_views(g, 5, 12)
+    y = f32(np.random.default_rng(41).standard_normal((g.batch, nsub, g.n_det)))
+    refs = {i: oracle.backproject(g, 1, y[i], 5, 12) for i in (0, 11)}
+    for shape in (SC | 32, T4 | 16):
+        plan = pinned(g, shape)
+        out = empty(g.batch, g.n, g.n)
+        plan.backproject(1, dev(y), out, 5, 12)
+        got = host(out)
+        for i, ref in refs.items():
+            assert rel(got[i], ref) < TOL, (shape, i, rel(got[i], ref))
+
+
 def test_launch_shapes_validation():
     g = GEOMS["c1"]
     plan = pnp.Plan(g)
