@@ -630,7 +630,7 @@ int pnp_project(const pnp_geom* g, int factor, const float* d_img, const float* 
     t_err.clear();
     if (int e = validate_geom(g)) return e;
     Layout L = make_layout(*g);
-    int li;
+    int li = 0;
     if (int e = check_level(*g, factor, L, &li)) return e;
     if (int e = check_subset(*g, subset, n_subsets)) return e;
     if (!d_img || !d_sino) return fail(PNP_EINVAL, "image or sinogram pointer is NULL");
@@ -649,7 +649,7 @@ int pnp_backproject(const pnp_geom* g, int factor, const float* d_sino, float* d
     t_err.clear();
     if (int e = validate_geom(g)) return e;
     Layout L = make_layout(*g);
-    int li;
+    int li = 0;
     if (int e = check_level(*g, factor, L, &li)) return e;
     if (int e = check_subset(*g, subset, n_subsets)) return e;
     if (!d_img || !d_sino) return fail(PNP_EINVAL, "image or sinogram pointer is NULL");
@@ -666,7 +666,7 @@ int pnp_sketch_kind(const pnp_geom* g, int factor, int kind, const float* d_fine
     t_err.clear();
     if (int e = validate_geom(g)) return e;
     Layout L = make_layout(*g);
-    int li;
+    int li = 0;
     if (int e = check_level(*g, factor, L, &li)) return e;
     if (kind != PNP_SKETCH_POOL && kind != PNP_SKETCH_BICUBIC) return fail(PNP_EINVAL, "unknown sketch kind %d", kind);
     if (!d_fine || !d_coarse) return fail(PNP_EINVAL, "image pointer is NULL");
@@ -688,7 +688,7 @@ int pnp_upsample_kind(const pnp_geom* g, int factor, int kind, const float* d_co
     t_err.clear();
     if (int e = validate_geom(g)) return e;
     Layout L = make_layout(*g);
-    int li;
+    int li = 0;
     if (int e = check_level(*g, factor, L, &li)) return e;
     if (kind != PNP_SKETCH_POOL && kind != PNP_SKETCH_BICUBIC) return fail(PNP_EINVAL, "unknown sketch kind %d", kind);
     if (!d_fine || !d_coarse) return fail(PNP_EINVAL, "image pointer is NULL");
@@ -717,7 +717,7 @@ int pnp_sketch_grad_kind(const pnp_geom* g, int factor, int kind, const float* d
     if (kind != PNP_SKETCH_POOL && kind != PNP_SKETCH_BICUBIC) return fail(PNP_EINVAL, "unknown sketch kind %d", kind);
     if (int e = validate_geom(g)) return e;
     Layout L = make_layout(*g);
-    int li;
+    int li = 0;
     if (int e = check_level(*g, factor, L, &li)) return e;
     if (int e = check_subset(*g, subset, n_subsets)) return e;
     if (!d_y || !d_b || !d_g) return fail(PNP_EINVAL, "y, b or g pointer is NULL");
@@ -781,7 +781,7 @@ int pnp_power_iter_kind(const pnp_geom* g, int factor, int kind, int max_iters, 
     if (kind != PNP_SKETCH_POOL && kind != PNP_SKETCH_BICUBIC) return fail(PNP_EINVAL, "unknown sketch kind %d", kind);
     if (int e = validate_geom(g)) return e;
     Layout L = make_layout(*g);
-    int li;
+    int li = 0;
     if (int e = check_level(*g, factor, L, &li)) return e;
     if (max_iters < 1 || !(tol >= 0.0)) return fail(PNP_EINVAL, "need max_iters >= 1 and tol >= 0");
     if (!h_L) return fail(PNP_EINVAL, "h_L is NULL");
@@ -859,7 +859,7 @@ int validate_problem(const pnp_problem& q, const pnp_run_params& pr, int idx, Pr
     long total = 0;
     bool any_subsets = false;
     for (int k = 0; k < q.n_stages; ++k) {
-        int li;
+        int li = 0;
         if (int e = check_level(*g, q.stages[k].factor, out->L, &li)) return e;
         if (q.stages[k].iters < 0) return fail(PNP_EINVAL, "stage %d has negative iterations", k);
         if (q.stages[k].n_subsets < 1 || q.stages[k].n_subsets > g->n_views)
@@ -1234,7 +1234,7 @@ int pnp_autotune(const pnp_geom* g, const pnp_stage* stages, int n_stages, const
     if (int e = check_ws(*g, d_ws)) return e;
     Layout L = make_layout(*g);
     for (int k = 0; k < n_stages; ++k) {
-        int li;
+        int li = 0;
         if (int e = check_level(*g, stages[k].factor, L, &li)) return e;
         if (stages[k].n_subsets < 1 || stages[k].n_subsets > g->n_views)
             return fail(PNP_EINVAL, "stage %d: n_subsets outside [1, n_views]", k);
@@ -1434,7 +1434,7 @@ int pnp_sample_count(const pnp_geom* g, int factor, int subset, int n_subsets, d
     t_err.clear();
     if (int e = validate_geom(g)) return e;
     Layout L = make_layout(*g);
-    int li;
+    int li = 0;
     if (int e = check_level(*g, factor, L, &li)) return e;
     if (int e = check_subset(*g, subset, n_subsets)) return e;
     if (!h_count) return fail(PNP_EINVAL, "h_count is NULL");
@@ -1541,7 +1541,7 @@ int unrolled_step_impl(const pnp_geom* g, int factor, int subset, int n_subsets,
 {
     t_err.clear();
     Layout L;
-    int li;
+    int li = 0;
     if (int e = check_step(g, factor, subset, n_subsets, eta, params, &L, &li)) return e;
     if (!d_y || !d_xprev || !d_b || !d_xout || !d_yout) return fail(PNP_EINVAL, "y, xprev, b, xout, yout required");
     if (d_xout == d_y || d_yout == d_y || d_xout == d_yout || d_xout == d_xprev)
@@ -1576,7 +1576,7 @@ int unrolled_step_vjp_impl(const pnp_geom* g, int factor, int subset, int n_subs
 {
     t_err.clear();
     Layout L;
-    int li;
+    int li = 0;
     if (int e = check_step(g, factor, subset, n_subsets, eta, params, &L, &li)) return e;
     if (!(d_zsaved || (d_y && d_b)) || !d_xbar || !d_ybar || !d_ybar_in || !d_xpbar)
         return fail(PNP_EINVAL, "z (or y and b), xbar, ybar, ybar_in, xpbar required");

@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
         }
         __syncthreads();
     }
-    if (!LAST) {
+    if constexpr (!LAST) {
 #pragma unroll
         for (int m = 0; m < NP; ++m) {
             if (flags[m] & 16) {
@@ -231,93 +231,93 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
                 a.sout[3 * a.plane + g] = p2[m];
             }
         }
-        return;
-    }
-    // x = z - lambda L(p) on the tile (and its ring), relaxation, momentum, squared error
+    } else {
+        // x = z - lambda L(p) on the tile (and its ring), relaxation, momentum, squared error
 #pragma unroll
-    for (int m = 0; m < NP; ++m)
-        if (dB[m] == 0) pp[q[m]] = make_float2(p1[m], p2[m]);
-    __syncthreads();
-    double e2 = 0.0;
-    float* ys = xt;                     // y on the tile and its ring, for the coefficient image
+        for (int m = 0; m < NP; ++m)
+            if (dB[m] == 0) pp[q[m]] = make_float2(p1[m], p2[m]);
+        __syncthreads();
+        double e2 = 0.0;
+        float* ys = xt;                     // y on the tile and its ring, for the coefficient image
 #pragma unroll
-    for (int m = 0; m < NP; ++m) {
-        const int f = threadIdx.x + m * blockDim.x;
-        const int li = f / S, lj = f - li * S;
-        const int i = oi + li, j = oj + lj;
-        const bool own = flags[m] & 16;
-        const bool rim = ring && f < S * S && !own && i >= i0 && j >= j0 && i < i0 + T + ring &&
-                         j < j0 + T + ring && i < n && j < n;
-        if (own || rim) {
-            float l = p1[m] + p2[m];
-            if (flags[m] & 1) l -= pp[q[m] - P].x;
-            if (flags[m] & 2) l -= pp[q[m] - 1].y;
-            const float x = z[m] - lam * l;
-            const float xi = (1.0f - t.alpha) * z[m] + t.alpha * x;
-            const long g = img + (long)i * n + j;
-            float yv = 0.0f;
-            if (a.y) {
-                const float xp = a.xin ? a.xin[g] : a.xprev[g];
-                yv = xi + a.amom * (xi - xp);
+        for (int m = 0; m < NP; ++m) {
+            const int f = threadIdx.x + m * blockDim.x;
+            const int li = f / S, lj = f - li * S;
+            const int i = oi + li, j = oj + lj;
+            const bool own = flags[m] & 16;
+            const bool rim = ring && f < S * S && !own && i >= i0 && j >= j0 && i < i0 + T + ring &&
+                             j < j0 + T + ring && i < n && j < n;
+            if (own || rim) {
+                float l = p1[m] + p2[m];
+                if (flags[m] & 1) l -= pp[q[m] - P].x;
+                if (flags[m] & 2) l -= pp[q[m] - 1].y;
+                const float x = z[m] - lam * l;
+                const float xi = (1.0f - t.alpha) * z[m] + t.alpha * x;
+                const long g = img + (long)i * n + j;
+                float yv = 0.0f;
+                if (a.y) {
+                    const float xp = a.xin ? a.xin[g] : a.xprev[g];
+                    yv = xi + a.amom * (xi - xp);
+                }
+                if (own) {
+                    if (a.y) a.y[g] = yv;
+                    a.xprev[g] = xi;
+                    if (a.xtrue) {
+                        const double d = (double)xi - (double)__ldg(a.xtrue + g);
+                        e2 += d * d;
+                    }
+                }
+                if (ring) ys[q[m]] = yv;
             }
-            if (own) {
-                if (a.y) a.y[g] = yv;
-                a.xprev[g] = xi;
-                if (a.xtrue) {
-                    const double d = (double)xi - (double)__ldg(a.xtrue + g);
-                    e2 += d * d;
+        }
+        if (ring) {
+            // coefficient cells of the level-qs image whose lower corner lies in the
+            // tile; the first tiles of a row/column also take the padding cells before
+            // the image, the last ones the cell after it (corners outside are zero).
+            // Level pixel (r, c) is the qs x qs average of y, summed in the order of
+            // the separate coefficient-image kernel, so the two agree bit for bit.
+            __syncthreads();
+            const int qs = a.qs, ns = n / qs;
+            const int r_lo = i0 == 0 ? -kPad : i0 / qs, r_hi = i0 + T >= n ? ns + 1 : (i0 + T) / qs;
+            const int c_lo = j0 == 0 ? -kPad : j0 / qs, c_hi = j0 + T >= n ? ns + 1 : (j0 + T) / qs;
+            const int cw = c_hi - c_lo, cells = (r_hi - r_lo) * cw;
+            float4* qimg = a.quad + (long)inst * a.qw * a.qw;
+            auto inside = [&](int r, int c) { return r >= 0 && c >= 0 && r < ns && c < ns; };
+            if (qs == 1) {
+                auto Y = [&](int r, int c) -> float { return inside(r, c) ? ys[(r - oi) * P + (c - oj)] : 0.0f; };
+                for (int k = threadIdx.x; k < cells; k += blockDim.x) {
+                    const int r = r_lo + k / cw, c = c_lo + k % cw;
+                    qimg[(long)(r + kPad) * a.qw + (c + kPad)] =
+                        make_quad(Y(r, c), Y(r, c + 1), Y(r + 1, c), Y(r + 1, c + 1));
+                }
+            } else {
+                auto Y = [&](int r, int c) -> float {
+                    if (!inside(r, c)) return 0.0f;
+                    const float* p0 = ys + (2 * r - oi) * P + (2 * c - oj);
+                    float acc = 0.0f;
+                    acc += p0[0];
+                    acc += p0[1];
+                    acc += p0[P];
+                    acc += p0[P + 1];
+                    return acc * 0.25f;
+                };
+                for (int k = threadIdx.x; k < cells; k += blockDim.x) {
+                    const int r = r_lo + k / cw, c = c_lo + k % cw;
+                    qimg[(long)(r + kPad) * a.qw + (c + kPad)] =
+                        make_quad(Y(r, c), Y(r, c + 1), Y(r + 1, c), Y(r + 1, c + 1));
                 }
             }
-            if (ring) ys[q[m]] = yv;
         }
-    }
-    if (ring) {
-        // coefficient cells of the level-qs image whose lower corner lies in the
-        // tile; the first tiles of a row/column also take the padding cells before
-        // the image, the last ones the cell after it (corners outside are zero).
-        // Level pixel (r, c) is the qs x qs average of y, summed in the order of
-        // the separate coefficient-image kernel, so the two agree bit for bit.
-        __syncthreads();
-        const int qs = a.qs, ns = n / qs;
-        const int r_lo = i0 == 0 ? -kPad : i0 / qs, r_hi = i0 + T >= n ? ns + 1 : (i0 + T) / qs;
-        const int c_lo = j0 == 0 ? -kPad : j0 / qs, c_hi = j0 + T >= n ? ns + 1 : (j0 + T) / qs;
-        const int cw = c_hi - c_lo, cells = (r_hi - r_lo) * cw;
-        float4* qimg = a.quad + (long)inst * a.qw * a.qw;
-        auto inside = [&](int r, int c) { return r >= 0 && c >= 0 && r < ns && c < ns; };
-        if (qs == 1) {
-            auto Y = [&](int r, int c) -> float { return inside(r, c) ? ys[(r - oi) * P + (c - oj)] : 0.0f; };
-            for (int k = threadIdx.x; k < cells; k += blockDim.x) {
-                const int r = r_lo + k / cw, c = c_lo + k % cw;
-                qimg[(long)(r + kPad) * a.qw + (c + kPad)] =
-                    make_quad(Y(r, c), Y(r, c + 1), Y(r + 1, c), Y(r + 1, c + 1));
+        if (a.mse_part) {
+            __shared__ double red[32];
+            for (int off = 16; off > 0; off >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, off);
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e2;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double v = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+                a.mse_part[(long)inst * a.tiles + tile] = v;
             }
-        } else {
-            auto Y = [&](int r, int c) -> float {
-                if (!inside(r, c)) return 0.0f;
-                const float* p0 = ys + (2 * r - oi) * P + (2 * c - oj);
-                float acc = 0.0f;
-                acc += p0[0];
-                acc += p0[1];
-                acc += p0[P];
-                acc += p0[P + 1];
-                return acc * 0.25f;
-            };
-            for (int k = threadIdx.x; k < cells; k += blockDim.x) {
-                const int r = r_lo + k / cw, c = c_lo + k % cw;
-                qimg[(long)(r + kPad) * a.qw + (c + kPad)] =
-                    make_quad(Y(r, c), Y(r, c + 1), Y(r + 1, c), Y(r + 1, c + 1));
-            }
-        }
-    }
-    if (a.mse_part) {
-        __shared__ double red[32];
-        for (int off = 16; off > 0; off >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, off);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e2;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double v = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
-            a.mse_part[(long)inst * a.tiles + tile] = v;
         }
     }
 }
