@@ -109,9 +109,11 @@ struct TileTvArgs {
     float mom[kTileMaxK];
 };
 
-// Row stride of the shared arrays: at least S and congruent to 8 mod 32, so
-// that rows sit on distinct bank offsets.
-__host__ __device__ inline int tile_pitch(int S) { return S + ((40 - S % 32) % 32); }
+// Row stride of the shared arrays, one constant for every region side (S <= 64
+// with at most four pixels per thread): congruent to 8 mod 32, so that rows sit
+// on distinct bank offsets, and known at compile time, so that the neighbour
+// offsets +-1 and +-P fold into the shared-memory instructions.
+constexpr int kTilePitch = 72;
 
 // Thread t owns the region pixels with flat index t, t + 1024, ... (NP of
 // them) for the whole launch: their z, r and p stay in registers together with
@@ -138,7 +140,7 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
     // columns further below/right, so that y is also known on the ring around the tile
     const int ring = a.ring;
     const int S = T + 1 + 2 * K + ring;          // side of the loaded region
-    const int P = tile_pitch(S);
+    constexpr int P = kTilePitch;
     const int oi = i0 - 1 - K, oj = j0 - 1 - K;  // its origin (may lie outside the image)
     extern __shared__ float sm[];
     float2* rr = reinterpret_cast<float2*>(sm);          // (r1, r2)   [S][P]
@@ -501,7 +503,7 @@ constexpr size_t kTileSmemMax = 112 * 1024;
 inline size_t tile_smem(int T, int K, int ring = 0)
 {
     const int S = T + 1 + 2 * K + ring;
-    return (size_t)5 * S * tile_pitch(S) * sizeof(float);
+    return (size_t)5 * S * kTilePitch * sizeof(float);
 }
 
 // pixels per thread needed to cover the (T + 1 + 2K + ring)^2 region with 1024 threads
@@ -672,6 +674,7 @@ cudaError_t launch_tv_tiled_multi(const TvItem* items, int count, float lambda, 
             ring = std::max(ring, a.c[c].ring);
         }
         for (int k = 0; k < K; ++k) a.mom[k] = mom[k0 + k];
+        if (Tmax + 1 + 2 * K + ring > kTilePitch) return cudaErrorInvalidValue;   // rows would overlap
         const dim3 grd((unsigned)a.begin[count]);
         const size_t sm = tile_smem(Tmax, K, ring);
         const dim3 blk(kTileThreads);
