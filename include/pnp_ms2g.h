@@ -52,7 +52,7 @@ enum {
     PNP_EINVAL = 1,        /* bad argument (size, pointer, factor, subset, geometry) */
     PNP_ECUDA = 2,         /* a CUDA runtime call or launch failed */
     PNP_ETIMEOUT = 3,      /* a bounded device-side wait gave up */
-    PNP_EUNSUPPORTED = 4,  /* valid request this build does not handle */
+    PNP_EUNSUPPORTED = 4,  /* valid request the library does not handle */
     PNP_ESTATE = 5         /* workspace not prepared by pnp_setup for this geometry */
 };
 
