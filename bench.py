@@ -15,6 +15,7 @@ step a bounded sample of the same schedule).  Prints one JSON line (rank 0).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -369,21 +370,27 @@ def _device_ms(fn, stream):
     return a.elapsed_time(b)
 
 
+def cut_schedule(stages, iters):
+    """The schedule stopped after `iters` iterations: every stage kept (with its
+    sketch kind and estimator), its iteration count cut, so that the step sizes
+    and the subset sequence stay aligned with the full schedule."""
+    cut, left = [], iters
+    for st_ in stages:
+        k = max(0, min(st_.iters, left))
+        cut.append(dataclasses.replace(st_, iters=k))
+        left -= k
+    return cut
+
+
 def _time_to_target(plan, stages, eta, seq, d_b, d_x, log, target, kw, stream):
     """Device time of the run cut at the first iteration whose mean PSNR reaches target."""
-    from paper_2203_07308_gb300 import synth
     hit = np.nonzero(log.mean(axis=1) >= target)[0]
     if hit.size == 0:
         return None, None
     it = int(hit[0]) + 1
-    cut, left = [], it
-    for st_ in stages:
-        k = min(st_.iters, left)
-        if k > 0:
-            cut.append(synth.Stage(st_.factor, k, st_.n_subsets))
-        left -= k
-    plan.run(cut, eta[:len(cut)], seq, d_b, d_x.zero_(), **kw)     # warm
-    return _device_ms(lambda: plan.run(cut, eta[:len(cut)], seq, d_b, d_x.zero_(), **kw), stream), it
+    cut = cut_schedule(stages, it)
+    plan.run(cut, eta, seq, d_b, d_x.zero_(), **kw)     # warm
+    return _device_ms(lambda: plan.run(cut, eta, seq, d_b, d_x.zero_(), **kw), stream), it
 
 
 def batched_512x16(dev, stream):
@@ -491,14 +498,8 @@ def mixed_64(dev, stream):
             hit = np.nonzero(log.mean(axis=1) >= target)[0]
             it = int(hit[0]) + 1 if hit.size else int(log.shape[0])
             hits.append(it)
-            cut, left = [], it
-            for st_ in p_["stages"]:
-                k = min(st_.iters, left)
-                if k > 0:
-                    cut.append(synth.Stage(st_.factor, k, st_.n_subsets))
-                left -= k
-            cut_probs.append(dict(plan=p_["plan"], b=p_["b"], x=p_["x"], stages=cut,
-                                  eta=p_["eta"][:len(cut)], seq=p_["seq"]))
+            cut_probs.append(dict(plan=p_["plan"], b=p_["b"], x=p_["x"], stages=cut_schedule(p_["stages"], it),
+                                  eta=p_["eta"], seq=p_["seq"]))
         run = lambda: pnp.run_many(fresh(cut_probs), **kw)      # noqa: E731
         run()
         arms[name] = {"ms": _device_ms(run, stream), "iters_per_class": hits}
@@ -692,17 +693,11 @@ def run_native(args, rank, world):
         if hit.size == 0:
             return None, None
         it = int(hit[0]) + 1
-        cut, left = [], it
-        for s in stages:
-            k = min(s.iters, left)
-            if k > 0:
-                cut.append(synth.Stage(s.factor, k, s.n_subsets))
-            left -= k
-        eta_c = etas[:len(cut)]
+        cut = cut_schedule(stages, it)
 
         def go():
             d_x.zero_()
-            plan.run(cut, eta_c, sq, d_b, d_x, **kw)
+            plan.run(cut, etas, sq, d_b, d_x, **kw)
         return timed(go, reps=5), it
 
     tts_s, it_s = time_to(wl.stages, eta, seq, log_s)
