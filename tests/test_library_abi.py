@@ -71,3 +71,33 @@ def test_estimator_buffer_sizes(lib):
     assert saga == 5 * img + max(3 * 2 * 32 * 32 * 4, 2 * img)
     with pytest.raises(pnp.PnpError):
         pnp.vr_buffer_size(g, [synth.Stage(3, 5, 3, estimator=1)])
+
+
+def test_binding_constants_match_the_header():
+    """Every constant the Python binding restates equals the C header's value
+    (error codes, sketch kinds, estimators, run flags, phases, launch-shape
+    flags, limits), so the two cannot drift apart."""
+    import re
+    from paper_2203_07308_gb300 import _native as N
+    text = open(N.HEADER).read()
+
+    def define(name):
+        m = re.search(r"#define\s+%s\s+(.+)" % name, text)
+        assert m, name
+        expr = m.group(1).split("/*")[0].strip().replace("u <<", " <<").replace("u)", ")")
+        return eval(expr, {})                     # plain integer expressions: 0, (1 << 8), (32 << 20)
+
+    codes = {k: int(v) for k, v in re.findall(r"(PNP_E[A-Z]+|PNP_OK)\s*=\s*(\d+)", text)}
+    assert codes == {"PNP_OK": N.PNP_OK, "PNP_EINVAL": N.PNP_EINVAL, "PNP_ECUDA": N.PNP_ECUDA,
+                     "PNP_ETIMEOUT": N.PNP_ETIMEOUT, "PNP_EUNSUPPORTED": N.PNP_EUNSUPPORTED,
+                     "PNP_ESTATE": N.PNP_ESTATE}
+    pairs = {"PNP_SKETCH_POOL": N.SKETCH_POOL, "PNP_SKETCH_BICUBIC": N.SKETCH_BICUBIC,
+             "PNP_EST_MINIBATCH": N.EST_MINIBATCH, "PNP_EST_SVRG": N.EST_SVRG, "PNP_EST_SAGA": N.EST_SAGA,
+             "PNP_RUN_GRAPH": N.RUN_GRAPH, "PNP_RUN_KERNEL_TIMES": N.RUN_KERNEL_TIMES,
+             "PNP_BACK_TILE4": N.BACK_TILE4, "PNP_BACK_SCATTER": N.BACK_SCATTER,
+             "PNP_MAX_LOG_ITERS": N.MAX_LOG_ITERS, "PNP_NOALLOC_SCRATCH_BYTES": N.NOALLOC_SCRATCH_BYTES,
+             "PNP_N_PHASES": len(N.PHASES)}
+    for name, value in pairs.items():
+        assert define(name) == value, name
+    for k, ph in enumerate(N.PHASES):
+        assert define("PNP_PHASE_" + ph.upper()) == k, ph
