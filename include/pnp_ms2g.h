@@ -307,8 +307,9 @@ int pnp_run_many(const pnp_problem* problems, int n_problems, const pnp_run_para
  * gather, which has no such dependence and is the shape to pin where that
  * matters); a non-finite residual turns the outputs of every scatter tile its
  * ray can reach into NaN.  pnp_autotune sets the
- * shapes; pnp_set_launch_shapes pins them (PNP_EINVAL for a shape outside
- * these sets). */
+ * shapes, choosing among the gather's shapes only (the scatter's error depends
+ * on the data, so it runs only where pnp_set_launch_shapes pins it);
+ * pnp_set_launch_shapes pins them (PNP_EINVAL for a shape outside these sets). */
 #define PNP_BACK_TILE4 (1 << 8)
 #define PNP_BACK_SCATTER (1 << 9)
 typedef struct {
@@ -320,7 +321,7 @@ int pnp_get_launch_shapes(const pnp_geom* g, pnp_launch_shapes* out, void* d_ws)
 int pnp_set_launch_shapes(const pnp_geom* g, const pnp_launch_shapes* in, void* d_ws);
 
 /* Times the launch shapes of this geometry's kernels on d_ws's own buffers
- * (forward lanes per ray 4/8/16 and backprojector view groups 1..16 for each
+ * (forward lanes per ray 4/8/16 and the gather backprojector's view groups for each
  * sketch level of the schedule, using its first angle subset; the FGP tile side
  * around the cost-model choice) and records the fastest for later calls that
  * use d_ws.  Shapes change only the order of floating-point sums (results stay
@@ -414,13 +415,19 @@ int pnp_unrolled_step_vjp_saved(const pnp_geom* g, int factor, int subset, int n
  * The paper has no counterpart; it is an interface for such callers.
  *   It allocates nothing and takes no workspace: its scratch lives in a fixed
  *   PNP_NOALLOC_SCRATCH_BYTES array compiled into the library.  A geometry needs
- *   24 B per ray and 16 B per view (ray tables), plus per batch image 16 (n+3)^2 B
- *   (coefficient image) and 4 B per ray (residual), each part rounded up to
- *   256 B; e.g. 256x256 with 360 views x 512 bins needs about 6.3 MB.
- *   Geometries that need more are rejected with PNP_EINVAL and a message.
+ *   32 B per ray (rayf 16, rayi 8, rayk 8) and 16 B per view (ray tables), plus
+ *   per batch image 16 (n+3)^2 B (coefficient image) and 4 B per ray (residual),
+ *   each part rounded up to 256 B; e.g. 256x256 with 360 views x 512 bins needs
+ *   about 7.7 MB.  Geometries that need more are rejected with PNP_EINVAL and a
+ *   message.
+ *   It is always the unweighted gradient: weights registered with
+ *   pnp_set_weights belong to a workspace and do not apply here, so it equals
+ *   pnp_full_grad only for a workspace without weights.
  *   The first call on a device looks up the array's device address (once per
- *   device, with that device current); make that first call before any stream
- *   capture.
+ *   device, with that device current) and keeps it for the life of the process;
+ *   make that first call before any stream capture.  The address is not valid
+ *   across cudaDeviceReset: a process that resets a device must not call this
+ *   entry point on it afterwards.
  *   All calls share the array: calls that overlap on the GPU (other streams or
  *   host threads) race and give wrong results; order them on one stream.
  *   Every call rewrites all the scratch it reads, so nothing needs clearing.

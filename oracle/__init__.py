@@ -22,8 +22,12 @@ Parity status per function (what pins it, see ``tests/test_oracle_pins.py``):
   pnp_run                 pinned for one and four iterations against a dense
                            restatement of Algorithm 1; longer trajectories rest
                            on those step identities
-The mutation tests (tests/test_oracle_mutations.py) plant sixteen plausible
-mistakes in a copy of pnp_oracle.c and check that these pins catch each one.
+  sample_count            pinned exactly (closed forms for an axis ray, with
+                           samples on the box edge, and a diagonal ray; the
+                           chord-interval count of every ray of a full geometry)
+The mutation tests (tests/test_oracle_mutations.py) plant plausible mistakes (one
+per entry of their table) in a copy of pnp_oracle.c and check that these pins
+catch each one.
 """
 from __future__ import annotations
 
@@ -53,7 +57,8 @@ class OrcGeom(C.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (OpenMP over rays of the forward projector)."""
+    """Compile the oracle with gcc (OpenMP over the rays of the forward projector and
+    over fixed view chunks of the backprojector)."""
     os.makedirs(_LIBDIR, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"

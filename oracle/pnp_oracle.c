@@ -164,7 +164,11 @@ void orc_project(const orc_geom *g, int s, const double *img, const double *b,
 }
 
 /* A_s^{(p)T} sino by scatter: every sample of every ray adds its weighted ray
- * value into the pixels whose hat functions cover it. */
+ * value into the pixels whose hat functions cover it.  The subset's views are
+ * cut into a fixed number of contiguous chunks (set by the view count alone,
+ * not by the number of threads); each chunk scatters into an image of its own
+ * in view order, and the chunk images are added in chunk order, so the result
+ * is the same whatever the thread count. */
 void orc_backproject(const orc_geom *g, int s, const double *sino, double *img, int p, int P)
 {
     int ns = g->n / s;
@@ -173,20 +177,32 @@ void orc_backproject(const orc_geom *g, int s, const double *sino, double *img, 
     int first = P <= 1 ? 0 : p;
     double delta = g->step * s;
     long K = sample_bound(g, s);
-    memset(img, 0, sizeof(double) * (size_t)ns * ns);
-    for (int vs = 0; vs < nsub; ++vs) {
-        int v = first + vs * step;
-        for (int j = 0; j < g->n_det; ++j) {
-            double r[6];
-            orc_ray(g, v, j, r);
-            double val = sino[(long)vs * g->n_det + j];
-            if (val == 0.0) continue;
-            for (long k = -K; k < K; ++k) {
-                double t = ((double)k + 0.5) * delta;
-                scatter(img, ns, s, r[4] + t * r[2], r[5] + t * r[3], delta * val);
+    size_t N = (size_t)ns * ns;
+    int nchunk = nsub < 32 ? nsub : 32;
+    memset(img, 0, sizeof(double) * N);
+    if (nchunk < 1) return;
+    double *part = calloc((size_t)nchunk * N, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int c = 0; c < nchunk; ++c) {
+        double *im = part + (size_t)c * N;
+        int v0 = (int)((long)nsub * c / nchunk), v1 = (int)((long)nsub * (c + 1) / nchunk);
+        for (int vs = v0; vs < v1; ++vs) {
+            int v = first + vs * step;
+            for (int j = 0; j < g->n_det; ++j) {
+                double r[6];
+                orc_ray(g, v, j, r);
+                double val = sino[(long)vs * g->n_det + j];
+                if (val == 0.0) continue;
+                for (long k = -K; k < K; ++k) {
+                    double t = ((double)k + 0.5) * delta;
+                    scatter(im, ns, s, r[4] + t * r[2], r[5] + t * r[3], delta * val);
+                }
             }
         }
     }
+    for (int c = 0; c < nchunk; ++c)
+        for (size_t i = 0; i < N; ++i) img[i] += part[(size_t)c * N + i];
+    free(part);
 }
 
 /* Sketch S: s x s average pooling, fine [n][n] -> coarse [n/s][n/s]. */

@@ -29,6 +29,19 @@ int level_index(int factor)
     }
 }
 
+int device_sm_count()
+{
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> cache[kMaxDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 1;
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) return 1;
+    cache[dev].store(v, std::memory_order_relaxed);
+    return v;
+}
+
 thread_local std::string t_err;
 
 void clear_error() { t_err.clear(); }
@@ -1291,8 +1304,8 @@ int pnp_autotune(const pnp_geom* g, const pnp_stage* stages, int n_stages, const
         for (int G = 1; G <= 16 && G <= nsub; G *= 2) shapes.push_back(G);
         for (int G : {8, 12, 16, 18, 20, 24, 32, 64, nsub, (nsub + 1) / 2})
             if (G >= 8 && G <= 64 && G <= nsub) shapes.push_back(PNP_BACK_TILE4 | G);
-        // the fixed-point scatter on square tiles (where the geometry allows it)
-        for (int TS : {12, 16, 22, 32}) shapes.push_back(PNP_BACK_SCATTER | TS);
+        // (the fixed-point scatter is not a candidate: its error depends on the
+        // residual's dynamic range; it runs only where pnp_set_launch_shapes pins it)
         for (int shp : shapes) {
             float ms = 0.0f;
             if (rc == PNP_OK)

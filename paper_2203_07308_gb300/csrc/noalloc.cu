@@ -13,7 +13,10 @@
 // contents; every call rewrites all of the scratch it reads, so nothing has to
 // start at zero.  Calls that overlap on the GPU (other streams, other host
 // threads, concurrent graphs) race on the array and give wrong results: issue
-// them one after another on one device.
+// them one after another on one device.  It is the unweighted gradient (no
+// pnp_set_weights weights: those belong to a workspace).  The device address of
+// the array is looked up on a device's first call and kept for the life of the
+// process; it does not survive cudaDeviceReset of that device.
 #include <cuda_runtime.h>
 
 #include <mutex>

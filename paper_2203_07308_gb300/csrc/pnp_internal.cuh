@@ -86,7 +86,10 @@ __device__ __forceinline__ float4 make_quad(float a, float b, float c, float d)
     q.w = (a - b) - (c - d);
     return q;
 }
-constexpr int kRedBlocks = 304;        // FP64 partial-sum blocks per instance (2 x 152 SMs)
+// FP64 partial-sum blocks per instance: a fixed count (not derived from the
+// device) so that the order of every FP64 reduction, and its result, is the same
+// on any GPU.
+constexpr int kRedBlocks = 304;
 constexpr int kRedThreads = 256;
 
 extern std::atomic<uint64_t> g_launches;
@@ -114,6 +117,10 @@ struct Layout {
 };
 
 int level_index(int factor);   // 0..3 or -1
+
+// Streaming multiprocessors of the current device (cached per device), for the
+// launch-shape heuristics; 1 if the query fails.
+int device_sm_count();
 
 // Error reporting and geometry checks shared by the C entry points (api.cu):
 // fail() records the message for pnp_last_error() and returns `code`.

@@ -756,10 +756,11 @@ cudaError_t launch_forward_multi(const FwdArgs* items, int count, cudaStream_t s
         t.c[c] = items[c];
         rays += (long)items[c].batch * items[c].n_sub * items[c].n_det;
     }
-    // lanes per ray: enough threads to fill the GPU (~2 waves of 152 x 2048),
-    // unless the autotuner chose
+    // lanes per ray: enough threads to fill the GPU (~2 waves of 2048 threads
+    // per SM), unless the autotuner chose
     int Q = lanes;
-    if (Q != 4 && Q != 8 && Q != 16) Q = rays * 4 >= 600000L ? 4 : rays * 8 >= 600000L ? 8 : 16;
+    const long fill = 2L * device_sm_count() * 2048;
+    if (Q != 4 && Q != 8 && Q != 16) Q = rays * 4 >= fill ? 4 : rays * 8 >= fill ? 8 : 16;
     const cudaError_t e = Q == 4 ? forward_q<4>(t, st) : Q == 8 ? forward_q<8>(t, st) : forward_q<16>(t, st);
     if (e != cudaSuccess) return e;
     return counted();
@@ -839,7 +840,8 @@ cudaError_t launch_backward_multi(const BackArgs* items, int count, cudaStream_t
     // unless the autotuner chose
     if (G < 1 || G * TX * kBack2TileY > 1024) {
         G = 1;
-        while (G < kBack2MaxGroups && blocks * G < 2L * 152 * 2048 && G * 2 <= min_views) G *= 2;
+        const long wave = 2L * device_sm_count() * 2048;
+        while (G < kBack2MaxGroups && blocks * G < wave && G * 2 <= min_views) G *= 2;
     }
     dim3 blk(TX, kBack2TileY, G), grd((unsigned)t.begin[count]);
     const size_t smem = (size_t)G * TX * kBack2TileY * sizeof(float4);

@@ -133,8 +133,9 @@ inline cudaError_t counted(cudaError_t e = cudaGetLastError())
 
 inline int grid_for(size_t count)
 {
+    const size_t cap = (size_t)8 * device_sm_count();   // 8 blocks of 256 threads per SM
     size_t g = (count + 255) / 256;
-    return (int)(g < 1216 ? (g < 1 ? 1 : g) : 1216);   // 8 blocks per SM on 152 SMs
+    return (int)(g < cap ? (g < 1 ? 1 : g) : cap);
 }
 
 }  // namespace

@@ -519,10 +519,11 @@ int choose_tile(int n, int batch)
 {
     int best = 16;
     double best_cost = 1e300;
+    const long sms = device_sm_count();
     for (int T = 8; T <= 40; ++T) {
         if (tile_smem(T, kTileKMax, 2) > kTileSmemMax || tile_np(T, kTileKMax, 2) > 4) break;
         const long tiles = (long)batch * ((n + T - 1) / T) * ((n + T - 1) / T);
-        const long waves = (tiles + 151) / 152;
+        const long waves = (tiles + sms - 1) / sms;
         const double side = (double)std::min(T, n) + 1 + kTileKMax;
         const double cost = (double)waves * side * side;
         if (cost < best_cost - 1e-9) {

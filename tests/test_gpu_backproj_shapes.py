@@ -144,9 +144,21 @@ def test_full_size_256_every_shape():
             assert rel(host(out)[0], refs[s]) < TOL, (shape, s, rel(host(out)[0], refs[s]))
 
 
+def test_autotune_never_picks_the_scatter():
+    """The autotuner chooses among the gather's shapes only, also on the 16 x 512^2
+    batch where the pinned scatter measured faster: the default product path stays
+    the exact FP32 transpose."""
+    for g, stages in ((GEOMS["c1"], [synth.Stage(2, 1, 3), synth.Stage(1, 1, 1)]),
+                      (synth.workloads()["c3_512x16"].geom, synth.workloads()["c3_512x16"].stages)):
+        plan = pnp.Plan(g)
+        plan.autotune(stages)
+        for b in plan.launch_shapes()["back"]:
+            assert not (b & SC), plan.launch_shapes()
+
+
 def test_full_size_512_batch_scatter_and_gather():
     """16 x 512^2 / 720 x 768 with 12 subsets (the batched workload, where the
-    autotuner picks the scatter at the full grid): a 60-view subset
+    pinned scatter measured faster than the gather at the full grid): a 60-view subset
     backprojection of the whole batch with the scatter on 32 x 32 tiles and the
     default gather, two sampled instances against the oracle."""
     wl = synth.workloads()["c3_512x16"]
@@ -197,6 +209,20 @@ def test_scatter_precision_follows_the_residual_range():
     print("relative L2 error by shape:", errs)
     assert errs["groups16"] < TOL, errs
     assert errs["scatter16"] < TOL and errs["scatter32"] < TOL, errs
+    # six decades: the gather keeps its bound; the scatter's error is recorded (it is
+    # never chosen by the autotuner, only where a caller pins it)
+    y6 = f32(rng.standard_normal((g.batch, g.n_views, g.n_det)) *
+             10.0 ** rng.uniform(-6.0, 0.0, (g.batch, g.n_views, g.n_det)))
+    ref6 = np.stack([oracle.backproject(g, 1, y6[i]) for i in range(g.batch)])
+    errs6 = {}
+    for name in ("groups16", "scatter16"):
+        plan = pinned(g, SHAPES[name])
+        out = empty(g.batch, g.n, g.n)
+        plan.backproject(1, dev(y6), out)
+        errs6[name] = rel(host(out), ref6)
+    print("six decades, relative L2 error by shape:", errs6)
+    assert errs6["groups16"] < TOL, errs6
+    assert errs6["scatter16"] < 1e-4, errs6
 
 
 def test_nonfinite_residual_propagates():

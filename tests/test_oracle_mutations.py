@@ -54,6 +54,10 @@ MUTATIONS = [
     ("saga table mean unscaled", "out[q] = gp[q] - psi[(size_t)p * N + q] + mean / (double)P;",
      "out[q] = gp[q] - psi[(size_t)p * N + q] + mean;"),
     ("saga table not updated", "memcpy(psi + (size_t)p * N, gp, sizeof(double) * N);", "(void)0;"),
+    ("sample-count box half a pixel small", "double H = (0.5 * ns + 0.5) * s, delta = g->step * s;",
+     "double H = (0.5 * ns) * s, delta = g->step * s;"),
+    ("sample-count box edge included", "if (fabs(qx) < H && fabs(qy) < H) count += 1.0;",
+     "if (fabs(qx) <= H && fabs(qy) <= H) count += 1.0;"),
     ("weights on the wrong views", "res[(long)vs * g->n_det + j] *= w[(long)(first + vs * step) * g->n_det + j];",
      "res[(long)vs * g->n_det + j] *= w[(long)vs * g->n_det + j];"),
 ]

@@ -5,6 +5,7 @@ form, a special case, an identity, or a brute-force restatement written here in
 a different way (dense matrices, rotation matrices, hat weights over all
 pixels, a different TV solver).
 """
+import dataclasses
 import json
 import math
 import os
@@ -666,10 +667,91 @@ def test_paper_operator_sizes():
         assert oracle.pool(np.zeros((case["n"], case["n"])), s).size == d // case["reduction"]
 
 
-def test_sample_count_near_estimate():
+def half_integers_inside(a):
+    """Number of k in Z with |k + 1/2| < a (a a Fraction or float >= 0)."""
+    from fractions import Fraction
+    a = Fraction(a)
+    # -a < k + 1/2 < a  <=>  -a - 1/2 < k < a - 1/2
+    lo = math.floor(-a - Fraction(1, 2)) + 1
+    hi = math.ceil(a - Fraction(1, 2)) - 1
+    return max(0, hi - lo + 1)
+
+
+@pytest.mark.parametrize("s", [1, 2, 4])
+@pytest.mark.parametrize("step", ["0.5", "1", "0.3"])
+def test_sample_count_axis_ray_closed_form(s, step):
+    """One ray (one view at angle 0, one bin): it runs along the x axis through the
+    origin, so its foot point is the origin and its samples sit at x = (k + 1/2) delta,
+    delta = step s.  The count is the number of half-integers strictly inside
+    (-H/delta, H/delta), H = (n_s/2 + 1/2) s the half-width of the support box.  With
+    step 1 and even n_s the outermost samples lie exactly on the box edge and are not
+    counted (strict inequality)."""
+    from fractions import Fraction
+    n = 64
+    g = dataclasses.replace(synth.make_geometry(n, 1, 1), step=float(step))
+    ns = n // s
+    H = (Fraction(ns, 2) + Fraction(1, 2)) * s
+    delta = Fraction(step) * s
+    want = half_integers_inside(H / delta)
+    assert oracle.sample_count(g, s) == want
+    if step == "0.5":
+        assert want == 2 * (ns + 1)
+    if step == "1":
+        assert want == ns   # (n_s + 1)/2 is a half-integer: the two edge samples drop out
+
+
+@pytest.mark.parametrize("s", [1, 2])
+@pytest.mark.parametrize("step", [0.5, 0.3])
+def test_sample_count_diagonal_ray_closed_form(s, step):
+    """One ray at 45 degrees through the origin: |x| = |y| = |t| / sqrt 2, so the
+    count is the number of half-integers inside (-sqrt2 H/delta, sqrt2 H/delta)
+    (irrational bound: no ties), i.e. 2 floor(sqrt2 H/delta + 1/2)."""
+    n = 64
+    g = synth.make_geometry(n, 1, 1, angle0=math.pi / 4, step=step)
+    ns = n // s
+    a = math.sqrt(2.0) * (0.5 * ns + 0.5) * s / (step * s)
+    assert oracle.sample_count(g, s) == 2 * math.floor(a + 0.5)
+
+
+def chord_count(g, s, v, j):
+    """Samples of ray (v, j) strictly inside the box |x|,|y| < H, counted from the
+    chord: the ray (source S, direction d, foot point F = S - (S.d) d, from the
+    rotated view frame) meets the box for t in (t_lo, t_hi) (slab intersection),
+    and the samples t = (k + 1/2) delta inside that interval are counted in closed
+    form."""
+    S, P = ray_endpoints(g, v, j)
+    d = (P - S) / np.linalg.norm(P - S)
+    F = S - np.dot(S, d) * d
+    ns = g.n // s
+    H = (0.5 * ns + 0.5) * s
+    delta = g.step * s
+    lo, hi = -math.inf, math.inf
+    for c in range(2):
+        if abs(d[c]) < 1e-15:
+            if abs(F[c]) >= H:
+                return 0
+            continue
+        t1, t2 = (-H - F[c]) / d[c], (H - F[c]) / d[c]
+        lo, hi = max(lo, min(t1, t2)), min(hi, max(t1, t2))
+    if not hi > lo:
+        return 0
+    # lo < (k + 1/2) delta < hi
+    k_lo = math.floor(lo / delta - 0.5) + 1
+    k_hi = math.ceil(hi / delta - 0.5) - 1
+    return max(0, k_hi - k_lo + 1)
+
+
+@pytest.mark.parametrize("s,P,p", [(1, 1, 0), (2, 1, 0), (1, 8, 3), (4, 5, 4)])
+def test_sample_count_equals_chord_count(s, P, p):
+    """The whole 64^2 / 90 views x 96 bins geometry (and subsets): the oracle's
+    brute-force count over all integer k equals the chord-interval count of every
+    ray, exactly."""
     g = synth.make_geometry(64, 90, 96)
-    cnt = oracle.sample_count(g)
-    assert 7.0e5 < cnt < 8.5e5
+    views = range(p, g.n_views, P) if P > 1 else range(g.n_views)
+    want = sum(chord_count(g, s, v, j) for v in views for j in range(g.n_det))
+    assert oracle.sample_count(g, s, p, P) == want
+    if (s, P) == (1, 1):
+        assert 7.0e5 < want < 8.5e5
 
 
 # ---------------------------------------------------------------- weighted least squares (Poisson data)
