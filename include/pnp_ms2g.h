@@ -135,7 +135,7 @@ typedef struct {
     pnp_geom geom;
     const pnp_stage* stages;
     int32_t n_stages;
-    const double* h_eta;          /* [n_stages] */
+    const double* h_eta;          /* [n_stages], or NULL: eta_k = 1/L_k as pnp_step_sizes computes it */
     const int32_t* h_subset_seq;  /* [sum iters], may be NULL when no stage uses subsets */
     const float* d_b;             /* [batch][n_views][n_det] */
     float* d_x;                   /* in: x_0, out: x */
@@ -253,8 +253,34 @@ int pnp_vr_buffer_size(const pnp_geom* g, const pnp_stage* stages, int n_stages,
  * interrupted run left.  PNP_ESTATE from pnp_run when a stage needs a larger one. */
 int pnp_set_vr_buffer(const pnp_geom* g, void* d_buf, size_t bytes, void* d_ws);
 
+/* Step sizes of Algorithm 1 for a schedule (Sec. 3: eta = O(1/L)):
+ * h_eta[k] = 1 / L_k, L_k = ||W^{1/2} A_{s_k} S_k||^2 for stage k's level and
+ * sketch kind (W the weights of pnp_set_weights, else I), by the power iteration
+ * of pnp_power_iter_kind with at most 100 iterations and relative tolerance 1e-6.
+ * Each L is cached in the workspace's registry entry (per level and sketch kind)
+ * until pnp_setup or pnp_set_weights; computing one is synchronous on `stream`
+ * and uses the workspace's scratch buffers, so call it outside stream capture.
+ * pnp_run and pnp_run_many use it for problems given without step sizes. */
+int pnp_step_sizes(const pnp_geom* g, const pnp_stage* stages, int n_stages, double* h_eta, void* d_ws,
+                   void* stream);
+
+/* The iteration schedule of Algorithm 1 as a caller that unrolls it walks it
+ * (the differentiable form): for iteration i = 1..T, T = the sum of the stages'
+ * iters (written to *h_total),
+ *   h_stage[i-1]   index k of its stage (factor s_k, subsets P_k, eta_k)
+ *   h_subset[i-1]  its angle subset: h_subset_seq[i-1] when P_k > 1, else 0
+ *   h_amom[i-1]    its momentum coefficient a_i = (i-1)/(i+3) (Sec. 3) when
+ *                  momentum != 0, else 0 (Eq. 5) -- the a_i that pnp_run uses.
+ * The arrays hold `capacity` entries; PNP_EINVAL (with *h_total set) when T
+ * exceeds it, or when a subset id lies outside its stage's [0, P_k).
+ * Host only; launches nothing. */
+int pnp_schedule(const pnp_stage* stages, int n_stages, const int32_t* h_subset_seq, int momentum,
+                 int32_t* h_stage, int32_t* h_subset, float* h_amom, int64_t capacity, int64_t* h_total);
+
 /* Algorithm 1 (PnP-MS2G) on every image of the batch.
- *   stages[n_stages]   the schedule; h_eta[n_stages] step sizes eta_k
+ *   stages[n_stages]   the schedule; h_eta[n_stages] step sizes eta_k, or NULL
+ *                      for eta_k = 1/L_k from pnp_step_sizes (the first run
+ *                      that needs a level's L then synchronises `stream`)
  *   h_subset_seq       subset id of every iteration (length sum iters); may be
  *                      NULL when every stage has n_subsets == 1
  *   params             alpha, lambda, tv_iters, momentum
@@ -433,6 +459,18 @@ int pnp_unrolled_step_vjp_saved(const pnp_geom* g, int factor, int subset, int n
  *   Every call rewrites all the scratch it reads, so nothing needs clearing.
  *   d_x, d_g [batch][n][n], d_b [batch][n_views][n_det]; asynchronous on `stream`. */
 int pnp_full_grad_noalloc(const pnp_geom* g, const float* d_x, const float* d_b, float* d_g, void* stream);
+
+/* Read bandwidth (GB/s) of the on-chip memory levels of the current GPU,
+ * measured with this library's probe kernels and CUDA events (best of three
+ * timed launches each, after a warm-up): h_gbs[0] L2 (a 24 MiB buffer streamed
+ * by every SM with L1-bypassing 16-byte loads), h_gbs[1] L1 (each block
+ * re-reading a private 16 KB window), h_gbs[2] shared memory (each block
+ * re-reading 32 KB, conflict-free 16-byte words).  These are the denominators of
+ * the projector kernels' on-chip rooflines.  d_buf: caller-owned scratch of at
+ * least 32 MiB (PNP_EINVAL names the size needed when it is short), 256-byte
+ * aligned, overwritten.  Synchronous.  Library instrumentation; the paper has no
+ * counterpart. */
+int pnp_onchip_bandwidth(void* d_buf, size_t bytes, double* h_gbs, void* stream);
 
 /* Device time (ms, summed) and number of timed launches of each phase over all
  * runs with PNP_RUN_KERNEL_TIMES since the last reset, indexed by PNP_PHASE_*.

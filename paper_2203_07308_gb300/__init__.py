@@ -9,6 +9,7 @@ from . import synth  # noqa: F401
 from ._native import (  # noqa: F401
     Geom, Plan, PnpError, backproject, full_grad, full_grad_noalloc,
     header_functions, kernel_times, launch_count, last_error, load,
-    objective, power_iter, project, run, run_many, autotune, sample_count, setup, sketch, sketch_grad, subset_views,
+    objective, onchip_bandwidth, power_iter, project, run, run_many, autotune, sample_count, schedule, setup,
+    sketch, sketch_grad, step_sizes, subset_views,
     tv_denoise, tv_workspace_size, upsample, vr_buffer_size, workspace_size,
 )

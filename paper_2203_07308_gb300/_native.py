@@ -137,6 +137,10 @@ def load(path: Optional[str] = None):
                                        vp, vp, vp, vp, vp, vp, vp, vp],
             "pnp_unrolled_step_vjp_saved": [gp, i32, i32, i32, C.c_double, C.POINTER(RunParams), C.c_float,
                                             vp, vp, vp, vp, vp, dp, vp, vp, sz, vp],
+            "pnp_step_sizes": [gp, C.POINTER(StageC), i32, dp, vp, vp],
+            "pnp_schedule": [C.POINTER(StageC), i32, C.POINTER(C.c_int32), i32, C.POINTER(C.c_int32),
+                             C.POINTER(C.c_int32), C.POINTER(C.c_float), C.c_int64, C.POINTER(C.c_int64)],
+            "pnp_onchip_bandwidth": [vp, sz, dp, vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -299,20 +303,58 @@ def vr_buffer_size(g, stages) -> int:
     return int(v.value)
 
 
+def step_sizes(g, stages, ws, stream=None) -> list:
+    """pnp_step_sizes: eta_k = 1/L_k of every stage (power iteration in the
+    library, cached per workspace)."""
+    st = _stages(stages)
+    out = (C.c_double * len(st))()
+    _check(load().pnp_step_sizes(C.byref(geom(g)), st, len(st), out, _ws(ws)[0], _stream(stream)))
+    return [float(v) for v in out]
+
+
+def schedule(stages, seq=None, momentum=True):
+    """pnp_schedule: (stage index, subset id, momentum coefficient a_i) of every
+    iteration of the schedule, as int32 / int32 / float32 arrays."""
+    st = _stages(stages)
+    total = sum(a.iters for a in st)
+    seq_np = None if seq is None else np.ascontiguousarray(np.asarray(seq, dtype=np.int32))
+    if seq_np is not None and seq_np.size < total:
+        raise PnpError(PNP_EINVAL, "subset sequence shorter than the schedule")
+    stage = np.zeros(max(total, 1), dtype=np.int32)
+    subset = np.zeros(max(total, 1), dtype=np.int32)
+    amom = np.zeros(max(total, 1), dtype=np.float32)
+    n = C.c_int64(0)
+    _check(load().pnp_schedule(st, len(st), None if seq_np is None else seq_np.ctypes.data_as(C.POINTER(C.c_int32)),
+                               int(bool(momentum)), stage.ctypes.data_as(C.POINTER(C.c_int32)),
+                               subset.ctypes.data_as(C.POINTER(C.c_int32)), amom.ctypes.data_as(C.POINTER(C.c_float)),
+                               stage.size, C.byref(n)))
+    return stage[:n.value], subset[:n.value], amom[:n.value]
+
+
+def onchip_bandwidth(device="cuda", stream=None) -> dict:
+    """pnp_onchip_bandwidth: measured L2, L1 and shared-memory read bandwidth (GB/s)."""
+    import torch
+    buf = torch.empty(32 << 20, dtype=torch.uint8, device=device)
+    out = (C.c_double * 3)()
+    _check(load().pnp_onchip_bandwidth(C.c_void_p(buf.data_ptr()), buf.numel(), out, _stream(stream)))
+    return {"l2_gbs": float(out[0]), "l1_gbs": float(out[1]), "smem_gbs": float(out[2])}
+
+
 def _flags(graph, kernel_times):
     return (RUN_GRAPH if graph else 0) | (RUN_KERNEL_TIMES if kernel_times else 0)
 
 
 def run(g, stages, eta, seq, b, x, *, alpha=1.0, lam=0.02, tv_iters=20, momentum=True,
         xtrue=None, ws=None, stream=None, graph=False, kernel_times=False):
-    """Algorithm 1; x holds x_0 on entry and the result on return.  Returns the
+    """Algorithm 1; x holds x_0 on entry and the result on return.  eta: step
+    size per stage, or None for eta_k = 1/L_k computed by the library.  Returns the
     PSNR log [total_iters, batch] when xtrue is given, else None.  graph=True
     captures the launch sequence once per distinct call and replays it;
     kernel_times=True brackets each phase launch with CUDA events (read them
     with kernel_times())."""
     st = _stages(stages)
     total = sum(a.iters for a in st)
-    eta_a = (C.c_double * len(st))(*[float(e) for e in eta])
+    eta_a = None if eta is None else (C.c_double * len(st))(*[float(e) for e in eta])
     seq_np = np.ascontiguousarray(np.asarray(seq if seq is not None else np.zeros(total), dtype=np.int32))
     if seq_np.size < total:
         raise PnpError(PNP_EINVAL, "subset sequence shorter than the schedule")
@@ -385,6 +427,9 @@ class Plan:
 
     def power_iter(self, factor, max_iters=100, tol=1e-7, stream=None, kind=0):
         return power_iter(self.g, factor, max_iters, tol, self.ws, stream, kind)
+
+    def step_sizes(self, stages, stream=None):
+        return step_sizes(self.g, stages, self.ws, stream)
 
     def ensure_vr_buffer(self, stages):
         """Allocates (PyTorch) and registers the SVRG/SAGA state buffer the
@@ -527,7 +572,7 @@ def run_many(problems, *, alpha=1.0, lam=0.02, tv_iters=20, momentum=True, strea
         plan.ensure_vr_buffer(pr["stages"])
         st = _stages(pr["stages"])
         total = sum(a.iters for a in st)
-        eta_a = (C.c_double * len(st))(*[float(e) for e in pr["eta"]])
+        eta_a = None if pr.get("eta") is None else (C.c_double * len(st))(*[float(e) for e in pr["eta"]])
         seq = pr.get("seq")
         seq_np = np.ascontiguousarray(np.asarray(seq if seq is not None else np.zeros(total), dtype=np.int32))
         img = g.batch * g.n * g.n

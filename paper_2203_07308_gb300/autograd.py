@@ -114,23 +114,25 @@ class UnrolledStep(torch.autograd.Function):
         return (ybar_in, xpbar, lam_grad) + (None,) * 11
 
 
-def unrolled_pnp(plan, stages: Sequence, eta: Sequence[float], seq, b, x0, lam, *, alpha: float = 1.0,
+def unrolled_pnp(plan, stages: Sequence, eta, seq, b, x0, lam, *, alpha: float = 1.0,
                  tv_iters: int = 20, momentum: bool = True, keep_z: bool = True):
     """x_T of Algorithm 1 as a differentiable function of x0 (float32 CUDA
     tensor [batch, n, n]) and lam (a float64 scalar tensor, may require grad).
-    keep_z: keep each iteration's gradient step z for the backward pass (one
-    projector pair fewer per iteration); False keeps only y and recomputes z."""
+    eta: step size per stage, or None for the library's eta_k = 1/L_k
+    (pnp_step_sizes).  The walk over iterations (stage, subset, momentum a_i)
+    comes from pnp_schedule.  keep_z: keep each iteration's gradient step z for
+    the backward pass (one projector pair fewer per iteration); False keeps only
+    y and recomputes z."""
     g = plan.g
+    if eta is None:
+        eta = plan.step_sizes(stages)
+    st = _native._stages(stages)
+    stage_of, subset_of, amom_of = _native.schedule(stages, seq, momentum)
     vjp_ws = torch.empty(_native.vjp_workspace_size(g, tv_iters), dtype=torch.uint8, device=x0.device)
     y = x0
     x = x0
-    i = 0
-    for k, st in enumerate(stages):
-        f, iters, P = (st.factor, st.iters, st.n_subsets) if hasattr(st, "factor") else st
-        for _ in range(iters):
-            i += 1
-            p = int(seq[i - 1]) if P > 1 else 0
-            a = (i - 1) / (i + 3) if momentum else 0.0
-            x, y = UnrolledStep.apply(y, x, lam, plan, b, f, p, P, float(eta[k]), alpha, tv_iters, a, vjp_ws,
-                                      keep_z)
+    for k, p, a in zip(stage_of.tolist(), subset_of.tolist(), amom_of.tolist()):
+        s_k = st[k]
+        x, y = UnrolledStep.apply(y, x, lam, plan, b, s_k.factor, p, s_k.n_subsets, float(eta[k]), alpha, tv_iters,
+                                  a, vjp_ws, keep_z)
     return x

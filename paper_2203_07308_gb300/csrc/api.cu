@@ -171,9 +171,18 @@ struct Tuned {
     int tile = 0;                            // tiled FGP: tile side
 };
 
+// Step-size constants L = ||W^{1/2} A_s S||^2 found by pnp_step_sizes (or a
+// pnp_run without step sizes), per level and sketch kind; cleared by pnp_setup and
+// pnp_set_weights.
+struct LCache {
+    double L[kMaxLevels][2] = {};
+    bool valid[kMaxLevels][2] = {};
+};
+
 struct RegEntry {
     const void* ws; uint64_t fp; size_t bytes; Tuned tuned; const float* weights;
     void* vr = nullptr; size_t vr_bytes = 0;     // estimator-state buffer (SVRG / SAGA)
+    LCache lc;
 };
 std::mutex g_reg_mu;
 std::vector<RegEntry> g_reg;
@@ -184,6 +193,7 @@ void reg_put(const void* ws, uint64_t fp, size_t bytes)
     for (auto& e : g_reg)
         if (e.ws == ws) {
             e.fp = fp; e.bytes = bytes; e.tuned = Tuned(); e.weights = nullptr; e.vr = nullptr; e.vr_bytes = 0;
+            e.lc = LCache();
             return;
         }
     if (g_reg.size() >= 4096) g_reg.erase(g_reg.begin());
@@ -258,7 +268,31 @@ void reg_set_weights(const void* ws, const float* w)
 {
     std::lock_guard<std::mutex> lk(g_reg_mu);
     for (auto& e : g_reg)
-        if (e.ws == ws) e.weights = w;
+        if (e.ws == ws) {
+            e.weights = w;
+            e.lc = LCache();     // L depends on the weights
+        }
+}
+
+bool reg_get_L(const void* ws, int li, int kind, double* L)
+{
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    for (const auto& e : g_reg)
+        if (e.ws == ws && e.lc.valid[li][kind]) {
+            *L = e.lc.L[li][kind];
+            return true;
+        }
+    return false;
+}
+
+void reg_put_L(const void* ws, int li, int kind, double L)
+{
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    for (auto& e : g_reg)
+        if (e.ws == ws) {
+            e.lc.L[li][kind] = L;
+            e.lc.valid[li][kind] = true;
+        }
 }
 
 void reg_set_tuned(const void* ws, const Tuned& t)
@@ -787,20 +821,18 @@ int pnp_power_iter(const pnp_geom* g, int factor, int max_iters, double tol, dou
     return pnp_power_iter_kind(g, factor, PNP_SKETCH_POOL, max_iters, tol, h_L, h_iters, d_ws, stream);
 }
 
-int pnp_power_iter_kind(const pnp_geom* g, int factor, int kind, int max_iters, double tol, double* h_L,
-                        int* h_iters, void* d_ws, void* stream)
+}  // extern "C"
+
+namespace pnp {
+namespace {
+
+// L = ||W^{1/2} A_s S||^2 of level li by power iteration on S^T A_s^T W A_s S from
+// the normalised all-ones image (FP32 operators, FP64 inner products and norm);
+// synchronous.  Arguments already checked.
+int power_iter_impl(const pnp_geom& gg, const Layout& L, int li, int kind, int max_iters, double tol, double* h_L,
+                    int* h_iters, char* ws, cudaStream_t st)
 {
-    t_err.clear();
-    if (kind != PNP_SKETCH_POOL && kind != PNP_SKETCH_BICUBIC) return fail(PNP_EINVAL, "unknown sketch kind %d", kind);
-    if (int e = validate_geom(g)) return e;
-    Layout L = make_layout(*g);
-    int li = 0;
-    if (int e = check_level(*g, factor, L, &li)) return e;
-    if (max_iters < 1 || !(tol >= 0.0)) return fail(PNP_EINVAL, "need max_iters >= 1 and tol >= 0");
-    if (!h_L) return fail(PNP_EINVAL, "h_L is NULL");
-    if (int e = check_ws(*g, d_ws)) return e;
-    char* ws = (char*)d_ws;
-    cudaStream_t st = S(stream);
+    const pnp_geom* g = &gg;
     pnp_geom g1 = *g;
     g1.batch = 1;
     const LevelLayout& lv = L.lv[li];
@@ -844,6 +876,115 @@ int pnp_power_iter_kind(const pnp_geom* g, int factor, int kind, int max_iters, 
     }
     *h_L = lam;
     if (h_iters) *h_iters = it > max_iters ? max_iters : it;
+    return PNP_OK;
+}
+
+// Power-iteration settings of the step sizes the library computes itself.
+constexpr int kStepPowerIters = 100;
+constexpr double kStepPowerTol = 1e-6;
+
+// eta_k = 1 / L_k for every stage (stages already checked): L_k of the stage's
+// level and sketch kind from the workspace's cache, else by power iteration
+// (then cached).
+int step_sizes(const pnp_geom& g, const Layout& L, const pnp_stage* stages, int n_stages, double* eta, char* ws,
+               cudaStream_t st)
+{
+    for (int k = 0; k < n_stages; ++k) {
+        const int li = level_index(stages[k].factor);
+        const int kind = stages[k].factor > 1 && stages[k].kind == PNP_SKETCH_BICUBIC ? 1 : 0;
+        double Lk = 0.0;
+        if (!reg_get_L(ws, li, kind, &Lk)) {
+            if (int e = power_iter_impl(g, L, li, kind, kStepPowerIters, kStepPowerTol, &Lk, nullptr, ws, st))
+                return e;
+            if (!(Lk > 0.0) || !std::isfinite(Lk))
+                return fail(PNP_EINVAL, "stage %d: operator norm %g is not positive (no ray meets the image?)", k, Lk);
+            reg_put_L(ws, li, kind, Lk);
+        }
+        eta[k] = 1.0 / Lk;
+    }
+    return PNP_OK;
+}
+
+int check_stages(const pnp_geom& g, const Layout& L, const pnp_stage* stages, int n_stages)
+{
+    if (!stages || n_stages < 1) return fail(PNP_EINVAL, "stages are required");
+    for (int k = 0; k < n_stages; ++k) {
+        int li = 0;
+        if (int e = check_level(g, stages[k].factor, L, &li)) return e;
+        if (stages[k].kind != PNP_SKETCH_POOL && stages[k].kind != PNP_SKETCH_BICUBIC)
+            return fail(PNP_EINVAL, "stage %d: unknown sketch kind %d", k, stages[k].kind);
+    }
+    return PNP_OK;
+}
+
+}  // namespace
+
+// a_i of iteration i (Sec. 3: a_i = (i-1)/(i+3); 0 without momentum, Eq. 5).
+float momentum_coef(long i, int momentum)
+{
+    return momentum ? (float)((double)(i - 1) / (double)(i + 3)) : 0.0f;
+}
+
+}  // namespace pnp
+
+extern "C" {
+
+int pnp_power_iter_kind(const pnp_geom* g, int factor, int kind, int max_iters, double tol, double* h_L,
+                        int* h_iters, void* d_ws, void* stream)
+{
+    t_err.clear();
+    if (kind != PNP_SKETCH_POOL && kind != PNP_SKETCH_BICUBIC) return fail(PNP_EINVAL, "unknown sketch kind %d", kind);
+    if (int e = validate_geom(g)) return e;
+    Layout L = make_layout(*g);
+    int li = 0;
+    if (int e = check_level(*g, factor, L, &li)) return e;
+    if (max_iters < 1 || !(tol >= 0.0)) return fail(PNP_EINVAL, "need max_iters >= 1 and tol >= 0");
+    if (!h_L) return fail(PNP_EINVAL, "h_L is NULL");
+    if (int e = check_ws(*g, d_ws)) return e;
+    return power_iter_impl(*g, L, li, kind, max_iters, tol, h_L, h_iters, (char*)d_ws, S(stream));
+}
+
+int pnp_step_sizes(const pnp_geom* g, const pnp_stage* stages, int n_stages, double* h_eta, void* d_ws,
+                   void* stream)
+{
+    t_err.clear();
+    if (int e = validate_geom(g)) return e;
+    Layout L = make_layout(*g);
+    if (int e = check_stages(*g, L, stages, n_stages)) return e;
+    if (!h_eta) return fail(PNP_EINVAL, "h_eta is NULL");
+    if (int e = check_ws(*g, d_ws)) return e;
+    return step_sizes(*g, L, stages, n_stages, h_eta, (char*)d_ws, S(stream));
+}
+
+int pnp_schedule(const pnp_stage* stages, int n_stages, const int32_t* h_subset_seq, int momentum,
+                 int32_t* h_stage, int32_t* h_subset, float* h_amom, int64_t capacity, int64_t* h_total)
+{
+    t_err.clear();
+    if (!stages || n_stages < 1 || !h_total) return fail(PNP_EINVAL, "stages and h_total are required");
+    int64_t total = 0;
+    bool any_subsets = false;
+    for (int k = 0; k < n_stages; ++k) {
+        if (stages[k].iters < 0) return fail(PNP_EINVAL, "stage %d has negative iterations", k);
+        if (stages[k].n_subsets < 1) return fail(PNP_EINVAL, "stage %d: n_subsets < 1", k);
+        any_subsets |= stages[k].n_subsets > 1 && stages[k].iters > 0;
+        total += stages[k].iters;
+    }
+    *h_total = total;
+    if (total > capacity) return fail(PNP_EINVAL, "schedule has %lld iterations, capacity %lld", (long long)total,
+                                      (long long)capacity);
+    if (total > 0 && (!h_stage || !h_subset || !h_amom)) return fail(PNP_EINVAL, "output arrays are required");
+    if (any_subsets && !h_subset_seq) return fail(PNP_EINVAL, "subset sequence required");
+    int64_t i = 0;
+    for (int k = 0; k < n_stages; ++k)
+        for (int jj = 0; jj < stages[k].iters; ++jj, ++i) {
+            const int P = stages[k].n_subsets;
+            const int p = P > 1 ? h_subset_seq[i] : 0;
+            if (p < 0 || p >= P)
+                return fail(PNP_EINVAL, "subset_seq[%lld]=%d outside stage %d's [0, %d)", (long long)i, p, k, P);
+            h_stage[i] = k;
+            h_subset[i] = p;
+            h_amom[i] = momentum_coef((long)(i + 1), momentum);
+        }
     return PNP_OK;
 }
 
@@ -918,11 +1059,27 @@ int validate_problem(const pnp_problem& q, const pnp_run_params& pr, int idx, Pr
     return PNP_OK;
 }
 
-int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, void* stream)
+int run_many_impl(const pnp_problem* pb_in, int np, const pnp_run_params* params, void* stream)
 {
-    if (!pb || np < 1) return fail(PNP_EINVAL, "no problems");
+    if (!pb_in || np < 1) return fail(PNP_EINVAL, "no problems");
     if (np > kMaxClasses) return fail(PNP_EUNSUPPORTED, "at most %d geometry classes per call", kMaxClasses);
     if (!params) return fail(PNP_EINVAL, "params are required");
+    // problems without step sizes get eta_k = 1/L_k from the library (cached per
+    // workspace; the first computation of a level's L synchronises the stream)
+    std::vector<pnp_problem> pbv(pb_in, pb_in + np);
+    std::vector<std::vector<double>> etas((size_t)np);
+    for (int c = 0; c < np; ++c) {
+        pnp_problem& q = pbv[c];
+        if (q.h_eta) continue;
+        if (int e = validate_geom(&q.geom)) return e;
+        const Layout Lq = make_layout(q.geom);
+        if (int e = check_stages(q.geom, Lq, q.stages, q.n_stages)) return e;
+        if (int e = check_ws(q.geom, q.d_ws)) return e;
+        etas[c].resize((size_t)q.n_stages);
+        if (int e = step_sizes(q.geom, Lq, q.stages, q.n_stages, etas[c].data(), (char*)q.d_ws, S(stream))) return e;
+        q.h_eta = etas[c].data();
+    }
+    const pnp_problem* pb = pbv.data();
     const pnp_run_params& pr = *params;
     if (!(pr.alpha > 0.0f && pr.alpha <= 1.0f)) return fail(PNP_EINVAL, "alpha must be in (0, 1]");
     if (!(pr.lambda >= 0.0f) || !std::isfinite(pr.lambda)) return fail(PNP_EINVAL, "lambda must be >= 0");
@@ -989,7 +1146,7 @@ int run_many_impl(const pnp_problem* pb, int np, const pnp_run_params* params, v
             int need_prep[kMaxClasses];
             int lvl[kMaxClasses];
             int na = 0;
-            const float amom = pr.momentum ? (float)((double)(i - 1) / (double)(i + 3)) : 0.0f;
+            const float amom = momentum_coef(i, pr.momentum);
             for (int c = 0; c < np; ++c) {
                 if (i > ps[c].total) continue;
                 const pnp_problem& q = pb[c];

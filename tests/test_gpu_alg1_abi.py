@@ -1,0 +1,121 @@
+"""Algorithm 1 wholly behind the C ABI: step sizes eta_k = 1/L_k computed by the
+library (Sec. 3: eta = O(1/L)) and the run without caller step sizes, checked
+against the FP64 oracle's L and against runs given the same step sizes; the
+unrolled form walking pnp_schedule."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2203_07308_gb300 as pnp
+from paper_2203_07308_gb300 import build, synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    pnp.load()
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def test_step_sizes_match_the_oracle_and_the_power_iteration():
+    """eta_k = 1/L_k per stage: the library's value equals 1/L of pnp_power_iter with
+    the same settings exactly, and the FP64 oracle's 1/L within the gradient
+    tolerance, for the pooled and the bicubic sketch; the cache is cleared by new
+    weights."""
+    g = synth.make_geometry(64, 90, 96, batch=2)
+    plan = pnp.Plan(g)
+    stages = [synth.Stage(4, 2, 3), synth.Stage(2, 2, 1, kind=1), synth.Stage(1, 3, 1)]
+    eta = plan.step_sizes(stages)
+    for st, e in zip(stages, eta):
+        L, _ = plan.power_iter(st.factor, 100, 1e-6, kind=st.kind if st.factor > 1 else 0)
+        assert e == 1.0 / L
+        Lo, _ = oracle.power_iter(g, st.factor, 400, 1e-12, kind=st.kind if st.factor > 1 else 0)
+        assert abs(e * Lo - 1.0) < TOL, (st, e * Lo)
+    assert plan.step_sizes(stages) == eta                       # cached, same values
+    w = np.random.default_rng(5).uniform(0.5, 2.0, (g.batch, g.n_views, g.n_det))
+    plan.set_weights(dev(w))
+    eta_w = plan.step_sizes(stages)
+    Lw, _ = oracle.power_iter(g, 1, 400, 1e-12, w=np.asarray(w[0], np.float32).astype(np.float64))
+    assert abs(eta_w[2] * Lw - 1.0) < TOL
+    assert eta_w[2] != eta[2]
+
+
+def test_run_without_step_sizes_equals_run_with_them():
+    """pnp_run with h_eta = NULL gives the same bits as with h_eta = pnp_step_sizes,
+    through pnp_run and pnp_run_many, with and without graph capture."""
+    import torch
+    g = synth.make_geometry(64, 90, 96, batch=2)
+    plan = pnp.Plan(g)
+    stages = [synth.Stage(2, 3, 3), synth.Stage(1, 4, 2)]
+    seq = synth.schedule_sequence(stages, 11)
+    x_true = np.stack([synth.ellipse_phantom(64, 300 + i, (6, 9)) for i in range(2)])
+    b = torch.empty(2, g.n_views, g.n_det, device="cuda")
+    plan.project(1, dev(x_true), b)
+    outs = []
+    for eta, graph in ((plan.step_sizes(stages), False), (None, False), (None, True)):
+        x = torch.zeros(2, 64, 64, device="cuda")
+        plan.run(stages, eta, seq, b, x, lam=0.02, tv_iters=20, momentum=True, graph=graph)
+        outs.append(host(x))
+    x = torch.zeros(2, 64, 64, device="cuda")
+    pnp.run_many([dict(plan=plan, stages=stages, eta=None, seq=seq, b=b, x=x)], lam=0.02, tv_iters=20)
+    outs.append(host(x))
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+
+
+def test_run_without_step_sizes_matches_the_oracle_run():
+    """The reconstruction with library step sizes against the oracle's run with its
+    own FP64 step sizes (so the two sides share no input): within the
+    reconstruction tolerance."""
+    import torch
+    g = synth.make_geometry(64, 90, 96)
+    plan = pnp.Plan(g)
+    stages = [synth.Stage(2, 4, 3), synth.Stage(1, 4, 1)]
+    seq = synth.schedule_sequence(stages, 12)
+    x_true = synth.ellipse_phantom(64, 77, (6, 9))
+    b = oracle.project(g, 1, x_true)
+    b = np.asarray(b, np.float32).astype(np.float64)
+    x = torch.zeros(1, 64, 64, device="cuda")
+    plan.run(stages, None, seq, dev(b[None]), x, lam=0.02, tv_iters=20, momentum=True)
+    eta_o = [1.0 / oracle.power_iter(g, s.factor, 400, 1e-12)[0] for s in stages]
+    xr, _ = oracle.pnp_run(g, stages, eta_o, seq, b, None, lam=0.02, tv_iters=20, momentum=True)
+    got = host(x)[0]
+    assert np.linalg.norm(got - xr) / np.linalg.norm(xr) < 1e-4
+
+
+def test_unrolled_without_step_sizes_equals_with_them():
+    """autograd.unrolled_pnp walks pnp_schedule; eta=None takes pnp_step_sizes: same
+    x_T and gradients as the explicit step sizes."""
+    import torch
+    from paper_2203_07308_gb300.autograd import unrolled_pnp
+    g = synth.make_geometry(48, 40, 64, batch=2)
+    plan = pnp.Plan(g)
+    stages = [synth.Stage(2, 2, 2), synth.Stage(1, 2, 1)]
+    seq = synth.schedule_sequence(stages, 4)
+    xt = dev(np.stack([synth.ellipse_phantom(48, 500 + i, (5, 7)) for i in range(2)]))
+    b = torch.empty(2, g.n_views, g.n_det, device="cuda")
+    plan.project(1, xt, b)
+    res = []
+    for eta in (plan.step_sizes(stages), None):
+        x0 = torch.zeros(2, 48, 48, device="cuda", requires_grad=True)
+        lam = torch.tensor(0.02, dtype=torch.float64, requires_grad=True)
+        xT = unrolled_pnp(plan, stages, eta, seq, b, x0, lam, tv_iters=10)
+        (0.5 * ((xT - xt) ** 2).sum()).backward()
+        res.append((host(xT), host(x0.grad), float(lam.grad)))
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    assert res[0][2] == res[1][2]

@@ -4,6 +4,7 @@ arguments on the host before anything is launched."""
 import ctypes as C
 import math
 
+import numpy as np
 import pytest
 
 import paper_2203_07308_gb300 as pnp
@@ -101,3 +102,43 @@ def test_binding_constants_match_the_header():
         assert define(name) == value, name
     for k, ph in enumerate(N.PHASES):
         assert define("PNP_PHASE_" + ph.upper()) == k, ph
+
+
+def test_schedule_walks_algorithm_1(lib):
+    """pnp_schedule (host only): iteration i of the schedule belongs to the stage
+    whose iterations cover it, takes its subset from the sequence only when that
+    stage has P_k > 1, and has the momentum a_i = (i-1)/(i+3) of Sec. 3 (a_1 = 0,
+    one global sequence with no restart at stage switches), or 0 without momentum."""
+    stages = [synth.Stage(4, 3, 5), synth.Stage(2, 0, 3), synth.Stage(1, 4, 1), synth.Stage(1, 2, 2)]
+    seq = [4, 0, 2, 9, 9, 9, 9, 1, 0]
+    stage, subset, amom = pnp.schedule(stages, seq, momentum=True)
+    assert stage.tolist() == [0, 0, 0, 2, 2, 2, 2, 3, 3]
+    assert subset.tolist() == [4, 0, 2, 0, 0, 0, 0, 1, 0]
+    for i in range(1, 10):
+        assert amom[i - 1] == np.float32((i - 1) / (i + 3))
+    assert amom[0] == 0.0
+    _, _, a0 = pnp.schedule(stages, seq, momentum=False)
+    assert not a0.any()
+    with pytest.raises(pnp.PnpError):          # subset id outside its stage's range
+        pnp.schedule([synth.Stage(1, 2, 3)], [0, 3])
+    with pytest.raises(pnp.PnpError):          # subsets without a sequence
+        pnp.schedule([synth.Stage(1, 2, 3)], None)
+    total = C.c_int64(0)
+    arr = (_native.StageC * 1)(_native.StageC(1, 5, 1, 0, 0))
+    i32 = (C.c_int32 * 4)()
+    f32 = (C.c_float * 4)()
+    assert lib.pnp_schedule(arr, 1, None, 1, i32, i32, f32, 4, C.byref(total)) == _native.PNP_EINVAL
+    assert total.value == 5 and "capacity" in pnp.last_error()
+
+
+def test_step_sizes_and_bandwidth_reject_bad_arguments(lib):
+    g = _native.geom(synth.make_geometry(64, 90, 96))
+    st = (_native.StageC * 1)(_native.StageC(3, 5, 1, 0, 0))
+    eta = (C.c_double * 1)()
+    null = C.c_void_p(0)
+    assert lib.pnp_step_sizes(C.byref(g), st, 1, eta, C.c_void_p(256), null) == _native.PNP_EINVAL   # factor 3
+    st[0] = _native.StageC(2, 5, 1, 0, 0)
+    assert lib.pnp_step_sizes(C.byref(g), st, 1, eta, C.c_void_p(4096), null) == _native.PNP_ESTATE
+    out = (C.c_double * 3)()
+    assert lib.pnp_onchip_bandwidth(C.c_void_p(256), 1 << 20, out, null) == _native.PNP_EINVAL
+    assert "needs" in pnp.last_error()
