@@ -318,7 +318,13 @@ int pnp_run_many(const pnp_problem* problems, int n_problems, const pnp_run_para
  *   back    backprojector CTA: G view groups (1..32) of 8 x 4 pixel blocks, or
  *           PNP_BACK_TILE4 | G: G view groups (1..64) of 4 x 4 pixel blocks
  *           (the pixel-driven gather), or PNP_BACK_SCATTER | TS: the
- *           sample-driven scatter on TS x TS tiles, TS in {12, 16, 22, 32}
+ *           sample-driven scatter on TS x TS tiles, TS in {12, 16, 22, 32};
+ *           a gather shape | PNP_BACK_BATCH(BC), BC in {4, 8, 16}, selects the
+ *           batched gather: each thread applies every hat product it computes to
+ *           the residuals of BC images of the batch (the images of one geometry
+ *           share all rays and samples), with at most 512 threads per CTA
+ *           (G x 32 or G x 16 for 8 x 4 or 4 x 4 blocks); its results are bitwise
+ *           those of the same gather shape without PNP_BACK_BATCH
  *   tile    FGP denoiser: side of the shared-memory tile (8..40), or 1 for the
  *           register-resident variant (warp tiles, five iterations per launch)
  * The gather's view groups fix its summation order: results are bitwise
@@ -338,6 +344,7 @@ int pnp_run_many(const pnp_problem* problems, int n_problems, const pnp_run_para
  * pnp_set_launch_shapes pins them (PNP_EINVAL for a shape outside these sets). */
 #define PNP_BACK_TILE4 (1 << 8)
 #define PNP_BACK_SCATTER (1 << 9)
+#define PNP_BACK_BATCH(bc) ((bc) << 16)
 typedef struct {
     int32_t lanes[4];
     int32_t back[4];

@@ -1461,6 +1461,14 @@ int pnp_autotune(const pnp_geom* g, const pnp_stage* stages, int n_stages, const
         for (int G = 1; G <= 16 && G <= nsub; G *= 2) shapes.push_back(G);
         for (int G : {8, 12, 16, 18, 20, 24, 32, 64, nsub, (nsub + 1) / 2})
             if (G >= 8 && G <= 64 && G <= nsub) shapes.push_back(PNP_BACK_TILE4 | G);
+        // batches: the batched gather with 4, 8 or 16 images per thread
+        for (int BC : {4, 8, 16}) {
+            if (BC > 2 * g->batch || g->batch < 2) continue;
+            for (int G : {4, 8, 16, 32})
+                if (G <= nsub) shapes.push_back(PNP_BACK_BATCH(BC) | PNP_BACK_TILE4 | G);
+            for (int G : {2, 4, 8, 16})
+                if (G <= nsub) shapes.push_back(PNP_BACK_BATCH(BC) | G);
+        }
         // (the fixed-point scatter is not a candidate: its error depends on the
         // residual's dynamic range; it runs only where pnp_set_launch_shapes pins it)
         for (int shp : shapes) {
@@ -1545,9 +1553,13 @@ int pnp_set_launch_shapes(const pnp_geom* g, const pnp_launch_shapes* in, void* 
         const int q = in->lanes[k], b = in->back[k];
         if (q != 0 && q != 4 && q != 8 && q != 16) return fail(PNP_EINVAL, "lanes[%d] = %d not in {0, 4, 8, 16}", k, q);
         const int bg = b & 0xff;
+        const int bc = back_batch_of(b);
         const bool scatter = (b & ~0xff) == PNP_BACK_SCATTER && (bg == 12 || bg == 16 || bg == 22 || bg == 32);
+        const int slots = (b & PNP_BACK_TILE4) ? 16 : 32;
+        const bool batch_ok = bc == 0 || bc == 1 || ((bc == 4 || bc == 8 || bc == 16) && bg * slots <= 512);
         const bool ok = b == 0 || scatter ||
-                        ((b & ~(PNP_BACK_TILE4 | 0xff)) == 0 && bg >= 1 && bg <= ((b & PNP_BACK_TILE4) ? 64 : 32));
+                        ((b & ~(PNP_BACK_TILE4 | 0xff | PNP_BACK_BATCH(0xff))) == 0 && bg >= 1 &&
+                         bg <= ((b & PNP_BACK_TILE4) ? 64 : 32) && batch_ok);
         if (!ok) return fail(PNP_EINVAL, "back[%d] = %#x is not a backprojector shape", k, b);
         tu.lanes[k] = q;
         tu.groups[k] = b;

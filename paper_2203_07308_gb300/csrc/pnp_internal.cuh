@@ -171,6 +171,9 @@ struct BackArgs {
 // `groups`: view groups per CTA of the 2x2-block gather (1..16, 0 = heuristic),
 // PNP_BACK_TILE4 | G for 4 x 4-block CTAs, or PNP_BACK_SCATTER | TS for the
 // fixed-point scatter form on TS x TS tiles (TS in {12, 16, 22, 32}).
+// PNP_BACK_BATCH(BC) | (gather shape) selects the batched gather (BC images per
+// thread, BC in {4, 8, 16}; at most 512 threads per CTA).
+inline int back_batch_of(int groups) { return (groups >> 16) & 0xff; }
 cudaError_t launch_backward(const BackArgs& a, cudaStream_t st, int groups = 0);
 cudaError_t launch_backward_multi(const BackArgs* items, int count, cudaStream_t st, int groups = 0);
 

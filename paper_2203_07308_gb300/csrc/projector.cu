@@ -389,6 +389,174 @@ __global__ void __launch_bounds__(1024, 1) k_backward2x2(const BackTable t)
     }
 }
 
+// Batched form of the gather for a class of B images that share one geometry:
+// the rays, their samples and therefore every hat product are the same for all
+// images; only the residuals differ.  A thread (2x2 pixel block, view group g)
+// now covers a chunk of BC images: each (ray, sample) hat product is computed
+// once and applied to the BC residuals (BC x 4 accumulators per thread).  The
+// view, ray and sample order of every accumulator and the fixed-order sum over
+// the G view groups are those of k_backward2x2 with the same TX and G, so the
+// result is bitwise the same as the unbatched gather's.  The view-group sums go
+// through shared memory in rounds of RB images (RB from the host, so that
+// G x RB x slots float4 fit the CTA's shared memory).
+struct BackBatchTable {
+    BackArgs c[kMaxClasses];
+    long begin[kMaxClasses + 1];   // cumulative CTA counts (tiles * chunks of BC images)
+    int count;
+    int rb;                        // images per reduction round
+};
+
+constexpr int kBackBatchThreads = 512;
+
+template <int NWIN, int TX, int BC>
+__global__ void __launch_bounds__(kBackBatchThreads, 1) k_backward_batch(const BackBatchTable t)
+{
+    pdl_begin();
+    const int tx = threadIdx.x, ty = threadIdx.y, g = threadIdx.z, G = blockDim.z;
+    int c = 0;
+#pragma unroll
+    for (int k = 1; k < kMaxClasses; ++k)
+        if (k < t.count && (long)blockIdx.x >= t.begin[k]) c = k;
+    const BackArgs& a = t.c[c];
+    const int nb = (a.ns + 1) / 2;                             // blocks per side
+    const int tiles_x = (nb + TX - 1) / TX;
+    const int tiles_y = (nb + kBack2TileY - 1) / kBack2TileY;
+    const long local = (long)blockIdx.x - t.begin[c];
+    const int tiles = tiles_x * tiles_y;
+    const int chunk = (int)(local / tiles);
+    const int tile = (int)(local - (long)chunk * tiles);
+    const int bx0 = (tile % tiles_x) * TX, by0 = (tile / tiles_x) * kBack2TileY;
+    const int bx = bx0 + tx, by = by0 + ty;
+    const int i0 = chunk * BC;
+    const int ni = min(BC, a.batch - i0);                      // images in this chunk
+    const bool inside = bx < nb && by < nb;
+    const long istride = (long)a.n_sub * a.n_det;              // residual stride between images
+    float acc[BC][4];
+#pragma unroll
+    for (int b = 0; b < BC; ++b) acc[b][0] = acc[b][1] = acc[b][2] = acc[b][3] = 0.0f;
+    if (inside) {
+        const int ix = 2 * bx, iy = 2 * by;
+        const float half = 0.5f * (float)(a.ns - 1);
+        const float cx = (float)ix + 0.5f - half, cy = (float)iy + 0.5f - half;   // centred, level units
+        const int c0 = a.ns / 2;
+        const float px = (float)(ix - c0) + 2.0f, py = (float)(iy - c0) + 2.0f;   // primed frame
+        const float jc = 0.5f * (float)(a.n_det - 1);
+        const float inv_step = 1.0f / a.step;
+        const float rho = 2.12132034f;                           // 1.5 sqrt(2)
+        const int nwin = NWIN > 0 ? NWIN : (int)floorf(2.0f * rho * inv_step) + 1;
+        const float* __restrict__ res = a.res + (long)i0 * istride;
+        for (int vs = g; vs < a.n_sub; vs += G) {
+            const int v = a.first_view + vs * a.view_step;
+            const float4 vp = __ldg(a.view + v);   // cos b, sin b, dso/s, (dso+ddo)/pitch
+            const float along = cx * vp.x + cy * vp.y;
+            const float lat = cy * vp.x - cx * vp.y;
+            const float inv = __fdividef(1.0f, vp.z - along);
+            const float uj = vp.w * lat * inv + jc;
+            const float invp = inv * (1.0f + 2.0f * rho * inv);
+            const float T = (fabsf(lat) + rho) * invp;
+            const float hw = rho * vp.w * fmaf(T, T, 1.0f) * invp * 1.01f + 0.02f;
+            const int jlo = max(0, (int)ceilf(uj - hw));
+            const int jhi = min(a.n_det - 1, (int)floorf(uj + hw));
+            const long base = (long)v * a.n_det;
+            const float* __restrict__ rrow = res + (long)vs * a.n_det;
+            float4 fn = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+            if (jlo <= jhi) fn = __ldg(a.rayf + base + jlo);
+            for (int j = jlo; j <= jhi; ++j) {
+                const float4 f = fn;
+                if (j < jhi) fn = __ldg(a.rayf + base + j + 1);
+                const float ax = px - f.x, ay = py - f.y;
+                const float e = ax * f.w - ay * f.z;
+                const float hwid = 1.5f * (fabsf(f.z) + fabsf(f.w));
+                if (fabsf(e) >= hwid) continue;
+                // the chunk's residuals of this ray, in flight while the hats are computed
+                float r[BC];
+#pragma unroll
+                for (int b = 0; b < BC; ++b) r[b] = b < ni ? __ldg(rrow + b * istride + j) : 0.0f;
+                const float tau = fmaf(ax, f.z, ay * f.w);
+                const float k0 = ceilf(fmaf(tau - hwid, inv_step, -0.5f));
+                const int cnt = (int)(2.0f * hwid * inv_step) + 1;
+                const float t0 = (k0 + 0.5f) * a.step;
+                const float X0 = fmaf(t0, f.z, -ax), Y0 = fmaf(t0, f.w, -ay);
+                const float xa0 = X0 + 0.5f, xb0 = X0 - 0.5f;
+                const float ya0 = Y0 + 0.5f, yb0 = Y0 - 0.5f;
+                const float sx = a.step * f.z, sy = a.step * f.w;
+                float w00 = 0.0f, w10 = 0.0f, w01 = 0.0f, w11 = 0.0f;
+                auto sample = [&](float fm) {
+                    const float hxa = __saturatef(1.0f - fabsf(fmaf(fm, sx, xa0)));
+                    const float hxb = __saturatef(1.0f - fabsf(fmaf(fm, sx, xb0)));
+                    const float hya = __saturatef(1.0f - fabsf(fmaf(fm, sy, ya0)));
+                    const float hyb = __saturatef(1.0f - fabsf(fmaf(fm, sy, yb0)));
+                    w00 = fmaf(hxa, hya, w00);
+                    w10 = fmaf(hxb, hya, w10);
+                    w01 = fmaf(hxa, hyb, w01);
+                    w11 = fmaf(hxb, hyb, w11);
+                };
+                if (NWIN > 0) {
+#pragma unroll
+                    for (int m = 0; m < (NWIN > 2 ? NWIN - 2 : 1); ++m) sample((float)m);
+                    if (cnt > NWIN - 2) sample((float)(NWIN - 2));
+                    if (cnt > NWIN - 1) sample((float)(NWIN - 1));
+                } else {
+                    for (int m = 0; m < min(cnt, nwin); ++m) sample((float)m);
+                }
+#pragma unroll
+                for (int b = 0; b < BC; ++b) {
+                    acc[b][0] = fmaf(w00, r[b], acc[b][0]);
+                    acc[b][1] = fmaf(w10, r[b], acc[b][1]);
+                    acc[b][2] = fmaf(w01, r[b], acc[b][2]);
+                    acc[b][3] = fmaf(w11, r[b], acc[b][3]);
+                }
+            }
+        }
+    }
+    // view-group sums in rounds of RB images: part[g][k][slot]
+    extern __shared__ float4 part[];
+    constexpr int kSlots = TX * kBack2TileY;
+    const int slot = ty * TX + tx;
+    const int RB = t.rb;
+    const int nthr = kSlots * G;
+    const int lt = (g * kBack2TileY + ty) * TX + tx;
+    const int s = a.s;
+    for (int b0 = 0; b0 < ni; b0 += RB) {
+        if (b0 > 0) __syncthreads();
+#pragma unroll
+        for (int b = 0; b < BC; ++b)
+            if (b >= b0 && b < b0 + RB)
+                part[(g * RB + (b - b0)) * kSlots + slot] = make_float4(acc[b][0], acc[b][1], acc[b][2], acc[b][3]);
+        __syncthreads();
+        for (int idx = lt; idx < RB * kSlots; idx += nthr) {
+            const int k = idx / kSlots, sl = idx - k * kSlots;
+            const int inst = i0 + b0 + k;
+            const int obx = bx0 + sl % TX, oby = by0 + sl / TX;
+            if (b0 + k >= ni || obx >= nb || oby >= nb) continue;
+            float s00 = 0.0f, s10 = 0.0f, s01 = 0.0f, s11 = 0.0f;
+            for (int q = 0; q < G; ++q) {
+                const float4 pq = part[(q * RB + k) * kSlots + sl];
+                s00 += pq.x; s10 += pq.y; s01 += pq.z; s11 += pq.w;
+            }
+            const float vals[4] = {a.scale * s00, a.scale * s10, a.scale * s01, a.scale * s11};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int ix = 2 * obx + (q & 1), iy = 2 * oby + (q >> 1);
+                if (ix >= a.ns || iy >= a.ns) continue;
+                if (a.mode == kBackRaw) {
+                    a.out[((long)inst * a.ns + iy) * a.ns + ix] = vals[q];
+                    continue;
+                }
+                for (int bb = 0; bb < s; ++bb) {
+                    const long row = ((long)inst * a.n + (long)iy * s + bb) * a.n + (long)ix * s;
+                    for (int aa = 0; aa < s; ++aa) {
+                        if (a.mode == kBackGradFine)
+                            a.out[row + aa] = vals[q];
+                        else
+                            a.out[row + aa] = __ldg(a.y + row + aa) - a.eta * vals[q];
+                    }
+                }
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ transpose A_s^T, scatter form
 // CTA = one TS x TS tile of the level image of one instance, all views of the
 // subset.  Every sample of every ray that can touch the tile is splatted with
@@ -801,9 +969,67 @@ bool scatter_usable(const BackArgs* items, int count, int nt)
 }
 }  // namespace
 
+namespace {
+template <int BC>
+cudaError_t batch_launch(const BackBatchTable& t, int TX, bool half_step, dim3 grd, dim3 blk, size_t smem,
+                         cudaStream_t st)
+{
+    if (TX == 4)
+        return half_step ? launch_pdl(k_backward_batch<9, 4, BC>, grd, blk, smem, st, t)
+                         : launch_pdl(k_backward_batch<0, 4, BC>, grd, blk, smem, st, t);
+    return half_step ? launch_pdl(k_backward_batch<9, kBack2TileX, BC>, grd, blk, smem, st, t)
+                     : launch_pdl(k_backward_batch<0, kBack2TileX, BC>, grd, blk, smem, st, t);
+}
+
+// The batched gather: BC in {4, 8, 16} images per thread, TX x 4 blocks x G view
+// groups per CTA (at most 512 threads).
+cudaError_t launch_backward_batch(const BackArgs* items, int count, cudaStream_t st, int groups)
+{
+    const int BC = back_batch_of(groups);
+    const int TX = (groups & PNP_BACK_TILE4) ? 4 : kBack2TileX;
+    int G = groups & 0xff;
+    BackBatchTable t{};
+    t.count = count;
+    t.begin[0] = 0;
+    long threads1 = 0;
+    int min_views = 1 << 30;
+    bool half_step = true;
+    for (int c = 0; c < count; ++c) {
+        t.c[c] = items[c];
+        const int nb = (items[c].ns + 1) / 2;
+        const int tiles = div_up(nb, TX) * div_up(nb, kBack2TileY);
+        const int chunks = div_up(items[c].batch, BC);
+        t.begin[c + 1] = t.begin[c] + (long)tiles * chunks;
+        threads1 += (long)tiles * chunks * TX * kBack2TileY;
+        min_views = min(min_views, items[c].n_sub);
+        half_step = half_step && items[c].step == 0.5f;
+    }
+    const int gmax = kBackBatchThreads / (TX * kBack2TileY);
+    if (G < 1 || G > gmax) {   // about two waves of 1024 threads per SM
+        G = 1;
+        const long wave = 2L * device_sm_count() * 1024;
+        while (G * 2 <= gmax && threads1 * G < wave && G * 2 <= min_views) G *= 2;
+    }
+    const int slots = TX * kBack2TileY;
+    t.rb = max(1, min(BC, (int)(32768 / ((long)G * slots * sizeof(float4)))));
+    const size_t smem = (size_t)G * t.rb * slots * sizeof(float4);
+    dim3 blk(TX, kBack2TileY, G), grd((unsigned)t.begin[count]);
+    cudaError_t e;
+    switch (BC) {
+        case 4: e = batch_launch<4>(t, TX, half_step, grd, blk, smem, st); break;
+        case 8: e = batch_launch<8>(t, TX, half_step, grd, blk, smem, st); break;
+        default: e = batch_launch<16>(t, TX, half_step, grd, blk, smem, st); break;
+    }
+    if (e != cudaSuccess) return e;
+    return counted();
+}
+}  // namespace
+
 cudaError_t launch_backward_multi(const BackArgs* items, int count, cudaStream_t st, int groups)
 {
     if (count < 1 || count > kMaxClasses) return cudaErrorInvalidValue;
+    if (!(groups & PNP_BACK_SCATTER) && back_batch_of(groups) > 1)
+        return launch_backward_batch(items, count, st, groups);
     if (groups & PNP_BACK_SCATTER) {
         const int ts = groups & 0xff;
         const int nt = ts >= 22 ? 512 : 256;

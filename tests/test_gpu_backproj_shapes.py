@@ -28,9 +28,18 @@ GEOMS = {
 }
 T4 = 1 << 8     # CTAs of 4 x 4 pixel blocks
 SC = 1 << 9     # the fixed-point scatter on square tiles
+
+
+def BATCH(bc):  # the batched gather: bc images per thread
+    return bc << 16
+
+
 SHAPES = {**{f"groups{G}": G for G in (1, 2, 4, 8, 16, 32)},
           **{f"tile4_groups{G}": T4 | G for G in (7, 16, 45, 64)},
-          **{f"scatter{TS}": SC | TS for TS in (12, 16, 22, 32)}}
+          **{f"scatter{TS}": SC | TS for TS in (12, 16, 22, 32)},
+          "batch4_groups4": BATCH(4) | 4, "batch8_tile4_groups16": BATCH(8) | T4 | 16,
+          "batch16_tile4_groups32": BATCH(16) | T4 | 32, "batch16_groups8": BATCH(16) | 8,
+          "batch4_tile4_groups3": BATCH(4) | T4 | 3}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -97,7 +106,7 @@ def test_backprojection_every_shape(name, shape):
 
 
 @pytest.mark.parametrize("shape", ["groups1", "groups16", "tile4_groups7", "tile4_groups64", "scatter12",
-                                   "scatter32"])
+                                   "scatter32", "batch4_groups4", "batch16_tile4_groups32"])
 @pytest.mark.parametrize("name,s,P", [("c1", 2, 5), ("ragged", 1, 3), ("ragged", 2, 1), ("step03", 4, 2)])
 def test_gradient_and_step_epilogues(name, s, P, shape):
     """Gradient on the fine grid (U = S^T) and, through a one-iteration PGD run,
@@ -144,6 +153,41 @@ def test_full_size_256_every_shape():
             assert rel(host(out)[0], refs[s]) < TOL, (shape, s, rel(host(out)[0], refs[s]))
 
 
+@pytest.mark.parametrize("unbatched", [8, T4 | 16, T4 | 3, 2])
+@pytest.mark.parametrize("bc", [4, 8, 16])
+def test_batched_gather_bitwise_equals_the_gather(bc, unbatched):
+    """The batched gather computes every hat product once for BC images and keeps,
+    per image, the view, ray and sample order and the view-group sum of the
+    unbatched gather with the same CTA shape: bitwise equal outputs, on a batch
+    that leaves a ragged last chunk (5 images) and at two levels, for the raw
+    backprojection, the fine-grid gradient and the fused step."""
+    import torch
+    g = synth.make_geometry(64, 30, 96, batch=5)
+    rng = np.random.default_rng(bc)
+    base = pinned(g, unbatched)
+    bat = pinned(g, BATCH(bc) | unbatched)
+    for s, P, p in ((1, 3, 2), (2, 1, 0)):
+        ns = g.n // s
+        y = f32(rng.standard_normal((g.batch, pnp.subset_views(g, p, P), g.n_det)))
+        o1, o2 = empty(g.batch, ns, ns), empty(g.batch, ns, ns)
+        base.backproject(s, dev(y), o1, p, P)
+        bat.backproject(s, dev(y), o2, p, P)
+        assert np.array_equal(host(o1), host(o2)), (s, P)
+    x = dev(rng.random((g.batch, g.n, g.n)))
+    b = dev(rng.standard_normal((g.batch, g.n_views, g.n_det)))
+    o1, o2 = empty(g.batch, g.n, g.n), empty(g.batch, g.n, g.n)
+    base.sketch_grad(2, x, b, o1, 1, 3)
+    bat.sketch_grad(2, x, b, o2, 1, 3)
+    assert np.array_equal(host(o1), host(o2))
+    stages = [synth.Stage(2, 2, 3), synth.Stage(1, 2, 1)]
+    outs = []
+    for plan in (base, bat):
+        xx = x.clone()
+        plan.run(stages, [1e-3, 1e-3], [0, 2, 0, 0], b, xx, tv_iters=5, lam=0.02, momentum=True)
+        outs.append(host(xx))
+    assert np.array_equal(outs[0], outs[1])
+
+
 def test_autotune_never_picks_the_scatter():
     """The autotuner chooses among the gather's shapes only, also on the 16 x 512^2
     batch where the pinned scatter measured faster: the default product path stays
@@ -166,7 +210,7 @@ def test_full_size_512_batch_scatter_and_gather():
     nsub = pnp.subset_views(g, 5, 12)
     y = f32(np.random.default_rng(41).standard_normal((g.batch, nsub, g.n_det)))
     refs = {i: oracle.backproject(g, 1, y[i], 5, 12) for i in (0, 11)}
-    for shape in (SC | 32, T4 | 16):
+    for shape in (SC | 32, T4 | 16, BATCH(16) | T4 | 16, BATCH(8) | 8):
         plan = pinned(g, shape)
         out = empty(g.batch, g.n, g.n)
         plan.backproject(1, dev(y), out, 5, 12)
@@ -182,6 +226,8 @@ def test_launch_shapes_validation():
     for bad in (dict(back=(33, 0, 0, 0)), dict(back=(T4 | 65, 0, 0, 0)), dict(back=(T4, 0, 0, 0)),
                 dict(back=(-1, 0, 0, 0)), dict(back=(SC | 4, 0, 0, 0)), dict(back=(SC | T4 | 16, 0, 0, 0)),
                 dict(back=(SC | 24, 0, 0, 0)), dict(lanes=(2, 0, 0, 0)),
+                dict(back=(BATCH(3) | 4, 0, 0, 0)), dict(back=(BATCH(16) | 32, 0, 0, 0)),
+                dict(back=(BATCH(16) | SC | 16, 0, 0, 0)), dict(back=(BATCH(4) | T4 | 33, 0, 0, 0)),
                 dict(tile=50), dict(tile=2), dict(tile=7)):
         with pytest.raises(pnp.PnpError):
             plan.set_launch_shapes(**bad)
