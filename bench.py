@@ -74,6 +74,12 @@ def parse():
                          'e.g. \'{"lanes": [16, 8, 4, 0], "back": [272, 280, 264, 0], "tile": 22}\' '
                          '(for profiler runs, whose timing would mislead the autotuner)')
     ap.add_argument("--workload", default=WORKLOAD, help="synth.workloads() key of the timed step")
+    ap.add_argument("--eta", type=float, default=None,
+                    help="one fixed step size for every stage instead of the library's eta_k = 1/L_k "
+                         "(profiler runs: kernel times do not depend on it)")
+    ap.add_argument("--stage-iters", type=int, default=None,
+                    help="cut every stage of the schedule to this many iterations (profiler captures of "
+                         "single kernels, so that few launches precede the captured one)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the 256^2, mixed, differentiable and paper-geometry comparisons")
     ap.add_argument("--profile", action="store_true",
@@ -624,6 +630,9 @@ def run_native(args, rank, world):
     build.build()
     pnp.load()
     wl = workload(args.workload)
+    if args.stage_iters is not None:
+        wl = dataclasses.replace(wl, stages=[dataclasses.replace(s_, iters=min(s_.iters, args.stage_iters))
+                                             for s_ in wl.stages])
     g = wl.geom
     B = g.batch
     dev = torch.device("cuda", local)
@@ -639,7 +648,7 @@ def run_native(args, rank, world):
     # by the library, and the launch shapes chosen by its autotuner for this schedule
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    eta = plan.step_sizes(wl.stages)
+    eta = plan.step_sizes(wl.stages) if args.eta is None else [args.eta] * len(wl.stages)
     setup_ms = 1000 * (time.perf_counter() - t0)
     t0 = time.perf_counter()
     if args.shapes:
@@ -658,21 +667,23 @@ def run_native(args, rank, world):
         plan.run(wl.stages, eta, seq, d_b, d_x.zero_(), graph=use_graph, **kw)
 
     launches_setup = pnp.launch_count()
-    for _ in range(max(args.warmup, 3)):
+    warm = args.warmup if args.profile else max(args.warmup, 3)
+    for _ in range(warm):
         step()
     torch.cuda.synchronize()
     barrier(world)
 
     if args.profile:
+        launches_warm = pnp.launch_count()
         torch.cuda.nvtx.range_push("timed")
         for _ in range(args.steps):
             step()
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         if rank == 0:
-            print(json.dumps({"profile": True, "steps": args.steps, "launch_shapes": plan.launch_shapes(),
-                              "launches_per_step": (pnp.launch_count() - launches_setup) //
-                              (args.steps + max(args.warmup, 3))}))
+            print(json.dumps({"profile": True, "steps": args.steps, "warmup": warm,
+                              "launch_shapes": plan.launch_shapes(), "launches_before_timed": launches_warm,
+                              "launches_per_step": (pnp.launch_count() - launches_warm) // max(args.steps, 1)}))
         return
 
     # ---- timed region: K steps, L2 flushed before each, device time by CUDA events
