@@ -1097,13 +1097,17 @@ int run_many_impl(const pnp_problem* pb_in, int np, const pnp_run_params* params
     cudaStream_t st = S(stream);
     const bool do_tv = pr.tv_iters > 0 && pr.lambda > 0.0f;
     // one denoiser launch covers every class, so the classes share its variant:
-    // the register-resident one only when every class was tuned to it
-    bool all_warp = true;
-    for (int c = 0; c < np; ++c) all_warp = all_warp && ps[c].tuned.tile == kTvTileWarp;
+    // a register-resident one only when every class was tuned to it (the strips
+    // then take the first class's CTA height)
+    bool same_family = true;
+    for (int c = 0; c < np; ++c) same_family = same_family && tv_family(ps[c].tuned.tile) == tv_family(ps[0].tuned.tile);
+    const bool all_warp = same_family && ps[0].tuned.tile == kTvTileWarp;
     for (int c = 0; c < np; ++c) {
-        if (!all_warp && ps[c].tuned.tile == kTvTileWarp) ps[c].tuned.tile = 0;
+        if (!same_family && tv_family(ps[c].tuned.tile) != 0) ps[c].tuned.tile = 0;
+        if (same_family && tv_is_strip(ps[0].tuned.tile)) ps[c].tuned.tile = ps[0].tuned.tile;
         if (do_tv) ps[c].tv_parts = tile_tv_parts_for(pb[c].geom.n, pb[c].geom.batch, ps[c].tuned.tile);
     }
+    const bool all_register = same_family && tv_family(ps[0].tuned.tile) != 0;
     long max_total = 0;
     for (const auto& q : ps) max_total = std::max(max_total, q.total);
 
@@ -1113,7 +1117,8 @@ int run_many_impl(const pnp_problem* pb_in, int np, const pnp_run_params* params
     // the denoiser's last launch also writes the coefficient image of the next
     // iteration's level (full grid, or the 2x pooled sketch) when that iteration
     // is a mini-batch one (it then needs no coefficient-image kernel)
-    const bool fuse_quad = do_tv && !all_warp && fuse_quad_enabled();
+    const bool fuse_quad = do_tv && !all_register && fuse_quad_enabled();
+    (void)all_warp;
     auto issue = [&]() -> int {
         int e0 = PNP_OK;
         for (int c = 0; c < np; ++c) {
@@ -1496,14 +1501,15 @@ int pnp_autotune(const pnp_geom* g, const pnp_stage* stages, int n_stages, const
         const int T0 = tile_tv_tile(g->n, g->batch);
         const int iters = std::min(pr.tv_iters, 20);   // up to two launches, the last one with the ring
         float best = 1e30f;
-        for (int T : {T0 - 6, T0 - 4, T0 - 2, T0, T0 + 2, T0 + 4, T0 + 6, 16, 24, 32, kTvTileWarp}) {
+        for (int T : {T0 - 6, T0 - 4, T0 - 2, T0, T0 + 2, T0 + 4, T0 + 6, 16, 24, 32, kTvTileWarp, kTvTileStrip8,
+                      kTvTileStrip12}) {
             if (rc != PNP_OK) break;
-            if (T != kTvTileWarp && (T < 8 || T > 40)) continue;
+            if (T != kTvTileWarp && !tv_is_strip(T) && (T < 8 || T > 40)) continue;
             TvItem it{};
             it.z = y; it.xprev = z; it.y = scratch + img; it.xin = scratch;
             it.state_a = tvb; it.state_b = tvb + 4 * img;
             it.n = g->n; it.batch = g->batch; it.tile = T; it.amom = 0.5f;
-            const bool own_prep = full_minibatch && T == kTvTileWarp;
+            const bool own_prep = full_minibatch && tv_family(T) != 0;
             if (fused && !own_prep) {
                 it.quad = (float4*)(ws + l1.off_quad);
                 it.qw = l1.qw;
@@ -1564,8 +1570,8 @@ int pnp_set_launch_shapes(const pnp_geom* g, const pnp_launch_shapes* in, void* 
         tu.lanes[k] = q;
         tu.groups[k] = b;
     }
-    if (in->tile != 0 && in->tile != kTvTileWarp && (in->tile < 8 || in->tile > 40))
-        return fail(PNP_EINVAL, "tile %d is neither 0, 1 nor in [8, 40]", in->tile);
+    if (in->tile != 0 && in->tile != kTvTileWarp && !tv_is_strip(in->tile) && (in->tile < 8 || in->tile > 40))
+        return fail(PNP_EINVAL, "tile %d is neither 0, 1, 2, 3 nor in [8, 40]", in->tile);
     tu.tile = in->tile;
     reg_set_tuned(d_ws, tu);
     return PNP_OK;

@@ -471,6 +471,248 @@ __global__ void __launch_bounds__(32 * kWarpTvWarps) k_tv_warp(const WarpTvArgs 
     }
 }
 
+// ------------------------------------------------------------------ register-resident FGP strips
+// The same temporal blocking as the tiles above, organised so that almost every
+// neighbour is in a register: a CTA owns a region of 64 columns x 8W rows (W
+// warps stacked vertically, W = 8 or 12), lane l of warp w holds columns 2l and 2l+1 of the
+// warp's 8 rows (z in shared memory; r and p in registers).  Vertical
+// neighbours inside a warp are the lane's own registers, horizontal ones the
+// lane's other column or the adjacent lane's (one shuffle per row and phase);
+// the rows where two warps meet go through a 64-float shared array per warp,
+// once per phase.  K <= 10 iterations per launch; the output tile is the region
+// minus K + 1 columns/rows on the left/top and K on the right/bottom.
+// Edge rules without per-pixel tests: the dual step's differences are set to
+// zero outside rows/columns [0, n-2], so p and r stay exactly zero on the last
+// row/column and on everything above/left of the image, which is what L(p)
+// subtracts there (the same values as the tests of the other variants give);
+// other pixels outside the image hold values no output depends on.
+constexpr int kStripK = 10;                                  // FGP iterations per launch (at most)
+constexpr int kStripR = 8;                                   // rows per warp
+constexpr int kStripWO = 64 - 2 * kStripK - 1;               // output columns per tile
+
+struct StripTvClass {
+    const float* z; const float* sin; float* sout;          // state planes [4][batch][n][n]: r1 r2 p1 p2
+    float* xprev; float* y; const float* xtrue; double* mse_part;
+    const float* xin;                                        // x_{i-1} (nullptr: xprev)
+    int n, tiles_x, tiles;
+    long plane;
+    float amom;
+};
+
+struct StripTvArgs {
+    StripTvClass c[kMaxClasses];
+    long begin[kMaxClasses + 1];                             // cumulative CTAs (batch * tiles)
+    int count, K, first, last, W;
+    float lambda, alpha;
+    float mom[kStripK];
+};
+
+template <bool LAST, int W>
+__global__ void __launch_bounds__(32 * W) k_tv_strip(const StripTvArgs t)
+{
+    pdl_begin();
+    constexpr int R = kStripR;
+    constexpr unsigned kAll = 0xffffffffu;
+    const int lane = threadIdx.x, w = threadIdx.y;
+    int cls = 0;
+#pragma unroll
+    for (int k = 1; k < kMaxClasses; ++k)
+        if (k < t.count && (long)blockIdx.x >= t.begin[k]) cls = k;
+    const StripTvClass& a = t.c[cls];
+    const long local = (long)blockIdx.x - t.begin[cls];
+    const int inst = (int)(local / a.tiles);
+    const int tile = (int)(local - (long)inst * a.tiles);
+    const int n = a.n;
+    const int HO = W * R - 2 * kStripK - 1;                 // output rows per tile
+    const int r0 = (tile / a.tiles_x) * HO, c0 = (tile % a.tiles_x) * kStripWO;
+    const int rb = r0 - kStripK - 1 + w * R;                 // image row of register row 0
+    const int ja = c0 - kStripK - 1 + 2 * lane, jb = ja + 1; // this lane's columns
+    const long img = (long)inst * n * n;
+    extern __shared__ float2 strip_sm[];
+    float2* zs = strip_sm;                                   // [W * R][32]  (z of columns 2l, 2l+1)
+    float2* up = zs + W * R * 32;                            // [W][32]      r1 of each warp's last row
+    float2* dn = up + W * 32;                                // [W][32]      x_tmp of each warp's first row
+    const bool ina = ja >= 0 && ja < n, inb = jb >= 0 && jb < n;
+    // the dual step's differences vanish outside rows / columns [0, n-2]
+    const float mca = (ja >= 0 && ja < n - 1) ? 1.0f : 0.0f;
+    const float mcb = (jb >= 0 && jb < n - 1) ? 1.0f : 0.0f;
+    float mrow[R];
+    float r1a[R], r2a[R], p1a[R], p2a[R], r1b[R], r2b[R], p1b[R], p2b[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+        const int i = rb + m;
+        mrow[m] = (i >= 0 && i < n - 1) ? 1.0f : 0.0f;
+        const bool ri = i >= 0 && i < n;
+        const long g = img + (long)i * n;
+        float za = 0.0f, zb = 0.0f;
+        r1a[m] = r2a[m] = p1a[m] = p2a[m] = r1b[m] = r2b[m] = p1b[m] = p2b[m] = 0.0f;
+        if (ri && ina) {
+            za = __ldg(a.z + g + ja);
+            if (!t.first) {
+                r1a[m] = __ldg(a.sin + g + ja);
+                r2a[m] = __ldg(a.sin + a.plane + g + ja);
+                p1a[m] = __ldg(a.sin + 2 * a.plane + g + ja);
+                p2a[m] = __ldg(a.sin + 3 * a.plane + g + ja);
+            }
+        }
+        if (ri && inb) {
+            zb = __ldg(a.z + g + jb);
+            if (!t.first) {
+                r1b[m] = __ldg(a.sin + g + jb);
+                r2b[m] = __ldg(a.sin + a.plane + g + jb);
+                p1b[m] = __ldg(a.sin + 2 * a.plane + g + jb);
+                p2b[m] = __ldg(a.sin + 3 * a.plane + g + jb);
+            }
+        }
+        zs[(w * R + m) * 32 + lane] = make_float2(za, zb);
+    }
+    up[w * 32 + lane] = make_float2(r1a[R - 1], r1b[R - 1]);
+    __syncthreads();
+    const float lam = t.lambda, inv8l = 1.0f / (8.0f * t.lambda);
+    const int wup = w > 0 ? w - 1 : 0, wdn = w + 1 < W ? w + 1 : w;
+    for (int k = 0; k < t.K; ++k) {
+        // x_tmp = z - lambda L(r)
+        float xa[R], xb[R];
+        {
+            const float2 u = up[wup * 32 + lane];
+            float ua = u.x, ub = u.y;
+#pragma unroll
+            for (int m = 0; m < R; ++m) {
+                const float left = __shfl_up_sync(kAll, r2b[m], 1);
+                const float2 z2 = zs[(w * R + m) * 32 + lane];
+                float la = r1a[m] + r2a[m];
+                la -= ua;
+                la -= left;
+                float lb = r1b[m] + r2b[m];
+                lb -= ub;
+                lb -= r2a[m];
+                xa[m] = z2.x - lam * la;
+                xb[m] = z2.y - lam * lb;
+                ua = r1a[m];
+                ub = r1b[m];
+            }
+        }
+        dn[w * 32 + lane] = make_float2(xa[0], xb[0]);
+        __syncthreads();
+        // dual step, isotropic projection, momentum
+        const float mo = t.mom[k];
+        {
+            const float2 d = dn[wdn * 32 + lane];
+#pragma unroll
+            for (int m = 0; m < R; ++m) {
+                const float da = m + 1 < R ? xa[m + 1 < R ? m + 1 : m] : d.x;
+                const float db = m + 1 < R ? xb[m + 1 < R ? m + 1 : m] : d.y;
+                const float right = __shfl_down_sync(kAll, xa[m], 1);
+                const float g1a = (xa[m] - da) * mrow[m];
+                const float g1b = (xb[m] - db) * mrow[m];
+                const float g2a = (xa[m] - xb[m]) * mca;
+                const float g2b = (xb[m] - right) * mcb;
+                float pa = fmaf(g1a, inv8l, r1a[m]);
+                float pc = fmaf(g2a, inv8l, r2a[m]);
+                float nrm2 = fmaf(pa, pa, pc * pc);
+                if (nrm2 > 1.0f) {
+                    const float sc = rsqrtf(nrm2);
+                    pa *= sc;
+                    pc *= sc;
+                }
+                r1a[m] = fmaf(mo, pa - p1a[m], pa);
+                r2a[m] = fmaf(mo, pc - p2a[m], pc);
+                p1a[m] = pa;
+                p2a[m] = pc;
+                pa = fmaf(g1b, inv8l, r1b[m]);
+                pc = fmaf(g2b, inv8l, r2b[m]);
+                nrm2 = fmaf(pa, pa, pc * pc);
+                if (nrm2 > 1.0f) {
+                    const float sc = rsqrtf(nrm2);
+                    pa *= sc;
+                    pc *= sc;
+                }
+                r1b[m] = fmaf(mo, pa - p1b[m], pa);
+                r2b[m] = fmaf(mo, pc - p2b[m], pc);
+                p1b[m] = pa;
+                p2b[m] = pc;
+            }
+        }
+        up[w * 32 + lane] = make_float2(r1a[R - 1], r1b[R - 1]);
+        __syncthreads();
+    }
+    // output pixels of this thread: rows [r0, r0 + HO), columns [c0, c0 + WO), inside the image
+    const bool oa = ina && ja >= c0 && ja < c0 + kStripWO, ob = inb && jb >= c0 && jb < c0 + kStripWO;
+    if constexpr (!LAST) {
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            const int i = rb + m;
+            if (i < r0 || i >= r0 + HO || i >= n) continue;
+            const long g = img + (long)i * n;
+            if (oa) {
+                a.sout[g + ja] = r1a[m];
+                a.sout[a.plane + g + ja] = r2a[m];
+                a.sout[2 * a.plane + g + ja] = p1a[m];
+                a.sout[3 * a.plane + g + ja] = p2a[m];
+            }
+            if (ob) {
+                a.sout[g + jb] = r1b[m];
+                a.sout[a.plane + g + jb] = r2b[m];
+                a.sout[2 * a.plane + g + jb] = p1b[m];
+                a.sout[3 * a.plane + g + jb] = p2b[m];
+            }
+        }
+    } else {
+        // x = z - lambda L(p), relaxation, momentum, squared error
+        up[w * 32 + lane] = make_float2(p1a[R - 1], p1b[R - 1]);
+        __syncthreads();
+        const float2 u = up[wup * 32 + lane];
+        float ua = u.x, ub = u.y;
+        double e2 = 0.0;
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            const float left = __shfl_up_sync(kAll, p2b[m], 1);
+            const float2 z2 = zs[(w * R + m) * 32 + lane];
+            float la = p1a[m] + p2a[m];
+            la -= ua;
+            la -= left;
+            float lb = p1b[m] + p2b[m];
+            lb -= ub;
+            lb -= p2a[m];
+            ua = p1a[m];
+            ub = p1b[m];
+            const int i = rb + m;
+            if (i < r0 || i >= r0 + HO || i >= n) continue;
+            const long g = img + (long)i * n;
+            const float xva[2] = {z2.x - lam * la, z2.y - lam * lb};
+            const float zv[2] = {z2.x, z2.y};
+            const bool ov[2] = {oa, ob};
+            const int jv[2] = {ja, jb};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (!ov[h]) continue;
+                const long gg = g + jv[h];
+                const float xi = (1.0f - t.alpha) * zv[h] + t.alpha * xva[h];
+                if (a.y) {
+                    const float xp = a.xin ? a.xin[gg] : a.xprev[gg];
+                    a.y[gg] = xi + a.amom * (xi - xp);
+                }
+                a.xprev[gg] = xi;
+                if (a.xtrue) {
+                    const double dd = (double)xi - (double)__ldg(a.xtrue + gg);
+                    e2 += dd * dd;
+                }
+            }
+        }
+        if (a.mse_part) {
+            __shared__ double red[16];
+            for (int off = 16; off > 0; off >>= 1) e2 += __shfl_xor_sync(kAll, e2, off);
+            if (lane == 0) red[w] = e2;
+            __syncthreads();
+            if (w == 0 && lane == 0) {
+                double v = 0.0;
+                for (int q = 0; q < W; ++q) v += red[q];
+                a.mse_part[(long)inst * a.tiles + tile] = v;
+            }
+        }
+    }
+}
+
 inline cudaError_t counted(cudaError_t e = cudaGetLastError())
 {
     g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -548,7 +790,7 @@ int resolve_tile(int tile, int n, int batch)
 
 bool tv_fuses_quad(int tile, int n, int batch, int qs)
 {
-    if (tile == kTvTileWarp) return false;
+    if (tile == kTvTileWarp || tv_is_strip(tile)) return false;
     if (qs == 1) return true;
     return qs == 2 && n % 2 == 0 && resolve_tile(tile, n, batch) % 2 == 0;
 }
@@ -557,6 +799,10 @@ int tile_tv_parts_for(int n, int batch, int tile)
 {
     if (tile == kTvTileWarp)
         return ((n + kWarpTvWV - 1) / kWarpTvWV) * ((n + kWarpTvHV - 1) / kWarpTvHV);
+    if (tv_is_strip(tile)) {
+        const int ho = tv_strip_warps(tile) * kStripR - 2 * kStripK - 1;
+        return ((n + kStripWO - 1) / kStripWO) * ((n + ho - 1) / ho);
+    }
     const int T = resolve_tile(tile, n, batch);
     return ((n + T - 1) / T) * ((n + T - 1) / T);
 }
@@ -607,6 +853,58 @@ cudaError_t launch_tv_warp_multi(const TvItem* items, int count, float lambda, i
 }
 }  // namespace
 
+// Register-resident strips: 64 x 8W regions, up to kStripK iterations per launch.
+cudaError_t launch_tv_strip_multi(const TvItem* items, int count, float lambda, int iters, float alpha,
+                                  const std::vector<float>& mom, cudaStream_t st)
+{
+    StripTvArgs a{};
+    a.count = count;
+    a.lambda = lambda;
+    a.alpha = alpha;
+    a.W = tv_strip_warps(items[0].tile);
+    a.begin[0] = 0;
+    const int ho = a.W * kStripR - 2 * kStripK - 1;
+    for (int c = 0; c < count; ++c) {
+        const TvItem& it = items[c];
+        if (iters > kStripK && (!it.state_a || !it.state_b)) return cudaErrorInvalidValue;
+        StripTvClass& sc = a.c[c];
+        sc.z = it.z; sc.xprev = it.xprev; sc.y = it.y; sc.xtrue = it.xtrue; sc.mse_part = it.mse_part;
+        sc.xin = it.xin;
+        sc.n = it.n;
+        sc.tiles_x = (it.n + kStripWO - 1) / kStripWO;
+        sc.tiles = sc.tiles_x * ((it.n + ho - 1) / ho);
+        sc.plane = (long)it.batch * it.n * it.n;
+        sc.amom = it.amom;
+        a.begin[c + 1] = a.begin[c] + (long)sc.tiles * it.batch;
+    }
+    const dim3 grd((unsigned)a.begin[count]), blk(32, a.W);
+    const size_t smem = (size_t)a.W * 32 * (kStripR + 2) * sizeof(float2);
+    int k0 = 0, pass = 0;
+    cudaError_t e = cudaSuccess;
+    do {
+        const int K = std::min(kStripK, iters - k0);
+        a.K = K;
+        a.first = k0 == 0;
+        a.last = k0 + K == iters;
+        for (int c = 0; c < count; ++c) {
+            a.c[c].sin = k0 == 0 ? nullptr : (pass % 2 == 1 ? items[c].state_a : items[c].state_b);
+            a.c[c].sout = a.last ? nullptr : (pass % 2 == 0 ? items[c].state_a : items[c].state_b);
+        }
+        for (int k = 0; k < K; ++k) a.mom[k] = mom[k0 + k];
+        if (a.W == 8)
+            e = a.last ? launch_pdl(k_tv_strip<true, 8>, grd, blk, smem, st, a)
+                       : launch_pdl(k_tv_strip<false, 8>, grd, blk, smem, st, a);
+        else
+            e = a.last ? launch_pdl(k_tv_strip<true, 12>, grd, blk, smem, st, a)
+                       : launch_pdl(k_tv_strip<false, 12>, grd, blk, smem, st, a);
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        if (e != cudaSuccess) return e;
+        k0 += K;
+        ++pass;
+    } while (k0 < iters);
+    return e;
+}
+
 int tile_tv_parts(int n, int batch) { return tile_tv_parts_for(n, batch, 0); }
 
 cudaError_t launch_tv_tiled_multi(const TvItem* items, int count, float lambda, int iters, float alpha,
@@ -634,6 +932,7 @@ cudaError_t launch_tv_tiled_multi(const TvItem* items, int count, float lambda, 
         tt = tn;
     }
     if (items[0].tile == kTvTileWarp) return launch_tv_warp_multi(items, count, lambda, iters, alpha, mom, st);
+    if (tv_is_strip(items[0].tile)) return launch_tv_strip_multi(items, count, lambda, iters, alpha, mom, st);
     TileTvArgs a{};
     a.count = count;
     a.lambda = lambda;

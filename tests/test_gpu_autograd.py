@@ -168,34 +168,117 @@ def test_unrolled_autograd_matches_oracle_and_fd(keep_z):
     assert abs(fdl - gl) < 2e-2 * max(1.0, abs(fdl)), (fdl, gl)
 
 
-def test_differentiable_workload_full_size():
-    """8 x 256x256, 360 views x 512 bins, 10 unrolled 2x-sketched iterations:
-    the gradient w.r.t. x0 of two instances against the oracle's reverse mode."""
+_C4 = {}
+
+
+def _c4_problem():
+    """The differentiable workload (8 x 256x256, 360 views x 512 bins, 10 unrolled
+    2x-sketched iterations) with data and step size from the oracle alone:
+    b = A x_true + 1% noise (FP64 projection, rounded to FP32) and eta = 1/L of the
+    oracle's power iteration."""
+    if not _C4:
+        wl = synth.workloads()["c4_256x8"]
+        g = wl.geom
+        xt = f32(synth.phantom_batch(wl))
+        clean = np.stack([oracle.project(g, 1, xt[i]) for i in range(g.batch)])
+        w = np.random.default_rng(4).standard_normal(clean.shape)
+        b = f32(clean + 0.01 * np.abs(clean).max() * w)
+        eta = [1.0 / oracle.power_iter(g, 2, 200, 1e-10)[0]]
+        _C4.update(wl=wl, g=g, xt=xt, b=b, eta=eta)
+    return _C4["wl"], _C4["g"], _C4["xt"], _C4["b"], _C4["eta"]
+
+
+def _gpu_unrolled(plan, wl, stages, eta, seq, b, xt, x0, lam0, inst):
+    """Loss 1/2 sum_{i in inst} ||x_T[i] - x_true[i]||^2 and its gradients w.r.t.
+    x0 (all instances) and lambda through torch.autograd."""
     import torch
     from paper_2203_07308_gb300.autograd import unrolled_pnp
-    wl = synth.workloads()["c4_256x8"]
-    g = wl.geom
+    X0 = dev(x0).requires_grad_(True)
+    lam = torch.tensor(lam0, dtype=torch.float64, requires_grad=True)
+    xT = unrolled_pnp(plan, stages, eta, seq, dev(b), X0, lam, alpha=wl.alpha, tv_iters=wl.tv_iters)
+    sel = list(inst)
+    loss = 0.5 * ((xT[sel] - dev(xt)[sel]) ** 2).sum()
+    loss.backward()
+    return float(loss), host(X0.grad), float(lam.grad)
+
+
+def test_differentiable_workload_full_size():
+    """8 x 256x256, 360 views x 512 bins, 10 unrolled 2x-sketched iterations, loss on
+    instances 0 and 5: the gradient w.r.t. x0 of both and w.r.t. lambda (the sum of
+    their two contributions) against the oracle's reverse mode; the other six
+    instances run alongside and get a zero gradient."""
+    wl, g, xt, b, eta = _c4_problem()
     plan = pnp.Plan(g)
-    xt = f32(synth.phantom_batch(wl))
-    rng = np.random.default_rng(4)
-    d_xt = dev(xt)
-    d_b = torch.empty(g.batch, g.n_views, g.n_det, device="cuda")
-    plan.project(1, d_xt, d_b)
-    d_b += 0.01 * float(d_b.abs().max()) * dev(rng.standard_normal((g.batch, g.n_views, g.n_det)))
-    b = host(d_b)
-    eta = [1.0 / plan.power_iter(2, 60, 1e-7)[0]]
     stages = wl.stages
     seq = synth.schedule_sequence(stages, 3)
-    X0 = torch.zeros(g.batch, g.n, g.n, device="cuda", requires_grad=True)
-    lam = torch.tensor(wl.tv_lambda, dtype=torch.float64, requires_grad=True)
-    xT = unrolled_pnp(plan, stages, eta, seq, d_b, X0, lam, alpha=wl.alpha, tv_iters=wl.tv_iters)
-    (0.5 * ((xT - d_xt) ** 2).sum()).backward()
-    gx = host(X0.grad)
+    x0 = np.zeros((g.batch, g.n, g.n))
+    _, gx, gl = _gpu_unrolled(plan, wl, stages, eta, seq, b, xt, x0, wl.tv_lambda, (0, 5))
+    ref_gl = 0.0
+    errs = {}
     for i in (0, 5):
-        _, rgx, _ = _oracle_unrolled(g, stages, eta, seq, b[i], np.zeros((g.n, g.n)), xt[i], wl.tv_lambda,
-                                     wl.alpha, wl.tv_iters)
-        assert rel(gx[i], rgx) < TOL_VJP_FULL, rel(gx[i], rgx)
-    assert np.isfinite(float(lam.grad))
+        _, rgx, rgl = _oracle_unrolled(g, stages, eta, seq, b[i], x0[i], xt[i], wl.tv_lambda, wl.alpha,
+                                       wl.tv_iters)
+        errs[i] = rel(gx[i], rgx)
+        ref_gl += rgl
+    print("full-size unroll: relative error of dJ/dx0 per instance", errs, "dJ/dlambda", gl, ref_gl)
+    for i, e in errs.items():
+        assert e < TOL_VJP_FULL, (i, e)
+    assert abs(gl - ref_gl) < TOL_VJP_FULL * abs(ref_gl), (gl, ref_gl)
+    others = [i for i in range(g.batch) if i not in (0, 5)]
+    assert not gx[others].any()
+
+
+def test_differentiable_workload_full_size_finite_differences():
+    """Central differences (h = 1e-3) of the GPU forward map at full size, against
+    the autograd gradients: along a direction that mixes the gradient with a random
+    unit vector (so the derivative is far above the FP32 noise of the loss, yet the
+    check is not along the gradient alone), and along lambda."""
+    import torch
+    from paper_2203_07308_gb300.autograd import unrolled_pnp
+    wl, g, xt, b, eta = _c4_problem()
+    plan = pnp.Plan(g)
+    stages = wl.stages
+    seq = synth.schedule_sequence(stages, 3)
+    x0 = f32(np.random.default_rng(8).random((g.batch, g.n, g.n)) * 0.1)
+    inst = (0, 5)
+    _, gx, gl = _gpu_unrolled(plan, wl, stages, eta, seq, b, xt, x0, wl.tv_lambda, inst)
+
+    def F(x0v, lv):
+        with torch.no_grad():
+            xx = unrolled_pnp(plan, stages, eta, seq, dev(b), dev(x0v), torch.tensor(lv, dtype=torch.float64),
+                              alpha=wl.alpha, tv_iters=wl.tv_iters)
+            d_ = xx[list(inst)].double() - dev(xt)[list(inst)].double()
+            return float(0.5 * (d_ ** 2).sum())
+    u = np.random.default_rng(9).standard_normal(x0.shape)
+    d = gx / np.linalg.norm(gx) + u / np.linalg.norm(u)
+    d /= np.linalg.norm(d)
+    h = 1e-3
+    fdx = (F(x0 + h * d, wl.tv_lambda) - F(x0 - h * d, wl.tv_lambda)) / (2 * h)
+    fdl = (F(x0, wl.tv_lambda + h) - F(x0, wl.tv_lambda - h)) / (2 * h)
+    print("full-size finite differences: x0", fdx, np.vdot(gx, d), "lambda", fdl, gl)
+    assert abs(fdx - np.vdot(gx, d)) < 2e-2 * abs(fdx)
+    assert abs(fdl - gl) < 2e-2 * abs(fdl)
+
+
+def test_differentiable_error_growth_with_unrolled_iterations():
+    """The reverse-mode error of the full-size unroll against the oracle for T = 5,
+    10 and 20 unrolled iterations (instance 0): each of the T forward and T reverse
+    gradient evaluations carries at most the single-gradient bound, so the error
+    stays below 2 T x 1e-5 and grows at most linearly in T."""
+    wl, g, xt, b, eta = _c4_problem()
+    plan = pnp.Plan(g)
+    x0 = np.zeros((g.batch, g.n, g.n))
+    errs = {}
+    for T in (5, 10, 20):
+        stages = [synth.Stage(2, T, 1)]
+        seq = synth.schedule_sequence(stages, 3)
+        _, gx, gl = _gpu_unrolled(plan, wl, stages, eta, seq, b, xt, x0, wl.tv_lambda, (0,))
+        _, rgx, rgl = _oracle_unrolled(g, stages, eta, seq, b[0], x0[0], xt[0], wl.tv_lambda, wl.alpha,
+                                       wl.tv_iters)
+        errs[T] = (rel(gx[0], rgx), abs(gl - rgl) / abs(rgl))
+    print("reverse-mode relative error by unrolled iterations (x0, lambda):", errs)
+    for T, (ex, el) in errs.items():
+        assert ex < 2 * T * 1e-5 and el < 2 * T * 1e-5, (T, ex, el)
 
 
 @pytest.mark.parametrize("s,P,p", [(1, 1, 0), (2, 3, 1)])
