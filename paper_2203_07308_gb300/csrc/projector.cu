@@ -104,32 +104,33 @@ __device__ __forceinline__ float pooled(const float* __restrict__ fine, int n, i
 
 struct PrepTable {
     PrepArgs c[kMaxClasses];
-    long begin[kMaxClasses + 1];   // cumulative cell counts (batch * qw * qw)
+    long ibegin[kMaxClasses + 1];  // cumulative image counts
     int count;
 };
 
+// grid.x covers the cells of one image (32-bit indices), grid.y the images of
+// all classes (strided when there are more than gridDim.y).
 __global__ void k_prep_quad(const PrepTable t)
 {
     pdl_begin();
-    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= t.begin[t.count]) return;
-    int c = 0;
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    for (long item = blockIdx.y; item < t.ibegin[t.count]; item += gridDim.y) {
+        int c = 0;
 #pragma unroll
-    for (int k = 1; k < kMaxClasses; ++k)
-        if (k < t.count && idx >= t.begin[k]) c = k;
-    const PrepArgs& a = t.c[c];
-    const long local = idx - t.begin[c];
-    const int qw = a.qw;
-    const long cells = (long)qw * qw;
-    const int inst = (int)(local / cells);
-    const int rem = (int)(local - (long)inst * cells);
-    const int qy = rem / qw, qx = rem - qy * qw;
-    const int n = a.n, s = a.s, ns = n / s;
-    const float* f = a.fine + (long)inst * n * n;
-    const int ix0 = qx - kPad, iy0 = qy - kPad;
-    const float pa = pooled(f, n, s, ns, ix0, iy0), pb = pooled(f, n, s, ns, ix0 + 1, iy0);
-    const float pc = pooled(f, n, s, ns, ix0, iy0 + 1), pd = pooled(f, n, s, ns, ix0 + 1, iy0 + 1);
-    a.quad[local] = make_quad(pa, pb, pc, pd);
+        for (int k = 1; k < kMaxClasses; ++k)
+            if (k < t.count && item >= t.ibegin[k]) c = k;
+        const PrepArgs& a = t.c[c];
+        const int qw = a.qw;
+        if (cell >= qw * qw) continue;
+        const long inst = item - t.ibegin[c];
+        const int qy = cell / qw, qx = cell - qy * qw;
+        const int n = a.n, s = a.s, ns = n / s;
+        const float* f = a.fine + inst * n * n;
+        const int ix0 = qx - kPad, iy0 = qy - kPad;
+        const float pa = pooled(f, n, s, ns, ix0, iy0), pb = pooled(f, n, s, ns, ix0 + 1, iy0);
+        const float pc = pooled(f, n, s, ns, ix0, iy0 + 1), pd = pooled(f, n, s, ns, ix0 + 1, iy0 + 1);
+        a.quad[inst * qw * qw + cell] = make_quad(pa, pb, pc, pd);
+    }
 }
 
 // ------------------------------------------------------------------ forward A_s
@@ -887,12 +888,15 @@ cudaError_t launch_prep_multi(const PrepArgs* items, int count, cudaStream_t st)
     if (count < 1 || count > kMaxClasses) return cudaErrorInvalidValue;
     PrepTable t{};
     t.count = count;
-    t.begin[0] = 0;
+    t.ibegin[0] = 0;
+    long cells = 0;
     for (int c = 0; c < count; ++c) {
         t.c[c] = items[c];
-        t.begin[c + 1] = t.begin[c] + (long)items[c].batch * items[c].qw * items[c].qw;
+        t.ibegin[c + 1] = t.ibegin[c] + items[c].batch;
+        cells = max(cells, (long)items[c].qw * items[c].qw);
     }
-    const cudaError_t e = launch_pdl(k_prep_quad, dim3(div_up(t.begin[count], 256)), dim3(256), 0, st, t);
+    const dim3 grd(div_up(cells, 256), (unsigned)min(t.ibegin[count], 65535L));
+    const cudaError_t e = launch_pdl(k_prep_quad, grd, dim3(256), 0, st, t);
     if (e != cudaSuccess) return e;
     return counted();
 }

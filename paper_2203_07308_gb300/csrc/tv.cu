@@ -507,8 +507,12 @@ struct StripTvArgs {
     float mom[kStripK];
 };
 
+// Packed pairs (column 2l in .x, 2l+1 in .y): FP32x2 instructions, each lane
+// rounded as the scalar operation would be (a - b as an exact -1 * b + a).
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+
 template <bool LAST, int W>
-__global__ void __launch_bounds__(32 * W) k_tv_strip(const StripTvArgs t)
+__global__ void __launch_bounds__(32 * W, W == 8 ? 2 : 1) k_tv_strip(const StripTvArgs t)
 {
     pdl_begin();
     constexpr int R = kStripR;
@@ -534,106 +538,86 @@ __global__ void __launch_bounds__(32 * W) k_tv_strip(const StripTvArgs t)
     float2* dn = up + W * 32;                                // [W][32]      x_tmp of each warp's first row
     const bool ina = ja >= 0 && ja < n, inb = jb >= 0 && jb < n;
     // the dual step's differences vanish outside rows / columns [0, n-2]
-    const float mca = (ja >= 0 && ja < n - 1) ? 1.0f : 0.0f;
-    const float mcb = (jb >= 0 && jb < n - 1) ? 1.0f : 0.0f;
+    const float2 mcol = make_float2((ja >= 0 && ja < n - 1) ? 1.0f : 0.0f, (jb >= 0 && jb < n - 1) ? 1.0f : 0.0f);
     float mrow[R];
-    float r1a[R], r2a[R], p1a[R], p2a[R], r1b[R], r2b[R], p1b[R], p2b[R];
+    float2 r1[R], r2[R], p1[R], p2[R];
 #pragma unroll
     for (int m = 0; m < R; ++m) {
         const int i = rb + m;
         mrow[m] = (i >= 0 && i < n - 1) ? 1.0f : 0.0f;
         const bool ri = i >= 0 && i < n;
         const long g = img + (long)i * n;
-        float za = 0.0f, zb = 0.0f;
-        r1a[m] = r2a[m] = p1a[m] = p2a[m] = r1b[m] = r2b[m] = p1b[m] = p2b[m] = 0.0f;
+        float2 z = make_float2(0.0f, 0.0f);
+        r1[m] = r2[m] = p1[m] = p2[m] = z;
         if (ri && ina) {
-            za = __ldg(a.z + g + ja);
+            z.x = __ldg(a.z + g + ja);
             if (!t.first) {
-                r1a[m] = __ldg(a.sin + g + ja);
-                r2a[m] = __ldg(a.sin + a.plane + g + ja);
-                p1a[m] = __ldg(a.sin + 2 * a.plane + g + ja);
-                p2a[m] = __ldg(a.sin + 3 * a.plane + g + ja);
+                r1[m].x = __ldg(a.sin + g + ja);
+                r2[m].x = __ldg(a.sin + a.plane + g + ja);
+                p1[m].x = __ldg(a.sin + 2 * a.plane + g + ja);
+                p2[m].x = __ldg(a.sin + 3 * a.plane + g + ja);
             }
         }
         if (ri && inb) {
-            zb = __ldg(a.z + g + jb);
+            z.y = __ldg(a.z + g + jb);
             if (!t.first) {
-                r1b[m] = __ldg(a.sin + g + jb);
-                r2b[m] = __ldg(a.sin + a.plane + g + jb);
-                p1b[m] = __ldg(a.sin + 2 * a.plane + g + jb);
-                p2b[m] = __ldg(a.sin + 3 * a.plane + g + jb);
+                r1[m].y = __ldg(a.sin + g + jb);
+                r2[m].y = __ldg(a.sin + a.plane + g + jb);
+                p1[m].y = __ldg(a.sin + 2 * a.plane + g + jb);
+                p2[m].y = __ldg(a.sin + 3 * a.plane + g + jb);
             }
         }
-        zs[(w * R + m) * 32 + lane] = make_float2(za, zb);
+        zs[(w * R + m) * 32 + lane] = z;
     }
-    up[w * 32 + lane] = make_float2(r1a[R - 1], r1b[R - 1]);
+    up[w * 32 + lane] = r1[R - 1];
     __syncthreads();
     const float lam = t.lambda, inv8l = 1.0f / (8.0f * t.lambda);
+    const float2 nlam2 = make_float2(-lam, -lam), inv8l2 = make_float2(inv8l, inv8l);
     const int wup = w > 0 ? w - 1 : 0, wdn = w + 1 < W ? w + 1 : w;
+#pragma unroll 2
     for (int k = 0; k < t.K; ++k) {
-        // x_tmp = z - lambda L(r)
-        float xa[R], xb[R];
+        // x_tmp = z - lambda L(r):  L = ((r1 + r2) - r1_up) - r2_left
+        float2 x[R];
         {
-            const float2 u = up[wup * 32 + lane];
-            float ua = u.x, ub = u.y;
+            float2 u = up[wup * 32 + lane];
 #pragma unroll
             for (int m = 0; m < R; ++m) {
-                const float left = __shfl_up_sync(kAll, r2b[m], 1);
-                const float2 z2 = zs[(w * R + m) * 32 + lane];
-                float la = r1a[m] + r2a[m];
-                la -= ua;
-                la -= left;
-                float lb = r1b[m] + r2b[m];
-                lb -= ub;
-                lb -= r2a[m];
-                xa[m] = z2.x - lam * la;
-                xb[m] = z2.y - lam * lb;
-                ua = r1a[m];
-                ub = r1b[m];
+                const float2 left = make_float2(__shfl_up_sync(kAll, r2[m].y, 1), r2[m].x);
+                float2 l = __fadd2_rn(r1[m], r2[m]);
+                l = sub2(l, u);
+                l = sub2(l, left);
+                x[m] = __ffma2_rn(nlam2, l, zs[(w * R + m) * 32 + lane]);
+                u = r1[m];
             }
         }
-        dn[w * 32 + lane] = make_float2(xa[0], xb[0]);
+        dn[w * 32 + lane] = x[0];
         __syncthreads();
         // dual step, isotropic projection, momentum
-        const float mo = t.mom[k];
+        const float2 mo = make_float2(t.mom[k], t.mom[k]);
         {
             const float2 d = dn[wdn * 32 + lane];
 #pragma unroll
             for (int m = 0; m < R; ++m) {
-                const float da = m + 1 < R ? xa[m + 1 < R ? m + 1 : m] : d.x;
-                const float db = m + 1 < R ? xb[m + 1 < R ? m + 1 : m] : d.y;
-                const float right = __shfl_down_sync(kAll, xa[m], 1);
-                const float g1a = (xa[m] - da) * mrow[m];
-                const float g1b = (xb[m] - db) * mrow[m];
-                const float g2a = (xa[m] - xb[m]) * mca;
-                const float g2b = (xb[m] - right) * mcb;
-                float pa = fmaf(g1a, inv8l, r1a[m]);
-                float pc = fmaf(g2a, inv8l, r2a[m]);
-                float nrm2 = fmaf(pa, pa, pc * pc);
-                if (nrm2 > 1.0f) {
-                    const float sc = rsqrtf(nrm2);
-                    pa *= sc;
-                    pc *= sc;
-                }
-                r1a[m] = fmaf(mo, pa - p1a[m], pa);
-                r2a[m] = fmaf(mo, pc - p2a[m], pc);
-                p1a[m] = pa;
-                p2a[m] = pc;
-                pa = fmaf(g1b, inv8l, r1b[m]);
-                pc = fmaf(g2b, inv8l, r2b[m]);
-                nrm2 = fmaf(pa, pa, pc * pc);
-                if (nrm2 > 1.0f) {
-                    const float sc = rsqrtf(nrm2);
-                    pa *= sc;
-                    pc *= sc;
-                }
-                r1b[m] = fmaf(mo, pa - p1b[m], pa);
-                r2b[m] = fmaf(mo, pc - p2b[m], pc);
-                p1b[m] = pa;
-                p2b[m] = pc;
+                const float2 down = m + 1 < R ? x[m + 1 < R ? m + 1 : m] : d;
+                const float2 right = make_float2(x[m].y, __shfl_down_sync(kAll, x[m].x, 1));
+                const float2 g1 = __fmul2_rn(sub2(x[m], down), make_float2(mrow[m], mrow[m]));
+                const float2 g2 = __fmul2_rn(sub2(x[m], right), mcol);
+                float2 pa = __ffma2_rn(g1, inv8l2, r1[m]);
+                float2 pc = __ffma2_rn(g2, inv8l2, r2[m]);
+                const float2 nrm2 = __ffma2_rn(pa, pa, __fmul2_rn(pc, pc));
+                // projection onto the unit disc without a branch: the scale is 1 (exact)
+                // unless |p| > 1
+                const float2 sc = make_float2(nrm2.x > 1.0f ? rsqrtf(nrm2.x) : 1.0f,
+                                              nrm2.y > 1.0f ? rsqrtf(nrm2.y) : 1.0f);
+                pa = __fmul2_rn(pa, sc);
+                pc = __fmul2_rn(pc, sc);
+                r1[m] = __ffma2_rn(mo, sub2(pa, p1[m]), pa);
+                r2[m] = __ffma2_rn(mo, sub2(pc, p2[m]), pc);
+                p1[m] = pa;
+                p2[m] = pc;
             }
         }
-        up[w * 32 + lane] = make_float2(r1a[R - 1], r1b[R - 1]);
+        up[w * 32 + lane] = r1[R - 1];
         __syncthreads();
     }
     // output pixels of this thread: rows [r0, r0 + HO), columns [c0, c0 + WO), inside the image
@@ -645,41 +629,37 @@ __global__ void __launch_bounds__(32 * W) k_tv_strip(const StripTvArgs t)
             if (i < r0 || i >= r0 + HO || i >= n) continue;
             const long g = img + (long)i * n;
             if (oa) {
-                a.sout[g + ja] = r1a[m];
-                a.sout[a.plane + g + ja] = r2a[m];
-                a.sout[2 * a.plane + g + ja] = p1a[m];
-                a.sout[3 * a.plane + g + ja] = p2a[m];
+                a.sout[g + ja] = r1[m].x;
+                a.sout[a.plane + g + ja] = r2[m].x;
+                a.sout[2 * a.plane + g + ja] = p1[m].x;
+                a.sout[3 * a.plane + g + ja] = p2[m].x;
             }
             if (ob) {
-                a.sout[g + jb] = r1b[m];
-                a.sout[a.plane + g + jb] = r2b[m];
-                a.sout[2 * a.plane + g + jb] = p1b[m];
-                a.sout[3 * a.plane + g + jb] = p2b[m];
+                a.sout[g + jb] = r1[m].y;
+                a.sout[a.plane + g + jb] = r2[m].y;
+                a.sout[2 * a.plane + g + jb] = p1[m].y;
+                a.sout[3 * a.plane + g + jb] = p2[m].y;
             }
         }
     } else {
         // x = z - lambda L(p), relaxation, momentum, squared error
-        up[w * 32 + lane] = make_float2(p1a[R - 1], p1b[R - 1]);
+        up[w * 32 + lane] = p1[R - 1];
         __syncthreads();
-        const float2 u = up[wup * 32 + lane];
-        float ua = u.x, ub = u.y;
+        float2 u = up[wup * 32 + lane];
         double e2 = 0.0;
 #pragma unroll
         for (int m = 0; m < R; ++m) {
-            const float left = __shfl_up_sync(kAll, p2b[m], 1);
+            const float2 left = make_float2(__shfl_up_sync(kAll, p2[m].y, 1), p2[m].x);
             const float2 z2 = zs[(w * R + m) * 32 + lane];
-            float la = p1a[m] + p2a[m];
-            la -= ua;
-            la -= left;
-            float lb = p1b[m] + p2b[m];
-            lb -= ub;
-            lb -= p2a[m];
-            ua = p1a[m];
-            ub = p1b[m];
+            float2 l = __fadd2_rn(p1[m], p2[m]);
+            l = sub2(l, u);
+            l = sub2(l, left);
+            const float2 xv = __ffma2_rn(nlam2, l, z2);
+            u = p1[m];
             const int i = rb + m;
             if (i < r0 || i >= r0 + HO || i >= n) continue;
             const long g = img + (long)i * n;
-            const float xva[2] = {z2.x - lam * la, z2.y - lam * lb};
+            const float xva[2] = {xv.x, xv.y};
             const float zv[2] = {z2.x, z2.y};
             const bool ov[2] = {oa, ob};
             const int jv[2] = {ja, jb};

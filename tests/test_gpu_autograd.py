@@ -17,12 +17,14 @@ from paper_2203_07308_gb300 import _native, build, synth
 pytestmark = pytest.mark.gpu
 
 TOL_VJP = 1e-4
-# Full-size unroll of N = 10 iterations: each of the N forward and N reverse
-# gradient evaluations carries up to the single-gradient parity bound (1e-5
-# relative, FP32 sums over ~10^2 samples per pixel and ~10^3 per ray); the step
-# I - eta A^T A with eta = 1/L is non-expansive, so these add rather than
-# multiply: 2 N x 1e-5.
-TOL_VJP_FULL = 2 * 10 * 1e-5
+# Full-size unroll (10 iterations): the reconstruction bound 1e-4.  Measured on
+# GB300: 1.5e-6 and 1.3e-5 for dJ/dx0 of the two checked instances, 1.4e-7 for
+# dJ/dlambda; 1.0e-6, 1.5e-6 and 1.8e-5 at 5, 10 and 20 unrolled iterations
+# (test_differentiable_error_growth_with_unrolled_iterations bounds the growth
+# by 2 T x 1e-5: each of the T forward and T reverse gradient evaluations
+# carries at most the single-gradient bound, and I - eta A^T A is
+# non-expansive, so the errors add).
+TOL_VJP_FULL = 1e-4
 
 
 @pytest.fixture(scope="module", autouse=True)
