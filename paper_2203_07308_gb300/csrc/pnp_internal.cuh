@@ -138,6 +138,14 @@ cudaError_t launch_setup_rays(const pnp_geom& g, const LevelLayout& L, char* ws,
 // one-entry case.  Autotuned launch shapes (0 = heuristic) ride along.
 constexpr int kMaxClasses = 4;
 
+// Coefficient images of a batch of at least kQuadIlMin images are stored
+// image-interleaved, quad[(qy * qw + qx) * batch + image], so that one 128-byte
+// line holds a cell of 8 images and the forward projector reads a sample of 8
+// images with one line; smaller batches are stored image-major,
+// quad[image][qy][qx].  Every writer and reader takes the layout from the batch.
+constexpr int kQuadIlMin = 8;
+__host__ __device__ inline bool quad_interleaved(int batch) { return batch >= kQuadIlMin; }
+
 struct PrepArgs { const float* fine; int n, s, batch; float4* quad; int qw; };
 cudaError_t launch_prep_quad(const float* fine, int n, int s, int batch, float4* quad, int qw,
                              cudaStream_t st);

@@ -133,6 +133,53 @@ __global__ void k_prep_quad(const PrepTable t)
     }
 }
 
+// Image-interleaved coefficient image, quad[(qy * qw + qx) * B + b].  A CTA
+// builds kIlCells consecutive cells of one row for all B images of its class:
+// it stages the two level-image rows those cells read (pooled for s > 1) in
+// shared memory image by image, then writes the cells with the image index
+// fastest, so that both the image reads and the cell writes are contiguous.
+constexpr int kIlCells = 32;
+constexpr int kIlImages = 64;    // images staged at a time (shared memory 64 x 2 x 33 floats)
+
+struct PrepIlTable {
+    PrepArgs c[kMaxClasses];
+    long begin[kMaxClasses + 1];   // cumulative CTA counts (qw rows x segments)
+    int count;
+};
+
+__global__ void __launch_bounds__(256) k_prep_quad_il(const PrepIlTable t)
+{
+    pdl_begin();
+    __shared__ float lv[kIlImages * 2 * (kIlCells + 1)];  // [image][2 rows][kIlCells + 1]
+    int c = 0;
+#pragma unroll
+    for (int k = 1; k < kMaxClasses; ++k)
+        if (k < t.count && (long)blockIdx.x >= t.begin[k]) c = k;
+    const PrepArgs& a = t.c[c];
+    const int qw = a.qw, B = a.batch;
+    const int segs = (qw + kIlCells - 1) / kIlCells;
+    const int local = (int)((long)blockIdx.x - t.begin[c]);
+    const int qy = local / segs, qx0 = (local - qy * segs) * kIlCells;
+    const int n = a.n, s = a.s, ns = n / s;
+    constexpr int C1 = kIlCells + 1;
+    const int cells = min(kIlCells, qw - qx0);
+    float4* row = a.quad + ((long)qy * qw + qx0) * B;
+    for (int b0 = 0; b0 < B; b0 += kIlImages) {          // images in chunks of kIlImages
+        const int nb = min(kIlImages, B - b0);
+        if (b0 > 0) __syncthreads();
+        for (int e = threadIdx.x; e < nb * 2 * C1; e += blockDim.x) {
+            const int b = e / (2 * C1), rem = e - b * 2 * C1, r = rem / C1, cx = rem - r * C1;
+            lv[e] = pooled(a.fine + (long)(b0 + b) * n * n, n, s, ns, qx0 - kPad + cx, qy - kPad + r);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < cells * nb; e += blockDim.x) {
+            const int cx = e / nb, b = e - cx * nb;
+            const float* l0 = lv + b * 2 * C1;
+            row[(long)cx * B + b0 + b] = make_quad(l0[cx], l0[cx + 1], l0[C1 + cx], l0[C1 + cx + 1]);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ forward A_s
 // Warp = R rays x Q phases (R*Q = 32): lane (r, q) sums the samples k = k_lo + q,
 // k_lo + q + Q, ... of ray r into four interleaved partial sums (independent
@@ -225,6 +272,97 @@ __global__ void __launch_bounds__(32 * kFwdWarps, 4) k_forward(const FwdTable t)
         if (a.b) val -= __ldg(a.b + bi);
         if (a.w) val *= __ldg(a.w + bi);
         a.out[out_idx] = val;
+    }
+}
+
+// Forward projector on an image-interleaved coefficient image.  A warp takes one
+// ray for all images of its class: lane (g, i) = (lane / 8, lane % 8) sums the
+// samples k = k_lo + g, k_lo + g + 4, ... of images i, i + 8, ..., i + 8 (IPL - 1),
+// so the position and cell of a sample are computed once for 8 IPL images and
+// each load instruction reads whole 128-byte lines (8 images' cells), 4
+// consecutive samples at a time; the four sample groups are joined in a fixed
+// order.  A CTA (8 warps) takes 8 adjacent bins of one view, CTAs numbered from
+// the detector's centre outwards as in k_forward.
+constexpr int kFwdIlWarps = 8;
+
+template <int IPL>
+__global__ void __launch_bounds__(32 * kFwdIlWarps) k_forward_il(const FwdTable t)
+{
+    pdl_begin();
+    const int lane = threadIdx.x & 31;
+    const int sg = lane >> 3, li = lane & 7;
+    const long cta = blockIdx.x;
+    int c = 0;
+#pragma unroll
+    for (int k = 1; k < kMaxClasses; ++k)
+        if (k < t.count && cta >= t.begin[k]) c = k;
+    const FwdArgs& a = t.c[c];
+    const int nb = (a.n_det + kFwdIlWarps - 1) / kFwdIlWarps;
+    const int per_chunk = a.n_sub * nb;
+    const int local = (int)(cta - t.begin[c]);
+    const int chunk = local / per_chunk;                    // images [8 IPL chunk, 8 IPL (chunk + 1))
+    const int rem = local - chunk * per_chunk;
+    const int rank = rem / a.n_sub, vs = rem - rank * a.n_sub;
+    const int mid = nb >> 1;
+    const int blk = (rank & 1) ? mid - ((rank + 1) >> 1) : mid + (rank >> 1);
+    const int j = blk * kFwdIlWarps + (threadIdx.x >> 5);
+    if (j >= a.n_det) return;                                  // whole warps only
+    const int v = a.first_view + vs * a.view_step;
+    const float4 f = __ldg(a.rayf + (long)v * a.n_det + j);
+    const int2 kr = __ldg(a.rayk + (long)v * a.n_det + j);
+    const int B = a.batch, qw = a.qw;
+    const int i0 = chunk * 8 * IPL + li;                     // this lane's first image
+    const int bias = kMagicBits - (qw - 3) / 2;             // column = round(X') + c0
+    const float step = a.step;
+    bool valid[IPL];
+#pragma unroll
+    for (int q = 0; q < IPL; ++q) valid[q] = i0 + 8 * q < B;
+    float acc[IPL];
+#pragma unroll
+    for (int q = 0; q < IPL; ++q) acc[q] = 0.0f;
+    const float4* __restrict__ img = a.quad + i0;
+    auto smp = [&](int k) {
+        const float tt = ((float)k + 0.5f) * step;
+        const float X = fmaf(tt, f.z, f.x);
+        const float Y = fmaf(tt, f.w, f.y);
+        const float mx = __fadd_rn(X, kMagic);
+        const float my = __fadd_rn(Y, kMagic);
+        const float u = __fsub_rn(X, __fsub_rn(mx, kMagic));
+        const float w = __fsub_rn(Y, __fsub_rn(my, kMagic));
+        const int ix = __float_as_int(mx) - bias;
+        const int iy = __float_as_int(my) - bias;
+        const float4* cell = img + (long)(iy * qw + ix) * B;
+#pragma unroll
+        for (int q = 0; q < IPL; ++q) {
+            if (!valid[q]) continue;
+            const float4 cq = __ldg(cell + 8 * q);
+            acc[q] += fmaf(w, fmaf(u, cq.w, cq.z), fmaf(u, cq.y, cq.x));
+        }
+    };
+    int k = kr.x + sg;
+#pragma unroll 1
+    for (; k + 4 <= kr.y; k += 8) {
+        smp(k);
+        smp(k + 4);
+    }
+    if (k <= kr.y) smp(k);
+#pragma unroll
+    for (int q = 0; q < IPL; ++q) {
+        acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 8);
+        acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 16);
+    }
+    if (sg != 0) return;
+    const long out_row = (long)vs * a.n_det + j;
+    const long b_row = (long)v * a.n_det + j;
+#pragma unroll
+    for (int q = 0; q < IPL; ++q) {
+        if (!valid[q]) continue;
+        const int inst = i0 + 8 * q;
+        const long bi = (long)inst * a.n_views * a.n_det + b_row;
+        float val = a.weight * acc[q];
+        if (a.b) val -= __ldg(a.b + bi);
+        if (a.w) val *= __ldg(a.w + bi);
+        a.out[(long)inst * a.n_sub * a.n_det + out_row] = val;
     }
 }
 
@@ -886,19 +1024,37 @@ cudaError_t launch_setup_rays(const pnp_geom& g, const LevelLayout& L, char* ws,
 cudaError_t launch_prep_multi(const PrepArgs* items, int count, cudaStream_t st)
 {
     if (count < 1 || count > kMaxClasses) return cudaErrorInvalidValue;
+    // image-major classes in one launch, image-interleaved ones in another
     PrepTable t{};
-    t.count = count;
+    PrepIlTable ti{};
     t.ibegin[0] = 0;
+    ti.begin[0] = 0;
     long cells = 0;
     for (int c = 0; c < count; ++c) {
-        t.c[c] = items[c];
-        t.ibegin[c + 1] = t.ibegin[c] + items[c].batch;
-        cells = max(cells, (long)items[c].qw * items[c].qw);
+        const PrepArgs& it = items[c];
+        if (quad_interleaved(it.batch)) {
+            ti.c[ti.count] = it;
+            ti.begin[ti.count + 1] = ti.begin[ti.count] + (long)it.qw * div_up(it.qw, kIlCells);
+            ++ti.count;
+        } else {
+            t.c[t.count] = it;
+            t.ibegin[t.count + 1] = t.ibegin[t.count] + it.batch;
+            ++t.count;
+            cells = max(cells, (long)it.qw * it.qw);
+        }
     }
-    const dim3 grd(div_up(cells, 256), (unsigned)min(t.ibegin[count], 65535L));
-    const cudaError_t e = launch_pdl(k_prep_quad, grd, dim3(256), 0, st, t);
-    if (e != cudaSuccess) return e;
-    return counted();
+    if (t.count > 0) {
+        const dim3 grd(div_up(cells, 256), (unsigned)min(t.ibegin[t.count], 65535L));
+        const cudaError_t e = launch_pdl(k_prep_quad, grd, dim3(256), 0, st, t);
+        if (e != cudaSuccess) return e;
+        counted();
+    }
+    if (ti.count > 0) {
+        const cudaError_t e = launch_pdl(k_prep_quad_il, dim3((unsigned)ti.begin[ti.count]), dim3(256), 0, st, ti);
+        if (e != cudaSuccess) return e;
+        counted();
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_prep_quad(const float* fine, int n, int s, int batch, float4* quad, int qw,
@@ -917,9 +1073,47 @@ cudaError_t forward_q(FwdTable t, cudaStream_t st)
     return launch_pdl(k_forward<Q>, dim3((unsigned)t.begin[t.count]), dim3(32 * kFwdWarps), 0, st, t);
 }
 
+namespace {
+template <int IPL>
+cudaError_t forward_il(const FwdTable& t, cudaStream_t st)
+{
+    return launch_pdl(k_forward_il<IPL>, dim3((unsigned)t.begin[t.count]), dim3(32 * kFwdIlWarps), 0, st, t);
+}
+}  // namespace
+
+// Classes with image-interleaved coefficient images (batch >= kQuadIlMin, at
+// most 32 images) take k_forward_il, the others k_forward; one launch each.
 cudaError_t launch_forward_multi(const FwdArgs* items, int count, cudaStream_t st, int lanes)
 {
     if (count < 1 || count > kMaxClasses) return cudaErrorInvalidValue;
+    FwdTable ti{};
+    ti.begin[0] = 0;
+    int maxb = 0;
+    FwdArgs rest[kMaxClasses];
+    int nrest = 0;
+    for (int c = 0; c < count; ++c) {
+        if (quad_interleaved(items[c].batch)) {
+            ti.c[ti.count] = items[c];
+            maxb = max(maxb, items[c].batch);
+            ++ti.count;
+        } else {
+            rest[nrest++] = items[c];
+        }
+    }
+    if (ti.count > 0) {
+        // images per lane: 1, 2 or 4 (chunks of 8, 16 or 32 images per warp)
+        const int ipl = maxb <= 8 ? 1 : maxb <= 16 ? 2 : 4;
+        for (int c = 0; c < ti.count; ++c)
+            ti.begin[c + 1] = ti.begin[c] + (long)ti.c[c].n_sub * div_up(ti.c[c].n_det, kFwdIlWarps) *
+                                                div_up(ti.c[c].batch, 8 * ipl);
+        const cudaError_t e = ipl == 1 ? forward_il<1>(ti, st) : ipl == 2 ? forward_il<2>(ti, st)
+                                                                          : forward_il<4>(ti, st);
+        if (e != cudaSuccess) return e;
+        counted();
+    }
+    if (nrest == 0) return cudaSuccess;
+    items = rest;
+    count = nrest;
     FwdTable t{};
     t.count = count;
     t.begin[0] = 0;

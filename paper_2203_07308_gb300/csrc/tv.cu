@@ -96,6 +96,7 @@ struct TileTvClass {
     const float* xin;                                 // x_{i-1} (nullptr: xprev)
     float4* quad;                                     // last launch: coefficient image of S_qs y
     int qw, qs, ring;                                 // qs = 1 or 2; ring = qs when quad is written
+    int qbatch;                                       // batch of the class (sets the image layout)
     int n, T, tiles_x, tiles;
     long plane;
     float amom;
@@ -283,13 +284,17 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
             const int r_lo = i0 == 0 ? -kPad : i0 / qs, r_hi = i0 + T >= n ? ns + 1 : (i0 + T) / qs;
             const int c_lo = j0 == 0 ? -kPad : j0 / qs, c_hi = j0 + T >= n ? ns + 1 : (j0 + T) / qs;
             const int cw = c_hi - c_lo, cells = (r_hi - r_lo) * cw;
-            float4* qimg = a.quad + (long)inst * a.qw * a.qw;
+            // image-major, or image-interleaved for large batches (quad_interleaved)
+            const int qB = a.qbatch;
+            const bool qil = quad_interleaved(qB);
+            float4* qimg = qil ? a.quad + inst : a.quad + (long)inst * a.qw * a.qw;
+            const long qstride = qil ? qB : 1;
             auto inside = [&](int r, int c) { return r >= 0 && c >= 0 && r < ns && c < ns; };
             if (qs == 1) {
                 auto Y = [&](int r, int c) -> float { return inside(r, c) ? ys[(r - oi) * P + (c - oj)] : 0.0f; };
                 for (int k = threadIdx.x; k < cells; k += blockDim.x) {
                     const int r = r_lo + k / cw, c = c_lo + k % cw;
-                    qimg[(long)(r + kPad) * a.qw + (c + kPad)] =
+                    qimg[((long)(r + kPad) * a.qw + (c + kPad)) * qstride] =
                         make_quad(Y(r, c), Y(r, c + 1), Y(r + 1, c), Y(r + 1, c + 1));
                 }
             } else {
@@ -305,7 +310,7 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
                 };
                 for (int k = threadIdx.x; k < cells; k += blockDim.x) {
                     const int r = r_lo + k / cw, c = c_lo + k % cw;
-                    qimg[(long)(r + kPad) * a.qw + (c + kPad)] =
+                    qimg[((long)(r + kPad) * a.qw + (c + kPad)) * qstride] =
                         make_quad(Y(r, c), Y(r, c + 1), Y(r + 1, c), Y(r + 1, c + 1));
                 }
             }
@@ -925,7 +930,7 @@ cudaError_t launch_tv_tiled_multi(const TvItem* items, int count, float lambda, 
         if (iters > kTileKMax && (!it.state_a || !it.state_b)) return cudaErrorInvalidValue;   // chaining needs state
         TileTvClass& tc = a.c[c];
         tc.z = it.z; tc.xprev = it.xprev; tc.y = it.y; tc.xtrue = it.xtrue; tc.mse_part = it.mse_part;
-        tc.xin = it.xin; tc.quad = it.quad; tc.qw = it.qw; tc.qs = it.qs;
+        tc.xin = it.xin; tc.quad = it.quad; tc.qw = it.qw; tc.qs = it.qs; tc.qbatch = it.batch;
         tc.n = it.n; tc.T = T; tc.tiles_x = (it.n + T - 1) / T; tc.tiles = tc.tiles_x * tc.tiles_x;
         tc.plane = (long)it.batch * it.n * it.n;
         tc.amom = it.amom;

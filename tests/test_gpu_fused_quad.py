@@ -6,7 +6,8 @@ PNP_FUSE_QUAD=0 (coefficient-image kernel in every iteration) must give the same
 bits in x and y, and the PSNR log up to FP64 summation order, over schedules
 that enter, leave and skip the fused path (sketched -> full grid, mini-batch ->
 SVRG, empty stages, resumed runs), ragged and exact tilings, chained denoiser
-launches and two classes in one call.
+launches, two classes in one call and a nine-image class (image-interleaved
+coefficient images).
 Parity with the oracle is checked by the run suites, which use the fused path."""
 import os
 import subprocess
@@ -64,6 +65,15 @@ logs = pnp.run_many([dict(plan=pa, stages=sa, eta=[1e-4] * 3, seq=synth.schedule
                      dict(plan=pb_, stages=sb, eta=[2e-4, 1e-4], seq=synth.schedule_sequence(sb, 12), b=bb,
                           x=xb_, xtrue=xb)], lam=0.02, tv_iters=12, momentum=False)
 out["xa"], out["xb"], out["pa"], out["pb"] = xa_.cpu().numpy(), xb_.cpu().numpy(), logs[0], logs[1]
+# nine images: image-interleaved coefficient images, written by the denoiser for the 2x and full levels
+gc, xc, bc = problem(48, 24, 64, 9, 13)
+pc = pnp.Plan(gc)
+pc.set_launch_shapes(tile=16)
+sc = [synth.Stage(2, 3, 3), synth.Stage(1, 3, 2)]
+xc_ = torch.zeros(9, 48, 48, device="cuda")
+logs = pnp.run_many([dict(plan=pc, stages=sc, eta=[2e-4, 1e-4], seq=synth.schedule_sequence(sc, 14), b=bc,
+                          x=xc_, xtrue=xc)], lam=0.02, tv_iters=12)
+out["xc"], out["pc"] = xc_.cpu().numpy(), logs[0]
 np.savez(sys.argv[1], **out)
 """
 
