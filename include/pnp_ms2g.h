@@ -299,13 +299,14 @@ int pnp_run(const pnp_geom* g, const pnp_stage* stages, int n_stages, const doub
             const int32_t* h_subset_seq, const pnp_run_params* params, const float* d_b,
             float* d_x, const float* d_xtrue, double* h_psnr_log, void* d_ws, void* stream);
 
-/* Algorithm 1 on up to 4 geometry classes at once (images of uneven size,
+/* Algorithm 1 on several geometry classes at once (images of uneven size,
  * views and bins): every iteration runs each projector and denoiser phase as
- * ONE launch covering all classes that are still iterating (classes may have
+ * ONE launch covering up to 4 classes that are still iterating (more classes:
+ * one launch per phase for each group of 4, in class order); classes may have
  * schedules of different lengths; iteration i of every class uses the same
- * momentum a_i and params).  Workspaces and outputs must be distinct per
+ * momentum a_i and params.  Workspaces and outputs must be distinct per
  * class.  Synchronous only when some class logs PSNR.  PNP_EUNSUPPORTED for
- * more than 4 classes.
+ * more than 1024 classes.
  * Checkpoint/resume: a class with start_iter = k continues Algorithm 1 from
  * iteration k + 1 with d_x = x_k and d_y = y_k (both returned by an earlier run
  * that stopped after k iterations, e.g. a schedule cut at k); the result is

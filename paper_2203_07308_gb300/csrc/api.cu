@@ -1062,7 +1062,7 @@ int validate_problem(const pnp_problem& q, const pnp_run_params& pr, int idx, Pr
 int run_many_impl(const pnp_problem* pb_in, int np, const pnp_run_params* params, void* stream)
 {
     if (!pb_in || np < 1) return fail(PNP_EINVAL, "no problems");
-    if (np > kMaxClasses) return fail(PNP_EUNSUPPORTED, "at most %d geometry classes per call", kMaxClasses);
+    if (np > kMaxRunClasses) return fail(PNP_EUNSUPPORTED, "at most %d geometry classes per call", kMaxRunClasses);
     if (!params) return fail(PNP_EINVAL, "params are required");
     // problems without step sizes get eta_k = 1/L_k from the library (cached per
     // workspace; the first computation of a level's L synchronises the stream)
@@ -1128,6 +1128,12 @@ int run_many_impl(const pnp_problem* pb_in, int np, const pnp_run_params* params
             PNP_CUDA(launch_copy(y0, (float*)(ws + ps[c].L.off_y), (size_t)g.batch * g.n * g.n, st));
         }
         std::vector<int> stage((size_t)np, 0), in_stage((size_t)np, 0);
+        // per-iteration launch items of the active classes
+        std::vector<PrepArgs> v_prep((size_t)np);
+        std::vector<FwdArgs> v_fwd((size_t)np);
+        std::vector<BackArgs> v_back((size_t)np);
+        std::vector<TvItem> v_tv((size_t)np);
+        std::vector<int> v_act((size_t)np), v_bic((size_t)np), v_need((size_t)np), v_lvl((size_t)np);
         // x alternates between d_x (even iteration count) and the workspace copy, so
         // that the denoiser can read x_{i-1} around its tile while writing x_i
         std::vector<long> done((size_t)np, 0);
@@ -1142,14 +1148,14 @@ int run_many_impl(const pnp_problem* pb_in, int np, const pnp_run_params* params
                 }
                 continue;
             }
-            PrepArgs prep[kMaxClasses];
-            FwdArgs fwd[kMaxClasses];
-            BackArgs back[kMaxClasses];
-            TvItem tv[kMaxClasses];
-            int act[kMaxClasses];
-            int bic[kMaxClasses];
-            int need_prep[kMaxClasses];
-            int lvl[kMaxClasses];
+            PrepArgs* prep = v_prep.data();
+            FwdArgs* fwd = v_fwd.data();
+            BackArgs* back = v_back.data();
+            TvItem* tv = v_tv.data();
+            int* act = v_act.data();
+            int* bic = v_bic.data();
+            int* need_prep = v_need.data();
+            int* lvl = v_lvl.data();
             int na = 0;
             const float amom = momentum_coef(i, pr.momentum);
             for (int c = 0; c < np; ++c) {
@@ -1226,29 +1232,33 @@ int run_many_impl(const pnp_problem* pb_in, int np, const pnp_run_params* params
                 (void)li;
             }
             if (na == 0) break;
-            // one launch shape per phase: the tuned one of the class with the most
-            // level pixels in it (the only class when there is one)
-            int lanes_sel = 0, groups_sel = 0;
-            {
-                double wmax = -1.0;
-                for (int a = 0; a < na; ++a) {
-                    if (bic[a]) continue;
-                    const pnp_geom& g = pb[act[a]].geom;
-                    const double ns = (double)g.n / (double)(1 << lvl[a]);
-                    const double work = (double)g.batch * ns * ns;
-                    if (work > wmax) {
-                        wmax = work;
-                        lanes_sel = ps[act[a]].tuned.lanes[lvl[a]];
-                        groups_sel = ps[act[a]].tuned.groups[lvl[a]];
+            // the active classes in groups of at most kMaxClasses: one launch per
+            // phase and group (a single launch per phase for up to kMaxClasses classes)
+            for (int a0 = 0; a0 < na; a0 += kMaxClasses) {
+                const int a1 = std::min(na, a0 + kMaxClasses);
+                // one launch shape per phase: the tuned one of the group's class with the
+                // most level pixels in it (the only class when there is one)
+                int lanes_sel = 0, groups_sel = 0;
+                {
+                    double wmax = -1.0;
+                    for (int a = a0; a < a1; ++a) {
+                        if (bic[a]) continue;
+                        const pnp_geom& g = pb[act[a]].geom;
+                        const double ns = (double)g.n / (double)(1 << lvl[a]);
+                        const double work = (double)g.batch * ns * ns;
+                        if (work > wmax) {
+                            wmax = work;
+                            lanes_sel = ps[act[a]].tuned.lanes[lvl[a]];
+                            groups_sel = ps[act[a]].tuned.groups[lvl[a]];
+                        }
                     }
                 }
-            }
-            {   // pooled-sketch classes share one launch per phase
+                // pooled-sketch classes share one launch per phase
                 PrepArgs pp[kMaxClasses];
                 FwdArgs ff[kMaxClasses];
                 BackArgs bb[kMaxClasses];
                 int m = 0, mp = 0;
-                for (int a = 0; a < na; ++a) {
+                for (int a = a0; a < a1; ++a) {
                     if (bic[a]) continue;
                     if (need_prep[a]) pp[mp++] = prep[a];
                     ff[m] = fwd[a];
@@ -1269,15 +1279,18 @@ int run_many_impl(const pnp_problem* pb_in, int np, const pnp_run_params* params
                     if (timed && (e0 = g_timer.mark(PNP_PHASE_BACKWARD, st, false))) return e0;
                 }
             }
-            if (do_tv) {
-                if (timed && (e0 = g_timer.mark(PNP_PHASE_DENOISE, st, true))) return e0;
-                PNP_CUDA(launch_tv_tiled_multi(tv, na, pr.lambda, pr.tv_iters, pr.alpha, st));
-                if (timed && (e0 = g_timer.mark(PNP_PHASE_DENOISE, st, false))) return e0;
-            } else {
-                for (int a = 0; a < na; ++a) {
-                    const TvItem& t = tv[a];
-                    PNP_CUDA(launch_tv_final(t.z, nullptr, 0, t.n, t.batch, pr.lambda, pr.alpha, t.amom, t.xprev,
-                                             t.y, t.xtrue, t.mse_part, st, t.xin));
+            for (int a0 = 0; a0 < na; a0 += kMaxClasses) {
+                const int cnt = std::min(na - a0, kMaxClasses);
+                if (do_tv) {
+                    if (timed && (e0 = g_timer.mark(PNP_PHASE_DENOISE, st, true))) return e0;
+                    PNP_CUDA(launch_tv_tiled_multi(tv + a0, cnt, pr.lambda, pr.tv_iters, pr.alpha, st));
+                    if (timed && (e0 = g_timer.mark(PNP_PHASE_DENOISE, st, false))) return e0;
+                } else {
+                    for (int a = a0; a < a0 + cnt; ++a) {
+                        const TvItem& t = tv[a];
+                        PNP_CUDA(launch_tv_final(t.z, nullptr, 0, t.n, t.batch, pr.lambda, pr.alpha, t.amom,
+                                                 t.xprev, t.y, t.xtrue, t.mse_part, st, t.xin));
+                    }
                 }
             }
             for (int a = 0; a < na; ++a) {

@@ -137,6 +137,8 @@ cudaError_t launch_setup_rays(const pnp_geom& g, const LevelLayout& L, char* ws,
 // covers all of them in one launch; the single-class launchers below are the
 // one-entry case.  Autotuned launch shapes (0 = heuristic) ride along.
 constexpr int kMaxClasses = 4;
+// geometry classes of one pnp_run_many call (launched in groups of kMaxClasses)
+constexpr int kMaxRunClasses = 1024;
 
 // Coefficient images of a batch of at least kQuadIlMin images are stored
 // image-interleaved, quad[(qy * qw + qx) * batch + image], so that one 128-byte

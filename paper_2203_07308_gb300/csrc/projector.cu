@@ -134,23 +134,27 @@ __global__ void k_prep_quad(const PrepTable t)
 }
 
 // Image-interleaved coefficient image, quad[(qy * qw + qx) * B + b].  A CTA
-// builds kIlCells consecutive cells of one row for all B images of its class:
-// it stages the two level-image rows those cells read (pooled for s > 1) in
-// shared memory image by image, then writes the cells with the image index
-// fastest, so that both the image reads and the cell writes are contiguous.
+// builds kIlRows x kIlCells cells for all B images of its class: it stages the
+// kIlRows + 1 level-image rows those cells read (pooled for s > 1) in shared
+// memory, kIlImages images at a time, then writes the cells with the image
+// index fastest, so that both the image reads and the cell writes are
+// contiguous.  (Blocks of 8 rows, which stage each row once for two rows of
+// cells, measured no faster than single rows.)
 constexpr int kIlCells = 32;
-constexpr int kIlImages = 64;    // images staged at a time (shared memory 64 x 2 x 33 floats)
+constexpr int kIlRows = 1;
+constexpr int kIlImages = 64;    // images staged at a time: 64 x 2 x 33 floats of shared memory
 
 struct PrepIlTable {
     PrepArgs c[kMaxClasses];
-    long begin[kMaxClasses + 1];   // cumulative CTA counts (qw rows x segments)
+    long begin[kMaxClasses + 1];   // cumulative CTA counts (row blocks x segments)
     int count;
 };
 
 __global__ void __launch_bounds__(256) k_prep_quad_il(const PrepIlTable t)
 {
     pdl_begin();
-    __shared__ float lv[kIlImages * 2 * (kIlCells + 1)];  // [image][2 rows][kIlCells + 1]
+    constexpr int C1 = kIlCells + 1, R1 = kIlRows + 1;
+    __shared__ float lv[kIlImages * R1 * C1];              // [image][row][column]
     int c = 0;
 #pragma unroll
     for (int k = 1; k < kMaxClasses; ++k)
@@ -159,23 +163,24 @@ __global__ void __launch_bounds__(256) k_prep_quad_il(const PrepIlTable t)
     const int qw = a.qw, B = a.batch;
     const int segs = (qw + kIlCells - 1) / kIlCells;
     const int local = (int)((long)blockIdx.x - t.begin[c]);
-    const int qy = local / segs, qx0 = (local - qy * segs) * kIlCells;
+    const int rblk = local / segs;
+    const int qy0 = rblk * kIlRows, qx0 = (local - rblk * segs) * kIlCells;
     const int n = a.n, s = a.s, ns = n / s;
-    constexpr int C1 = kIlCells + 1;
-    const int cells = min(kIlCells, qw - qx0);
-    float4* row = a.quad + ((long)qy * qw + qx0) * B;
-    for (int b0 = 0; b0 < B; b0 += kIlImages) {          // images in chunks of kIlImages
+    const int cells = min(kIlCells, qw - qx0), rows = min(kIlRows, qw - qy0);
+    for (int b0 = 0; b0 < B; b0 += kIlImages) {
         const int nb = min(kIlImages, B - b0);
         if (b0 > 0) __syncthreads();
-        for (int e = threadIdx.x; e < nb * 2 * C1; e += blockDim.x) {
-            const int b = e / (2 * C1), rem = e - b * 2 * C1, r = rem / C1, cx = rem - r * C1;
-            lv[e] = pooled(a.fine + (long)(b0 + b) * n * n, n, s, ns, qx0 - kPad + cx, qy - kPad + r);
+        for (int e = threadIdx.x; e < nb * R1 * C1; e += blockDim.x) {
+            const int b = e / (R1 * C1), rem = e - b * R1 * C1, r = rem / C1, cx = rem - r * C1;
+            lv[e] = pooled(a.fine + (long)(b0 + b) * n * n, n, s, ns, qx0 - kPad + cx, qy0 - kPad + r);
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < cells * nb; e += blockDim.x) {
-            const int cx = e / nb, b = e - cx * nb;
-            const float* l0 = lv + b * 2 * C1;
-            row[(long)cx * B + b0 + b] = make_quad(l0[cx], l0[cx + 1], l0[C1 + cx], l0[C1 + cx + 1]);
+        for (int e = threadIdx.x; e < rows * cells * nb; e += blockDim.x) {
+            const int rc = e / nb, b = e - rc * nb;
+            const int r = rc / cells, cx = rc - r * cells;
+            const float* l0 = lv + (b * R1 + r) * C1;
+            a.quad[((long)(qy0 + r) * qw + qx0 + cx) * B + b0 + b] =
+                make_quad(l0[cx], l0[cx + 1], l0[C1 + cx], l0[C1 + cx + 1]);
         }
     }
 }
@@ -1034,7 +1039,7 @@ cudaError_t launch_prep_multi(const PrepArgs* items, int count, cudaStream_t st)
         const PrepArgs& it = items[c];
         if (quad_interleaved(it.batch)) {
             ti.c[ti.count] = it;
-            ti.begin[ti.count + 1] = ti.begin[ti.count] + (long)it.qw * div_up(it.qw, kIlCells);
+            ti.begin[ti.count + 1] = ti.begin[ti.count] + (long)div_up(it.qw, kIlRows) * div_up(it.qw, kIlCells);
             ++ti.count;
         } else {
             t.c[t.count] = it;

@@ -90,6 +90,35 @@ def test_run_many_uneven_classes():
         assert np.abs(log - rl).max() < 1e-3
 
 
+def test_run_many_more_classes_than_one_launch_holds():
+    """Six classes (more than the four one launch covers): the phases run as one
+    launch per group of four classes, with schedules of different lengths, a
+    nine-image class (image-interleaved coefficient images) and the PSNR log;
+    every class against the oracle."""
+    import torch
+    specs = [
+        (synth.make_geometry(24, 16, 36, batch=2), [synth.Stage(2, 2, 3), synth.Stage(1, 2, 1)]),
+        (synth.make_geometry(32, 20, 48, batch=1), [synth.Stage(1, 3, 2)]),
+        (synth.make_geometry(28, 18, 40, batch=9), [synth.Stage(2, 3, 1)]),
+        (synth.make_geometry(36, 24, 52, batch=1), [synth.Stage(4, 1, 1), synth.Stage(1, 4, 3)]),
+        (synth.make_geometry(20, 12, 30, batch=3), [synth.Stage(1, 2, 1)]),
+        (synth.make_geometry(40, 22, 56, batch=2), [synth.Stage(2, 2, 2), synth.Stage(1, 3, 2)]),
+    ]
+    problems, refs = [], []
+    for k, (g, stages) in enumerate(specs):
+        x, b, eta, seq = make_problem(g, stages, 300 + 10 * k)
+        plan = pnp.Plan(g)
+        d_x = torch.zeros(g.batch, g.n, g.n, device="cuda")
+        problems.append(dict(plan=plan, stages=stages, eta=eta, seq=seq, b=dev(b), x=d_x, xtrue=dev(x)))
+        refs.append((g, stages, eta, seq, b, x))
+    logs = pnp.run_many(problems, lam=0.02, tv_iters=20)
+    for prob, (g, stages, eta, seq, b, x), log in zip(problems, refs, logs):
+        rx, rl = oracle_runs(g, stages, eta, seq, b, x, 0.02)
+        got = host(prob["x"])
+        assert rel(got, rx) < TOL_RECON, (g.n, rel(got, rx))
+        assert np.abs(log - rl).max() < 1e-3
+
+
 @pytest.mark.parametrize("back", [1 << 9 | 16, 1 << 8 | 8])
 def test_run_many_takes_the_largest_class_shapes(back):
     """One launch per phase uses the tuned (here pinned) projector shapes of the
