@@ -175,12 +175,16 @@ __global__ void __launch_bounds__(256) k_prep_quad_il(const PrepIlTable t)
             lv[e] = pooled(a.fine + (long)(b0 + b) * n * n, n, s, ns, qx0 - kPad + cx, qy0 - kPad + r);
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < rows * cells * nb; e += blockDim.x) {
-            const int rc = e / nb, b = e - rc * nb;
-            const int r = rc / cells, cx = rc - r * cells;
-            const float* l0 = lv + (b * R1 + r) * C1;
-            a.quad[((long)(qy0 + r) * qw + qx0 + cx) * B + b0 + b] =
-                make_quad(l0[cx], l0[cx + 1], l0[C1 + cx], l0[C1 + cx + 1]);
+        // thread -> image b = tid % nb (fixed), cells tid / nb, + cstep, ...: two
+        // divisions per thread, consecutive threads on consecutive images of a cell
+        const int b = threadIdx.x % nb, cstep = blockDim.x / nb;
+        if (threadIdx.x < cstep * nb) {
+            for (int r = 0; r < rows; ++r) {
+                const float* l0 = lv + (b * R1 + r) * C1;
+                float4* qrow = a.quad + ((long)(qy0 + r) * qw + qx0) * B + b0 + b;
+                for (int cx = threadIdx.x / nb; cx < cells; cx += cstep)
+                    qrow[(long)cx * B] = make_quad(l0[cx], l0[cx + 1], l0[C1 + cx], l0[C1 + cx + 1]);
+            }
         }
     }
 }

@@ -496,7 +496,7 @@ constexpr int kStripR = 8;                                   // rows per warp
 constexpr int kStripWO = 64 - 2 * kStripK - 1;               // output columns per tile
 
 struct StripTvClass {
-    const float* z; const float* sin; float* sout;          // state planes [4][batch][n][n]: r1 r2 p1 p2
+    const float* z; const float* sin; float* sout;          // state [batch][n][n] of float4 (r1, r2, p1, p2)
     float* xprev; float* y; const float* xtrue; double* mse_part;
     const float* xin;                                        // x_{i-1} (nullptr: xprev)
     int n, tiles_x, tiles;
@@ -554,22 +554,19 @@ __global__ void __launch_bounds__(32 * W, W == 8 ? 2 : 1) k_tv_strip(const Strip
         const long g = img + (long)i * n;
         float2 z = make_float2(0.0f, 0.0f);
         r1[m] = r2[m] = p1[m] = p2[m] = z;
+        const float4* sin4 = reinterpret_cast<const float4*>(a.sin);
         if (ri && ina) {
             z.x = __ldg(a.z + g + ja);
             if (!t.first) {
-                r1[m].x = __ldg(a.sin + g + ja);
-                r2[m].x = __ldg(a.sin + a.plane + g + ja);
-                p1[m].x = __ldg(a.sin + 2 * a.plane + g + ja);
-                p2[m].x = __ldg(a.sin + 3 * a.plane + g + ja);
+                const float4 q = __ldg(sin4 + g + ja);
+                r1[m].x = q.x; r2[m].x = q.y; p1[m].x = q.z; p2[m].x = q.w;
             }
         }
         if (ri && inb) {
             z.y = __ldg(a.z + g + jb);
             if (!t.first) {
-                r1[m].y = __ldg(a.sin + g + jb);
-                r2[m].y = __ldg(a.sin + a.plane + g + jb);
-                p1[m].y = __ldg(a.sin + 2 * a.plane + g + jb);
-                p2[m].y = __ldg(a.sin + 3 * a.plane + g + jb);
+                const float4 q = __ldg(sin4 + g + jb);
+                r1[m].y = q.x; r2[m].y = q.y; p1[m].y = q.z; p2[m].y = q.w;
             }
         }
         zs[(w * R + m) * 32 + lane] = z;
@@ -633,18 +630,9 @@ __global__ void __launch_bounds__(32 * W, W == 8 ? 2 : 1) k_tv_strip(const Strip
             const int i = rb + m;
             if (i < r0 || i >= r0 + HO || i >= n) continue;
             const long g = img + (long)i * n;
-            if (oa) {
-                a.sout[g + ja] = r1[m].x;
-                a.sout[a.plane + g + ja] = r2[m].x;
-                a.sout[2 * a.plane + g + ja] = p1[m].x;
-                a.sout[3 * a.plane + g + ja] = p2[m].x;
-            }
-            if (ob) {
-                a.sout[g + jb] = r1[m].y;
-                a.sout[a.plane + g + jb] = r2[m].y;
-                a.sout[2 * a.plane + g + jb] = p1[m].y;
-                a.sout[3 * a.plane + g + jb] = p2[m].y;
-            }
+            float4* sout4 = reinterpret_cast<float4*>(a.sout);
+            if (oa) sout4[g + ja] = make_float4(r1[m].x, r2[m].x, p1[m].x, p2[m].x);
+            if (ob) sout4[g + jb] = make_float4(r1[m].y, r2[m].y, p1[m].y, p2[m].y);
         }
     } else {
         // x = z - lambda L(p), relaxation, momentum, squared error
