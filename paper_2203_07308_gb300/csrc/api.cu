@@ -341,11 +341,14 @@ inline int subset_views(const pnp_geom& g, int p, int P)
 inline cudaStream_t S(void* st) { return (cudaStream_t)st; }
 
 // Forward residual r = A_s^{(p)} (level image in quad) - b^{(p)} into the workspace.
+// il: the output is a workspace residual that a backprojector of this batch reads
+// next (image-interleaved for batches with interleaved coefficient images).
 FwdArgs fwd_args(const pnp_geom& g, const LevelLayout& lv, char* ws, int p, int P, const float* b,
-                 float* out, int batch, const float* w = nullptr)
+                 float* out, int batch, const float* w = nullptr, bool il = false)
 {
     FwdArgs a{};
     a.w = w;
+    a.out_il = il && quad_interleaved(batch);
     a.quad = (const float4*)(ws + lv.off_quad);
     a.qw = lv.qw;
     a.quad_stride = (size_t)lv.qw * lv.qw;
@@ -390,9 +393,10 @@ float scatter_terms_bound(const pnp_geom& g, int factor)
 }
 
 BackArgs back_args(const pnp_geom& g, const LevelLayout& lv, char* ws, int p, int P, const float* res,
-                   int mode, float scale, const float* y, float eta, float* out, int batch)
+                   int mode, float scale, const float* y, float eta, float* out, int batch, bool il = false)
 {
     BackArgs a{};
+    a.res_il = il && quad_interleaved(batch);
     a.cmax = scatter_terms_bound(g, lv.factor);
     a.res = res;
     a.rayf = (const float4*)(ws + lv.off_rayf);
@@ -430,19 +434,19 @@ int grad_into(const pnp_geom& g, const Layout& L, int li, char* ws, const float*
         float* cgrad = cimg + (size_t)g.batch * (g.n / 2) * (g.n / 2);
         PNP_CUDA(launch_bicubic_down(y, cimg, g.n, lv.factor, g.batch, st));
         PNP_CUDA(launch_prep_quad(cimg, lv.ns, 1, g.batch, (float4*)(ws + lv.off_quad), lv.qw, st));
-        PNP_CUDA(launch_forward(fwd_args(g, lv, ws, p, P, b, res, g.batch, reg_weights(ws)), st, tu.lanes[li]));
+        PNP_CUDA(launch_forward(fwd_args(g, lv, ws, p, P, b, res, g.batch, reg_weights(ws), true), st, tu.lanes[li]));
         const double c = P <= 1 ? 1.0 : (double)P;
         PNP_CUDA(launch_backward(back_args(g, lv, ws, p, P, res, kBackRaw, (float)(g.step * lv.factor * c), nullptr,
-                                           0.0f, cgrad, g.batch), st, tu.groups[li]));
+                                           0.0f, cgrad, g.batch, true), st, tu.groups[li]));
         PNP_CUDA(launch_bicubic_up(cgrad, mode == kBackStep ? y : nullptr, out, g.n, lv.factor, g.batch, 1.0f, eta,
                                    st));
         return PNP_OK;
     }
     PNP_CUDA(launch_prep_quad(y, g.n, lv.factor, g.batch, (float4*)(ws + lv.off_quad), lv.qw, st));
-    PNP_CUDA(launch_forward(fwd_args(g, lv, ws, p, P, b, res, g.batch, reg_weights(ws)), st, tu.lanes[li]));
+    PNP_CUDA(launch_forward(fwd_args(g, lv, ws, p, P, b, res, g.batch, reg_weights(ws), true), st, tu.lanes[li]));
     const double c = P <= 1 ? 1.0 : (double)P;
     const float scale = (float)(g.step * lv.factor * c / ((double)lv.factor * lv.factor));
-    PNP_CUDA(launch_backward(back_args(g, lv, ws, p, P, res, mode, scale, y, eta, out, g.batch), st,
+    PNP_CUDA(launch_backward(back_args(g, lv, ws, p, P, res, mode, scale, y, eta, out, g.batch, true), st,
                              tu.groups[li]));
     return PNP_OK;
 }
@@ -510,9 +514,9 @@ int coarse_grad(const pnp_geom& g, const Layout& L, int li, char* ws, int kind, 
     } else {
         PNP_CUDA(launch_prep_quad(img, g.n, lv.factor, g.batch, (float4*)(ws + lv.off_quad), lv.qw, st));
     }
-    PNP_CUDA(launch_forward(fwd_args(g, lv, ws, p, P, b, res, g.batch, reg_weights(ws)), st, tu.lanes[li]));
+    PNP_CUDA(launch_forward(fwd_args(g, lv, ws, p, P, b, res, g.batch, reg_weights(ws), true), st, tu.lanes[li]));
     PNP_CUDA(launch_backward(back_args(g, lv, ws, p, P, res, kBackRaw, (float)(g.step * lv.factor), nullptr,
-                                       0.0f, out, g.batch), st, tu.groups[li]));
+                                       0.0f, out, g.batch, true), st, tu.groups[li]));
     return PNP_OK;
 }
 
@@ -1194,10 +1198,11 @@ int run_many_impl(const pnp_problem* pb_in, int np, const pnp_run_params* params
                 need_prep[na] = quad_ready[c] != lv.factor;
                 lvl[na] = li;
                 prep[na] = PrepArgs{y, g.n, lv.factor, g.batch, (float4*)(ws + lv.off_quad), lv.qw};
-                fwd[na] = fwd_args(g, lv, ws, p, P, q.d_b, res, g.batch, reg_weights(ws));
+                fwd[na] = fwd_args(g, lv, ws, p, P, q.d_b, res, g.batch, reg_weights(ws), true);
                 const double cs = P <= 1 ? 1.0 : (double)P;
                 const float scale = (float)(g.step * lv.factor * cs / ((double)lv.factor * lv.factor));
-                back[na] = back_args(g, lv, ws, p, P, res, kBackStep, scale, y, (float)q.h_eta[stage[c]], z, g.batch);
+                back[na] = back_args(g, lv, ws, p, P, res, kBackStep, scale, y, (float)q.h_eta[stage[c]], z, g.batch,
+                                     true);
                 const size_t img = (size_t)g.batch * g.n * g.n;
                 float* tvb = (float*)(ws + L.off_tv);
                 float* x2 = (float*)(ws + L.off_x2);
@@ -1463,14 +1468,14 @@ int pnp_autotune(const pnp_geom* g, const pnp_stage* stages, int n_stages, const
         const int P = stages[k].n_subsets;
         rc = launch_prep_quad(y, g->n, lv.factor, g->batch, (float4*)(ws + lv.off_quad), lv.qw, st) == cudaSuccess
                  ? PNP_OK : fail(PNP_ECUDA, "prep failed");
-        const FwdArgs fa = fwd_args(*g, lv, ws, 0, P, nullptr, res, g->batch);
+        const FwdArgs fa = fwd_args(*g, lv, ws, 0, P, nullptr, res, g->batch, nullptr, true);
         float best = 1e30f;
         for (int Q : {4, 8, 16}) {
             float ms = 0.0f;
             if (rc == PNP_OK) rc = timeit([&]() -> int { PNP_CUDA(launch_forward(fa, st, Q)); return PNP_OK; }, &ms);
             if (rc == PNP_OK && ms < best) { best = ms; tu.lanes[li] = Q; }
         }
-        const BackArgs ba = back_args(*g, lv, ws, 0, P, res, kBackRaw, 1.0f, nullptr, 0.0f, z, g->batch);
+        const BackArgs ba = back_args(*g, lv, ws, 0, P, res, kBackRaw, 1.0f, nullptr, 0.0f, z, g->batch, true);
         best = 1e30f;
         const int nsub = subset_views(*g, 0, P);
         // 8 x 4 blocks with 1..16 view groups; 4 x 4 blocks with 8..64 groups (one,

@@ -159,15 +159,16 @@ struct FwdArgs {
     int n_det, first_view, view_step, n_sub, batch;
     float step, weight;
     const float* b; int n_views;     // b: [batch][n_views][n_det] or null
-    float* out;                      // [batch][n_sub][n_det]
+    float* out;                      // [batch][n_sub][n_det], or [n_sub][n_det][batch] with out_il
     const float* w;                  // null or weights [batch][n_views][n_det]: out = w (A x - b)
+    int out_il = 0;                  // 1: image-interleaved output (a residual read by the backprojector)
 };
 cudaError_t launch_forward(const FwdArgs& a, cudaStream_t st, int lanes = 0);
 cudaError_t launch_forward_multi(const FwdArgs* items, int count, cudaStream_t st, int lanes = 0);
 
 enum BackMode { kBackRaw = 0, kBackGradFine = 1, kBackStep = 2 };
 struct BackArgs {
-    const float* res;                // [batch][n_sub][n_det]
+    const float* res;                // [batch][n_sub][n_det], or [n_sub][n_det][batch] with res_il
     const float4* rayf; const float2* rayi; const float4* view; const int2* rayk;
     int ns, n_det, first_view, view_step, n_sub, batch;
     float step;
@@ -177,7 +178,11 @@ struct BackArgs {
     float* out;
     float cmax = 0.0f;               // bound on the (ray, sample) terms one pixel receives from one
                                      // view (scatter form; 0: scatter unavailable, gather used)
+    int res_il = 0;                  // 1: image-interleaved residual (written with FwdArgs::out_il)
 };
+// Residual strides: element (image, view row, bin) at image * is + (row * n_det + bin) * js.
+__host__ __device__ inline long res_is(const BackArgs& a) { return a.res_il ? 1L : (long)a.n_sub * a.n_det; }
+__host__ __device__ inline int res_js(const BackArgs& a) { return a.res_il ? a.batch : 1; }
 // `groups`: view groups per CTA of the 2x2-block gather (1..16, 0 = heuristic),
 // PNP_BACK_TILE4 | G for 4 x 4-block CTAs, or PNP_BACK_SCATTER | TS for the
 // fixed-point scatter form on TS x TS tiles (TS in {12, 16, 22, 32}).

@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(32 * kFwdWarps, 4) k_forward(const FwdTable t)
     int v = 0;
     if (active) {
         v = a.first_view + vs * a.view_step;
-        out_idx = ((long)inst * a.n_sub + vs) * a.n_det + j;
+        out_idx = a.out_il ? ((long)vs * a.n_det + j) * a.batch + inst : ((long)inst * a.n_sub + vs) * a.n_det + j;
         const float4 f = __ldg(a.rayf + (long)v * a.n_det + j);
         const int2 kr = __ldg(a.rayk + (long)v * a.n_det + j);
         const float4* __restrict__ img = a.quad + (long)inst * a.quad_stride;
@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(32 * kFwdIlWarps) k_forward_il(const FwdTable 
         float val = a.weight * acc[q];
         if (a.b) val -= __ldg(a.b + bi);
         if (a.w) val *= __ldg(a.w + bi);
-        a.out[(long)inst * a.n_sub * a.n_det + out_row] = val;
+        a.out[a.out_il ? out_row * B + inst : (long)inst * a.n_sub * a.n_det + out_row] = val;
     }
 }
 
@@ -438,7 +438,8 @@ __global__ void __launch_bounds__(1024, 1) k_backward2x2(const BackTable t)
         const float inv_step = 1.0f / a.step;
         const float rho = 2.12132034f;                           // 1.5 sqrt(2)
         const int nwin = NWIN > 0 ? NWIN : (int)floorf(2.0f * rho * inv_step) + 1;
-        const float* __restrict__ res = a.res + (long)inst * a.n_sub * a.n_det;
+        const int js = res_js(a);
+        const float* __restrict__ res = a.res + (long)inst * res_is(a);
         for (int vs = g; vs < a.n_sub; vs += G) {
             const int v = a.first_view + vs * a.view_step;
             const float4 vp = __ldg(a.view + v);   // cos b, sin b, dso/s, (dso+ddo)/pitch
@@ -453,19 +454,19 @@ __global__ void __launch_bounds__(1024, 1) k_backward2x2(const BackTable t)
             const int jlo = max(0, (int)ceilf(uj - hw));
             const int jhi = min(a.n_det - 1, (int)floorf(uj + hw));
             const long base = (long)v * a.n_det;
-            const float* __restrict__ rrow = res + (long)vs * a.n_det;
+            const float* __restrict__ rrow = res + (long)vs * a.n_det * js;
             float4 fn = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
             float rn = 0.0f;
             if (jlo <= jhi) {
                 fn = __ldg(a.rayf + base + jlo);
-                rn = __ldg(rrow + jlo);
+                rn = __ldg(rrow + (long)jlo * js);
             }
             for (int j = jlo; j <= jhi; ++j) {
                 const float4 f = fn;
                 const float r = rn;
                 if (j < jhi) {
                     fn = __ldg(a.rayf + base + j + 1);
-                    rn = __ldg(rrow + j + 1);
+                    rn = __ldg(rrow + (long)(j + 1) * js);
                 }
                 const float ax = px - f.x, ay = py - f.y;
                 const float e = ax * f.w - ay * f.z;
@@ -578,7 +579,11 @@ __global__ void __launch_bounds__(kBackBatchThreads, 1) k_backward_batch(const B
     const int i0 = chunk * BC;
     const int ni = min(BC, a.batch - i0);                      // images in this chunk
     const bool inside = bx < nb && by < nb;
-    const long istride = (long)a.n_sub * a.n_det;              // residual stride between images
+    const long istride = res_is(a);                            // residual stride between images
+    const int js = res_js(a);                                  // ... and between bins
+    // image-interleaved residuals of a batch of a multiple of 4: the chunk's
+    // residuals of a ray are contiguous and 16-byte aligned
+    const bool vec = a.res_il && (a.batch & 3) == 0 && (BC & 3) == 0;
     float acc[BC][4];
 #pragma unroll
     for (int b = 0; b < BC; ++b) acc[b][0] = acc[b][1] = acc[b][2] = acc[b][3] = 0.0f;
@@ -606,7 +611,7 @@ __global__ void __launch_bounds__(kBackBatchThreads, 1) k_backward_batch(const B
             const int jlo = max(0, (int)ceilf(uj - hw));
             const int jhi = min(a.n_det - 1, (int)floorf(uj + hw));
             const long base = (long)v * a.n_det;
-            const float* __restrict__ rrow = res + (long)vs * a.n_det;
+            const float* __restrict__ rrow = res + (long)vs * a.n_det * js;
             float4 fn = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
             if (jlo <= jhi) fn = __ldg(a.rayf + base + jlo);
             for (int j = jlo; j <= jhi; ++j) {
@@ -618,8 +623,17 @@ __global__ void __launch_bounds__(kBackBatchThreads, 1) k_backward_batch(const B
                 if (fabsf(e) >= hwid) continue;
                 // the chunk's residuals of this ray, in flight while the hats are computed
                 float r[BC];
+                if (vec) {
+                    const float4* r4 = reinterpret_cast<const float4*>(rrow + (long)j * js);
 #pragma unroll
-                for (int b = 0; b < BC; ++b) r[b] = b < ni ? __ldg(rrow + b * istride + j) : 0.0f;
+                    for (int b = 0; b < BC; b += 4) {
+                        const float4 q = b < ni ? __ldg(r4 + b / 4) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                        r[b] = q.x; r[b + 1] = q.y; r[b + 2] = q.z; r[b + 3] = q.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int b = 0; b < BC; ++b) r[b] = b < ni ? __ldg(rrow + b * istride + (long)j * js) : 0.0f;
+                }
                 const float tau = fmaf(ax, f.z, ay * f.w);
                 const float k0 = ceilf(fmaf(tau - hwid, inv_step, -0.5f));
                 const int cnt = (int)(2.0f * hwid * inv_step) + 1;
@@ -754,7 +768,8 @@ __global__ void __launch_bounds__(NT) k_backward_scatter(const BackScTable t)
     const int tx0 = (tile % tiles_x) * TS, ty0 = (tile / tiles_x) * TS;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < AP * AP; i += NT) acc[i] = 0;
-    const float* __restrict__ res = a.res + (long)inst * a.n_sub * a.n_det;
+    const int js = res_js(a);
+    const float* __restrict__ res = a.res + (long)inst * res_is(a);
     const float half = 0.5f * (float)(ns - 1);
     const float jc = 0.5f * (float)(a.n_det - 1);
     // bins of a view that can reach the tile: the central projection of the
@@ -790,9 +805,9 @@ __global__ void __launch_bounds__(NT) k_backward_scatter(const BackScTable t)
     for (int vs = wid; vs < a.n_sub; vs += NW) {
         int jlo, jhi;
         shadow(__ldg(a.view + a.first_view + vs * a.view_step), jlo, jhi);
-        const float* __restrict__ rrow = res + (long)vs * a.n_det;
+        const float* __restrict__ rrow = res + (long)vs * a.n_det * js;
         for (int j = jlo + lane; j <= jhi; j += 32) {
-            const float rv = fabsf(__ldg(rrow + j));
+            const float rv = fabsf(__ldg(rrow + (long)j * js));
             bad |= !(rv <= 3.402823466e38f);
             m = fmaxf(m, rv);
         }
@@ -822,7 +837,7 @@ __global__ void __launch_bounds__(NT) k_backward_scatter(const BackScTable t)
             int jlo, jhi;
             shadow(__ldg(a.view + v), jlo, jhi);
             const long base = (long)v * a.n_det;
-            const float* __restrict__ rrow = res + (long)vs * a.n_det;
+            const float* __restrict__ rrow = res + (long)vs * a.n_det * js;
             // lane = ray; lanes start five rays apart, so that the samples of one
             // atomic instruction rarely share a pixel
             for (int j = jlo + ((lane * 5) & 31); j <= jhi; j += 32) {
@@ -837,7 +852,7 @@ __global__ void __launch_bounds__(NT) k_backward_scatter(const BackScTable t)
                 const float fb = fminf(fmaf(thi, inv_step, -0.5f), (float)kr.y + 2.0f);
                 const int ka = max(kr.x, (int)ceilf(fa) - 1);
                 const int kb = min(kr.y, (int)floorf(fb) + 1);
-                const float rS = __ldg(rrow + j) * S;
+                const float rS = __ldg(rrow + (long)j * js) * S;
                 for (int k = ka; k <= kb; ++k) {
                     const float tt = ((float)k + 0.5f) * a.step;
                     const float X = fmaf(tt, f.z, f.x);

@@ -84,3 +84,26 @@ def test_interleaved_gradient_weighted_parity():
     for i in (0, 7, 11):
         ref = oracle.grad(g, 2, y[i], b[i], 2, 3, w=w[i])
         assert rel(got[i], ref) < TOL, (i, rel(got[i], ref))
+
+
+@pytest.mark.parametrize("back", [8, 1 << 8 | 16, 4 << 16 | 4, 8 << 16 | 1 << 8 | 8, 16 << 16 | 8, 1 << 9 | 16])
+@pytest.mark.parametrize("batch", [12, 10])
+def test_interleaved_residual_every_backprojector_shape(back, batch):
+    """Inside the gradient path the residual of an interleaved batch is stored
+    image-interleaved too; every backprojector form reads it (the batched gather
+    with 16-byte loads when the batch is a multiple of 4, scalar loads otherwise):
+    the sketched subset gradient against the oracle."""
+    import torch
+    g = synth.make_geometry(40, 24, 60, batch=batch)
+    plan = pnp.Plan(g)
+    plan.set_launch_shapes(back=(back,) * 4)
+    rng = np.random.default_rng(batch)
+    y = f32(rng.random((batch, 40, 40)))
+    b = f32(rng.standard_normal((batch, 24, 60)) * 3)
+    for s, p, P in ((1, 1, 3), (2, 0, 1)):
+        out = torch.empty(batch, 40, 40, device="cuda")
+        plan.sketch_grad(s, dev(y), dev(b), out, p, P)
+        got = host(out)
+        for i in (0, batch - 1):
+            ref = oracle.grad(g, s, y[i], b[i], p, P)
+            assert rel(got[i], ref) < TOL, (back, s, i, rel(got[i], ref))
