@@ -42,21 +42,47 @@ L2_FLUSH_BYTES = 512 << 20
 FLOP_PER_SAMPLE = 12
 BYTES_PER_SAMPLE = 16
 
-# DRAM bytes per launch of the dominant kernel at the headline workload, from
-# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only
-# while that kernel's source is the one that was measured (else null).
-DOMINANT_TRAFFIC = {"bytes_per_launch": None, "source_sha256": None, "profile": None}
+# Algorithmic work per pixel and FGP iteration of the TV-prox denoiser (Beck &
+# Teboulle's FGP): L(r) 3 adds, z - lambda L 1 FMA, two differences, two dual
+# FMAs, |a|^2 (mul + FMA), projection (compare, rsqrt, 2 mul), momentum (2 x
+# (sub + FMA)): 24 FP32 operations.
+FLOP_PER_PIXEL_ITER = 24
+
+# DRAM bytes per unit of each kernel at the headline workload, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum, cold caches), valid only
+# while the kernel's source is the one that was measured (else null).  Units: one
+# launch of the projector kernels (the forward's figure weighted over the
+# schedule's 24 / 24 / 72 launches at the 4x / 2x / full levels, whose captured
+# launches read 8.3 / 21.0 / 79.9 MB), one denoise (two launches) of the FGP strips.
+KERNEL_TRAFFIC = {
+    "backward": {"bytes_per_unit": 20122581, "unit": "launch", "source": "projector.cu",
+                 "begin": "struct BackTable {",
+                 "end": "// ------------------------------------------------------------------ transpose A_s^T, scatter form",
+                 "sha256": "d41b2c67aba3a5c6bfe7404ffd4f7dbf6b10ddf6f3e76050350d7e87f268399e",
+                 "profile": "profiles/k_backward_batch_512x16_720x768.md"},
+    "forward": {"bytes_per_unit": 53812000, "unit": "launch", "source": "projector.cu",
+                "begin": "// Forward projector on an image-interleaved coefficient image.",
+                "end": "// ------------------------------------------------------------------ transpose A_s^T\n// Pixel-driven gather.",
+                "sha256": "2a6b15942b2a4ecf1af21a1cdd52adde7ee8a2332c4b56b8d25735b2d8c22694",
+                 "profile": "profiles/k_forward_il_512x16_720x768.md"},
+    "denoise": {"bytes_per_unit": 142013440, "unit": "denoise (two launches)", "source": "tv.cu",
+                "begin": "// ------------------------------------------------------------------ register-resident FGP strips",
+                "end": "inline cudaError_t counted(cudaError_t e = cudaGetLastError())",
+                "sha256": "08066feaf92c520bee06bd03b0a373676928e1ef034434d4d611cbd326d3b308",
+                 "profile": "profiles/k_tv_strip_512x16.md"},
+}
 
 
-def kernel_source_sha():
-    """SHA-256 of the gather backprojector's source (its table, kernels and
-    launcher text), so that the stored DRAM traffic is reported only for the
-    kernel it was measured on."""
+def kernel_source_sha(kind):
+    """SHA-256 of a kernel's source text (the section between two markers of its
+    file), so that a stored DRAM traffic is reported only for the kernel it was
+    measured on."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_2203_07308_gb300", "csrc", "projector.cu")) as f:
+    k = KERNEL_TRAFFIC[kind]
+    with open(os.path.join(ROOT, "paper_2203_07308_gb300", "csrc", k["source"])) as f:
         src = f.read()
-    a = src.index("struct BackTable {")
-    b = src.index("// ------------------------------------------------------------------ transpose A_s^T, scatter form")
+    a = src.index(k["begin"])
+    b = src.index(k["end"].replace("\\n", "\n"), a)
     return hashlib.sha256(src[a:b].encode()).hexdigest()
 
 
@@ -379,20 +405,32 @@ def onchip_peaks():
     return pnp.onchip_bandwidth()
 
 
-def rooflines(samples_step, steps, ph_ms, ph_n, n_sm, clock_mhz, onchip):
-    """Per-kernel rooflines of the projector pair from their live launch durations
-    (phase events) and the algorithmic work per sample."""
+def rooflines(samples_step, pixel_iters_step, steps, ph_ms, ph_n, n_sm, clock_mhz, onchip):
+    """Per-kernel rooflines of the projector pair and the denoiser from their live
+    launch durations (phase events) and their algorithmic work: per projected
+    sample 12 FP32 operations and 16 B of taps, per pixel and FGP iteration 24
+    FP32 operations."""
     alu_peak = n_sm * 128 * 2 * clock_mhz * 1e6 / 1e12      # FP32 TFLOP/s: 128 lanes x FMA per SM per clock
     out = {}
-    for ph, kname in (("backward", "k_backward (A_s^T, U and the gradient step)"),
-                      ("forward", "k_forward (A_s S y - b)")):
+    for ph, kname in (("backward", "k_backward_batch (A_s^T, U and the gradient step)"),
+                      ("forward", "k_forward_il (A_s S y - b)"),
+                      ("denoise", "k_tv_strip (TV-prox by FGP, relaxation, momentum)")):
         if ph_n.get(ph, 0) <= 0 or ph_ms.get(ph, 0.0) <= 0.0:
             continue
         secs = ph_ms[ph] / 1000.0
+        if ph == "denoise":
+            flop = FLOP_PER_PIXEL_ITER * pixel_iters_step * steps
+            tflops = flop / secs / 1e12
+            out[ph] = {"kernel": kname, "units": ph_n[ph], "unit": "denoise (20 FGP iterations, two launches)",
+                       "mean_unit_us": 1000.0 * ph_ms[ph] / ph_n[ph],
+                       "gpixel_iters_per_s": pixel_iters_step * steps / secs / 1e9,
+                       "alu": {"achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s", "frac": tflops / alu_peak}}
+            continue
         samples = samples_step * steps
         tflops = FLOP_PER_SAMPLE * samples / secs / 1e12
         gbs = BYTES_PER_SAMPLE * samples / secs / 1e9
-        out[ph] = {"kernel": kname, "launches": ph_n[ph], "mean_launch_us": 1000.0 * ph_ms[ph] / ph_n[ph],
+        out[ph] = {"kernel": kname, "units": ph_n[ph], "unit": "launch",
+                   "mean_unit_us": 1000.0 * ph_ms[ph] / ph_n[ph],
                    "gsamples_per_s": samples / secs / 1e9,
                    "alu": {"achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s", "frac": tflops / alu_peak},
                    "l1": {"achieved": gbs, "peak": onchip["l1_gbs"], "unit": "GB/s", "frac": gbs / onchip["l1_gbs"]},
@@ -790,19 +828,23 @@ def run_native(args, rank, world):
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     clock_mhz = clocks.get("sm_max_mhz") or 2070.0
     samples_step = step_samples(plan, wl, seq)
-    per_kernel, alu_peak = rooflines(samples_step, args.steps, ph_ms, ph_n, n_sm, clock_mhz, onchip)
+    pixel_iters_step = float(B) * g.n * g.n * wl.tv_iters * total_iters
+    per_kernel, alu_peak = rooflines(samples_step, pixel_iters_step, args.steps, ph_ms, ph_n, n_sm, clock_mhz, onchip)
     dominant = max(per_kernel, key=lambda k: ph_ms[k])
     dk = per_kernel[dominant]
     traffic = None
-    if DOMINANT_TRAFFIC["bytes_per_launch"] and kernel_source_sha() == DOMINANT_TRAFFIC["source_sha256"]:
-        traffic = DOMINANT_TRAFFIC["bytes_per_launch"]
+    kt = KERNEL_TRAFFIC.get(dominant)
+    if kt and kt["bytes_per_unit"] and kt["sha256"] and kernel_source_sha(dominant) == kt["sha256"]:
+        traffic = kt["bytes_per_unit"]
+    work = (f"{FLOP_PER_PIXEL_ITER} FLOP per pixel and FGP iteration" if dominant == "denoise"
+            else f"{FLOP_PER_SAMPLE} FLOP per projected sample")
     roof = {"kernel": dk["kernel"], "bound": "alu", "achieved": dk["alu"]["achieved"], "peak": alu_peak,
             "unit": "TFLOP/s", "frac": dk["alu"]["frac"], "traffic": traffic,
-            "flop_per_sample": FLOP_PER_SAMPLE, "samples_per_step": samples_step,
-            "launches_per_step": ph_n[dominant] // args.steps,
-            "mean_launch_us": dk["mean_launch_us"],
-            "timing": (f"CUDA event pair on the run's stream around each of the {ph_n[dominant]} launches of "
-                       f"the K timed steps, re-run with phase events"),
+            "traffic_unit": kt["unit"] if kt else None,
+            "work": work, "samples_per_step": samples_step, "pixel_iterations_per_step": pixel_iters_step,
+            "units_per_step": ph_n[dominant] // args.steps, "mean_unit_us": dk["mean_unit_us"],
+            "timing": (f"CUDA event pair on the run's stream around each of the {ph_n[dominant]} "
+                       f"{dominant} phases of the K timed steps, re-run with phase events"),
             "peak_source": (f"{n_sm} SMs x 128 FP32 lanes x 2 FLOP (FMA) x {clock_mhz:.0f} MHz "
                             "(derived from the unit counts and the sampled maximum SM clock)"),
             "hbm_gbs_measured_peak": None}
