@@ -206,12 +206,11 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
                 const float g2 = (flags[m] & 8) ? x0[m] - xt[q[m] + 1] : 0.0f;
                 float pa = fmaf(g1, inv8l, r1[m]);
                 float pc = fmaf(g2, inv8l, r2[m]);
+                // projection onto the unit disc: scale min(1, 1/|a|) without a branch
                 const float nrm2 = fmaf(pa, pa, pc * pc);
-                if (nrm2 > 1.0f) {
-                    const float sc = rsqrtf(nrm2);
-                    pa *= sc;
-                    pc *= sc;
-                }
+                const float sc = fminf(1.0f, rsqrtf(nrm2));
+                pa *= sc;
+                pc *= sc;
                 r1[m] = fmaf(mo, pa - p1[m], pa);
                 r2[m] = fmaf(mo, pc - p2[m], pc);
                 p1[m] = pa;
@@ -418,12 +417,11 @@ __global__ void __launch_bounds__(32 * kWarpTvWarps) k_tv_warp(const WarpTvArgs 
             const float g2 = jlast ? xt[m] - right : 0.0f;
             float pa = fmaf(g1, inv8l, r1[m]);
             float pc = fmaf(g2, inv8l, r2[m]);
+            // projection onto the unit disc: scale min(1, 1/|a|) without a branch
             const float nrm2 = fmaf(pa, pa, pc * pc);
-            if (nrm2 > 1.0f) {
-                const float sc = rsqrtf(nrm2);
-                pa *= sc;
-                pc *= sc;
-            }
+            const float sc = fminf(1.0f, rsqrtf(nrm2));
+            pa *= sc;
+            pc *= sc;
             r1[m] = fmaf(mo, pa - p1[m], pa);
             r2[m] = fmaf(mo, pc - p2[m], pc);
             p1[m] = pa;
@@ -607,10 +605,9 @@ __global__ void __launch_bounds__(32 * W, W == 8 ? 2 : 1) k_tv_strip(const Strip
                 float2 pa = __ffma2_rn(g1, inv8l2, r1[m]);
                 float2 pc = __ffma2_rn(g2, inv8l2, r2[m]);
                 const float2 nrm2 = __ffma2_rn(pa, pa, __fmul2_rn(pc, pc));
-                // projection onto the unit disc without a branch: the scale is 1 (exact)
-                // unless |p| > 1
-                const float2 sc = make_float2(nrm2.x > 1.0f ? rsqrtf(nrm2.x) : 1.0f,
-                                              nrm2.y > 1.0f ? rsqrtf(nrm2.y) : 1.0f);
+                // projection onto the unit disc without a branch: scale min(1, 1/|a|)
+                // (1 for |a| <= 1 up to the last bit of rsqrt at |a| = 1; inf at 0 gives 1)
+                const float2 sc = make_float2(fminf(1.0f, rsqrtf(nrm2.x)), fminf(1.0f, rsqrtf(nrm2.y)));
                 pa = __fmul2_rn(pa, sc);
                 pc = __fmul2_rn(pc, sc);
                 r1[m] = __ffma2_rn(mo, sub2(pa, p1[m]), pa);
