@@ -327,9 +327,9 @@ int pnp_run_many(const pnp_problem* problems, int n_problems, const pnp_run_para
  *           (G x 32 or G x 16 for 8 x 4 or 4 x 4 blocks); its results are bitwise
  *           those of the same gather shape without PNP_BACK_BATCH
  *   tile    FGP denoiser: side of the shared-memory tile (8..40), 1 for the
- *           register-resident warp tiles (five iterations per launch), or 2 / 3
- *           for the register-resident strips (64 columns x 64 / 96 rows per CTA,
- *           two columns per lane, ten iterations per launch)
+ *           register-resident warp tiles (five iterations per launch), or 2 / 3 / 4
+ *           for the register-resident strips (64 columns x 64 / 96 / 128 rows per
+ *           CTA, two columns per lane, ten iterations per launch)
  * The gather's view groups fix its summation order: results are bitwise
  * reproducible for fixed shapes.  The scatter adds each sample's four bilinear
  * terms as 32-bit fixed-point integers (scale: the tile's largest |residual|

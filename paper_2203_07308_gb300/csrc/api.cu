@@ -1520,7 +1520,7 @@ int pnp_autotune(const pnp_geom* g, const pnp_stage* stages, int n_stages, const
         const int iters = std::min(pr.tv_iters, 20);   // up to two launches, the last one with the ring
         float best = 1e30f;
         for (int T : {T0 - 6, T0 - 4, T0 - 2, T0, T0 + 2, T0 + 4, T0 + 6, 16, 24, 32, kTvTileWarp, kTvTileStrip8,
-                      kTvTileStrip12}) {
+                      kTvTileStrip12, kTvTileStrip16}) {
             if (rc != PNP_OK) break;
             if (T != kTvTileWarp && !tv_is_strip(T) && (T < 8 || T > 40)) continue;
             TvItem it{};
@@ -1589,7 +1589,7 @@ int pnp_set_launch_shapes(const pnp_geom* g, const pnp_launch_shapes* in, void* 
         tu.groups[k] = b;
     }
     if (in->tile != 0 && in->tile != kTvTileWarp && !tv_is_strip(in->tile) && (in->tile < 8 || in->tile > 40))
-        return fail(PNP_EINVAL, "tile %d is neither 0, 1, 2, 3 nor in [8, 40]", in->tile);
+        return fail(PNP_EINVAL, "tile %d is neither 0, 1, 2, 3, 4 nor in [8, 40]", in->tile);
     tu.tile = in->tile;
     reg_set_tuned(d_ws, tu);
     return PNP_OK;

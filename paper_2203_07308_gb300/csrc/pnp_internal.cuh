@@ -222,14 +222,15 @@ cudaError_t launch_tv_tiled(const float* z, int n, int batch, float lambda, int 
                             float amom, float* xprev, float* y, const float* xtrue, double* mse_part,
                             float* state_a, float* state_b, cudaStream_t st, int tile = 0);
 // TvItem::tile: 0 = cost model, 8..40 = shared-memory tiles of that side,
-// kTvTileWarp = register-resident warp tiles, kTvTileStrip8 / kTvTileStrip12 =
-// register-resident strips of 64 columns x 64 / 96 rows (8 / 12 warps per CTA)
-// (the first item decides the variant).
+// kTvTileWarp = register-resident warp tiles, kTvTileStrip8 / 12 / 16 =
+// register-resident strips of 64 columns x 64 / 96 / 128 rows (8 / 12 / 16 warps
+// per CTA) (the first item decides the variant).
 constexpr int kTvTileWarp = 1;
 constexpr int kTvTileStrip8 = 2;
 constexpr int kTvTileStrip12 = 3;
-inline bool tv_is_strip(int tile) { return tile == kTvTileStrip8 || tile == kTvTileStrip12; }
-inline int tv_strip_warps(int tile) { return tile == kTvTileStrip8 ? 8 : 12; }
+constexpr int kTvTileStrip16 = 4;
+inline bool tv_is_strip(int tile) { return tile >= kTvTileStrip8 && tile <= kTvTileStrip16; }
+inline int tv_strip_warps(int tile) { return tile == kTvTileStrip8 ? 8 : tile == kTvTileStrip12 ? 12 : 16; }
 // the denoiser family of a tile code: 0 shared-memory tiles, 1 warp tiles, 2 strips
 inline int tv_family(int tile) { return tile == kTvTileWarp ? 1 : tv_is_strip(tile) ? 2 : 0; }
 struct TvItem {

@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(32 * kWarpTvWarps) k_tv_warp(const WarpTvArgs 
 // ------------------------------------------------------------------ register-resident FGP strips
 // The same temporal blocking as the tiles above, organised so that almost every
 // neighbour is in a register: a CTA owns a region of 64 columns x 8W rows (W
-// warps stacked vertically, W = 8 or 12), lane l of warp w holds columns 2l and 2l+1 of the
+// warps stacked vertically, W = 8, 12 or 16), lane l of warp w holds columns 2l and 2l+1 of the
 // warp's 8 rows (z in shared memory; r and p in registers).  Vertical
 // neighbours inside a warp are the lane's own registers, horizontal ones the
 // lane's other column or the adjacent lane's (one shuffle per row and phase);
@@ -515,7 +515,7 @@ struct StripTvArgs {
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
 
 template <bool LAST, int W>
-__global__ void __launch_bounds__(32 * W, W == 8 ? 2 : 1) k_tv_strip(const StripTvArgs t)
+__global__ void __launch_bounds__(32 * W, W == 8 ? 2 : 1) k_tv_strip(const StripTvArgs t)   // W = 8, 12 or 16
 {
     pdl_begin();
     constexpr int R = kStripR;
@@ -864,9 +864,12 @@ cudaError_t launch_tv_strip_multi(const TvItem* items, int count, float lambda, 
         if (a.W == 8)
             e = a.last ? launch_pdl(k_tv_strip<true, 8>, grd, blk, smem, st, a)
                        : launch_pdl(k_tv_strip<false, 8>, grd, blk, smem, st, a);
-        else
+        else if (a.W == 12)
             e = a.last ? launch_pdl(k_tv_strip<true, 12>, grd, blk, smem, st, a)
                        : launch_pdl(k_tv_strip<false, 12>, grd, blk, smem, st, a);
+        else
+            e = a.last ? launch_pdl(k_tv_strip<true, 16>, grd, blk, smem, st, a)
+                       : launch_pdl(k_tv_strip<false, 16>, grd, blk, smem, st, a);
         g_launches.fetch_add(1, std::memory_order_relaxed);
         if (e != cudaSuccess) return e;
         k0 += K;

@@ -1,6 +1,6 @@
 """The FGP denoiser variants inside Algorithm 1 against the FP64 oracle: the
 shared-memory tiles, the register-resident warp tiles (tile = 1) and strips
-(tile = 2, 3), pinned
+(tile = 2, 3, 4), pinned
 with pnp_set_launch_shapes, on ragged and uneven sizes, with iteration counts
 that split unevenly over launches, and with the PSNR log (per-tile partials)."""
 import numpy as np
@@ -41,7 +41,7 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
 
 
-@pytest.mark.parametrize("tile", [1, 2, 3, 16, 22])
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 16, 22])
 @pytest.mark.parametrize("n,views,det,batch,tv_iters", [(64, 60, 96, 2, 20), (37, 24, 60, 3, 7),
                                                        (100, 40, 150, 1, 3), (48, 30, 72, 2, 11)])
 def test_denoiser_variants_in_algorithm1(tile, n, views, det, batch, tv_iters):
@@ -94,14 +94,14 @@ def test_mixed_classes_with_different_denoiser_variants():
 @pytest.mark.parametrize("n,batch,tv_iters", [(200, 2, 20), (130, 3, 13), (37, 1, 20)])
 def test_strip_heights_agree_bitwise(n, batch, tv_iters):
     """The strips compute every kept value with the arithmetic of a global FGP
-    iteration, so the two CTA heights (64 and 96 rows: different tilings and halos)
-    give the same bits, and both the oracle's denoiser output within 1e-5."""
+    iteration, so the three CTA heights (64, 96 and 128 rows: different tilings and
+    halos) give the same bits, and all the oracle's denoiser output within 1e-5."""
     import torch
     g = synth.make_geometry(n, 30, int(1.5 * n), batch=batch)
     rng = np.random.default_rng(n)
     z = f32(rng.random((batch, n, n)))
     outs = []
-    for tile in (2, 3):
+    for tile in (2, 3, 4):
         plan = pnp.Plan(g)
         plan.set_launch_shapes(tile=tile)
         d_x = dev(z)
@@ -109,7 +109,7 @@ def test_strip_heights_agree_bitwise(n, batch, tv_iters):
         plan.run([synth.Stage(1, 1, 1)], [0.0], None, dev(np.zeros((batch, 30, g.n_det))), d_x,
                  alpha=1.0, lam=0.05, tv_iters=tv_iters, momentum=False)
         outs.append(host(d_x))
-    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
     for i in range(batch):
         ref = oracle.fgp(z[i], 0.05, tv_iters)
         assert rel(outs[0][i], ref) < 1e-5, rel(outs[0][i], ref)
