@@ -632,24 +632,43 @@ __global__ void __launch_bounds__(32 * W, W == 8 ? 2 : 1) k_tv_strip(const Strip
             if (ob) sout4[g + jb] = make_float4(r1[m].y, r2[m].y, p1[m].y, p2[m].y);
         }
     } else {
-        // x = z - lambda L(p), relaxation, momentum, squared error
+        // x = z - lambda L(p), relaxation, momentum, squared error.  All of this
+        // thread's x values are formed and all its x_{i-1} loads issued before the
+        // first store (the stores could alias the loads for the compiler, which
+        // would otherwise serialise sixteen round trips to memory).
         up[w * 32 + lane] = p1[R - 1];
         __syncthreads();
         float2 u = up[wup * 32 + lane];
-        double e2 = 0.0;
+        float2 xv[R];
 #pragma unroll
         for (int m = 0; m < R; ++m) {
             const float2 left = make_float2(__shfl_up_sync(kAll, p2[m].y, 1), p2[m].x);
-            const float2 z2 = zs[(w * R + m) * 32 + lane];
             float2 l = __fadd2_rn(p1[m], p2[m]);
             l = sub2(l, u);
             l = sub2(l, left);
-            const float2 xv = __ffma2_rn(nlam2, l, z2);
+            xv[m] = __ffma2_rn(nlam2, l, zs[(w * R + m) * 32 + lane]);
             u = p1[m];
+        }
+        const float* __restrict__ xold = a.xin ? a.xin : a.xprev;
+        float2 xo[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            const int i = rb + m;
+            const bool row = i >= r0 && i < r0 + HO && i < n;
+            const long g = img + (long)(row ? i : 0) * n;
+            xo[m] = make_float2(0.0f, 0.0f);
+            if (a.y && row && oa) xo[m].x = xold[g + ja];
+            if (a.y && row && ob) xo[m].y = xold[g + jb];
+        }
+        double e2 = 0.0;
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
             const int i = rb + m;
             if (i < r0 || i >= r0 + HO || i >= n) continue;
             const long g = img + (long)i * n;
-            const float xva[2] = {xv.x, xv.y};
+            const float2 z2 = zs[(w * R + m) * 32 + lane];
+            const float xva[2] = {xv[m].x, xv[m].y};
+            const float xpa[2] = {xo[m].x, xo[m].y};
             const float zv[2] = {z2.x, z2.y};
             const bool ov[2] = {oa, ob};
             const int jv[2] = {ja, jb};
@@ -658,10 +677,7 @@ __global__ void __launch_bounds__(32 * W, W == 8 ? 2 : 1) k_tv_strip(const Strip
                 if (!ov[h]) continue;
                 const long gg = g + jv[h];
                 const float xi = (1.0f - t.alpha) * zv[h] + t.alpha * xva[h];
-                if (a.y) {
-                    const float xp = a.xin ? a.xin[gg] : a.xprev[gg];
-                    a.y[gg] = xi + a.amom * (xi - xp);
-                }
+                if (a.y) a.y[gg] = xi + a.amom * (xi - xpa[h]);
                 a.xprev[gg] = xi;
                 if (a.xtrue) {
                     const double dd = (double)xi - (double)__ldg(a.xtrue + gg);
