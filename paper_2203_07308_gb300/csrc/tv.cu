@@ -241,6 +241,23 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
         __syncthreads();
         double e2 = 0.0;
         float* ys = xt;                     // y on the tile and its ring, for the coefficient image
+        // every x_{i-1} load of this thread is issued before its first store (the
+        // stores could alias the loads for the compiler, which would serialise them)
+        float xpv[NP];
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+            const int f = threadIdx.x + m * blockDim.x;
+            const int li = f / S, lj = f - li * S;
+            const int i = oi + li, j = oj + lj;
+            const bool own = flags[m] & 16;
+            const bool rim = ring && f < S * S && !own && i >= i0 && j >= j0 && i < i0 + T + ring &&
+                             j < j0 + T + ring && i < n && j < n;
+            xpv[m] = 0.0f;
+            if (a.y && (own || rim)) {
+                const long g = img + (long)i * n + j;
+                xpv[m] = a.xin ? a.xin[g] : a.xprev[g];
+            }
+        }
 #pragma unroll
         for (int m = 0; m < NP; ++m) {
             const int f = threadIdx.x + m * blockDim.x;
@@ -257,10 +274,7 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
                 const float xi = (1.0f - t.alpha) * z[m] + t.alpha * x;
                 const long g = img + (long)i * n + j;
                 float yv = 0.0f;
-                if (a.y) {
-                    const float xp = a.xin ? a.xin[g] : a.xprev[g];
-                    yv = xi + a.amom * (xi - xp);
-                }
+                if (a.y) yv = xi + a.amom * (xi - xpv[m]);
                 if (own) {
                     if (a.y) a.y[g] = yv;
                     a.xprev[g] = xi;
@@ -444,8 +458,16 @@ __global__ void __launch_bounds__(32 * kWarpTvWarps) k_tv_warp(const WarpTvArgs 
         }
         return;
     }
-    // x = z - lambda L(p) on the tile, relaxation, momentum, squared error
+    // x = z - lambda L(p) on the tile, relaxation, momentum, squared error; every
+    // x_{i-1} load is issued before the first store (the stores could alias them)
     double e2 = 0.0;
+    float xpv[kWarpTvHV];
+#pragma unroll
+    for (int m = kWarpTvK + 1; m < kWarpTvK + 1 + kWarpTvHV; ++m) {
+        const int i = ib + m;
+        const long g = img + (long)i * n + j;
+        xpv[m - kWarpTvK - 1] = (a.y && lane_out && i < n) ? (a.xin ? a.xin[g] : a.xprev[g]) : 0.0f;
+    }
 #pragma unroll
     for (int m = kWarpTvK + 1; m < kWarpTvK + 1 + kWarpTvHV; ++m) {
         const float left = __shfl_up_sync(kAll, p2[m], 1);
@@ -457,10 +479,7 @@ __global__ void __launch_bounds__(32 * kWarpTvWarps) k_tv_warp(const WarpTvArgs 
             const float x = z[m] - lam * l;
             const float xi = (1.0f - t.alpha) * z[m] + t.alpha * x;
             const long g = img + (long)i * n + j;
-            if (a.y) {
-                const float xp = a.xin ? a.xin[g] : a.xprev[g];
-                a.y[g] = xi + a.amom * (xi - xp);
-            }
+            if (a.y) a.y[g] = xi + a.amom * (xi - xpv[m - kWarpTvK - 1]);
             a.xprev[g] = xi;
             if (a.xtrue) {
                 const double d = (double)xi - (double)__ldg(a.xtrue + g);

@@ -228,7 +228,7 @@ def test_launch_shapes_validation():
                 dict(back=(SC | 24, 0, 0, 0)), dict(lanes=(2, 0, 0, 0)),
                 dict(back=(BATCH(3) | 4, 0, 0, 0)), dict(back=(BATCH(16) | 32, 0, 0, 0)),
                 dict(back=(BATCH(16) | SC | 16, 0, 0, 0)), dict(back=(BATCH(4) | T4 | 33, 0, 0, 0)),
-                dict(tile=50), dict(tile=4), dict(tile=7)):
+                dict(tile=50), dict(tile=5), dict(tile=7)):
         with pytest.raises(pnp.PnpError):
             plan.set_launch_shapes(**bad)
     plan.set_launch_shapes(lanes=(8, 4, 0, 0), back=(16, T4 | 45, 3, SC | 22), tile=24)
