@@ -65,10 +65,10 @@ KERNEL_TRAFFIC = {
                 "end": "// ------------------------------------------------------------------ transpose A_s^T\n// Pixel-driven gather.",
                 "sha256": "2a6b15942b2a4ecf1af21a1cdd52adde7ee8a2332c4b56b8d25735b2d8c22694",
                  "profile": "profiles/k_forward_il_512x16_720x768.md"},
-    "denoise": {"bytes_per_unit": 142013440, "unit": "denoise (two launches)", "source": "tv.cu",
+    "denoise": {"bytes_per_unit": 140144640, "unit": "denoise (two launches)", "source": "tv.cu",
                 "begin": "// ------------------------------------------------------------------ register-resident FGP strips",
                 "end": "inline cudaError_t counted(cudaError_t e = cudaGetLastError())",
-                "sha256": "08066feaf92c520bee06bd03b0a373676928e1ef034434d4d611cbd326d3b308",
+                "sha256": "39d1893657f68b06bf042170418eccb97c590abba90c1577cf88378c5f96580b",
                  "profile": "profiles/k_tv_strip_512x16.md"},
 }
 
