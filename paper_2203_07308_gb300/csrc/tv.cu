@@ -25,6 +25,18 @@ namespace {
 
 __host__ __device__ inline int div_up(long a, long b) { return (int)((a + b - 1) / b); }
 
+// Scale of the isotropic projection onto the unit disc, min(1, 1/|a|), from
+// |a|^2: PTX rsqrt.approx with subnormal inputs flushed.  For normal inputs it
+// gives the bits rsqrtf gives (rsqrtf only adds a rescaling of subnormal
+// inputs); a subnormal or zero |a|^2 gives +inf where rsqrtf gives a value
+// above 2^63, and the min makes both 1.  NaN stays NaN in both, so the min is 1.
+__device__ __forceinline__ float proj_scale(float nrm2)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(nrm2));
+    return fminf(1.0f, r);
+}
+
 __global__ void k_tv_final(const float* __restrict__ z, const float* __restrict__ p, int have_p,
                            int n, long plane, float lambda, float alpha, float amom,
                            float* __restrict__ xprev, float* __restrict__ y,
@@ -208,7 +220,7 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
                 float pc = fmaf(g2, inv8l, r2[m]);
                 // projection onto the unit disc: scale min(1, 1/|a|) without a branch
                 const float nrm2 = fmaf(pa, pa, pc * pc);
-                const float sc = fminf(1.0f, rsqrtf(nrm2));
+                const float sc = proj_scale(nrm2);
                 pa *= sc;
                 pc *= sc;
                 r1[m] = fmaf(mo, pa - p1[m], pa);
@@ -433,7 +445,7 @@ __global__ void __launch_bounds__(32 * kWarpTvWarps) k_tv_warp(const WarpTvArgs 
             float pc = fmaf(g2, inv8l, r2[m]);
             // projection onto the unit disc: scale min(1, 1/|a|) without a branch
             const float nrm2 = fmaf(pa, pa, pc * pc);
-            const float sc = fminf(1.0f, rsqrtf(nrm2));
+            const float sc = proj_scale(nrm2);
             pa *= sc;
             pc *= sc;
             r1[m] = fmaf(mo, pa - p1[m], pa);
@@ -560,13 +572,16 @@ __global__ void __launch_bounds__(32 * W, W == 8 ? 2 : 1) k_tv_strip(const Strip
     float2* dn = up + W * 32;                                // [W][32]      x_tmp of each warp's first row
     const bool ina = ja >= 0 && ja < n, inb = jb >= 0 && jb < n;
     // the dual step's differences vanish outside rows / columns [0, n-2]
-    const float2 mcol = make_float2((ja >= 0 && ja < n - 1) ? 1.0f : 0.0f, (jb >= 0 && jb < n - 1) ? 1.0f : 0.0f);
-    float mrow[R];
+    // (as the step 1/(8 lambda) of the difference, or 0: the same bits as the
+    // difference times a 0/1 mask, then times 1/(8 lambda))
+    const float inv8l = 1.0f / (8.0f * t.lambda);
+    const float2 kcol = make_float2((ja >= 0 && ja < n - 1) ? inv8l : 0.0f, (jb >= 0 && jb < n - 1) ? inv8l : 0.0f);
+    float krow[R];
     float2 r1[R], r2[R], p1[R], p2[R];
 #pragma unroll
     for (int m = 0; m < R; ++m) {
         const int i = rb + m;
-        mrow[m] = (i >= 0 && i < n - 1) ? 1.0f : 0.0f;
+        krow[m] = (i >= 0 && i < n - 1) ? inv8l : 0.0f;
         const bool ri = i >= 0 && i < n;
         const long g = img + (long)i * n;
         float2 z = make_float2(0.0f, 0.0f);
@@ -590,8 +605,8 @@ __global__ void __launch_bounds__(32 * W, W == 8 ? 2 : 1) k_tv_strip(const Strip
     }
     up[w * 32 + lane] = r1[R - 1];
     __syncthreads();
-    const float lam = t.lambda, inv8l = 1.0f / (8.0f * t.lambda);
-    const float2 nlam2 = make_float2(-lam, -lam), inv8l2 = make_float2(inv8l, inv8l);
+    const float lam = t.lambda;
+    const float2 nlam2 = make_float2(-lam, -lam);
     const int wup = w > 0 ? w - 1 : 0, wdn = w + 1 < W ? w + 1 : w;
 #pragma unroll 2
     for (int k = 0; k < t.K; ++k) {
@@ -619,14 +634,12 @@ __global__ void __launch_bounds__(32 * W, W == 8 ? 2 : 1) k_tv_strip(const Strip
             for (int m = 0; m < R; ++m) {
                 const float2 down = m + 1 < R ? x[m + 1 < R ? m + 1 : m] : d;
                 const float2 right = make_float2(x[m].y, __shfl_down_sync(kAll, x[m].x, 1));
-                const float2 g1 = __fmul2_rn(sub2(x[m], down), make_float2(mrow[m], mrow[m]));
-                const float2 g2 = __fmul2_rn(sub2(x[m], right), mcol);
-                float2 pa = __ffma2_rn(g1, inv8l2, r1[m]);
-                float2 pc = __ffma2_rn(g2, inv8l2, r2[m]);
+                float2 pa = __ffma2_rn(sub2(x[m], down), make_float2(krow[m], krow[m]), r1[m]);
+                float2 pc = __ffma2_rn(sub2(x[m], right), kcol, r2[m]);
                 const float2 nrm2 = __ffma2_rn(pa, pa, __fmul2_rn(pc, pc));
                 // projection onto the unit disc without a branch: scale min(1, 1/|a|)
                 // (1 for |a| <= 1 up to the last bit of rsqrt at |a| = 1; inf at 0 gives 1)
-                const float2 sc = make_float2(fminf(1.0f, rsqrtf(nrm2.x)), fminf(1.0f, rsqrtf(nrm2.y)));
+                const float2 sc = make_float2(proj_scale(nrm2.x), proj_scale(nrm2.y));
                 pa = __fmul2_rn(pa, sc);
                 pc = __fmul2_rn(pc, sc);
                 r1[m] = __ffma2_rn(mo, sub2(pa, p1[m]), pa);
