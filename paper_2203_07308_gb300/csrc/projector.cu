@@ -240,22 +240,25 @@ __global__ void __launch_bounds__(32 * kFwdWarps, 4) k_forward(const FwdTable t)
         const int2 kr = __ldg(a.rayk + (long)v * a.n_det + j);
         const float4* __restrict__ img = a.quad + (long)inst * a.quad_stride;
         const int qw = a.qw;
+        // cell iy qw + ix as bits(Y + kMagic) qw + bits(X + kMagic) - bias (qw + 1)
+        // modulo 2^32, with ix = bits(X + kMagic) - bias (likewise iy)
         const int bias = kMagicBits - (qw - 3) / 2;   // column = round(X') + c0
-        float kf = (float)(kr.x + q) + 0.5f;
+        const unsigned cbias = (unsigned)bias * (unsigned)(qw + 1);
+        // sample k at F + (k + 1/2) step d, as k (step d) + (F + step d / 2)
+        const float sx = a.step * f.z, sy = a.step * f.w;
+        const float hx = fmaf(0.5f * a.step, f.z, f.x), hy = fmaf(0.5f * a.step, f.w, f.y);
+        float kf = (float)(kr.x + q);                 // sample indices below 2^24: exact
         const float dk = (float)Q;
-        const float step = a.step;
         float acc2 = 0.0f, acc3 = 0.0f, acc4 = 0.0f;
         auto smp = [&](float kk) {
-            const float tt = kk * step;
-            const float X = fmaf(tt, f.z, f.x);
-            const float Y = fmaf(tt, f.w, f.y);
+            const float X = fmaf(kk, sx, hx);
+            const float Y = fmaf(kk, sy, hy);
             const float mx = __fadd_rn(X, kMagic);
             const float my = __fadd_rn(Y, kMagic);
             const float u = __fsub_rn(X, __fsub_rn(mx, kMagic));
             const float w = __fsub_rn(Y, __fsub_rn(my, kMagic));
-            const int ix = __float_as_int(mx) - bias;
-            const int iy = __float_as_int(my) - bias;
-            const float4 cq = __ldg(img + iy * qw + ix);
+            const unsigned ci = (unsigned)__float_as_int(my) * (unsigned)qw + (unsigned)__float_as_int(mx) - cbias;
+            const float4 cq = __ldg(img + ci);
             return fmaf(w, fmaf(u, cq.w, cq.z), fmaf(u, cq.y, cq.x));
         };
         int k = kr.x + q;
@@ -321,8 +324,13 @@ __global__ void __launch_bounds__(32 * kFwdIlWarps) k_forward_il(const FwdTable 
     const int2 kr = __ldg(a.rayk + (long)v * a.n_det + j);
     const int B = a.batch, qw = a.qw;
     const int i0 = chunk * 8 * IPL + li;                     // this lane's first image
+    // cell iy qw + ix with ix = bits(X + kMagic) - bias (likewise iy), formed as
+    // bits(Y + kMagic) qw + bits(X + kMagic) - bias (qw + 1) modulo 2^32
     const int bias = kMagicBits - (qw - 3) / 2;             // column = round(X') + c0
-    const float step = a.step;
+    const unsigned cbias = (unsigned)bias * (unsigned)(qw + 1);
+    // sample k at F + (k + 1/2) step d, as k (step d) + (F + step d / 2)
+    const float sx = a.step * f.z, sy = a.step * f.w;
+    const float hx = fmaf(0.5f * a.step, f.z, f.x), hy = fmaf(0.5f * a.step, f.w, f.y);
     bool valid[IPL];
 #pragma unroll
     for (int q = 0; q < IPL; ++q) valid[q] = i0 + 8 * q < B;
@@ -330,17 +338,15 @@ __global__ void __launch_bounds__(32 * kFwdIlWarps) k_forward_il(const FwdTable 
 #pragma unroll
     for (int q = 0; q < IPL; ++q) acc[q] = 0.0f;
     const float4* __restrict__ img = a.quad + i0;
-    auto smp = [&](int k) {
-        const float tt = ((float)k + 0.5f) * step;
-        const float X = fmaf(tt, f.z, f.x);
-        const float Y = fmaf(tt, f.w, f.y);
+    auto smp = [&](float kf) {
+        const float X = fmaf(kf, sx, hx);
+        const float Y = fmaf(kf, sy, hy);
         const float mx = __fadd_rn(X, kMagic);
         const float my = __fadd_rn(Y, kMagic);
         const float u = __fsub_rn(X, __fsub_rn(mx, kMagic));
         const float w = __fsub_rn(Y, __fsub_rn(my, kMagic));
-        const int ix = __float_as_int(mx) - bias;
-        const int iy = __float_as_int(my) - bias;
-        const float4* cell = img + (long)(iy * qw + ix) * B;
+        const unsigned ci = (unsigned)__float_as_int(my) * (unsigned)qw + (unsigned)__float_as_int(mx) - cbias;
+        const float4* cell = img + (size_t)ci * (unsigned)B;
 #pragma unroll
         for (int q = 0; q < IPL; ++q) {
             if (!valid[q]) continue;
@@ -348,13 +354,14 @@ __global__ void __launch_bounds__(32 * kFwdIlWarps) k_forward_il(const FwdTable 
             acc[q] += fmaf(w, fmaf(u, cq.w, cq.z), fmaf(u, cq.y, cq.x));
         }
     };
-    int k = kr.x + sg;
+    float kf = (float)(kr.x + sg);
+    const float klast = (float)kr.y;                         // sample indices below 2^24: exact
 #pragma unroll 1
-    for (; k + 4 <= kr.y; k += 8) {
-        smp(k);
-        smp(k + 4);
+    for (; kf + 4.0f <= klast; kf += 8.0f) {
+        smp(kf);
+        smp(kf + 4.0f);
     }
-    if (k <= kr.y) smp(k);
+    if (kf <= klast) smp(kf);
 #pragma unroll
     for (int q = 0; q < IPL; ++q) {
         acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 8);
