@@ -591,9 +591,11 @@ __global__ void __launch_bounds__(kBackBatchThreads, 1) k_backward_batch(const B
     // image-interleaved residuals of a batch of a multiple of 4: the chunk's
     // residuals of a ray are contiguous and 16-byte aligned
     const bool vec = a.res_il && (a.batch & 3) == 0 && (BC & 3) == 0;
-    float acc[BC][4];
+    // accumulators of images (2h, 2h + 1) as FP32x2 pairs: each lane of a packed
+    // FMA rounds as the scalar FMA would
+    float2 acc2[BC / 2][4];
 #pragma unroll
-    for (int b = 0; b < BC; ++b) acc[b][0] = acc[b][1] = acc[b][2] = acc[b][3] = 0.0f;
+    for (int h = 0; h < BC / 2; ++h) acc2[h][0] = acc2[h][1] = acc2[h][2] = acc2[h][3] = make_float2(0.0f, 0.0f);
     if (inside) {
         const int ix = 2 * bx, iy = 2 * by;
         const float half = 0.5f * (float)(a.ns - 1);
@@ -668,12 +670,15 @@ __global__ void __launch_bounds__(kBackBatchThreads, 1) k_backward_batch(const B
                 } else {
                     for (int m = 0; m < min(cnt, nwin); ++m) sample((float)m);
                 }
+                const float2 v00 = make_float2(w00, w00), v10 = make_float2(w10, w10);
+                const float2 v01 = make_float2(w01, w01), v11 = make_float2(w11, w11);
 #pragma unroll
-                for (int b = 0; b < BC; ++b) {
-                    acc[b][0] = fmaf(w00, r[b], acc[b][0]);
-                    acc[b][1] = fmaf(w10, r[b], acc[b][1]);
-                    acc[b][2] = fmaf(w01, r[b], acc[b][2]);
-                    acc[b][3] = fmaf(w11, r[b], acc[b][3]);
+                for (int h = 0; h < BC / 2; ++h) {
+                    const float2 rr = make_float2(r[2 * h], r[2 * h + 1]);
+                    acc2[h][0] = __ffma2_rn(v00, rr, acc2[h][0]);
+                    acc2[h][1] = __ffma2_rn(v10, rr, acc2[h][1]);
+                    acc2[h][2] = __ffma2_rn(v01, rr, acc2[h][2]);
+                    acc2[h][3] = __ffma2_rn(v11, rr, acc2[h][3]);
                 }
             }
         }
@@ -691,7 +696,9 @@ __global__ void __launch_bounds__(kBackBatchThreads, 1) k_backward_batch(const B
 #pragma unroll
         for (int b = 0; b < BC; ++b)
             if (b >= b0 && b < b0 + RB)
-                part[(g * RB + (b - b0)) * kSlots + slot] = make_float4(acc[b][0], acc[b][1], acc[b][2], acc[b][3]);
+                part[(g * RB + (b - b0)) * kSlots + slot] =
+                    (b & 1) ? make_float4(acc2[b / 2][0].y, acc2[b / 2][1].y, acc2[b / 2][2].y, acc2[b / 2][3].y)
+                            : make_float4(acc2[b / 2][0].x, acc2[b / 2][1].x, acc2[b / 2][2].x, acc2[b / 2][3].x);
         __syncthreads();
         for (int idx = lt; idx < RB * kSlots; idx += nthr) {
             const int k = idx / kSlots, sl = idx - k * kSlots;

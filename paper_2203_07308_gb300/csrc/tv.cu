@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <vector>
 
 #include "pnp_internal.cuh"
@@ -545,6 +546,36 @@ struct StripTvArgs {
 // rounded as the scalar operation would be (a - b as an exact -1 * b + a).
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
 
+// L2 eviction priorities for the strips' state between their launches: the
+// first launch stores it evict-last (it is read back by the next launch while
+// the image-sized buffers of the other phases stream through L2), the next
+// launch reads it evict-first (dead after that read).  Cache hints only: the
+// values are untouched.
+__device__ __forceinline__ uint64_t l2_policy_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void st_hint(float4* a, float4 v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(a), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w), "l"(pol) : "memory");
+}
+__device__ __forceinline__ float4 ld_hint(const float4* a, uint64_t pol)
+{
+    float4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(a), "l"(pol));
+    return v;
+}
+
 template <bool LAST, int W>
 __global__ void __launch_bounds__(32 * W, W == 8 ? 2 : 1) k_tv_strip(const StripTvArgs t)   // W = 8, 12 or 16
 {
@@ -578,6 +609,7 @@ __global__ void __launch_bounds__(32 * W, W == 8 ? 2 : 1) k_tv_strip(const Strip
     const float2 kcol = make_float2((ja >= 0 && ja < n - 1) ? inv8l : 0.0f, (jb >= 0 && jb < n - 1) ? inv8l : 0.0f);
     float krow[R];
     float2 r1[R], r2[R], p1[R], p2[R];
+    const uint64_t polf = l2_policy_first();
 #pragma unroll
     for (int m = 0; m < R; ++m) {
         const int i = rb + m;
@@ -590,14 +622,14 @@ __global__ void __launch_bounds__(32 * W, W == 8 ? 2 : 1) k_tv_strip(const Strip
         if (ri && ina) {
             z.x = __ldg(a.z + g + ja);
             if (!t.first) {
-                const float4 q = __ldg(sin4 + g + ja);
+                const float4 q = ld_hint(sin4 + g + ja, polf);
                 r1[m].x = q.x; r2[m].x = q.y; p1[m].x = q.z; p2[m].x = q.w;
             }
         }
         if (ri && inb) {
             z.y = __ldg(a.z + g + jb);
             if (!t.first) {
-                const float4 q = __ldg(sin4 + g + jb);
+                const float4 q = ld_hint(sin4 + g + jb, polf);
                 r1[m].y = q.x; r2[m].y = q.y; p1[m].y = q.z; p2[m].y = q.w;
             }
         }
@@ -654,14 +686,15 @@ __global__ void __launch_bounds__(32 * W, W == 8 ? 2 : 1) k_tv_strip(const Strip
     // output pixels of this thread: rows [r0, r0 + HO), columns [c0, c0 + WO), inside the image
     const bool oa = ina && ja >= c0 && ja < c0 + kStripWO, ob = inb && jb >= c0 && jb < c0 + kStripWO;
     if constexpr (!LAST) {
+        const uint64_t pol = l2_policy_last();
 #pragma unroll
         for (int m = 0; m < R; ++m) {
             const int i = rb + m;
             if (i < r0 || i >= r0 + HO || i >= n) continue;
             const long g = img + (long)i * n;
             float4* sout4 = reinterpret_cast<float4*>(a.sout);
-            if (oa) sout4[g + ja] = make_float4(r1[m].x, r2[m].x, p1[m].x, p2[m].x);
-            if (ob) sout4[g + jb] = make_float4(r1[m].y, r2[m].y, p1[m].y, p2[m].y);
+            if (oa) st_hint(sout4 + g + ja, make_float4(r1[m].x, r2[m].x, p1[m].x, p2[m].x), pol);
+            if (ob) st_hint(sout4 + g + jb, make_float4(r1[m].y, r2[m].y, p1[m].y, p2[m].y), pol);
         }
     } else {
         // x = z - lambda L(p), relaxation, momentum, squared error.  All of this
