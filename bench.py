@@ -53,22 +53,22 @@ FLOP_PER_PIXEL_ITER = 24
 # while the kernel's source is the one that was measured (else null).  Units: one
 # launch of the projector kernels (the forward's figure weighted over the
 # schedule's 24 / 24 / 72 launches at the 4x / 2x / full levels, whose captured
-# launches read 8.3 / 21.0 / 79.9 MB), one denoise (two launches) of the FGP strips.
+# launches move 8.3 / 21.0 / 81.0 MB), one denoise (two launches) of the FGP strips.
 KERNEL_TRAFFIC = {
-    "backward": {"bytes_per_unit": 20122581, "unit": "launch", "source": "projector.cu",
+    "backward": {"bytes_per_unit": 20120269, "unit": "launch", "source": "projector.cu",
                  "begin": "struct BackTable {",
                  "end": "// ------------------------------------------------------------------ transpose A_s^T, scatter form",
-                 "sha256": "d41b2c67aba3a5c6bfe7404ffd4f7dbf6b10ddf6f3e76050350d7e87f268399e",
+                 "sha256": "c78e03f76b65ec7b86043f9c728828bf485de3e0a29827b0539a41bab277aa7a",
                  "profile": "profiles/k_backward_batch_512x16_720x768.md"},
-    "forward": {"bytes_per_unit": 53812000, "unit": "launch", "source": "projector.cu",
+    "forward": {"bytes_per_unit": 54460877, "unit": "launch", "source": "projector.cu",
                 "begin": "// Forward projector on an image-interleaved coefficient image.",
                 "end": "// ------------------------------------------------------------------ transpose A_s^T\n// Pixel-driven gather.",
-                "sha256": "2a6b15942b2a4ecf1af21a1cdd52adde7ee8a2332c4b56b8d25735b2d8c22694",
+                "sha256": "48a6d7dd0e06e12f651b61a42423c8e59049ddfde0467d0f3adfa9370c92816f",
                  "profile": "profiles/k_forward_il_512x16_720x768.md"},
-    "denoise": {"bytes_per_unit": 140144640, "unit": "denoise (two launches)", "source": "tv.cu",
+    "denoise": {"bytes_per_unit": 125760512, "unit": "denoise (two launches)", "source": "tv.cu",
                 "begin": "// ------------------------------------------------------------------ register-resident FGP strips",
                 "end": "inline cudaError_t counted(cudaError_t e = cudaGetLastError())",
-                "sha256": "39d1893657f68b06bf042170418eccb97c590abba90c1577cf88378c5f96580b",
+                "sha256": "9fda072952e44442802b8c27f4cdf61bbf81576b0140ae96a9742ee2ab19a05f",
                  "profile": "profiles/k_tv_strip_512x16.md"},
 }
 
