@@ -293,9 +293,9 @@ __global__ void __launch_bounds__(32 * kFwdWarps, 4) k_forward(const FwdTable t)
 // so the position and cell of a sample are computed once for 8 IPL images and
 // each load instruction reads whole 128-byte lines (8 images' cells), 4
 // consecutive samples at a time; the four sample groups are joined in a fixed
-// order.  A CTA (8 warps) takes 8 adjacent bins of one view, CTAs numbered from
+// order.  A CTA (4 warps) takes 4 adjacent bins of one view, CTAs numbered from
 // the detector's centre outwards as in k_forward.
-constexpr int kFwdIlWarps = 8;
+constexpr int kFwdIlWarps = 4;
 
 template <int IPL>
 __global__ void __launch_bounds__(32 * kFwdIlWarps) k_forward_il(const FwdTable t)
