@@ -528,14 +528,15 @@ def gray_by_config(dev, stream):
 
 def single_256(dev, stream, args):
     """The single-image 256^2 / 360 x 512 workload (2x sketch for 20 iterations,
-    then the full grid for 80, 8 subsets): gradient estimates per second of the
-    whole schedule and time-to-PSNR against full-gradient PnP-FISTA."""
+    then the full grid for 80, 8 subsets), with the stored gather table
+    registered: gradient estimates per second of the whole schedule and
+    time-to-PSNR against full-gradient PnP-FISTA."""
     import torch
     import paper_2203_07308_gb300 as pnp
     from paper_2203_07308_gb300 import synth
     wl = synth.workloads()["c2_256"]
     g = wl.geom
-    plan = pnp.Plan(g)
+    plan = pnp.Plan(g, gather_table=True)          # the autotuner also times the stored-table gather
     d_xt, d_b = _simulate(plan, wl, dev)
     kw = dict(alpha=wl.alpha, lam=wl.tv_lambda, tv_iters=wl.tv_iters, momentum=wl.momentum)
     plan.autotune(wl.stages, **kw)
@@ -559,7 +560,7 @@ def single_256(dev, stream, args):
     tts_f, it_f = _time_to_target(plan, full, eta_full, None, d_b, d_x, log_f, target, kw, stream)
     return {"workload": "256x256, 360 views x 512 bins, 2x (20 it) then full grid (80 it), 8 subsets",
             "ms_per_run": float(np.mean(ms)), "gradient_estimates_per_s": total / (float(np.mean(ms)) / 1000.0),
-            "launch_shapes": plan.launch_shapes(),
+            "launch_shapes": plan.launch_shapes(), "gather_table_bytes": int(plan.table.numel()),
             "time_to_psnr": {"target_db": target, "sketched_ms": tts_s, "sketched_iters": it_s,
                              "full_ms": tts_f, "full_iters": it_f,
                              "speedup": (tts_f / tts_s) if (tts_s and tts_f) else None}}

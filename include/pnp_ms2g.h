@@ -344,10 +344,16 @@ int pnp_run_many(const pnp_problem* problems, int n_problems, const pnp_run_para
  * ray can reach into NaN.  pnp_autotune sets the
  * shapes, choosing among the gather's shapes only (the scatter's error depends
  * on the data, so it runs only where pnp_set_launch_shapes pins it);
- * pnp_set_launch_shapes pins them (PNP_EINVAL for a shape outside these sets). */
+ * pnp_set_launch_shapes pins them (PNP_EINVAL for a shape outside these sets).
+ * PNP_BACK_TABLE | PNP_BACK_BATCH(BC) | G (G 1..16, BC in {2, 4, 8, 16}; 0 counts
+ * as 2) reads the stored gather table of pnp_set_gather_table instead of
+ * evaluating the hats: CTAs of 32 blocks x G view groups, bitwise the sums of
+ * the gather with the same G; without a registered table it runs as that
+ * gather (batched for BC >= 4). */
 #define PNP_BACK_TILE4 (1 << 8)
 #define PNP_BACK_SCATTER (1 << 9)
 #define PNP_BACK_BATCH(bc) ((bc) << 16)
+#define PNP_BACK_TABLE (1 << 10)
 typedef struct {
     int32_t lanes[4];
     int32_t back[4];
@@ -355,6 +361,29 @@ typedef struct {
 } pnp_launch_shapes;
 int pnp_get_launch_shapes(const pnp_geom* g, pnp_launch_shapes* out, void* d_ws);
 int pnp_set_launch_shapes(const pnp_geom* g, const pnp_launch_shapes* in, void* d_ws);
+
+/* Stored gather table of A_s^T (Eq. 5's transpose, with the weights of the
+ * pixel-driven gather): the gather's weights depend on the geometry alone, so
+ * they can be computed once per geometry and read back from HBM instead of
+ * being re-evaluated in every backprojection.  For every sketch level present
+ * in the workspace, every view and 2x2 pixel block: the bins of the rays that
+ * meet the block's support (in increasing order) and the four summed hat
+ * products of each, in groups of 32 blocks stored slot by slot (a group takes
+ * as many slots as its block with the most rays).  About 2.3 entries of 20 B
+ * per block and view: 2.6 GB for the full grid of 512^2 / 720 x 768, 3.4 GB for
+ * all its levels.
+ * pnp_gather_table_size: bytes the table of d_ws's geometry needs (runs the
+ *   counting kernel on the workspace's ray tables; overwrites the workspace's
+ *   denoiser state buffers; synchronous).
+ * pnp_set_gather_table: builds the table into d_table (caller-owned, at least
+ *   that many bytes, 256-byte aligned; PNP_EINVAL otherwise) and registers it
+ *   with d_ws, so that launch shapes with PNP_BACK_TABLE (and pnp_autotune,
+ *   which then times them) use it; d_table == NULL unregisters.  The caller
+ *   keeps the buffer alive while the workspace uses it; pnp_setup on the
+ *   workspace drops the registration.  Synchronous.  Library instrumentation
+ *   of the path, no counterpart in the paper (which evaluates A^T matrix-free). */
+int pnp_gather_table_size(const pnp_geom* g, void* d_ws, size_t* bytes, void* stream);
+int pnp_set_gather_table(const pnp_geom* g, void* d_table, size_t bytes, void* d_ws, void* stream);
 
 /* Times the launch shapes of this geometry's kernels on d_ws's own buffers
  * (forward lanes per ray 4/8/16 and the gather backprojector's view groups for each

@@ -48,6 +48,12 @@ class LaunchShapes(C.Structure):
 
 BACK_TILE4 = 1 << 8     # backprojector CTAs of 4 x 4 pixel blocks (| view groups)
 BACK_SCATTER = 1 << 9   # backprojector as the fixed-point scatter (| tile side 12, 16, 22 or 32)
+BACK_TABLE = 1 << 10    # backprojector reading the stored gather table (| BACK_BATCH(bc) | view groups)
+
+
+def BACK_BATCH(bc):
+    """Images per thread of the batched and table gathers (PNP_BACK_BATCH)."""
+    return int(bc) << 16
 
 SKETCH_POOL, SKETCH_BICUBIC = 0, 1
 EST_MINIBATCH, EST_SVRG, EST_SAGA = 0, 1, 2
@@ -122,6 +128,8 @@ def load(path: Optional[str] = None):
             "pnp_get_launch_shapes": [gp, C.POINTER(LaunchShapes), vp],
             "pnp_set_launch_shapes": [gp, C.POINTER(LaunchShapes), vp],
             "pnp_set_vr_buffer": [gp, vp, sz, vp],
+            "pnp_gather_table_size": [gp, vp, C.POINTER(sz), vp],
+            "pnp_set_gather_table": [gp, vp, sz, vp, vp],
             "pnp_upsample_kind": [gp, i32, i32, vp, vp, vp],
             "pnp_sketch_grad_kind": [gp, i32, i32, vp, vp, vp, i32, i32, vp, vp],
             "pnp_power_iter_kind": [gp, i32, i32, i32, C.c_double, dp, C.POINTER(i32), vp, vp],
@@ -406,12 +414,35 @@ def last_error() -> str:
 class Plan:
     """A geometry with its device workspace allocated (by PyTorch) and prepared."""
 
-    def __init__(self, g, device="cuda", stream=None):
+    def __init__(self, g, device="cuda", stream=None, gather_table=False):
         import torch
         self.g = g
         self.cg = geom(g)
         self.ws = torch.empty(workspace_size(g), dtype=torch.uint8, device=device)
         setup(g, self.ws, stream)
+        self.table = None
+        if gather_table:
+            self.set_gather_table(stream=stream)
+
+    def gather_table_size(self, stream=None) -> int:
+        """Bytes of the stored gather table of this geometry (pnp_gather_table_size)."""
+        n = C.c_size_t(0)
+        _check(load().pnp_gather_table_size(C.byref(self.cg), _ws(self.ws)[0], C.byref(n), _stream(stream)))
+        return int(n.value)
+
+    def set_gather_table(self, enable=True, stream=None):
+        """Allocates (PyTorch), builds and registers the stored gather table, or
+        unregisters and frees it (enable=False)."""
+        import torch
+        if not enable:
+            _check(load().pnp_set_gather_table(C.byref(self.cg), None, 0, _ws(self.ws)[0], _stream(stream)))
+            self.table = None
+            return
+        n = self.gather_table_size(stream)
+        buf = torch.empty(max(n, 256), dtype=torch.uint8, device=self.ws.device)
+        _check(load().pnp_set_gather_table(C.byref(self.cg), C.c_void_p(buf.data_ptr()), buf.numel(),
+                                           _ws(self.ws)[0], _stream(stream)))
+        self.table = buf
 
     def project(self, factor, img, sino, b=None, subset=0, n_subsets=1, stream=None):
         project(self.g, factor, img, sino, b, subset, n_subsets, self.ws, stream)

@@ -179,10 +179,20 @@ struct LCache {
     bool valid[kMaxLevels][2] = {};
 };
 
+// Stored gather table registered with pnp_set_gather_table: per level, byte offsets
+// of the header, weights and bins in the caller's buffer.
+struct GatherTab {
+    char* base = nullptr;
+    size_t bytes = 0;
+    size_t off_hdr[kMaxLevels] = {}, off_w[kMaxLevels] = {}, off_ray[kMaxLevels] = {};
+    bool present[kMaxLevels] = {};
+};
+
 struct RegEntry {
     const void* ws; uint64_t fp; size_t bytes; Tuned tuned; const float* weights;
     void* vr = nullptr; size_t vr_bytes = 0;     // estimator-state buffer (SVRG / SAGA)
     LCache lc;
+    GatherTab tab;
 };
 std::mutex g_reg_mu;
 std::vector<RegEntry> g_reg;
@@ -194,6 +204,7 @@ void reg_put(const void* ws, uint64_t fp, size_t bytes)
         if (e.ws == ws) {
             e.fp = fp; e.bytes = bytes; e.tuned = Tuned(); e.weights = nullptr; e.vr = nullptr; e.vr_bytes = 0;
             e.lc = LCache();
+            e.tab = GatherTab();
             return;
         }
     if (g_reg.size() >= 4096) g_reg.erase(g_reg.begin());
@@ -293,6 +304,21 @@ void reg_put_L(const void* ws, int li, int kind, double L)
             e.lc.L[li][kind] = L;
             e.lc.valid[li][kind] = true;
         }
+}
+
+GatherTab reg_table(const void* ws)
+{
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    for (const auto& e : g_reg)
+        if (e.ws == ws) return e.tab;
+    return GatherTab();
+}
+
+void reg_set_table(const void* ws, const GatherTab& t)
+{
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    for (auto& e : g_reg)
+        if (e.ws == ws) e.tab = t;
 }
 
 void reg_set_tuned(const void* ws, const Tuned& t)
@@ -417,6 +443,13 @@ BackArgs back_args(const pnp_geom& g, const LevelLayout& lv, char* ws, int p, in
     a.y = y;
     a.eta = eta;
     a.out = out;
+    const int li = level_index(lv.factor);
+    const GatherTab tb = reg_table(ws);
+    if (li >= 0 && tb.present[li]) {
+        a.thdr = (const int2*)(tb.base + tb.off_hdr[li]);
+        a.tw = (const float4*)(tb.base + tb.off_w[li]);
+        a.tray = (const int*)(tb.base + tb.off_ray[li]);
+    }
     return a;
 }
 
@@ -648,6 +681,93 @@ int pnp_kernel_times(double* h_ms, int64_t* h_launches, int reset)
             g_timer.launches[k] = 0;
         }
     }
+    return PNP_OK;
+}
+
+// Sizes (tab == nullptr) or builds (tab != nullptr) the stored gather table of
+// every level of the layout: per level, slot counts of each (view, block group)
+// from the count kernel, a host prefix sum into the header, then the entries.
+// The counts go through the workspace's TV state planes, in chunks of views.
+static int gather_table(const pnp_geom& g, const Layout& L, char* ws, char* tab, size_t tab_bytes, size_t* need,
+                 GatherTab* out, cudaStream_t st)
+{
+    size_t off = 0;
+    int* wd = (int*)(ws + L.off_tv);
+    const size_t wd_ints = (size_t)8 * g.batch * g.n * g.n;
+    for (int li = 0; li < kMaxLevels; ++li) {
+        const LevelLayout& lv = L.lv[li];
+        if (lv.factor == 0) continue;
+        BackArgs a = back_args(g, lv, ws, 0, 1, nullptr, kBackRaw, 1.0f, nullptr, 0.0f, nullptr, 1);
+        const int groups = table_groups(lv.ns);
+        const size_t nh = (size_t)g.n_views * groups;
+        const int vchunk = (int)std::max<size_t>(1, std::min<size_t>(g.n_views, wd_ints / groups));
+        std::vector<int> widths(nh);
+        for (int v0 = 0; v0 < g.n_views; v0 += vchunk) {
+            const int nv = std::min(vchunk, g.n_views - v0);
+            BackArgs av = a;
+            av.rayf = a.rayf + (size_t)v0 * g.n_det;
+            av.view = a.view + v0;
+            PNP_CUDA(launch_table_count(av, nv, wd, st));
+            PNP_CUDA(cudaMemcpyAsync(widths.data() + (size_t)v0 * groups, wd, (size_t)nv * groups * sizeof(int),
+                                     cudaMemcpyDeviceToHost, st));
+            PNP_CUDA(cudaStreamSynchronize(st));
+        }
+        std::vector<int2> hdr(nh);
+        long slots = 0;
+        for (size_t i = 0; i < nh; ++i) {
+            if (slots > (long)INT32_MAX - widths[i]) return fail(PNP_EINVAL, "gather table exceeds 2^31 slots");
+            hdr[i] = make_int2((int)slots, widths[i]);
+            slots += widths[i];
+        }
+        const size_t oh = off;
+        off = align_up(off + nh * sizeof(int2));
+        const size_t ow = off;
+        off = align_up(off + (size_t)slots * 32 * sizeof(float4));
+        const size_t orr = off;
+        off = align_up(off + (size_t)slots * 32 * sizeof(int));
+        if (!tab) continue;
+        if (off > tab_bytes) return fail(PNP_EINVAL, "gather table buffer of %zu bytes is too small", tab_bytes);
+        PNP_CUDA(cudaMemcpyAsync(tab + oh, hdr.data(), nh * sizeof(int2), cudaMemcpyHostToDevice, st));
+        PNP_CUDA(launch_table_fill(a, g.n_views, (const int2*)(tab + oh), (float4*)(tab + ow), (int*)(tab + orr), st));
+        PNP_CUDA(cudaStreamSynchronize(st));
+        out->off_hdr[li] = oh;
+        out->off_w[li] = ow;
+        out->off_ray[li] = orr;
+        out->present[li] = true;
+    }
+    *need = off;
+    return PNP_OK;
+}
+
+int pnp_gather_table_size(const pnp_geom* g, void* d_ws, size_t* bytes, void* stream)
+{
+    t_err.clear();
+    if (int e = validate_geom(g)) return e;
+    if (!bytes) return fail(PNP_EINVAL, "bytes pointer is NULL");
+    if (int e = check_ws(*g, d_ws)) return e;
+    const Layout L = make_layout(*g);
+    GatherTab tb;
+    return gather_table(*g, L, (char*)d_ws, nullptr, 0, bytes, &tb, S(stream));
+}
+
+int pnp_set_gather_table(const pnp_geom* g, void* d_table, size_t bytes, void* d_ws, void* stream)
+{
+    t_err.clear();
+    if (int e = validate_geom(g)) return e;
+    if (int e = check_ws(*g, d_ws)) return e;
+    if (!d_table) {
+        reg_set_table(d_ws, GatherTab());
+        return PNP_OK;
+    }
+    if (reinterpret_cast<uintptr_t>(d_table) % 256) return fail(PNP_EINVAL, "gather table buffer not 256-byte aligned");
+    reg_set_table(d_ws, GatherTab());            // the gather stays on the hats while the table is rebuilt
+    const Layout L = make_layout(*g);
+    GatherTab tb;
+    tb.base = (char*)d_table;
+    tb.bytes = bytes;
+    size_t need = 0;
+    if (int e = gather_table(*g, L, (char*)d_ws, (char*)d_table, bytes, &need, &tb, S(stream))) return e;
+    reg_set_table(d_ws, tb);
     return PNP_OK;
 }
 
@@ -1492,6 +1612,14 @@ int pnp_autotune(const pnp_geom* g, const pnp_stage* stages, int n_stages, const
             for (int G : {2, 4, 8, 16})
                 if (G <= nsub) shapes.push_back(PNP_BACK_BATCH(BC) | G);
         }
+        // the stored gather table, when one is registered
+        if (ba.thdr) {
+            for (int bc : {16, 8, 4}) {
+                if (bc > g->batch && bc != 4) continue;     // (one to three images: 4 per thread)
+                for (int G : {2, 4, 8, 16})
+                    if (G <= nsub) shapes.push_back(PNP_BACK_TABLE | PNP_BACK_BATCH(bc) | G);
+            }
+        }
         // (the fixed-point scatter is not a candidate: its error depends on the
         // residual's dynamic range; it runs only where pnp_set_launch_shapes pins it)
         for (int shp : shapes) {
@@ -1581,7 +1709,9 @@ int pnp_set_launch_shapes(const pnp_geom* g, const pnp_launch_shapes* in, void* 
         const bool scatter = (b & ~0xff) == PNP_BACK_SCATTER && (bg == 12 || bg == 16 || bg == 22 || bg == 32);
         const int slots = (b & PNP_BACK_TILE4) ? 16 : 32;
         const bool batch_ok = bc == 0 || bc == 1 || ((bc == 4 || bc == 8 || bc == 16) && bg * slots <= 512);
-        const bool ok = b == 0 || scatter ||
+        const bool table = (b & ~(0xff | PNP_BACK_BATCH(0xff))) == PNP_BACK_TABLE && bg >= 1 && bg <= 16 &&
+                           (bc == 0 || bc == 2 || bc == 4 || bc == 8 || bc == 16);
+        const bool ok = b == 0 || scatter || table ||
                         ((b & ~(PNP_BACK_TILE4 | 0xff | PNP_BACK_BATCH(0xff))) == 0 && bg >= 1 &&
                          bg <= ((b & PNP_BACK_TILE4) ? 64 : 32) && batch_ok);
         if (!ok) return fail(PNP_EINVAL, "back[%d] = %#x is not a backprojector shape", k, b);

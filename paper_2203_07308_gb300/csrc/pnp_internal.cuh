@@ -179,6 +179,9 @@ struct BackArgs {
     float cmax = 0.0f;               // bound on the (ray, sample) terms one pixel receives from one
                                      // view (scatter form; 0: scatter unavailable, gather used)
     int res_il = 0;                  // 1: image-interleaved residual (written with FwdArgs::out_il)
+    // stored gather table of this level (all views; null: none): hdr [n_views][groups] of
+    // (first slot, slots), weights [slots][32], bins [slots][32]; groups = table_groups(ns)
+    const int2* thdr = nullptr; const float4* tw = nullptr; const int* tray = nullptr;
 };
 // Residual strides: element (image, view row, bin) at image * is + (row * n_det + bin) * js.
 __host__ __device__ inline long res_is(const BackArgs& a) { return a.res_il ? 1L : (long)a.n_sub * a.n_det; }
@@ -188,9 +191,25 @@ __host__ __device__ inline int res_js(const BackArgs& a) { return a.res_il ? a.b
 // fixed-point scatter form on TS x TS tiles (TS in {12, 16, 22, 32}).
 // PNP_BACK_BATCH(BC) | (gather shape) selects the batched gather (BC images per
 // thread, BC in {4, 8, 16}; at most 512 threads per CTA).
+// PNP_BACK_TABLE | PNP_BACK_BATCH(BC) | G reads the stored gather table (every
+// class must have one; BC in {2, 4, 8, 16}, 2 when BC < 2) with G view groups.
 inline int back_batch_of(int groups) { return (groups >> 16) & 0xff; }
 cudaError_t launch_backward(const BackArgs& a, cudaStream_t st, int groups = 0);
 cudaError_t launch_backward_multi(const BackArgs* items, int count, cudaStream_t st, int groups = 0);
+// Gather table construction for one level (a: the level's ray tables; all n_views views):
+// widths[view][group] = slots of each (view, group of 32 blocks), then the entries.
+// groups of 32 blocks = tiles of 8 x 4 blocks (16 x 8 pixels), row-major; lane l of
+// group k is the block (8 (k % tiles_x) + l % 8, 4 (k / tiles_x) + l / 8)
+__host__ __device__ inline int table_groups(int ns) { const int nb = (ns + 1) / 2; return ((nb + 7) / 8) * ((nb + 3) / 4); }
+__host__ __device__ inline void table_block(int ns, int k, int lane, int& bx, int& by)
+{
+    const int nb = (ns + 1) / 2, tx = (nb + 7) / 8;
+    bx = 8 * (k % tx) + (lane & 7);
+    by = 4 * (k / tx) + (lane >> 3);
+}
+cudaError_t launch_table_count(const BackArgs& a, int n_views, int* widths, cudaStream_t st);
+cudaError_t launch_table_fill(const BackArgs& a, int n_views, const int2* hdr, float4* tw, int* tray,
+                              cudaStream_t st);
 
 cudaError_t launch_pool(const float* fine, float* coarse, int n, int s, int batch, cudaStream_t st);
 // Bicubic sketch (kind PNP_SKETCH_BICUBIC) and its adjoint: out = base - eta scale S^T g,

@@ -733,6 +733,287 @@ __global__ void __launch_bounds__(kBackBatchThreads, 1) k_backward_batch(const B
     }
 }
 
+// ------------------------------------------------------------------ transpose A_s^T from a stored table
+// The gather's weights depend on the geometry only, so they can be computed once
+// and stored: for every (view, 2x2 block) the bins of the rays that meet the
+// block's support (ascending) and the four summed hat products of each, exactly
+// as k_backward2x2 / k_backward_batch form them.  Blocks go in groups of 32 (tiles
+// of 8 x 4 blocks, whose rays stay close together); the entries of a (view,
+// group) are sliced-ELL: slot s
+// of the group holds entry s of each of its 32 blocks, so a warp reads one
+// slot as 32 consecutive float4 (weights) and 32 ints (bins, -1 past a block's
+// own entries), and a group takes as many slots as its block with the most rays.
+// Layout per level: hdr int2 [n_views][groups] (first slot, slots), weights
+// float4 [slots][32], bins int [slots][32].  The gather then streams the table
+// from HBM instead of evaluating the hats (about 2.3 entries of 20 B per block
+// and view at 512^2 / 720 x 768); with the same view-group count G its sums are
+// the bits of the two gathers (same weights, same view and ray order, same
+// fixed-order sum over the view groups).
+
+// per-view candidate bins of the block at (bx, by): the conservative shadow of its support
+struct GatherFrame {
+    float cx, cy, px, py, jc, inv_step, rho;
+    int nwin;
+};
+
+template <int NWIN>
+__device__ __forceinline__ GatherFrame gather_frame(const BackArgs& a, int bx, int by)
+{
+    GatherFrame f;
+    const int ix = 2 * bx, iy = 2 * by;
+    const float half = 0.5f * (float)(a.ns - 1);
+    f.cx = (float)ix + 0.5f - half;
+    f.cy = (float)iy + 0.5f - half;
+    const int c0 = a.ns / 2;
+    f.px = (float)(ix - c0) + 2.0f;
+    f.py = (float)(iy - c0) + 2.0f;
+    f.jc = 0.5f * (float)(a.n_det - 1);
+    f.inv_step = 1.0f / a.step;
+    f.rho = 2.12132034f;
+    f.nwin = NWIN > 0 ? NWIN : (int)floorf(2.0f * f.rho * f.inv_step) + 1;
+    return f;
+}
+
+__device__ __forceinline__ void gather_bins(const BackArgs& a, const GatherFrame& fr, int v, int& jlo, int& jhi)
+{
+    const float4 vp = __ldg(a.view + v);
+    const float along = fr.cx * vp.x + fr.cy * vp.y;
+    const float lat = fr.cy * vp.x - fr.cx * vp.y;
+    const float inv = __fdividef(1.0f, vp.z - along);
+    const float uj = vp.w * lat * inv + fr.jc;
+    const float invp = inv * (1.0f + 2.0f * fr.rho * inv);
+    const float T = (fabsf(lat) + fr.rho) * invp;
+    const float hw = fr.rho * vp.w * fmaf(T, T, 1.0f) * invp * 1.01f + 0.02f;
+    jlo = max(0, (int)ceilf(uj - hw));
+    jhi = min(a.n_det - 1, (int)floorf(uj + hw));
+}
+
+// the four summed hat products of ray f on the block; false when the ray misses its support
+template <int NWIN>
+__device__ __forceinline__ bool gather_weights(const BackArgs& a, const GatherFrame& fr, const float4 f, float4& wq)
+{
+    const float ax = fr.px - f.x, ay = fr.py - f.y;
+    const float e = ax * f.w - ay * f.z;
+    const float hwid = 1.5f * (fabsf(f.z) + fabsf(f.w));
+    if (fabsf(e) >= hwid) return false;
+    const float tau = fmaf(ax, f.z, ay * f.w);
+    const float k0 = ceilf(fmaf(tau - hwid, fr.inv_step, -0.5f));
+    const int cnt = (int)(2.0f * hwid * fr.inv_step) + 1;
+    const float t0 = (k0 + 0.5f) * a.step;
+    const float X0 = fmaf(t0, f.z, -ax), Y0 = fmaf(t0, f.w, -ay);
+    const float xa0 = X0 + 0.5f, xb0 = X0 - 0.5f;
+    const float ya0 = Y0 + 0.5f, yb0 = Y0 - 0.5f;
+    const float sx = a.step * f.z, sy = a.step * f.w;
+    float w00 = 0.0f, w10 = 0.0f, w01 = 0.0f, w11 = 0.0f;
+    auto sample = [&](float fm) {
+        const float hxa = __saturatef(1.0f - fabsf(fmaf(fm, sx, xa0)));
+        const float hxb = __saturatef(1.0f - fabsf(fmaf(fm, sx, xb0)));
+        const float hya = __saturatef(1.0f - fabsf(fmaf(fm, sy, ya0)));
+        const float hyb = __saturatef(1.0f - fabsf(fmaf(fm, sy, yb0)));
+        w00 = fmaf(hxa, hya, w00);
+        w10 = fmaf(hxb, hya, w10);
+        w01 = fmaf(hxa, hyb, w01);
+        w11 = fmaf(hxb, hyb, w11);
+    };
+    if (NWIN > 0) {
+#pragma unroll
+        for (int m = 0; m < (NWIN > 2 ? NWIN - 2 : 1); ++m) sample((float)m);
+        if (cnt > NWIN - 2) sample((float)(NWIN - 2));
+        if (cnt > NWIN - 1) sample((float)(NWIN - 1));
+    } else {
+        for (int m = 0; m < min(cnt, fr.nwin); ++m) sample((float)m);
+    }
+    wq = make_float4(w00, w10, w01, w11);
+    return true;
+}
+
+// one warp per (view, group of 32 blocks): the group's slot count (its largest entry count)
+__global__ void __launch_bounds__(256) k_table_count(const BackArgs a, int n_views, int* widths)
+{
+    const int nb = (a.ns + 1) / 2, groups = table_groups(a.ns);
+    const long wid = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= (long)n_views * groups) return;                // whole warps
+    const int v = (int)(wid / groups), k = (int)(wid - (long)v * groups);
+    int bx, by;
+    table_block(a.ns, k, lane, bx, by);
+    int cnt = 0;
+    if (bx < nb && by < nb) {
+        const GatherFrame fr = gather_frame<0>(a, bx, by);
+        int jlo, jhi;
+        gather_bins(a, fr, v, jlo, jhi);
+        const long base = (long)v * a.n_det;
+        for (int j = jlo; j <= jhi; ++j) {
+            const float4 f = __ldg(a.rayf + base + j);
+            const float ax = fr.px - f.x, ay = fr.py - f.y;
+            const float e = ax * f.w - ay * f.z;
+            const float hwid = 1.5f * (fabsf(f.z) + fabsf(f.w));
+            if (fabsf(e) < hwid) ++cnt;
+        }
+    }
+    cnt = __reduce_max_sync(0xffffffffu, cnt);
+    if (lane == 0) widths[wid] = cnt;
+}
+
+template <int NWIN>
+__global__ void __launch_bounds__(256) k_table_fill(const BackArgs a, int n_views, const int2* __restrict__ hdr,
+                                                     float4* __restrict__ tw, int* __restrict__ tray)
+{
+    const int nb = (a.ns + 1) / 2, groups = table_groups(a.ns);
+    const long wid = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= (long)n_views * groups) return;                // whole warps
+    const int v = (int)(wid / groups), k = (int)(wid - (long)v * groups);
+    int bx, by;
+    table_block(a.ns, k, lane, bx, by);
+    const int2 h = hdr[wid];
+    int s = 0;
+    if (bx < nb && by < nb) {
+        const GatherFrame fr = gather_frame<NWIN>(a, bx, by);
+        int jlo, jhi;
+        gather_bins(a, fr, v, jlo, jhi);
+        const long base = (long)v * a.n_det;
+        for (int j = jlo; j <= jhi && s < h.y; ++j) {
+            float4 wq;
+            if (!gather_weights<NWIN>(a, fr, __ldg(a.rayf + base + j), wq)) continue;
+            const long idx = ((long)h.x + s) * 32 + lane;
+            tw[idx] = wq;
+            tray[idx] = j;
+            ++s;
+        }
+    }
+    for (; s < h.y; ++s) {
+        const long idx = ((long)h.x + s) * 32 + lane;
+        tw[idx] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        tray[idx] = -1;
+    }
+}
+
+// The table gather: CTA = one group of 32 blocks x G view groups (warp g walks
+// the views g, g + G, ... of the subset), BC images per thread as in
+// k_backward_batch, whose reduction and epilogue it shares.
+template <int BC>
+__global__ void __launch_bounds__(512, 1) k_backward_table(const BackBatchTable t)
+{
+    pdl_begin();
+    const int lane = threadIdx.x, g = threadIdx.y, G = blockDim.y;
+    int c = 0;
+#pragma unroll
+    for (int k = 1; k < kMaxClasses; ++k)
+        if (k < t.count && (long)blockIdx.x >= t.begin[k]) c = k;
+    const BackArgs& a = t.c[c];
+    const int nb = (a.ns + 1) / 2, groups = table_groups(a.ns);
+    const int chunks = (a.batch + BC - 1) / BC;
+    const long local = (long)blockIdx.x - t.begin[c];
+    const int k = (int)(local / chunks);                       // the chunks of a group are adjacent
+    const int chunk = (int)(local - (long)k * chunks);         // CTAs: their table reads meet in L2
+    const int i0 = chunk * BC;
+    const int ni = min(BC, a.batch - i0);                      // images in this chunk
+    const long istride = res_is(a);
+    const int js = res_js(a);
+    const bool vec = a.res_il && (a.batch & 3) == 0 && (BC & 3) == 0;
+    float2 acc2[BC / 2][4];
+#pragma unroll
+    for (int h = 0; h < BC / 2; ++h) acc2[h][0] = acc2[h][1] = acc2[h][2] = acc2[h][3] = make_float2(0.0f, 0.0f);
+    const float* __restrict__ res = a.res + (long)i0 * istride;
+    auto entry = [&](int j, const float4 wq, const float* __restrict__ rrow) {
+        float r[BC];
+        if (vec) {
+            const float4* r4 = reinterpret_cast<const float4*>(rrow + (long)j * js);
+#pragma unroll
+            for (int b = 0; b < BC; b += 4) {
+                const float4 q = b < ni ? __ldg(r4 + b / 4) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                r[b] = q.x; r[b + 1] = q.y; r[b + 2] = q.z; r[b + 3] = q.w;
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < BC; ++b) r[b] = b < ni ? __ldg(rrow + b * istride + (long)j * js) : 0.0f;
+        }
+        const float2 v00 = make_float2(wq.x, wq.x), v10 = make_float2(wq.y, wq.y);
+        const float2 v01 = make_float2(wq.z, wq.z), v11 = make_float2(wq.w, wq.w);
+#pragma unroll
+        for (int h = 0; h < BC / 2; ++h) {
+            const float2 rr = make_float2(r[2 * h], r[2 * h + 1]);
+            acc2[h][0] = __ffma2_rn(v00, rr, acc2[h][0]);
+            acc2[h][1] = __ffma2_rn(v10, rr, acc2[h][1]);
+            acc2[h][2] = __ffma2_rn(v01, rr, acc2[h][2]);
+            acc2[h][3] = __ffma2_rn(v11, rr, acc2[h][3]);
+        }
+    };
+    // headers of the next view fetched one view ahead; the slots of a view in
+    // batches of kTabPre (bins and weights loaded together, then used in order)
+    constexpr int kTabPre = 4;
+    int vs = g;
+    int2 hd = make_int2(0, 0);
+    if (vs < a.n_sub) hd = __ldg(a.thdr + (long)(a.first_view + vs * a.view_step) * groups + k);
+    for (; vs < a.n_sub; vs += G) {
+        const int2 cur = hd;
+        if (vs + G < a.n_sub) hd = __ldg(a.thdr + (long)(a.first_view + (vs + G) * a.view_step) * groups + k);
+        const float* __restrict__ rrow = res + (long)vs * a.n_det * js;
+        for (int sl = 0; sl < cur.y; sl += kTabPre) {
+            int jj[kTabPre];
+            float4 ww[kTabPre];
+#pragma unroll
+            for (int q = 0; q < kTabPre; ++q) {
+                const long idx = ((long)cur.x + sl + q) * 32 + lane;
+                jj[q] = sl + q < cur.y ? __ldg(a.tray + idx) : -1;
+                ww[q] = sl + q < cur.y ? __ldg(a.tw + idx) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int q = 0; q < kTabPre; ++q)
+                if (jj[q] >= 0) entry(jj[q], ww[q], rrow);
+        }
+    }
+    // view-group sums in rounds of RB images: part[g][k][slot]
+    extern __shared__ float4 part[];
+    constexpr int kSlots = 32;
+    const int RB = t.rb;
+    const int nthr = kSlots * G;
+    const int lt = g * 32 + lane;
+    const int s = a.s;
+    for (int b0 = 0; b0 < ni; b0 += RB) {
+        if (b0 > 0) __syncthreads();
+#pragma unroll
+        for (int b = 0; b < BC; ++b)
+            if (b >= b0 && b < b0 + RB)
+                part[(g * RB + (b - b0)) * kSlots + lane] =
+                    (b & 1) ? make_float4(acc2[b / 2][0].y, acc2[b / 2][1].y, acc2[b / 2][2].y, acc2[b / 2][3].y)
+                            : make_float4(acc2[b / 2][0].x, acc2[b / 2][1].x, acc2[b / 2][2].x, acc2[b / 2][3].x);
+        __syncthreads();
+        for (int idx = lt; idx < RB * kSlots; idx += nthr) {
+            const int kk = idx / kSlots, sl = idx - kk * kSlots;
+            const int inst = i0 + b0 + kk;
+            int obx, oby;
+            table_block(a.ns, k, sl, obx, oby);
+            if (b0 + kk >= ni || obx >= nb || oby >= nb) continue;
+            float s00 = 0.0f, s10 = 0.0f, s01 = 0.0f, s11 = 0.0f;
+            for (int q = 0; q < G; ++q) {
+                const float4 pq = part[(q * RB + kk) * kSlots + sl];
+                s00 += pq.x; s10 += pq.y; s01 += pq.z; s11 += pq.w;
+            }
+            const float vals[4] = {a.scale * s00, a.scale * s10, a.scale * s01, a.scale * s11};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int ix = 2 * obx + (q & 1), iy = 2 * oby + (q >> 1);
+                if (ix >= a.ns || iy >= a.ns) continue;
+                if (a.mode == kBackRaw) {
+                    a.out[((long)inst * a.ns + iy) * a.ns + ix] = vals[q];
+                    continue;
+                }
+                for (int bb = 0; bb < s; ++bb) {
+                    const long row = ((long)inst * a.n + (long)iy * s + bb) * a.n + (long)ix * s;
+                    for (int aa = 0; aa < s; ++aa) {
+                        if (a.mode == kBackGradFine)
+                            a.out[row + aa] = vals[q];
+                        else
+                            a.out[row + aa] = __ldg(a.y + row + aa) - a.eta * vals[q];
+                    }
+                }
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ transpose A_s^T, scatter form
 // CTA = one TS x TS tile of the level image of one instance, all views of the
 // subset.  Every sample of every ray that can touch the tile is splatted with
@@ -1261,9 +1542,82 @@ cudaError_t launch_backward_batch(const BackArgs* items, int count, cudaStream_t
 }
 }  // namespace
 
+namespace {
+template <int BC>
+cudaError_t table_launch(const BackBatchTable& t, dim3 grd, dim3 blk, size_t smem, cudaStream_t st)
+{
+    return launch_pdl(k_backward_table<BC>, grd, blk, smem, st, t);
+}
+
+// The table gather: BC in {2, 4, 8, 16} images per thread, 32 blocks x G view groups per CTA.
+cudaError_t launch_backward_table(const BackArgs* items, int count, cudaStream_t st, int groups)
+{
+    int BC = back_batch_of(groups);
+    BC = BC >= 16 ? 16 : BC >= 8 ? 8 : BC >= 4 ? 4 : 2;
+    int G = groups & 0xff;
+    BackBatchTable t{};
+    t.count = count;
+    t.begin[0] = 0;
+    int min_views = 1 << 30;
+    long warps1 = 0;
+    for (int c = 0; c < count; ++c) {
+        if (!items[c].thdr || !items[c].tw || !items[c].tray) return cudaErrorInvalidValue;
+        t.c[c] = items[c];
+        const int chunks = div_up(items[c].batch, BC);
+        t.begin[c + 1] = t.begin[c] + (long)table_groups(items[c].ns) * chunks;
+        warps1 += (long)table_groups(items[c].ns) * chunks;
+        min_views = min(min_views, items[c].n_sub);
+    }
+    if (G < 1 || G > 16) {   // about two waves of 32 warps per SM
+        G = 1;
+        const long wave = 2L * device_sm_count() * 32;
+        while (G * 2 <= 16 && warps1 * G < wave && G * 2 <= min_views) G *= 2;
+    }
+    t.rb = max(1, min(BC, (int)(32768 / ((long)G * 32 * sizeof(float4)))));
+    const size_t smem = (size_t)G * t.rb * 32 * sizeof(float4);
+    dim3 blk(32, G), grd((unsigned)t.begin[count]);
+    cudaError_t e;
+    switch (BC) {
+        case 2: e = table_launch<2>(t, grd, blk, smem, st); break;
+        case 4: e = table_launch<4>(t, grd, blk, smem, st); break;
+        case 8: e = table_launch<8>(t, grd, blk, smem, st); break;
+        default: e = table_launch<16>(t, grd, blk, smem, st); break;
+    }
+    if (e != cudaSuccess) return e;
+    return counted();
+}
+}  // namespace
+
+cudaError_t launch_table_count(const BackArgs& a, int n_views, int* widths, cudaStream_t st)
+{
+    const long warps = (long)n_views * table_groups(a.ns);
+    k_table_count<<<(unsigned)div_up(warps * 32, 256), 256, 0, st>>>(a, n_views, widths);
+    return counted();
+}
+
+cudaError_t launch_table_fill(const BackArgs& a, int n_views, const int2* hdr, float4* tw, int* tray,
+                              cudaStream_t st)
+{
+    const long warps = (long)n_views * table_groups(a.ns);
+    const unsigned grd = (unsigned)div_up(warps * 32, 256);
+    if (a.step == 0.5f)
+        k_table_fill<9><<<grd, 256, 0, st>>>(a, n_views, hdr, tw, tray);
+    else
+        k_table_fill<0><<<grd, 256, 0, st>>>(a, n_views, hdr, tw, tray);
+    return counted();
+}
+
 cudaError_t launch_backward_multi(const BackArgs* items, int count, cudaStream_t st, int groups)
 {
     if (count < 1 || count > kMaxClasses) return cudaErrorInvalidValue;
+    if (groups & PNP_BACK_TABLE) {
+        bool all = true;
+        for (int c = 0; c < count; ++c) all = all && items[c].thdr && items[c].tw && items[c].tray;
+        if (all) return launch_backward_table(items, count, st, groups);
+        // no table registered: the gather with the same view groups (batched for BC >= 4)
+        groups &= ~PNP_BACK_TABLE;
+        if (back_batch_of(groups) < 4) groups &= 0xffff;
+    }
     if (!(groups & PNP_BACK_SCATTER) && back_batch_of(groups) > 1)
         return launch_backward_batch(items, count, st, groups);
     if (groups & PNP_BACK_SCATTER) {
