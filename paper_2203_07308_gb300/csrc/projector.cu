@@ -134,15 +134,14 @@ __global__ void k_prep_quad(const PrepTable t)
 }
 
 // Image-interleaved coefficient image, quad[(qy * qw + qx) * B + b].  A CTA
-// builds kIlRows x kIlCells cells for all B images of its class: it stages the
-// kIlRows + 1 level-image rows those cells read (pooled for s > 1) in shared
-// memory, kIlImages images at a time, then writes the cells with the image
+// builds ROWS x kIlCells cells for all B images of its class: it stages the
+// ROWS + 1 level-image rows those cells read (pooled for s > 1) in shared
+// memory, 64 / ROWS images at a time, then writes the cells with the image
 // index fastest, so that both the image reads and the cell writes are
-// contiguous.  (Blocks of 8 rows, which stage each row once for two rows of
-// cells, measured no faster than single rows.)
+// contiguous.  ROWS = 4 for level images of 256 or more (each staged row serves
+// two rows of cells, and a CTA's fixed costs spread over four times the cells:
+// 39 -> 29 us at 16 x 512^2), 1 below (enough CTAs for the small images).
 constexpr int kIlCells = 32;
-constexpr int kIlRows = 1;
-constexpr int kIlImages = 64;    // images staged at a time: 64 x 2 x 33 floats of shared memory
 
 struct PrepIlTable {
     PrepArgs c[kMaxClasses];
@@ -150,9 +149,12 @@ struct PrepIlTable {
     int count;
 };
 
+template <int ROWS>
 __global__ void __launch_bounds__(256) k_prep_quad_il(const PrepIlTable t)
 {
     pdl_begin();
+    constexpr int kIlRows = ROWS;
+    constexpr int kIlImages = ROWS == 1 ? 64 : 32;   // images staged at a time
     constexpr int C1 = kIlCells + 1, R1 = kIlRows + 1;
     __shared__ float lv[kIlImages * R1 * C1];              // [image][row][column]
     int c = 0;
@@ -1349,11 +1351,15 @@ cudaError_t launch_prep_multi(const PrepArgs* items, int count, cudaStream_t st)
     t.ibegin[0] = 0;
     ti.begin[0] = 0;
     long cells = 0;
+    // four cell rows per CTA when the interleaved classes' level images are large
+    int il_rows = 1;
+    for (int c = 0; c < count; ++c)
+        if (quad_interleaved(items[c].batch) && items[c].n / items[c].s >= 256) il_rows = 4;
     for (int c = 0; c < count; ++c) {
         const PrepArgs& it = items[c];
         if (quad_interleaved(it.batch)) {
             ti.c[ti.count] = it;
-            ti.begin[ti.count + 1] = ti.begin[ti.count] + (long)div_up(it.qw, kIlRows) * div_up(it.qw, kIlCells);
+            ti.begin[ti.count + 1] = ti.begin[ti.count] + (long)div_up(it.qw, il_rows) * div_up(it.qw, kIlCells);
             ++ti.count;
         } else {
             t.c[t.count] = it;
@@ -1369,7 +1375,9 @@ cudaError_t launch_prep_multi(const PrepArgs* items, int count, cudaStream_t st)
         counted();
     }
     if (ti.count > 0) {
-        const cudaError_t e = launch_pdl(k_prep_quad_il, dim3((unsigned)ti.begin[ti.count]), dim3(256), 0, st, ti);
+        const dim3 grd((unsigned)ti.begin[ti.count]);
+        const cudaError_t e = il_rows == 4 ? launch_pdl(k_prep_quad_il<4>, grd, dim3(256), 0, st, ti)
+                                           : launch_pdl(k_prep_quad_il<1>, grd, dim3(256), 0, st, ti);
         if (e != cudaSuccess) return e;
         counted();
     }
