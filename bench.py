@@ -53,17 +53,17 @@ FLOP_PER_PIXEL_ITER = 24
 # while the kernel's source is the one that was measured (else null).  Units: one
 # launch of the projector kernels (the forward's figure weighted over the
 # schedule's 24 / 24 / 72 launches at the 4x / 2x / full levels, whose captured
-# launches move 8.3 / 21.0 / 81.0 MB), one denoise (two launches) of the FGP strips.
+# launches move 8.3 / 21.0 / 81.2 MB), one denoise (two launches) of the FGP strips.
 KERNEL_TRAFFIC = {
     "backward": {"bytes_per_unit": 20120269, "unit": "launch", "source": "projector.cu",
                  "begin": "struct BackTable {",
-                 "end": "// ------------------------------------------------------------------ transpose A_s^T, scatter form",
+                 "end": "// ------------------------------------------------------------------ transpose A_s^T from a stored table",
                  "sha256": "c78e03f76b65ec7b86043f9c728828bf485de3e0a29827b0539a41bab277aa7a",
                  "profile": "profiles/k_backward_batch_512x16_720x768.md"},
-    "forward": {"bytes_per_unit": 54460877, "unit": "launch", "source": "projector.cu",
+    "forward": {"bytes_per_unit": 54566502, "unit": "launch", "source": "projector.cu",
                 "begin": "// Forward projector on an image-interleaved coefficient image.",
                 "end": "// ------------------------------------------------------------------ transpose A_s^T\n// Pixel-driven gather.",
-                "sha256": "48a6d7dd0e06e12f651b61a42423c8e59049ddfde0467d0f3adfa9370c92816f",
+                "sha256": "c4482dca11e7fd288c290417344cddc0d7e2ef23f0f818d8d30bc222cba75bd9",
                  "profile": "profiles/k_forward_il_512x16_720x768.md"},
     "denoise": {"bytes_per_unit": 125760512, "unit": "denoise (two launches)", "source": "tv.cu",
                 "begin": "// ------------------------------------------------------------------ register-resident FGP strips",
