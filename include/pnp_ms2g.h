@@ -121,6 +121,15 @@ typedef struct {
  * pair of CUDA events on the run's stream, so that pnp_kernel_times can report
  * the device time of each phase.  Not combinable with PNP_RUN_GRAPH. */
 #define PNP_RUN_KERNEL_TIMES 2
+/* Flag for pnp_run_params.flags: every phase kernel of the run (coefficient
+ * image, forward projector, gather backprojector, FGP denoiser) launches in its
+ * persistent form: only as many CTAs as the GPU holds at once, each walking
+ * the phase's work table of (geometry class, instance, tile / ray block) items
+ * with a stride of the grid (no waits between CTAs).  Every item computes what
+ * it computes in the direct form, so the results are the same bits; what
+ * changes is who schedules the items (the kernel instead of the hardware's CTA
+ * dispatcher).  Combines with PNP_RUN_GRAPH. */
+#define PNP_RUN_PERSISTENT 4
 
 /* Phases of one iteration of Algorithm 1, as timed by PNP_RUN_KERNEL_TIMES. */
 #define PNP_PHASE_PREP 0      /* sketch S and the bilinear coefficient image */

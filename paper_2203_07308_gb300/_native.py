@@ -66,6 +66,7 @@ class RunParams(C.Structure):
 
 RUN_GRAPH = 1
 RUN_KERNEL_TIMES = 2
+RUN_PERSISTENT = 4     # phase kernels in their persistent form (CTAs that fit at once walk the work table)
 PHASES = ("prep", "forward", "backward", "denoise")
 
 
@@ -348,12 +349,13 @@ def onchip_bandwidth(device="cuda", stream=None) -> dict:
     return {"l2_gbs": float(out[0]), "l1_gbs": float(out[1]), "smem_gbs": float(out[2])}
 
 
-def _flags(graph, kernel_times):
-    return (RUN_GRAPH if graph else 0) | (RUN_KERNEL_TIMES if kernel_times else 0)
+def _flags(graph, kernel_times, persistent=False):
+    return (RUN_GRAPH if graph else 0) | (RUN_KERNEL_TIMES if kernel_times else 0) | \
+        (RUN_PERSISTENT if persistent else 0)
 
 
 def run(g, stages, eta, seq, b, x, *, alpha=1.0, lam=0.02, tv_iters=20, momentum=True,
-        xtrue=None, ws=None, stream=None, graph=False, kernel_times=False):
+        xtrue=None, ws=None, stream=None, graph=False, kernel_times=False, persistent=False):
     """Algorithm 1; x holds x_0 on entry and the result on return.  eta: step
     size per stage, or None for eta_k = 1/L_k computed by the library.  Returns the
     PSNR log [total_iters, batch] when xtrue is given, else None.  graph=True
@@ -366,7 +368,8 @@ def run(g, stages, eta, seq, b, x, *, alpha=1.0, lam=0.02, tv_iters=20, momentum
     seq_np = np.ascontiguousarray(np.asarray(seq if seq is not None else np.zeros(total), dtype=np.int32))
     if seq_np.size < total:
         raise PnpError(PNP_EINVAL, "subset sequence shorter than the schedule")
-    prm = RunParams(float(alpha), float(lam), int(tv_iters), int(bool(momentum)), _flags(graph, kernel_times))
+    prm = RunParams(float(alpha), float(lam), int(tv_iters), int(bool(momentum)),
+                    _flags(graph, kernel_times, persistent))
     img = g.batch * g.n * g.n
     log = np.zeros((total, g.batch)) if xtrue is not None else None
     _check(load().pnp_run(C.byref(geom(g)), st, len(st), eta_a,
@@ -589,7 +592,7 @@ def unrolled_step_vjp(g, factor, subset, n_subsets, eta, alpha, lam, tv_iters, a
 
 # ---------------------------------------------------------------- uneven batches, autotuning
 def run_many(problems, *, alpha=1.0, lam=0.02, tv_iters=20, momentum=True, stream=None, graph=False,
-             kernel_times=False):
+             kernel_times=False, persistent=False):
     """pnp_run_many.  ``problems``: list of dicts with keys plan, stages, eta, seq,
     b, x and optional xtrue, start_iter, y (checkpoint/resume: x and y of
     iteration start_iter in, x and y of the last iteration out); returns the
@@ -617,7 +620,8 @@ def run_many(problems, *, alpha=1.0, lam=0.02, tv_iters=20, momentum=True, strea
                           log.ctypes.data_as(C.POINTER(C.c_double)) if log is not None else None,
                           _ws(plan.ws)[0], int(pr.get("start_iter", 0)),
                           _ptr(pr.get("y"), img, "y", True))
-    prm = RunParams(float(alpha), float(lam), int(tv_iters), int(bool(momentum)), _flags(graph, kernel_times))
+    prm = RunParams(float(alpha), float(lam), int(tv_iters), int(bool(momentum)),
+                    _flags(graph, kernel_times, persistent))
     _check(load().pnp_run_many(arr, len(problems), C.byref(prm), _stream(stream)))
     return logs
 

@@ -1208,9 +1208,16 @@ int run_many_impl(const pnp_problem* pb_in, int np, const pnp_run_params* params
     if (!(pr.alpha > 0.0f && pr.alpha <= 1.0f)) return fail(PNP_EINVAL, "alpha must be in (0, 1]");
     if (!(pr.lambda >= 0.0f) || !std::isfinite(pr.lambda)) return fail(PNP_EINVAL, "lambda must be >= 0");
     if (pr.tv_iters < 0 || pr.tv_iters > 100000) return fail(PNP_EINVAL, "tv_iters outside [0, 100000]");
-    if (pr.flags & ~(PNP_RUN_GRAPH | PNP_RUN_KERNEL_TIMES)) return fail(PNP_EINVAL, "unknown run flags %d", pr.flags);
+    if (pr.flags & ~(PNP_RUN_GRAPH | PNP_RUN_KERNEL_TIMES | PNP_RUN_PERSISTENT))
+        return fail(PNP_EINVAL, "unknown run flags %d", pr.flags);
     if ((pr.flags & PNP_RUN_GRAPH) && (pr.flags & PNP_RUN_KERNEL_TIMES))
         return fail(PNP_EINVAL, "PNP_RUN_KERNEL_TIMES cannot be combined with PNP_RUN_GRAPH");
+    // the phase kernels in their persistent form for this call (restored on return)
+    struct PersistentScope {
+        bool prev;
+        explicit PersistentScope(bool on) : prev(persistent_mode()) { set_persistent_mode(on); }
+        ~PersistentScope() { set_persistent_mode(prev); }
+    } persistent_scope((pr.flags & PNP_RUN_PERSISTENT) != 0);
     std::vector<ProblemState> ps((size_t)np);
     for (int c = 0; c < np; ++c)
         if (int e = validate_problem(pb[c], pr, c, &ps[c])) return e;

@@ -70,6 +70,32 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 }
 
 
+// Persistent launches (PNP_RUN_PERSISTENT, set by pnp_run / pnp_run_many for the
+// duration of the call on the calling thread): the phase kernels then launch in
+// their persistent form, as many CTAs as fit on the GPU at once, each walking
+// the phase's work table (class, instance, tile) with a stride of the grid.
+bool persistent_mode();
+void set_persistent_mode(bool on);
+int device_sm_count();
+
+// direct: one CTA per work item (grid = items); persistent: the same items walked
+// by the CTAs that fit at once (occupancy x SMs), at most one per item
+template <typename... KArgs, typename... Args>
+cudaError_t launch_items(void (*direct)(KArgs...), void (*persistent)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                         cudaStream_t st, Args&&... args)
+{
+    if (!persistent_mode()) return launch_pdl(direct, grid, block, smem, st, std::forward<Args>(args)...);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent, (int)(block.x * block.y * block.z), smem) !=
+            cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const long cap = (long)per_sm * device_sm_count();
+    const dim3 pg((unsigned)((long)grid.x < cap ? (long)grid.x : cap), grid.y, grid.z);
+    return launch_pdl(persistent, pg, block, smem, st, std::forward<Args>(args)...);
+}
+
 constexpr int kMaxLevels = 4;          // factors 1, 2, 4, 8
 constexpr int kPad = 2;                // padding of the coefficient image
 

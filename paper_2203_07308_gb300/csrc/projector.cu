@@ -22,6 +22,12 @@ namespace pnp {
 std::atomic<uint64_t> g_launches{0};
 
 namespace {
+thread_local bool t_persistent = false;
+}
+bool persistent_mode() { return t_persistent; }
+void set_persistent_mode(bool on) { t_persistent = on; }
+
+namespace {
 
 constexpr float kMagic = 12582912.0f;      // 1.5 * 2^23: x + kMagic rounds x to an integer
 constexpr int kMagicBits = 0x4B400000;     // bit pattern of kMagic
@@ -150,9 +156,8 @@ struct PrepIlTable {
 };
 
 template <int ROWS>
-__global__ void __launch_bounds__(256) k_prep_quad_il(const PrepIlTable t)
+__device__ __forceinline__ void k_prep_quad_il_item(const PrepIlTable& t, const long vb)
 {
-    pdl_begin();
     constexpr int kIlRows = ROWS;
     constexpr int kIlImages = ROWS == 1 ? 64 : 32;   // images staged at a time
     constexpr int C1 = kIlCells + 1, R1 = kIlRows + 1;
@@ -160,11 +165,11 @@ __global__ void __launch_bounds__(256) k_prep_quad_il(const PrepIlTable t)
     int c = 0;
 #pragma unroll
     for (int k = 1; k < kMaxClasses; ++k)
-        if (k < t.count && (long)blockIdx.x >= t.begin[k]) c = k;
+        if (k < t.count && (long)vb >= t.begin[k]) c = k;
     const PrepArgs& a = t.c[c];
     const int qw = a.qw, B = a.batch;
     const int segs = (qw + kIlCells - 1) / kIlCells;
-    const int local = (int)((long)blockIdx.x - t.begin[c]);
+    const int local = (int)((long)vb - t.begin[c]);
     const int rblk = local / segs;
     const int qy0 = rblk * kIlRows, qx0 = (local - rblk * segs) * kIlCells;
     const int n = a.n, s = a.s, ns = n / s;
@@ -191,6 +196,25 @@ __global__ void __launch_bounds__(256) k_prep_quad_il(const PrepIlTable t)
     }
 }
 
+template <int ROWS>
+__global__ void __launch_bounds__(256) k_prep_quad_il(const PrepIlTable t)
+{
+    pdl_begin();
+    k_prep_quad_il_item<ROWS>(t, (long)blockIdx.x);
+}
+
+// persistent form (PNP_RUN_PERSISTENT): as many CTAs as fit at once walk the items
+template <int ROWS>
+__global__ void __launch_bounds__(256) k_prep_quad_il_persistent(const PrepIlTable t)
+{
+    pdl_begin();
+    const long total = t.begin[t.count];
+    for (long vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        if (vb != (long)blockIdx.x) __syncthreads();   // the previous item's shared memory is free
+        k_prep_quad_il_item<ROWS>(t, vb);
+    }
+}
+
 // ------------------------------------------------------------------ forward A_s
 // Warp = R rays x Q phases (R*Q = 32): lane (r, q) sums the samples k = k_lo + q,
 // k_lo + q + Q, ... of ray r into four interleaved partial sums (independent
@@ -209,14 +233,13 @@ struct FwdTable {
 constexpr int kFwdWarps = 8;       // warps per forward CTA
 
 template <int Q>
-__global__ void __launch_bounds__(32 * kFwdWarps, 4) k_forward(const FwdTable t)
+__device__ __forceinline__ void k_forward_item(const FwdTable& t, const long vb)
 {
-    pdl_begin();
     constexpr int R = 32 / Q;
     constexpr int RB = kFwdWarps * R;   // bins per CTA
     const int lane = threadIdx.x & 31;
     const int r = lane / Q, q = lane % Q;
-    const long cta = blockIdx.x;
+    const long cta = vb;
     int c = 0;
 #pragma unroll
     for (int k = 1; k < kMaxClasses; ++k)
@@ -289,6 +312,24 @@ __global__ void __launch_bounds__(32 * kFwdWarps, 4) k_forward(const FwdTable t)
     }
 }
 
+template <int Q>
+__global__ void __launch_bounds__(32 * kFwdWarps, 4) k_forward(const FwdTable t)
+{
+    pdl_begin();
+    k_forward_item<Q>(t, (long)blockIdx.x);
+}
+
+// persistent form (PNP_RUN_PERSISTENT): as many CTAs as fit at once walk the items
+template <int Q>
+__global__ void __launch_bounds__(32 * kFwdWarps, 4) k_forward_persistent(const FwdTable t)
+{
+    pdl_begin();
+    const long total = t.begin[t.count];
+    for (long vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        k_forward_item<Q>(t, vb);
+    }
+}
+
 // Forward projector on an image-interleaved coefficient image.  A warp takes one
 // ray for all images of its class: lane (g, i) = (lane / 8, lane % 8) sums the
 // samples k = k_lo + g, k_lo + g + 4, ... of images i, i + 8, ..., i + 8 (IPL - 1),
@@ -300,12 +341,11 @@ __global__ void __launch_bounds__(32 * kFwdWarps, 4) k_forward(const FwdTable t)
 constexpr int kFwdIlWarps = 4;
 
 template <int IPL>
-__global__ void __launch_bounds__(32 * kFwdIlWarps) k_forward_il(const FwdTable t)
+__device__ __forceinline__ void k_forward_il_item(const FwdTable& t, const long vb)
 {
-    pdl_begin();
     const int lane = threadIdx.x & 31;
     const int sg = lane >> 3, li = lane & 7;
-    const long cta = blockIdx.x;
+    const long cta = vb;
     int c = 0;
 #pragma unroll
     for (int k = 1; k < kMaxClasses; ++k)
@@ -384,6 +424,24 @@ __global__ void __launch_bounds__(32 * kFwdIlWarps) k_forward_il(const FwdTable 
     }
 }
 
+template <int IPL>
+__global__ void __launch_bounds__(32 * kFwdIlWarps) k_forward_il(const FwdTable t)
+{
+    pdl_begin();
+    k_forward_il_item<IPL>(t, (long)blockIdx.x);
+}
+
+// persistent form (PNP_RUN_PERSISTENT): as many CTAs as fit at once walk the items
+template <int IPL>
+__global__ void __launch_bounds__(32 * kFwdIlWarps) k_forward_il_persistent(const FwdTable t)
+{
+    pdl_begin();
+    const long total = t.begin[t.count];
+    for (long vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        k_forward_il_item<IPL>(t, vb);
+    }
+}
+
 // ------------------------------------------------------------------ transpose A_s^T
 // Pixel-driven gather.  Thread (2x2 pixel block, g) gathers the views g, g+G,
 // g+2G, ... of the subset: for each view, the detector interval that the
@@ -416,19 +474,18 @@ struct BackTable {
 };
 
 template <int NWIN, int TX>
-__global__ void __launch_bounds__(1024, 1) k_backward2x2(const BackTable t)
+__device__ __forceinline__ void k_backward2x2_item(const BackTable& t, const long vb)
 {
-    pdl_begin();
     const int tx = threadIdx.x, ty = threadIdx.y, g = threadIdx.z, G = blockDim.z;
     int c = 0;
 #pragma unroll
     for (int k = 1; k < kMaxClasses; ++k)
-        if (k < t.count && (long)blockIdx.x >= t.begin[k]) c = k;
+        if (k < t.count && (long)vb >= t.begin[k]) c = k;
     const BackArgs& a = t.c[c];
     const int nb = (a.ns + 1) / 2;                             // blocks per side
     const int tiles_x = (nb + TX - 1) / TX;
     const int tiles_y = (nb + kBack2TileY - 1) / kBack2TileY;
-    const long local = (long)blockIdx.x - t.begin[c];
+    const long local = (long)vb - t.begin[c];
     const int tiles = tiles_x * tiles_y;
     const int inst = (int)(local / tiles);
     const int tile = (int)(local - (long)inst * tiles);
@@ -547,6 +604,25 @@ __global__ void __launch_bounds__(1024, 1) k_backward2x2(const BackTable t)
     }
 }
 
+template <int NWIN, int TX>
+__global__ void __launch_bounds__(1024, 1) k_backward2x2(const BackTable t)
+{
+    pdl_begin();
+    k_backward2x2_item<NWIN, TX>(t, (long)blockIdx.x);
+}
+
+// persistent form (PNP_RUN_PERSISTENT): as many CTAs as fit at once walk the items
+template <int NWIN, int TX>
+__global__ void __launch_bounds__(1024, 1) k_backward2x2_persistent(const BackTable t)
+{
+    pdl_begin();
+    const long total = t.begin[t.count];
+    for (long vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        if (vb != (long)blockIdx.x) __syncthreads();   // the previous item's shared memory is free
+        k_backward2x2_item<NWIN, TX>(t, vb);
+    }
+}
+
 // Batched form of the gather for a class of B images that share one geometry:
 // the rays, their samples and therefore every hat product are the same for all
 // images; only the residuals differ.  A thread (2x2 pixel block, view group g)
@@ -567,19 +643,18 @@ struct BackBatchTable {
 constexpr int kBackBatchThreads = 512;
 
 template <int NWIN, int TX, int BC>
-__global__ void __launch_bounds__(kBackBatchThreads, 1) k_backward_batch(const BackBatchTable t)
+__device__ __forceinline__ void k_backward_batch_item(const BackBatchTable& t, const long vb)
 {
-    pdl_begin();
     const int tx = threadIdx.x, ty = threadIdx.y, g = threadIdx.z, G = blockDim.z;
     int c = 0;
 #pragma unroll
     for (int k = 1; k < kMaxClasses; ++k)
-        if (k < t.count && (long)blockIdx.x >= t.begin[k]) c = k;
+        if (k < t.count && (long)vb >= t.begin[k]) c = k;
     const BackArgs& a = t.c[c];
     const int nb = (a.ns + 1) / 2;                             // blocks per side
     const int tiles_x = (nb + TX - 1) / TX;
     const int tiles_y = (nb + kBack2TileY - 1) / kBack2TileY;
-    const long local = (long)blockIdx.x - t.begin[c];
+    const long local = (long)vb - t.begin[c];
     const int tiles = tiles_x * tiles_y;
     const int chunk = (int)(local / tiles);
     const int tile = (int)(local - (long)chunk * tiles);
@@ -732,6 +807,25 @@ __global__ void __launch_bounds__(kBackBatchThreads, 1) k_backward_batch(const B
                 }
             }
         }
+    }
+}
+
+template <int NWIN, int TX, int BC>
+__global__ void __launch_bounds__(kBackBatchThreads, 1) k_backward_batch(const BackBatchTable t)
+{
+    pdl_begin();
+    k_backward_batch_item<NWIN, TX, BC>(t, (long)blockIdx.x);
+}
+
+// persistent form (PNP_RUN_PERSISTENT): as many CTAs as fit at once walk the items
+template <int NWIN, int TX, int BC>
+__global__ void __launch_bounds__(kBackBatchThreads, 1) k_backward_batch_persistent(const BackBatchTable t)
+{
+    pdl_begin();
+    const long total = t.begin[t.count];
+    for (long vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        if (vb != (long)blockIdx.x) __syncthreads();   // the previous item's shared memory is free
+        k_backward_batch_item<NWIN, TX, BC>(t, vb);
     }
 }
 
@@ -1376,8 +1470,8 @@ cudaError_t launch_prep_multi(const PrepArgs* items, int count, cudaStream_t st)
     }
     if (ti.count > 0) {
         const dim3 grd((unsigned)ti.begin[ti.count]);
-        const cudaError_t e = il_rows == 4 ? launch_pdl(k_prep_quad_il<4>, grd, dim3(256), 0, st, ti)
-                                           : launch_pdl(k_prep_quad_il<1>, grd, dim3(256), 0, st, ti);
+        const cudaError_t e = il_rows == 4 ? launch_items(k_prep_quad_il<4>, k_prep_quad_il_persistent<4>, grd, dim3(256), 0, st, ti)
+                                           : launch_items(k_prep_quad_il<1>, k_prep_quad_il_persistent<1>, grd, dim3(256), 0, st, ti);
         if (e != cudaSuccess) return e;
         counted();
     }
@@ -1397,14 +1491,14 @@ cudaError_t forward_q(FwdTable t, cudaStream_t st)
     constexpr int RB = kFwdWarps * (32 / Q);
     for (int c = 0; c < t.count; ++c)
         t.begin[c + 1] = t.begin[c] + (long)t.c[c].batch * t.c[c].n_sub * div_up(t.c[c].n_det, RB);
-    return launch_pdl(k_forward<Q>, dim3((unsigned)t.begin[t.count]), dim3(32 * kFwdWarps), 0, st, t);
+    return launch_items(k_forward<Q>, k_forward_persistent<Q>, dim3((unsigned)t.begin[t.count]), dim3(32 * kFwdWarps), 0, st, t);
 }
 
 namespace {
 template <int IPL>
 cudaError_t forward_il(const FwdTable& t, cudaStream_t st)
 {
-    return launch_pdl(k_forward_il<IPL>, dim3((unsigned)t.begin[t.count]), dim3(32 * kFwdIlWarps), 0, st, t);
+    return launch_items(k_forward_il<IPL>, k_forward_il_persistent<IPL>, dim3((unsigned)t.begin[t.count]), dim3(32 * kFwdIlWarps), 0, st, t);
 }
 }  // namespace
 
@@ -1500,10 +1594,10 @@ cudaError_t batch_launch(const BackBatchTable& t, int TX, bool half_step, dim3 g
                          cudaStream_t st)
 {
     if (TX == 4)
-        return half_step ? launch_pdl(k_backward_batch<9, 4, BC>, grd, blk, smem, st, t)
-                         : launch_pdl(k_backward_batch<0, 4, BC>, grd, blk, smem, st, t);
-    return half_step ? launch_pdl(k_backward_batch<9, kBack2TileX, BC>, grd, blk, smem, st, t)
-                     : launch_pdl(k_backward_batch<0, kBack2TileX, BC>, grd, blk, smem, st, t);
+        return half_step ? launch_items(k_backward_batch<9, 4, BC>, k_backward_batch_persistent<9, 4, BC>, grd, blk, smem, st, t)
+                         : launch_items(k_backward_batch<0, 4, BC>, k_backward_batch_persistent<0, 4, BC>, grd, blk, smem, st, t);
+    return half_step ? launch_items(k_backward_batch<9, kBack2TileX, BC>, k_backward_batch_persistent<9, kBack2TileX, BC>, grd, blk, smem, st, t)
+                     : launch_items(k_backward_batch<0, kBack2TileX, BC>, k_backward_batch_persistent<0, kBack2TileX, BC>, grd, blk, smem, st, t);
 }
 
 // The batched gather: BC in {4, 8, 16} images per thread, TX x 4 blocks x G view
@@ -1671,11 +1765,11 @@ cudaError_t launch_backward_multi(const BackArgs* items, int count, cudaStream_t
     const size_t smem = (size_t)G * TX * kBack2TileY * sizeof(float4);
     cudaError_t e;
     if (TX == 4)
-        e = half_step ? launch_pdl(k_backward2x2<9, 4>, grd, blk, smem, st, t)
-                      : launch_pdl(k_backward2x2<0, 4>, grd, blk, smem, st, t);
+        e = half_step ? launch_items(k_backward2x2<9, 4>, k_backward2x2_persistent<9, 4>, grd, blk, smem, st, t)
+                      : launch_items(k_backward2x2<0, 4>, k_backward2x2_persistent<0, 4>, grd, blk, smem, st, t);
     else
-        e = half_step ? launch_pdl(k_backward2x2<9, kBack2TileX>, grd, blk, smem, st, t)
-                      : launch_pdl(k_backward2x2<0, kBack2TileX>, grd, blk, smem, st, t);
+        e = half_step ? launch_items(k_backward2x2<9, kBack2TileX>, k_backward2x2_persistent<9, kBack2TileX>, grd, blk, smem, st, t)
+                      : launch_items(k_backward2x2<0, kBack2TileX>, k_backward2x2_persistent<0, kBack2TileX>, grd, blk, smem, st, t);
     if (e != cudaSuccess) return e;
     return counted();
 }

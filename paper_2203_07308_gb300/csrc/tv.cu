@@ -136,17 +136,16 @@ constexpr int kTilePitch = 72;
 // only what neighbours read: r (phase A; zero outside the image, so that the
 // edge rule of L needs no test there), x_tmp (phase B) and, at the end, p.
 template <int NP, bool LAST>
-__global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
+__device__ __forceinline__ void k_tv_tile_item(const TileTvArgs& t, const long vb)
 {
-    pdl_begin();
     int cls = 0;
 #pragma unroll
     for (int k = 1; k < kMaxClasses; ++k)
-        if (k < t.count && (long)blockIdx.x >= t.begin[k]) cls = k;
+        if (k < t.count && (long)vb >= t.begin[k]) cls = k;
     const TileTvClass& a = t.c[cls];
     const int n = a.n, K = t.K, T = a.T;
     const int tiles_x = a.tiles_x;
-    const long local = (long)blockIdx.x - t.begin[cls];
+    const long local = (long)vb - t.begin[cls];
     const int inst = (int)(local / a.tiles);
     const int tile = (int)(local - (long)inst * a.tiles);
     const int i0 = (tile / tiles_x) * T, j0 = (tile % tiles_x) * T;
@@ -355,6 +354,25 @@ __global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
     }
 }
 
+template <int NP, bool LAST>
+__global__ void __launch_bounds__(1024) k_tv_tile(const TileTvArgs t)
+{
+    pdl_begin();
+    k_tv_tile_item<NP, LAST>(t, (long)blockIdx.x);
+}
+
+// persistent form (PNP_RUN_PERSISTENT): as many CTAs as fit at once walk the items
+template <int NP, bool LAST>
+__global__ void __launch_bounds__(1024) k_tv_tile_persistent(const TileTvArgs t)
+{
+    pdl_begin();
+    const long total = t.begin[t.count];
+    for (long vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        if (vb != (long)blockIdx.x) __syncthreads();   // the previous item's shared memory is free
+        k_tv_tile_item<NP, LAST>(t, vb);
+    }
+}
+
 // ------------------------------------------------------------------ register-resident FGP
 // The same K-iteration temporal blocking with no shared memory and no barrier:
 // a warp owns a tile of kWarpTvWV x kWarpTvHV output pixels; lane l holds one
@@ -386,13 +404,12 @@ struct WarpTvArgs {
     float mom[kWarpTvK];
 };
 
-__global__ void __launch_bounds__(32 * kWarpTvWarps) k_tv_warp(const WarpTvArgs t)
+__device__ __forceinline__ void k_tv_warp_item(const WarpTvArgs& t, const long vb)
 {
-    pdl_begin();
     constexpr int H = kWarpTvH;
     constexpr unsigned kAll = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const long wt = (long)blockIdx.x * kWarpTvWarps + (threadIdx.x >> 5);
+    const long wt = (long)vb * kWarpTvWarps + (threadIdx.x >> 5);
     if (wt >= t.begin[t.count]) return;                      // whole warps only
     int cls = 0;
 #pragma unroll
@@ -506,6 +523,23 @@ __global__ void __launch_bounds__(32 * kWarpTvWarps) k_tv_warp(const WarpTvArgs 
     }
 }
 
+__global__ void __launch_bounds__(32 * kWarpTvWarps) k_tv_warp(const WarpTvArgs t)
+{
+    pdl_begin();
+    k_tv_warp_item(t, (long)blockIdx.x);
+}
+
+// persistent form (PNP_RUN_PERSISTENT): as many CTAs as fit at once walk the items
+__global__ void __launch_bounds__(32 * kWarpTvWarps) k_tv_warp_persistent(const WarpTvArgs t)
+{
+    pdl_begin();
+    const long total = (t.begin[t.count] + kWarpTvWarps - 1) / kWarpTvWarps;
+    for (long vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        if (vb != (long)blockIdx.x) __syncthreads();   // the previous item's shared memory is free
+        k_tv_warp_item(t, vb);
+    }
+}
+
 // ------------------------------------------------------------------ register-resident FGP strips
 // The same temporal blocking as the tiles above, organised so that almost every
 // neighbour is in a register: a CTA owns a region of 64 columns x 8W rows (W
@@ -577,18 +611,17 @@ __device__ __forceinline__ float4 ld_hint(const float4* a, uint64_t pol)
 }
 
 template <bool LAST, int W>
-__global__ void __launch_bounds__(32 * W, W == 8 ? 2 : 1) k_tv_strip(const StripTvArgs t)   // W = 8, 12 or 16
+__device__ __forceinline__ void k_tv_strip_item(const StripTvArgs& t, const long vb)
 {
-    pdl_begin();
     constexpr int R = kStripR;
     constexpr unsigned kAll = 0xffffffffu;
     const int lane = threadIdx.x, w = threadIdx.y;
     int cls = 0;
 #pragma unroll
     for (int k = 1; k < kMaxClasses; ++k)
-        if (k < t.count && (long)blockIdx.x >= t.begin[k]) cls = k;
+        if (k < t.count && (long)vb >= t.begin[k]) cls = k;
     const StripTvClass& a = t.c[cls];
-    const long local = (long)blockIdx.x - t.begin[cls];
+    const long local = (long)vb - t.begin[cls];
     const int inst = (int)(local / a.tiles);
     const int tile = (int)(local - (long)inst * a.tiles);
     const int n = a.n;
@@ -764,6 +797,25 @@ __global__ void __launch_bounds__(32 * W, W == 8 ? 2 : 1) k_tv_strip(const Strip
     }
 }
 
+template <bool LAST, int W>
+__global__ void __launch_bounds__(32 * W, W == 8 ? 2 : 1) k_tv_strip(const StripTvArgs t)   // W = 8, 12 or 16
+{
+    pdl_begin();
+    k_tv_strip_item<LAST, W>(t, (long)blockIdx.x);
+}
+
+// persistent form (PNP_RUN_PERSISTENT): as many CTAs as fit at once walk the items
+template <bool LAST, int W>
+__global__ void __launch_bounds__(32 * W, W == 8 ? 2 : 1) k_tv_strip_persistent(const StripTvArgs t)
+{
+    pdl_begin();
+    const long total = t.begin[t.count];
+    for (long vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        if (vb != (long)blockIdx.x) __syncthreads();   // the previous item's shared memory is free
+        k_tv_strip_item<LAST, W>(t, vb);
+    }
+}
+
 inline cudaError_t counted(cudaError_t e = cudaGetLastError())
 {
     g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -894,7 +946,7 @@ cudaError_t launch_tv_warp_multi(const TvItem* items, int count, float lambda, i
             a.c[c].sout = a.last ? nullptr : (pass % 2 == 0 ? items[c].state_a : items[c].state_b);
         }
         for (int k = 0; k < K; ++k) a.mom[k] = mom[k0 + k];
-        e = launch_pdl(k_tv_warp, grd, blk, 0, st, a);
+        e = launch_items(k_tv_warp, k_tv_warp_persistent, grd, blk, 0, st, a);
         g_launches.fetch_add(1, std::memory_order_relaxed);
         if (e != cudaSuccess) return e;
         k0 += K;
@@ -943,14 +995,14 @@ cudaError_t launch_tv_strip_multi(const TvItem* items, int count, float lambda, 
         }
         for (int k = 0; k < K; ++k) a.mom[k] = mom[k0 + k];
         if (a.W == 8)
-            e = a.last ? launch_pdl(k_tv_strip<true, 8>, grd, blk, smem, st, a)
-                       : launch_pdl(k_tv_strip<false, 8>, grd, blk, smem, st, a);
+            e = a.last ? launch_items(k_tv_strip<true, 8>, k_tv_strip_persistent<true, 8>, grd, blk, smem, st, a)
+                       : launch_items(k_tv_strip<false, 8>, k_tv_strip_persistent<false, 8>, grd, blk, smem, st, a);
         else if (a.W == 12)
-            e = a.last ? launch_pdl(k_tv_strip<true, 12>, grd, blk, smem, st, a)
-                       : launch_pdl(k_tv_strip<false, 12>, grd, blk, smem, st, a);
+            e = a.last ? launch_items(k_tv_strip<true, 12>, k_tv_strip_persistent<true, 12>, grd, blk, smem, st, a)
+                       : launch_items(k_tv_strip<false, 12>, k_tv_strip_persistent<false, 12>, grd, blk, smem, st, a);
         else
-            e = a.last ? launch_pdl(k_tv_strip<true, 16>, grd, blk, smem, st, a)
-                       : launch_pdl(k_tv_strip<false, 16>, grd, blk, smem, st, a);
+            e = a.last ? launch_items(k_tv_strip<true, 16>, k_tv_strip_persistent<true, 16>, grd, blk, smem, st, a)
+                       : launch_items(k_tv_strip<false, 16>, k_tv_strip_persistent<false, 16>, grd, blk, smem, st, a);
         g_launches.fetch_add(1, std::memory_order_relaxed);
         if (e != cudaSuccess) return e;
         k0 += K;
@@ -975,6 +1027,14 @@ cudaError_t launch_tv_tiled_multi(const TvItem* items, int count, float lambda, 
         cudaFuncSetAttribute(k_tv_tile<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         cudaFuncSetAttribute(k_tv_tile<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         cudaFuncSetAttribute(k_tv_tile<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_tv_tile_persistent<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_tv_tile_persistent<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_tv_tile_persistent<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_tv_tile_persistent<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_tv_tile_persistent<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_tv_tile_persistent<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_tv_tile_persistent<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_tv_tile_persistent<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         attr = true;
     }
     if (count < 1 || count > kMaxClasses || iters < 1) return cudaErrorInvalidValue;
@@ -1033,14 +1093,14 @@ cudaError_t launch_tv_tiled_multi(const TvItem* items, int count, float lambda, 
         const size_t sm = tile_smem(Tmax, K, ring);
         const dim3 blk(kTileThreads);
         switch (tile_np(Tmax, K, ring)) {
-            case 1: e = a.last ? launch_pdl(k_tv_tile<1, true>, grd, blk, sm, st, a)
-                               : launch_pdl(k_tv_tile<1, false>, grd, blk, sm, st, a); break;
-            case 2: e = a.last ? launch_pdl(k_tv_tile<2, true>, grd, blk, sm, st, a)
-                               : launch_pdl(k_tv_tile<2, false>, grd, blk, sm, st, a); break;
-            case 3: e = a.last ? launch_pdl(k_tv_tile<3, true>, grd, blk, sm, st, a)
-                               : launch_pdl(k_tv_tile<3, false>, grd, blk, sm, st, a); break;
-            default: e = a.last ? launch_pdl(k_tv_tile<4, true>, grd, blk, sm, st, a)
-                                : launch_pdl(k_tv_tile<4, false>, grd, blk, sm, st, a); break;
+            case 1: e = a.last ? launch_items(k_tv_tile<1, true>, k_tv_tile_persistent<1, true>, grd, blk, sm, st, a)
+                               : launch_items(k_tv_tile<1, false>, k_tv_tile_persistent<1, false>, grd, blk, sm, st, a); break;
+            case 2: e = a.last ? launch_items(k_tv_tile<2, true>, k_tv_tile_persistent<2, true>, grd, blk, sm, st, a)
+                               : launch_items(k_tv_tile<2, false>, k_tv_tile_persistent<2, false>, grd, blk, sm, st, a); break;
+            case 3: e = a.last ? launch_items(k_tv_tile<3, true>, k_tv_tile_persistent<3, true>, grd, blk, sm, st, a)
+                               : launch_items(k_tv_tile<3, false>, k_tv_tile_persistent<3, false>, grd, blk, sm, st, a); break;
+            default: e = a.last ? launch_items(k_tv_tile<4, true>, k_tv_tile_persistent<4, true>, grd, blk, sm, st, a)
+                                : launch_items(k_tv_tile<4, false>, k_tv_tile_persistent<4, false>, grd, blk, sm, st, a); break;
         }
         g_launches.fetch_add(1, std::memory_order_relaxed);
         if (e != cudaSuccess) return e;

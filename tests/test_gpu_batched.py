@@ -294,3 +294,55 @@ np.save(sys.argv[1], x.cpu().numpy())
         subprocess.run([sys.executable, str(script), str(out)], env=env, check=True, timeout=600)
         outs.append(np.load(out))
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4, 16])
+def test_persistent_launches_give_the_same_bits(tile):
+    """PNP_RUN_PERSISTENT: every phase kernel as CTAs that fit at once walking
+    the work table.  Three uneven classes (sizes 48 / 64 / 96, one of them a
+    batch of 9 with image-interleaved layouts) in one run_many call, every
+    denoiser variant, direct and graph-captured: the iterates and PSNR logs
+    equal those of the direct launches; one class against the oracle."""
+    import torch
+    specs = [(synth.make_geometry(48, 40, 72, batch=2), [synth.Stage(2, 2, 3), synth.Stage(1, 3, 2)]),
+             (synth.make_geometry(64, 60, 96, batch=9), [synth.Stage(4, 2, 1), synth.Stage(1, 3, 4)]),
+             (synth.make_geometry(96, 50, 144, batch=1), [synth.Stage(2, 3, 2), synth.Stage(1, 2, 1)])]
+    base = []
+    for k, (g, stages) in enumerate(specs):
+        plan = pnp.Plan(g)
+        if tile:
+            plan.set_launch_shapes(tile=tile)
+        x, b, eta, seq = make_problem(g, stages, 40 + k)
+        base.append((plan, stages, eta, seq, dev(b), dev(x), x, b))
+    outs = []
+    for persistent, graph in ((False, False), (True, False), (True, True), (True, True)):
+        probs = [dict(plan=plan, stages=st, eta=eta, seq=seq, b=b, x=torch.zeros(plan.g.batch, plan.g.n, plan.g.n,
+                                                                                  device="cuda"), xtrue=xt)
+                 for plan, st, eta, seq, b, xt, _, _ in base]
+        logs = pnp.run_many(probs, lam=0.02, tv_iters=12, persistent=persistent, graph=graph)
+        outs.append(([host(p["x"]) for p in probs], [np.asarray(l) for l in logs]))
+    for run in outs[1:]:
+        for k in range(len(specs)):
+            assert np.array_equal(outs[0][0][k], run[0][k]), k
+            assert np.array_equal(outs[0][1][k], run[1][k]), k
+    plan, stages, eta, seq, _, _, x, b = base[0]
+    rx, _ = oracle_runs(plan.g, stages, eta, seq, b, x, 0.02, tv_iters=12)
+    assert rel(outs[1][0][0], rx) < TOL_RECON
+
+
+def test_persistent_single_problem_run():
+    """pnp_run with PNP_RUN_PERSISTENT on a 16-image class (batched gather,
+    interleaved forward, strips): the bits of the direct launches."""
+    import torch
+    g = synth.make_geometry(128, 60, 192, batch=16)
+    stages = [synth.Stage(2, 2, 4), synth.Stage(1, 3, 4)]
+    rng = np.random.default_rng(16)
+    b = dev(rng.standard_normal((16, 60, 192)))
+    plan = pnp.Plan(g)
+    plan.set_launch_shapes(back=((16 << 16) | (1 << 8) | 8,) * 4, tile=2)
+    outs = []
+    for persistent in (False, True):
+        d_x = torch.zeros(16, 128, 128, device="cuda")
+        plan.run(stages, [1e-4, 1e-4], [0, 1, 2, 3, 0], b, d_x, lam=0.02, tv_iters=20, persistent=persistent)
+        outs.append(host(d_x))
+    assert np.array_equal(outs[0], outs[1])

@@ -95,6 +95,7 @@ def test_binding_constants_match_the_header():
     pairs = {"PNP_SKETCH_POOL": N.SKETCH_POOL, "PNP_SKETCH_BICUBIC": N.SKETCH_BICUBIC,
              "PNP_EST_MINIBATCH": N.EST_MINIBATCH, "PNP_EST_SVRG": N.EST_SVRG, "PNP_EST_SAGA": N.EST_SAGA,
              "PNP_RUN_GRAPH": N.RUN_GRAPH, "PNP_RUN_KERNEL_TIMES": N.RUN_KERNEL_TIMES,
+             "PNP_RUN_PERSISTENT": N.RUN_PERSISTENT,
              "PNP_BACK_TILE4": N.BACK_TILE4, "PNP_BACK_SCATTER": N.BACK_SCATTER, "PNP_BACK_TABLE": N.BACK_TABLE,
              "PNP_MAX_LOG_ITERS": N.MAX_LOG_ITERS, "PNP_NOALLOC_SCRATCH_BYTES": N.NOALLOC_SCRATCH_BYTES,
              "PNP_N_PHASES": len(N.PHASES)}
