@@ -53,22 +53,22 @@ FLOP_PER_PIXEL_ITER = 24
 # while the kernel's source is the one that was measured (else null).  Units: one
 # launch of the projector kernels (the forward's figure weighted over the
 # schedule's 24 / 24 / 72 launches at the 4x / 2x / full levels, whose captured
-# launches move 8.3 / 21.0 / 81.2 MB), one denoise (two launches) of the FGP strips.
+# launches move 8.3 / 21.0 / 81.7 MB), one denoise (two launches) of the FGP strips.
 KERNEL_TRAFFIC = {
-    "backward": {"bytes_per_unit": 20120269, "unit": "launch", "source": "projector.cu",
+    "backward": {"bytes_per_unit": 20119040, "unit": "launch", "source": "projector.cu",
                  "begin": "struct BackTable {",
                  "end": "// ------------------------------------------------------------------ transpose A_s^T from a stored table",
-                 "sha256": "c78e03f76b65ec7b86043f9c728828bf485de3e0a29827b0539a41bab277aa7a",
+                 "sha256": "2f8fa2711e611cb611aff4100728e2c28dd89026404b31e1d60ae795b95014e8",
                  "profile": "profiles/k_backward_batch_512x16_720x768.md"},
-    "forward": {"bytes_per_unit": 54566502, "unit": "launch", "source": "projector.cu",
+    "forward": {"bytes_per_unit": 54855782, "unit": "launch", "source": "projector.cu",
                 "begin": "// Forward projector on an image-interleaved coefficient image.",
                 "end": "// ------------------------------------------------------------------ transpose A_s^T\n// Pixel-driven gather.",
-                "sha256": "c4482dca11e7fd288c290417344cddc0d7e2ef23f0f818d8d30bc222cba75bd9",
+                "sha256": "8200a95fafaaef7a9f5ffe6ae83b6eeeea278d83369f712a07bd979f85925580",
                  "profile": "profiles/k_forward_il_512x16_720x768.md"},
-    "denoise": {"bytes_per_unit": 125760512, "unit": "denoise (two launches)", "source": "tv.cu",
+    "denoise": {"bytes_per_unit": 126000128, "unit": "denoise (two launches)", "source": "tv.cu",
                 "begin": "// ------------------------------------------------------------------ register-resident FGP strips",
                 "end": "inline cudaError_t counted(cudaError_t e = cudaGetLastError())",
-                "sha256": "9fda072952e44442802b8c27f4cdf61bbf81576b0140ae96a9742ee2ab19a05f",
+                "sha256": "e20a75d6f0fd5609643ab084cd3afa299298d80e8eb1646c7c4f2756ace31cd4",
                  "profile": "profiles/k_tv_strip_512x16.md"},
 }
 
