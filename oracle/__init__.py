@@ -22,6 +22,9 @@ Parity status per function (what pins it, see ``tests/test_oracle_pins.py``):
   pnp_run                 pinned for one and four iterations against a dense
                            restatement of Algorithm 1; longer trajectories rest
                            on those step identities
+  subset_sequence         pinned (published SplitMix64 outputs; every epoch a
+                           permutation; uniform over all P! orders; one stream
+                           across stages)
   sample_count            pinned exactly (closed forms for an axis ray, with
                            samples on the box edge, and a diagonal ray; the
                            chord-interval count of every ray of a full geometry)
@@ -108,6 +111,10 @@ def _load():
             lib.orc_power_iter_wk.restype = C.c_double
             lib.orc_keys.argtypes = [C.c_double]
             lib.orc_keys.restype = C.c_double
+            lib.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
+            lib.orc_splitmix64.restype = C.c_uint64
+            lib.orc_subset_sequence.argtypes = [C.c_int, ip, C.c_uint64, ip]
+            lib.orc_subset_sequence.restype = C.c_long
             lib.orc_bicubic_down.argtypes = [C.c_int, C.c_int, dp, dp]
             lib.orc_bicubic_up.argtypes = [C.c_int, C.c_int, dp, dp]
             lib.orc_power_iter_w.argtypes = [gp, C.c_int, dp, C.c_int, C.c_double, ip]
@@ -254,13 +261,36 @@ def psnr(x, xt) -> float:
     return float(_load().orc_psnr(x.size, _dp(x), _dp(xt)))
 
 
+def _stage_ints(stages) -> np.ndarray:
+    """Stages as 5 ints each: factor, iters, n_subsets, kind, estimator."""
+    return np.ascontiguousarray(np.array([[s.factor, s.iters, s.n_subsets, getattr(s, "kind", 0),
+                                           getattr(s, "estimator", 0)]
+                                          if hasattr(s, "factor") else (list(s) + [0, 0])[:5]
+                                          for s in stages], dtype=np.int32).ravel())
+
+
+def splitmix64(seed: int, t: int) -> int:
+    """The t-th number (t >= 1) of the SplitMix64 stream with this seed
+    (Steele, Lea & Flood 2014), the generator of the subset order."""
+    return int(_load().orc_splitmix64(seed & (2**64 - 1), t))
+
+
+def subset_sequence(stages: Sequence, seed: int) -> np.ndarray:
+    """Subset id of every iteration of Algorithm 1's schedule: per stage with
+    P > 1 subsets, one uniform permutation of the subsets per epoch of P
+    iterations (Fisher-Yates on a seeded SplitMix64 stream); zeros for P = 1.
+    The minibatch of each iteration is drawn at random (Sec. 2, Eq. 6-7)."""
+    st = _stage_ints(stages)
+    out = np.zeros(max(int(sum(st[1::5])), 1), np.int32)
+    n = _load().orc_subset_sequence(len(st) // 5, st.ctypes.data_as(C.POINTER(C.c_int)),
+                                    seed & (2**64 - 1), out.ctypes.data_as(C.POINTER(C.c_int)))
+    return out[:n]
+
+
 def pnp_run(g, stages: Sequence, eta: Sequence[float], seq, b, x0=None, *, alpha: float = 1.0,
             lam: float = 0.02, tv_iters: int = 20, momentum: bool = True, xt=None, w=None):
     """Algorithm 1 on one image; returns (x, psnr_log or None)."""
-    st = np.ascontiguousarray(np.array([[s.factor, s.iters, s.n_subsets, getattr(s, "kind", 0),
-                                          getattr(s, "estimator", 0)]
-                                         if hasattr(s, "factor") else (list(s) + [0, 0])[:5]
-                                         for s in stages], dtype=np.int32).ravel())
+    st = _stage_ints(stages)
     total = int(sum(st[1::5]))
     seq = np.ascontiguousarray(np.asarray(seq, dtype=np.int32))
     if seq.size < total:

@@ -38,8 +38,13 @@
  *   subsets  subset p of P holds views v = p, p+P, p+2P, ...; its sinogram rows
  *            are those views in increasing order; the minibatch gradient is
  *            scaled by P so that its mean over p is the full gradient.
+ *   order    the minibatch of each iteration is drawn at random (Sec. 2, the
+ *            stochastic gradient of Eq. 6-7); read as sampling the P subsets
+ *            without replacement within each epoch of P iterations (a fresh
+ *            uniform permutation per epoch), from a seeded SplitMix64 stream.
  */
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
@@ -829,6 +834,65 @@ void orc_step_vjp(const orc_geom *g, int s, int p, int P, double eta, double alp
     orc_grad(g, s, zbar, zero, gr, p, P);
     for (size_t i = 0; i < N; ++i) ybar_in[i] = zbar[i] - eta * gr[i];
     free(gr); free(z); free(xt); free(dz); free(zbar); free(zero);
+}
+
+/* Subset order of Algorithm 1's minibatches.
+ *
+ * Random numbers: SplitMix64 (Steele, Lea & Flood, "Fast splittable
+ * pseudorandom number generators", OOPSLA 2014), used as a counter-based
+ * generator: the t-th number (t = 1, 2, ...) of the stream with seed `seed` is
+ * the 64-bit finaliser applied to seed + t * gamma, gamma = 0x9e3779b97f4a7c15. */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t t)
+{
+    uint64_t z = seed + t * 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+/* A uniform integer in [0, m), m >= 1, from the stream: take the next number u,
+ * discard it while u < 2^64 mod m (so that the accepted range is a whole number
+ * of copies of [0, m)), and return u mod m.  *t counts the numbers taken. */
+static uint32_t orc_uniform_below(uint64_t seed, uint64_t *t, uint32_t m)
+{
+    uint64_t reject_below = (0 - (uint64_t)m) % (uint64_t)m;   /* 2^64 mod m */
+    for (;;) {
+        *t += 1;
+        uint64_t u = orc_splitmix64(seed, *t);
+        if (u >= reject_below) return (uint32_t)(u % m);
+    }
+}
+
+/* The subset id of every iteration of the schedule (stages as orc_pnp_run
+ * takes them: 5 ints per stage, {factor, iters, n_subsets, kind, estimator}).
+ * Stages in order; a stage with P = n_subsets > 1 runs in epochs of P
+ * iterations, each epoch visiting the subsets in the order of a new uniform
+ * permutation of 0..P-1 (the last epoch of the stage, when shorter, takes the
+ * first entries of its permutation); a stage with P = 1 contributes zeros and
+ * draws nothing.  A permutation is Durstenfeld's form of the Fisher-Yates
+ * shuffle (Knuth, TAOCP vol. 2, Algorithm 3.4.2P) of the identity: for
+ * j = P-1 down to 1, swap entry j with entry r, r uniform in [0, j].  One
+ * stream serves the whole schedule, its counter running on across epochs and
+ * stages.  Writes sum(iters) entries to seq and returns that count. */
+long orc_subset_sequence(int n_stages, const int *stages, uint64_t seed, int *seq)
+{
+    uint64_t t = 0;
+    long i = 0;
+    for (int k = 0; k < n_stages; ++k) {
+        int iters = stages[5 * k + 1], P = stages[5 * k + 2];
+        int *perm = (int *)malloc(sizeof(int) * (size_t)(P > 0 ? P : 1));
+        for (int done = 0; done < iters;) {
+            if (P <= 1) { seq[i++] = 0; ++done; continue; }
+            for (int a = 0; a < P; ++a) perm[a] = a;
+            for (int j = P - 1; j >= 1; --j) {
+                int r = (int)orc_uniform_below(seed, &t, (uint32_t)(j + 1));
+                int tmp = perm[j]; perm[j] = perm[r]; perm[r] = tmp;
+            }
+            for (int a = 0; a < P && done < iters; ++a, ++done) seq[i++] = perm[a];
+        }
+        free(perm);
+    }
+    return i;
 }
 
 /* Threads of the OpenMP loops (timing only; results do not depend on it). */

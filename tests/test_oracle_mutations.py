@@ -58,6 +58,16 @@ MUTATIONS = [
      "double H = (0.5 * ns) * s, delta = g->step * s;"),
     ("sample-count box edge included", "if (fabs(qx) < H && fabs(qy) < H) count += 1.0;",
      "if (fabs(qx) <= H && fabs(qy) <= H) count += 1.0;"),
+    ("splitmix64 finaliser shift", "z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;",
+     "z = (z ^ (z >> 31)) * 0xbf58476d1ce4e5b9ull;"),
+    ("shuffle draws below j (cyclic orders only)",
+     "int r = (int)orc_uniform_below(seed, &t, (uint32_t)(j + 1));",
+     "int r = (int)orc_uniform_below(seed, &t, (uint32_t)j);"),
+    ("stream restarts at every stage", "        int *perm = (int *)malloc(sizeof(int) * (size_t)(P > 0 ? P : 1));",
+     "        int *perm = (int *)malloc(sizeof(int) * (size_t)(P > 0 ? P : 1)); t = 0;"),
+    ("naive shuffle over the whole range",
+     "int r = (int)orc_uniform_below(seed, &t, (uint32_t)(j + 1));",
+     "int r = (int)orc_uniform_below(seed, &t, (uint32_t)P);"),
     ("weights on the wrong views", "res[(long)vs * g->n_det + j] *= w[(long)(first + vs * step) * g->n_det + j];",
      "res[(long)vs * g->n_det + j] *= w[(long)vs * g->n_det + j];"),
 ]

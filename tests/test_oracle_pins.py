@@ -871,3 +871,73 @@ def test_bicubic_gradient_and_step_size():
     lmax = np.linalg.eigvalsh(M.T @ M).max()
     L, _ = oracle.power_iter(g, 2, 3000, 1e-14, kind=1)
     assert abs(L - lmax) < 1e-8 * lmax
+
+
+# ---------------------------------------------------------------- subset order
+def test_splitmix64_published_outputs():
+    """The subset order draws from SplitMix64: its first numbers from seed 0 are
+    the published ones."""
+    with open(os.path.join(GOLDEN, "splitmix64.json")) as f:
+        ref = json.load(f)
+    for case in ref["streams"]:
+        got = [oracle.splitmix64(case["seed"], t) for t in range(1, len(case["outputs"]) + 1)]
+        assert got == [int(h, 16) for h in case["outputs"]]
+
+
+def test_subset_sequence_epochs_are_permutations():
+    """Sec. 2 draws each minibatch at random; the reading samples the P subsets
+    without replacement per epoch: every full epoch is a permutation of 0..P-1,
+    a shorter last epoch has distinct ids, a stage with P = 1 gives zeros."""
+    stages = [synth.Stage(4, 29, 12), synth.Stage(2, 5, 1), synth.Stage(1, 10, 7), synth.Stage(1, 0, 5)]
+    seq = oracle.subset_sequence(stages, 123)
+    assert seq.size == 44
+    a, z, c = seq[:29], seq[29:34], seq[34:]
+    for e in range(2):
+        assert sorted(a[12 * e:12 * e + 12]) == list(range(12))
+    assert len(set(a[24:])) == 5 and all(0 <= v < 12 for v in a[24:])
+    assert (z == 0).all()
+    assert sorted(c[:7]) == list(range(7))
+    assert len(set(c[7:])) == 3 and all(0 <= v < 7 for v in c[7:])
+    assert oracle.subset_sequence([synth.Stage(1, 0, 4)], 1).size == 0
+
+
+def test_subset_sequence_uniform_over_orders():
+    """Each epoch's order is uniform over all P! permutations (Fisher-Yates):
+    chi-square over many seeds, for P = 3 and P = 4.  Thresholds sit near the
+    1e-5 tail of the chi-square law with P! - 1 degrees of freedom; a shuffle
+    that draws from the wrong range (cyclic orders only, or the naive shuffle)
+    lands far beyond them."""
+    for P, seeds, limit in ((3, 6000, 28.0), (4, 12000, 62.0)):
+        counts = {}
+        for s in range(seeds):
+            key = tuple(oracle.subset_sequence([synth.Stage(1, P, P)], s))
+            counts[key] = counts.get(key, 0) + 1
+        assert len(counts) == math.factorial(P)
+        expect = seeds / math.factorial(P)
+        chi2 = sum((c - expect) ** 2 / expect for c in counts.values())
+        assert chi2 < limit, (P, chi2)
+
+
+def test_subset_sequence_two_subsets_follow_the_stream():
+    """P = 2: an epoch's one draw r is uniform in {0, 1} (2^64 mod 2 = 0, no
+    rejection); the epoch is (0, 1) when r = 1 (the swap of entry 1 with
+    itself) and (1, 0) when r = 0, r being the stream's next number mod 2."""
+    seed = 0
+    seq = oracle.subset_sequence([synth.Stage(1, 16, 2)], seed)
+    for e in range(8):
+        r = oracle.splitmix64(seed, e + 1) % 2
+        assert tuple(seq[2 * e:2 * e + 2]) == ((0, 1) if r == 1 else (1, 0))
+
+
+def test_subset_sequence_one_stream_across_stages():
+    """One stream serves the whole schedule: splitting a stage at an epoch
+    boundary, or putting a P = 1 stage (which draws nothing) between the
+    halves, leaves the sequence unchanged; two epochs are not copies of each
+    other; different seeds give different orders."""
+    whole = oracle.subset_sequence([synth.Stage(1, 36, 12)], 77)
+    split = oracle.subset_sequence([synth.Stage(2, 12, 12), synth.Stage(1, 24, 12)], 77)
+    gap = oracle.subset_sequence([synth.Stage(2, 12, 12), synth.Stage(2, 5, 1), synth.Stage(1, 24, 12)], 77)
+    assert (whole == split).all()
+    assert (gap[:12] == whole[:12]).all() and (gap[12:17] == 0).all() and (gap[17:] == whole[12:]).all()
+    assert not (whole[:12] == whole[12:24]).all()
+    assert not (whole == oracle.subset_sequence([synth.Stage(1, 36, 12)], 78)).all()
