@@ -108,6 +108,8 @@ typedef struct {
     int32_t tv_iters;   /* FGP iterations of D (Beck & Teboulle 2009); 0 = identity */
     int32_t momentum;   /* 0: a_i = 0 (Eq. 5); 1: a_i = (i-1)/(i+3) (Sec. 3) */
     int32_t flags;      /* PNP_RUN_* bits */
+    uint64_t subset_seed; /* seed of the subset order of problems given without a
+                             subset sequence (pnp_subset_sequence) */
 } pnp_run_params;
 
 /* pnp_run / pnp_run_many: capture the whole launch sequence as a CUDA graph the
@@ -145,7 +147,7 @@ typedef struct {
     const pnp_stage* stages;
     int32_t n_stages;
     const double* h_eta;          /* [n_stages], or NULL: eta_k = 1/L_k as pnp_step_sizes computes it */
-    const int32_t* h_subset_seq;  /* [sum iters], may be NULL when no stage uses subsets */
+    const int32_t* h_subset_seq;  /* [sum iters], or NULL: pnp_subset_sequence(params.subset_seed) */
     const float* d_b;             /* [batch][n_views][n_det] */
     float* d_x;                   /* in: x_0, out: x */
     const float* d_xtrue;         /* optional, with h_psnr_log */
@@ -286,12 +288,32 @@ int pnp_step_sizes(const pnp_geom* g, const pnp_stage* stages, int n_stages, dou
 int pnp_schedule(const pnp_stage* stages, int n_stages, const int32_t* h_subset_seq, int momentum,
                  int32_t* h_stage, int32_t* h_subset, float* h_amom, int64_t capacity, int64_t* h_total);
 
+/* The subset order of Algorithm 1's minibatches (Sec. 2: each iteration's
+ * minibatch is drawn at random, Eq. 6-7), read as sampling the P angle subsets
+ * without replacement per epoch.  Writes the subset id of every iteration
+ * i = 1..T (T = sum of the stages' iters, written to *h_total) to h_seq[i-1]:
+ * stage by stage, a stage with P = n_subsets > 1 runs in epochs of P
+ * iterations, each a uniform permutation of 0..P-1 (a shorter last epoch takes
+ * the first entries of its permutation); a stage with P = 1 gives zeros.
+ * Permutation: Durstenfeld's Fisher-Yates shuffle of the identity, for
+ * j = P-1 down to 1 swapping entries j and r, r uniform in [0, j].  Uniform
+ * integers in [0, m): the next number u of a SplitMix64 stream (Steele, Lea &
+ * Flood 2014: the t-th number, t = 1, 2, ..., is SplitMix64's finaliser of
+ * seed + t * 0x9e3779b97f4a7c15), redrawn while u < 2^64 mod m, taken mod m.
+ * One stream serves the whole schedule.  h_seq holds `capacity` entries (it
+ * may be NULL with capacity 0 to ask for T); PNP_EINVAL (with *h_total set)
+ * when T exceeds it or a stage has iters < 0 or n_subsets < 1.
+ * Host only; launches nothing. */
+int pnp_subset_sequence(const pnp_stage* stages, int n_stages, uint64_t seed, int32_t* h_seq, int64_t capacity,
+                        int64_t* h_total);
+
 /* Algorithm 1 (PnP-MS2G) on every image of the batch.
  *   stages[n_stages]   the schedule; h_eta[n_stages] step sizes eta_k, or NULL
  *                      for eta_k = 1/L_k from pnp_step_sizes (the first run
  *                      that needs a level's L then synchronises `stream`)
- *   h_subset_seq       subset id of every iteration (length sum iters); may be
- *                      NULL when every stage has n_subsets == 1
+ *   h_subset_seq       subset id of every iteration (length sum iters), or
+ *                      NULL for the order pnp_subset_sequence draws from
+ *                      params->subset_seed
  *   params             alpha, lambda, tv_iters, momentum
  *   d_b                data [batch][n_views][n_det]
  *   d_x                in: x_0 (= y_0), out: x after the last iteration
@@ -313,8 +335,9 @@ int pnp_run(const pnp_geom* g, const pnp_stage* stages, int n_stages, const doub
  * ONE launch covering up to 4 classes that are still iterating (more classes:
  * one launch per phase for each group of 4, in class order); classes may have
  * schedules of different lengths; iteration i of every class uses the same
- * momentum a_i and params.  Workspaces and outputs must be distinct per
- * class.  Synchronous only when some class logs PSNR.  PNP_EUNSUPPORTED for
+ * momentum a_i and params.  A class given without a subset sequence takes
+ * the order pnp_subset_sequence draws for its stages from params->subset_seed.
+ * Workspaces and outputs must be distinct per class.  Synchronous only when some class logs PSNR.  PNP_EUNSUPPORTED for
  * more than 1024 classes.
  * Checkpoint/resume: a class with start_iter = k continues Algorithm 1 from
  * iteration k + 1 with d_x = x_k and d_y = y_k (both returned by an earlier run

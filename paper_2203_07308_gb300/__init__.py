@@ -10,6 +10,6 @@ from ._native import (  # noqa: F401
     Geom, Plan, PnpError, backproject, full_grad, full_grad_noalloc,
     header_functions, kernel_times, launch_count, last_error, load,
     objective, onchip_bandwidth, power_iter, project, run, run_many, autotune, sample_count, schedule, setup,
-    sketch, sketch_grad, step_sizes, subset_views,
+    sketch, sketch_grad, step_sizes, subset_sequence, subset_views,
     tv_denoise, tv_workspace_size, upsample, vr_buffer_size, workspace_size,
 )

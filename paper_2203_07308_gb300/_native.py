@@ -61,7 +61,7 @@ EST_MINIBATCH, EST_SVRG, EST_SAGA = 0, 1, 2
 
 class RunParams(C.Structure):
     _fields_ = [("alpha", C.c_float), ("lambda_", C.c_float), ("tv_iters", C.c_int32),
-                ("momentum", C.c_int32), ("flags", C.c_int32)]
+                ("momentum", C.c_int32), ("flags", C.c_int32), ("subset_seed", C.c_uint64)]
 
 
 RUN_GRAPH = 1
@@ -149,6 +149,8 @@ def load(path: Optional[str] = None):
             "pnp_step_sizes": [gp, C.POINTER(StageC), i32, dp, vp, vp],
             "pnp_schedule": [C.POINTER(StageC), i32, C.POINTER(C.c_int32), i32, C.POINTER(C.c_int32),
                              C.POINTER(C.c_int32), C.POINTER(C.c_float), C.c_int64, C.POINTER(C.c_int64)],
+            "pnp_subset_sequence": [C.POINTER(StageC), i32, C.c_uint64, C.POINTER(C.c_int32), C.c_int64,
+                                    C.POINTER(C.c_int64)],
             "pnp_onchip_bandwidth": [vp, sz, dp, vp],
         }
         for name, args in sig.items():
@@ -340,6 +342,29 @@ def schedule(stages, seq=None, momentum=True):
     return stage[:n.value], subset[:n.value], amom[:n.value]
 
 
+def subset_sequence(stages, seed=0):
+    """pnp_subset_sequence: the subset id of every iteration, one Fisher-Yates
+    permutation of the stage's subsets per epoch drawn from a SplitMix64 stream
+    with this seed (zeros for stages without subsets); int32 array."""
+    st = _stages(stages)
+    out = np.zeros(max(sum(a.iters for a in st), 1), dtype=np.int32)
+    n = C.c_int64(0)
+    _check(load().pnp_subset_sequence(st, len(st), int(seed) & (2**64 - 1),
+                                      out.ctypes.data_as(C.POINTER(C.c_int32)), out.size, C.byref(n)))
+    return out[:n.value]
+
+
+def _seq_ptr(seq, total):
+    """The caller's subset sequence as an int32 array and pointer; (None, None)
+    when there is none (the library then draws the seeded order)."""
+    if seq is None:
+        return None, None
+    seq_np = np.ascontiguousarray(np.asarray(seq, dtype=np.int32))
+    if seq_np.size < total:
+        raise PnpError(PNP_EINVAL, "subset sequence shorter than the schedule")
+    return seq_np, seq_np.ctypes.data_as(C.POINTER(C.c_int32))
+
+
 def onchip_bandwidth(device="cuda", stream=None) -> dict:
     """pnp_onchip_bandwidth: measured L2, L1 and shared-memory read bandwidth (GB/s)."""
     import torch
@@ -355,9 +380,12 @@ def _flags(graph, kernel_times, persistent=False):
 
 
 def run(g, stages, eta, seq, b, x, *, alpha=1.0, lam=0.02, tv_iters=20, momentum=True,
-        xtrue=None, ws=None, stream=None, graph=False, kernel_times=False, persistent=False):
+        xtrue=None, ws=None, stream=None, graph=False, kernel_times=False, persistent=False,
+        subset_seed=0):
     """Algorithm 1; x holds x_0 on entry and the result on return.  eta: step
-    size per stage, or None for eta_k = 1/L_k computed by the library.  Returns the
+    size per stage, or None for eta_k = 1/L_k computed by the library.  seq: the
+    subset id of every iteration, or None for the library's order drawn from
+    subset_seed (subset_sequence).  Returns the
     PSNR log [total_iters, batch] when xtrue is given, else None.  graph=True
     captures the launch sequence once per distinct call and replays it;
     kernel_times=True brackets each phase launch with CUDA events (read them
@@ -365,15 +393,13 @@ def run(g, stages, eta, seq, b, x, *, alpha=1.0, lam=0.02, tv_iters=20, momentum
     st = _stages(stages)
     total = sum(a.iters for a in st)
     eta_a = None if eta is None else (C.c_double * len(st))(*[float(e) for e in eta])
-    seq_np = np.ascontiguousarray(np.asarray(seq if seq is not None else np.zeros(total), dtype=np.int32))
-    if seq_np.size < total:
-        raise PnpError(PNP_EINVAL, "subset sequence shorter than the schedule")
+    seq_np, seq_p = _seq_ptr(seq, total)
     prm = RunParams(float(alpha), float(lam), int(tv_iters), int(bool(momentum)),
-                    _flags(graph, kernel_times, persistent))
+                    _flags(graph, kernel_times, persistent), int(subset_seed) & (2**64 - 1))
     img = g.batch * g.n * g.n
     log = np.zeros((total, g.batch)) if xtrue is not None else None
     _check(load().pnp_run(C.byref(geom(g)), st, len(st), eta_a,
-                          seq_np.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(prm),
+                          seq_p, C.byref(prm),
                           _ptr(b, g.batch * g.n_views * g.n_det, "b"), _ptr(x, img, "x"),
                           _ptr(xtrue, img, "xtrue", True),
                           log.ctypes.data_as(C.POINTER(C.c_double)) if log is not None else None,
@@ -592,11 +618,12 @@ def unrolled_step_vjp(g, factor, subset, n_subsets, eta, alpha, lam, tv_iters, a
 
 # ---------------------------------------------------------------- uneven batches, autotuning
 def run_many(problems, *, alpha=1.0, lam=0.02, tv_iters=20, momentum=True, stream=None, graph=False,
-             kernel_times=False, persistent=False):
+             kernel_times=False, persistent=False, subset_seed=0):
     """pnp_run_many.  ``problems``: list of dicts with keys plan, stages, eta, seq,
     b, x and optional xtrue, start_iter, y (checkpoint/resume: x and y of
-    iteration start_iter in, x and y of the last iteration out); returns the
-    list of PSNR logs (None where no xtrue)."""
+    iteration start_iter in, x and y of the last iteration out); a problem whose
+    seq is None takes the library's order drawn from subset_seed for its
+    stages.  Returns the list of PSNR logs (None where no xtrue)."""
     arr = (ProblemC * len(problems))()
     keep = []
     logs = []
@@ -607,21 +634,20 @@ def run_many(problems, *, alpha=1.0, lam=0.02, tv_iters=20, momentum=True, strea
         st = _stages(pr["stages"])
         total = sum(a.iters for a in st)
         eta_a = None if pr.get("eta") is None else (C.c_double * len(st))(*[float(e) for e in pr["eta"]])
-        seq = pr.get("seq")
-        seq_np = np.ascontiguousarray(np.asarray(seq if seq is not None else np.zeros(total), dtype=np.int32))
+        seq_np, seq_p = _seq_ptr(pr.get("seq"), total)
         img = g.batch * g.n * g.n
         xt = pr.get("xtrue")
         log = np.zeros((total, g.batch)) if xt is not None else None
         keep += [st, eta_a, seq_np, log]
         logs.append(log)
-        arr[k] = ProblemC(geom(g), st, len(st), eta_a, seq_np.ctypes.data_as(C.POINTER(C.c_int32)),
+        arr[k] = ProblemC(geom(g), st, len(st), eta_a, seq_p,
                           _ptr(pr["b"], g.batch * g.n_views * g.n_det, "b"), _ptr(pr["x"], img, "x"),
                           _ptr(xt, img, "xtrue", True),
                           log.ctypes.data_as(C.POINTER(C.c_double)) if log is not None else None,
                           _ws(plan.ws)[0], int(pr.get("start_iter", 0)),
                           _ptr(pr.get("y"), img, "y", True))
     prm = RunParams(float(alpha), float(lam), int(tv_iters), int(bool(momentum)),
-                    _flags(graph, kernel_times, persistent))
+                    _flags(graph, kernel_times, persistent), int(subset_seed) & (2**64 - 1))
     _check(load().pnp_run_many(arr, len(problems), C.byref(prm), _stream(stream)))
     return logs
 

@@ -115,11 +115,13 @@ class UnrolledStep(torch.autograd.Function):
 
 
 def unrolled_pnp(plan, stages: Sequence, eta, seq, b, x0, lam, *, alpha: float = 1.0,
-                 tv_iters: int = 20, momentum: bool = True, keep_z: bool = True):
+                 tv_iters: int = 20, momentum: bool = True, keep_z: bool = True, subset_seed: int = 0):
     """x_T of Algorithm 1 as a differentiable function of x0 (float32 CUDA
     tensor [batch, n, n]) and lam (a float64 scalar tensor, may require grad).
     eta: step size per stage, or None for the library's eta_k = 1/L_k
-    (pnp_step_sizes).  The walk over iterations (stage, subset, momentum a_i)
+    (pnp_step_sizes).  seq: the subset id of every iteration, or None for the
+    library's order drawn from subset_seed (pnp_subset_sequence, as pnp_run
+    draws it).  The walk over iterations (stage, subset, momentum a_i)
     comes from pnp_schedule.  keep_z: keep each iteration's gradient step z for
     the backward pass (one projector pair fewer per iteration); False keeps only
     y and recomputes z."""
@@ -127,6 +129,8 @@ def unrolled_pnp(plan, stages: Sequence, eta, seq, b, x0, lam, *, alpha: float =
     if eta is None:
         eta = plan.step_sizes(stages)
     st = _native._stages(stages)
+    if seq is None:
+        seq = _native.subset_sequence(stages, subset_seed)
     stage_of, subset_of, amom_of = _native.schedule(stages, seq, momentum)
     vjp_ws = torch.empty(_native.vjp_workspace_size(g, tv_iters), dtype=torch.uint8, device=x0.device)
     y = x0

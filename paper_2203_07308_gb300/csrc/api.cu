@@ -1049,6 +1049,62 @@ float momentum_coef(long i, int momentum)
     return momentum ? (float)((double)(i - 1) / (double)(i + 3)) : 0.0f;
 }
 
+namespace {
+
+// Counter-based SplitMix64 (Steele, Lea & Flood 2014): number t of the stream is
+// the generator's finaliser applied to seed + t * golden gamma.
+class SplitMixStream {
+public:
+    explicit SplitMixStream(uint64_t seed) : seed_(seed) {}
+    uint64_t next()
+    {
+        ++count_;
+        uint64_t x = seed_ + count_ * 0x9e3779b97f4a7c15ull;
+        x ^= x >> 30;
+        x *= 0xbf58476d1ce4e5b9ull;
+        x ^= x >> 27;
+        x *= 0x94d049bb133111ebull;
+        return x ^ (x >> 31);
+    }
+    // uniform in [0, m): redraw the numbers below 2^64 mod m, then reduce
+    uint32_t below(uint32_t m)
+    {
+        const uint64_t lo = (~(uint64_t)0 - (uint64_t)m + 1) % m;  // (2^64 - m) mod m = 2^64 mod m
+        uint64_t u;
+        do u = next(); while (u < lo);
+        return (uint32_t)(u % m);
+    }
+private:
+    uint64_t seed_;
+    uint64_t count_ = 0;
+};
+
+}  // namespace
+
+// The subset order of a schedule: per stage with P > 1, a Fisher-Yates
+// permutation of the subsets per epoch of P iterations; zeros where P = 1.
+void subset_order(const pnp_stage* stages, int n_stages, uint64_t seed, int32_t* out)
+{
+    SplitMixStream rng(seed);
+    std::vector<int32_t> perm;
+    for (int k = 0; k < n_stages; ++k) {
+        const int P = stages[k].n_subsets, T = stages[k].iters;
+        if (P <= 1) {
+            std::fill(out, out + T, 0);
+            out += T;
+            continue;
+        }
+        perm.resize((size_t)P);
+        for (int first = 0; first < T; first += P) {
+            for (int a = 0; a < P; ++a) perm[(size_t)a] = a;
+            for (int j = P - 1; j > 0; --j) std::swap(perm[(size_t)j], perm[rng.below((uint32_t)j + 1)]);
+            const int take = std::min(P, T - first);
+            std::copy(perm.begin(), perm.begin() + take, out);
+            out += take;
+        }
+    }
+}
+
 }  // namespace pnp
 
 extern "C" {
@@ -1109,6 +1165,25 @@ int pnp_schedule(const pnp_stage* stages, int n_stages, const int32_t* h_subset_
             h_subset[i] = p;
             h_amom[i] = momentum_coef((long)(i + 1), momentum);
         }
+    return PNP_OK;
+}
+
+int pnp_subset_sequence(const pnp_stage* stages, int n_stages, uint64_t seed, int32_t* h_seq, int64_t capacity,
+                        int64_t* h_total)
+{
+    t_err.clear();
+    if (!stages || n_stages < 1 || !h_total) return fail(PNP_EINVAL, "stages and h_total are required");
+    int64_t total = 0;
+    for (int k = 0; k < n_stages; ++k) {
+        if (stages[k].iters < 0) return fail(PNP_EINVAL, "stage %d has negative iterations", k);
+        if (stages[k].n_subsets < 1) return fail(PNP_EINVAL, "stage %d: n_subsets < 1", k);
+        total += stages[k].iters;
+    }
+    *h_total = total;
+    if (total > capacity) return fail(PNP_EINVAL, "schedule has %lld iterations, capacity %lld", (long long)total,
+                                      (long long)capacity);
+    if (total > 0 && !h_seq) return fail(PNP_EINVAL, "h_seq is NULL");
+    subset_order(stages, n_stages, seed, h_seq);
     return PNP_OK;
 }
 
@@ -1192,6 +1267,23 @@ int run_many_impl(const pnp_problem* pb_in, int np, const pnp_run_params* params
     // workspace; the first computation of a level's L synchronises the stream)
     std::vector<pnp_problem> pbv(pb_in, pb_in + np);
     std::vector<std::vector<double>> etas((size_t)np);
+    // problems without a subset sequence get the seeded order of their stages
+    std::vector<std::vector<int32_t>> seqs((size_t)np);
+    for (int c = 0; c < np; ++c) {
+        pnp_problem& q = pbv[c];
+        if (q.h_subset_seq || !q.stages || q.n_stages < 1) continue;
+        int64_t total = 0;
+        bool any_subsets = false;
+        for (int k = 0; k < q.n_stages; ++k) {
+            if (q.stages[k].iters < 0 || q.stages[k].n_subsets < 1) { total = -1; break; }
+            total += q.stages[k].iters;
+            any_subsets |= q.stages[k].n_subsets > 1;
+        }
+        if (!any_subsets || total < 0 || total > (1L << 30)) continue;   // validate_problem reports these
+        seqs[c].resize((size_t)std::max<int64_t>(total, 1));
+        subset_order(q.stages, q.n_stages, params->subset_seed, seqs[c].data());
+        q.h_subset_seq = seqs[c].data();
+    }
     for (int c = 0; c < np; ++c) {
         pnp_problem& q = pbv[c];
         if (q.h_eta) continue;
@@ -1452,7 +1544,7 @@ int run_many_impl(const pnp_problem* pb_in, int np, const pnp_run_params* params
 
     Hasher h;
     h.val(np);
-    h.val(pr);
+    h.val(pr.alpha); h.val(pr.lambda); h.val(pr.tv_iters); h.val(pr.momentum); h.val(pr.flags);
     h.val(stream);
     for (int c = 0; c < np; ++c) {
         const pnp_problem& q = pb[c];

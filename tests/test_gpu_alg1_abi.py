@@ -1,7 +1,8 @@
 """Algorithm 1 wholly behind the C ABI: step sizes eta_k = 1/L_k computed by the
 library (Sec. 3: eta = O(1/L)) and the run without caller step sizes, checked
 against the FP64 oracle's L and against runs given the same step sizes; the
-unrolled form walking pnp_schedule."""
+unrolled form walking pnp_schedule; the seeded subset order drawn by the library
+(pnp_subset_sequence) when no sequence is given."""
 import numpy as np
 import pytest
 
@@ -119,3 +120,47 @@ def test_unrolled_without_step_sizes_equals_with_them():
         res.append((host(xT), host(x0.grad), float(lam.grad)))
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
     assert res[0][2] == res[1][2]
+
+
+def test_run_with_a_subset_seed_uses_the_seeded_order():
+    """With no subset sequence the library draws the order from params.subset_seed
+    (Sec. 2: the minibatch of each iteration is random): the same bits as a run
+    given the oracle's order for that seed, through pnp_run (with and without
+    graph capture), pnp_run_many and the unrolled form; within the
+    reconstruction tolerance of the oracle's run on that order; another seed
+    gives another reconstruction."""
+    import torch
+    from paper_2203_07308_gb300.autograd import unrolled_pnp
+    g = synth.make_geometry(64, 90, 96, batch=2)
+    plan = pnp.Plan(g)
+    stages = [synth.Stage(2, 5, 3), synth.Stage(1, 6, 4)]
+    seed = 2**63 + 5
+    seq_o = oracle.subset_sequence(stages, seed)
+    assert np.array_equal(pnp.subset_sequence(stages, seed), seq_o)
+    x_true = np.stack([synth.ellipse_phantom(64, 320 + i, (6, 9)) for i in range(2)])
+    b = oracle.project(g, 1, x_true[0]), oracle.project(g, 1, x_true[1])
+    b = np.stack([np.asarray(v, np.float32) for v in b]).astype(np.float64)
+    d_b = dev(b)
+    eta = plan.step_sizes(stages)
+    kw = dict(lam=0.02, tv_iters=20, momentum=True)
+    x = torch.zeros(2, 64, 64, device="cuda")
+    plan.run(stages, eta, seq_o, d_b, x, **kw)
+    ref = host(x)
+    for graph in (False, True):
+        x = torch.zeros(2, 64, 64, device="cuda")
+        plan.run(stages, eta, None, d_b, x, subset_seed=seed, graph=graph, **kw)
+        assert np.array_equal(host(x), ref), graph
+    x = torch.zeros(2, 64, 64, device="cuda")
+    pnp.run_many([dict(plan=plan, stages=stages, eta=eta, seq=None, b=d_b, x=x)], subset_seed=seed, **kw)
+    assert np.array_equal(host(x), ref)
+    x = torch.zeros(2, 64, 64, device="cuda")
+    plan.run(stages, eta, None, d_b, x, subset_seed=seed + 1, **kw)
+    assert not np.array_equal(host(x), ref)
+    xr, _ = oracle.pnp_run(g, stages, eta, seq_o, b[0], None, **kw)
+    assert np.linalg.norm(ref[0] - xr) / np.linalg.norm(xr) < 1e-4
+    x0 = torch.zeros(2, 64, 64, device="cuda")
+    lam = torch.tensor(0.02, dtype=torch.float64)
+    with torch.no_grad():
+        xa = unrolled_pnp(plan, stages, eta, None, d_b, x0, lam, subset_seed=seed)
+        xb = unrolled_pnp(plan, stages, eta, seq_o, d_b, x0, lam)
+    assert np.array_equal(host(xa), host(xb))

@@ -132,6 +132,30 @@ def test_schedule_walks_algorithm_1(lib):
     assert total.value == 5 and "capacity" in pnp.last_error()
 
 
+def test_subset_sequence_matches_the_oracle(lib):
+    """pnp_subset_sequence (host only) draws the same subset order as the
+    oracle's independent SplitMix64 / Fisher-Yates restatement, bit for bit, for
+    mixed schedules (P = 1 stages, short last epochs, P up to n_views) and
+    seeds including 2^64 - 1; counts and argument errors are reported."""
+    import oracle
+    cases = [([synth.Stage(4, 30, 12), synth.Stage(2, 7, 1), synth.Stage(1, 41, 8)], 7308),
+             ([synth.Stage(1, 100, 2)], 0),
+             ([synth.Stage(2, 13, 5), synth.Stage(1, 0, 9), synth.Stage(1, 400, 360)], 2**64 - 1),
+             ([synth.Stage(1, 5, 1)], 12345)]
+    for stages, seed in cases:
+        got = pnp.subset_sequence(stages, seed)
+        ref = oracle.subset_sequence(stages, seed)
+        assert got.dtype == np.int32 and np.array_equal(got, ref), (stages, seed)
+    total = C.c_int64(0)
+    arr = (_native.StageC * 2)(_native.StageC(1, 5, 3, 0, 0), _native.StageC(1, 4, 2, 0, 0))
+    assert lib.pnp_subset_sequence(arr, 2, 1, None, 0, C.byref(total)) == _native.PNP_EINVAL
+    assert total.value == 9 and "capacity" in pnp.last_error()
+    bad = (_native.StageC * 1)(_native.StageC(1, 5, 0, 0, 0))
+    assert lib.pnp_subset_sequence(bad, 1, 1, None, 0, C.byref(total)) == _native.PNP_EINVAL
+    with pytest.raises(pnp.PnpError):
+        pnp.subset_sequence([synth.Stage(1, -1, 2)], 3)
+
+
 def test_step_sizes_and_bandwidth_reject_bad_arguments(lib):
     g = _native.geom(synth.make_geometry(64, 90, 96))
     st = (_native.StageC * 1)(_native.StageC(3, 5, 1, 0, 0))
