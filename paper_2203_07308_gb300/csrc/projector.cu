@@ -108,6 +108,40 @@ __device__ __forceinline__ float pooled(const float* __restrict__ fine, int n, i
     return acc * (1.0f / (float)(s * s));
 }
 
+// pooled() read with one vector load per fine row (float2 / float4 for s = 2 /
+// 4), summed in pooled()'s order (rows outer, columns inner, from 0), so the
+// same bits.  `vec`: the fine image's base is aligned to the vector (the
+// offsets j s n + i s and image strides n^2 are multiples of s floats);
+// otherwise, and for other s, pooled() itself.
+__device__ __forceinline__ float pooled_rows(const float* __restrict__ fine, int n, int s, int ns, int i, int j,
+                                             bool vec)
+{
+    if (!vec || (s != 2 && s != 4)) return pooled(fine, n, s, ns, i, j);
+    if (i < 0 || j < 0 || i >= ns || j >= ns) return 0.0f;
+    const float* p = fine + (long)j * s * n + (long)i * s;
+    float acc = 0.0f;
+    if (s == 2) {
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const float2 v = __ldg(reinterpret_cast<const float2*>(p + (long)b * n));
+            acc += v.x;
+            acc += v.y;
+        }
+    } else {
+        float4 v[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) v[b] = __ldg(reinterpret_cast<const float4*>(p + (long)b * n));
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            acc += v[b].x;
+            acc += v[b].y;
+            acc += v[b].z;
+            acc += v[b].w;
+        }
+    }
+    return acc * (1.0f / (float)(s * s));
+}
+
 struct PrepTable {
     PrepArgs c[kMaxClasses];
     long ibegin[kMaxClasses + 1];  // cumulative image counts
@@ -132,9 +166,11 @@ __global__ void k_prep_quad(const PrepTable t)
         const int qy = cell / qw, qx = cell - qy * qw;
         const int n = a.n, s = a.s, ns = n / s;
         const float* f = a.fine + inst * n * n;
+        const bool vec = (reinterpret_cast<uintptr_t>(a.fine) & (uintptr_t)(4 * min(s, 4) - 1)) == 0;
         const int ix0 = qx - kPad, iy0 = qy - kPad;
-        const float pa = pooled(f, n, s, ns, ix0, iy0), pb = pooled(f, n, s, ns, ix0 + 1, iy0);
-        const float pc = pooled(f, n, s, ns, ix0, iy0 + 1), pd = pooled(f, n, s, ns, ix0 + 1, iy0 + 1);
+        const float pa = pooled_rows(f, n, s, ns, ix0, iy0, vec), pb = pooled_rows(f, n, s, ns, ix0 + 1, iy0, vec);
+        const float pc = pooled_rows(f, n, s, ns, ix0, iy0 + 1, vec);
+        const float pd = pooled_rows(f, n, s, ns, ix0 + 1, iy0 + 1, vec);
         a.quad[inst * qw * qw + cell] = make_quad(pa, pb, pc, pd);
     }
 }
@@ -174,12 +210,22 @@ __device__ __forceinline__ void k_prep_quad_il_item(const PrepIlTable& t, const 
     const int qy0 = rblk * kIlRows, qx0 = (local - rblk * segs) * kIlCells;
     const int n = a.n, s = a.s, ns = n / s;
     const int cells = min(kIlCells, qw - qx0), rows = min(kIlRows, qw - qy0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+    const bool vec = (reinterpret_cast<uintptr_t>(a.fine) & (uintptr_t)(4 * min(s, 4) - 1)) == 0;
     for (int b0 = 0; b0 < B; b0 += kIlImages) {
         const int nb = min(kIlImages, B - b0);
         if (b0 > 0) __syncthreads();
-        for (int e = threadIdx.x; e < nb * R1 * C1; e += blockDim.x) {
-            const int b = e / (R1 * C1), rem = e - b * R1 * C1, r = rem / C1, cx = rem - r * C1;
-            lv[e] = pooled(a.fine + (long)(b0 + b) * n * n, n, s, ns, qx0 - kPad + cx, qy0 - kPad + r);
+        // a warp stages columns 0..31 of one level row of one image at a time
+        // (lane = column), then one thread per row its 33rd column
+        for (int it = warp; it < nb * R1; it += warps) {
+            const int b = it / R1, r = it - b * R1;
+            lv[it * C1 + lane] = pooled_rows(a.fine + (long)(b0 + b) * n * n, n, s, ns, qx0 - kPad + lane,
+                                             qy0 - kPad + r, vec);
+        }
+        for (int it = threadIdx.x; it < nb * R1; it += blockDim.x) {
+            const int b = it / R1, r = it - b * R1;
+            lv[it * C1 + kIlCells] = pooled_rows(a.fine + (long)(b0 + b) * n * n, n, s, ns, qx0 - kPad + kIlCells,
+                                                 qy0 - kPad + r, vec);
         }
         __syncthreads();
         // thread -> image b = tid % nb (fixed), cells tid / nb, + cstep, ...: two
@@ -197,7 +243,7 @@ __device__ __forceinline__ void k_prep_quad_il_item(const PrepIlTable& t, const 
 }
 
 template <int ROWS>
-__global__ void __launch_bounds__(256) k_prep_quad_il(const PrepIlTable t)
+__global__ void __launch_bounds__(256, 8) k_prep_quad_il(const PrepIlTable t)
 {
     pdl_begin();
     k_prep_quad_il_item<ROWS>(t, (long)blockIdx.x);
@@ -205,7 +251,7 @@ __global__ void __launch_bounds__(256) k_prep_quad_il(const PrepIlTable t)
 
 // persistent form (PNP_RUN_PERSISTENT): as many CTAs as fit at once walk the items
 template <int ROWS>
-__global__ void __launch_bounds__(256) k_prep_quad_il_persistent(const PrepIlTable t)
+__global__ void __launch_bounds__(256, 8) k_prep_quad_il_persistent(const PrepIlTable t)
 {
     pdl_begin();
     const long total = t.begin[t.count];
