@@ -164,3 +164,41 @@ def test_run_with_a_subset_seed_uses_the_seeded_order():
         xa = unrolled_pnp(plan, stages, eta, None, d_b, x0, lam, subset_seed=seed)
         xb = unrolled_pnp(plan, stages, eta, seq_o, d_b, x0, lam)
     assert np.array_equal(host(xa), host(xb))
+
+
+def test_run_many_draws_each_class_order_from_its_own_stages():
+    """pnp_run_many with two classes given no subset sequences: each class takes
+    pnp_subset_sequence(its stages, params.subset_seed), so the call gives the
+    same bits as the same call given the oracle's order for each class's stages;
+    a class given a sequence keeps it.  (Several classes share one denoiser
+    variant per launch, so the comparison is between calls on the same classes.)"""
+    import torch
+    ga = synth.make_geometry(64, 90, 96, batch=2)
+    gb = synth.make_geometry(48, 60, 72, batch=1)
+    pa, pb = pnp.Plan(ga), pnp.Plan(gb)
+    sa = [synth.Stage(2, 4, 3), synth.Stage(1, 5, 6)]
+    sb = [synth.Stage(1, 7, 5)]
+    seed = 991
+    kw = dict(lam=0.02, tv_iters=10, momentum=True)
+    cls = []
+    for g, plan, stages, pid in ((ga, pa, sa, 0), (gb, pb, sb, 1)):
+        xt = np.stack([synth.ellipse_phantom(g.n, 40 + 7 * pid + i, (5, 8)) for i in range(g.batch)])
+        b = torch.empty(g.batch, g.n_views, g.n_det, device="cuda")
+        plan.project(1, dev(xt), b)
+        cls.append(dict(plan=plan, stages=stages, eta=plan.step_sizes(stages), b=b, g=g))
+
+    def call(seqs):
+        xs = [torch.zeros(c["g"].batch, c["g"].n, c["g"].n, device="cuda") for c in cls]
+        pnp.run_many([dict(plan=c["plan"], stages=c["stages"], eta=c["eta"], seq=q, b=c["b"], x=x)
+                      for c, q, x in zip(cls, seqs, xs)], subset_seed=seed, **kw)
+        return [host(x) for x in xs]
+
+    ref = call([oracle.subset_sequence(sa, seed), oracle.subset_sequence(sb, seed)])
+    got = call([None, None])
+    assert all(np.array_equal(u, v) for u, v in zip(got, ref))
+    own = synth.schedule_sequence(sb, 3)
+    assert not np.array_equal(own, oracle.subset_sequence(sb, seed))
+    ref2 = call([oracle.subset_sequence(sa, seed), own])
+    got2 = call([None, own])
+    assert all(np.array_equal(u, v) for u, v in zip(got2, ref2))
+    assert not np.array_equal(got2[1], got[1])
