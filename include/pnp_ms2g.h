@@ -335,8 +335,12 @@ int pnp_run(const pnp_geom* g, const pnp_stage* stages, int n_stages, const doub
  * ONE launch covering up to 4 classes that are still iterating (more classes:
  * one launch per phase for each group of 4, in class order); classes may have
  * schedules of different lengths; iteration i of every class uses the same
- * momentum a_i and params.  A class given without a subset sequence takes
- * the order pnp_subset_sequence draws for its stages from params->subset_seed.
+ * momentum a_i and params.  One denoiser launch serves every class, so the
+ * classes share its variant (the register-resident ones only when every class
+ * was tuned to one); a class whose own tuned variant differs can then differ
+ * from its single-class pnp_run in the last bits (both within the reconstruction
+ * tolerance).  A class given without a subset sequence takes the order
+ * pnp_subset_sequence draws for its stages from params->subset_seed.
  * Workspaces and outputs must be distinct per class.  Synchronous only when some class logs PSNR.  PNP_EUNSUPPORTED for
  * more than 1024 classes.
  * Checkpoint/resume: a class with start_iter = k continues Algorithm 1 from
