@@ -68,6 +68,12 @@ MUTATIONS = [
     ("naive shuffle over the whole range",
      "int r = (int)orc_uniform_below(seed, &t, (uint32_t)(j + 1));",
      "int r = (int)orc_uniform_below(seed, &t, (uint32_t)P);"),
+    ("objective without the 1/2", "out[0] = 0.5 * f;", "out[0] = f;"),
+    ("objective TV anisotropic", "acc += sqrt(a * a + c * c);", "acc += fabs(a) + fabs(c);"),
+    ("objective TV zero past the last row",
+     "double a = i < m - 1 ? x[(i + 1) * m + j] - x[i * m + j] : 0.0;",
+     "double a = i < m - 1 ? x[(i + 1) * m + j] - x[i * m + j] : -x[i * m + j];"),
+    ("psnr of the summed squared error", "mse /= (double)count;", "(void)count;"),
     ("weights on the wrong views", "res[(long)vs * g->n_det + j] *= w[(long)(first + vs * step) * g->n_det + j];",
      "res[(long)vs * g->n_det + j] *= w[(long)vs * g->n_det + j];"),
 ]

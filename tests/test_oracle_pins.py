@@ -460,6 +460,18 @@ def test_tv_of_step_image():
     assert abs(oracle.tv(z) - 10 * 2.0) < 1e-13
 
 
+def test_tv_of_diagonal_ramp_is_isotropic():
+    """Isotropic TV with forward differences and nothing past the last row or
+    column (the denoiser's TV_iso): on x[i, j] = i + 2 j every pixel off the last
+    row and column has gradient (1, 2), norm sqrt 5 (anisotropic TV would give
+    3); the last row has (0, 2), the last column (1, 0), the corner 0:
+    TV = (m-1)^2 sqrt 5 + 2 (m-1) + (m-1)."""
+    m = 9
+    i, j = np.mgrid[0:m, 0:m].astype(np.float64)
+    want = (m - 1) ** 2 * np.sqrt(5.0) + 3.0 * (m - 1)
+    assert abs(oracle.tv(i + 2.0 * j) - want) < 1e-12
+
+
 # ---------------------------------------------------------------- Algorithm 1
 def dense_alg1(A_by_s, S_by_s, stages, eta, seq, b, x0, alpha, lam, tv_iters, momentum, nv):
     """Algorithm 1 with dense A_s and S matrices (U = S^T, subsets = interleaved rows)."""
