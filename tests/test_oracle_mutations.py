@@ -74,6 +74,24 @@ MUTATIONS = [
      "double a = i < m - 1 ? x[(i + 1) * m + j] - x[i * m + j] : 0.0;",
      "double a = i < m - 1 ? x[(i + 1) * m + j] - x[i * m + j] : -x[i * m + j];"),
     ("psnr of the summed squared error", "mse /= (double)count;", "(void)count;"),
+    ("samples at whole steps (half-step offset dropped)",
+     "double t = ((double)k + 0.5) * delta;\n        acc += interp(",
+     "double t = (double)k * delta;\n        acc += interp("),
+    ("contiguous view blocks as subsets", """    int first = P <= 1 ? 0 : p;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int vs = 0; vs < nsub; ++vs) {
+        int v = first + vs * step;
+        for (int j = 0; j < g->n_det; ++j) {
+            double val = ray_sum(g, s, img, v, j);""", """    int first = P <= 1 ? 0 : p;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int vs = 0; vs < nsub; ++vs) {
+        int v = P <= 1 ? vs : first * nsub + vs; (void)step;
+        for (int j = 0; j < g->n_det; ++j) {
+            double val = ray_sum(g, s, img, v, j);"""),
+    ("fgp momentum sequence without the 4", """        /* t_{k+1} and the momentum point (r_{k+1}, s_{k+1}) */
+        double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));""", """        /* t_{k+1} and the momentum point (r_{k+1}, s_{k+1}) */
+        double tn = 0.5 * (1.0 + sqrt(1.0 + t * t));"""),
+    ("keys kernel a = -3/4", "const double a = -0.5;", "const double a = -0.75;"),
     ("weights on the wrong views", "res[(long)vs * g->n_det + j] *= w[(long)(first + vs * step) * g->n_det + j];",
      "res[(long)vs * g->n_det + j] *= w[(long)vs * g->n_det + j];"),
 ]
