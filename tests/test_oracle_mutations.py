@@ -92,6 +92,12 @@ MUTATIONS = [
         double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));""", """        /* t_{k+1} and the momentum point (r_{k+1}, s_{k+1}) */
         double tn = 0.5 * (1.0 + sqrt(1.0 + t * t));"""),
     ("keys kernel a = -3/4", "const double a = -0.5;", "const double a = -0.75;"),
+    ("source at the detector distance", "double sx = g->dso * cb, sy = g->dso * sb;",
+     "double sx = g->ddo * cb, sy = g->ddo * sb;"),
+    ("pixel centres half a pixel off",
+     "    double X = qx / s + 0.5 * (ns - 1), Y = qy / s + 0.5 * (ns - 1);\n    double fx = floor(X), fy = floor(Y);\n    double val = 0.0;",
+     "    double X = qx / s + 0.5 * ns, Y = qy / s + 0.5 * ns;\n    double fx = floor(X), fy = floor(Y);\n    double val = 0.0;"),
+    ("residual sign flipped", "if (b) val -= b[(long)v * g->n_det + j];", "if (b) val = b[(long)v * g->n_det + j] - val;"),
     ("weights on the wrong views", "res[(long)vs * g->n_det + j] *= w[(long)(first + vs * step) * g->n_det + j];",
      "res[(long)vs * g->n_det + j] *= w[(long)vs * g->n_det + j];"),
 ]

@@ -178,6 +178,26 @@ def test_paraboloid_closed_form_and_order():
     assert math.log2(errs[0] / errs[2]) / 2 > 1.6, errs
 
 
+def test_paraboloid_closed_form_unequal_distances():
+    """The paraboloid's closed form again with the source and the detector at
+    different distances (source 3n from the centre, detector n on the other
+    side), so that each ray's distance from the centre depends on both: an
+    exchanged distance or magnification moves every off-centre ray."""
+    n = 64
+    g = synth.make_geometry(n, 8, 64, dso_ratio=3.0, ddo_ratio=1.0)
+    r = 0.3 * n
+    X, Y = pixel_centres(n)
+    img = np.clip(r * r - X ** 2 - Y ** 2, 0, None) / (r * r)
+    sino = oracle.project(g, 1, img)
+    exact = np.zeros_like(sino)
+    for v in range(g.n_views):
+        for j in range(g.n_det):
+            S, P = ray_endpoints(g, v, j)
+            p = line_distance((0.0, 0.0), S, P)
+            exact[v, j] = (4.0 / 3.0) * max(r * r - p * p, 0.0) ** 1.5 / (r * r)
+    assert np.abs(sino - exact).max() / exact.max() < 1e-2
+
+
 def test_axis_rays_are_row_and_column_sums():
     """With an odd grid and an odd detector the central ray of the view at 0 runs
     along the middle row and the one at 90 degrees along the middle column; the
