@@ -98,6 +98,7 @@ MUTATIONS = [
      "    double X = qx / s + 0.5 * (ns - 1), Y = qy / s + 0.5 * (ns - 1);\n    double fx = floor(X), fy = floor(Y);\n    double val = 0.0;",
      "    double X = qx / s + 0.5 * ns, Y = qy / s + 0.5 * ns;\n    double fx = floor(X), fy = floor(Y);\n    double val = 0.0;"),
     ("residual sign flipped", "if (b) val -= b[(long)v * g->n_det + j];", "if (b) val = b[(long)v * g->n_det + j] - val;"),
+    ("uneven subsets rounded down", "return (g->n_views - p + P - 1) / P;", "return g->n_views / P;"),
     ("weights on the wrong views", "res[(long)vs * g->n_det + j] *= w[(long)(first + vs * step) * g->n_det + j];",
      "res[(long)vs * g->n_det + j] *= w[(long)vs * g->n_det + j];"),
 ]
