@@ -178,9 +178,9 @@ __global__ void k_prep_quad(const PrepTable t)
 // Image-interleaved coefficient image, quad[(qy * qw + qx) * B + b].  A CTA
 // builds ROWS x kIlCells cells for all B images of its class: it stages the
 // ROWS + 1 level-image rows those cells read (pooled for s > 1) in shared
-// memory, 64 / ROWS images at a time, then writes the cells with the image
-// index fastest, so that both the image reads and the cell writes are
-// contiguous.  ROWS = 4 for level images of 256 or more (each staged row serves
+// memory, 64 images at a time for ROWS = 1 and 32 for ROWS = 4 (a warp per
+// staged row of one image), then writes the cells with the image index
+// fastest, so that both the image reads and the cell writes are contiguous.  ROWS = 4 for level images of 256 or more (each staged row serves
 // two rows of cells, and a CTA's fixed costs spread over four times the cells:
 // 39 -> 29 us at 16 x 512^2), 1 below (enough CTAs for the small images).
 constexpr int kIlCells = 32;
